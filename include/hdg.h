@@ -1,0 +1,192 @@
+/*
+ * hdg.h - C ABI of the GB300 HDG trace solver for the implicit, linearised,
+ * rotating shallow-water step
+ *
+ *      u + tau (f u_perp + g grad h) = r_u,      h + tau H div u = r_h,
+ *
+ * discretised with the upwind hybridised DG method of Betteridge, Gibson,
+ * Graham & Mueller, "Multigrid preconditioners for the hybridised
+ * discontinuous Galerkin discretisation of the shallow water equations"
+ * (arXiv 2004.09389): cell fields u in [P^p(K)]^2, h in P^p(K), a scalar
+ * trace lambda in P^p(e) on every facet (Eq. DG_space_def, Eq. DG_trace_def),
+ * the upwind HDG form of Eq. bilinear_HDG_upwind written with tau for
+ * alpha*Delta t, g for c_g*phi_B, H for c_g and tau_s = sqrt(g H) for
+ * c_g*sqrt(phi_B), plus the Coriolis term taken implicitly.
+ *
+ * A solve is the three steps of Sec. 4.2: condensed right-hand side
+ * (step 1), the trace system S lambda = g (Eq. schur_system, step 2, solved by
+ * FGMRES preconditioned with the non-nested two-level V-cycle of
+ * Alg. twolevel_vcycle whose coarse space is P1, Sec. 4.4), and local
+ * recovery of (u, h) (Eq. reconstruct_solution, step 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Mesh: triangles, cell_vertices counter-clockwise (seen from outside on the
+ *   sphere).  Flat periodic meshes (dim = 2) give wrapped vertex coordinates
+ *   plus cell_shift[K][i][2] offsets that unwrap vertex i of cell K.  Sphere
+ *   meshes (dim = 3) give 3-D vertices; every cell is the flat triangle
+ *   through its vertices.
+ * Cell unknowns: n_p = (p+1)(p+2)/2 Lagrange nodes per cell; node k runs row
+ *   by row (b = 0..p outer, a = 0..p-b inner) at X0 + (a/p)(X1-X0) +
+ *   (b/p)(X2-X0).  Velocities are Cartesian (flat) or in the cell frame
+ *   e1 = (X1-X0)/|X1-X0|, e2 = n x e1 (sphere).
+ *   r_u, u: double [n_cells][2][n_p];  r_h, h: double [n_cells][n_p]
+ *   (nodal values of the right-hand-side functions / of the solution).
+ * Facets: numbered in order of first appearance over (cell, local edge),
+ *   local edge i being opposite local vertex i.  The p+1 trace nodes of a
+ *   facet are equispaced, endpoints included, from its lower global vertex id
+ *   to the higher.  lambda: double [n_facets][p+1].
+ *
+ * Ownership and errors: the caller owns every buffer it passes; the library
+ * copies what it keeps.  The handle owns its device memory.  Every function
+ * returns HDG_OK (0) or a negative HDG_E* code; hdg_last_error() describes
+ * the last failure on a handle.  A handle must not be used by two host
+ * threads at once.  Host-pointer entry points copy to and from the device
+ * and synchronise; *_dev entry points take device pointers, run on the
+ * handle's stream and return once the work is enqueued (they synchronise only
+ * where a result decides the control flow, e.g. the convergence test).
+ */
+#ifndef HDG_H
+#define HDG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HDG_API __attribute__((visibility("default")))
+#else
+#define HDG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HDG_OK          0
+#define HDG_EINVAL     -1   /* bad argument: sizes, p outside 1..4, tau <= 0, mesh not closed ... */
+#define HDG_ESINGULAR  -2   /* a zero pivot in a cell or facet block factorisation            */
+#define HDG_ENOCONV    -3   /* max_iter reached; lambda holds the last iterate                */
+#define HDG_EBREAKDOWN -4   /* Krylov breakdown without convergence                           */
+#define HDG_ENAN       -5   /* NaN or Inf met in the iteration or the input                   */
+#define HDG_ECUDA      -6   /* a CUDA runtime call failed                                     */
+#define HDG_ETIMEOUT   -7   /* a bounded device-side wait ran out                             */
+#define HDG_ENOMEM     -8   /* device allocation failed                                       */
+#define HDG_ESTATE     -9   /* call out of order (e.g. solve before condense)                 */
+
+#define HDG_FP64        0   /* every step in double precision                                 */
+#define HDG_MIXED_FP32  1   /* FP32 inner FGMRES + V-cycle, FP64 iterative refinement         */
+
+typedef struct hdg_handle hdg_handle;
+
+/* One mesh level.  For coarse P1 levels, parent[i] = (a, b) says that vertex i
+ * of the next finer level lies at the midpoint of this level's vertices a and
+ * b (a == b: the vertex exists on both levels).  parent is ignored on the
+ * fine level. */
+typedef struct {
+    int32_t        n_vertices;
+    int32_t        n_cells;
+    int32_t        dim;            /* 2: flat periodic, 3: sphere                   */
+    const double  *vertex_xyz;     /* [n_vertices][dim]                              */
+    const int32_t *cell_vertices;  /* [n_cells][3]                                   */
+    const double  *cell_shift;     /* [n_cells][3][2] (dim 2) or NULL                */
+    const int32_t *parent;         /* [n_vertices of next finer level][2] or NULL    */
+} hdg_mesh_level;
+
+typedef struct {
+    hdg_mesh_level        fine;
+    int32_t               n_coarse;   /* number of coarse P1 levels (0: P1 on the fine mesh only) */
+    const hdg_mesh_level *coarse;     /* [n_coarse], next-coarser first                         */
+} hdg_mesh_desc;
+
+typedef struct {
+    int32_t       p;            /* polynomial degree, 1..4                               */
+    double        tau;          /* alpha * Delta t > 0                                   */
+    double        g, H;         /* gravity and mean depth (> 0)                          */
+    double        tau_s;        /* upwind stabilisation; <= 0 selects sqrt(g H)          */
+    const double *f_vertex;     /* Coriolis parameter at fine vertices, P1 per cell; NULL = 0 */
+    int32_t       precision;    /* HDG_FP64 or HDG_MIXED_FP32                            */
+    double        rtol;         /* stop at ||g - S lambda|| <= rtol ||g|| (FP64 residual) */
+    int32_t       restart;      /* FGMRES restart length m (1..64)                        */
+    int32_t       max_iter;     /* total Krylov iterations allowed                        */
+    int32_t       n_pre, n_post;/* block-Jacobi sweeps before / after the coarse correction */
+    double        omega;        /* block-Jacobi damping                                   */
+    int32_t       p1_nu_pre, p1_nu_post; /* Jacobi sweeps per level of the P1 V-cycle     */
+    double        p1_omega;     /* Jacobi damping of the P1 V-cycle                       */
+    double        inner_rtol;   /* HDG_MIXED_FP32: relative tolerance of each inner solve */
+} hdg_params;
+
+typedef struct {
+    int32_t iters;            /* Krylov iterations (inner iterations in mixed mode)    */
+    int32_t outer;            /* restarts (FP64) / refinement steps (mixed)            */
+    int32_t status;           /* same code as the return value                         */
+    int32_t fallback_used;    /* reserved: 1 if a fallback preconditioner took over    */
+    double  true_rel_res;     /* ||g - S lambda|| / ||g|| in FP64 at exit              */
+    double  est_rel_res;      /* last Arnoldi residual estimate                        */
+} hdg_solve_info;
+
+/* Fill *prm with the defaults: p = 1, tau = 1, g = H = 1, tau_s = sqrt(gH),
+ * FP64, rtol 1e-8, restart 30, max_iter 500, 2 + 2 sweeps, omega = 2/3,
+ * 2 + 2 P1 sweeps, p1_omega = 2/3, inner_rtol 1e-4. */
+HDG_API void hdg_default_params(hdg_params *prm);
+
+/* Build a handle: validate and copy the mesh (facet numbering, orientation,
+ * cell frames, P1 hierarchy and its geometric mass / stiffness matrices) to
+ * the device.  stream: a cudaStream_t to run on, or NULL for a new
+ * non-blocking stream owned by the handle.  On failure *out is NULL and the
+ * error text is available from hdg_last_error(NULL). */
+HDG_API int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hdg_handle **out);
+
+/* (Re)build the cell operators for the handle's parameters: for every cell the
+ * local blocks A_K, B_K, C_K and tau_s M_dK of the ABCM split (Eq. ABCMform,
+ * App. B), A_K^-1 B_K, A_K^-1 M_K, S_K = tau_s M_dK + C_K A_K^-1 B_K and
+ * C_K A_K^-1 M_K; then the facet-row trace operator (the S_K summed onto the
+ * facets), the inverted facet diagonal blocks of the block-Jacobi smoother and
+ * the P1 level operators (Eq. coarse_problem_upwind, divided by tau).
+ * HDG_ESINGULAR if a cell or facet block has a zero pivot. */
+HDG_API int hdg_condense(hdg_handle *h);
+
+/* Change tau (and with it the operators); equivalent to a new hdg_condense. */
+HDG_API int hdg_set_tau(hdg_handle *h, double tau);
+
+/* Steps 1 and 2 with host buffers: r_u, r_h in, lambda out ([n_facets][p+1]).
+ * info may be NULL.  Returns HDG_ENOCONV / HDG_EBREAKDOWN / HDG_ENAN with the
+ * last iterate in lambda. */
+HDG_API int hdg_solve(hdg_handle *h, const double *r_u, const double *r_h, double *lambda,
+              hdg_solve_info *info);
+/* The same with device pointers. */
+HDG_API int hdg_solve_dev(hdg_handle *h, const double *r_u, const double *r_h, double *lambda,
+                  hdg_solve_info *info);
+
+/* Step 3 with host buffers: (u, h) from lambda and the right-hand side.
+ * lambda may be NULL to use the handle's last solution; r_u / r_h may be NULL
+ * to use the right-hand side of the handle's last solve. */
+HDG_API int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lambda,
+                double *u, double *h_out);
+HDG_API int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h, const double *lambda,
+                    double *u, double *h_out);
+
+/* Operator entry points on device vectors in the lambda layout [n_facets][p+1]. */
+/* y = S x, S the assembled trace operator of Eq. schur_system. */
+HDG_API int hdg_trace_apply_dev(hdg_handle *h, const double *x, double *y);
+/* g = sum_K P_K^T C_K A_K^-1 F_K, the condensed right-hand side of step 1. */
+HDG_API int hdg_condensed_rhs_dev(hdg_handle *h, const double *r_u, const double *r_h, double *g);
+/* z = V(v): one application of the two-level V-cycle (Alg. twolevel_vcycle)
+ * with zero initial guess. */
+HDG_API int hdg_precond_apply_dev(hdg_handle *h, const double *v, double *z);
+
+/* Inspection (host buffers) for checking against an independent code. */
+/* sizes[0..5] = n_cells, n_facets, n_trace, n_p, 3(p+1), number of P1 levels. */
+HDG_API int hdg_get_sizes(const hdg_handle *h, int64_t *sizes);
+/* facet_of [n_cells][3], flip [n_cells][3] (1: local edge runs high -> low id),
+ * facet_verts [n_facets][2] (lo, hi).  Any pointer may be NULL. */
+HDG_API int hdg_get_facets(const hdg_handle *h, int32_t *facet_of, int32_t *flip, int32_t *facet_verts);
+/* Per-cell S_K in the local trace order (edge i, node j along the edge from
+ * local vertex (i+1)%3 to (i+2)%3), [n_cells][3(p+1)][3(p+1)].  Needs condense. */
+HDG_API int hdg_get_cell_schur(hdg_handle *h, double *S);
+
+HDG_API int hdg_destroy(hdg_handle *h);
+HDG_API const char *hdg_last_error(const hdg_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDG_H */

@@ -214,7 +214,7 @@ class HDGProblem:
     monolithic and condensed systems."""
 
     def __init__(self, mesh, p: int, tau: float, g: float, H: float,
-                 f_vertex: np.ndarray, tau_s: float | None = None):
+                 f_vertex: np.ndarray, tau_s: float | None = None, lazy: bool = False):
         self.md = MeshData.of(mesh)
         self.prm = Params(p, tau, g, H, np.sqrt(g * H) if tau_s is None else tau_s)
         self.f_vertex = np.asarray(f_vertex, np.float64)
@@ -227,10 +227,23 @@ class HDGProblem:
         self.m = 3 * (p + 1)
         self.n_trace = self.n_facets * (p + 1)
         self.gdof = trace_dof_map(self.facet_of, self.flip, p)
-        self.ops = []
-        for K in range(self.N):
+        # cell operators, built on first use when lazy (large meshes checked on samples)
+        self._ops: dict[int, tuple] = {}
+        if not lazy:
+            for K in range(self.N):
+                self.op(K)
+
+    def op(self, K: int):
+        """(A_K, B_K, C_K, Mt_K, Mass_K) of cell K."""
+        K = int(K)
+        if K not in self._ops:
             fK = self.f_vertex[self.md.cell_vertices[K]]
-            self.ops.append(local_operators(self.X[K], fK, self.prm))
+            self._ops[K] = local_operators(self.X[K], fK, self.prm)
+        return self._ops[K]
+
+    @property
+    def ops(self):
+        return [self.op(K) for K in range(self.N)]
 
     # -- input layout helpers
     def cell_rhs(self, r_u: np.ndarray, r_h: np.ndarray) -> np.ndarray:
@@ -240,7 +253,49 @@ class HDGProblem:
     def load(self, r_u, r_h) -> np.ndarray:
         """F_K = Mass_K r_K (the Riesz map of the RHS functions)."""
         rc = self.cell_rhs(r_u, r_h)
-        return np.stack([self.ops[K][4] @ rc[K] for K in range(self.N)])
+        return np.stack([self.op(K)[4] @ rc[K] for K in range(self.N)])
+
+    def local_cells(self, cells, r_u, r_h, lam):
+        """Step 3 for selected cells only: q_K = A_K^-1 (Mass_K r_K - B_K lambda_K)."""
+        out = []
+        for K in cells:
+            A, B, C, Mt, Mass = self.op(K)
+            rK = np.concatenate([r_u[K, 0], r_u[K, 1], r_h[K]])
+            out.append(np.linalg.solve(A, Mass @ rK - B @ lam[self.gdof[K]]))
+        return np.array(out)
+
+    def facet_rows(self, facets, x):
+        """(S x) restricted to the trace dofs of the selected facets, from the
+        S_K of their two cells."""
+        pp = self.prm.p + 1
+        cells_of = {}
+        for K in range(self.N):
+            for i in range(3):
+                cells_of.setdefault(int(self.facet_of[K, i]), []).append(K)
+        out = []
+        for e in facets:
+            y = np.zeros(self.n_trace)
+            for K in cells_of[int(e)]:
+                np.add.at(y, self.gdof[K], self.cell_schur(K) @ x[self.gdof[K]])
+            out.append(y[int(e) * pp:(int(e) + 1) * pp])
+        return np.array(out)
+
+    def facet_rhs(self, facets, r_u, r_h):
+        """Step 1 restricted to the selected facets."""
+        pp = self.prm.p + 1
+        cells_of = {}
+        for K in range(self.N):
+            for i in range(3):
+                cells_of.setdefault(int(self.facet_of[K, i]), []).append(K)
+        out = []
+        for e in facets:
+            gl = np.zeros(self.n_trace)
+            for K in cells_of[int(e)]:
+                A, B, C, Mt, Mass = self.op(K)
+                rK = np.concatenate([r_u[K, 0], r_u[K, 1], r_h[K]])
+                np.add.at(gl, self.gdof[K], C @ np.linalg.solve(A, Mass @ rK))
+            out.append(gl[int(e) * pp:(int(e) + 1) * pp])
+        return np.array(out)
 
     # -- route (i): the monolithic system
     def monolithic(self):
@@ -248,7 +303,7 @@ class HDGProblem:
         nq = N * nK
         rows, cols, vals = [], [], []
         for K in range(N):
-            A, B, C, Mt, _ = self.ops[K]
+            A, B, C, Mt, _ = self.op(K)
             q0 = K * nK
             qi = q0 + np.arange(nK)
             li = nq + self.gdof[K]
@@ -275,7 +330,7 @@ class HDGProblem:
     # -- route (ii): Schur complement (Sec. 4.2, steps 1-3)
     def cell_schur(self, K: int) -> np.ndarray:
         """S_K = Mt_K + C_K A_K^-1 B_K (local trace order)."""
-        A, B, C, Mt, _ = self.ops[K]
+        A, B, C, Mt, _ = self.op(K)
         return Mt + C @ np.linalg.solve(A, B)
 
     def trace_operator(self) -> sp.csr_matrix:
@@ -293,7 +348,7 @@ class HDGProblem:
         F = self.load(r_u, r_h)
         gvec = np.zeros(self.n_trace)
         for K in range(self.N):
-            A, B, C, Mt, _ = self.ops[K]
+            A, B, C, Mt, _ = self.op(K)
             np.add.at(gvec, self.gdof[K], C @ np.linalg.solve(A, F[K]))
         return gvec
 
@@ -302,7 +357,7 @@ class HDGProblem:
         F = self.load(r_u, r_h)
         q = np.empty((self.N, self.nK))
         for K in range(self.N):
-            A, B, C, Mt, _ = self.ops[K]
+            A, B, C, Mt, _ = self.op(K)
             q[K] = np.linalg.solve(A, F[K] - B @ lam[self.gdof[K]])
         return self.split(q)
 
@@ -314,7 +369,7 @@ class HDGProblem:
 
     # -- quantities used by the pins
     def cell_mass(self, K: int) -> np.ndarray:
-        return self.ops[K][4][2 * self.np:, 2 * self.np:]
+        return self.op(K)[4][2 * self.np:, 2 * self.np:]
 
     def integral_of_h(self, h: np.ndarray) -> float:
         R = ref.reference_matrices(self.prm.p)

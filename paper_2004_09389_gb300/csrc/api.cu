@@ -1,0 +1,851 @@
+// C ABI of the HDG trace solver: handle lifecycle, condensation, the
+// two-level preconditioner, the Krylov drivers and the entry points of hdg.h.
+//
+// Solve (Sec. 4.2): step 1 builds g = sum_K P_K^T C_K A_K^-1 F_K; step 2 solves
+// S lambda = g (Eq. schur_system) with right-preconditioned FGMRES whose
+// preconditioner is one pass of Alg. twolevel_vcycle (zero initial guess):
+// n_pre block-Jacobi sweeps, residual, restriction to P1 (pi^T), a geometric
+// P1 V-cycle for the coarse problem of Eq. coarse_problem_upwind, prolongation
+// (pi) and n_post sweeps.  Step 3 recovers (u, h) cell by cell.
+// HDG_MIXED_FP32 runs step 2 as FP64 iterative refinement: the residual
+// g - S lambda and the update of lambda are FP64, each correction comes from an
+// FP32 FGMRES on the FP32 copy of the operator and preconditioner.
+#include "common.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+namespace hdg {
+
+template <typename T> cudaError_t launch_apply_t(hdg_handle *, const T *, T *);
+template <typename T> cudaError_t launch_residual_t(hdg_handle *, const T *, const T *, T *);
+template <typename T> cudaError_t launch_smooth_t(hdg_handle *, const T *, const T *, T *);
+template <typename T> cudaError_t launch_smooth_first_t(hdg_handle *, const T *, T *);
+template <typename T> cudaError_t launch_restrict_t(hdg_handle *, const T *, T *);
+template <typename T> cudaError_t launch_prolong_add_t(hdg_handle *, const T *, T *);
+
+// Krylov vectors of one precision
+template <typename T>
+struct KSpace {
+    T *V = nullptr, *Z = nullptr, *w = nullptr;      // (m+1) x NT, m x NT, NT
+    T *t0 = nullptr, *t1 = nullptr, *res = nullptr;  // preconditioner work
+    T *b = nullptr, *x = nullptr;                    // right-hand side / solution (FP32 inner solve)
+};
+
+struct Workspace {
+    int m = 0;
+    size_t NT = 0;
+    int nchunk = 1;
+    double *g = nullptr, *x = nullptr, *r = nullptr, *ycell = nullptr;
+    KSpace<double> k64;
+    KSpace<float> k32;
+    // small device arrays
+    double *Hm = nullptr, *cs = nullptr, *sn = nullptr, *sv = nullptr, *h1 = nullptr, *h2 = nullptr;
+    double *nrm2 = nullptr, *est = nullptr, *y = nullptr, *partial = nullptr;
+    int32_t *flags = nullptr;
+    // pinned readback
+    double *host_buf = nullptr;   // [4]
+    int32_t *host_flags = nullptr;
+    // staging for host-pointer entry points and for recover defaults
+    double *ru = nullptr, *rh = nullptr, *lam_ext = nullptr, *u = nullptr, *hh = nullptr;
+    bool have_rhs = false, have_lambda = false;
+    double *lam_int = nullptr;    // last solution, internal layout
+};
+
+}  // namespace hdg
+
+using namespace hdg;
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+int fail(hdg_handle *h, int code, const std::string &msg) {
+    if (h) h->err = msg;
+    else g_setup_error = msg;
+    return code;
+}
+
+#define TRY(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(h, HDG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+}
+template <typename T>
+cudaError_t upload(T **p, const std::vector<T> &v, cudaStream_t s) {
+    cudaError_t e = dalloc(p, v.size());
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+std::string check_params(const hdg_params *prm) {
+    if (!prm) return "params is NULL";
+    if (prm->p < 1 || prm->p > 4) return "p must be in 1..4";
+    if (!(prm->tau > 0) || !(prm->g > 0) || !(prm->H > 0)) return "tau, g and H must be positive";
+    if (!(prm->rtol > 0)) return "rtol must be positive";
+    if (prm->restart < 1 || prm->restart > 64) return "restart must be in 1..64";
+    if (prm->max_iter < 1) return "max_iter must be positive";
+    if (prm->n_pre < 0 || prm->n_post < 0 || prm->p1_nu_pre < 0 || prm->p1_nu_post < 0) return "negative sweep count";
+    if (!(prm->omega > 0) || !(prm->p1_omega > 0)) return "damping factors must be positive";
+    if (prm->precision != HDG_FP64 && prm->precision != HDG_MIXED_FP32) return "unknown precision mode";
+    if (prm->precision == HDG_MIXED_FP32 && !(prm->inner_rtol > 0 && prm->inner_rtol < 1)) return "inner_rtol must be in (0, 1)";
+    return "";
+}
+
+// ---------------------------------------------------------------- preconditioner
+
+template <typename T>
+const T *levA(const DevLevel &L);
+template <>
+const double *levA<double>(const DevLevel &L) { return L.A; }
+template <>
+const float *levA<float>(const DevLevel &L) { return L.A32; }
+template <typename T>
+const T *levD(const DevLevel &L);
+template <>
+const double *levD<double>(const DevLevel &L) { return L.dinv; }
+template <>
+const float *levD<float>(const DevLevel &L) { return L.dinv32; }
+template <typename T>
+T *levX(DevLevel &L);
+template <>
+double *levX<double>(DevLevel &L) { return L.x; }
+template <>
+float *levX<float>(DevLevel &L) { return L.x32; }
+template <typename T>
+T *levX2(DevLevel &L);
+template <>
+double *levX2<double>(DevLevel &L) { return L.x2; }
+template <>
+float *levX2<float>(DevLevel &L) { return L.x232; }
+template <typename T>
+T *levB(DevLevel &L);
+template <>
+double *levB<double>(DevLevel &L) { return L.b; }
+template <>
+float *levB<float>(DevLevel &L) { return L.b32; }
+template <typename T>
+T *levR(DevLevel &L);
+template <>
+double *levR<double>(DevLevel &L) { return L.r; }
+template <>
+float *levR<float>(DevLevel &L) { return L.r32; }
+template <typename T>
+const T *coarse_inv(hdg_handle *h);
+template <>
+const double *coarse_inv<double>(hdg_handle *h) { return h->d_coarse_inv; }
+template <>
+const float *coarse_inv<float>(hdg_handle *h) { return h->d_coarse_inv32; }
+template <typename T>
+KSpace<T> &kspace(hdg_handle *h);
+template <>
+KSpace<double> &kspace<double>(hdg_handle *h) { return h->ws->k64; }
+template <>
+KSpace<float> &kspace<float>(hdg_handle *h) { return h->ws->k32; }
+
+// P1 V-cycle on level l: solve A_l x = b_l approximately; result in levX(l)
+template <typename T>
+cudaError_t p1_vcycle(hdg_handle *h, int l) {
+    DevLevel &L = h->lev[l];
+    cudaStream_t s = h->stream;
+    const int last = int(h->lev.size()) - 1;
+    if (l == last) return launch_dense_apply<T>(coarse_inv<T>(h), L.nv, levB<T>(L), levX<T>(L), s);
+    const T om = T(h->prm.p1_omega);
+    const T *A = levA<T>(L), *D = levD<T>(L);
+    T *x = levX<T>(L), *x2 = levX2<T>(L), *b = levB<T>(L), *r = levR<T>(L);
+    cudaError_t e;
+    int nu1 = h->prm.p1_nu_pre, nu2 = h->prm.p1_nu_post;
+    if (nu1 == 0) {
+        if ((e = launch_fill<T>(x, T(0), L.nv, s)) != cudaSuccess) return e;
+    } else {
+        if ((e = launch_p1_jacobi<T>(L, A, D, b, x, x, om, true, s)) != cudaSuccess) return e;
+        for (int k = 1; k < nu1; ++k) {
+            if ((e = launch_p1_jacobi<T>(L, A, D, b, x, x2, om, false, s)) != cudaSuccess) return e;
+            std::swap(x, x2);
+        }
+    }
+    if ((e = launch_p1_residual<T>(L, A, b, x, r, s)) != cudaSuccess) return e;
+    DevLevel &C = h->lev[l + 1];
+    if ((e = launch_p1_restrict<T>(C, r, levB<T>(C), s)) != cudaSuccess) return e;
+    if ((e = p1_vcycle<T>(h, l + 1)) != cudaSuccess) return e;
+    if ((e = launch_p1_prolong_add<T>(C, L.nv, levX<T>(C), x, s)) != cudaSuccess) return e;
+    for (int k = 0; k < nu2; ++k) {
+        if ((e = launch_p1_jacobi<T>(L, A, D, b, x, x2, om, false, s)) != cudaSuccess) return e;
+        std::swap(x, x2);
+    }
+    // make the result land in the level's primary buffer
+    if (x != levX<T>(L))
+        return cudaMemcpyAsync(levX<T>(L), x, sizeof(T) * L.nv, cudaMemcpyDeviceToDevice, s);
+    return cudaSuccess;
+}
+
+// z = V(v), Alg. twolevel_vcycle with zero initial guess (internal layout)
+template <typename T>
+cudaError_t precond(hdg_handle *h, const T *v, T *z) {
+    KSpace<T> &k = kspace<T>(h);
+    cudaStream_t s = h->stream;
+    const size_t NT = h->NT;
+    T *x = k.t0, *x2 = k.t1;
+    cudaError_t e;
+    if (h->prm.n_pre == 0) {
+        if ((e = launch_fill<T>(x, T(0), NT, s)) != cudaSuccess) return e;
+    } else {
+        if ((e = launch_smooth_first_t<T>(h, v, x)) != cudaSuccess) return e;
+        for (int i = 1; i < h->prm.n_pre; ++i) {
+            if ((e = launch_smooth_t<T>(h, v, x, x2)) != cudaSuccess) return e;
+            std::swap(x, x2);
+        }
+    }
+    if ((e = launch_residual_t<T>(h, v, x, k.res)) != cudaSuccess) return e;
+    DevLevel &L0 = h->lev[0];
+    if ((e = launch_restrict_t<T>(h, k.res, levB<T>(L0))) != cudaSuccess) return e;
+    if ((e = p1_vcycle<T>(h, 0)) != cudaSuccess) return e;
+    if ((e = launch_prolong_add_t<T>(h, levX<T>(L0), x)) != cudaSuccess) return e;
+    const int np = h->prm.n_post;
+    for (int i = 0; i < np; ++i) {
+        T *out = (i == np - 1) ? z : x2;
+        if ((e = launch_smooth_t<T>(h, v, x, out)) != cudaSuccess) return e;
+        if (i < np - 1) std::swap(x, x2);
+    }
+    if (np == 0) return cudaMemcpyAsync(z, x, sizeof(T) * NT, cudaMemcpyDeviceToDevice, s);
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- Krylov helpers
+
+template <typename T>
+cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out) {
+    Workspace &W = *h->ws;
+    cudaError_t e = launch_multidot<T>(V, W.NT, k, w, W.NT, W.partial, W.nchunk, h->stream);
+    if (e != cudaSuccess) return e;
+    return launch_reduce_partials(W.partial, k, W.nchunk, out, h->stream);
+}
+
+template <typename T>
+int norm_host(hdg_handle *h, const T *v, double &out) {
+    Workspace &W = *h->ws;
+    TRY(dots<T>(h, v, 1, v, W.nrm2));
+    TRY(cudaMemcpyAsync(W.host_buf, W.nrm2, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    TRY(cudaStreamSynchronize(h->stream));
+    out = std::sqrt(W.host_buf[0]);
+    return HDG_OK;
+}
+
+// One FGMRES cycle (at most m iterations, possibly fewer) on S x = b starting
+// from x, with the current residual r0 = b - S x of norm beta already in
+// k.V[0] (scaled).  Stops when the estimate drops below tol_abs / bnorm.
+// Returns the number of iterations; x is updated.
+template <typename T>
+int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_target, int max_it, int &its_done,
+                 double &est_out, int &flag_out) {
+    Workspace &W = *h->ws;
+    KSpace<T> &k = kspace<T>(h);
+    cudaStream_t s = h->stream;
+    const size_t NT = W.NT;
+    const int m = W.m, ldh = m + 1;
+    its_done = 0;
+    flag_out = 0;
+    est_out = beta / bnorm;
+    // s = [beta, 0, ...]
+    TRY(cudaMemsetAsync(W.sv, 0, sizeof(double) * (m + 1), s));
+    TRY(cudaMemsetAsync(W.Hm, 0, sizeof(double) * (m + 1) * m, s));
+    double hb = beta;
+    TRY(cudaMemcpyAsync(W.sv, &hb, sizeof(double), cudaMemcpyHostToDevice, s));
+    int j = 0;
+    for (; j < m && j < max_it; ++j) {
+        T *vj = k.V + size_t(j) * NT, *zj = k.Z + size_t(j) * NT;
+        TRY(precond<T>(h, vj, zj));
+        TRY(launch_apply_t<T>(h, zj, k.w));
+        // classical Gram-Schmidt, twice
+        TRY(dots<T>(h, k.V, j + 1, k.w, W.h1));
+        TRY(launch_multi_axpy<T>(k.w, k.V, NT, j + 1, W.h1, -1.0, NT, s));
+        TRY(dots<T>(h, k.V, j + 1, k.w, W.h2));
+        TRY(launch_multi_axpy<T>(k.w, k.V, NT, j + 1, W.h2, -1.0, NT, s));
+        TRY(dots<T>(h, k.w, 1, k.w, W.nrm2));
+        double *Hcol = W.Hm + size_t(j) * ldh;
+        TRY(launch_arnoldi_finish(Hcol, W.h1, W.h2, W.nrm2, j, s));
+        TRY(launch_scale_copy<T>(k.w, k.V + size_t(j + 1) * NT, Hcol + j + 1, NT, s));
+        TRY(launch_givens(W.Hm, ldh, W.cs, W.sn, W.sv, j, bnorm, W.est, W.flags, s));
+        TRY(cudaMemcpyAsync(W.host_buf, W.est, sizeof(double), cudaMemcpyDeviceToHost, s));
+        TRY(cudaMemcpyAsync(W.host_flags, W.flags, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        TRY(cudaStreamSynchronize(s));
+        est_out = W.host_buf[0];
+        flag_out = W.host_flags[0];
+        if (est_out <= rel_target || (flag_out & 6)) { ++j; break; }
+    }
+    its_done = j;
+    if (j > 0 && !(flag_out & 4)) {
+        TRY(launch_hessenberg_solve(W.Hm, ldh, W.sv, j, W.y, s));
+        TRY(launch_multi_axpy<T>(x, k.Z, NT, j, W.y, 1.0, NT, s));
+    }
+    return HDG_OK;
+}
+
+// Full FGMRES(m) on S x = b in precision T; stops on the true residual (FP64
+// mode) or on the Arnoldi estimate (inner FP32 solves).  x must hold the
+// initial guess.
+template <typename T>
+int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_residual, hdg_solve_info &info) {
+    Workspace &W = *h->ws;
+    KSpace<T> &k = kspace<T>(h);
+    cudaStream_t s = h->stream;
+    double bnorm;
+    int rc = norm_host<T>(h, b, bnorm);
+    if (rc) return rc;
+    info.iters = 0;
+    info.outer = 0;
+    info.est_rel_res = 0;
+    info.true_rel_res = 0;
+    if (!std::isfinite(bnorm)) return fail(h, HDG_ENAN, "NaN or Inf in the right-hand side");
+    if (bnorm == 0.0) {
+        TRY(launch_fill<T>(x, T(0), W.NT, s));
+        return HDG_OK;
+    }
+    int total = 0;
+    for (;;) {
+        // r = b - S x into V[0]
+        TRY(launch_residual_t<T>(h, b, x, k.V));
+        double beta;
+        rc = norm_host<T>(h, k.V, beta);
+        if (rc) return rc;
+        const double rel = beta / bnorm;
+        info.true_rel_res = rel;
+        if (!std::isfinite(rel)) return fail(h, HDG_ENAN, "NaN or Inf in the Krylov iteration");
+        if (rel <= rtol) return HDG_OK;
+        if (total >= max_it) return fail(h, HDG_ENOCONV, "maximum number of iterations reached");
+        double inv = beta;
+        TRY(cudaMemcpyAsync(W.nrm2, &inv, sizeof(double), cudaMemcpyHostToDevice, s));
+        TRY(launch_scale_copy<T>(k.V, k.V, W.nrm2, W.NT, s));
+        int done, flag;
+        double est;
+        rc = fgmres_cycle<T>(h, x, beta, bnorm, rtol, max_it - total, done, est, flag);
+        if (rc) return rc;
+        total += done;
+        info.iters = total;
+        info.outer += 1;
+        info.est_rel_res = est;
+        if (flag & 4) return fail(h, HDG_ENAN, "NaN or Inf in the Krylov iteration");
+        if (!true_residual && (est <= rtol || total >= max_it)) {
+            // inner solve: trust the estimate
+            info.true_rel_res = est;
+            return HDG_OK;
+        }
+        if ((flag & 2) && est > rtol) {
+            // breakdown without convergence: check the true residual once more
+            TRY(launch_residual_t<T>(h, b, x, k.V));
+            double beta2;
+            rc = norm_host<T>(h, k.V, beta2);
+            if (rc) return rc;
+            info.true_rel_res = beta2 / bnorm;
+            if (beta2 / bnorm <= rtol) return HDG_OK;
+            return fail(h, HDG_EBREAKDOWN, "Krylov breakdown without convergence");
+        }
+    }
+}
+
+// FP64 iterative refinement with FP32 inner FGMRES solves
+int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info) {
+    Workspace &W = *h->ws;
+    KSpace<float> &k = W.k32;
+    cudaStream_t s = h->stream;
+    double bnorm;
+    int rc = norm_host<double>(h, g, bnorm);
+    if (rc) return rc;
+    info = hdg_solve_info{};
+    if (!std::isfinite(bnorm)) return fail(h, HDG_ENAN, "NaN or Inf in the right-hand side");
+    TRY(launch_fill<double>(x, 0.0, W.NT, s));
+    if (bnorm == 0.0) return HDG_OK;
+    int total = 0;
+    for (int outer = 0;; ++outer) {
+        TRY(launch_residual_t<double>(h, g, x, W.r));
+        double beta;
+        rc = norm_host<double>(h, W.r, beta);
+        if (rc) return rc;
+        info.true_rel_res = beta / bnorm;
+        info.outer = outer;
+        if (!std::isfinite(beta)) return fail(h, HDG_ENAN, "NaN or Inf in the refinement");
+        if (beta / bnorm <= h->prm.rtol) return HDG_OK;
+        if (total >= h->prm.max_iter || outer >= 100)
+            return fail(h, HDG_ENOCONV, "maximum number of iterations reached");
+        // b32 = r / ||r||, solve S d = b32 in FP32, x += ||r|| d
+        TRY(cudaMemcpyAsync(W.nrm2, &beta, sizeof(double), cudaMemcpyHostToDevice, s));
+        TRY(launch_d2f_scaled(W.r, k.b, W.nrm2, W.NT, s));
+        TRY(launch_fill<float>(k.x, 0.0f, W.NT, s));
+        hdg_solve_info inner{};
+        const double inner_tol = std::max(h->prm.inner_rtol, 0.5 * h->prm.rtol * bnorm / beta);
+        rc = fgmres<float>(h, k.b, k.x, inner_tol, h->prm.max_iter - total, false, inner);
+        if (rc && rc != HDG_ENOCONV) return rc;
+        total += inner.iters;
+        info.iters = total;
+        info.est_rel_res = inner.est_rel_res;
+        // x += beta * d  (beta = ||r|| still in W.nrm2)
+        TRY(launch_axpby_mixed(x, k.x, W.nrm2, W.NT, s));
+    }
+}
+
+int ensure_staging(hdg_handle *h) {
+    Workspace &W = *h->ws;
+    if (W.ru) return HDG_OK;
+    TRY(dalloc(&W.ru, size_t(h->N) * 2 * h->np));
+    TRY(dalloc(&W.rh, size_t(h->N) * h->np));
+    TRY(dalloc(&W.lam_ext, size_t(h->NT)));
+    TRY(dalloc(&W.u, size_t(h->N) * 2 * h->np));
+    TRY(dalloc(&W.hh, size_t(h->N) * h->np));
+    return HDG_OK;
+}
+
+void free_handle(hdg_handle *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    dfree(h->d_ref); dfree(h->d_X); dfree(h->d_fcell); dfree(h->d_facet_of); dfree(h->d_flip);
+    dfree(h->d_facet_cell); dfree(h->d_facet_edge); dfree(h->d_facet_verts); dfree(h->d_v2f_ptr); dfree(h->d_v2f);
+    dfree(h->d_nbr); dfree(h->d_Xb); dfree(h->d_Rm); dfree(h->d_W); dfree(h->d_Scell); dfree(h->d_Sval);
+    dfree(h->d_Dinv); dfree(h->d_Sval32); dfree(h->d_Dinv32); dfree(h->d_status); dfree(h->d_coarse_inv);
+    dfree(h->d_coarse_inv32); dfree(h->d_coarse_work);
+    for (auto &L : h->lev) {
+        dfree(L.row_ptr); dfree(L.col); dfree(L.diag); dfree(L.mass); dfree(L.stiff); dfree(L.A); dfree(L.dinv);
+        dfree(L.A32); dfree(L.dinv32); dfree(L.parent); dfree(L.child_ptr); dfree(L.child_idx); dfree(L.child_w);
+        dfree(L.x); dfree(L.x2); dfree(L.b); dfree(L.r); dfree(L.x32); dfree(L.x232); dfree(L.b32); dfree(L.r32);
+    }
+    if (h->ws) {
+        Workspace &W = *h->ws;
+        dfree(W.g); dfree(W.x); dfree(W.r); dfree(W.ycell);
+        dfree(W.k64.V); dfree(W.k64.Z); dfree(W.k64.w); dfree(W.k64.t0); dfree(W.k64.t1); dfree(W.k64.res);
+        dfree(W.k32.V); dfree(W.k32.Z); dfree(W.k32.w); dfree(W.k32.t0); dfree(W.k32.t1); dfree(W.k32.res);
+        dfree(W.k32.b); dfree(W.k32.x);
+        dfree(W.Hm); dfree(W.cs); dfree(W.sn); dfree(W.sv); dfree(W.h1); dfree(W.h2); dfree(W.nrm2);
+        dfree(W.est); dfree(W.y); dfree(W.partial); dfree(W.flags);
+        dfree(W.ru); dfree(W.rh); dfree(W.lam_ext); dfree(W.u); dfree(W.hh); dfree(W.lam_int);
+        if (W.host_buf) cudaFreeHost(W.host_buf);
+        if (W.host_flags) cudaFreeHost(W.host_flags);
+        delete h->ws;
+    }
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int setup_device(hdg_handle *h, const hdg_params *prm) {
+    cudaStream_t s = h->stream;
+    const HostMesh &hm = h->hm;
+    RefElem re = build_ref_elem(h->p);
+    TRY(upload(&h->d_ref, re.packed(), s));
+    TRY(upload(&h->d_X, hm.X, s));
+    std::vector<double> fcell(size_t(h->N) * 3, 0.0);
+    if (prm->f_vertex)
+        for (int K = 0; K < h->N; ++K)
+            for (int i = 0; i < 3; ++i) fcell[size_t(K) * 3 + i] = prm->f_vertex[hm.cells[3 * K + i]];
+    TRY(upload(&h->d_fcell, fcell, s));
+    TRY(upload(&h->d_facet_of, hm.facet_of, s));
+    TRY(upload(&h->d_flip, hm.flip, s));
+    TRY(upload(&h->d_facet_cell, hm.facet_cell, s));
+    TRY(upload(&h->d_facet_edge, hm.facet_edge, s));
+    TRY(upload(&h->d_facet_verts, hm.facet_verts, s));
+    TRY(upload(&h->d_v2f_ptr, hm.v2f_ptr, s));
+    TRY(upload(&h->d_v2f, hm.v2f, s));
+    const size_t N = h->N, NF = h->NF, nK = h->nK, m = h->m, pp = h->pp;
+    TRY(dalloc(&h->d_nbr, 4 * NF));
+    TRY(dalloc(&h->d_Xb, nK * m * N));
+    TRY(dalloc(&h->d_Rm, nK * nK * N));
+    TRY(dalloc(&h->d_W, m * nK * N));
+    TRY(dalloc(&h->d_Scell, N * m * m));
+    TRY(dalloc(&h->d_Sval, 5 * pp * pp * NF));
+    TRY(dalloc(&h->d_Dinv, pp * pp * NF));
+    TRY(dalloc(&h->d_status, 1));
+    const bool mixed = prm->precision == HDG_MIXED_FP32;
+    if (mixed) {
+        TRY(dalloc(&h->d_Sval32, 5 * pp * pp * NF));
+        TRY(dalloc(&h->d_Dinv32, pp * pp * NF));
+    }
+    h->lev.resize(hm.levels.size());
+    for (size_t l = 0; l < hm.levels.size(); ++l) {
+        const HostLevel &hl = hm.levels[l];
+        DevLevel &L = h->lev[l];
+        L.nv = hl.nv;
+        L.nnz = int(hl.col.size());
+        TRY(upload(&L.row_ptr, hl.row_ptr, s));
+        TRY(upload(&L.col, hl.col, s));
+        TRY(upload(&L.diag, hl.diag, s));
+        TRY(upload(&L.mass, hl.mass, s));
+        TRY(upload(&L.stiff, hl.stiff, s));
+        TRY(dalloc(&L.A, size_t(L.nnz)));
+        TRY(dalloc(&L.dinv, size_t(L.nv)));
+        if (l > 0) {
+            TRY(upload(&L.parent, hl.parent, s));
+            TRY(upload(&L.child_ptr, hl.child_ptr, s));
+            TRY(upload(&L.child_idx, hl.child_idx, s));
+            TRY(upload(&L.child_w, hl.child_w, s));
+        }
+        TRY(dalloc(&L.x, size_t(L.nv)));
+        TRY(dalloc(&L.x2, size_t(L.nv)));
+        TRY(dalloc(&L.b, size_t(L.nv)));
+        TRY(dalloc(&L.r, size_t(L.nv)));
+        if (mixed) {
+            TRY(dalloc(&L.A32, size_t(L.nnz)));
+            TRY(dalloc(&L.dinv32, size_t(L.nv)));
+            TRY(dalloc(&L.x32, size_t(L.nv)));
+            TRY(dalloc(&L.x232, size_t(L.nv)));
+            TRY(dalloc(&L.b32, size_t(L.nv)));
+            TRY(dalloc(&L.r32, size_t(L.nv)));
+        }
+    }
+    const size_t nc = h->lev.back().nv;
+    TRY(dalloc(&h->d_coarse_inv, nc * nc));
+    TRY(dalloc(&h->d_coarse_work, nc * nc));
+    if (mixed) TRY(dalloc(&h->d_coarse_inv32, nc * nc));
+
+    h->ws = new Workspace();
+    Workspace &W = *h->ws;
+    W.m = prm->restart;
+    W.NT = h->NT;
+    W.nchunk = int(std::min<size_t>(std::max<size_t>((W.NT + 4095) / 4096, 1), 608));
+    TRY(dalloc(&W.g, W.NT));
+    TRY(dalloc(&W.x, W.NT));
+    TRY(dalloc(&W.r, W.NT));
+    TRY(dalloc(&W.lam_int, W.NT));
+    TRY(dalloc(&W.ycell, N * m));
+    const size_t mm = W.m;
+    if (!mixed) {
+        TRY(dalloc(&W.k64.V, (mm + 1) * W.NT));
+        TRY(dalloc(&W.k64.Z, mm * W.NT));
+        TRY(dalloc(&W.k64.w, W.NT));
+    } else {
+        // FP64 vectors still needed by the FP64 operator entry points
+        TRY(dalloc(&W.k64.V, W.NT));
+        TRY(dalloc(&W.k64.w, W.NT));
+        TRY(dalloc(&W.k32.V, (mm + 1) * W.NT));
+        TRY(dalloc(&W.k32.Z, mm * W.NT));
+        TRY(dalloc(&W.k32.w, W.NT));
+        TRY(dalloc(&W.k32.t0, W.NT));
+        TRY(dalloc(&W.k32.t1, W.NT));
+        TRY(dalloc(&W.k32.res, W.NT));
+        TRY(dalloc(&W.k32.b, W.NT));
+        TRY(dalloc(&W.k32.x, W.NT));
+    }
+    TRY(dalloc(&W.k64.t0, W.NT));
+    TRY(dalloc(&W.k64.t1, W.NT));
+    TRY(dalloc(&W.k64.res, W.NT));
+    TRY(dalloc(&W.Hm, (mm + 1) * mm));
+    TRY(dalloc(&W.cs, mm + 1));
+    TRY(dalloc(&W.sn, mm + 1));
+    TRY(dalloc(&W.sv, mm + 1));
+    TRY(dalloc(&W.h1, mm + 1));
+    TRY(dalloc(&W.h2, mm + 1));
+    TRY(dalloc(&W.nrm2, 1));
+    TRY(dalloc(&W.est, 1));
+    TRY(dalloc(&W.y, mm + 1));
+    TRY(dalloc(&W.partial, (mm + 1) * size_t(W.nchunk)));
+    TRY(dalloc(&W.flags, 1));
+    TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_buf), 4 * sizeof(double)));
+    TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_flags), 4 * sizeof(int32_t)));
+    TRY(cudaStreamSynchronize(s));
+    return HDG_OK;
+}
+
+int check_status(hdg_handle *h) {
+    int32_t st = 0;
+    TRY(cudaMemcpyAsync(&st, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    TRY(cudaStreamSynchronize(h->stream));
+    if (st & 1) return fail(h, HDG_ESINGULAR, "zero pivot in a cell matrix A_K");
+    if (st & 2) return fail(h, HDG_ESINGULAR, "singular facet block of the trace operator");
+    if (st & 4) return fail(h, HDG_ESINGULAR, "singular coarsest P1 operator");
+    return HDG_OK;
+}
+
+int require_condensed(hdg_handle *h) {
+    if (!h) return HDG_EINVAL;
+    if (!h->condensed) return fail(h, HDG_ESTATE, "hdg_condense has not run on this handle");
+    return HDG_OK;
+}
+
+int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solve_info &info) {
+    Workspace &W = *h->ws;
+    cudaStream_t s = h->stream;
+    TRY(launch_rhs(h, r_u, r_h, W.g, W.ycell));
+    int rc;
+    if (h->prm.precision == HDG_FP64) {
+        TRY(launch_fill<double>(W.x, 0.0, W.NT, s));
+        rc = fgmres<double>(h, W.g, W.x, h->prm.rtol, h->prm.max_iter, true, info);
+    } else {
+        rc = solve_mixed(h, W.g, W.x, info);
+    }
+    info.status = rc;
+    TRY(cudaMemcpyAsync(W.lam_int, W.x, sizeof(double) * W.NT, cudaMemcpyDeviceToDevice, s));
+    W.have_lambda = true;
+    return rc;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+
+void hdg_default_params(hdg_params *prm) {
+    if (!prm) return;
+    std::memset(prm, 0, sizeof(*prm));
+    prm->p = 1;
+    prm->tau = 1.0;
+    prm->g = 1.0;
+    prm->H = 1.0;
+    prm->tau_s = 0.0;
+    prm->f_vertex = nullptr;
+    prm->precision = HDG_FP64;
+    prm->rtol = 1e-8;
+    prm->restart = 30;
+    prm->max_iter = 500;
+    prm->n_pre = 2;
+    prm->n_post = 2;
+    prm->omega = 2.0 / 3.0;
+    prm->p1_nu_pre = 2;
+    prm->p1_nu_post = 2;
+    prm->p1_omega = 2.0 / 3.0;
+    prm->inner_rtol = 1e-4;
+}
+
+int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hdg_handle **out) {
+    if (!out) return fail(nullptr, HDG_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string e = check_params(prm);
+    if (!e.empty()) return fail(nullptr, HDG_EINVAL, e);
+    hdg_handle *h = new hdg_handle();
+    h->prm = *prm;
+    h->prm.f_vertex = nullptr;      // not kept: the values are copied
+    e = build_host_mesh(mesh, h->hm);
+    if (!e.empty()) {
+        delete h;
+        return fail(nullptr, HDG_EINVAL, e);
+    }
+    h->p = prm->p;
+    h->pp = prm->p + 1;
+    h->np = n_cell_nodes(prm->p);
+    h->nK = 3 * h->np;
+    h->m = 3 * h->pp;
+    h->N = h->hm.nc;
+    h->NF = h->hm.nf;
+    h->NT = h->NF * h->pp;
+    h->nv = h->hm.nv;
+    h->dim = h->hm.dim;
+    h->tau_s = prm->tau_s > 0 ? prm->tau_s : std::sqrt(prm->g * prm->H);
+    if (stream) {
+        h->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        cudaError_t ce = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) {
+            delete h;
+            return fail(nullptr, HDG_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(ce));
+        }
+        h->own_stream = true;
+    }
+    int rc = setup_device(h, prm);
+    if (rc) {
+        std::string msg = h->err;
+        free_handle(h);
+        return fail(nullptr, rc == HDG_ECUDA && msg.find("memory") != std::string::npos ? HDG_ENOMEM : rc, msg);
+    }
+    *out = h;
+    return HDG_OK;
+}
+
+int hdg_condense(hdg_handle *h) {
+    if (!h) return HDG_EINVAL;
+    cudaStream_t s = h->stream;
+    h->condensed = false;
+    TRY(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), s));
+    TRY(launch_condense(h));
+    TRY(launch_assemble(h));
+    const double tau = h->prm.tau, ctau2 = tau * tau * h->prm.g * h->prm.H;
+    for (auto &L : h->lev) TRY(launch_p1_combine(h, L, tau, ctau2));
+    const DevLevel &Lc = h->lev.back();
+    TRY(launch_dense_inverse(h, Lc, h->d_coarse_work, h->d_coarse_inv, Lc.nv));
+    if (h->prm.precision == HDG_MIXED_FP32) {
+        const size_t NF = h->NF, pp = h->pp;
+        TRY(launch_to_f32(h->d_Sval, h->d_Sval32, 5 * pp * pp * NF, s));
+        TRY(launch_to_f32(h->d_Dinv, h->d_Dinv32, pp * pp * NF, s));
+        for (auto &L : h->lev) {
+            TRY(launch_to_f32(L.A, L.A32, size_t(L.nnz), s));
+            TRY(launch_to_f32(L.dinv, L.dinv32, size_t(L.nv), s));
+        }
+        TRY(launch_to_f32(h->d_coarse_inv, h->d_coarse_inv32, size_t(Lc.nv) * Lc.nv, s));
+    }
+    int rc = check_status(h);
+    if (rc) return rc;
+    h->condensed = true;
+    return HDG_OK;
+}
+
+int hdg_set_tau(hdg_handle *h, double tau) {
+    if (!h) return HDG_EINVAL;
+    if (!(tau > 0)) return fail(h, HDG_EINVAL, "tau must be positive");
+    h->prm.tau = tau;
+    return hdg_condense(h);
+}
+
+int hdg_solve_dev(hdg_handle *h, const double *r_u, const double *r_h, double *lambda, hdg_solve_info *info) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    if (!r_u || !r_h || !lambda) return fail(h, HDG_EINVAL, "NULL pointer argument");
+    hdg_solve_info loc{};
+    rc = solve_internal(h, r_u, r_h, loc);
+    if (rc == HDG_ECUDA) {
+        if (info) *info = loc;
+        return rc;
+    }
+    TRY(launch_to_external(h, h->ws->x, lambda));
+    h->ws->have_rhs = false;
+    if (info) *info = loc;
+    return rc;
+}
+
+int hdg_solve(hdg_handle *h, const double *r_u, const double *r_h, double *lambda, hdg_solve_info *info) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    if (!r_u || !r_h || !lambda) return fail(h, HDG_EINVAL, "NULL pointer argument");
+    rc = ensure_staging(h);
+    if (rc) return rc;
+    Workspace &W = *h->ws;
+    cudaStream_t s = h->stream;
+    TRY(cudaMemcpyAsync(W.ru, r_u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyHostToDevice, s));
+    TRY(cudaMemcpyAsync(W.rh, r_h, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyHostToDevice, s));
+    hdg_solve_info loc{};
+    rc = solve_internal(h, W.ru, W.rh, loc);
+    if (rc == HDG_ECUDA) {
+        if (info) *info = loc;
+        return rc;
+    }
+    TRY(launch_to_external(h, W.x, W.lam_ext));
+    TRY(cudaMemcpyAsync(lambda, W.lam_ext, sizeof(double) * W.NT, cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    W.have_rhs = true;
+    if (info) *info = loc;
+    return rc;
+}
+
+int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h, const double *lambda, double *u,
+                    double *h_out) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    if (!u || !h_out || !r_u || !r_h) return fail(h, HDG_EINVAL, "NULL pointer argument");
+    Workspace &W = *h->ws;
+    const double *lam = W.lam_int;
+    if (lambda) {
+        TRY(launch_to_internal(h, lambda, W.k64.res));
+        lam = W.k64.res;
+    } else if (!W.have_lambda) {
+        return fail(h, HDG_ESTATE, "no lambda given and no previous solve");
+    }
+    TRY(launch_recover(h, r_u, r_h, lam, u, h_out));
+    return HDG_OK;
+}
+
+int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lambda, double *u, double *h_out) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    if (!u || !h_out) return fail(h, HDG_EINVAL, "NULL output pointer");
+    rc = ensure_staging(h);
+    if (rc) return rc;
+    Workspace &W = *h->ws;
+    cudaStream_t s = h->stream;
+    if (r_u && r_h) {
+        TRY(cudaMemcpyAsync(W.ru, r_u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyHostToDevice, s));
+        TRY(cudaMemcpyAsync(W.rh, r_h, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyHostToDevice, s));
+    } else if (!W.have_rhs) {
+        return fail(h, HDG_ESTATE, "no right-hand side given and none kept from hdg_solve");
+    }
+    const double *lam = W.lam_int;
+    if (lambda) {
+        TRY(cudaMemcpyAsync(W.lam_ext, lambda, sizeof(double) * W.NT, cudaMemcpyHostToDevice, s));
+        TRY(launch_to_internal(h, W.lam_ext, W.k64.res));
+        lam = W.k64.res;
+    } else if (!W.have_lambda) {
+        return fail(h, HDG_ESTATE, "no lambda given and no previous solve");
+    }
+    TRY(launch_recover(h, W.ru, W.rh, lam, W.u, W.hh));
+    TRY(cudaMemcpyAsync(u, W.u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyDeviceToHost, s));
+    TRY(cudaMemcpyAsync(h_out, W.hh, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    return HDG_OK;
+}
+
+int hdg_trace_apply_dev(hdg_handle *h, const double *x, double *y) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    Workspace &W = *h->ws;
+    TRY(launch_to_internal(h, x, W.k64.t0));
+    TRY(launch_apply_t<double>(h, W.k64.t0, W.k64.t1));
+    TRY(launch_to_external(h, W.k64.t1, y));
+    return HDG_OK;
+}
+
+int hdg_condensed_rhs_dev(hdg_handle *h, const double *r_u, const double *r_h, double *g) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    Workspace &W = *h->ws;
+    TRY(launch_rhs(h, r_u, r_h, W.g, W.ycell));
+    TRY(launch_to_external(h, W.g, g));
+    return HDG_OK;
+}
+
+int hdg_precond_apply_dev(hdg_handle *h, const double *v, double *z) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    Workspace &W = *h->ws;
+    TRY(launch_to_internal(h, v, W.r));
+    TRY(precond<double>(h, W.r, W.x));
+    TRY(launch_to_external(h, W.x, z));
+    return HDG_OK;
+}
+
+int hdg_get_sizes(const hdg_handle *h, int64_t *sizes) {
+    if (!h || !sizes) return HDG_EINVAL;
+    sizes[0] = h->N;
+    sizes[1] = h->NF;
+    sizes[2] = h->NT;
+    sizes[3] = h->np;
+    sizes[4] = h->m;
+    sizes[5] = int64_t(h->lev.size());
+    return HDG_OK;
+}
+
+int hdg_get_facets(const hdg_handle *h, int32_t *facet_of, int32_t *flip, int32_t *facet_verts) {
+    if (!h) return HDG_EINVAL;
+    if (facet_of) std::memcpy(facet_of, h->hm.facet_of.data(), sizeof(int32_t) * h->hm.facet_of.size());
+    if (flip) std::memcpy(flip, h->hm.flip.data(), sizeof(int32_t) * h->hm.flip.size());
+    if (facet_verts) std::memcpy(facet_verts, h->hm.facet_verts.data(), sizeof(int32_t) * h->hm.facet_verts.size());
+    return HDG_OK;
+}
+
+int hdg_get_cell_schur(hdg_handle *h, double *S) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    if (!S) return fail(h, HDG_EINVAL, "NULL output pointer");
+    TRY(cudaMemcpyAsync(S, h->d_Scell, sizeof(double) * size_t(h->N) * h->m * h->m, cudaMemcpyDeviceToHost,
+                        h->stream));
+    TRY(cudaStreamSynchronize(h->stream));
+    return HDG_OK;
+}
+
+int hdg_destroy(hdg_handle *h) {
+    free_handle(h);
+    return HDG_OK;
+}
+
+const char *hdg_last_error(const hdg_handle *h) {
+    return h ? h->err.c_str() : g_setup_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// Internal declarations of the HDG trace-solver library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hdg.h"
+
+namespace hdg {
+
+// ---------------------------------------------------------------- sizes
+
+inline int n_cell_nodes(int p) { return (p + 1) * (p + 2) / 2; }
+
+// ---------------------------------------------------------------- reference element
+// Reference triangle (0,0),(1,0),(0,1); Lagrange basis at (a/p, b/p), b outer;
+// local edge i from vertex (i+1)%3 to (i+2)%3; trace basis at t_j = j/p.
+struct RefElem {
+    int p = 0, n = 0, pp = 0;
+    std::vector<double> M;        // [n][n]      int phi_a phi_b
+    std::vector<double> ML;       // [3][n][n]   int L_i phi_a phi_b
+    std::vector<double> Dxi;      // [n][n]      int phi_a d_xi phi_b
+    std::vector<double> Deta;     // [n][n]
+    std::vector<double> E;        // [3][n][n]   edge i: int_0^1 phi_a phi_b dt
+    std::vector<double> N;        // [3][n][pp]  edge i: int_0^1 phi_a mu_j dt
+    std::vector<double> M1;       // [pp][pp]    int_0^1 mu_j mu_k dt
+    // packed copy for the device: M | ML | Dxi | Deta | E | N | M1
+    std::vector<double> packed() const;
+};
+RefElem build_ref_elem(int p);
+
+// offsets into the packed reference data
+struct RefOffsets {
+    int M, ML, Dxi, Deta, E, N, M1, total;
+};
+inline RefOffsets ref_offsets(int p) {
+    int n = n_cell_nodes(p), pp = p + 1;
+    RefOffsets o;
+    o.M = 0; o.ML = o.M + n * n; o.Dxi = o.ML + 3 * n * n; o.Deta = o.Dxi + n * n;
+    o.E = o.Deta + n * n; o.N = o.E + 3 * n * n; o.M1 = o.N + 3 * n * pp; o.total = o.M1 + pp * pp;
+    return o;
+}
+
+// ---------------------------------------------------------------- host mesh data
+struct HostLevel {
+    int nv = 0, nc = 0;
+    std::vector<double> X;        // [nc][3][2] local 2-D vertex coordinates
+    std::vector<int32_t> cells;   // [nc][3]
+    // geometric P1 matrices, CSR with sorted columns
+    std::vector<int32_t> row_ptr, col, diag;
+    std::vector<double> mass, stiff;
+    // transfer to the next finer level (empty on the fine level)
+    std::vector<int32_t> parent;      // [nv_finer][2]
+    std::vector<int32_t> child_ptr;   // [nv + 1]  restriction: coarse vertex <- fine vertices
+    std::vector<int32_t> child_idx;
+    std::vector<double> child_w;
+};
+
+struct HostMesh {
+    int dim = 0, nv = 0, nc = 0, nf = 0;
+    std::vector<double> X;            // [nc][3][2] local 2-D coordinates of the fine cells
+    std::vector<int32_t> cells;       // [nc][3]
+    std::vector<int32_t> facet_of;    // [nc][3]
+    std::vector<int32_t> flip;        // [nc][3]
+    std::vector<int32_t> facet_verts; // [nf][2] lo, hi
+    std::vector<int32_t> facet_cell;  // [nf][2] incident cells (order of appearance)
+    std::vector<int32_t> facet_edge;  // [nf][2] local edge index in each cell
+    std::vector<int32_t> v2f_ptr;     // [nv+1] vertex -> incident facet ends
+    std::vector<int32_t> v2f;         // 2*facet + (0: lo end, 1: hi end)
+    std::vector<HostLevel> levels;    // P1 levels, level 0 = fine mesh
+};
+
+// Returns empty string on success, else the reason.
+std::string build_host_mesh(const hdg_mesh_desc *desc, HostMesh &hm);
+
+// ---------------------------------------------------------------- device data
+struct DevLevel {
+    int nv = 0, nnz = 0;
+    int32_t *row_ptr = nullptr, *col = nullptr, *diag = nullptr;
+    double *mass = nullptr, *stiff = nullptr, *A = nullptr, *dinv = nullptr;
+    float *A32 = nullptr, *dinv32 = nullptr;
+    int32_t *parent = nullptr;                         // [nv_finer][2]
+    int32_t *child_ptr = nullptr, *child_idx = nullptr;
+    double *child_w = nullptr;
+    // work vectors
+    double *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;
+    float *x32 = nullptr, *x232 = nullptr, *b32 = nullptr, *r32 = nullptr;
+};
+
+struct Workspace;   // solver vectors, defined in api.cu
+
+}  // namespace hdg
+
+// The handle (opaque to callers).
+struct hdg_handle {
+    std::string err;
+    hdg_params prm{};
+    int p = 0, pp = 0, np = 0, nK = 0, m = 0;
+    int N = 0, NF = 0, NT = 0, nv = 0, dim = 0;
+    double tau_s = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool condensed = false;
+    hdg::HostMesh hm;
+
+    // device mesh / geometry
+    double *d_ref = nullptr;        // packed reference matrices
+    double *d_X = nullptr;          // [N][3][2]
+    double *d_fcell = nullptr;      // [N][3] Coriolis at the cell vertices
+    int32_t *d_facet_of = nullptr, *d_flip = nullptr;   // [N][3]
+    int32_t *d_facet_cell = nullptr, *d_facet_edge = nullptr;  // [NF][2]
+    int32_t *d_facet_verts = nullptr;  // [NF][2]
+    int32_t *d_v2f_ptr = nullptr, *d_v2f = nullptr;
+    int32_t *d_nbr = nullptr;       // [4][NF] neighbour facets of the facet-row operator
+
+    // cell operators (component-major [j][N] layouts)
+    double *d_Xb = nullptr;         // A^-1 B        [nK*m][N]
+    double *d_Rm = nullptr;         // A^-1 Mass     [nK*nK][N]
+    double *d_W = nullptr;          // C A^-1 Mass   [m*nK][N]
+    double *d_Scell = nullptr;      // S_K           [N][m][m]
+    // facet-row trace operator
+    double *d_Sval = nullptr;       // [5*pp*pp][NF]
+    double *d_Dinv = nullptr;       // [pp*pp][NF]
+    float *d_Sval32 = nullptr, *d_Dinv32 = nullptr;
+    int32_t *d_status = nullptr;    // device error flags
+
+    std::vector<hdg::DevLevel> lev;
+    double *d_coarse_inv = nullptr;   // dense inverse of the coarsest P1 operator
+    double *d_coarse_work = nullptr;
+    float *d_coarse_inv32 = nullptr;
+    hdg::Workspace *ws = nullptr;
+};
+
+// ---------------------------------------------------------------- error helpers
+#define HDG_CUDA_TRY(h, call)                                                        \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            (h)->err = std::string(#call) + ": " + cudaGetErrorString(e_);           \
+            return HDG_ECUDA;                                                        \
+        }                                                                            \
+    } while (0)
+
+namespace hdg {
+
+// ---------------------------------------------------------------- kernel launchers
+// condense / assembly (k_condense.cu)
+cudaError_t launch_condense(hdg_handle *h);
+cudaError_t launch_assemble(hdg_handle *h);
+cudaError_t launch_p1_combine(hdg_handle *h, DevLevel &L, double tau, double ctau2);
+cudaError_t launch_dense_inverse(hdg_handle *h, const DevLevel &L, double *work, double *inv, int n);
+cudaError_t launch_to_f32(const double *x, float *y, size_t n, cudaStream_t s);
+
+// trace-space kernels (k_trace.cu); vectors in the internal layout [pp][NF]
+cudaError_t launch_to_internal(hdg_handle *h, const double *ext, double *in);
+cudaError_t launch_to_external(hdg_handle *h, const double *in, double *ext);
+cudaError_t launch_rhs(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell);
+cudaError_t launch_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lam,
+                           double *u, double *hout);
+
+// P1 multigrid kernels (k_p1.cu)
+template <typename T>
+cudaError_t launch_p1_jacobi(const DevLevel &L, const T *A, const T *dinv, const T *b, const T *x,
+                             T *xout, T omega, bool first, cudaStream_t s);
+template <typename T>
+cudaError_t launch_p1_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, cudaStream_t s);
+template <typename T>
+cudaError_t launch_p1_restrict(const DevLevel &coarse, const T *rf, T *bc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_p1_prolong_add(const DevLevel &coarse, int nv_fine, const T *ec, T *xf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_dense_apply(const T *inv, int n, const T *b, T *x, cudaStream_t s);
+
+// Krylov kernels (k_krylov.cu)
+template <typename T>
+cudaError_t launch_multidot(const T *V, size_t ld, int k, const T *w, size_t n, double *partial,
+                            int nchunk, cudaStream_t s);
+cudaError_t launch_reduce_partials(const double *partial, int k, int nchunk, double *out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_multi_axpy(T *w, const T *V, size_t ld, int k, const double *coef, double sign,
+                              size_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scale_copy(const T *w, T *v, const double *denom, size_t n, cudaStream_t s);
+cudaError_t launch_arnoldi_finish(double *Hcol, const double *h1, const double *h2, const double *nrm2,
+                                  int j, cudaStream_t s);
+cudaError_t launch_givens(double *Hm, int ldh, double *cs, double *sn, double *sv, int j, double bnorm,
+                          double *est, int32_t *flags, cudaStream_t s);
+cudaError_t launch_hessenberg_solve(const double *Hm, int ldh, const double *sv, int k, double *y,
+                                    cudaStream_t s);
+template <typename T>
+cudaError_t launch_fill(T *x, T v, size_t n, cudaStream_t s);
+cudaError_t launch_axpby_mixed(double *x, const float *d, const double *scale, size_t n, cudaStream_t s);
+cudaError_t launch_d2f_scaled(const double *x, float *y, const double *scale, size_t n, cudaStream_t s);
+
+}  // namespace hdg

@@ -1,0 +1,419 @@
+// Static condensation (Sec. 4.2) and assembly of the facet-row trace operator.
+//
+// Per cell K (one CTA per cell), with u_perp = (-u_y, u_x), the cell rows of
+// the upwind HDG form (Eq. bilinear_HDG_upwind, ABCM split of Eq. ABCMform /
+// App. B, Coriolis implicit) are assembled in the integrated-by-parts form
+//   momentum: (u,w) + tau (f u_perp, w) - tau g (h, div w)         + tau g <lambda, w.n>
+//   mass:     (h,psi) + tau H (div u, psi) + tau tau_s <h, psi>_dK - tau tau_s <lambda, psi>
+//   facet:    <H u.n + tau_s h, mu> - tau_s <lambda, mu>
+// i.e. A_K q + B_K lambda = Mass_K r on the cell and C_K q - Mt_K lambda on its
+// facets.  The momentum rows are scaled by H/g: the scaled A_K has the
+// positive-definite symmetric part  diag((H/g) M, M + tau tau_s E)  (the
+// Coriolis and the tau H div coupling are skew after scaling), so every
+// leading minor is non-zero and Gauss-Jordan elimination needs no pivoting.
+// Elimination of [A | B | Mass] gives X_B = A^-1 B and R_M = A^-1 Mass; then
+//   S_K = Mt_K + C_K X_B      (the cell's part of Eq. schur_system)
+//   W_K = C_K R_M             (step 1: g = sum_K P_K^T W_K r_K)
+// and R_M, X_B serve step 3 (Eq. reconstruct_solution): q = R_M r - X_B lambda_K.
+#include "common.h"
+
+namespace hdg {
+
+namespace {
+
+constexpr int kCondenseThreads = 128;
+
+template <int P>
+struct Sz {
+    static constexpr int PP = P + 1;
+    static constexpr int NP = (P + 1) * (P + 2) / 2;
+    static constexpr int NK = 3 * NP;
+    static constexpr int M = 3 * PP;
+    static constexpr int LDA = NK + M + NK;
+};
+
+struct CondenseArgs {
+    int N;
+    double tau, g, H, tau_s;
+    const double *ref;      // packed reference matrices
+    const double *X;        // [N][3][2]
+    const double *fcell;    // [N][3]
+    double *Xb, *Rm, *W, *Scell;
+    int32_t *status;
+};
+
+template <int P>
+__global__ void __launch_bounds__(kCondenseThreads) condense_kernel(CondenseArgs a) {
+    using S = Sz<P>;
+    constexpr int NP = S::NP, NK = S::NK, M = S::M, PP = S::PP, LDA = S::LDA;
+    constexpr int oM = 0, oML = oM + NP * NP, oDxi = oML + 3 * NP * NP, oDeta = oDxi + NP * NP,
+                  oE = oDeta + NP * NP, oN = oE + 3 * NP * NP, oM1 = oN + 3 * NP * PP;
+    extern __shared__ double smem[];
+    double *Aug = smem;                 // [NK][LDA]
+    double *Cm = Aug + NK * LDA;        // [M][NK]
+    double *prow = Cm + M * NK;         // [LDA]
+    double *fac = prow + LDA;           // [NK]
+    __shared__ double geo[16];          // detJ, Jit[4], len[3], nrm[6], pad
+    __shared__ double fK[3];
+    __shared__ int bad;
+
+    const int K = blockIdx.x;
+    const int tid = threadIdx.x;
+    const double *ref = a.ref;
+    if (tid == 0) {
+        const double *x = a.X + size_t(K) * 6;
+        double J00 = x[2] - x[0], J01 = x[4] - x[0], J10 = x[3] - x[1], J11 = x[5] - x[1];
+        double det = J00 * J11 - J01 * J10;
+        geo[0] = det;
+        // Jit = J^-T
+        geo[1] = J11 / det;  geo[2] = -J10 / det;
+        geo[3] = -J01 / det; geo[4] = J00 / det;
+        for (int i = 0; i < 3; ++i) {
+            int v1 = (i + 1) % 3, v2 = (i + 2) % 3;
+            double tx = x[2 * v2] - x[2 * v1], ty = x[2 * v2 + 1] - x[2 * v1 + 1];
+            double l = sqrt(tx * tx + ty * ty);
+            geo[5 + i] = l;
+            geo[8 + 2 * i] = ty / l;       // outward normal of a counter-clockwise cell
+            geo[9 + 2 * i] = -tx / l;
+        }
+        for (int i = 0; i < 3; ++i) fK[i] = a.fcell[size_t(K) * 3 + i];
+        bad = 0;
+    }
+    __syncthreads();
+    const double det = geo[0], j00 = geo[1], j01 = geo[2], j10 = geo[3], j11 = geo[4];
+    const double tau = a.tau, g = a.g, H = a.H, ts = a.tau_s, sH = H / g;
+
+    // ---- assemble [D A | D B | D Mass] and C
+    for (int idx = tid; idx < NK * LDA; idx += blockDim.x) {
+        const int rho = idx / LDA, col = idx % LDA;
+        const int R = rho / NP, ia = rho % NP;
+        double v = 0.0;
+        if (col < NK) {
+            const int Cc = col / NP, ib = col % NP;
+            const double Mab = det * ref[oM + ia * NP + ib];
+            if (R < 2) {
+                if (Cc == R) v = Mab;
+                else if (Cc < 2) {
+                    double mf = det * (fK[0] * ref[oML + ia * NP + ib] + fK[1] * ref[oML + NP * NP + ia * NP + ib] +
+                                       fK[2] * ref[oML + 2 * NP * NP + ia * NP + ib]);
+                    v = (R == 0 ? -tau : tau) * mf;
+                } else {
+                    // -tau g (h, d_x phi_a): D_x[b][a] = int phi_b d_x phi_a
+                    double dxi = ref[oDxi + ib * NP + ia], deta = ref[oDeta + ib * NP + ia];
+                    double d = (R == 0) ? det * (j00 * dxi + j01 * deta) : det * (j10 * dxi + j11 * deta);
+                    v = -tau * g * d;
+                }
+                v *= sH;
+            } else {
+                if (Cc < 2) {
+                    // tau H (d_x u_x, psi_a): D_x[a][b]
+                    double dxi = ref[oDxi + ia * NP + ib], deta = ref[oDeta + ia * NP + ib];
+                    double d = (Cc == 0) ? det * (j00 * dxi + j01 * deta) : det * (j10 * dxi + j11 * deta);
+                    v = tau * H * d;
+                } else {
+                    double e = 0.0;
+                    for (int i = 0; i < 3; ++i) e += geo[5 + i] * ref[oE + (i * NP + ia) * NP + ib];
+                    v = Mab + tau * ts * e;
+                }
+            }
+        } else if (col < NK + M) {
+            const int t = col - NK, i = t / PP, j = t % PP;
+            const double nl = geo[5 + i] * ref[oN + (i * NP + ia) * PP + j];
+            if (R == 0) v = tau * H * geo[8 + 2 * i] * nl;        // (H/g) tau g n_x <lambda, phi_a>
+            else if (R == 1) v = tau * H * geo[9 + 2 * i] * nl;
+            else v = -tau * ts * nl;
+        } else {
+            const int kap = col - NK - M, Cc = kap / NP, ib = kap % NP;
+            if (Cc == R) v = det * ref[oM + ia * NP + ib] * (R < 2 ? sH : 1.0);
+        }
+        Aug[idx] = v;
+    }
+    for (int idx = tid; idx < M * NK; idx += blockDim.x) {
+        const int t = idx / NK, kap = idx % NK;
+        const int i = t / PP, j = t % PP, Cc = kap / NP, ib = kap % NP;
+        const double nl = geo[5 + i] * ref[oN + (i * NP + ib) * PP + j];
+        Cm[idx] = (Cc == 0) ? H * geo[8 + 2 * i] * nl : (Cc == 1) ? H * geo[9 + 2 * i] * nl : ts * nl;
+    }
+    __syncthreads();
+
+    // ---- Gauss-Jordan elimination, no pivoting (see the header comment)
+    for (int k = 0; k < NK; ++k) {
+        const double piv = Aug[k * LDA + k];
+        if (!(fabs(piv) > 1e-300)) {
+            if (tid == 0) bad = 1;
+        }
+        const double pinv = 1.0 / piv;
+        for (int c = k + 1 + tid; c < LDA; c += blockDim.x) prow[c] = Aug[k * LDA + c] * pinv;
+        for (int r = tid; r < NK; r += blockDim.x) fac[r] = Aug[r * LDA + k];
+        __syncthreads();
+        const int W = LDA - k - 1;
+        for (int idx = tid; idx < NK * W; idx += blockDim.x) {
+            const int r = idx / W, c = k + 1 + idx % W;
+            if (r == k) Aug[r * LDA + c] = prow[c];
+            else Aug[r * LDA + c] -= fac[r] * prow[c];
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) atomicOr(a.status, 1);
+        return;
+    }
+
+    // ---- outputs
+    const size_t N = a.N;
+    for (int idx = tid; idx < NK * M; idx += blockDim.x) {
+        const int rho = idx / M, t = idx % M;
+        a.Xb[size_t(idx) * N + K] = Aug[rho * LDA + NK + t];
+    }
+    for (int idx = tid; idx < NK * NK; idx += blockDim.x) {
+        const int rho = idx / NK, kap = idx % NK;
+        a.Rm[size_t(idx) * N + K] = Aug[rho * LDA + NK + M + kap];
+    }
+    for (int idx = tid; idx < M * M; idx += blockDim.x) {
+        const int t = idx / M, t2 = idx % M;
+        double s = 0.0;
+        for (int kap = 0; kap < NK; ++kap) s += Cm[t * NK + kap] * Aug[kap * LDA + NK + t2];
+        if (t / PP == t2 / PP)
+            s += ts * geo[5 + t / PP] * ref[oM1 + (t % PP) * PP + (t2 % PP)];
+        a.Scell[size_t(K) * M * M + idx] = s;
+    }
+    for (int idx = tid; idx < M * NK; idx += blockDim.x) {
+        const int t = idx / NK, kap = idx % NK;
+        double s = 0.0;
+        for (int r = 0; r < NK; ++r) s += Cm[t * NK + r] * Aug[r * LDA + NK + M + kap];
+        a.W[size_t(idx) * N + K] = s;
+    }
+}
+
+// ---------------------------------------------------------------- facet-row assembly
+// For facet e with incident (cell, local edge) pairs (K_s, i_s), s = 0, 1, row r
+// of the facet (trace node r from the lower to the higher vertex id) is
+//   (S x)_{e,r} = sum_c D_e[r][c] x_{e,c} + sum_{s,k} O_{s,k}[r][c] x_{nbr(s,k),c}
+// with D_e the sum of both cells' diagonal blocks and O_{s,k} the block of S_{K_s}
+// coupling edge i_s to edge (i_s + 1 + k) % 3 (neighbour facet nbr(s,k)).
+// Stored as Sval[(r*5 + b)*PP + c][e], b = 0 (D_e), 1 + 2s + k; Dinv = D_e^-1.
+struct AssembleArgs {
+    int N, NF;
+    const double *Scell;
+    const int32_t *facet_of, *flip, *facet_cell, *facet_edge;
+    double *Sval, *Dinv;
+    int32_t *nbr;
+    int32_t *status;
+};
+
+template <int P>
+__global__ void assemble_kernel(AssembleArgs a) {
+    constexpr int PP = P + 1, M = 3 * PP;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.NF) return;
+    const size_t NF = a.NF;
+    int K[2], I[2], F[2];
+    for (int s = 0; s < 2; ++s) {
+        K[s] = a.facet_cell[2 * e + s];
+        I[s] = a.facet_edge[2 * e + s];
+        F[s] = a.flip[3 * K[s] + I[s]];
+    }
+    double D[PP][PP];
+    for (int r = 0; r < PP; ++r)
+        for (int c = 0; c < PP; ++c) {
+            double v = 0.0;
+            for (int s = 0; s < 2; ++s) {
+                const int lr = I[s] * PP + (F[s] ? P - r : r);
+                const int lc = I[s] * PP + (F[s] ? P - c : c);
+                v += a.Scell[size_t(K[s]) * M * M + lr * M + lc];
+            }
+            D[r][c] = v;
+            a.Sval[size_t((r * 5 + 0) * PP + c) * NF + e] = v;
+        }
+    for (int s = 0; s < 2; ++s)
+        for (int k = 0; k < 2; ++k) {
+            const int b = 1 + 2 * s + k;
+            const int i2 = (I[s] + 1 + k) % 3;
+            const int f2 = a.flip[3 * K[s] + i2];
+            a.nbr[size_t(b - 1) * NF + e] = a.facet_of[3 * K[s] + i2];
+            for (int r = 0; r < PP; ++r) {
+                const int lr = I[s] * PP + (F[s] ? P - r : r);
+                for (int c = 0; c < PP; ++c) {
+                    const int lc = i2 * PP + (f2 ? P - c : c);
+                    a.Sval[size_t((r * 5 + b) * PP + c) * NF + e] = a.Scell[size_t(K[s]) * M * M + lr * M + lc];
+                }
+            }
+        }
+    // invert D_e (Gauss-Jordan with partial pivoting, in registers)
+    double Inv[PP][PP];
+    for (int r = 0; r < PP; ++r)
+        for (int c = 0; c < PP; ++c) Inv[r][c] = (r == c) ? 1.0 : 0.0;
+    bool singular = false;
+    for (int k = 0; k < PP; ++k) {
+        int pr = k;
+        double best = fabs(D[k][k]);
+        for (int r = k + 1; r < PP; ++r)
+            if (fabs(D[r][k]) > best) { best = fabs(D[r][k]); pr = r; }
+        if (!(best > 1e-300)) { singular = true; break; }
+        if (pr != k)
+            for (int c = 0; c < PP; ++c) {
+                double t = D[k][c]; D[k][c] = D[pr][c]; D[pr][c] = t;
+                t = Inv[k][c]; Inv[k][c] = Inv[pr][c]; Inv[pr][c] = t;
+            }
+        const double pinv = 1.0 / D[k][k];
+        for (int c = 0; c < PP; ++c) { D[k][c] *= pinv; Inv[k][c] *= pinv; }
+        for (int r = 0; r < PP; ++r) {
+            if (r == k) continue;
+            const double f = D[r][k];
+            for (int c = 0; c < PP; ++c) { D[r][c] -= f * D[k][c]; Inv[r][c] -= f * Inv[k][c]; }
+        }
+    }
+    if (singular) atomicOr(a.status, 2);
+    for (int r = 0; r < PP; ++r)
+        for (int c = 0; c < PP; ++c) a.Dinv[size_t(r * PP + c) * NF + e] = Inv[r][c];
+}
+
+// ---------------------------------------------------------------- P1 level operator
+// A = (M + (tau c)^2 K) / tau  (Eq. coarse_problem_upwind at the scale of the
+// trace operator on smooth traces); dinv = 1 / diag(A).
+__global__ void p1_combine_kernel(int nv, int nnz, const int32_t *diag, const double *mass, const double *stiff,
+                                  double tau, double ctau2, double *A, double *dinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nnz) A[i] = (mass[i] + ctau2 * stiff[i]) / tau;
+    if (i < nv) dinv[i] = tau / (mass[diag[i]] + ctau2 * stiff[diag[i]]);
+}
+
+// dense copy of a CSR matrix (n <= 1024), then in-place Gauss-Jordan inverse with
+// partial pivoting by one CTA.
+__global__ void csr_to_dense_kernel(int n, const int32_t *row_ptr, const int32_t *col, const double *A,
+                                    double *D) {
+    const int r = blockIdx.x;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) D[size_t(r) * n + c] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = row_ptr[r]; k < row_ptr[r + 1]; ++k) D[size_t(r) * n + col[k]] = A[k];
+}
+
+__global__ void dense_inverse_kernel(int n, double *Aw, double *inv, int32_t *status) {
+    // Aw: working copy [n][n], destroyed; inv: output [n][n]
+    __shared__ int piv_row;
+    __shared__ double red_v[1024];
+    __shared__ int red_i[1024];
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) inv[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        double best = -1.0;
+        int bi = k;
+        for (int r = k + tid; r < n; r += blockDim.x) {
+            double v = fabs(Aw[size_t(r) * n + k]);
+            if (v > best) { best = v; bi = r; }
+        }
+        red_v[tid] = best;
+        red_i[tid] = bi;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (tid < s && red_v[tid + s] > red_v[tid]) { red_v[tid] = red_v[tid + s]; red_i[tid] = red_i[tid + s]; }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            piv_row = red_i[0];
+            if (!(red_v[0] > 1e-300)) atomicOr(status, 4);
+        }
+        __syncthreads();
+        const int pr = piv_row;
+        if (pr != k)
+            for (int c = tid; c < n; c += blockDim.x) {
+                double t = Aw[size_t(k) * n + c]; Aw[size_t(k) * n + c] = Aw[size_t(pr) * n + c]; Aw[size_t(pr) * n + c] = t;
+                t = inv[size_t(k) * n + c]; inv[size_t(k) * n + c] = inv[size_t(pr) * n + c]; inv[size_t(pr) * n + c] = t;
+            }
+        __syncthreads();
+        const double pinv = 1.0 / Aw[size_t(k) * n + k];
+        __syncthreads();
+        for (int c = tid; c < n; c += blockDim.x) {
+            Aw[size_t(k) * n + c] *= pinv;
+            inv[size_t(k) * n + c] *= pinv;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < n * n; idx += blockDim.x) {
+            const int r = idx / n, c = idx % n;
+            if (r == k) continue;
+            const double f = Aw[size_t(r) * n + k];
+            if (c != k) Aw[size_t(r) * n + c] -= f * Aw[size_t(k) * n + c];
+            inv[size_t(r) * n + c] -= f * inv[size_t(k) * n + c];
+        }
+        __syncthreads();
+        for (int r = tid; r < n; r += blockDim.x)
+            if (r != k) Aw[size_t(r) * n + k] = 0.0;
+        __syncthreads();
+    }
+}
+
+__global__ void to_f32_kernel(const double *x, float *y, size_t n) {
+    size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = float(x[i]);
+}
+
+template <int P>
+cudaError_t condense_p(hdg_handle *h) {
+    using S = Sz<P>;
+    size_t smem = sizeof(double) * (S::NK * S::LDA + S::M * S::NK + S::LDA + S::NK);
+    cudaError_t e = cudaFuncSetAttribute(condense_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    CondenseArgs a;
+    a.N = h->N; a.tau = h->prm.tau; a.g = h->prm.g; a.H = h->prm.H; a.tau_s = h->tau_s;
+    a.ref = h->d_ref; a.X = h->d_X; a.fcell = h->d_fcell;
+    a.Xb = h->d_Xb; a.Rm = h->d_Rm; a.W = h->d_W; a.Scell = h->d_Scell; a.status = h->d_status;
+    condense_kernel<P><<<h->N, kCondenseThreads, smem, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t assemble_p(hdg_handle *h) {
+    AssembleArgs a;
+    a.N = h->N; a.NF = h->NF; a.Scell = h->d_Scell;
+    a.facet_of = h->d_facet_of; a.flip = h->d_flip; a.facet_cell = h->d_facet_cell; a.facet_edge = h->d_facet_edge;
+    a.Sval = h->d_Sval; a.Dinv = h->d_Dinv; a.nbr = h->d_nbr; a.status = h->d_status;
+    assemble_kernel<P><<<(h->NF + 127) / 128, 128, 0, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_condense(hdg_handle *h) {
+    switch (h->p) {
+        case 1: return condense_p<1>(h);
+        case 2: return condense_p<2>(h);
+        case 3: return condense_p<3>(h);
+        case 4: return condense_p<4>(h);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_assemble(hdg_handle *h) {
+    switch (h->p) {
+        case 1: return assemble_p<1>(h);
+        case 2: return assemble_p<2>(h);
+        case 3: return assemble_p<3>(h);
+        case 4: return assemble_p<4>(h);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_p1_combine(hdg_handle *h, DevLevel &L, double tau, double ctau2) {
+    int n = L.nnz > L.nv ? L.nnz : L.nv;
+    p1_combine_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(L.nv, L.nnz, L.diag, L.mass, L.stiff, tau, ctau2,
+                                                               L.A, L.dinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_inverse(hdg_handle *h, const DevLevel &L, double *work, double *inv, int n) {
+    csr_to_dense_kernel<<<n, 128, 0, h->stream>>>(n, L.row_ptr, L.col, L.A, work);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dense_inverse_kernel<<<1, 1024, 0, h->stream>>>(n, work, inv, h->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double *x, float *y, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    to_f32_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(x, y, n);
+    return cudaGetLastError();
+}
+
+}  // namespace hdg

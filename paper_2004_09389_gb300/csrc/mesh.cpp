@@ -1,0 +1,236 @@
+// Host-side mesh processing at hdg_setup: validation, facet numbering and
+// orientation, local 2-D cell coordinates, vertex->facet incidence for the
+// P1 restriction, and the nested P1 levels with their geometric mass and
+// stiffness matrices (Sec. 4.4: the upwind coarse space is P1 on the same
+// triangulation; coarser P1 levels serve the geometric V-cycle).
+#include "common.h"
+
+#include <algorithm>
+#include <cmath>
+#include <unordered_map>
+
+namespace hdg {
+
+namespace {
+
+std::string local_coords(const hdg_mesh_level &L, std::vector<double> &X) {
+    X.assign(size_t(L.n_cells) * 6, 0.0);
+    for (int K = 0; K < L.n_cells; ++K) {
+        double P[3][3] = {};
+        for (int i = 0; i < 3; ++i) {
+            int v = L.cell_vertices[3 * K + i];
+            for (int d = 0; d < L.dim; ++d) P[i][d] = L.vertex_xyz[size_t(v) * L.dim + d];
+            if (L.dim == 2 && L.cell_shift) {
+                P[i][0] += L.cell_shift[(size_t(K) * 3 + i) * 2 + 0];
+                P[i][1] += L.cell_shift[(size_t(K) * 3 + i) * 2 + 1];
+            }
+        }
+        double *x = &X[size_t(K) * 6];
+        if (L.dim == 2) {
+            for (int i = 0; i < 3; ++i) { x[2 * i] = P[i][0]; x[2 * i + 1] = P[i][1]; }
+        } else {
+            double d1[3], d2[3], e1[3], nn[3], e2[3];
+            for (int d = 0; d < 3; ++d) { d1[d] = P[1][d] - P[0][d]; d2[d] = P[2][d] - P[0][d]; }
+            double l1 = std::sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
+            if (!(l1 > 0)) return "degenerate cell";
+            for (int d = 0; d < 3; ++d) e1[d] = d1[d] / l1;
+            nn[0] = d1[1] * d2[2] - d1[2] * d2[1];
+            nn[1] = d1[2] * d2[0] - d1[0] * d2[2];
+            nn[2] = d1[0] * d2[1] - d1[1] * d2[0];
+            double ln = std::sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+            if (!(ln > 0)) return "degenerate cell";
+            for (int d = 0; d < 3; ++d) nn[d] /= ln;
+            e2[0] = nn[1] * e1[2] - nn[2] * e1[1];
+            e2[1] = nn[2] * e1[0] - nn[0] * e1[2];
+            e2[2] = nn[0] * e1[1] - nn[1] * e1[0];
+            for (int i = 0; i < 3; ++i) {
+                double dd[3] = {P[i][0] - P[0][0], P[i][1] - P[0][1], P[i][2] - P[0][2]};
+                x[2 * i] = dd[0] * e1[0] + dd[1] * e1[1] + dd[2] * e1[2];
+                x[2 * i + 1] = dd[0] * e2[0] + dd[1] * e2[1] + dd[2] * e2[2];
+            }
+        }
+        double det = (x[2] - x[0]) * (x[5] - x[1]) - (x[4] - x[0]) * (x[3] - x[1]);
+        if (!(det > 0)) return "cell " + std::to_string(K) + " is not counter-clockwise";
+    }
+    return "";
+}
+
+std::string check_level(const hdg_mesh_level &L, const char *what) {
+    if (L.n_vertices <= 0 || L.n_cells <= 0) return std::string(what) + ": empty mesh";
+    if (L.dim != 2 && L.dim != 3) return std::string(what) + ": dim must be 2 or 3";
+    if (!L.vertex_xyz || !L.cell_vertices) return std::string(what) + ": NULL array";
+    for (long i = 0; i < 3L * L.n_cells; ++i)
+        if (L.cell_vertices[i] < 0 || L.cell_vertices[i] >= L.n_vertices)
+            return std::string(what) + ": vertex index out of range";
+    return "";
+}
+
+// geometric P1 mass and stiffness on one level, CSR with sorted columns
+void p1_matrices(HostLevel &hl) {
+    std::vector<std::vector<std::pair<int, std::pair<double, double>>>> rows(hl.nv);
+    for (int K = 0; K < hl.nc; ++K) {
+        const double *x = &hl.X[size_t(K) * 6];
+        double J00 = x[2] - x[0], J01 = x[4] - x[0], J10 = x[3] - x[1], J11 = x[5] - x[1];
+        double det = J00 * J11 - J01 * J10;
+        // gradients of the barycentric coordinates: grad L = J^-T grad_ref L
+        double gref[3][2] = {{-1, -1}, {1, 0}, {0, 1}};
+        double G[3][2];
+        for (int a = 0; a < 3; ++a) {
+            G[a][0] = (J11 * gref[a][0] - J10 * gref[a][1]) / det;
+            G[a][1] = (-J01 * gref[a][0] + J00 * gref[a][1]) / det;
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double mv = det / 24.0 * (a == b ? 2.0 : 1.0);
+                double kv = 0.5 * det * (G[a][0] * G[b][0] + G[a][1] * G[b][1]);
+                rows[hl.cells[3 * K + a]].push_back({hl.cells[3 * K + b], {mv, kv}});
+            }
+    }
+    hl.row_ptr.assign(hl.nv + 1, 0);
+    hl.col.clear(); hl.mass.clear(); hl.stiff.clear(); hl.diag.assign(hl.nv, -1);
+    for (int v = 0; v < hl.nv; ++v) {
+        auto &r = rows[v];
+        std::sort(r.begin(), r.end(), [](auto &a, auto &b) { return a.first < b.first; });
+        for (size_t k = 0; k < r.size();) {
+            size_t k2 = k;
+            double m = 0, s = 0;
+            // sum duplicates in a fixed order (sorted by column, then cell order)
+            while (k2 < r.size() && r[k2].first == r[k].first) { m += r[k2].second.first; s += r[k2].second.second; ++k2; }
+            if (r[k].first == v) hl.diag[v] = int(hl.col.size());
+            hl.col.push_back(r[k].first);
+            hl.mass.push_back(m);
+            hl.stiff.push_back(s);
+            k = k2;
+        }
+        hl.row_ptr[v + 1] = int(hl.col.size());
+    }
+}
+
+}  // namespace
+
+std::string build_host_mesh(const hdg_mesh_desc *desc, HostMesh &hm) {
+    if (!desc) return "mesh descriptor is NULL";
+    const hdg_mesh_level &F = desc->fine;
+    std::string e = check_level(F, "fine level");
+    if (!e.empty()) return e;
+    if (F.dim == 2 && !F.cell_shift) return "flat meshes need cell_shift (periodic unwrapping)";
+    hm.dim = F.dim;
+    hm.nv = F.n_vertices;
+    hm.nc = F.n_cells;
+    hm.cells.assign(F.cell_vertices, F.cell_vertices + 3 * size_t(F.n_cells));
+    e = local_coords(F, hm.X);
+    if (!e.empty()) return "fine level: " + e;
+
+    // facets in order of first appearance over (cell, local edge)
+    hm.facet_of.assign(3 * size_t(hm.nc), -1);
+    hm.flip.assign(3 * size_t(hm.nc), 0);
+    std::unordered_map<uint64_t, int> ids;
+    ids.reserve(size_t(hm.nc) * 2);
+    std::vector<int> count;
+    hm.facet_verts.clear();
+    hm.facet_cell.clear();
+    hm.facet_edge.clear();
+    for (int K = 0; K < hm.nc; ++K) {
+        for (int i = 0; i < 3; ++i) {
+            int a = hm.cells[3 * K + (i + 1) % 3], b = hm.cells[3 * K + (i + 2) % 3];
+            if (a == b) return "cell with a repeated vertex";
+            int lo = std::min(a, b), hi = std::max(a, b);
+            uint64_t key = (uint64_t(uint32_t(lo)) << 32) | uint32_t(hi);
+            auto it = ids.find(key);
+            int f;
+            if (it == ids.end()) {
+                f = int(count.size());
+                ids.emplace(key, f);
+                count.push_back(0);
+                hm.facet_verts.push_back(lo);
+                hm.facet_verts.push_back(hi);
+                hm.facet_cell.push_back(K);
+                hm.facet_cell.push_back(-1);
+                hm.facet_edge.push_back(i);
+                hm.facet_edge.push_back(-1);
+            } else {
+                f = it->second;
+                if (count[f] >= 2) return "a facet has more than two cells (non-manifold mesh)";
+                hm.facet_cell[2 * f + 1] = K;
+                hm.facet_edge[2 * f + 1] = i;
+            }
+            count[f] += 1;
+            hm.facet_of[3 * K + i] = f;
+            hm.flip[3 * K + i] = a > b ? 1 : 0;
+        }
+    }
+    hm.nf = int(count.size());
+    for (int f = 0; f < hm.nf; ++f)
+        if (count[f] != 2) return "mesh is not closed: a facet has only one cell";
+    // the two cells must traverse a shared facet in opposite directions
+    for (int f = 0; f < hm.nf; ++f) {
+        int K0 = hm.facet_cell[2 * f], K1 = hm.facet_cell[2 * f + 1];
+        int i0 = hm.facet_edge[2 * f], i1 = hm.facet_edge[2 * f + 1];
+        if (hm.flip[3 * K0 + i0] == hm.flip[3 * K1 + i1]) return "inconsistent cell orientation";
+    }
+
+    // vertex -> incident facet ends
+    hm.v2f_ptr.assign(hm.nv + 1, 0);
+    for (int f = 0; f < hm.nf; ++f) {
+        hm.v2f_ptr[hm.facet_verts[2 * f] + 1]++;
+        hm.v2f_ptr[hm.facet_verts[2 * f + 1] + 1]++;
+    }
+    for (int v = 0; v < hm.nv; ++v) hm.v2f_ptr[v + 1] += hm.v2f_ptr[v];
+    hm.v2f.assign(hm.v2f_ptr[hm.nv], 0);
+    {
+        std::vector<int> fill(hm.v2f_ptr.begin(), hm.v2f_ptr.end() - 1);
+        for (int f = 0; f < hm.nf; ++f) {
+            hm.v2f[fill[hm.facet_verts[2 * f]]++] = 2 * f;
+            hm.v2f[fill[hm.facet_verts[2 * f + 1]]++] = 2 * f + 1;
+        }
+    }
+
+    // P1 levels
+    hm.levels.clear();
+    HostLevel L0;
+    L0.nv = hm.nv;
+    L0.nc = hm.nc;
+    L0.X = hm.X;
+    L0.cells = hm.cells;
+    p1_matrices(L0);
+    hm.levels.push_back(std::move(L0));
+    if (desc->n_coarse < 0 || (desc->n_coarse > 0 && !desc->coarse)) return "bad coarse level list";
+    for (int l = 0; l < desc->n_coarse; ++l) {
+        const hdg_mesh_level &C = desc->coarse[l];
+        std::string what = "coarse level " + std::to_string(l);
+        e = check_level(C, what.c_str());
+        if (!e.empty()) return e;
+        if (C.dim != F.dim) return what + ": dim differs from the fine level";
+        if (C.dim == 2 && !C.cell_shift) return what + ": flat meshes need cell_shift";
+        if (!C.parent) return what + ": parent array is NULL";
+        HostLevel hl;
+        hl.nv = C.n_vertices;
+        hl.nc = C.n_cells;
+        hl.cells.assign(C.cell_vertices, C.cell_vertices + 3 * size_t(C.n_cells));
+        e = local_coords(C, hl.X);
+        if (!e.empty()) return what + ": " + e;
+        const int nvf = hm.levels.back().nv;
+        hl.parent.assign(C.parent, C.parent + 2 * size_t(nvf));
+        for (long i = 0; i < 2L * nvf; ++i)
+            if (hl.parent[i] < 0 || hl.parent[i] >= hl.nv) return what + ": parent index out of range";
+        // restriction (transpose of the midpoint prolongation)
+        std::vector<std::vector<std::pair<int, double>>> ch(hl.nv);
+        for (int i = 0; i < nvf; ++i) {
+            int a = hl.parent[2 * i], b = hl.parent[2 * i + 1];
+            if (a == b) ch[a].push_back({i, 1.0});
+            else { ch[a].push_back({i, 0.5}); ch[b].push_back({i, 0.5}); }
+        }
+        hl.child_ptr.assign(hl.nv + 1, 0);
+        for (int c = 0; c < hl.nv; ++c) {
+            for (auto &pr : ch[c]) { hl.child_idx.push_back(pr.first); hl.child_w.push_back(pr.second); }
+            hl.child_ptr[c + 1] = int(hl.child_idx.size());
+        }
+        p1_matrices(hl);
+        hm.levels.push_back(std::move(hl));
+    }
+    if (hm.levels.back().nv > 1024)
+        return "the coarsest P1 level has more than 1024 vertices; pass more coarse levels";
+    return "";
+}
+
+}  // namespace hdg

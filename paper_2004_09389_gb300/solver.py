@@ -1,0 +1,131 @@
+"""One HDG solver handle (argument marshalling around ``include/hdg.h``)."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+class HDGSolver:
+    """Handle for one mesh and one parameter set.
+
+    ``mesh`` is any object with ``dim``, ``vertex_xyz``, ``cell_vertices``,
+    ``cell_shift`` and an optional list ``levels`` of coarse P1 levels (each with
+    ``parent``).  Keyword arguments override the fields of ``hdg_params``.
+    ``stream``: a ``cudaStream_t`` value; by default the current PyTorch stream
+    so that ``*_dev`` calls on tensors are ordered with PyTorch's work.
+    """
+
+    def __init__(self, mesh, p: int, tau: float, g: float = 1.0, H: float = 1.0, f_vertex=None,
+                 stream=None, condense: bool = True, **params):
+        self.lib = L.load()
+        prm = L.default_params()
+        prm.p, prm.tau, prm.g, prm.H = int(p), float(tau), float(g), float(H)
+        self._keep = []
+        if f_vertex is not None:
+            fv = np.ascontiguousarray(f_vertex, dtype=np.float64)
+            self._keep.append(fv)
+            prm.f_vertex = fv.ctypes.data_as(C.POINTER(C.c_double))
+        for k, v in params.items():
+            if not hasattr(prm, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(prm, k, v)
+        desc = L.make_mesh_desc(mesh, self._keep)
+        h = C.c_void_p()
+        st = _torch_stream() if stream is None else stream
+        rc = self.lib.hdg_setup(C.byref(desc), C.byref(prm), C.c_void_p(st or 0), C.byref(h))
+        self._keep = []
+        if rc != 0:
+            raise L.HDGError(rc, self.lib.hdg_last_error(None).decode())
+        self.h = h
+        self.p = int(p)
+        sz = (C.c_int64 * 6)()
+        L.check(h, self.lib.hdg_get_sizes(h, sz))
+        self.n_cells, self.n_facets, self.n_trace, self.n_p, self.m, self.n_levels = (int(v) for v in sz)
+        if condense:
+            self.condense()
+
+    # ---------------------------------------------------------------- lifecycle
+    def condense(self) -> None:
+        L.check(self.h, self.lib.hdg_condense(self.h))
+
+    def set_tau(self, tau: float) -> None:
+        L.check(self.h, self.lib.hdg_set_tau(self.h, C.c_double(tau)))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.hdg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- host buffers
+    def solve(self, r_u: np.ndarray, r_h: np.ndarray, allow_fail: bool = False):
+        """Steps 1-2 from host arrays; returns (lambda [n_facets, p+1], info dict)."""
+        ru = np.ascontiguousarray(r_u, dtype=np.float64)
+        rh = np.ascontiguousarray(r_h, dtype=np.float64)
+        assert ru.shape == (self.n_cells, 2, self.n_p) and rh.shape == (self.n_cells, self.n_p)
+        lam = np.empty((self.n_facets, self.p + 1))
+        info = L.hdg_solve_info()
+        rc = self.lib.hdg_solve(self.h, ru.ctypes.data, rh.ctypes.data, lam.ctypes.data, C.byref(info))
+        L.check(self.h, rc, allow=(L.HDG_ENOCONV, L.HDG_EBREAKDOWN) if allow_fail else ())
+        return lam, info.as_dict()
+
+    def recover(self, r_u=None, r_h=None, lam=None):
+        """Step 3 from host arrays; None selects the last solve's data."""
+        u = np.empty((self.n_cells, 2, self.n_p))
+        h = np.empty((self.n_cells, self.n_p))
+        ru = None if r_u is None else np.ascontiguousarray(r_u, dtype=np.float64)
+        rh = None if r_h is None else np.ascontiguousarray(r_h, dtype=np.float64)
+        lm = None if lam is None else np.ascontiguousarray(lam, dtype=np.float64)
+        rc = self.lib.hdg_recover(self.h, L._ptr(ru), L._ptr(rh), L._ptr(lm), u.ctypes.data, h.ctypes.data)
+        L.check(self.h, rc)
+        return u, h
+
+    # ---------------------------------------------------------------- device buffers
+    def solve_dev(self, r_u, r_h, lam, allow_fail: bool = False) -> dict:
+        info = L.hdg_solve_info()
+        rc = self.lib.hdg_solve_dev(self.h, L._ptr(r_u), L._ptr(r_h), L._ptr(lam), C.byref(info))
+        L.check(self.h, rc, allow=(L.HDG_ENOCONV, L.HDG_EBREAKDOWN) if allow_fail else ())
+        return info.as_dict()
+
+    def recover_dev(self, r_u, r_h, lam, u, h) -> None:
+        L.check(self.h, self.lib.hdg_recover_dev(self.h, L._ptr(r_u), L._ptr(r_h), L._ptr(lam), L._ptr(u), L._ptr(h)))
+
+    def trace_apply_dev(self, x, y) -> None:
+        L.check(self.h, self.lib.hdg_trace_apply_dev(self.h, L._ptr(x), L._ptr(y)))
+
+    def condensed_rhs_dev(self, r_u, r_h, g) -> None:
+        L.check(self.h, self.lib.hdg_condensed_rhs_dev(self.h, L._ptr(r_u), L._ptr(r_h), L._ptr(g)))
+
+    def precond_apply_dev(self, v, z) -> None:
+        L.check(self.h, self.lib.hdg_precond_apply_dev(self.h, L._ptr(v), L._ptr(z)))
+
+    # ---------------------------------------------------------------- inspection
+    def facets(self):
+        fo = np.empty((self.n_cells, 3), np.int32)
+        fl = np.empty((self.n_cells, 3), np.int32)
+        fv = np.empty((self.n_facets, 2), np.int32)
+        L.check(self.h, self.lib.hdg_get_facets(self.h, fo.ctypes.data, fl.ctypes.data, fv.ctypes.data))
+        return fo, fl, fv
+
+    def cell_schur(self) -> np.ndarray:
+        S = np.empty((self.n_cells, self.m, self.m))
+        L.check(self.h, self.lib.hdg_get_cell_schur(self.h, S.ctypes.data))
+        return S

@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Tolerances (FP64 path): cell blocks, trace operator, right-hand side,
+preconditioner and recovery agree to <= 1e-12 relative (same arithmetic up to
+rounding order, operators of norm ~1); the end-to-end solve, run to a true
+relative residual of 1e-13, agrees with the oracle's direct solve to <= 1e-10
+relative in every field (lambda, u, h).  Mixed mode: see test_mixed_precision.
+Integer data (facet numbering, orientation) must match exactly.
+"""
+import numpy as np
+import pytest
+
+import hdg_inputs as I
+from oracle.hdg import HDGProblem
+from oracle.solver import TwoLevelPreconditioner, gmres
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2004_09389_gb300 import build
+    build.build()
+
+
+def _solver(mesh, p, tau, g, H, f, **kw):
+    from paper_2004_09389_gb300 import HDGSolver
+    return HDGSolver(mesh, p, tau, g, H, f_vertex=f, **kw)
+
+
+def _case(kind, p, seed=0):
+    """Small meshes spanning several 256-thread tiles with a ragged tail."""
+    if kind == "flat":
+        mesh = I.periodic_square_hierarchy(12, n_coarsest=3)       # 288 cells, 432 facets
+        g, H, f = 1.3, 0.7, I.coriolis_flat(mesh, 1.0)
+    else:
+        mesh = I.sphere_hierarchy(2, 1.0, r_coarsest=0)            # 320 cells, 480 facets
+        g, H, f = 1.0, 1.0, I.coriolis_sphere(mesh, 0.5)
+    tau = 8 * mesh.h / np.sqrt(g * H)
+    prob = HDGProblem(mesh, p, tau=tau, g=g, H=H, f_vertex=f)
+    rng = np.random.default_rng(seed)
+    ru = rng.standard_normal((mesh.n_cells, 2, prob.np))
+    rh = rng.standard_normal((mesh.n_cells, prob.np))
+    return mesh, prob, (tau, g, H, f), ru, rh
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+CASES = [("flat", 1), ("flat", 2), ("flat", 3), ("flat", 4), ("sphere", 1), ("sphere", 3)]
+
+
+@pytest.mark.parametrize("kind", ["flat", "sphere"])
+def test_facet_numbering_matches_oracle(kind):
+    mesh, prob, (tau, g, H, f), _, _ = _case(kind, 1)
+    s = _solver(mesh, 1, tau, g, H, f, condense=False)
+    fo, fl, fv = s.facets()
+    assert (fo == prob.facet_of).all()
+    assert (fl == prob.flip.astype(np.int32)).all()
+    assert (fv == prob.facet_verts).all()
+    s.close()
+
+
+@pytest.mark.parametrize("kind,p", CASES)
+def test_cell_schur_matches_oracle(kind, p):
+    mesh, prob, (tau, g, H, f), _, _ = _case(kind, p)
+    s = _solver(mesh, p, tau, g, H, f)
+    S = s.cell_schur()
+    S0 = np.stack([prob.cell_schur(K) for K in range(prob.N)])
+    assert np.abs(S - S0).max() <= 1e-12 * np.abs(S0).max()
+    s.close()
+
+
+@pytest.mark.parametrize("kind,p", CASES)
+def test_trace_apply_matches_oracle(kind, p):
+    mesh, prob, (tau, g, H, f), _, _ = _case(kind, p)
+    s = _solver(mesh, p, tau, g, H, f)
+    x = np.random.default_rng(1).standard_normal(prob.n_trace)
+    y0 = prob.trace_operator() @ x
+    y = torch.empty(prob.n_trace, dtype=torch.float64, device="cuda")
+    s.trace_apply_dev(_dev(x), y)
+    torch.cuda.synchronize()
+    assert _rel(y.cpu().numpy(), y0) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("kind,p", CASES)
+def test_condensed_rhs_matches_oracle(kind, p):
+    mesh, prob, (tau, g, H, f), ru, rh = _case(kind, p)
+    s = _solver(mesh, p, tau, g, H, f)
+    g0 = prob.condensed_rhs(ru, rh)
+    gd = torch.empty(prob.n_trace, dtype=torch.float64, device="cuda")
+    s.condensed_rhs_dev(_dev(ru), _dev(rh), gd)
+    torch.cuda.synchronize()
+    assert _rel(gd.cpu().numpy(), g0) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("kind,p", [("flat", 1), ("flat", 3), ("sphere", 2)])
+@pytest.mark.parametrize("n_pre,n_post", [(2, 2), (0, 1), (1, 0), (3, 3)])
+def test_precond_matches_oracle(kind, p, n_pre, n_post):
+    mesh, prob, (tau, g, H, f), _, _ = _case(kind, p)
+    s = _solver(mesh, p, tau, g, H, f, n_pre=n_pre, n_post=n_post)
+    S = prob.trace_operator()
+    pc = TwoLevelPreconditioner(prob, mesh, S, n_pre=n_pre, n_post=n_post, coarse="gmg")
+    v = np.random.default_rng(2).standard_normal(prob.n_trace)
+    z0 = pc(v)
+    z = torch.empty(prob.n_trace, dtype=torch.float64, device="cuda")
+    s.precond_apply_dev(_dev(v), z)
+    torch.cuda.synchronize()
+    assert _rel(z.cpu().numpy(), z0) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("kind,p", CASES)
+def test_solve_and_recover_match_oracle(kind, p):
+    mesh, prob, (tau, g, H, f), ru, rh = _case(kind, p)
+    s = _solver(mesh, p, tau, g, H, f, rtol=1e-13)
+    lam, info = s.solve(ru, rh)
+    u, h = s.recover()
+    (u0, h0), lam0 = prob.solve_condensed(ru, rh)
+    assert info["true_rel_res"] <= 1e-13
+    assert _rel(lam, lam0) <= 1e-10
+    assert _rel(u, u0) <= 1e-10
+    assert _rel(h, h0) <= 1e-10
+    # recover from an explicit lambda (the oracle's) matches the oracle too
+    u1, h1 = s.recover(ru, rh, lam0.reshape(lam.shape))
+    assert _rel(u1, u0) <= 1e-12 and _rel(h1, h0) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("kind,p", [("flat", 2), ("sphere", 2)])
+def test_iteration_count_matches_oracle(kind, p):
+    """Same algorithm on both sides (FGMRES(30) + the same V-cycle): the
+    iteration counts to rtol 1e-8 agree within one."""
+    mesh, prob, (tau, g, H, f), ru, rh = _case(kind, p)
+    s = _solver(mesh, p, tau, g, H, f, rtol=1e-8)
+    _, info = s.solve(ru, rh)
+    S = prob.trace_operator()
+    pc = TwoLevelPreconditioner(prob, mesh, S, coarse="gmg")
+    _, info0 = gmres(lambda v: S @ v, prob.condensed_rhs(ru, rh), pc, restart=30, rtol=1e-8)
+    assert abs(info["iters"] - info0["iters"]) <= 1
+    s.close()
+
+
+def test_device_entry_points_match_host_ones():
+    mesh, prob, (tau, g, H, f), ru, rh = _case("flat", 2)
+    s = _solver(mesh, 2, tau, g, H, f, rtol=1e-12)
+    lam, _ = s.solve(ru, rh)
+    u, h = s.recover()
+    lam_d = torch.empty((prob.n_facets, 3), dtype=torch.float64, device="cuda")
+    s.solve_dev(_dev(ru), _dev(rh), lam_d)
+    u_d = torch.empty((prob.N, 2, prob.np), dtype=torch.float64, device="cuda")
+    h_d = torch.empty((prob.N, prob.np), dtype=torch.float64, device="cuda")
+    s.recover_dev(_dev(ru), _dev(rh), lam_d, u_d, h_d)
+    torch.cuda.synchronize()
+    assert np.array_equal(lam_d.cpu().numpy(), lam)
+    assert np.array_equal(u_d.cpu().numpy(), u) and np.array_equal(h_d.cpu().numpy(), h)
+    s.close()
+
+
+@pytest.mark.parametrize("kind,p", [("flat", 2), ("sphere", 3)])
+def test_mixed_precision(kind, p):
+    """FP32 inner FGMRES + FP32 V-cycle with FP64 iterative refinement reaches the
+    FP64 residual target; stated tolerance vs the oracle: 1e-8 relative at
+    rtol 1e-10 (the trace operator's condition number here is < 100)."""
+    from paper_2004_09389_gb300 import HDG_MIXED_FP32
+    mesh, prob, (tau, g, H, f), ru, rh = _case(kind, p)
+    s = _solver(mesh, p, tau, g, H, f, rtol=1e-10, precision=HDG_MIXED_FP32)
+    lam, info = s.solve(ru, rh)
+    u, h = s.recover()
+    (u0, h0), lam0 = prob.solve_condensed(ru, rh)
+    assert info["true_rel_res"] <= 1e-10
+    assert info["outer"] >= 2                  # refinement did happen
+    assert _rel(lam, lam0) <= 1e-8 and _rel(u, u0) <= 1e-8 and _rel(h, h0) <= 1e-8
+    s.close()
+
+
+def test_zero_rhs_and_nan_rhs():
+    from paper_2004_09389_gb300 import HDGError
+    mesh, prob, (tau, g, H, f), ru, rh = _case("flat", 1)
+    s = _solver(mesh, 1, tau, g, H, f)
+    lam, info = s.solve(np.zeros_like(ru), np.zeros_like(rh))
+    assert np.all(lam == 0) and info["iters"] == 0
+    rh2 = rh.copy()
+    rh2[3, 1] = np.nan
+    with pytest.raises(HDGError) as ei:
+        s.solve(ru, rh2)
+    assert ei.value.code == -5          # HDG_ENAN
+    # the handle stays usable afterwards
+    lam, info = s.solve(ru, rh)
+    assert info["true_rel_res"] <= 1e-8
+    s.close()
+
+
+def test_iteration_cap_reports_noconv():
+    from paper_2004_09389_gb300 import HDGError
+    mesh, prob, (tau, g, H, f), ru, rh = _case("flat", 2)
+    s = _solver(mesh, 2, tau, g, H, f, rtol=1e-14, max_iter=3)
+    with pytest.raises(HDGError) as ei:
+        s.solve(ru, rh)
+    assert ei.value.code == -3          # HDG_ENOCONV
+    lam, info = s.solve(ru, rh, allow_fail=True)
+    assert info["iters"] == 3 and info["true_rel_res"] < 1.0
+    s.close()
+
+
+def test_invalid_arguments():
+    from paper_2004_09389_gb300 import HDGError
+    mesh, prob, (tau, g, H, f), ru, rh = _case("flat", 1)
+    for kw in ({"p": 5}, {"tau": -1.0}, {"restart": 0}):
+        args = dict(p=1, tau=tau)
+        args.update(kw)
+        with pytest.raises(HDGError) as ei:
+            _solver(mesh, args.pop("p"), args.pop("tau"), g, H, f, **args)
+        assert ei.value.code == -1
+    # open mesh: drop one cell
+    bad = I.periodic_square(4)
+    bad.cell_vertices = bad.cell_vertices[1:]
+    bad.cell_shift = bad.cell_shift[1:]
+    with pytest.raises(HDGError) as ei:
+        _solver(bad, 1, 0.1, 1.0, 1.0, None)
+    assert ei.value.code == -1
+    # solve before condense
+    s = _solver(mesh, 1, tau, g, H, f, condense=False)
+    with pytest.raises(HDGError) as ei:
+        s.solve(ru, rh)
+    assert ei.value.code == -9
+    s.close()
