@@ -1,0 +1,379 @@
+"""Benchmark: HDG trace solves/s to a relative residual of 1e-8 on one GB300.
+
+Workload (flat periodic square, 256 x 256 x 2 = 131,072 triangles): side
+5.12e6 m, g = 9.81, H = 1e3 m, f = 1e-4 1/s, acoustic Courant number
+c tau / h = 8, DG degree p = 3 (local blocks 30, trace blocks 12), right-hand
+sides = seeded zero-mean unit-RMS Gaussian random fields with a k^-3 power
+spectrum (synthetic data shaped like the paper's flat-domain workload).
+
+A step = one solve: condensed right-hand side (step 1), (F)GMRES with the
+two-level V-cycle to a true relative residual of 1e-8 (step 2), recovery of
+(u, h) (step 3).  ``value`` is the mixed-precision solver (FP32 inner solves,
+FP64 iterative refinement); the plain FP64 solver on the same GPU is reported
+beside it (``plain_fp64``), as is the CPU oracle on a bounded sample
+(``cpu_baseline``).  ``--impl reference`` times the CPU oracle alone.
+
+Multi-GPU: replicas only (independent solves per rank, no collective on the
+data path); launched by torchrun, rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HDG trace solves/s to rel.res 1e-8: mixed/learned vs plain FP64 MG, same GB300"
+SIDE, NGRID, G, DEPTH, F0 = 5.12e6, 256, 9.81, 1.0e3, 1.0e-4
+SAMPLE_N = 64            # oracle sample: 64 x 64 x 2 = 8,192 triangles of the same workload
+
+
+def workload(n: int, p: int, courant: float, seed: int):
+    import hdg_inputs as I
+    mesh = I.periodic_square_hierarchy(n, side=SIDE * n / NGRID, n_coarsest=4)
+    c = math.sqrt(G * DEPTH)
+    tau = courant * mesh.h / c
+    f = I.coriolis_flat(mesh, F0)
+    ru, rh = I.gaussian_field_rhs(mesh, p, seed, grid=max(4 * n, 128), kmax=n / 2)
+    return mesh, tau, f, ru, rh
+
+
+def workload_name(n, p, courant):
+    return (f"flat periodic {n}x{n}x2 ({2 * n * n:,} triangles), HDG p={p}, acoustic Courant {courant:g}, "
+            f"g={G}, H={DEPTH:g} m, f={F0:g}, k^-3 Gaussian RHS")
+
+
+# ---------------------------------------------------------------- algorithmic bytes per launch
+def trace_bytes(cat: str, NF: int, pp: int) -> float:
+    """Minimum bytes a facet-row kernel must move: the operator values (5 blocks
+    of (p+1)^2 per facet), the neighbour ids, the inverted facet blocks where
+    used, and each trace vector it touches read or written once."""
+    w = 8 if cat.endswith("64") else 4
+    S = 5 * pp * pp * w + 16
+    vec = pp * w
+    base = cat[:-2]
+    if base == "apply":
+        per = S + 2 * vec
+    elif base == "residual":
+        per = S + 3 * vec
+    elif base == "smooth":
+        per = S + pp * pp * w + 3 * vec
+    elif base == "smooth_first":
+        per = pp * pp * w + 2 * vec
+    else:
+        raise KeyError(cat)
+    return float(NF) * per
+
+
+# ---------------------------------------------------------------- clocks
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(p: int, courant: float, steps: int, seed: int = 0) -> dict:
+    """Time the oracle (plain FP64 FGMRES + V-cycle, as it stands) on the
+    sample mesh; run in a spawned single-threaded process."""
+    import numpy as np
+    from oracle.hdg import HDGProblem
+    from oracle.solver import TwoLevelPreconditioner, gmres
+    mesh, tau, f, ru, rh = workload(SAMPLE_N, p, courant, seed)
+    prob = HDGProblem(mesh, p, tau=tau, g=G, H=DEPTH, f_vertex=f)
+    S = prob.trace_operator()
+    pc = TwoLevelPreconditioner(prob, mesh, S, coarse="gmg")
+    times, iters = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        gvec = prob.condensed_rhs(ru, rh)
+        lam, info = gmres(lambda v: S @ v, gvec, pc, restart=30, rtol=1e-8)
+        prob.recover(lam, ru, rh)
+        times.append(time.perf_counter() - t0)
+        iters.append(info["iters"])
+    return {"sec_per_solve": float(np.median(times)), "iters": iters, "n_cells": mesh.n_cells}
+
+
+def run_oracle_subprocess(p: int, courant: float, steps: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--p", str(p), "--courant", str(courant),
+           "--steps", str(steps)]
+    res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    if res.returncode != 0:
+        raise RuntimeError(f"oracle sample failed: {res.stderr[-2000:]}")
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(p, courant, steps):
+    t0 = time.perf_counter()
+    r = run_oracle_subprocess(p, courant, steps)
+    n_full = 2 * NGRID * NGRID
+    val = (1.0 / r["sec_per_solve"]) * (r["n_cells"] / n_full)
+    return {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"{SAMPLE_N}x{SAMPLE_N}x2 = {r['n_cells']} triangles of the same workload (same p, Courant, "
+                       f"RHS generator), {steps} solves, median time per solve scaled to 131,072 triangles by the "
+                       f"cell ratio; single-threaded NumPy/SciPy"),
+            "sec_per_solve_sample": r["sec_per_solve"], "iters": r["iters"],
+            "wall_s": time.perf_counter() - t0}
+
+
+# ---------------------------------------------------------------- GPU arms
+def gpu_arm(args, rank: int, world: int):
+    import numpy as np
+    import torch
+    from paper_2004_09389_gb300 import HDGSolver, HDG_FP64, HDG_MIXED_FP32, build
+    build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    mesh, tau, f, ru, rh = workload(NGRID, args.p, args.courant, args.seed + rank)
+    ru_d = torch.from_numpy(ru).to(dev)
+    rh_d = torch.from_numpy(rh).to(dev)
+    out = {}
+    for arm, prec in (("mixed", HDG_MIXED_FP32), ("fp64", HDG_FP64)):
+        s = HDGSolver(mesh, args.p, tau, G, DEPTH, f_vertex=f, rtol=args.rtol, precision=prec,
+                      inner_rtol=args.inner_rtol, restart=args.restart)
+        NF, pp = s.n_facets, args.p + 1
+        lam_d = torch.empty((NF, pp), dtype=torch.float64, device=dev)
+        u_d = torch.empty((s.n_cells, 2, s.n_p), dtype=torch.float64, device=dev)
+        h_d = torch.empty((s.n_cells, s.n_p), dtype=torch.float64, device=dev)
+        infos = []
+
+        def step():
+            infos.append(s.solve_dev(ru_d, rh_d, lam_d))
+            s.recover_dev(ru_d, rh_d, lam_d, u_d, h_d)
+
+        for _ in range(args.warmup):
+            step()
+        infos.clear()
+        s.profile_enable(timing=False)          # launch counters only
+        stream = torch.cuda.current_stream()
+        barrier()
+        clocks = ClockSampler(dev.index) if arm == "mixed" else None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        clk = clocks.stop() if clocks else None
+        launches = sum(n for _, n in s.profile_read().values())
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        # second pass with per-kernel event timing for the roofline
+        s.profile_enable(timing=True)
+        for _ in range(max(1, min(args.steps, 3))):
+            step()
+        prof = s.profile_read()
+        # end to end through the host-pointer C-ABI calls (pinned host buffers)
+        ru_h = torch.from_numpy(ru).pin_memory()
+        rh_h = torch.from_numpy(rh).pin_memory()
+        lam_h = torch.empty((NF, pp), dtype=torch.float64).pin_memory()
+        u_h = torch.empty((s.n_cells, 2, s.n_p), dtype=torch.float64).pin_memory()
+        hh_h = torch.empty((s.n_cells, s.n_p), dtype=torch.float64).pin_memory()
+        import ctypes as C
+        from paper_2004_09389_gb300 import _lib
+        info = _lib.hdg_solve_info()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _lib.check(s.h, s.lib.hdg_solve(s.h, ru_h.data_ptr(), rh_h.data_ptr(), lam_h.data_ptr(), C.byref(info)))
+            _lib.check(s.h, s.lib.hdg_recover(s.h, None, None, None, u_h.data_ptr(), hh_h.data_ptr()))
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        h2d = ru.nbytes + rh.nbytes
+        d2h = lam_h.numel() * 8 + u_h.numel() * 8 + hh_h.numel() * 8
+        out[arm] = dict(ms=ms, infos=infos, clocks=clk, launches=launches, prof=prof, e2e_s=e2e_s,
+                        h2d=h2d, d2h=d2h, NF=NF, pp=pp, n_cells=s.n_cells)
+        s.close()
+        torch.cuda.empty_cache()
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+def roofline(arm: dict, peaks: dict) -> dict:
+    prof, NF, pp = arm["prof"], arm["NF"], arm["pp"]
+    cats = [c for c in prof if c.startswith(("apply", "residual", "smooth"))]
+    total = sum(ms for ms, _ in prof.values())
+    best = max(cats, key=lambda c: prof[c][0])
+    ms, n = prof[best]
+    per_launch = trace_bytes(best, NF, pp)
+    achieved = per_launch * n / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        tr = json.load(open(tpath))
+        ent = tr.get(f"{best}_p{pp - 1}")
+        if ent and ent.get("source_sha") == source_sha():
+            traffic = ent["bytes_per_launch"]
+    family_ms = sum(prof[c][0] for c in cats)
+    return {"bound": "hbm", "kernel": best, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes_per_launch": per_launch,
+            "launches": n, "avg_us": ms * 1e3 / max(n, 1), "share_of_kernel_time": ms / total if total else None,
+            "facet_row_family_share": family_ms / total if total else None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback"}
+
+
+def source_sha() -> str:
+    import hashlib
+    hsh = hashlib.sha256()
+    for name in ("k_trace.cu", "common.h"):
+        hsh.update(open(os.path.join(ROOT, "paper_2004_09389_gb300", "csrc", name), "rb").read())
+    return hsh.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--courant", type=float, default=8.0)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--inner-rtol", dest="inner_rtol", type=float, default=1e-4)
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--oracle-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    args = ap.parse_args()
+
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.p, args.courant, args.steps)))
+        return
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    name = workload_name(NGRID, args.p, args.courant)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = args.warmup + args.steps
+        t0 = time.perf_counter()
+        r = run_oracle_subprocess(args.p, args.courant, max(steps, 1))
+        n_full = 2 * NGRID * NGRID
+        val = (1.0 / r["sec_per_solve"]) * (r["n_cells"] / n_full)
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / val, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": name, "rtol": args.rtol},
+                "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"{SAMPLE_N}x{SAMPLE_N}x2 = {r['n_cells']} triangles per step, median "
+                                           f"time per solve scaled to 131,072 triangles by the cell ratio"},
+                "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "iters": r["iters"], "wall_s": time.perf_counter() - t0}
+        print(json.dumps(line))
+        return
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # spawned before the first CUDA call
+        cpu = cpu_baseline_entry(args.p, args.courant, args.oracle_steps)
+    res = gpu_arm(args, rank, world)
+    if rank != 0:
+        return
+    peaks = {}
+    ppath = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(ppath):
+        peaks = json.load(open(ppath))
+    mx, fp = res["mixed"], res["fp64"]
+    K = args.steps
+    value = world * K / (mx["ms"] * 1e-3)
+    fp_value = world * K / (fp["ms"] * 1e-3)
+    it_mx = [i["iters"] for i in mx["infos"]]
+    it_fp = [i["iters"] for i in fp["infos"]]
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": mx["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 inner + f64 refinement", "data": "synthetic",
+        "config": {"workload": name, "n_cells": mx["n_cells"], "n_trace_dofs": mx["NF"] * mx["pp"],
+                   "rtol": args.rtol, "inner_rtol": args.inner_rtol, "restart": args.restart,
+                   "smoother": "2+2 block-Jacobi omega=2/3", "coarse": "P1 geometric V-cycle 256->4",
+                   "l2": "inputs larger than L2 (operator data ~1.8 GB resident in HBM), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "iters": it_mx, "true_rel_res": [i["true_rel_res"] for i in mx["infos"]],
+        "plain_fp64": {"value": fp_value, "unit": "solves/s", "ms_per_step": fp["ms"] / K, "iters": it_fp,
+                       "true_rel_res": [i["true_rel_res"] for i in fp["infos"]],
+                       "roofline": roofline(fp, peaks)},
+        "speedup_vs_plain_fp64": value / fp_value,
+        "roofline": roofline(mx, peaks),
+        "kernel_ms": {k: v[0] for k, v in mx["prof"].items() if v[1]},
+        "gpu_launches": mx["launches"],
+        "clocks": mx["clocks"],
+        "e2e": {"value": world * K / mx["e2e_s"], "unit": "solves/s", "h2d_bytes_per_step": mx["h2d"],
+                "d2h_bytes_per_step": mx["d2h"]},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -183,6 +183,30 @@ HDG_API int hdg_get_facets(const hdg_handle *h, int32_t *facet_of, int32_t *flip
  * local vertex (i+1)%3 to (i+2)%3), [n_cells][3(p+1)][3(p+1)].  Needs condense. */
 HDG_API int hdg_get_cell_schur(hdg_handle *h, double *S);
 
+/* Kernel accounting.  Launch counts per category are always kept; with
+ * timing enabled every launch is bracketed by CUDA events on the handle's
+ * stream and the elapsed times are summed per category (read at the
+ * library's own synchronisation points).  hdg_profile_enable resets both.
+ * ms / launches: arrays of HDG_PROF_N entries (either may be NULL). */
+#define HDG_PROF_APPLY64        0   /* y = S x, FP64                         */
+#define HDG_PROF_RESIDUAL64     1   /* r = b - S x, FP64                     */
+#define HDG_PROF_SMOOTH64       2   /* block-Jacobi sweep, FP64              */
+#define HDG_PROF_SMOOTH_FIRST64 3   /* first sweep from zero, FP64           */
+#define HDG_PROF_APPLY32        4
+#define HDG_PROF_RESIDUAL32     5
+#define HDG_PROF_SMOOTH32       6
+#define HDG_PROF_SMOOTH_FIRST32 7
+#define HDG_PROF_TRANSFER       8   /* trace <-> P1 restriction / prolongation */
+#define HDG_PROF_P1             9   /* P1 V-cycle kernels                    */
+#define HDG_PROF_KRYLOV        10   /* dots, updates, Givens, conversions    */
+#define HDG_PROF_RHS           11   /* step 1                                */
+#define HDG_PROF_RECOVER       12   /* step 3                                */
+#define HDG_PROF_LAYOUT        13   /* lambda layout conversions             */
+#define HDG_PROF_CONDENSE      14   /* condensation and assembly             */
+#define HDG_PROF_N             15
+HDG_API int hdg_profile_enable(hdg_handle *h, int timing_on);
+HDG_API int hdg_profile_read(hdg_handle *h, double *ms, int64_t *launches);
+
 HDG_API int hdg_destroy(hdg_handle *h);
 HDG_API const char *hdg_last_error(const hdg_handle *h);
 

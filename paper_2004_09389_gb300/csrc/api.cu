@@ -44,6 +44,8 @@ struct Workspace {
     // small device arrays
     double *Hm = nullptr, *cs = nullptr, *sn = nullptr, *sv = nullptr, *h1 = nullptr, *h2 = nullptr;
     double *nrm2 = nullptr, *est = nullptr, *y = nullptr, *partial = nullptr;
+    double *scal = nullptr;   // restart normalisation of a Krylov cycle
+    double *beta = nullptr;   // refinement scale ||g - S x|| (mixed mode)
     int32_t *flags = nullptr;
     // pinned readback
     double *host_buf = nullptr;   // [4]
@@ -106,6 +108,53 @@ std::string check_params(const hdg_params *prm) {
     return "";
 }
 
+// ---------------------------------------------------------------- kernel accounting
+
+cudaEvent_t prof_event(hdg_handle *h) {
+    Prof &P = h->prof;
+    if (!P.pool.empty()) {
+        cudaEvent_t e = P.pool.back();
+        P.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Sum the elapsed times of the bracketed launches; call after a stream sync.
+void prof_flush(hdg_handle *h) {
+    Prof &P = h->prof;
+    for (auto &q : P.pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) P.ms[q.cat] += ms;
+        P.pool.push_back(q.a);
+        P.pool.push_back(q.b);
+    }
+    P.pending.clear();
+}
+
+// Launch through f(), counting nk kernels in category cat and, with timing
+// on, bracketing them with events on the handle's stream.
+template <class F>
+cudaError_t klaunch(hdg_handle *h, int cat, int nk, F &&f) {
+    Prof &P = h->prof;
+    P.launches[cat] += nk;
+    if (!P.on) return f();
+    cudaEvent_t a = prof_event(h), b = prof_event(h);
+    cudaEventRecord(a, h->stream);
+    cudaError_t e = f();
+    cudaEventRecord(b, h->stream);
+    P.pending.push_back({cat, a, b});
+    return e;
+}
+#define KL(cat, nk, expr) klaunch(h, (cat), (nk), [&]() { return (expr); })
+
+template <typename T> constexpr int cat_apply() { return sizeof(T) == 8 ? HDG_PROF_APPLY64 : HDG_PROF_APPLY32; }
+template <typename T> constexpr int cat_res() { return sizeof(T) == 8 ? HDG_PROF_RESIDUAL64 : HDG_PROF_RESIDUAL32; }
+template <typename T> constexpr int cat_smooth() { return sizeof(T) == 8 ? HDG_PROF_SMOOTH64 : HDG_PROF_SMOOTH32; }
+template <typename T> constexpr int cat_first() { return sizeof(T) == 8 ? HDG_PROF_SMOOTH_FIRST64 : HDG_PROF_SMOOTH_FIRST32; }
+
 // ---------------------------------------------------------------- preconditioner
 
 template <typename T>
@@ -163,28 +212,28 @@ cudaError_t p1_vcycle(hdg_handle *h, int l) {
     DevLevel &L = h->lev[l];
     cudaStream_t s = h->stream;
     const int last = int(h->lev.size()) - 1;
-    if (l == last) return launch_dense_apply<T>(coarse_inv<T>(h), L.nv, levB<T>(L), levX<T>(L), s);
+    if (l == last) return KL(HDG_PROF_P1, 1, launch_dense_apply<T>(coarse_inv<T>(h), L.nv, levB<T>(L), levX<T>(L), s));
     const T om = T(h->prm.p1_omega);
     const T *A = levA<T>(L), *D = levD<T>(L);
     T *x = levX<T>(L), *x2 = levX2<T>(L), *b = levB<T>(L), *r = levR<T>(L);
     cudaError_t e;
     int nu1 = h->prm.p1_nu_pre, nu2 = h->prm.p1_nu_post;
     if (nu1 == 0) {
-        if ((e = launch_fill<T>(x, T(0), L.nv, s)) != cudaSuccess) return e;
+        if ((e = KL(HDG_PROF_P1, 1, launch_fill<T>(x, T(0), L.nv, s))) != cudaSuccess) return e;
     } else {
-        if ((e = launch_p1_jacobi<T>(L, A, D, b, x, x, om, true, s)) != cudaSuccess) return e;
+        if ((e = KL(HDG_PROF_P1, 1, launch_p1_jacobi<T>(L, A, D, b, x, x, om, true, s))) != cudaSuccess) return e;
         for (int k = 1; k < nu1; ++k) {
-            if ((e = launch_p1_jacobi<T>(L, A, D, b, x, x2, om, false, s)) != cudaSuccess) return e;
+            if ((e = KL(HDG_PROF_P1, 1, launch_p1_jacobi<T>(L, A, D, b, x, x2, om, false, s))) != cudaSuccess) return e;
             std::swap(x, x2);
         }
     }
-    if ((e = launch_p1_residual<T>(L, A, b, x, r, s)) != cudaSuccess) return e;
+    if ((e = KL(HDG_PROF_P1, 1, launch_p1_residual<T>(L, A, b, x, r, s))) != cudaSuccess) return e;
     DevLevel &C = h->lev[l + 1];
-    if ((e = launch_p1_restrict<T>(C, r, levB<T>(C), s)) != cudaSuccess) return e;
+    if ((e = KL(HDG_PROF_P1, 1, launch_p1_restrict<T>(C, r, levB<T>(C), s))) != cudaSuccess) return e;
     if ((e = p1_vcycle<T>(h, l + 1)) != cudaSuccess) return e;
-    if ((e = launch_p1_prolong_add<T>(C, L.nv, levX<T>(C), x, s)) != cudaSuccess) return e;
+    if ((e = KL(HDG_PROF_P1, 1, launch_p1_prolong_add<T>(C, L.nv, levX<T>(C), x, s))) != cudaSuccess) return e;
     for (int k = 0; k < nu2; ++k) {
-        if ((e = launch_p1_jacobi<T>(L, A, D, b, x, x2, om, false, s)) != cudaSuccess) return e;
+        if ((e = KL(HDG_PROF_P1, 1, launch_p1_jacobi<T>(L, A, D, b, x, x2, om, false, s))) != cudaSuccess) return e;
         std::swap(x, x2);
     }
     // make the result land in the level's primary buffer
@@ -202,23 +251,23 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z) {
     T *x = k.t0, *x2 = k.t1;
     cudaError_t e;
     if (h->prm.n_pre == 0) {
-        if ((e = launch_fill<T>(x, T(0), NT, s)) != cudaSuccess) return e;
+        if ((e = KL(HDG_PROF_KRYLOV, 1, launch_fill<T>(x, T(0), NT, s))) != cudaSuccess) return e;
     } else {
-        if ((e = launch_smooth_first_t<T>(h, v, x)) != cudaSuccess) return e;
+        if ((e = KL(cat_first<T>(), 1, launch_smooth_first_t<T>(h, v, x))) != cudaSuccess) return e;
         for (int i = 1; i < h->prm.n_pre; ++i) {
-            if ((e = launch_smooth_t<T>(h, v, x, x2)) != cudaSuccess) return e;
+            if ((e = KL(cat_smooth<T>(), 1, launch_smooth_t<T>(h, v, x, x2))) != cudaSuccess) return e;
             std::swap(x, x2);
         }
     }
-    if ((e = launch_residual_t<T>(h, v, x, k.res)) != cudaSuccess) return e;
+    if ((e = KL(cat_res<T>(), 1, launch_residual_t<T>(h, v, x, k.res))) != cudaSuccess) return e;
     DevLevel &L0 = h->lev[0];
-    if ((e = launch_restrict_t<T>(h, k.res, levB<T>(L0))) != cudaSuccess) return e;
+    if ((e = KL(HDG_PROF_TRANSFER, 1, launch_restrict_t<T>(h, k.res, levB<T>(L0)))) != cudaSuccess) return e;
     if ((e = p1_vcycle<T>(h, 0)) != cudaSuccess) return e;
-    if ((e = launch_prolong_add_t<T>(h, levX<T>(L0), x)) != cudaSuccess) return e;
+    if ((e = KL(HDG_PROF_TRANSFER, 1, launch_prolong_add_t<T>(h, levX<T>(L0), x))) != cudaSuccess) return e;
     const int np = h->prm.n_post;
     for (int i = 0; i < np; ++i) {
         T *out = (i == np - 1) ? z : x2;
-        if ((e = launch_smooth_t<T>(h, v, x, out)) != cudaSuccess) return e;
+        if ((e = KL(cat_smooth<T>(), 1, launch_smooth_t<T>(h, v, x, out))) != cudaSuccess) return e;
         if (i < np - 1) std::swap(x, x2);
     }
     if (np == 0) return cudaMemcpyAsync(z, x, sizeof(T) * NT, cudaMemcpyDeviceToDevice, s);
@@ -230,9 +279,9 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z) {
 template <typename T>
 cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out) {
     Workspace &W = *h->ws;
-    cudaError_t e = launch_multidot<T>(V, W.NT, k, w, W.NT, W.partial, W.nchunk, h->stream);
+    cudaError_t e = KL(HDG_PROF_KRYLOV, 1, launch_multidot<T>(V, W.NT, k, w, W.NT, W.partial, W.nchunk, h->stream));
     if (e != cudaSuccess) return e;
-    return launch_reduce_partials(W.partial, k, W.nchunk, out, h->stream);
+    return KL(HDG_PROF_KRYLOV, 1, launch_reduce_partials(W.partial, k, W.nchunk, out, h->stream));
 }
 
 template <typename T>
@@ -241,6 +290,7 @@ int norm_host(hdg_handle *h, const T *v, double &out) {
     TRY(dots<T>(h, v, 1, v, W.nrm2));
     TRY(cudaMemcpyAsync(W.host_buf, W.nrm2, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     TRY(cudaStreamSynchronize(h->stream));
+    prof_flush(h);
     out = std::sqrt(W.host_buf[0]);
     return HDG_OK;
 }
@@ -263,34 +313,35 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
     // s = [beta, 0, ...]
     TRY(cudaMemsetAsync(W.sv, 0, sizeof(double) * (m + 1), s));
     TRY(cudaMemsetAsync(W.Hm, 0, sizeof(double) * (m + 1) * m, s));
-    double hb = beta;
-    TRY(cudaMemcpyAsync(W.sv, &hb, sizeof(double), cudaMemcpyHostToDevice, s));
+    W.host_buf[3] = beta;
+    TRY(cudaMemcpyAsync(W.sv, W.host_buf + 3, sizeof(double), cudaMemcpyHostToDevice, s));
     int j = 0;
     for (; j < m && j < max_it; ++j) {
         T *vj = k.V + size_t(j) * NT, *zj = k.Z + size_t(j) * NT;
         TRY(precond<T>(h, vj, zj));
-        TRY(launch_apply_t<T>(h, zj, k.w));
+        TRY(KL(cat_apply<T>(), 1, launch_apply_t<T>(h, zj, k.w)));
         // classical Gram-Schmidt, twice
         TRY(dots<T>(h, k.V, j + 1, k.w, W.h1));
-        TRY(launch_multi_axpy<T>(k.w, k.V, NT, j + 1, W.h1, -1.0, NT, s));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_multi_axpy<T>(k.w, k.V, NT, j + 1, W.h1, -1.0, NT, s)));
         TRY(dots<T>(h, k.V, j + 1, k.w, W.h2));
-        TRY(launch_multi_axpy<T>(k.w, k.V, NT, j + 1, W.h2, -1.0, NT, s));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_multi_axpy<T>(k.w, k.V, NT, j + 1, W.h2, -1.0, NT, s)));
         TRY(dots<T>(h, k.w, 1, k.w, W.nrm2));
         double *Hcol = W.Hm + size_t(j) * ldh;
-        TRY(launch_arnoldi_finish(Hcol, W.h1, W.h2, W.nrm2, j, s));
-        TRY(launch_scale_copy<T>(k.w, k.V + size_t(j + 1) * NT, Hcol + j + 1, NT, s));
-        TRY(launch_givens(W.Hm, ldh, W.cs, W.sn, W.sv, j, bnorm, W.est, W.flags, s));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_arnoldi_finish(Hcol, W.h1, W.h2, W.nrm2, j, s)));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_scale_copy<T>(k.w, k.V + size_t(j + 1) * NT, Hcol + j + 1, NT, s)));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_givens(W.Hm, ldh, W.cs, W.sn, W.sv, j, bnorm, W.est, W.flags, s)));
         TRY(cudaMemcpyAsync(W.host_buf, W.est, sizeof(double), cudaMemcpyDeviceToHost, s));
         TRY(cudaMemcpyAsync(W.host_flags, W.flags, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         TRY(cudaStreamSynchronize(s));
+        prof_flush(h);
         est_out = W.host_buf[0];
         flag_out = W.host_flags[0];
         if (est_out <= rel_target || (flag_out & 6)) { ++j; break; }
     }
     its_done = j;
     if (j > 0 && !(flag_out & 4)) {
-        TRY(launch_hessenberg_solve(W.Hm, ldh, W.sv, j, W.y, s));
-        TRY(launch_multi_axpy<T>(x, k.Z, NT, j, W.y, 1.0, NT, s));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_hessenberg_solve(W.Hm, ldh, W.sv, j, W.y, s)));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_multi_axpy<T>(x, k.Z, NT, j, W.y, 1.0, NT, s)));
     }
     return HDG_OK;
 }
@@ -312,13 +363,13 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
     info.true_rel_res = 0;
     if (!std::isfinite(bnorm)) return fail(h, HDG_ENAN, "NaN or Inf in the right-hand side");
     if (bnorm == 0.0) {
-        TRY(launch_fill<T>(x, T(0), W.NT, s));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<T>(x, T(0), W.NT, s)));
         return HDG_OK;
     }
     int total = 0;
     for (;;) {
         // r = b - S x into V[0]
-        TRY(launch_residual_t<T>(h, b, x, k.V));
+        TRY(KL(cat_res<T>(), 1, launch_residual_t<T>(h, b, x, k.V)));
         double beta;
         rc = norm_host<T>(h, k.V, beta);
         if (rc) return rc;
@@ -327,9 +378,9 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
         if (!std::isfinite(rel)) return fail(h, HDG_ENAN, "NaN or Inf in the Krylov iteration");
         if (rel <= rtol) return HDG_OK;
         if (total >= max_it) return fail(h, HDG_ENOCONV, "maximum number of iterations reached");
-        double inv = beta;
-        TRY(cudaMemcpyAsync(W.nrm2, &inv, sizeof(double), cudaMemcpyHostToDevice, s));
-        TRY(launch_scale_copy<T>(k.V, k.V, W.nrm2, W.NT, s));
+        W.host_buf[1] = beta;
+        TRY(cudaMemcpyAsync(W.scal, W.host_buf + 1, sizeof(double), cudaMemcpyHostToDevice, s));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_scale_copy<T>(k.V, k.V, W.scal, W.NT, s)));
         int done, flag;
         double est;
         rc = fgmres_cycle<T>(h, x, beta, bnorm, rtol, max_it - total, done, est, flag);
@@ -346,7 +397,7 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
         }
         if ((flag & 2) && est > rtol) {
             // breakdown without convergence: check the true residual once more
-            TRY(launch_residual_t<T>(h, b, x, k.V));
+            TRY(KL(cat_res<T>(), 1, launch_residual_t<T>(h, b, x, k.V)));
             double beta2;
             rc = norm_host<T>(h, k.V, beta2);
             if (rc) return rc;
@@ -367,11 +418,11 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info)
     if (rc) return rc;
     info = hdg_solve_info{};
     if (!std::isfinite(bnorm)) return fail(h, HDG_ENAN, "NaN or Inf in the right-hand side");
-    TRY(launch_fill<double>(x, 0.0, W.NT, s));
+    TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<double>(x, 0.0, W.NT, s)));
     if (bnorm == 0.0) return HDG_OK;
     int total = 0;
     for (int outer = 0;; ++outer) {
-        TRY(launch_residual_t<double>(h, g, x, W.r));
+        TRY(KL(HDG_PROF_RESIDUAL64, 1, launch_residual_t<double>(h, g, x, W.r)));
         double beta;
         rc = norm_host<double>(h, W.r, beta);
         if (rc) return rc;
@@ -382,9 +433,10 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info)
         if (total >= h->prm.max_iter || outer >= 100)
             return fail(h, HDG_ENOCONV, "maximum number of iterations reached");
         // b32 = r / ||r||, solve S d = b32 in FP32, x += ||r|| d
-        TRY(cudaMemcpyAsync(W.nrm2, &beta, sizeof(double), cudaMemcpyHostToDevice, s));
-        TRY(launch_d2f_scaled(W.r, k.b, W.nrm2, W.NT, s));
-        TRY(launch_fill<float>(k.x, 0.0f, W.NT, s));
+        W.host_buf[2] = beta;
+        TRY(cudaMemcpyAsync(W.beta, W.host_buf + 2, sizeof(double), cudaMemcpyHostToDevice, s));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_d2f_scaled(W.r, k.b, W.beta, W.NT, s)));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<float>(k.x, 0.0f, W.NT, s)));
         hdg_solve_info inner{};
         const double inner_tol = std::max(h->prm.inner_rtol, 0.5 * h->prm.rtol * bnorm / beta);
         rc = fgmres<float>(h, k.b, k.x, inner_tol, h->prm.max_iter - total, false, inner);
@@ -392,8 +444,8 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info)
         total += inner.iters;
         info.iters = total;
         info.est_rel_res = inner.est_rel_res;
-        // x += beta * d  (beta = ||r|| still in W.nrm2)
-        TRY(launch_axpby_mixed(x, k.x, W.nrm2, W.NT, s));
+        // x += beta * d
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_axpby_mixed(x, k.x, W.beta, W.NT, s)));
     }
 }
 
@@ -411,6 +463,9 @@ int ensure_staging(hdg_handle *h) {
 void free_handle(hdg_handle *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    prof_flush(h);
+    for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+    h->prof.pool.clear();
     dfree(h->d_ref); dfree(h->d_X); dfree(h->d_fcell); dfree(h->d_facet_of); dfree(h->d_flip);
     dfree(h->d_facet_cell); dfree(h->d_facet_edge); dfree(h->d_facet_verts); dfree(h->d_v2f_ptr); dfree(h->d_v2f);
     dfree(h->d_nbr); dfree(h->d_Xb); dfree(h->d_Rm); dfree(h->d_W); dfree(h->d_Scell); dfree(h->d_Sval);
@@ -428,7 +483,7 @@ void free_handle(hdg_handle *h) {
         dfree(W.k32.V); dfree(W.k32.Z); dfree(W.k32.w); dfree(W.k32.t0); dfree(W.k32.t1); dfree(W.k32.res);
         dfree(W.k32.b); dfree(W.k32.x);
         dfree(W.Hm); dfree(W.cs); dfree(W.sn); dfree(W.sv); dfree(W.h1); dfree(W.h2); dfree(W.nrm2);
-        dfree(W.est); dfree(W.y); dfree(W.partial); dfree(W.flags);
+        dfree(W.est); dfree(W.scal); dfree(W.beta); dfree(W.y); dfree(W.partial); dfree(W.flags);
         dfree(W.ru); dfree(W.rh); dfree(W.lam_ext); dfree(W.u); dfree(W.hh); dfree(W.lam_int);
         if (W.host_buf) cudaFreeHost(W.host_buf);
         if (W.host_flags) cudaFreeHost(W.host_flags);
@@ -546,6 +601,8 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(dalloc(&W.h2, mm + 1));
     TRY(dalloc(&W.nrm2, 1));
     TRY(dalloc(&W.est, 1));
+    TRY(dalloc(&W.scal, 1));
+    TRY(dalloc(&W.beta, 1));
     TRY(dalloc(&W.y, mm + 1));
     TRY(dalloc(&W.partial, (mm + 1) * size_t(W.nchunk)));
     TRY(dalloc(&W.flags, 1));
@@ -559,6 +616,7 @@ int check_status(hdg_handle *h) {
     int32_t st = 0;
     TRY(cudaMemcpyAsync(&st, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     TRY(cudaStreamSynchronize(h->stream));
+    prof_flush(h);
     if (st & 1) return fail(h, HDG_ESINGULAR, "zero pivot in a cell matrix A_K");
     if (st & 2) return fail(h, HDG_ESINGULAR, "singular facet block of the trace operator");
     if (st & 4) return fail(h, HDG_ESINGULAR, "singular coarsest P1 operator");
@@ -574,10 +632,10 @@ int require_condensed(hdg_handle *h) {
 int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solve_info &info) {
     Workspace &W = *h->ws;
     cudaStream_t s = h->stream;
-    TRY(launch_rhs(h, r_u, r_h, W.g, W.ycell));
+    TRY(KL(HDG_PROF_RHS, 2, launch_rhs(h, r_u, r_h, W.g, W.ycell)));
     int rc;
     if (h->prm.precision == HDG_FP64) {
-        TRY(launch_fill<double>(W.x, 0.0, W.NT, s));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<double>(W.x, 0.0, W.NT, s)));
         rc = fgmres<double>(h, W.g, W.x, h->prm.rtol, h->prm.max_iter, true, info);
     } else {
         rc = solve_mixed(h, W.g, W.x, info);
@@ -666,21 +724,21 @@ int hdg_condense(hdg_handle *h) {
     cudaStream_t s = h->stream;
     h->condensed = false;
     TRY(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), s));
-    TRY(launch_condense(h));
-    TRY(launch_assemble(h));
+    TRY(KL(HDG_PROF_CONDENSE, 1, launch_condense(h)));
+    TRY(KL(HDG_PROF_CONDENSE, 1, launch_assemble(h)));
     const double tau = h->prm.tau, ctau2 = tau * tau * h->prm.g * h->prm.H;
-    for (auto &L : h->lev) TRY(launch_p1_combine(h, L, tau, ctau2));
+    for (auto &L : h->lev) TRY(KL(HDG_PROF_CONDENSE, 1, launch_p1_combine(h, L, tau, ctau2)));
     const DevLevel &Lc = h->lev.back();
-    TRY(launch_dense_inverse(h, Lc, h->d_coarse_work, h->d_coarse_inv, Lc.nv));
+    TRY(KL(HDG_PROF_CONDENSE, 2, launch_dense_inverse(h, Lc, h->d_coarse_work, h->d_coarse_inv, Lc.nv)));
     if (h->prm.precision == HDG_MIXED_FP32) {
         const size_t NF = h->NF, pp = h->pp;
-        TRY(launch_to_f32(h->d_Sval, h->d_Sval32, 5 * pp * pp * NF, s));
-        TRY(launch_to_f32(h->d_Dinv, h->d_Dinv32, pp * pp * NF, s));
+        TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(h->d_Sval, h->d_Sval32, 5 * pp * pp * NF, s)));
+        TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(h->d_Dinv, h->d_Dinv32, pp * pp * NF, s)));
         for (auto &L : h->lev) {
-            TRY(launch_to_f32(L.A, L.A32, size_t(L.nnz), s));
-            TRY(launch_to_f32(L.dinv, L.dinv32, size_t(L.nv), s));
+            TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(L.A, L.A32, size_t(L.nnz), s)));
+            TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(L.dinv, L.dinv32, size_t(L.nv), s)));
         }
-        TRY(launch_to_f32(h->d_coarse_inv, h->d_coarse_inv32, size_t(Lc.nv) * Lc.nv, s));
+        TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(h->d_coarse_inv, h->d_coarse_inv32, size_t(Lc.nv) * Lc.nv, s)));
     }
     int rc = check_status(h);
     if (rc) return rc;
@@ -705,7 +763,7 @@ int hdg_solve_dev(hdg_handle *h, const double *r_u, const double *r_h, double *l
         if (info) *info = loc;
         return rc;
     }
-    TRY(launch_to_external(h, h->ws->x, lambda));
+    TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_external(h, h->ws->x, lambda)));
     h->ws->have_rhs = false;
     if (info) *info = loc;
     return rc;
@@ -727,7 +785,7 @@ int hdg_solve(hdg_handle *h, const double *r_u, const double *r_h, double *lambd
         if (info) *info = loc;
         return rc;
     }
-    TRY(launch_to_external(h, W.x, W.lam_ext));
+    TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_external(h, W.x, W.lam_ext)));
     TRY(cudaMemcpyAsync(lambda, W.lam_ext, sizeof(double) * W.NT, cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
     W.have_rhs = true;
@@ -743,12 +801,12 @@ int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h, const d
     Workspace &W = *h->ws;
     const double *lam = W.lam_int;
     if (lambda) {
-        TRY(launch_to_internal(h, lambda, W.k64.res));
+        TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_internal(h, lambda, W.k64.res)));
         lam = W.k64.res;
     } else if (!W.have_lambda) {
         return fail(h, HDG_ESTATE, "no lambda given and no previous solve");
     }
-    TRY(launch_recover(h, r_u, r_h, lam, u, h_out));
+    TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, r_u, r_h, lam, u, h_out)));
     return HDG_OK;
 }
 
@@ -769,12 +827,12 @@ int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, const doubl
     const double *lam = W.lam_int;
     if (lambda) {
         TRY(cudaMemcpyAsync(W.lam_ext, lambda, sizeof(double) * W.NT, cudaMemcpyHostToDevice, s));
-        TRY(launch_to_internal(h, W.lam_ext, W.k64.res));
+        TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_internal(h, W.lam_ext, W.k64.res)));
         lam = W.k64.res;
     } else if (!W.have_lambda) {
         return fail(h, HDG_ESTATE, "no lambda given and no previous solve");
     }
-    TRY(launch_recover(h, W.ru, W.rh, lam, W.u, W.hh));
+    TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, W.ru, W.rh, lam, W.u, W.hh)));
     TRY(cudaMemcpyAsync(u, W.u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyDeviceToHost, s));
     TRY(cudaMemcpyAsync(h_out, W.hh, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
@@ -785,9 +843,9 @@ int hdg_trace_apply_dev(hdg_handle *h, const double *x, double *y) {
     int rc = require_condensed(h);
     if (rc) return rc;
     Workspace &W = *h->ws;
-    TRY(launch_to_internal(h, x, W.k64.t0));
-    TRY(launch_apply_t<double>(h, W.k64.t0, W.k64.t1));
-    TRY(launch_to_external(h, W.k64.t1, y));
+    TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_internal(h, x, W.k64.t0)));
+    TRY(KL(HDG_PROF_APPLY64, 1, launch_apply_t<double>(h, W.k64.t0, W.k64.t1)));
+    TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_external(h, W.k64.t1, y)));
     return HDG_OK;
 }
 
@@ -795,8 +853,8 @@ int hdg_condensed_rhs_dev(hdg_handle *h, const double *r_u, const double *r_h, d
     int rc = require_condensed(h);
     if (rc) return rc;
     Workspace &W = *h->ws;
-    TRY(launch_rhs(h, r_u, r_h, W.g, W.ycell));
-    TRY(launch_to_external(h, W.g, g));
+    TRY(KL(HDG_PROF_RHS, 2, launch_rhs(h, r_u, r_h, W.g, W.ycell)));
+    TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_external(h, W.g, g)));
     return HDG_OK;
 }
 
@@ -804,9 +862,9 @@ int hdg_precond_apply_dev(hdg_handle *h, const double *v, double *z) {
     int rc = require_condensed(h);
     if (rc) return rc;
     Workspace &W = *h->ws;
-    TRY(launch_to_internal(h, v, W.r));
+    TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_internal(h, v, W.r)));
     TRY(precond<double>(h, W.r, W.x));
-    TRY(launch_to_external(h, W.x, z));
+    TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_external(h, W.x, z)));
     return HDG_OK;
 }
 
@@ -836,6 +894,29 @@ int hdg_get_cell_schur(hdg_handle *h, double *S) {
     TRY(cudaMemcpyAsync(S, h->d_Scell, sizeof(double) * size_t(h->N) * h->m * h->m, cudaMemcpyDeviceToHost,
                         h->stream));
     TRY(cudaStreamSynchronize(h->stream));
+    return HDG_OK;
+}
+
+int hdg_profile_enable(hdg_handle *h, int timing_on) {
+    if (!h) return HDG_EINVAL;
+    TRY(cudaStreamSynchronize(h->stream));
+    prof_flush(h);
+    h->prof.on = timing_on != 0;
+    for (int i = 0; i < HDG_PROF_N; ++i) {
+        h->prof.ms[i] = 0.0;
+        h->prof.launches[i] = 0;
+    }
+    return HDG_OK;
+}
+
+int hdg_profile_read(hdg_handle *h, double *ms, int64_t *launches) {
+    if (!h) return HDG_EINVAL;
+    TRY(cudaStreamSynchronize(h->stream));
+    prof_flush(h);
+    for (int i = 0; i < HDG_PROF_N; ++i) {
+        if (ms) ms[i] = h->prof.ms[i];
+        if (launches) launches[i] = h->prof.launches[i];
+    }
     return HDG_OK;
 }
 

@@ -91,6 +91,16 @@ struct DevLevel {
 
 struct Workspace;   // solver vectors, defined in api.cu
 
+// per-category kernel accounting (see hdg_profile_enable)
+struct Prof {
+    bool on = false;
+    double ms[HDG_PROF_N] = {};
+    int64_t launches[HDG_PROF_N] = {};
+    struct Pending { int cat; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+};
+
 }  // namespace hdg
 
 // The handle (opaque to callers).
@@ -131,6 +141,7 @@ struct hdg_handle {
     double *d_coarse_work = nullptr;
     float *d_coarse_inv32 = nullptr;
     hdg::Workspace *ws = nullptr;
+    hdg::Prof prof;
 };
 
 // ---------------------------------------------------------------- error helpers

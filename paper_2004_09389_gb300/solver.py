@@ -117,6 +117,16 @@ class HDGSolver:
     def precond_apply_dev(self, v, z) -> None:
         L.check(self.h, self.lib.hdg_precond_apply_dev(self.h, L._ptr(v), L._ptr(z)))
 
+    # ---------------------------------------------------------------- accounting
+    def profile_enable(self, timing: bool = True) -> None:
+        L.check(self.h, self.lib.hdg_profile_enable(self.h, 1 if timing else 0))
+
+    def profile_read(self) -> dict:
+        ms = np.zeros(L.HDG_PROF_N)
+        n = np.zeros(L.HDG_PROF_N, dtype=np.int64)
+        L.check(self.h, self.lib.hdg_profile_read(self.h, ms.ctypes.data, n.ctypes.data))
+        return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(L.PROF_NAMES)}
+
     # ---------------------------------------------------------------- inspection
     def facets(self):
         fo = np.empty((self.n_cells, 3), np.int32)
