@@ -169,6 +169,21 @@ HDG_API int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h,
 HDG_API int hdg_trace_apply_dev(hdg_handle *h, const double *x, double *y);
 /* g = sum_K P_K^T C_K A_K^-1 F_K, the condensed right-hand side of step 1. */
 HDG_API int hdg_condensed_rhs_dev(hdg_handle *h, const double *r_u, const double *r_h, double *g);
+/* Same result as hdg_condensed_rhs_dev, for callers that must not cause any
+ * device allocation once the handle exists (e.g. an application that gives
+ * all device memory to its own pool up front, or code that records a CUDA
+ * graph, during which allocation calls are not allowed).  The paper has no
+ * counterpart: this is an engineering variant.  Its scratch is a fixed
+ * 32 MiB array inside the library's device image, shared by every call on
+ * the device and kept by every GPU that loads the library until the process
+ * exits; sizes needing more than 2^22 doubles (n_cells * 3(p+1) +
+ * n_facets * (p+1)) return HDG_EINVAL.  It calls no cudaMalloc / cudaFree and
+ * no allocating library routine.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current, so
+ * make that first call before any stream capture.  The array keeps the last
+ * call's contents; calls whose GPU work overlaps (two streams, two handles on
+ * one device) race on it and must be serialised by the caller. */
+HDG_API int hdg_condensed_rhs_noalloc_dev(hdg_handle *h, const double *r_u, const double *r_h, double *g);
 /* z = V(v): one application of the two-level V-cycle (Alg. twolevel_vcycle)
  * with zero initial guess. */
 HDG_API int hdg_precond_apply_dev(hdg_handle *h, const double *v, double *z);

@@ -60,7 +60,7 @@ _LIB = None
 EXPORTS = ["hdg_default_params", "hdg_setup", "hdg_condense", "hdg_set_tau", "hdg_solve", "hdg_solve_dev",
            "hdg_recover", "hdg_recover_dev", "hdg_trace_apply_dev", "hdg_condensed_rhs_dev",
            "hdg_precond_apply_dev", "hdg_get_sizes", "hdg_get_facets", "hdg_get_cell_schur", "hdg_destroy",
-           "hdg_last_error", "hdg_profile_enable", "hdg_profile_read"]
+           "hdg_last_error", "hdg_profile_enable", "hdg_profile_read", "hdg_condensed_rhs_noalloc_dev"]
 
 HDG_PROF_N = 15
 PROF_NAMES = ["apply64", "residual64", "smooth64", "smooth_first64", "apply32", "residual32", "smooth32",
@@ -88,6 +88,7 @@ def load() -> C.CDLL:
         getattr(lib, name).argtypes = [vp, vp, vp, vp, vp, vp]
     lib.hdg_trace_apply_dev.argtypes = [vp, vp, vp]
     lib.hdg_condensed_rhs_dev.argtypes = [vp, vp, vp, vp]
+    lib.hdg_condensed_rhs_noalloc_dev.argtypes = [vp, vp, vp, vp]
     lib.hdg_precond_apply_dev.argtypes = [vp, vp, vp]
     lib.hdg_get_sizes.argtypes = [vp, C.POINTER(C.c_int64)]
     lib.hdg_get_facets.argtypes = [vp, vp, vp, vp]

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libhdg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["refelem.cpp", "mesh.cpp", "k_condense.cu", "k_trace.cu", "k_p1.cu", "k_krylov.cu", "api.cu"]
+SOURCES = ["refelem.cpp", "mesh.cpp", "k_condense.cu", "k_trace.cu", "k_p1.cu", "k_krylov.cu", "api.cu",
+           "noalloc.cu"]
 
 
 def nvcc() -> str:
