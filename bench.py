@@ -203,7 +203,7 @@ def gpu_arm(args, rank: int, world: int):
             step()
         infos.clear()
         s.profile_enable(timing=False)          # launch counters only
-        stream = torch.cuda.current_stream()
+        stream = s.stream                        # the handle's stream: every kernel of the solve runs on it
         barrier()
         clocks = ClockSampler(dev.index) if arm == "mixed" else None
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 
@@ -45,10 +46,15 @@ struct Workspace {
     double *Hm = nullptr, *cs = nullptr, *sn = nullptr, *sv = nullptr, *h1 = nullptr, *h2 = nullptr;
     double *nrm2 = nullptr, *est = nullptr, *y = nullptr, *partial = nullptr;
     double *scal = nullptr;   // restart normalisation of a Krylov cycle
+    double *bnorm = nullptr;  // ||b|| of the current Krylov solve
+    // CUDA graphs of one Arnoldi step per (precision, j); see arnoldi_step
+    struct StepGraph { cudaGraphExec_t exec = nullptr; int64_t counts[HDG_PROF_N] = {}; };
+    std::vector<StepGraph> graphs[2];
+    bool use_graphs = true;
     double *beta = nullptr;   // refinement scale ||g - S x|| (mixed mode)
     int32_t *flags = nullptr;
     // pinned readback
-    double *host_buf = nullptr;   // [4]
+    double *host_buf = nullptr;   // [8]: 0 readback, 1 restart scale, 2 refinement scale, 3 s_0, 4 ||b||
     int32_t *host_flags = nullptr;
     // staging for host-pointer entry points and for recover defaults
     double *ru = nullptr, *rh = nullptr, *lam_ext = nullptr, *u = nullptr, *hh = nullptr;
@@ -295,6 +301,74 @@ int norm_host(hdg_handle *h, const T *v, double &out) {
     return HDG_OK;
 }
 
+// One Arnoldi step j of FGMRES: z_j = V(v_j), w = S z_j, classical
+// Gram-Schmidt twice against v_0..v_j, h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j},
+// Givens rotation j and the residual estimate copied to pinned host memory.
+// Every argument is a fixed device address, so the step can be captured once
+// in a CUDA graph and replayed.
+template <typename T>
+cudaError_t arnoldi_step(hdg_handle *h, int j) {
+    Workspace &W = *h->ws;
+    KSpace<T> &k = kspace<T>(h);
+    cudaStream_t s = h->stream;
+    const size_t NT = W.NT;
+    const int ldh = W.m + 1;
+    T *vj = k.V + size_t(j) * NT, *zj = k.Z + size_t(j) * NT;
+    cudaError_t e;
+    if ((e = precond<T>(h, vj, zj)) != cudaSuccess) return e;
+    if ((e = KL(cat_apply<T>(), 1, launch_apply_t<T>(h, zj, k.w))) != cudaSuccess) return e;
+    if ((e = dots<T>(h, k.V, j + 1, k.w, W.h1)) != cudaSuccess) return e;
+    if ((e = KL(HDG_PROF_KRYLOV, 1, launch_multi_axpy<T>(k.w, k.V, NT, j + 1, W.h1, -1.0, NT, s))) != cudaSuccess) return e;
+    if ((e = dots<T>(h, k.V, j + 1, k.w, W.h2)) != cudaSuccess) return e;
+    if ((e = KL(HDG_PROF_KRYLOV, 1, launch_multi_axpy<T>(k.w, k.V, NT, j + 1, W.h2, -1.0, NT, s))) != cudaSuccess) return e;
+    if ((e = dots<T>(h, k.w, 1, k.w, W.nrm2)) != cudaSuccess) return e;
+    double *Hcol = W.Hm + size_t(j) * ldh;
+    if ((e = KL(HDG_PROF_KRYLOV, 1, launch_arnoldi_finish(Hcol, W.h1, W.h2, W.nrm2, j, s))) != cudaSuccess) return e;
+    if ((e = KL(HDG_PROF_KRYLOV, 1, launch_scale_copy<T>(k.w, k.V + size_t(j + 1) * NT, Hcol + j + 1, NT, s))) != cudaSuccess) return e;
+    if ((e = KL(HDG_PROF_KRYLOV, 1, launch_givens(W.Hm, ldh, W.cs, W.sn, W.sv, j, W.bnorm, W.est, W.flags, s))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(W.host_buf, W.est, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    return cudaMemcpyAsync(W.host_flags, W.flags, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+}
+
+// Run Arnoldi step j: directly while kernel timing is on, otherwise through
+// its CUDA graph (captured on first use).
+template <typename T>
+int run_arnoldi_step(hdg_handle *h, int j) {
+    Workspace &W = *h->ws;
+    cudaStream_t s = h->stream;
+    if (h->prof.on || !W.use_graphs) {
+        TRY(arnoldi_step<T>(h, j));
+        return HDG_OK;
+    }
+    Workspace::StepGraph &G = W.graphs[sizeof(T) == 8 ? 0 : 1][j];
+    if (!G.exec) {
+        int64_t before[HDG_PROF_N];
+        std::memcpy(before, h->prof.launches, sizeof(before));
+        TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = arnoldi_step<T>(h, j);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+        for (int c = 0; c < HDG_PROF_N; ++c) {
+            G.counts[c] = h->prof.launches[c] - before[c];
+            h->prof.launches[c] = before[c];
+        }
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(h, HDG_ECUDA, std::string("capturing an Arnoldi step: ") +
+                                          cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        cudaError_t e3 = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e3 != cudaSuccess) {
+            G.exec = nullptr;
+            return fail(h, HDG_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e3));
+        }
+    }
+    TRY(cudaGraphLaunch(G.exec, s));
+    for (int c = 0; c < HDG_PROF_N; ++c) h->prof.launches[c] += G.counts[c];
+    return HDG_OK;
+}
+
 // One FGMRES cycle (at most m iterations, possibly fewer) on S x = b starting
 // from x, with the current residual r0 = b - S x of norm beta already in
 // k.V[0] (scaled).  Stops when the estimate drops below tol_abs / bnorm.
@@ -317,21 +391,8 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
     TRY(cudaMemcpyAsync(W.sv, W.host_buf + 3, sizeof(double), cudaMemcpyHostToDevice, s));
     int j = 0;
     for (; j < m && j < max_it; ++j) {
-        T *vj = k.V + size_t(j) * NT, *zj = k.Z + size_t(j) * NT;
-        TRY(precond<T>(h, vj, zj));
-        TRY(KL(cat_apply<T>(), 1, launch_apply_t<T>(h, zj, k.w)));
-        // classical Gram-Schmidt, twice
-        TRY(dots<T>(h, k.V, j + 1, k.w, W.h1));
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_multi_axpy<T>(k.w, k.V, NT, j + 1, W.h1, -1.0, NT, s)));
-        TRY(dots<T>(h, k.V, j + 1, k.w, W.h2));
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_multi_axpy<T>(k.w, k.V, NT, j + 1, W.h2, -1.0, NT, s)));
-        TRY(dots<T>(h, k.w, 1, k.w, W.nrm2));
-        double *Hcol = W.Hm + size_t(j) * ldh;
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_arnoldi_finish(Hcol, W.h1, W.h2, W.nrm2, j, s)));
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_scale_copy<T>(k.w, k.V + size_t(j + 1) * NT, Hcol + j + 1, NT, s)));
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_givens(W.Hm, ldh, W.cs, W.sn, W.sv, j, bnorm, W.est, W.flags, s)));
-        TRY(cudaMemcpyAsync(W.host_buf, W.est, sizeof(double), cudaMemcpyDeviceToHost, s));
-        TRY(cudaMemcpyAsync(W.host_flags, W.flags, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        int rc = run_arnoldi_step<T>(h, j);
+        if (rc) return rc;
         TRY(cudaStreamSynchronize(s));
         prof_flush(h);
         est_out = W.host_buf[0];
@@ -366,6 +427,9 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<T>(x, T(0), W.NT, s)));
         return HDG_OK;
     }
+    W.host_buf[4] = bnorm;
+    TRY(cudaMemcpyAsync(W.bnorm, W.host_buf + 4, sizeof(double), cudaMemcpyHostToDevice, s));
+    TRY(cudaStreamSynchronize(s));
     int total = 0;
     for (;;) {
         // r = b - S x into V[0]
@@ -483,7 +547,10 @@ void free_handle(hdg_handle *h) {
         dfree(W.k32.V); dfree(W.k32.Z); dfree(W.k32.w); dfree(W.k32.t0); dfree(W.k32.t1); dfree(W.k32.res);
         dfree(W.k32.b); dfree(W.k32.x);
         dfree(W.Hm); dfree(W.cs); dfree(W.sn); dfree(W.sv); dfree(W.h1); dfree(W.h2); dfree(W.nrm2);
-        dfree(W.est); dfree(W.scal); dfree(W.beta); dfree(W.y); dfree(W.partial); dfree(W.flags);
+        dfree(W.est); dfree(W.scal); dfree(W.bnorm);
+        for (auto &gv : W.graphs)
+            for (auto &G : gv)
+                if (G.exec) cudaGraphExecDestroy(G.exec); dfree(W.beta); dfree(W.y); dfree(W.partial); dfree(W.flags);
         dfree(W.ru); dfree(W.rh); dfree(W.lam_ext); dfree(W.u); dfree(W.hh); dfree(W.lam_int);
         if (W.host_buf) cudaFreeHost(W.host_buf);
         if (W.host_flags) cudaFreeHost(W.host_flags);
@@ -602,11 +669,18 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(dalloc(&W.nrm2, 1));
     TRY(dalloc(&W.est, 1));
     TRY(dalloc(&W.scal, 1));
+    TRY(dalloc(&W.bnorm, 1));
+    W.graphs[0].resize(W.m);
+    W.graphs[1].resize(W.m);
+    {
+        const char *ev = std::getenv("HDG_DISABLE_GRAPHS");
+        W.use_graphs = !(ev && ev[0] == '1');
+    }
     TRY(dalloc(&W.beta, 1));
     TRY(dalloc(&W.y, mm + 1));
     TRY(dalloc(&W.partial, (mm + 1) * size_t(W.nchunk)));
     TRY(dalloc(&W.flags, 1));
-    TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_buf), 4 * sizeof(double)));
+    TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_buf), 8 * sizeof(double)));
     TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_flags), 4 * sizeof(int32_t)));
     TRY(cudaStreamSynchronize(s));
     return HDG_OK;

@@ -196,7 +196,7 @@ template <typename T>
 cudaError_t launch_scale_copy(const T *w, T *v, const double *denom, size_t n, cudaStream_t s);
 cudaError_t launch_arnoldi_finish(double *Hcol, const double *h1, const double *h2, const double *nrm2,
                                   int j, cudaStream_t s);
-cudaError_t launch_givens(double *Hm, int ldh, double *cs, double *sn, double *sv, int j, double bnorm,
+cudaError_t launch_givens(double *Hm, int ldh, double *cs, double *sn, double *sv, int j, const double *bnorm,
                           double *est, int32_t *flags, cudaStream_t s);
 cudaError_t launch_hessenberg_solve(const double *Hm, int ldh, const double *sv, int k, double *y,
                                     cudaStream_t s);

@@ -76,8 +76,9 @@ __global__ void arnoldi_finish_kernel(double *Hcol, const double *h1, const doub
 // Apply the previous rotations to column j, form rotation j, update the RHS of
 // the least-squares problem; est = |s_{j+1}| / ||b||.  flags: 2 = breakdown,
 // 4 = NaN/Inf.
-__global__ void givens_kernel(double *Hm, int ldh, double *cs, double *sn, double *sv, int j, double bnorm,
+__global__ void givens_kernel(double *Hm, int ldh, double *cs, double *sn, double *sv, int j, const double *bnorm_p,
                               double *est, int32_t *flags) {
+    const double bnorm = bnorm_p[0];
     double *col = Hm + size_t(j) * ldh;
     for (int i = 0; i < j; ++i) {
         const double t = cs[i] * col[i] + sn[i] * col[i + 1];
@@ -158,7 +159,7 @@ cudaError_t launch_arnoldi_finish(double *Hcol, const double *h1, const double *
     arnoldi_finish_kernel<<<1, 1, 0, s>>>(Hcol, h1, h2, nrm2, j);
     return cudaGetLastError();
 }
-cudaError_t launch_givens(double *Hm, int ldh, double *cs, double *sn, double *sv, int j, double bnorm, double *est,
+cudaError_t launch_givens(double *Hm, int ldh, double *cs, double *sn, double *sv, int j, const double *bnorm, double *est,
                           int32_t *flags, cudaStream_t s) {
     givens_kernel<<<1, 1, 0, s>>>(Hm, ldh, cs, sn, sv, j, bnorm, est, flags);
     return cudaGetLastError();

@@ -8,11 +8,11 @@ import numpy as np
 from . import _lib as L
 
 
-def _torch_stream():
+def _torch():
     try:
         import torch
         if torch.cuda.is_available():
-            return torch.cuda.current_stream().cuda_stream
+            return torch
     except ImportError:
         pass
     return None
@@ -24,8 +24,10 @@ class HDGSolver:
     ``mesh`` is any object with ``dim``, ``vertex_xyz``, ``cell_vertices``,
     ``cell_shift`` and an optional list ``levels`` of coarse P1 levels (each with
     ``parent``).  Keyword arguments override the fields of ``hdg_params``.
-    ``stream``: a ``cudaStream_t`` value; by default the current PyTorch stream
-    so that ``*_dev`` calls on tensors are ordered with PyTorch's work.
+    ``stream``: a ``torch.cuda.Stream`` (or a raw ``cudaStream_t`` value) for the
+    handle's work; by default a new PyTorch stream.  ``*_dev`` calls are ordered
+    after the work already queued on PyTorch's current stream, and that stream
+    waits for them, so tensors can be used right before and after the call.
     """
 
     def __init__(self, mesh, p: int, tau: float, g: float = 1.0, H: float = 1.0, f_vertex=None,
@@ -44,8 +46,12 @@ class HDGSolver:
             setattr(prm, k, v)
         desc = L.make_mesh_desc(mesh, self._keep)
         h = C.c_void_p()
-        st = _torch_stream() if stream is None else stream
-        rc = self.lib.hdg_setup(C.byref(desc), C.byref(prm), C.c_void_p(st or 0), C.byref(h))
+        torch = _torch()
+        if stream is None and torch is not None:
+            stream = torch.cuda.Stream()
+        self.stream = stream
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        rc = self.lib.hdg_setup(C.byref(desc), C.byref(prm), C.c_void_p(raw), C.byref(h))
         self._keep = []
         if rc != 0:
             raise L.HDGError(rc, self.lib.hdg_last_error(None).decode())
@@ -99,23 +105,36 @@ class HDGSolver:
         return u, h
 
     # ---------------------------------------------------------------- device buffers
+    def _ordered(self, fn, *args):
+        """Run a *_dev call on the handle's stream, ordered with PyTorch's current stream."""
+        torch = _torch()
+        own = hasattr(self.stream, "wait_stream") and torch is not None
+        if own:
+            cur = torch.cuda.current_stream()
+            self.stream.wait_stream(cur)
+        rc = fn(self.h, *args)
+        if own:
+            cur.wait_stream(self.stream)
+        return rc
+
     def solve_dev(self, r_u, r_h, lam, allow_fail: bool = False) -> dict:
         info = L.hdg_solve_info()
-        rc = self.lib.hdg_solve_dev(self.h, L._ptr(r_u), L._ptr(r_h), L._ptr(lam), C.byref(info))
+        rc = self._ordered(self.lib.hdg_solve_dev, L._ptr(r_u), L._ptr(r_h), L._ptr(lam), C.byref(info))
         L.check(self.h, rc, allow=(L.HDG_ENOCONV, L.HDG_EBREAKDOWN) if allow_fail else ())
         return info.as_dict()
 
     def recover_dev(self, r_u, r_h, lam, u, h) -> None:
-        L.check(self.h, self.lib.hdg_recover_dev(self.h, L._ptr(r_u), L._ptr(r_h), L._ptr(lam), L._ptr(u), L._ptr(h)))
+        L.check(self.h, self._ordered(self.lib.hdg_recover_dev, L._ptr(r_u), L._ptr(r_h), L._ptr(lam), L._ptr(u),
+                                      L._ptr(h)))
 
     def trace_apply_dev(self, x, y) -> None:
-        L.check(self.h, self.lib.hdg_trace_apply_dev(self.h, L._ptr(x), L._ptr(y)))
+        L.check(self.h, self._ordered(self.lib.hdg_trace_apply_dev, L._ptr(x), L._ptr(y)))
 
     def condensed_rhs_dev(self, r_u, r_h, g) -> None:
-        L.check(self.h, self.lib.hdg_condensed_rhs_dev(self.h, L._ptr(r_u), L._ptr(r_h), L._ptr(g)))
+        L.check(self.h, self._ordered(self.lib.hdg_condensed_rhs_dev, L._ptr(r_u), L._ptr(r_h), L._ptr(g)))
 
     def precond_apply_dev(self, v, z) -> None:
-        L.check(self.h, self.lib.hdg_precond_apply_dev(self.h, L._ptr(v), L._ptr(z)))
+        L.check(self.h, self._ordered(self.lib.hdg_precond_apply_dev, L._ptr(v), L._ptr(z)))
 
     # ---------------------------------------------------------------- accounting
     def profile_enable(self, timing: bool = True) -> None:

@@ -42,6 +42,7 @@ def test_noalloc_rhs_matches_existing_entry_point(lib):
         rh = torch.from_numpy(rng.standard_normal((s.n_cells, s.n_p))).cuda()
         g_ref = torch.empty((s.n_facets, p + 1), dtype=torch.float64, device="cuda")
         g_new = torch.full((s.n_facets, p + 1), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()         # inputs were written on PyTorch's stream; the calls run on the handle's
         lib.check(s.h, s.lib.hdg_condensed_rhs_dev(s.h, ru.data_ptr(), rh.data_ptr(), g_ref.data_ptr()))
         lib.check(s.h, s.lib.hdg_condensed_rhs_noalloc_dev(s.h, ru.data_ptr(), rh.data_ptr(), g_new.data_ptr()))
         torch.cuda.synchronize()
