@@ -51,12 +51,13 @@ def workload_name(n, p, courant):
 
 
 # ---------------------------------------------------------------- algorithmic bytes per launch
-def trace_bytes(cat: str, NF: int, pp: int) -> float:
+def trace_bytes(cat: str, NF: int, pp: int, s_width: int | None = None) -> float:
     """Minimum bytes a facet-row kernel must move: the operator values (5 blocks
     of (p+1)^2 per facet), the neighbour ids, the inverted facet blocks where
-    used, and each trace vector it touches read or written once."""
+    used, and each trace vector it touches read or written once.  s_width
+    overrides the bytes per operator value (2 for the BF16 preconditioner copy)."""
     w = 8 if cat.endswith("64") else 4
-    S = 5 * pp * pp * w + 16
+    S = 5 * pp * pp * (s_width or w) + 16
     vec = pp * w
     base = cat[:-2]
     if base == "apply":
@@ -168,7 +169,7 @@ def cpu_baseline_entry(p, courant, steps):
 def gpu_arm(args, rank: int, world: int):
     import numpy as np
     import torch
-    from paper_2004_09389_gb300 import HDGSolver, HDG_FP64, HDG_MIXED_FP32, build
+    from paper_2004_09389_gb300 import HDGSolver, HDG_FP64, HDG_MIXED_FP32, HDG_MIXED_BF16, build
     build.build()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
@@ -186,7 +187,7 @@ def gpu_arm(args, rank: int, world: int):
     ru_d = torch.from_numpy(ru).to(dev)
     rh_d = torch.from_numpy(rh).to(dev)
     out = {}
-    for arm, prec in (("mixed", HDG_MIXED_FP32), ("fp64", HDG_FP64)):
+    for arm, prec in (("mixed", HDG_MIXED_FP32), ("mixed_bf16", HDG_MIXED_BF16), ("fp64", HDG_FP64)):
         s = HDGSolver(mesh, args.p, tau, G, DEPTH, f_vertex=f, rtol=args.rtol, precision=prec,
                       inner_rtol=args.inner_rtol, restart=args.restart)
         NF, pp = s.n_facets, args.p + 1
@@ -256,13 +257,14 @@ def gpu_arm(args, rank: int, world: int):
     return out
 
 
-def roofline(arm: dict, peaks: dict) -> dict:
+def roofline(arm: dict, peaks: dict, bf16_pre: bool = False) -> dict:
     prof, NF, pp = arm["prof"], arm["NF"], arm["pp"]
     cats = [c for c in prof if c.startswith(("apply", "residual", "smooth"))]
     total = sum(ms for ms, _ in prof.values())
     best = max(cats, key=lambda c: prof[c][0])
     ms, n = prof[best]
-    per_launch = trace_bytes(best, NF, pp)
+    per_launch = trace_bytes(best, NF, pp, 2 if (bf16_pre and best.startswith("smooth") and best.endswith("32")
+                                                 and not best.startswith("smooth_first")) else None)
     achieved = per_launch * n / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
     peak = peaks.get("hbm_gbs", 6800.0)
     traffic = None
@@ -344,7 +346,7 @@ def main():
     ppath = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(ppath):
         peaks = json.load(open(ppath))
-    mx, fp = res["mixed"], res["fp64"]
+    mx, fp, mb = res["mixed"], res["fp64"], res["mixed_bf16"]
     K = args.steps
     value = world * K / (mx["ms"] * 1e-3)
     fp_value = world * K / (fp["ms"] * 1e-3)
@@ -363,6 +365,10 @@ def main():
         "plain_fp64": {"value": fp_value, "unit": "solves/s", "ms_per_step": fp["ms"] / K, "iters": it_fp,
                        "true_rel_res": [i["true_rel_res"] for i in fp["infos"]],
                        "roofline": roofline(fp, peaks)},
+        "mixed_bf16_smoother": {"value": world * K / (mb["ms"] * 1e-3), "unit": "solves/s",
+                                "ms_per_step": mb["ms"] / K, "iters": [i["iters"] for i in mb["infos"]],
+                                "true_rel_res": [i["true_rel_res"] for i in mb["infos"]],
+                                "roofline": roofline(mb, peaks, bf16_pre=True)},
         "speedup_vs_plain_fp64": value / fp_value,
         "roofline": roofline(mx, peaks),
         "kernel_ms": {k: v[0] for k, v in mx["prof"].items() if v[1]},

@@ -74,6 +74,8 @@ extern "C" {
 
 #define HDG_FP64        0   /* every step in double precision                                 */
 #define HDG_MIXED_FP32  1   /* FP32 inner FGMRES + V-cycle, FP64 iterative refinement         */
+#define HDG_MIXED_BF16  2   /* as HDG_MIXED_FP32, with a BF16 copy of the trace operator for the
+                               smoother and V-cycle residual (FP32 accumulation)              */
 
 typedef struct hdg_handle hdg_handle;
 
@@ -103,7 +105,7 @@ typedef struct {
     double        g, H;         /* gravity and mean depth (> 0)                          */
     double        tau_s;        /* upwind stabilisation; <= 0 selects sqrt(g H)          */
     const double *f_vertex;     /* Coriolis parameter at fine vertices, P1 per cell; NULL = 0 */
-    int32_t       precision;    /* HDG_FP64 or HDG_MIXED_FP32                            */
+    int32_t       precision;    /* HDG_FP64, HDG_MIXED_FP32 or HDG_MIXED_BF16             */
     double        rtol;         /* stop at ||g - S lambda|| <= rtol ||g|| (FP64 residual) */
     int32_t       restart;      /* FGMRES restart length m (1..64)                        */
     int32_t       max_iter;     /* total Krylov iterations allowed                        */
@@ -111,7 +113,7 @@ typedef struct {
     double        omega;        /* block-Jacobi damping                                   */
     int32_t       p1_nu_pre, p1_nu_post; /* Jacobi sweeps per level of the P1 V-cycle     */
     double        p1_omega;     /* Jacobi damping of the P1 V-cycle                       */
-    double        inner_rtol;   /* HDG_MIXED_FP32: relative tolerance of each inner solve */
+    double        inner_rtol;   /* mixed modes: relative tolerance of each inner solve   */
 } hdg_params;
 
 typedef struct {

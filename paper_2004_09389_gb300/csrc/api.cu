@@ -21,10 +21,11 @@
 namespace hdg {
 
 template <typename T> cudaError_t launch_apply_t(hdg_handle *, const T *, T *);
-template <typename T> cudaError_t launch_residual_t(hdg_handle *, const T *, const T *, T *);
+template <typename T> cudaError_t launch_residual_t(hdg_handle *, const T *, const T *, T *, bool);
 template <typename T> cudaError_t launch_smooth_t(hdg_handle *, const T *, const T *, T *);
 template <typename T> cudaError_t launch_smooth_first_t(hdg_handle *, const T *, T *);
-template <typename T> cudaError_t launch_restrict_t(hdg_handle *, const T *, T *);
+template <typename T> cudaError_t launch_restrict_t(hdg_handle *, const T *, T *, const T *, T, T *);
+template <typename T> cudaError_t launch_smooth_prolong_t(hdg_handle *, const T *, const T *, const T *, T *);
 template <typename T> cudaError_t launch_prolong_add_t(hdg_handle *, const T *, T *);
 
 // Krylov vectors of one precision
@@ -38,7 +39,11 @@ struct KSpace {
 struct Workspace {
     int m = 0;
     size_t NT = 0;
+    size_t ld = 0;        // leading dimension of the Krylov basis (NT rounded up to 16 bytes, zero padded)
     int nchunk = 1;
+    int nblk_gs = 1;      // blocks of the fused Gram-Schmidt kernels
+    unsigned int *counter = nullptr;
+    ReadBack *rb = nullptr, *host_rb = nullptr;
     double *g = nullptr, *x = nullptr, *r = nullptr, *ycell = nullptr;
     KSpace<double> k64;
     KSpace<float> k32;
@@ -82,11 +87,13 @@ int fail(hdg_handle *h, int code, const std::string &msg) {
         if (e_ != cudaSuccess) return fail(h, HDG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// every device array is its own allocation, padded to a multiple of 16 bytes
+// (TMA bulk copies move whole 16-byte words)
 template <typename T>
 cudaError_t dalloc(T **p, size_t n) {
     *p = nullptr;
     if (n == 0) return cudaSuccess;
-    return cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+    return cudaMalloc(reinterpret_cast<void **>(p), (n * sizeof(T) + 15) / 16 * 16);
 }
 template <typename T>
 cudaError_t upload(T **p, const std::vector<T> &v, cudaStream_t s) {
@@ -109,8 +116,9 @@ std::string check_params(const hdg_params *prm) {
     if (prm->max_iter < 1) return "max_iter must be positive";
     if (prm->n_pre < 0 || prm->n_post < 0 || prm->p1_nu_pre < 0 || prm->p1_nu_post < 0) return "negative sweep count";
     if (!(prm->omega > 0) || !(prm->p1_omega > 0)) return "damping factors must be positive";
-    if (prm->precision != HDG_FP64 && prm->precision != HDG_MIXED_FP32) return "unknown precision mode";
-    if (prm->precision == HDG_MIXED_FP32 && !(prm->inner_rtol > 0 && prm->inner_rtol < 1)) return "inner_rtol must be in (0, 1)";
+    if (prm->precision != HDG_FP64 && prm->precision != HDG_MIXED_FP32 && prm->precision != HDG_MIXED_BF16)
+        return "unknown precision mode";
+    if (prm->precision != HDG_FP64 && !(prm->inner_rtol > 0 && prm->inner_rtol < 1)) return "inner_rtol must be in (0, 1)";
     return "";
 }
 
@@ -212,39 +220,93 @@ KSpace<double> &kspace<double>(hdg_handle *h) { return h->ws->k64; }
 template <>
 KSpace<float> &kspace<float>(hdg_handle *h) { return h->ws->k32; }
 
-// P1 V-cycle on level l: solve A_l x = b_l approximately; result in levX(l)
+}  // namespace
+
+size_t hdg::tail_smem_bytes(const std::vector<DevLevel> &lev, int first, size_t tsz) {
+    auto pad = [](size_t b) { return (b + 15) / 16 * 16; };
+    size_t bytes = 0;
+    for (size_t l = first; l < lev.size(); ++l) {
+        const bool top = int(l) == first;
+        const size_t nv = lev[l].nv, nnz = lev[l].nnz, nci = top ? 0 : lev[l].nci;
+        const size_t nfin = top ? 0 : lev[l - 1].nv;
+        bytes += pad(tsz * nnz) + pad(tsz * nv) + pad(tsz * nci) + 4 * pad(tsz * nv);
+        bytes += pad(4 * (nv + 1)) + pad(4 * nnz) + (top ? 0 : pad(4 * (nv + 1))) + pad(4 * nci) + pad(4 * 2 * nfin);
+    }
+    return bytes;
+}
+
+namespace {
+
+// P1 V-cycle for the coarse problem (Eq. coarse_problem_upwind) with
+// right-hand side levB(level 0).  Levels above the tail: fused kernels (the
+// first pre-smoothing sweep of each level rides on the restriction that
+// produced its right-hand side; the prolongation rides on the first
+// post-smoothing sweep); levels from tail_start down: one single-CTA kernel.
+// Returns the device vector that holds the level-0 result.  The first
+// pre-smoothing sweep of level 0 (when it is above the tail) was done by the
+// trace-to-P1 restriction.
 template <typename T>
-cudaError_t p1_vcycle(hdg_handle *h, int l) {
-    DevLevel &L = h->lev[l];
+cudaError_t p1_cycle(hdg_handle *h, T **result) {
     cudaStream_t s = h->stream;
-    const int last = int(h->lev.size()) - 1;
-    if (l == last) return KL(HDG_PROF_P1, 1, launch_dense_apply<T>(coarse_inv<T>(h), L.nv, levB<T>(L), levX<T>(L), s));
+    const int nlev = int(h->lev.size()), ts = h->tail_start[sizeof(T) == 8 ? 0 : 1];
+    const int nu1 = h->prm.p1_nu_pre, nu2 = h->prm.p1_nu_post;
     const T om = T(h->prm.p1_omega);
-    const T *A = levA<T>(L), *D = levD<T>(L);
-    T *x = levX<T>(L), *x2 = levX2<T>(L), *b = levB<T>(L), *r = levR<T>(L);
+    std::vector<T *> cur(nlev), oth(nlev), res(nlev);
     cudaError_t e;
-    int nu1 = h->prm.p1_nu_pre, nu2 = h->prm.p1_nu_post;
-    if (nu1 == 0) {
-        if ((e = KL(HDG_PROF_P1, 1, launch_fill<T>(x, T(0), L.nv, s))) != cudaSuccess) return e;
-    } else {
-        if ((e = KL(HDG_PROF_P1, 1, launch_p1_jacobi<T>(L, A, D, b, x, x, om, true, s))) != cudaSuccess) return e;
+    for (int l = 0; l < ts; ++l) {
+        DevLevel &L = h->lev[l];
+        T *x = levX<T>(L), *x2 = levX2<T>(L);
+        if (nu1 == 0 && (e = KL(HDG_PROF_P1, 1, launch_fill<T>(x, T(0), L.nv, s))) != cudaSuccess) return e;
         for (int k = 1; k < nu1; ++k) {
-            if ((e = KL(HDG_PROF_P1, 1, launch_p1_jacobi<T>(L, A, D, b, x, x2, om, false, s))) != cudaSuccess) return e;
+            if ((e = KL(HDG_PROF_P1, 1, launch_p1_jacobi<T>(L, levA<T>(L), levD<T>(L), levB<T>(L), x, x2, om, false, s))) != cudaSuccess) return e;
             std::swap(x, x2);
         }
+        cur[l] = x; oth[l] = x2;
+        DevLevel &C = h->lev[l + 1];
+        const bool fuse = (l + 1 < ts) && nu1 >= 1;
+        if ((e = KL(HDG_PROF_P1, 1, launch_p1_down<T>(L, C, levA<T>(L), levB<T>(L), x, levD<T>(C), om, levB<T>(C),
+                                                      fuse ? levX<T>(C) : nullptr, s))) != cudaSuccess) return e;
     }
-    if ((e = KL(HDG_PROF_P1, 1, launch_p1_residual<T>(L, A, b, x, r, s))) != cudaSuccess) return e;
-    DevLevel &C = h->lev[l + 1];
-    if ((e = KL(HDG_PROF_P1, 1, launch_p1_restrict<T>(C, r, levB<T>(C), s))) != cudaSuccess) return e;
-    if ((e = p1_vcycle<T>(h, l + 1)) != cudaSuccess) return e;
-    if ((e = KL(HDG_PROF_P1, 1, launch_p1_prolong_add<T>(C, L.nv, levX<T>(C), x, s))) != cudaSuccess) return e;
-    for (int k = 0; k < nu2; ++k) {
-        if ((e = KL(HDG_PROF_P1, 1, launch_p1_jacobi<T>(L, A, D, b, x, x2, om, false, s))) != cudaSuccess) return e;
-        std::swap(x, x2);
+    {
+        TailArgs a{};
+        a.nlev = nlev - ts;
+        a.nu1 = nu1;
+        a.nu2 = nu2;
+        a.omega = h->prm.p1_omega;
+        size_t smem = 0;
+        for (int l = ts; l < nlev; ++l) {
+            DevLevel &L = h->lev[l];
+            TailLevel &t = a.lev[l - ts];
+            t.nv = L.nv; t.nnz = L.nnz; t.nci = (l > ts) ? L.nci : 0;
+            t.rp = L.row_ptr; t.col = L.col; t.A = levA<T>(L); t.dinv = levD<T>(L);
+            t.cp = L.child_ptr; t.ci = L.child_idx; t.parent = L.parent;
+            t.cw = sizeof(T) == 4 ? static_cast<const void *>(L.child_w32) : static_cast<const void *>(L.child_w);
+        }
+        smem = tail_smem_bytes(h->lev, ts, sizeof(T));
+        a.inv = coarse_inv<T>(h);
+        a.status = h->d_status;
+        a.b_top = levB<T>(h->lev[ts]);
+        a.x_top = levX<T>(h->lev[ts]);
+        if ((e = KL(HDG_PROF_P1, 1, launch_p1_tail<T>(a, smem, s))) != cudaSuccess) return e;
+        res[ts] = levX<T>(h->lev[ts]);
     }
-    // make the result land in the level's primary buffer
-    if (x != levX<T>(L))
-        return cudaMemcpyAsync(levX<T>(L), x, sizeof(T) * L.nv, cudaMemcpyDeviceToDevice, s);
+    for (int l = ts - 1; l >= 0; --l) {
+        DevLevel &L = h->lev[l];
+        DevLevel &C = h->lev[l + 1];
+        T *x = cur[l], *x2 = oth[l];
+        if (nu2 == 0) {
+            if ((e = KL(HDG_PROF_P1, 1, launch_p1_prolong_add<T>(C, L.nv, res[l + 1], x, s))) != cudaSuccess) return e;
+        } else {
+            if ((e = KL(HDG_PROF_P1, 1, launch_p1_up<T>(L, C, levA<T>(L), levD<T>(L), levB<T>(L), x, res[l + 1], x2, om, s))) != cudaSuccess) return e;
+            std::swap(x, x2);
+            for (int k = 1; k < nu2; ++k) {
+                if ((e = KL(HDG_PROF_P1, 1, launch_p1_jacobi<T>(L, levA<T>(L), levD<T>(L), levB<T>(L), x, x2, om, false, s))) != cudaSuccess) return e;
+                std::swap(x, x2);
+            }
+        }
+        res[l] = x;
+    }
+    *result = res[0];
     return cudaSuccess;
 }
 
@@ -256,6 +318,7 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z) {
     const size_t NT = h->NT;
     T *x = k.t0, *x2 = k.t1;
     cudaError_t e;
+    // lines 1-2: pre-smoothing and residual
     if (h->prm.n_pre == 0) {
         if ((e = KL(HDG_PROF_KRYLOV, 1, launch_fill<T>(x, T(0), NT, s))) != cudaSuccess) return e;
     } else {
@@ -265,18 +328,29 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z) {
             std::swap(x, x2);
         }
     }
-    if ((e = KL(cat_res<T>(), 1, launch_residual_t<T>(h, v, x, k.res))) != cudaSuccess) return e;
+    if ((e = KL(cat_res<T>(), 1, launch_residual_t<T>(h, v, x, k.res, true))) != cudaSuccess) return e;
+    // line 3: restriction r_c = pi^T r (with the first P1 sweep when level 0 is above the tail)
     DevLevel &L0 = h->lev[0];
-    if ((e = KL(HDG_PROF_TRANSFER, 1, launch_restrict_t<T>(h, k.res, levB<T>(L0)))) != cudaSuccess) return e;
-    if ((e = p1_vcycle<T>(h, 0)) != cudaSuccess) return e;
-    if ((e = KL(HDG_PROF_TRANSFER, 1, launch_prolong_add_t<T>(h, levX<T>(L0), x))) != cudaSuccess) return e;
+    const bool fuse0 = h->tail_start[sizeof(T) == 8 ? 0 : 1] > 0 && h->prm.p1_nu_pre >= 1;
+    if ((e = KL(HDG_PROF_TRANSFER, 1, launch_restrict_t<T>(h, k.res, levB<T>(L0), fuse0 ? levD<T>(L0) : nullptr,
+                                                           T(h->prm.p1_omega), fuse0 ? levX<T>(L0) : nullptr))) != cudaSuccess) return e;
+    // line 4: coarse problem
+    T *ec = nullptr;
+    if ((e = p1_cycle<T>(h, &ec)) != cudaSuccess) return e;
+    // lines 5-6: x += pi e_c and post-smoothing (the prolongation rides on the first sweep)
     const int np = h->prm.n_post;
-    for (int i = 0; i < np; ++i) {
-        T *out = (i == np - 1) ? z : x2;
-        if ((e = KL(cat_smooth<T>(), 1, launch_smooth_t<T>(h, v, x, out))) != cudaSuccess) return e;
+    if (np == 0) {
+        if ((e = KL(HDG_PROF_TRANSFER, 1, launch_prolong_add_t<T>(h, ec, x))) != cudaSuccess) return e;
+        return cudaMemcpyAsync(z, x, sizeof(T) * NT, cudaMemcpyDeviceToDevice, s);
+    }
+    T *out = (np == 1) ? z : x2;
+    if ((e = KL(cat_smooth<T>(), 1, launch_smooth_prolong_t<T>(h, ec, v, x, out))) != cudaSuccess) return e;
+    std::swap(x, x2);
+    for (int i = 1; i < np; ++i) {
+        T *o = (i == np - 1) ? z : x2;
+        if ((e = KL(cat_smooth<T>(), 1, launch_smooth_t<T>(h, v, x, o))) != cudaSuccess) return e;
         if (i < np - 1) std::swap(x, x2);
     }
-    if (np == 0) return cudaMemcpyAsync(z, x, sizeof(T) * NT, cudaMemcpyDeviceToDevice, s);
     return cudaSuccess;
 }
 
@@ -313,21 +387,16 @@ cudaError_t arnoldi_step(hdg_handle *h, int j) {
     cudaStream_t s = h->stream;
     const size_t NT = W.NT;
     const int ldh = W.m + 1;
-    T *vj = k.V + size_t(j) * NT, *zj = k.Z + size_t(j) * NT;
+    const size_t ld = W.ld;
+    T *vj = k.V + size_t(j) * ld, *zj = k.Z + size_t(j) * ld;
     cudaError_t e;
     if ((e = precond<T>(h, vj, zj)) != cudaSuccess) return e;
     if ((e = KL(cat_apply<T>(), 1, launch_apply_t<T>(h, zj, k.w))) != cudaSuccess) return e;
-    if ((e = dots<T>(h, k.V, j + 1, k.w, W.h1)) != cudaSuccess) return e;
-    if ((e = KL(HDG_PROF_KRYLOV, 1, launch_multi_axpy<T>(k.w, k.V, NT, j + 1, W.h1, -1.0, NT, s))) != cudaSuccess) return e;
-    if ((e = dots<T>(h, k.V, j + 1, k.w, W.h2)) != cudaSuccess) return e;
-    if ((e = KL(HDG_PROF_KRYLOV, 1, launch_multi_axpy<T>(k.w, k.V, NT, j + 1, W.h2, -1.0, NT, s))) != cudaSuccess) return e;
-    if ((e = dots<T>(h, k.w, 1, k.w, W.nrm2)) != cudaSuccess) return e;
-    double *Hcol = W.Hm + size_t(j) * ldh;
-    if ((e = KL(HDG_PROF_KRYLOV, 1, launch_arnoldi_finish(Hcol, W.h1, W.h2, W.nrm2, j, s))) != cudaSuccess) return e;
-    if ((e = KL(HDG_PROF_KRYLOV, 1, launch_scale_copy<T>(k.w, k.V + size_t(j + 1) * NT, Hcol + j + 1, NT, s))) != cudaSuccess) return e;
-    if ((e = KL(HDG_PROF_KRYLOV, 1, launch_givens(W.Hm, ldh, W.cs, W.sn, W.sv, j, W.bnorm, W.est, W.flags, s))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(W.host_buf, W.est, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
-    return cudaMemcpyAsync(W.host_flags, W.flags, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if ((e = KL(HDG_PROF_KRYLOV, 4, launch_gs_step<T>(k.V, ld, j, k.w, W.partial, W.counter, W.nblk_gs, W.h1, W.h2,
+                                                      W.nrm2, W.Hm, ldh, W.cs, W.sn, W.sv, W.bnorm, W.rb,
+                                                      k.V + size_t(j + 1) * ld, s))) != cudaSuccess) return e;
+    (void)NT;
+    return cudaMemcpyAsync(W.host_rb, W.rb, sizeof(ReadBack), cudaMemcpyDeviceToHost, s);
 }
 
 // Run Arnoldi step j: directly while kernel timing is on, otherwise through
@@ -395,14 +464,14 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
         if (rc) return rc;
         TRY(cudaStreamSynchronize(s));
         prof_flush(h);
-        est_out = W.host_buf[0];
-        flag_out = W.host_flags[0];
+        est_out = W.host_rb->est;
+        flag_out = W.host_rb->flags;
         if (est_out <= rel_target || (flag_out & 6)) { ++j; break; }
     }
     its_done = j;
     if (j > 0 && !(flag_out & 4)) {
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_hessenberg_solve(W.Hm, ldh, W.sv, j, W.y, s)));
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_multi_axpy<T>(x, k.Z, NT, j, W.y, 1.0, NT, s)));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_multi_axpy<T>(x, k.Z, W.ld, j, W.y, 1.0, NT, s)));
     }
     return HDG_OK;
 }
@@ -433,7 +502,7 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
     int total = 0;
     for (;;) {
         // r = b - S x into V[0]
-        TRY(KL(cat_res<T>(), 1, launch_residual_t<T>(h, b, x, k.V)));
+        TRY(KL(cat_res<T>(), 1, launch_residual_t<T>(h, b, x, k.V, false)));
         double beta;
         rc = norm_host<T>(h, k.V, beta);
         if (rc) return rc;
@@ -461,7 +530,7 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
         }
         if ((flag & 2) && est > rtol) {
             // breakdown without convergence: check the true residual once more
-            TRY(KL(cat_res<T>(), 1, launch_residual_t<T>(h, b, x, k.V)));
+            TRY(KL(cat_res<T>(), 1, launch_residual_t<T>(h, b, x, k.V, false)));
             double beta2;
             rc = norm_host<T>(h, k.V, beta2);
             if (rc) return rc;
@@ -486,7 +555,7 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info)
     if (bnorm == 0.0) return HDG_OK;
     int total = 0;
     for (int outer = 0;; ++outer) {
-        TRY(KL(HDG_PROF_RESIDUAL64, 1, launch_residual_t<double>(h, g, x, W.r)));
+        TRY(KL(HDG_PROF_RESIDUAL64, 1, launch_residual_t<double>(h, g, x, W.r, false)));
         double beta;
         rc = norm_host<double>(h, W.r, beta);
         if (rc) return rc;
@@ -533,11 +602,11 @@ void free_handle(hdg_handle *h) {
     dfree(h->d_ref); dfree(h->d_X); dfree(h->d_fcell); dfree(h->d_facet_of); dfree(h->d_flip);
     dfree(h->d_facet_cell); dfree(h->d_facet_edge); dfree(h->d_facet_verts); dfree(h->d_v2f_ptr); dfree(h->d_v2f);
     dfree(h->d_nbr); dfree(h->d_Xb); dfree(h->d_Rm); dfree(h->d_W); dfree(h->d_Scell); dfree(h->d_Sval);
-    dfree(h->d_Dinv); dfree(h->d_Sval32); dfree(h->d_Dinv32); dfree(h->d_status); dfree(h->d_coarse_inv);
+    dfree(h->d_Dinv); dfree(h->d_Sval32); dfree(h->d_Dinv32); dfree(h->d_Sval16); dfree(h->d_status); dfree(h->d_coarse_inv);
     dfree(h->d_coarse_inv32); dfree(h->d_coarse_work);
     for (auto &L : h->lev) {
         dfree(L.row_ptr); dfree(L.col); dfree(L.diag); dfree(L.mass); dfree(L.stiff); dfree(L.A); dfree(L.dinv);
-        dfree(L.A32); dfree(L.dinv32); dfree(L.parent); dfree(L.child_ptr); dfree(L.child_idx); dfree(L.child_w);
+        dfree(L.A32); dfree(L.dinv32); dfree(L.parent); dfree(L.child_ptr); dfree(L.child_idx); dfree(L.child_w); dfree(L.child_w32);
         dfree(L.x); dfree(L.x2); dfree(L.b); dfree(L.r); dfree(L.x32); dfree(L.x232); dfree(L.b32); dfree(L.r32);
     }
     if (h->ws) {
@@ -547,7 +616,9 @@ void free_handle(hdg_handle *h) {
         dfree(W.k32.V); dfree(W.k32.Z); dfree(W.k32.w); dfree(W.k32.t0); dfree(W.k32.t1); dfree(W.k32.res);
         dfree(W.k32.b); dfree(W.k32.x);
         dfree(W.Hm); dfree(W.cs); dfree(W.sn); dfree(W.sv); dfree(W.h1); dfree(W.h2); dfree(W.nrm2);
-        dfree(W.est); dfree(W.scal); dfree(W.bnorm);
+        dfree(W.est); dfree(W.counter); dfree(W.rb);
+        if (W.host_rb) cudaFreeHost(W.host_rb);
+        dfree(W.scal); dfree(W.bnorm);
         for (auto &gv : W.graphs)
             for (auto &G : gv)
                 if (G.exec) cudaGraphExecDestroy(G.exec); dfree(W.beta); dfree(W.y); dfree(W.partial); dfree(W.flags);
@@ -584,13 +655,15 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(dalloc(&h->d_Rm, nK * nK * N));
     TRY(dalloc(&h->d_W, m * nK * N));
     TRY(dalloc(&h->d_Scell, N * m * m));
-    TRY(dalloc(&h->d_Sval, 5 * pp * pp * NF));
-    TRY(dalloc(&h->d_Dinv, pp * pp * NF));
+    auto packed = [&](size_t n, size_t G) { return (n + G - 1) / G * G * NF; };
+    TRY(dalloc(&h->d_Sval, packed(5 * pp * pp, 2)));
+    TRY(dalloc(&h->d_Dinv, packed(pp * pp, 2)));
     TRY(dalloc(&h->d_status, 1));
-    const bool mixed = prm->precision == HDG_MIXED_FP32;
+    const bool mixed = prm->precision != HDG_FP64;
     if (mixed) {
-        TRY(dalloc(&h->d_Sval32, 5 * pp * pp * NF));
-        TRY(dalloc(&h->d_Dinv32, pp * pp * NF));
+        TRY(dalloc(&h->d_Sval32, packed(5 * pp * pp, 4)));
+        TRY(dalloc(&h->d_Dinv32, packed(pp * pp, 4)));
+        if (prm->precision == HDG_MIXED_BF16) TRY(dalloc(&h->d_Sval16, packed(5 * pp * pp, 8)));
     }
     h->lev.resize(hm.levels.size());
     for (size_t l = 0; l < hm.levels.size(); ++l) {
@@ -610,6 +683,9 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
             TRY(upload(&L.child_ptr, hl.child_ptr, s));
             TRY(upload(&L.child_idx, hl.child_idx, s));
             TRY(upload(&L.child_w, hl.child_w, s));
+            std::vector<float> w32(hl.child_w.begin(), hl.child_w.end());
+            TRY(upload(&L.child_w32, w32, s));
+            L.nci = int(hl.child_idx.size());
         }
         TRY(dalloc(&L.x, size_t(L.nv)));
         TRY(dalloc(&L.x2, size_t(L.nv)));
@@ -622,6 +698,23 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
             TRY(dalloc(&L.x232, size_t(L.nv)));
             TRY(dalloc(&L.b32, size_t(L.nv)));
             TRY(dalloc(&L.r32, size_t(L.nv)));
+        }
+    }
+    // first level of the single-CTA tail, per precision: small enough to stage
+    // every tail level (operator, transfers, four vectors) in shared memory
+    {
+        int tail_max = kTailMaxVertices;
+        if (const char *ev = std::getenv("HDG_TAIL_MAX_VERTICES")) tail_max = std::max(16, std::min(4096, std::atoi(ev)));
+        const int nlev = int(h->lev.size());
+        for (int pi = 0; pi < 2; ++pi) {
+            const size_t tsz = pi == 0 ? sizeof(double) : sizeof(float);
+            int ts = nlev - 1;
+            while (ts > 0 && h->lev[ts - 1].nv <= tail_max && nlev - (ts - 1) <= kTailMaxLevels &&
+                   tail_smem_bytes(h->lev, ts - 1, tsz) <= size_t(220) * 1024)
+                --ts;
+            if (tail_smem_bytes(h->lev, ts, tsz) > size_t(226) * 1024)
+                return fail(h, HDG_EINVAL, "coarsest P1 level too large for the single-CTA coarse cycle");
+            h->tail_start[pi] = ts;
         }
     }
     const size_t nc = h->lev.back().nv;
@@ -640,17 +733,23 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(dalloc(&W.lam_int, W.NT));
     TRY(dalloc(&W.ycell, N * m));
     const size_t mm = W.m;
+    W.ld = (W.NT + 3) / 4 * 4;
+    W.nblk_gs = int(std::min<size_t>(std::max<size_t>((W.ld / 4 + 1023) / 1024, 1), 304));
     if (!mixed) {
-        TRY(dalloc(&W.k64.V, (mm + 1) * W.NT));
-        TRY(dalloc(&W.k64.Z, mm * W.NT));
-        TRY(dalloc(&W.k64.w, W.NT));
+        TRY(dalloc(&W.k64.V, (mm + 1) * W.ld));
+        TRY(dalloc(&W.k64.Z, mm * W.ld));
+        TRY(dalloc(&W.k64.w, W.ld));
+        TRY(cudaMemsetAsync(W.k64.V, 0, sizeof(double) * (mm + 1) * W.ld, s));
+        TRY(cudaMemsetAsync(W.k64.w, 0, sizeof(double) * W.ld, s));
     } else {
         // FP64 vectors still needed by the FP64 operator entry points
-        TRY(dalloc(&W.k64.V, W.NT));
-        TRY(dalloc(&W.k64.w, W.NT));
-        TRY(dalloc(&W.k32.V, (mm + 1) * W.NT));
-        TRY(dalloc(&W.k32.Z, mm * W.NT));
-        TRY(dalloc(&W.k32.w, W.NT));
+        TRY(dalloc(&W.k64.V, W.ld));
+        TRY(dalloc(&W.k64.w, W.ld));
+        TRY(dalloc(&W.k32.V, (mm + 1) * W.ld));
+        TRY(dalloc(&W.k32.Z, mm * W.ld));
+        TRY(dalloc(&W.k32.w, W.ld));
+        TRY(cudaMemsetAsync(W.k32.V, 0, sizeof(float) * (mm + 1) * W.ld, s));
+        TRY(cudaMemsetAsync(W.k32.w, 0, sizeof(float) * W.ld, s));
         TRY(dalloc(&W.k32.t0, W.NT));
         TRY(dalloc(&W.k32.t1, W.NT));
         TRY(dalloc(&W.k32.res, W.NT));
@@ -678,7 +777,11 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     }
     TRY(dalloc(&W.beta, 1));
     TRY(dalloc(&W.y, mm + 1));
-    TRY(dalloc(&W.partial, (mm + 1) * size_t(W.nchunk)));
+    TRY(dalloc(&W.partial, (mm + 1) * size_t(std::max(W.nchunk, 608))));
+    TRY(dalloc(&W.counter, 1));
+    TRY(cudaMemsetAsync(W.counter, 0, sizeof(unsigned int), s));
+    TRY(dalloc(&W.rb, 1));
+    TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_rb), sizeof(ReadBack)));
     TRY(dalloc(&W.flags, 1));
     TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_buf), 8 * sizeof(double)));
     TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_flags), 4 * sizeof(int32_t)));
@@ -713,6 +816,15 @@ int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solv
         rc = fgmres<double>(h, W.g, W.x, h->prm.rtol, h->prm.max_iter, true, info);
     } else {
         rc = solve_mixed(h, W.g, W.x, info);
+    }
+    {
+        int32_t st = 0;
+        TRY(cudaMemcpyAsync(&st, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        TRY(cudaStreamSynchronize(s));
+        if (st & 8) {
+            rc = fail(h, HDG_ETIMEOUT, "a bounded device-side wait ran out (coarse-cycle staging)");
+            TRY(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), s));
+        }
     }
     info.status = rc;
     TRY(cudaMemcpyAsync(W.lam_int, W.x, sizeof(double) * W.NT, cudaMemcpyDeviceToDevice, s));
@@ -804,10 +916,8 @@ int hdg_condense(hdg_handle *h) {
     for (auto &L : h->lev) TRY(KL(HDG_PROF_CONDENSE, 1, launch_p1_combine(h, L, tau, ctau2)));
     const DevLevel &Lc = h->lev.back();
     TRY(KL(HDG_PROF_CONDENSE, 2, launch_dense_inverse(h, Lc, h->d_coarse_work, h->d_coarse_inv, Lc.nv)));
-    if (h->prm.precision == HDG_MIXED_FP32) {
-        const size_t NF = h->NF, pp = h->pp;
-        TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(h->d_Sval, h->d_Sval32, 5 * pp * pp * NF, s)));
-        TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(h->d_Dinv, h->d_Dinv32, pp * pp * NF, s)));
+    if (h->prm.precision != HDG_FP64) {
+        TRY(KL(HDG_PROF_CONDENSE, h->d_Sval16 ? 3 : 2, launch_repack(h)));
         for (auto &L : h->lev) {
             TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(L.A, L.A32, size_t(L.nnz), s)));
             TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(L.dinv, L.dinv32, size_t(L.nv), s)));

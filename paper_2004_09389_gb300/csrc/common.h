@@ -1,6 +1,7 @@
 // Internal declarations of the HDG trace-solver library (not part of the ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -84,12 +85,45 @@ struct DevLevel {
     int32_t *parent = nullptr;                         // [nv_finer][2]
     int32_t *child_ptr = nullptr, *child_idx = nullptr;
     double *child_w = nullptr;
+    float *child_w32 = nullptr;
+    int nci = 0;                                        // restriction entries (children)
     // work vectors
     double *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;
     float *x32 = nullptr, *x232 = nullptr, *b32 = nullptr, *r32 = nullptr;
 };
 
 struct Workspace;   // solver vectors, defined in api.cu
+
+// per-iteration readback of the Krylov driver (pinned host copy)
+struct ReadBack {
+    double est;      // |s_{j+1}| / ||b||
+    double hnext;    // h_{j+1,j} before rotation
+    int32_t flags;   // 2: breakdown, 4: NaN/Inf
+    int32_t pad;
+};
+
+// levels of the single-CTA V-cycle tail (k_p1.cu)
+constexpr int kTailMaxLevels = 8;
+constexpr int kTailMaxVertices = 1024;     // default largest level run inside the tail kernel
+struct TailLevel {
+    int nv, nnz, nci;
+    const int32_t *rp, *col;            // CSR of the level operator
+    const void *A, *dinv;               // values in the solve precision
+    const int32_t *cp, *ci;             // restriction into this level (children in the finer level)
+    const void *cw;                     // child weights in the solve precision
+    const int32_t *parent;              // prolongation from this level to the finer one
+};
+// shared-memory bytes of the tail kernel for levels [first, levels.size()) in precision of size tsz
+size_t tail_smem_bytes(const std::vector<DevLevel> &lev, int first, size_t tsz);
+struct TailArgs {
+    int nlev, nu1, nu2;
+    double omega;
+    TailLevel lev[kTailMaxLevels];
+    int32_t *status;                    // device error flags (8: shared-memory staging timed out)
+    const void *inv;                    // dense inverse of the last level
+    const void *b_top;                  // right-hand side of the first tail level (global)
+    void *x_top;                        // its solution (global)
+};
 
 // per-category kernel accounting (see hdg_profile_enable)
 struct Prof {
@@ -131,12 +165,14 @@ struct hdg_handle {
     double *d_W = nullptr;          // C A^-1 Mass   [m*nK][N]
     double *d_Scell = nullptr;      // S_K           [N][m][m]
     // facet-row trace operator
-    double *d_Sval = nullptr;       // [5*pp*pp][NF]
-    double *d_Dinv = nullptr;       // [pp*pp][NF]
+    double *d_Sval = nullptr;       // 5(p+1)^2 values per facet, packed in 16-byte groups
+    double *d_Dinv = nullptr;       // (p+1)^2 values per facet, packed likewise
     float *d_Sval32 = nullptr, *d_Dinv32 = nullptr;
+    __nv_bfloat16 *d_Sval16 = nullptr;   // preconditioner copy (HDG_MIXED_BF16)
     int32_t *d_status = nullptr;    // device error flags
 
     std::vector<hdg::DevLevel> lev;
+    int tail_start[2] = {0, 0};       // first P1 level of the single-CTA tail kernel (FP64, FP32)
     double *d_coarse_inv = nullptr;   // dense inverse of the coarsest P1 operator
     double *d_coarse_work = nullptr;
     float *d_coarse_inv32 = nullptr;
@@ -166,6 +202,11 @@ cudaError_t launch_to_f32(const double *x, float *y, size_t n, cudaStream_t s);
 
 // trace-space kernels (k_trace.cu); vectors in the internal layout [pp][NF]
 cudaError_t launch_to_internal(hdg_handle *h, const double *ext, double *in);
+cudaError_t launch_repack(hdg_handle *h);
+// index of element j of facet e in an operator array packed in groups of G
+inline __host__ __device__ size_t packed_index(size_t j, size_t e, size_t NF, size_t G) {
+    return ((j / G) * NF + e) * G + j % G;
+}
 cudaError_t launch_to_external(hdg_handle *h, const double *in, double *ext);
 cudaError_t launch_rhs(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell);
 cudaError_t launch_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lam,
@@ -183,6 +224,14 @@ template <typename T>
 cudaError_t launch_p1_prolong_add(const DevLevel &coarse, int nv_fine, const T *ec, T *xf, cudaStream_t s);
 template <typename T>
 cudaError_t launch_dense_apply(const T *inv, int n, const T *b, T *x, cudaStream_t s);
+template <typename T>
+cudaError_t launch_p1_down(const DevLevel &fine, const DevLevel &coarse, const T *A_f, const T *b_f, const T *x_f,
+                           const T *dinv_c, T omega, T *b_c, T *x_c, cudaStream_t s);
+template <typename T>
+cudaError_t launch_p1_up(const DevLevel &fine, const DevLevel &coarse, const T *A_f, const T *dinv_f, const T *b_f,
+                         const T *x_f, const T *ec, T *xout, T omega, cudaStream_t s);
+template <typename T>
+cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s);
 
 // Krylov kernels (k_krylov.cu)
 template <typename T>
@@ -202,6 +251,10 @@ cudaError_t launch_hessenberg_solve(const double *Hm, int ldh, const double *sv,
                                     cudaStream_t s);
 template <typename T>
 cudaError_t launch_fill(T *x, T v, size_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gs_step(const T *V, size_t ld, int j, T *w, double *partial, unsigned int *counter, int nblk,
+                           double *h1, double *h2, double *nrm2, double *Hm, int ldh, double *cs, double *sn,
+                           double *sv, const double *bnorm, ReadBack *rb, T *vnext, cudaStream_t s);
 cudaError_t launch_axpby_mixed(double *x, const float *d, const double *scale, size_t n, cudaStream_t s);
 cudaError_t launch_d2f_scaled(const double *x, float *y, const double *scale, size_t n, cudaStream_t s);
 

@@ -191,7 +191,9 @@ __global__ void __launch_bounds__(kCondenseThreads) condense_kernel(CondenseArgs
 //   (S x)_{e,r} = sum_c D_e[r][c] x_{e,c} + sum_{s,k} O_{s,k}[r][c] x_{nbr(s,k),c}
 // with D_e the sum of both cells' diagonal blocks and O_{s,k} the block of S_{K_s}
 // coupling edge i_s to edge (i_s + 1 + k) % 3 (neighbour facet nbr(s,k)).
-// Stored as Sval[(r*5 + b)*PP + c][e], b = 0 (D_e), 1 + 2s + k; Dinv = D_e^-1.
+// Element j = (r*5 + b)*PP + c (b = 0: D_e, b = 1 + 2s + k) of facet e is stored at
+// packed_index(j, e, NF, 2) (16-byte groups of two doubles); Dinv = D_e^-1 likewise.
+// Padding lanes of the last group are zero.
 struct AssembleArgs {
     int N, NF;
     const double *Scell;
@@ -223,7 +225,7 @@ __global__ void assemble_kernel(AssembleArgs a) {
                 v += a.Scell[size_t(K[s]) * M * M + lr * M + lc];
             }
             D[r][c] = v;
-            a.Sval[size_t((r * 5 + 0) * PP + c) * NF + e] = v;
+            a.Sval[packed_index((r * 5 + 0) * PP + c, e, NF, 2)] = v;
         }
     for (int s = 0; s < 2; ++s)
         for (int k = 0; k < 2; ++k) {
@@ -235,7 +237,7 @@ __global__ void assemble_kernel(AssembleArgs a) {
                 const int lr = I[s] * PP + (F[s] ? P - r : r);
                 for (int c = 0; c < PP; ++c) {
                     const int lc = i2 * PP + (f2 ? P - c : c);
-                    a.Sval[size_t((r * 5 + b) * PP + c) * NF + e] = a.Scell[size_t(K[s]) * M * M + lr * M + lc];
+                    a.Sval[packed_index((r * 5 + b) * PP + c, e, NF, 2)] = a.Scell[size_t(K[s]) * M * M + lr * M + lc];
                 }
             }
         }
@@ -265,7 +267,9 @@ __global__ void assemble_kernel(AssembleArgs a) {
     }
     if (singular) atomicOr(a.status, 2);
     for (int r = 0; r < PP; ++r)
-        for (int c = 0; c < PP; ++c) a.Dinv[size_t(r * PP + c) * NF + e] = Inv[r][c];
+        for (int c = 0; c < PP; ++c) a.Dinv[packed_index(r * PP + c, e, NF, 2)] = Inv[r][c];
+    if ((5 * PP * PP) % 2) a.Sval[packed_index(5 * PP * PP, e, NF, 2)] = 0.0;
+    if ((PP * PP) % 2) a.Dinv[packed_index(PP * PP, e, NF, 2)] = 0.0;
 }
 
 // ---------------------------------------------------------------- P1 level operator

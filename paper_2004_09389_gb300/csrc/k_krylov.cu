@@ -15,6 +15,7 @@ inline unsigned blocks(size_t n, int bs) { return unsigned((n + bs - 1) / bs); }
 
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double red[32];
+    __syncthreads();      // red[] may still be read by a previous call
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
     if (lane == 0) red[warp] = v;
@@ -34,10 +35,10 @@ __global__ void __launch_bounds__(256) multidot_kernel(const T *__restrict__ V, 
     const size_t len = (n + nchunk - 1) / nchunk;
     const size_t beg = size_t(c) * len, end = beg + len < n ? beg + len : n;
     const T *v = V + size_t(i) * ld;
-    double acc = 0.0;
-    for (size_t k = beg + threadIdx.x; k < end; k += blockDim.x) acc = fma(double(v[k]), double(w[k]), acc);
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) partial[size_t(i) * nchunk + c] = acc;
+    T acc = T(0);
+    for (size_t k = beg + threadIdx.x; k < end; k += blockDim.x) acc = fma(v[k], w[k], acc);
+    const double tot = block_sum(double(acc));
+    if (threadIdx.x == 0) partial[size_t(i) * nchunk + c] = tot;
 }
 
 __global__ void reduce_partials_kernel(const double *__restrict__ partial, int nchunk, double *__restrict__ out) {
@@ -52,11 +53,14 @@ __global__ void reduce_partials_kernel(const double *__restrict__ partial, int n
 template <typename T>
 __global__ void __launch_bounds__(256) multi_axpy_kernel(T *__restrict__ w, const T *__restrict__ V, size_t ld, int k,
                                                          const double *__restrict__ coef, double sign, size_t n) {
+    __shared__ T cf[66];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) cf[i] = T(sign * coef[i]);
+    __syncthreads();
     const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (idx >= n) return;
-    double acc = 0.0;
-    for (int i = 0; i < k; ++i) acc = fma(coef[i], double(V[size_t(i) * ld + idx]), acc);
-    w[idx] = T(double(w[idx]) + sign * acc);
+    T acc = w[idx];
+    for (int i = 0; i < k; ++i) acc = fma(cf[i], V[size_t(i) * ld + idx], acc);
+    w[idx] = acc;
 }
 
 template <typename T>
@@ -64,7 +68,7 @@ __global__ void scale_copy_kernel(const T *__restrict__ w, T *__restrict__ v, co
                                   size_t n) {
     const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (idx >= n) return;
-    v[idx] = T(double(w[idx]) / denom[0]);
+    v[idx] = w[idx] * T(1.0 / denom[0]);
 }
 
 // Hessenberg column j from the two Gram-Schmidt passes; h[j+1] = ||w||
@@ -127,7 +131,190 @@ __global__ void axpby_mixed_kernel(double *x, const float *d, const double *scal
 // y = float(x / scale[0])
 __global__ void d2f_scaled_kernel(const double *x, float *y, const double *scale, size_t n) {
     const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx < n) y[idx] = float(x[idx] / scale[0]);
+    if (idx < n) y[idx] = float(x[idx] * (1.0 / scale[0]));
+}
+
+
+// ---------------------------------------------------------------- fused CGS2
+// Vectors of the Krylov basis are padded to a multiple of 16 bytes (zero
+// padding) so every thread moves 16-byte words.  Arithmetic stays in the
+// vector precision per element (GB300's FP64 and conversion throughput is a
+// small fraction of its FP32 throughput); only the per-block partial sums are
+// combined in double.
+template <typename T> struct V16;
+template <> struct V16<float> {
+    using type = float4;
+    using acc = float;
+    __device__ static float dot(const float4 a, const float4 b) {
+        return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+    }
+    __device__ static float4 axpy(float c, const float4 v, const float4 w) {
+        return make_float4(fmaf(c, v.x, w.x), fmaf(c, v.y, w.y), fmaf(c, v.z, w.z), fmaf(c, v.w, w.w));
+    }
+    __device__ static float4 scale(const float4 v, float s) { return make_float4(v.x * s, v.y * s, v.z * s, v.w * s); }
+};
+template <> struct V16<double> {
+    using type = double2;
+    using acc = double;
+    __device__ static double dot(const double2 a, const double2 b) { return fma(a.x, b.x, a.y * b.y); }
+    __device__ static double2 axpy(double c, const double2 v, const double2 w) {
+        return make_double2(fma(c, v.x, w.x), fma(c, v.y, w.y));
+    }
+    __device__ static double2 scale(const double2 v, double s) { return make_double2(v.x * s, v.y * s); }
+};
+
+// Partial sums of V_i . w for i < k over this block's grid-stride range, in
+// groups of kGroup vectors (one pass over w per group, kGroup accumulators per
+// thread), then the last block to finish adds the partials in block order,
+// one warp per vector (deterministic).
+constexpr int kGroup = 16;
+
+template <typename T>
+__device__ void dots_and_finish(const typename V16<T>::type *__restrict__ V, size_t ld4, int k,
+                                const typename V16<T>::type *w, size_t n4, double *partial,
+                                unsigned int *counter, double *out, bool *is_last) {
+    using A = typename V16<T>::acc;
+    __shared__ bool last;
+    __shared__ A red[kGroup][9];
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nwarp = blockDim.x / 32;
+    for (int i0 = 0; i0 < k; i0 += kGroup) {
+        A acc[kGroup];
+#pragma unroll
+        for (int g = 0; g < kGroup; ++g) acc[g] = A(0);
+        for (size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < n4; idx += size_t(gridDim.x) * blockDim.x) {
+            const typename V16<T>::type wv = w[idx];
+#pragma unroll
+            for (int g = 0; g < kGroup; ++g)
+                if (i0 + g < k) acc[g] += V16<T>::dot(V[size_t(i0 + g) * ld4 + idx], wv);
+        }
+#pragma unroll
+        for (int g = 0; g < kGroup; ++g) {
+            A v = acc[g];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) red[g][warp] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < kGroup && i0 + int(threadIdx.x) < k) {
+            A v = A(0);
+            for (int q = 0; q < nwarp; ++q) v += red[threadIdx.x][q];
+            partial[size_t(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = double(v);
+        }
+        __syncthreads();
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    *is_last = last;
+    if (!last) return;
+    __threadfence();
+    for (int i = warp; i < k; i += nwarp) {
+        double v = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32) v += partial[size_t(i) * gridDim.x + b];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) out[i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// w -= V c over this block's grid-stride range, coefficients staged in shared
+// memory in the vector precision
+template <typename T>
+__device__ void block_update(const typename V16<T>::type *__restrict__ V, size_t ld4, int k,
+                             typename V16<T>::type *w, size_t n4, const double *c) {
+    __shared__ T cs_[66];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) cs_[i] = T(-c[i]);
+    __syncthreads();
+    for (size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < n4; idx += size_t(gridDim.x) * blockDim.x) {
+        typename V16<T>::type acc = w[idx];
+        for (int i = 0; i < k; ++i) acc = V16<T>::axpy(cs_[i], V[size_t(i) * ld4 + idx], acc);
+        w[idx] = acc;
+    }
+    __syncthreads();
+}
+
+// pass 1: h1 = V^T w
+template <typename T>
+__global__ void __launch_bounds__(256) gs_dots_kernel(const T *V, size_t ld, int k, const T *w, size_t n,
+                                                      double *partial, unsigned int *counter, double *h1) {
+    using V4 = typename V16<T>::type;
+    bool last;
+    dots_and_finish<T>(reinterpret_cast<const V4 *>(V), ld / (16 / sizeof(T)), k, reinterpret_cast<const V4 *>(w),
+                       n / (16 / sizeof(T)), partial, counter, h1, &last);
+}
+
+// w -= V h1, then pass 2: h2 = V^T w
+template <typename T>
+__global__ void __launch_bounds__(256) gs_update_dots_kernel(const T *V, size_t ld, int k, T *w, size_t n,
+                                                             const double *h1, double *partial, unsigned int *counter,
+                                                             double *h2) {
+    using V4 = typename V16<T>::type;
+    const size_t ld4 = ld / (16 / sizeof(T)), n4 = n / (16 / sizeof(T));
+    const V4 *V4p = reinterpret_cast<const V4 *>(V);
+    V4 *w4 = reinterpret_cast<V4 *>(w);
+    block_update<T>(V4p, ld4, k, w4, n4, h1);
+    bool last;
+    dots_and_finish<T>(V4p, ld4, k, w4, n4, partial, counter, h2, &last);
+}
+
+// w -= V h2, ||w||^2; the last block forms Hessenberg column j (h1 + h2,
+// h_{j+1,j} = ||w||), applies the previous Givens rotations, forms rotation j,
+// updates the least-squares right-hand side and writes the residual
+// estimate |s_{j+1}| / ||b|| and the flags (2: breakdown, 4: NaN/Inf) to rb.
+template <typename T>
+__global__ void __launch_bounds__(256) gs_update_norm_givens_kernel(const T *V, size_t ld, int k, T *w, size_t n,
+                                                                    const double *h1, const double *h2,
+                                                                    double *partial, unsigned int *counter,
+                                                                    double *nrm2, double *Hm, int ldh, double *cs,
+                                                                    double *sn, double *sv, int j,
+                                                                    const double *bnorm, ReadBack *rb) {
+    using V4 = typename V16<T>::type;
+    const size_t ld4 = ld / (16 / sizeof(T)), n4 = n / (16 / sizeof(T));
+    const V4 *V4p = reinterpret_cast<const V4 *>(V);
+    V4 *w4 = reinterpret_cast<V4 *>(w);
+    block_update<T>(V4p, ld4, k, w4, n4, h2);
+    bool last;
+    dots_and_finish<T>(w4, 0, 1, w4, n4, partial, counter, nrm2, &last);
+    if (!last || threadIdx.x != 0) return;
+    double *col = Hm + size_t(j) * ldh;
+    for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+    col[j + 1] = sqrt(nrm2[0]);
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double den = hypot(a, b);
+    int32_t fl = 0;
+    if (!(den > 0.0)) {
+        cs[j] = 1.0; sn[j] = 0.0;
+        fl |= 2;
+    } else {
+        cs[j] = a / den; sn[j] = b / den;
+    }
+    if (!(fabs(b) > 1e-300 * (fabs(a) + 1e-300))) fl |= 2;
+    col[j] = (den > 0.0) ? den : a;
+    col[j + 1] = 0.0;
+    sv[j + 1] = -sn[j] * sv[j];
+    sv[j] = cs[j] * sv[j];
+    const double est = fabs(sv[j + 1]) / bnorm[0];
+    if (!isfinite(est) || !isfinite(den)) fl |= 4;
+    rb->est = est;
+    rb->flags = fl;
+    rb->hnext = b;
+}
+
+// v_{j+1} = w / h_{j+1,j}  (the unrotated norm kept in rb->hnext)
+template <typename T>
+__global__ void gs_scale_kernel(const T *w, T *v, size_t n, const ReadBack *rb) {
+    using V4 = typename V16<T>::type;
+    const size_t n4 = n / (16 / sizeof(T));
+    const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= n4) return;
+    const T inv = T(1.0 / rb->hnext);
+    reinterpret_cast<V4 *>(v)[idx] = V16<T>::scale(reinterpret_cast<const V4 *>(w)[idx], inv);
 }
 
 }  // namespace
@@ -182,6 +369,27 @@ cudaError_t launch_d2f_scaled(const double *x, float *y, const double *scale, si
     d2f_scaled_kernel<<<blocks(n, 256), 256, 0, s>>>(x, y, scale, n);
     return cudaGetLastError();
 }
+
+
+template <typename T>
+cudaError_t launch_gs_step(const T *V, size_t ld, int j, T *w, double *partial, unsigned int *counter, int nblk,
+                           double *h1, double *h2, double *nrm2, double *Hm, int ldh, double *cs, double *sn,
+                           double *sv, const double *bnorm, ReadBack *rb, T *vnext, cudaStream_t s) {
+    const int k = j + 1;
+    gs_dots_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, partial, counter, h1);
+    gs_update_dots_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, h1, partial, counter, h2);
+    gs_update_norm_givens_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, h1, h2, partial, counter, nrm2, Hm, ldh, cs,
+                                                        sn, sv, j, bnorm, rb);
+    const size_t n4 = ld / (16 / sizeof(T));
+    gs_scale_kernel<T><<<blocks(n4, 256), 256, 0, s>>>(w, vnext, ld, rb);
+    return cudaGetLastError();
+}
+template cudaError_t launch_gs_step<float>(const float *, size_t, int, float *, double *, unsigned int *, int, double *,
+                                           double *, double *, double *, int, double *, double *, double *,
+                                           const double *, ReadBack *, float *, cudaStream_t);
+template cudaError_t launch_gs_step<double>(const double *, size_t, int, double *, double *, unsigned int *, int,
+                                            double *, double *, double *, double *, int, double *, double *, double *,
+                                            const double *, ReadBack *, double *, cudaStream_t);
 
 #define HDG_KRYLOV_INST(T)                                                                                      \
     template cudaError_t launch_multidot<T>(const T *, size_t, int, const T *, size_t, double *, int,           \

@@ -68,6 +68,238 @@ __global__ void dense_apply_kernel(const T *__restrict__ inv, int n, const T *__
     if (lane == 0) x[row] = T(acc);
 }
 
+
+// Going down one level, fused: b_c = R (b_f - A_f x_f) with the fine residual
+// formed on the fly for each child, and the first pre-smoothing sweep of the
+// coarse level from zero, x_c = omega D_c^-1 b_c (skipped when xc is null).
+// Eight lanes per coarse vertex share its children; their partial sums are
+// combined by a fixed shuffle tree (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(256) down_kernel(int nc, const int32_t *__restrict__ cp,
+                                                   const int32_t *__restrict__ ci, const T *__restrict__ cw,
+                                                   const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                                   const T *__restrict__ A, const T *__restrict__ bf,
+                                                   const T *__restrict__ xf, const T *__restrict__ dinv_c, T omega,
+                                                   T *__restrict__ bc, T *__restrict__ xc) {
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 3, lane = threadIdx.x & 7;
+    const bool valid = gid < nc;
+    T acc = T(0);
+    if (valid) {
+        for (int k = cp[gid] + lane; k < cp[gid + 1]; k += 8) {
+            const int f = ci[k];
+            T ax = T(0);
+            for (int q = rp[f]; q < rp[f + 1]; ++q) ax = fma(A[q], xf[col[q]], ax);
+            acc = fma(cw[k], bf[f] - ax, acc);
+        }
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (valid && lane == 0) {
+        bc[gid] = acc;
+        if (xc) xc[gid] = omega * dinv_c[gid] * acc;
+    }
+}
+
+// Going up one level, fused: x' = x + P e_c (midpoint prolongation, formed on
+// the fly for every column) followed by one damped Jacobi sweep on x'.
+template <typename T>
+__global__ void up_kernel(int nf, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                          const T *__restrict__ A, const T *__restrict__ dinv, const T *__restrict__ b,
+                          const T *__restrict__ x, const int32_t *__restrict__ parent, const T *__restrict__ ec,
+                          T *__restrict__ xout, T omega) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    T ax = T(0);
+    for (int q = rp[i]; q < rp[i + 1]; ++q) {
+        const int j = col[q], a = parent[2 * j], bb = parent[2 * j + 1];
+        const T pj = (a == bb) ? ec[a] : T(0.5) * (ec[a] + ec[bb]);
+        ax = fma(A[q], x[j] + pj, ax);
+    }
+    const int a = parent[2 * i], bb = parent[2 * i + 1];
+    const T xi = x[i] + ((a == bb) ? ec[a] : T(0.5) * (ec[a] + ec[bb]));
+    xout[i] = fma(omega * dinv[i], b[i] - ax, xi);
+}
+
+// The V-cycle over the small levels in one CTA.  Every level's operator
+// (CSR, values, inverse diagonal) and transfer lists are first copied into
+// shared memory by TMA bulk copies (cp.async.bulk, one mbarrier with a
+// transaction count), then the steps run with __syncthreads between them.
+// Level 0 of the tail takes b from global memory and returns x there; the last
+// level is solved with its dense inverse (read from global memory).
+// Every staged array starts 16-byte aligned in global memory (separate
+// allocations padded to 16 bytes) and in shared memory (offsets rounded up).
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+// bounded wait on phase 0 of the barrier; false if the limit ran out
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(smem_u32(bar)) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__host__ __device__ constexpr size_t pad16(size_t bytes) { return (bytes + 15) / 16 * 16; }
+
+template <typename T>
+__global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    __shared__ __align__(8) uint64_t bar;
+    // per level: A[nnz], dinv[nv], cw[nci], x, x2, b, r [nv] (T); rp[nv+1], col[nnz],
+    // cp[nv+1], ci[nci], par[2 nv_finer] (int32), each 16-byte aligned
+    int32_t *RP[kTailMaxLevels], *COL[kTailMaxLevels], *CP[kTailMaxLevels], *CI[kTailMaxLevels], *PAR[kTailMaxLevels];
+    T *AV[kTailMaxLevels], *DV[kTailMaxLevels], *CW[kTailMaxLevels];
+    T *X[kTailMaxLevels], *X2[kTailMaxLevels], *B[kTailMaxLevels], *R[kTailMaxLevels];
+    {
+        unsigned char *q = tail_smem;
+        for (int l = 0; l < a.nlev; ++l) {
+            const TailLevel &L = a.lev[l];
+            const int nfin = l > 0 ? a.lev[l - 1].nv : 0;
+            AV[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nnz);
+            DV[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nv);
+            CW[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nci);
+            X[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nv);
+            X2[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nv);
+            B[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nv);
+            R[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nv);
+            RP[l] = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(L.nv + 1));
+            COL[l] = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(L.nnz));
+            CP[l] = reinterpret_cast<int32_t *>(q); q += l > 0 ? pad16(4 * size_t(L.nv + 1)) : 0;
+            CI[l] = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(L.nci));
+            PAR[l] = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(2 * nfin));
+        }
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tx = 0;
+        for (int l = 0; l < a.nlev; ++l) {
+            const TailLevel &L = a.lev[l];
+            tx += pad16(sizeof(T) * L.nnz) + pad16(sizeof(T) * L.nv) + pad16(4 * size_t(L.nv + 1)) + pad16(4 * size_t(L.nnz));
+            if (l > 0) tx += pad16(sizeof(T) * L.nci) + pad16(4 * size_t(L.nv + 1)) + pad16(4 * size_t(L.nci)) +
+                             pad16(4 * size_t(2 * a.lev[l - 1].nv));
+        }
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(&bar)), "r"(tx) : "memory");
+        for (int l = 0; l < a.nlev; ++l) {
+            const TailLevel &L = a.lev[l];
+            bulk_g2s(AV[l], L.A, pad16(sizeof(T) * L.nnz), &bar);
+            bulk_g2s(DV[l], L.dinv, pad16(sizeof(T) * L.nv), &bar);
+            bulk_g2s(RP[l], L.rp, pad16(4 * size_t(L.nv + 1)), &bar);
+            bulk_g2s(COL[l], L.col, pad16(4 * size_t(L.nnz)), &bar);
+            if (l > 0) {
+                bulk_g2s(CW[l], L.cw, pad16(sizeof(T) * L.nci), &bar);
+                bulk_g2s(CP[l], L.cp, pad16(4 * size_t(L.nv + 1)), &bar);
+                bulk_g2s(CI[l], L.ci, pad16(4 * size_t(L.nci)), &bar);
+                bulk_g2s(PAR[l], L.parent, pad16(4 * size_t(2 * a.lev[l - 1].nv)), &bar);
+            }
+        }
+    }
+    // right-hand side of the top level with plain loads meanwhile
+    {
+        const T *btop = static_cast<const T *>(a.b_top);
+        for (int i = threadIdx.x; i < a.lev[0].nv; i += blockDim.x) B[0][i] = btop[i];
+    }
+    if (!bar_wait(&bar, 1ll << 22)) {
+        // the copies did not complete: record it, give them one more bounded
+        // wait so none is left writing into this CTA's shared memory, return
+        if (threadIdx.x == 0) atomicOr(a.status, 8);
+        bar_wait(&bar, 1ll << 22);
+        return;
+    }
+    __syncthreads();
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const T om = T(a.omega);
+    const int last = a.nlev - 1;
+    // ---- down
+    for (int l = 0; l < last; ++l) {
+        const int nv = a.lev[l].nv;
+        const int32_t *rp = RP[l], *cl = COL[l];
+        const T *A = AV[l], *D = DV[l];
+        T *x = X[l], *x2 = X2[l];
+        if (a.nu1 == 0) {
+            for (int i = tid; i < nv; i += nt) x[i] = T(0);
+        } else {
+            for (int i = tid; i < nv; i += nt) x[i] = om * D[i] * B[l][i];
+        }
+        __syncthreads();
+        for (int k = 1; k < a.nu1; ++k) {
+            for (int i = tid; i < nv; i += nt) {
+                T ax = T(0);
+                for (int q = rp[i]; q < rp[i + 1]; ++q) ax = fma(A[q], x[cl[q]], ax);
+                x2[i] = fma(om * D[i], B[l][i] - ax, x[i]);
+            }
+            __syncthreads();
+            T *t = x; x = x2; x2 = t;
+        }
+        X[l] = x; X2[l] = x2;
+        for (int i = tid; i < nv; i += nt) {
+            T ax = T(0);
+            for (int q = rp[i]; q < rp[i + 1]; ++q) ax = fma(A[q], x[cl[q]], ax);
+            R[l][i] = B[l][i] - ax;
+        }
+        __syncthreads();
+        const int ncv = a.lev[l + 1].nv;
+        const int32_t *cp = CP[l + 1], *ci = CI[l + 1];
+        const T *cw = CW[l + 1];
+        for (int i = tid; i < ncv; i += nt) {
+            T acc = T(0);
+            for (int k = cp[i]; k < cp[i + 1]; ++k) acc = fma(cw[k], R[l][ci[k]], acc);
+            B[l + 1][i] = acc;
+        }
+        __syncthreads();
+    }
+    // ---- coarsest: dense inverse
+    {
+        const T *inv = static_cast<const T *>(a.inv);
+        const int n = a.lev[last].nv;
+        for (int i = tid; i < n; i += nt) {
+            T acc = T(0);
+            for (int j = 0; j < n; ++j) acc = fma(inv[size_t(i) * n + j], B[last][j], acc);
+            X[last][i] = acc;
+        }
+        __syncthreads();
+    }
+    // ---- up
+    for (int l = last - 1; l >= 0; --l) {
+        const int nv = a.lev[l].nv;
+        const int32_t *rp = RP[l], *cl = COL[l], *par = PAR[l + 1];
+        const T *A = AV[l], *D = DV[l];
+        T *x = X[l], *x2 = X2[l];
+        const T *ec = X[l + 1];
+        for (int i = tid; i < nv; i += nt) {
+            const int p0 = par[2 * i], p1 = par[2 * i + 1];
+            x[i] += (p0 == p1) ? ec[p0] : T(0.5) * (ec[p0] + ec[p1]);
+        }
+        __syncthreads();
+        for (int k = 0; k < a.nu2; ++k) {
+            for (int i = tid; i < nv; i += nt) {
+                T ax = T(0);
+                for (int q = rp[i]; q < rp[i + 1]; ++q) ax = fma(A[q], x[cl[q]], ax);
+                x2[i] = fma(om * D[i], B[l][i] - ax, x[i]);
+            }
+            __syncthreads();
+            T *t = x; x = x2; x2 = t;
+        }
+        X[l] = x; X2[l] = x2;
+    }
+    T *xtop = static_cast<T *>(a.x_top);
+    for (int i = tid; i < a.lev[0].nv; i += nt) xtop[i] = X[0][i];
+}
+
 }  // namespace
 
 template <typename T>
@@ -98,6 +330,30 @@ cudaError_t launch_dense_apply(const T *inv, int n, const T *b, T *x, cudaStream
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_p1_down(const DevLevel &fine, const DevLevel &coarse, const T *A_f, const T *b_f, const T *x_f,
+                           const T *dinv_c, T omega, T *b_c, T *x_c, cudaStream_t s) {
+    const T *cw = sizeof(T) == 4 ? reinterpret_cast<const T *>(coarse.child_w32) : reinterpret_cast<const T *>(coarse.child_w);
+    down_kernel<T><<<blocks(size_t(coarse.nv) * 8, 256), 256, 0, s>>>(coarse.nv, coarse.child_ptr, coarse.child_idx, cw,
+                                                                      fine.row_ptr, fine.col, A_f, b_f, x_f, dinv_c,
+                                                                      omega, b_c, x_c);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_p1_up(const DevLevel &fine, const DevLevel &coarse, const T *A_f, const T *dinv_f, const T *b_f,
+                         const T *x_f, const T *ec, T *xout, T omega, cudaStream_t s) {
+    up_kernel<T><<<blocks(fine.nv, 256), 256, 0, s>>>(fine.nv, fine.row_ptr, fine.col, A_f, dinv_f, b_f, x_f,
+                                                      coarse.parent, ec, xout, omega);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(tail_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    tail_kernel<T><<<1, 1024, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 #define HDG_P1_INST(T)                                                                                         \
     template cudaError_t launch_p1_jacobi<T>(const DevLevel &, const T *, const T *, const T *, const T *, T *, \
                                              T, bool, cudaStream_t);                                           \
@@ -105,7 +361,12 @@ cudaError_t launch_dense_apply(const T *inv, int n, const T *b, T *x, cudaStream
                                                cudaStream_t);                                                  \
     template cudaError_t launch_p1_restrict<T>(const DevLevel &, const T *, T *, cudaStream_t);                 \
     template cudaError_t launch_p1_prolong_add<T>(const DevLevel &, int, const T *, T *, cudaStream_t);         \
-    template cudaError_t launch_dense_apply<T>(const T *, int, const T *, T *, cudaStream_t);
+    template cudaError_t launch_dense_apply<T>(const T *, int, const T *, T *, cudaStream_t);                  \
+    template cudaError_t launch_p1_down<T>(const DevLevel &, const DevLevel &, const T *, const T *, const T *,  \
+                                           const T *, T, T *, T *, cudaStream_t);                               \
+    template cudaError_t launch_p1_up<T>(const DevLevel &, const DevLevel &, const T *, const T *, const T *,    \
+                                         const T *, const T *, T *, T, cudaStream_t);                           \
+    template cudaError_t launch_p1_tail<T>(const TailArgs &, size_t, cudaStream_t);
 HDG_P1_INST(double)
 HDG_P1_INST(float)
 

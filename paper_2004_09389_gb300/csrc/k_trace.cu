@@ -14,75 +14,184 @@
 //   x_new = x + omega D_e^-1 (b - S x)  on the facet's p+1 values.
 #include "common.h"
 
+#include <cuda_bf16.h>
+#include <type_traits>
+
 namespace hdg {
 
 namespace {
 
+template <typename TO> __device__ __forceinline__ TO convert_to(double v);
+template <> __device__ __forceinline__ double convert_to<double>(double v) { return v; }
+template <> __device__ __forceinline__ float convert_to<float>(double v) { return float(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 convert_to<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+
+// Operator values are packed in 16-byte groups: element j of facet e lives at
+// group (j / G, e), lane j % G, with G = 16 / sizeof(storage); every thread
+// issues one 16-byte load per group.  Storage FP64 (G = 2), FP32 (G = 4) or
+// BF16 (G = 8, unpacked to FP32); arithmetic in the compute type T.
+template <typename ST> struct Pack;
+template <> struct Pack<double> {
+    static constexpr int G = 2;
+    using V = double2;
+    __device__ static void unpack(const V &v, double (&o)[2]) { o[0] = v.x; o[1] = v.y; }
+};
+template <> struct Pack<float> {
+    static constexpr int G = 4;
+    using V = float4;
+    __device__ static void unpack(const V &v, float (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+};
+template <> struct Pack<__nv_bfloat16> {
+    static constexpr int G = 8;
+    using V = uint4;
+    __device__ static void unpack(const V &v, float (&o)[8]) {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            o[2 * k] = __uint_as_float(w[k] << 16);
+            o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
+    }
+};
+template <typename ST> using unpacked_t = typename std::conditional<std::is_same<ST, double>::value, double, float>::type;
+
+// gather the p+1 trace values of the facet and its four neighbours
 template <int P, typename T>
-__device__ __forceinline__ void facet_rows(const T *__restrict__ Sval, const int32_t *__restrict__ nbr,
-                                           const T *__restrict__ x, int e, size_t NF, T (&y)[P + 1]) {
-    constexpr int PP = P + 1;
+__device__ __forceinline__ void gather_x(const int32_t *__restrict__ nbr, const T *__restrict__ x, int e, size_t NF,
+                                         T (&xs)[5][P + 1]) {
     int src[5];
     src[0] = e;
 #pragma unroll
     for (int b = 1; b < 5; ++b) src[b] = __ldg(nbr + size_t(b - 1) * NF + e);
-    T xs[5][PP];
 #pragma unroll
     for (int b = 0; b < 5; ++b)
 #pragma unroll
-        for (int c = 0; c < PP; ++c) xs[b][c] = x[size_t(c) * NF + src[b]];
+        for (int c = 0; c < P + 1; ++c) xs[b][c] = x[size_t(c) * NF + src[b]];
+}
+
+// y_r = sum_{b,c} S[(r*5+b)*PP+c] xs[b][c] with packed loads
+template <int P, typename T, typename ST>
+__device__ __forceinline__ void facet_rows_packed(const ST *__restrict__ Sval, int e, size_t NF,
+                                                  const T (&xs)[5][P + 1], T (&y)[P + 1]) {
+    constexpr int PP = P + 1, NS = 5 * PP * PP, G = Pack<ST>::G, NQ = (NS + G - 1) / G;
+    using V = typename Pack<ST>::V;
+    const V *Sp = reinterpret_cast<const V *>(Sval);
 #pragma unroll
-    for (int r = 0; r < PP; ++r) {
-        T acc = T(0);
+    for (int r = 0; r < PP; ++r) y[r] = T(0);
 #pragma unroll
-        for (int b = 0; b < 5; ++b)
+    for (int q = 0; q < NQ; ++q) {
+        const V v = __ldg(Sp + size_t(q) * NF + e);
+        unpacked_t<ST> o[G];
+        Pack<ST>::unpack(v, o);
 #pragma unroll
-            for (int c = 0; c < PP; ++c) acc = fma(__ldg(Sval + size_t((r * 5 + b) * PP + c) * NF + e), xs[b][c], acc);
-        y[r] = acc;
+        for (int g = 0; g < G; ++g) {
+            constexpr int dummy = 0;
+            (void)dummy;
+            const int j = q * G + g;
+            if (j < NS) {
+                const int r = j / (5 * PP), rem = j % (5 * PP), b = rem / PP, c = rem % PP;
+                y[r] = fma(T(o[g]), xs[b][c], y[r]);
+            }
+        }
     }
 }
 
-template <int P, typename T>
-__global__ void __launch_bounds__(256) apply_kernel(int NF, const T *__restrict__ Sval, const int32_t *__restrict__ nbr,
+// out_r = sum_c Dinv[r*PP+c] v_c with packed loads
+template <int P, typename T, typename DT>
+__device__ __forceinline__ void block_solve_packed(const DT *__restrict__ Dinv, int e, size_t NF, const T (&v)[P + 1],
+                                                   T (&out)[P + 1]) {
+    constexpr int PP = P + 1, ND = PP * PP, G = Pack<DT>::G, NQ = (ND + G - 1) / G;
+    using V = typename Pack<DT>::V;
+    const V *Dp = reinterpret_cast<const V *>(Dinv);
+#pragma unroll
+    for (int r = 0; r < PP; ++r) out[r] = T(0);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const V w = __ldg(Dp + size_t(q) * NF + e);
+        unpacked_t<DT> o[G];
+        Pack<DT>::unpack(w, o);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int j = q * G + g;
+            if (j < ND) out[j / PP] = fma(T(o[g]), v[j % PP], out[j / PP]);
+        }
+    }
+}
+
+template <int P, typename T, typename ST>
+__global__ void __launch_bounds__(256) apply_kernel(int NF, const ST *__restrict__ Sval, const int32_t *__restrict__ nbr,
                                                     const T *__restrict__ x, T *__restrict__ y) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= NF) return;
-    T v[P + 1];
-    facet_rows<P, T>(Sval, nbr, x, e, NF, v);
+    T xs[5][P + 1], v[P + 1];
+    gather_x<P, T>(nbr, x, e, NF, xs);
+    facet_rows_packed<P, T, ST>(Sval, e, NF, xs, v);
 #pragma unroll
     for (int r = 0; r <= P; ++r) y[size_t(r) * NF + e] = v[r];
 }
 
-template <int P, typename T>
-__global__ void __launch_bounds__(256) residual_kernel(int NF, const T *__restrict__ Sval,
+template <int P, typename T, typename ST>
+__global__ void __launch_bounds__(256) residual_kernel(int NF, const ST *__restrict__ Sval,
                                                        const int32_t *__restrict__ nbr, const T *__restrict__ b,
                                                        const T *__restrict__ x, T *__restrict__ res) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= NF) return;
-    T v[P + 1];
-    facet_rows<P, T>(Sval, nbr, x, e, NF, v);
+    T xs[5][P + 1], v[P + 1];
+    gather_x<P, T>(nbr, x, e, NF, xs);
+    facet_rows_packed<P, T, ST>(Sval, e, NF, xs, v);
 #pragma unroll
     for (int r = 0; r <= P; ++r) res[size_t(r) * NF + e] = b[size_t(r) * NF + e] - v[r];
 }
 
-template <int P, typename T>
-__global__ void __launch_bounds__(256) smooth_kernel(int NF, const T *__restrict__ Sval, const T *__restrict__ Dinv,
+template <int P, typename T, typename ST>
+__global__ void __launch_bounds__(256) smooth_kernel(int NF, const ST *__restrict__ Sval, const T *__restrict__ Dinv,
                                                      const int32_t *__restrict__ nbr, const T *__restrict__ b,
                                                      const T *__restrict__ x, T *__restrict__ xout, T omega) {
     constexpr int PP = P + 1;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= NF) return;
-    T v[PP];
-    facet_rows<P, T>(Sval, nbr, x, e, NF, v);
+    T xs[5][PP], v[PP], d[PP];
+    gather_x<P, T>(nbr, x, e, NF, xs);
+    facet_rows_packed<P, T, ST>(Sval, e, NF, xs, v);
 #pragma unroll
     for (int r = 0; r < PP; ++r) v[r] = b[size_t(r) * NF + e] - v[r];
+    block_solve_packed<P, T, T>(Dinv, e, NF, v, d);
 #pragma unroll
-    for (int r = 0; r < PP; ++r) {
-        T acc = T(0);
+    for (int r = 0; r < PP; ++r) xout[size_t(r) * NF + e] = fma(omega, d[r], xs[0][r]);
+}
+
+// First post-smoothing sweep with the coarse correction folded in:
+// x' = x + pi e_c is formed on the fly for the five facets the rows touch,
+// then x_out = x' + omega D_e^-1 (b - S x')_e.
+template <int P, typename T, typename ST>
+__global__ void __launch_bounds__(256) smooth_prolong_kernel(int NF, const ST *__restrict__ Sval,
+                                                             const T *__restrict__ Dinv, const int32_t *__restrict__ nbr,
+                                                             const int32_t *__restrict__ fverts,
+                                                             const T *__restrict__ ec, const T *__restrict__ b,
+                                                             const T *__restrict__ x, T *__restrict__ xout, T omega) {
+    constexpr int PP = P + 1;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= NF) return;
+    int src[5];
+    src[0] = e;
 #pragma unroll
-        for (int c = 0; c < PP; ++c) acc = fma(__ldg(Dinv + size_t(r * PP + c) * NF + e), v[c], acc);
-        xout[size_t(r) * NF + e] = fma(omega, acc, x[size_t(r) * NF + e]);
+    for (int bb = 1; bb < 5; ++bb) src[bb] = __ldg(nbr + size_t(bb - 1) * NF + e);
+    T xs[5][PP], v[PP], d[PP];
+#pragma unroll
+    for (int bb = 0; bb < 5; ++bb) {
+        const T lo = ec[__ldg(fverts + 2 * src[bb])], hi = ec[__ldg(fverts + 2 * src[bb] + 1)];
+#pragma unroll
+        for (int c = 0; c < PP; ++c) {
+            const T t = T(c) / T(P);
+            xs[bb][c] = x[size_t(c) * NF + src[bb]] + (T(1) - t) * lo + t * hi;
+        }
     }
+    facet_rows_packed<P, T, ST>(Sval, e, NF, xs, v);
+#pragma unroll
+    for (int r = 0; r < PP; ++r) v[r] = b[size_t(r) * NF + e] - v[r];
+    block_solve_packed<P, T, T>(Dinv, e, NF, v, d);
+#pragma unroll
+    for (int r = 0; r < PP; ++r) xout[size_t(r) * NF + e] = fma(omega, d[r], xs[0][r]);
 }
 
 // first sweep from a zero initial guess: x = omega D^-1 b
@@ -92,15 +201,29 @@ __global__ void smooth_first_kernel(int NF, const T *__restrict__ Dinv, const T 
     constexpr int PP = P + 1;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= NF) return;
-    T v[PP];
+    T v[PP], d[PP];
 #pragma unroll
     for (int c = 0; c < PP; ++c) v[c] = b[size_t(c) * NF + e];
+    block_solve_packed<P, T, T>(Dinv, e, NF, v, d);
 #pragma unroll
-    for (int r = 0; r < PP; ++r) {
-        T acc = T(0);
+    for (int r = 0; r < PP; ++r) xout[size_t(r) * NF + e] = omega * d[r];
+}
+
+// Repack the FP64 operator (groups of 2) into another storage precision
+// (groups of 16 / sizeof(TO)); padding lanes are zero.
+template <typename TO>
+__global__ void repack_kernel(const double *__restrict__ src, int ns, size_t NF, TO *__restrict__ dst) {
+    constexpr int G = 16 / int(sizeof(TO));
+    const size_t tid = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t nq = (size_t(ns) + G - 1) / G;
+    if (tid >= nq * NF) return;
+    const size_t q = tid / NF, e = tid % NF;
 #pragma unroll
-        for (int c = 0; c < PP; ++c) acc = fma(__ldg(Dinv + size_t(r * PP + c) * NF + e), v[c], acc);
-        xout[size_t(r) * NF + e] = omega * acc;
+    for (int g = 0; g < G; ++g) {
+        const size_t j = q * G + g;
+        double v = 0.0;
+        if (j < size_t(ns)) v = src[((j / 2) * NF + e) * 2 + (j % 2)];
+        dst[(q * NF + e) * G + g] = convert_to<TO>(v);
     }
 }
 
@@ -189,7 +312,8 @@ __global__ void recover_kernel(int N, int NF, const double *__restrict__ Rm, con
 // weights of the linear interpolant (1 - t_r at the lower vertex, t_r at the higher)
 template <int P, typename T>
 __global__ void restrict_kernel(int nv, int NF, const int32_t *__restrict__ v2f_ptr, const int32_t *__restrict__ v2f,
-                                const T *__restrict__ r, T *__restrict__ rc) {
+                                const T *__restrict__ r, T *__restrict__ rc, const T *__restrict__ dinv0, T omega,
+                                T *__restrict__ x0) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     T acc = T(0);
@@ -202,6 +326,8 @@ __global__ void restrict_kernel(int nv, int NF, const int32_t *__restrict__ v2f_
         }
     }
     rc[v] = acc;
+    // first damped Jacobi sweep of the P1 level from zero, fused (x0 may be null)
+    if (x0) x0[v] = omega * dinv0[v] * acc;
 }
 
 // x += pi e_c (linear interpolation along each facet)
@@ -231,44 +357,70 @@ inline unsigned blocks(size_t n, int bs) { return unsigned((n + bs - 1) / bs); }
 
 }  // namespace
 
-template <typename T>
-static const T *sval_of(hdg_handle *h);
-template <>
-const double *sval_of<double>(hdg_handle *h) { return h->d_Sval; }
-template <>
-const float *sval_of<float>(hdg_handle *h) { return h->d_Sval32; }
-template <typename T>
-static const T *dinv_of(hdg_handle *h);
-template <>
-const double *dinv_of<double>(hdg_handle *h) { return h->d_Dinv; }
-template <>
-const float *dinv_of<float>(hdg_handle *h) { return h->d_Dinv32; }
+// operator storage per use: FP64 path, FP32 Krylov operator, and the
+// preconditioner's copy (BF16 in HDG_MIXED_BF16, else the FP32 one)
+template <typename T> struct Ops;
+template <> struct Ops<double> {
+    static const double *S(hdg_handle *h, bool) { return h->d_Sval; }
+    static const double *D(hdg_handle *h) { return h->d_Dinv; }
+};
+template <> struct Ops<float> {
+    static const float *S(hdg_handle *h, bool) { return h->d_Sval32; }
+    static const float *D(hdg_handle *h) { return h->d_Dinv32; }
+};
+inline bool bf16_pre(hdg_handle *h) { return h->prm.precision == HDG_MIXED_BF16 && h->d_Sval16; }
 
 template <typename T>
 cudaError_t launch_apply_t(hdg_handle *h, const T *x, T *y) {
-    HDG_DISPATCH_P(h->p, (apply_kernel<P, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, sval_of<T>(h), h->d_nbr, x, y)));
+    HDG_DISPATCH_P(h->p, (apply_kernel<P, T, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, Ops<T>::S(h, false), h->d_nbr, x, y)));
     return cudaGetLastError();
 }
+// residual / smoothing kernels serve the preconditioner (pre = true) or the
+// Krylov residual (pre = false)
 template <typename T>
-cudaError_t launch_residual_t(hdg_handle *h, const T *b, const T *x, T *r) {
-    HDG_DISPATCH_P(h->p, (residual_kernel<P, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, sval_of<T>(h), h->d_nbr, b, x, r)));
+cudaError_t launch_residual_t(hdg_handle *h, const T *b, const T *x, T *r, bool pre) {
+    if constexpr (std::is_same<T, float>::value) if (pre && bf16_pre(h)) {
+        HDG_DISPATCH_P(h->p, (residual_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, h->d_Sval16, h->d_nbr, b, x, r)));
+        return cudaGetLastError();
+    }
+    {
+        HDG_DISPATCH_P(h->p, (residual_kernel<P, T, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, Ops<T>::S(h, pre), h->d_nbr, b, x, r)));
+    }
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_smooth_t(hdg_handle *h, const T *b, const T *x, T *xout) {
     const T om = T(h->prm.omega);
-    HDG_DISPATCH_P(h->p, (smooth_kernel<P, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, sval_of<T>(h), dinv_of<T>(h), h->d_nbr, b, x, xout, om)));
+    if constexpr (std::is_same<T, float>::value) if (bf16_pre(h)) {
+        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, om)));
+        return cudaGetLastError();
+    }
+    {
+        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, om)));
+    }
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_smooth_first_t(hdg_handle *h, const T *b, T *x) {
     const T om = T(h->prm.omega);
-    HDG_DISPATCH_P(h->p, (smooth_first_kernel<P, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, dinv_of<T>(h), b, x, om)));
+    HDG_DISPATCH_P(h->p, (smooth_first_kernel<P, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, Ops<T>::D(h), b, x, om)));
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_restrict_t(hdg_handle *h, const T *r, T *rc) {
-    HDG_DISPATCH_P(h->p, (restrict_kernel<P, T><<<blocks(h->nv, 256), 256, 0, h->stream>>>(h->nv, h->NF, h->d_v2f_ptr, h->d_v2f, r, rc)));
+cudaError_t launch_restrict_t(hdg_handle *h, const T *r, T *rc, const T *dinv0, T omega, T *x0) {
+    HDG_DISPATCH_P(h->p, (restrict_kernel<P, T><<<blocks(h->nv, 256), 256, 0, h->stream>>>(h->nv, h->NF, h->d_v2f_ptr, h->d_v2f, r, rc, dinv0, omega, x0)));
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_smooth_prolong_t(hdg_handle *h, const T *ec, const T *b, const T *x, T *xout) {
+    const T om = T(h->prm.omega);
+    if constexpr (std::is_same<T, float>::value) if (bf16_pre(h)) {
+        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om)));
+        return cudaGetLastError();
+    }
+    {
+        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om)));
+    }
     return cudaGetLastError();
 }
 template <typename T>
@@ -277,16 +429,32 @@ cudaError_t launch_prolong_add_t(hdg_handle *h, const T *ec, T *x) {
     return cudaGetLastError();
 }
 
+// FP32 / BF16 copies of the packed FP64 operator and the FP32 inverse blocks
+cudaError_t launch_repack(hdg_handle *h) {
+    const int pp = h->pp, ns = 5 * pp * pp, nd = pp * pp;
+    const size_t NF = h->NF;
+    auto nq = [&](int n, int G) { return (size_t(n) + G - 1) / G * NF; };
+    if (h->d_Sval32) {
+        repack_kernel<float><<<blocks(nq(ns, 4), 256), 256, 0, h->stream>>>(h->d_Sval, ns, NF, h->d_Sval32);
+        repack_kernel<float><<<blocks(nq(nd, 4), 256), 256, 0, h->stream>>>(h->d_Dinv, nd, NF, h->d_Dinv32);
+    }
+    if (h->d_Sval16)
+        repack_kernel<__nv_bfloat16><<<blocks(nq(ns, 8), 256), 256, 0, h->stream>>>(h->d_Sval, ns, NF, h->d_Sval16);
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_apply_t<double>(hdg_handle *, const double *, double *);
 template cudaError_t launch_apply_t<float>(hdg_handle *, const float *, float *);
-template cudaError_t launch_residual_t<double>(hdg_handle *, const double *, const double *, double *);
-template cudaError_t launch_residual_t<float>(hdg_handle *, const float *, const float *, float *);
+template cudaError_t launch_residual_t<double>(hdg_handle *, const double *, const double *, double *, bool);
+template cudaError_t launch_residual_t<float>(hdg_handle *, const float *, const float *, float *, bool);
 template cudaError_t launch_smooth_t<double>(hdg_handle *, const double *, const double *, double *);
 template cudaError_t launch_smooth_t<float>(hdg_handle *, const float *, const float *, float *);
 template cudaError_t launch_smooth_first_t<double>(hdg_handle *, const double *, double *);
 template cudaError_t launch_smooth_first_t<float>(hdg_handle *, const float *, float *);
-template cudaError_t launch_restrict_t<double>(hdg_handle *, const double *, double *);
-template cudaError_t launch_restrict_t<float>(hdg_handle *, const float *, float *);
+template cudaError_t launch_restrict_t<double>(hdg_handle *, const double *, double *, const double *, double, double *);
+template cudaError_t launch_restrict_t<float>(hdg_handle *, const float *, float *, const float *, float, float *);
+template cudaError_t launch_smooth_prolong_t<double>(hdg_handle *, const double *, const double *, const double *, double *);
+template cudaError_t launch_smooth_prolong_t<float>(hdg_handle *, const float *, const float *, const float *, float *);
 template cudaError_t launch_prolong_add_t<double>(hdg_handle *, const double *, double *);
 template cudaError_t launch_prolong_add_t<float>(hdg_handle *, const float *, float *);
 

@@ -168,14 +168,15 @@ def test_device_entry_points_match_host_ones():
     s.close()
 
 
-@pytest.mark.parametrize("kind,p", [("flat", 2), ("sphere", 3)])
-def test_mixed_precision(kind, p):
-    """FP32 inner FGMRES + FP32 V-cycle with FP64 iterative refinement reaches the
-    FP64 residual target; stated tolerance vs the oracle: 1e-8 relative at
-    rtol 1e-10 (the trace operator's condition number here is < 100)."""
-    from paper_2004_09389_gb300 import HDG_MIXED_FP32
+@pytest.mark.parametrize("kind,p", [("flat", 2), ("sphere", 3), ("flat", 4), ("flat", 1)])
+@pytest.mark.parametrize("mode", [1, 2])
+def test_mixed_precision(kind, p, mode):
+    """FP32 inner FGMRES + FP32 V-cycle (mode 1) or with a BF16 operator copy in
+    the smoother and V-cycle residual (mode 2), with FP64 iterative refinement,
+    reaches the FP64 residual target; stated tolerance vs the oracle: 1e-8
+    relative at rtol 1e-10 (the trace operator's condition number here is < 100)."""
     mesh, prob, (tau, g, H, f), ru, rh = _case(kind, p)
-    s = _solver(mesh, p, tau, g, H, f, rtol=1e-10, precision=HDG_MIXED_FP32)
+    s = _solver(mesh, p, tau, g, H, f, rtol=1e-10, precision=mode)
     lam, info = s.solve(ru, rh)
     u, h = s.recover()
     (u0, h0), lam0 = prob.solve_condensed(ru, rh)
