@@ -87,7 +87,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={CLOCK_QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -187,7 +187,9 @@ def gpu_arm(args, rank: int, world: int):
     ru_d = torch.from_numpy(ru).to(dev)
     rh_d = torch.from_numpy(rh).to(dev)
     out = {}
-    for arm, prec in (("mixed", HDG_MIXED_FP32), ("mixed_bf16", HDG_MIXED_BF16), ("fp64", HDG_FP64)):
+    arms = [(a, p) for a, p in (("mixed", HDG_MIXED_FP32), ("mixed_bf16", HDG_MIXED_BF16), ("fp64", HDG_FP64))
+            if a in args.arms.split(",")]
+    for arm, prec in arms:
         s = HDGSolver(mesh, args.p, tau, G, DEPTH, f_vertex=f, rtol=args.rtol, precision=prec,
                       inner_rtol=args.inner_rtol, restart=args.restart)
         NF, pp = s.n_facets, args.p + 1
@@ -293,7 +295,7 @@ def source_sha() -> str:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--p", type=int, default=3)
@@ -304,6 +306,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--oracle-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--arms", default="mixed,mixed_bf16,fp64",
+                    help="solver arms to run (profiling runs may pick one)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
 
@@ -341,6 +345,11 @@ def main():
         cpu = cpu_baseline_entry(args.p, args.courant, args.oracle_steps)
     res = gpu_arm(args, rank, world)
     if rank != 0:
+        return
+    if set(res) != {"mixed", "mixed_bf16", "fp64"}:
+        # partial run (profiling): a short summary, not a bench line
+        print(json.dumps({k: {"ms_per_step": v["ms"] / args.steps, "iters": [i["iters"] for i in v["infos"]]}
+                          for k, v in res.items()}))
         return
     peaks = {}
     ppath = os.path.join(ROOT, "MEASURED_PEAKS.json")

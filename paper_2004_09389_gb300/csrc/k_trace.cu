@@ -118,8 +118,13 @@ __device__ __forceinline__ void block_solve_packed(const DT *__restrict__ Dinv, 
     }
 }
 
+// FP32 facet-row kernels are bound by memory latency: cap registers so six
+// 256-thread blocks fit per SM (one wave over the facets of large meshes);
+// FP64 ones are bound by the FP64 pipe and keep their registers.
+template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 6 : 1; };
+
 template <int P, typename T, typename ST>
-__global__ void __launch_bounds__(256) apply_kernel(int NF, const ST *__restrict__ Sval, const int32_t *__restrict__ nbr,
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) apply_kernel(int NF, const ST *__restrict__ Sval, const int32_t *__restrict__ nbr,
                                                     const T *__restrict__ x, T *__restrict__ y) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= NF) return;
@@ -131,7 +136,7 @@ __global__ void __launch_bounds__(256) apply_kernel(int NF, const ST *__restrict
 }
 
 template <int P, typename T, typename ST>
-__global__ void __launch_bounds__(256) residual_kernel(int NF, const ST *__restrict__ Sval,
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) residual_kernel(int NF, const ST *__restrict__ Sval,
                                                        const int32_t *__restrict__ nbr, const T *__restrict__ b,
                                                        const T *__restrict__ x, T *__restrict__ res) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,7 +149,7 @@ __global__ void __launch_bounds__(256) residual_kernel(int NF, const ST *__restr
 }
 
 template <int P, typename T, typename ST>
-__global__ void __launch_bounds__(256) smooth_kernel(int NF, const ST *__restrict__ Sval, const T *__restrict__ Dinv,
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_kernel(int NF, const ST *__restrict__ Sval, const T *__restrict__ Dinv,
                                                      const int32_t *__restrict__ nbr, const T *__restrict__ b,
                                                      const T *__restrict__ x, T *__restrict__ xout, T omega) {
     constexpr int PP = P + 1;
@@ -164,7 +169,7 @@ __global__ void __launch_bounds__(256) smooth_kernel(int NF, const ST *__restric
 // x' = x + pi e_c is formed on the fly for the five facets the rows touch,
 // then x_out = x' + omega D_e^-1 (b - S x')_e.
 template <int P, typename T, typename ST>
-__global__ void __launch_bounds__(256) smooth_prolong_kernel(int NF, const ST *__restrict__ Sval,
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_prolong_kernel(int NF, const ST *__restrict__ Sval,
                                                              const T *__restrict__ Dinv, const int32_t *__restrict__ nbr,
                                                              const int32_t *__restrict__ fverts,
                                                              const T *__restrict__ ec, const T *__restrict__ b,
