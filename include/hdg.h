@@ -114,6 +114,13 @@ typedef struct {
     int32_t       p1_nu_pre, p1_nu_post; /* Jacobi sweeps per level of the P1 V-cycle     */
     double        p1_omega;     /* Jacobi damping of the P1 V-cycle                       */
     double        inner_rtol;   /* mixed modes: relative tolerance of each inner solve   */
+    int32_t       coarse_mode;  /* P1 coarse operator (Sec. 4.4 recipe: eliminate u from the
+                                   time-implicit continuum equations, divided by tau):
+                                   0 = with the implicit Coriolis term, per cell
+                                       (phi,psi) + tau^2 g H kappa_K [(grad phi,grad psi)
+                                       - tau f_K (J grad phi,grad psi)], kappa_K = 1/(1+tau^2 f_K^2);
+                                   1 = as printed in Eq. coarse_problem_upwind (no rotation).
+                                   Both agree when f = 0.                                  */
 } hdg_params;
 
 typedef struct {
@@ -127,7 +134,7 @@ typedef struct {
 
 /* Fill *prm with the defaults: p = 1, tau = 1, g = H = 1, tau_s = sqrt(gH),
  * FP64, rtol 1e-8, restart 30, max_iter 500, 2 + 2 sweeps, omega = 2/3,
- * 2 + 2 P1 sweeps, p1_omega = 2/3, inner_rtol 1e-4. */
+ * 2 + 2 P1 sweeps, p1_omega = 2/3, inner_rtol 1e-4, coarse_mode 0. */
 HDG_API void hdg_default_params(hdg_params *prm);
 
 /* Build a handle: validate and copy the mesh (facet numbering, orientation,
@@ -165,6 +172,27 @@ HDG_API int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, con
                 double *u, double *h_out);
 HDG_API int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h, const double *lambda,
                     double *u, double *h_out);
+
+/* Many independent solves at once: handle i solves r_u[i], r_h[i] into
+ * lambda[i] (device pointers), as hdg_solve_dev would, while the others run
+ * concurrently on their own streams (the handles must be distinct and have
+ * distinct streams).  n_threads host threads (<= 0: up to 16) drive the
+ * solves; every Arnoldi step is a replayed CUDA graph.  infos (may be NULL)
+ * gets one entry per handle; the return value is the first non-OK status in
+ * handle order.  Like hdg_solve_dev, results are complete once each handle's
+ * stream has been synchronised.  (North-star batching; the paper solves one
+ * system at a time.) */
+HDG_API int hdg_solve_batch_dev(hdg_handle *const *hs, int n, const double *const *r_u, const double *const *r_h,
+                                double *const *lambda, hdg_solve_info *infos, int n_threads);
+
+/* Pick launch shapes for this handle by timing one Arnoldi step (preconditioner,
+ * operator application, Gram-Schmidt) for each candidate: threads per block of
+ * the facet-row kernels (64 / 128 / 256), blocks of the fused Gram-Schmidt
+ * kernels (152 / 304 / 608) and the largest level of the single-CTA coarse
+ * cycle (256 / 1024 / 4096 vertices), one parameter at a time.  Needs
+ * hdg_condense.  choice[0..2] (may be NULL) receives the three picks.  Results
+ * do not depend on the choice beyond floating-point summation order. */
+HDG_API int hdg_autotune(hdg_handle *h, int32_t *choice);
 
 /* Operator entry points on device vectors in the lambda layout [n_facets][p+1]. */
 /* y = S x, S the assembled trace operator of Eq. schur_system. */
@@ -223,6 +251,10 @@ HDG_API int hdg_get_cell_schur(hdg_handle *h, double *S);
 #define HDG_PROF_N             15
 HDG_API int hdg_profile_enable(hdg_handle *h, int timing_on);
 HDG_API int hdg_profile_read(hdg_handle *h, double *ms, int64_t *launches);
+
+/* The CUDA stream (cudaStream_t) the handle runs on: the one given to
+ * hdg_setup, or the non-blocking stream the handle created and owns. */
+HDG_API void *hdg_get_stream(const hdg_handle *h);
 
 HDG_API int hdg_destroy(hdg_handle *h);
 HDG_API const char *hdg_last_error(const hdg_handle *h);

@@ -10,11 +10,19 @@ Test infrastructure only (see the package docstring).
   n_pre damped block-Jacobi sweeps on the facet blocks, residual, restriction
   ``r_c = pi^T r`` (pi = the natural injection of P1 into the trace space,
   Sec. 4.4, upwind), coarse solve, ``x += pi e_c``, n_post sweeps.
-* Coarse problem (Eq. coarse_problem_upwind), dimensional form
-  ``S_c(phi, psi) = (phi, psi) + tau^2 g H (grad phi, grad psi)`` divided by
-  tau (the scale at which the trace operator acts on smooth traces, from the
-  energy identity ``x^T S+ x = (1/tau)(||h||^2 + (H/g)||u||^2) + ...``), or
-  the Galerkin choice ``pi^T S+ pi`` of the footnote in Sec. 4.4.  It is
+* Coarse problem: the weak form of the second-order problem that the
+  time-implicit continuum equations give after eliminating u (the recipe of
+  Sec. 4.4, Eq. coarse_problem_upwind), divided by tau (the scale at which the
+  trace operator acts on smooth traces, from the energy identity
+  ``x^T S+ x = (1/tau)(||h||^2 + (H/g)||u||^2) + ...``).  With the Coriolis
+  term implicit, u = (I - tau f J)(r_u - tau g grad h) / (1 + tau^2 f^2)
+  (J the rotation by 90 degrees), so per cell K with f_K the mean of f:
+      S_c(phi, psi) = (phi, psi) + tau^2 g H kappa_K [(grad phi, grad psi)_K
+                                                     - tau f_K (J grad phi, grad psi)_K],
+      kappa_K = 1 / (1 + tau^2 f_K^2)                      ("rotating", default)
+  which is exactly Eq. coarse_problem_upwind when f = 0; or the paper's form
+  without rotation ("rediscretised"); or the Galerkin choice pi^T S+ pi of
+  the footnote in Sec. 4.4 ("galerkin").  It is
   solved exactly (sparse LU) or by a geometric P1 V-cycle over the nested
   coarse meshes (damped Jacobi smoothing, rediscretised level operators,
   sparse LU on the coarsest level).
@@ -85,6 +93,38 @@ def gmres(apply_A, b: np.ndarray, precond=None, restart: int = 30, rtol: float =
 
 
 # ------------------------------------------------------------------ P1 spaces
+
+def p1_rotating_operator(md: MeshData, f_vertex: np.ndarray, tau: float, g: float, H: float) -> sp.csr_matrix:
+    """Coarse operator with implicit rotation (module docstring), divided by tau."""
+    X = local_coordinates(md)
+    nv = md.vertex_xyz.shape[0]
+    gref = np.array([[-1.0, -1.0], [1.0, 0.0], [0.0, 1.0]])
+    Jrot = np.array([[0.0, -1.0], [1.0, 0.0]])          # u_perp = J u
+    rows, cols, vals = [], [], []
+    for K in range(md.n_cells):
+        detJ, Jit, _, _ = cell_geometry(X[K])
+        G = gref @ Jit.T                                 # row a = grad L_a
+        fK = f_vertex[md.cell_vertices[K]].mean()
+        kap = 1.0 / (1.0 + (tau * fK) ** 2)
+        Me = detJ / 24.0 * (np.ones((3, 3)) + np.eye(3))
+        Ke = 0.5 * detJ * G @ G.T                       # (grad L_b, grad L_a) at [a, b]
+        Se = 0.5 * detJ * G @ (G @ Jrot.T).T            # (J grad L_b, grad L_a) at [a, b]
+        Ae = (Me + tau * tau * g * H * kap * (Ke - tau * fK * Se)) / tau
+        vv = md.cell_vertices[K]
+        rr, cc = np.meshgrid(vv, vv, indexing="ij")
+        rows.append(rr.ravel()); cols.append(cc.ravel()); vals.append(Ae.ravel())
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(nv, nv))
+
+
+def coarse_vertex_values(fine_values: np.ndarray, parent: np.ndarray, n_coarse: int) -> np.ndarray:
+    """Values at the vertices of a coarser level, taken from the finer-level
+    vertex that coincides with each (parent pair (a, a))."""
+    out = np.empty(n_coarse)
+    for i, (a, b) in enumerate(parent):
+        if a == b:
+            out[a] = fine_values[i]
+    return out
+
 
 def p1_matrices(md: MeshData):
     """Assembled P1 mass and stiffness matrices on a (flat or sphere) mesh."""
@@ -158,7 +198,7 @@ class P1Multigrid:
 
 class TwoLevelPreconditioner:
     def __init__(self, prob: HDGProblem, mesh, S: sp.csr_matrix, n_pre: int = 2, n_post: int = 2,
-                 omega: float = 2.0 / 3.0, coarse: str = "gmg", coarse_mode: str = "rediscretised",
+                 omega: float = 2.0 / 3.0, coarse: str = "gmg", coarse_mode: str = "rotating",
                  p1_nu: tuple = (2, 2), p1_omega: float = 2.0 / 3.0):
         self.prob, self.S = prob, S
         self.n_pre, self.n_post, self.omega = n_pre, n_post, omega
@@ -174,7 +214,15 @@ class TwoLevelPreconditioner:
         self.Pi = injection(prob, nv)
         tau, g, H = prob.prm.tau, prob.prm.g, prob.prm.H
         levels = [mesh] + list(mesh.levels)
-        if coarse_mode == "rediscretised":
+        if coarse_mode == "rotating":
+            # f on the coarse levels by injection through the parent maps
+            ops = []
+            fv = prob.f_vertex
+            for li, lev in enumerate(levels):
+                if li > 0:
+                    fv = coarse_vertex_values(fv, lev.parent, lev.n_vertices)
+                ops.append(p1_rotating_operator(MeshData.of(lev), fv, tau, g, H).tocsr())
+        elif coarse_mode == "rediscretised":
             ops = []
             for lev in levels:
                 Mm, Km = p1_matrices(MeshData.of(lev))

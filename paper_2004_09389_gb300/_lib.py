@@ -39,7 +39,7 @@ class hdg_params(C.Structure):
                 ("tau_s", C.c_double), ("f_vertex", _dp), ("precision", C.c_int32), ("rtol", C.c_double),
                 ("restart", C.c_int32), ("max_iter", C.c_int32), ("n_pre", C.c_int32), ("n_post", C.c_int32),
                 ("omega", C.c_double), ("p1_nu_pre", C.c_int32), ("p1_nu_post", C.c_int32),
-                ("p1_omega", C.c_double), ("inner_rtol", C.c_double)]
+                ("p1_omega", C.c_double), ("inner_rtol", C.c_double), ("coarse_mode", C.c_int32)]
 
 
 class hdg_solve_info(C.Structure):
@@ -60,7 +60,8 @@ _LIB = None
 EXPORTS = ["hdg_default_params", "hdg_setup", "hdg_condense", "hdg_set_tau", "hdg_solve", "hdg_solve_dev",
            "hdg_recover", "hdg_recover_dev", "hdg_trace_apply_dev", "hdg_condensed_rhs_dev",
            "hdg_precond_apply_dev", "hdg_get_sizes", "hdg_get_facets", "hdg_get_cell_schur", "hdg_destroy",
-           "hdg_last_error", "hdg_profile_enable", "hdg_profile_read", "hdg_condensed_rhs_noalloc_dev"]
+           "hdg_last_error", "hdg_profile_enable", "hdg_profile_read", "hdg_condensed_rhs_noalloc_dev",
+           "hdg_solve_batch_dev", "hdg_autotune", "hdg_get_stream"]
 
 HDG_PROF_N = 15
 PROF_NAMES = ["apply64", "residual64", "smooth64", "smooth_first64", "apply32", "residual32", "smooth32",
@@ -93,12 +94,16 @@ def load() -> C.CDLL:
     lib.hdg_get_sizes.argtypes = [vp, C.POINTER(C.c_int64)]
     lib.hdg_get_facets.argtypes = [vp, vp, vp, vp]
     lib.hdg_get_cell_schur.argtypes = [vp, vp]
+    lib.hdg_solve_batch_dev.argtypes = [vp, C.c_int, vp, vp, vp, C.POINTER(hdg_solve_info), C.c_int]
+    lib.hdg_autotune.argtypes = [vp, vp]
+    lib.hdg_get_stream.argtypes = [vp]
+    lib.hdg_get_stream.restype = vp
     lib.hdg_profile_enable.argtypes = [vp, C.c_int]
     lib.hdg_profile_read.argtypes = [vp, vp, vp]
     lib.hdg_last_error.argtypes = [vp]
     lib.hdg_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("hdg_default_params", "hdg_last_error"):
+        if name not in ("hdg_default_params", "hdg_last_error", "hdg_get_stream"):
             getattr(lib, name).restype = C.c_int
     _LIB = lib
     return lib

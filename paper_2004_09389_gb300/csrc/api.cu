@@ -13,6 +13,8 @@
 #include "common.h"
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -116,6 +118,7 @@ std::string check_params(const hdg_params *prm) {
     if (prm->max_iter < 1) return "max_iter must be positive";
     if (prm->n_pre < 0 || prm->n_post < 0 || prm->p1_nu_pre < 0 || prm->p1_nu_post < 0) return "negative sweep count";
     if (!(prm->omega > 0) || !(prm->p1_omega > 0)) return "damping factors must be positive";
+    if (prm->coarse_mode != 0 && prm->coarse_mode != 1) return "coarse_mode must be 0 or 1";
     if (prm->precision != HDG_FP64 && prm->precision != HDG_MIXED_FP32 && prm->precision != HDG_MIXED_BF16)
         return "unknown precision mode";
     if (prm->precision != HDG_FP64 && !(prm->inner_rtol > 0 && prm->inner_rtol < 1)) return "inner_rtol must be in (0, 1)";
@@ -605,7 +608,7 @@ void free_handle(hdg_handle *h) {
     dfree(h->d_Dinv); dfree(h->d_Sval32); dfree(h->d_Dinv32); dfree(h->d_Sval16); dfree(h->d_status); dfree(h->d_coarse_inv);
     dfree(h->d_coarse_inv32); dfree(h->d_coarse_work);
     for (auto &L : h->lev) {
-        dfree(L.row_ptr); dfree(L.col); dfree(L.diag); dfree(L.mass); dfree(L.stiff); dfree(L.A); dfree(L.dinv);
+        dfree(L.row_ptr); dfree(L.col); dfree(L.diag); dfree(L.elem); dfree(L.fK); dfree(L.contrib_ptr); dfree(L.contrib); dfree(L.A); dfree(L.dinv);
         dfree(L.A32); dfree(L.dinv32); dfree(L.parent); dfree(L.child_ptr); dfree(L.child_idx); dfree(L.child_w); dfree(L.child_w32);
         dfree(L.x); dfree(L.x2); dfree(L.b); dfree(L.r); dfree(L.x32); dfree(L.x232); dfree(L.b32); dfree(L.r32);
     }
@@ -629,6 +632,33 @@ void free_handle(hdg_handle *h) {
     }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
+}
+
+// First level of the single-CTA coarse cycle, per precision: the largest
+// suffix of P1 levels whose levels have at most tail_max vertices and whose
+// operators, transfers and vectors fit in one CTA's shared memory.
+int set_tail_start(hdg_handle *h, int tail_max) {
+    const int nlev = int(h->lev.size());
+    for (int pi = 0; pi < 2; ++pi) {
+        const size_t tsz = pi == 0 ? sizeof(double) : sizeof(float);
+        int ts = nlev - 1;
+        while (ts > 0 && h->lev[ts - 1].nv <= tail_max && nlev - (ts - 1) <= kTailMaxLevels &&
+               tail_smem_bytes(h->lev, ts - 1, tsz) <= size_t(220) * 1024)
+            --ts;
+        if (tail_smem_bytes(h->lev, ts, tsz) > kTailSmemMax)
+            return fail(h, HDG_EINVAL, "coarsest P1 level too large for the single-CTA coarse cycle");
+        h->tail_start[pi] = ts;
+    }
+    return HDG_OK;
+}
+
+void drop_graphs(hdg_handle *h) {
+    for (auto &gv : h->ws->graphs)
+        for (auto &G : gv)
+            if (G.exec) {
+                cudaGraphExecDestroy(G.exec);
+                G.exec = nullptr;
+            }
 }
 
 int setup_device(hdg_handle *h, const hdg_params *prm) {
@@ -665,17 +695,42 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
         TRY(dalloc(&h->d_Dinv32, packed(pp * pp, 4)));
         if (prm->precision == HDG_MIXED_BF16) TRY(dalloc(&h->d_Sval16, packed(5 * pp * pp, 8)));
     }
+    // Coriolis parameter per cell (mean of its vertices) on every P1 level; on a
+    // coarser level a vertex takes the value of the finer-level vertex that
+    // coincides with it (parent pair (a, a))
+    std::vector<std::vector<double>> lev_fK(hm.levels.size());
+    {
+        std::vector<double> fv(size_t(h->nv), 0.0);
+        if (prm->f_vertex) fv.assign(prm->f_vertex, prm->f_vertex + h->nv);
+        for (size_t l = 0; l < hm.levels.size(); ++l) {
+            const HostLevel &hl = hm.levels[l];
+            if (l > 0) {
+                std::vector<double> fc(size_t(hl.nv), 0.0);
+                for (size_t i = 0; i + 1 < hl.parent.size(); i += 2)
+                    if (hl.parent[i] == hl.parent[i + 1]) fc[hl.parent[i]] = fv[i / 2];
+                fv.swap(fc);
+            }
+            lev_fK[l].resize(size_t(hl.nc));
+            for (int K = 0; K < hl.nc; ++K)
+                lev_fK[l][K] = (fv[hl.cells[3 * K]] + fv[hl.cells[3 * K + 1]] + fv[hl.cells[3 * K + 2]]) / 3.0;
+        }
+    }
     h->lev.resize(hm.levels.size());
     for (size_t l = 0; l < hm.levels.size(); ++l) {
         const HostLevel &hl = hm.levels[l];
         DevLevel &L = h->lev[l];
         L.nv = hl.nv;
         L.nnz = int(hl.col.size());
+        if (L.nnz == 0 || int(hl.diag.size()) != L.nv) return fail(h, HDG_EINVAL, "empty P1 level operator");
+        for (int v = 0; v < L.nv; ++v)
+            if (hl.diag[v] < 0) return fail(h, HDG_EINVAL, "P1 vertex without a cell");
         TRY(upload(&L.row_ptr, hl.row_ptr, s));
         TRY(upload(&L.col, hl.col, s));
         TRY(upload(&L.diag, hl.diag, s));
-        TRY(upload(&L.mass, hl.mass, s));
-        TRY(upload(&L.stiff, hl.stiff, s));
+        TRY(upload(&L.elem, hl.elem, s));
+        TRY(upload(&L.contrib_ptr, hl.contrib_ptr, s));
+        TRY(upload(&L.contrib, hl.contrib, s));
+        TRY(upload(&L.fK, lev_fK[l], s));
         TRY(dalloc(&L.A, size_t(L.nnz)));
         TRY(dalloc(&L.dinv, size_t(L.nv)));
         if (l > 0) {
@@ -700,22 +755,11 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
             TRY(dalloc(&L.r32, size_t(L.nv)));
         }
     }
-    // first level of the single-CTA tail, per precision: small enough to stage
-    // every tail level (operator, transfers, four vectors) in shared memory
     {
         int tail_max = kTailMaxVertices;
         if (const char *ev = std::getenv("HDG_TAIL_MAX_VERTICES")) tail_max = std::max(16, std::min(4096, std::atoi(ev)));
-        const int nlev = int(h->lev.size());
-        for (int pi = 0; pi < 2; ++pi) {
-            const size_t tsz = pi == 0 ? sizeof(double) : sizeof(float);
-            int ts = nlev - 1;
-            while (ts > 0 && h->lev[ts - 1].nv <= tail_max && nlev - (ts - 1) <= kTailMaxLevels &&
-                   tail_smem_bytes(h->lev, ts - 1, tsz) <= size_t(220) * 1024)
-                --ts;
-            if (tail_smem_bytes(h->lev, ts, tsz) > size_t(226) * 1024)
-                return fail(h, HDG_EINVAL, "coarsest P1 level too large for the single-CTA coarse cycle");
-            h->tail_start[pi] = ts;
-        }
+        int rc = set_tail_start(h, tail_max);
+        if (rc) return rc;
     }
     const size_t nc = h->lev.back().nv;
     TRY(dalloc(&h->d_coarse_inv, nc * nc));
@@ -859,6 +903,7 @@ void hdg_default_params(hdg_params *prm) {
     prm->p1_nu_post = 2;
     prm->p1_omega = 2.0 / 3.0;
     prm->inner_rtol = 1e-4;
+    prm->coarse_mode = 0;
 }
 
 int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hdg_handle **out) {
@@ -912,8 +957,9 @@ int hdg_condense(hdg_handle *h) {
     TRY(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), s));
     TRY(KL(HDG_PROF_CONDENSE, 1, launch_condense(h)));
     TRY(KL(HDG_PROF_CONDENSE, 1, launch_assemble(h)));
-    const double tau = h->prm.tau, ctau2 = tau * tau * h->prm.g * h->prm.H;
-    for (auto &L : h->lev) TRY(KL(HDG_PROF_CONDENSE, 1, launch_p1_combine(h, L, tau, ctau2)));
+    const double tau = h->prm.tau, gH = h->prm.g * h->prm.H;
+    for (auto &L : h->lev)
+        TRY(KL(HDG_PROF_CONDENSE, 2, launch_p1_assemble(h, L, tau, gH, h->prm.coarse_mode == 0 ? 1 : 0)));
     const DevLevel &Lc = h->lev.back();
     TRY(KL(HDG_PROF_CONDENSE, 2, launch_dense_inverse(h, Lc, h->d_coarse_work, h->d_coarse_inv, Lc.nv)));
     if (h->prm.precision != HDG_FP64) {
@@ -1103,6 +1149,122 @@ int hdg_profile_read(hdg_handle *h, double *ms, int64_t *launches) {
     }
     return HDG_OK;
 }
+
+int hdg_autotune(hdg_handle *h, int32_t *choice) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    Workspace &W = *h->ws;
+    cudaStream_t s = h->stream;
+    const bool f32 = h->prm.precision != HDG_FP64;
+    const size_t ld = W.ld;
+    const int jt = std::min(4, W.m - 1);
+    // basis vectors with arbitrary finite content for timing
+    if (f32) {
+        TRY(launch_fill<float>(W.k32.V, 1.0f, ld * size_t(jt + 2), s));
+    } else {
+        TRY(launch_fill<double>(W.k64.V, 1.0, ld * size_t(jt + 2), s));
+    }
+    const bool was_on = h->prof.on;
+    h->prof.on = false;
+    cudaEvent_t e0, e1;
+    TRY(cudaEventCreate(&e0));
+    TRY(cudaEventCreate(&e1));
+    // time of one Arnoldi step (preconditioner, operator, Gram-Schmidt), best of 3
+    auto time_step = [&](float &best) -> int {
+        best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            TRY(cudaEventRecord(e0, s));
+            cudaError_t e = f32 ? arnoldi_step<float>(h, jt) : arnoldi_step<double>(h, jt);
+            if (e != cudaSuccess) return fail(h, HDG_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+            TRY(cudaEventRecord(e1, s));
+            TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) best = std::min(best, ms);
+        }
+        return HDG_OK;
+    };
+    float t;
+    // threads per block of the facet-row kernels
+    int best_bs = h->bs_facet;
+    float best_t = 1e30f;
+    for (int bs : {64, 128, 256}) {
+        h->bs_facet = bs;
+        if ((rc = time_step(t))) return rc;
+        if (t < best_t) { best_t = t; best_bs = bs; }
+    }
+    h->bs_facet = best_bs;
+    // blocks of the fused Gram-Schmidt kernels
+    int best_nb = W.nblk_gs;
+    best_t = 1e30f;
+    for (int nb : {152, 304, 608}) {
+        W.nblk_gs = nb;
+        if ((rc = time_step(t))) return rc;
+        if (t < best_t) { best_t = t; best_nb = nb; }
+    }
+    W.nblk_gs = best_nb;
+    // first level of the single-CTA coarse cycle
+    int best_tm = kTailMaxVertices;
+    best_t = 1e30f;
+    int last_ts = -1;
+    for (int tm : {256, 1024, 4096}) {
+        if ((rc = set_tail_start(h, tm))) return rc;
+        const int ts = h->tail_start[f32 ? 1 : 0];
+        if (ts == last_ts) continue;
+        last_ts = ts;
+        if ((rc = time_step(t))) return rc;
+        if (t < best_t) { best_t = t; best_tm = tm; }
+    }
+    if ((rc = set_tail_start(h, best_tm))) return rc;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->prof.on = was_on;
+    drop_graphs(h);
+    if (choice) {
+        choice[0] = h->bs_facet;
+        choice[1] = W.nblk_gs;
+        choice[2] = h->lev[h->tail_start[f32 ? 1 : 0]].nv;
+    }
+    return HDG_OK;
+}
+
+int hdg_solve_batch_dev(hdg_handle *const *hs, int n, const double *const *r_u, const double *const *r_h,
+                        double *const *lambda, hdg_solve_info *infos, int n_threads) {
+    if (n < 0 || (n > 0 && (!hs || !r_u || !r_h || !lambda))) return fail(nullptr, HDG_EINVAL, "bad batch arguments");
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i]) return fail(nullptr, HDG_EINVAL, "NULL handle in the batch");
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i] || hs[j]->stream == hs[i]->stream)
+                return fail(nullptr, HDG_EINVAL, "batch handles must be distinct and use distinct streams");
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, HDG_ECUDA, "cudaGetDevice failed");
+    const int nt = std::max(1, std::min(n_threads > 0 ? n_threads : 16, n));
+    std::atomic<int> next(0);
+    std::vector<int> rcs(size_t(std::max(n, 1)), HDG_OK);
+    auto worker = [&]() {
+        cudaSetDevice(dev);
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= n) break;
+            hdg_solve_info info{};
+            rcs[i] = hdg_solve_dev(hs[i], r_u[i], r_h[i], lambda[i], &info);
+            if (infos) infos[i] = info;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t2 = 1; t2 < nt; ++t2) pool.emplace_back(worker);
+    worker();
+    for (auto &th : pool) th.join();
+    for (int i = 0; i < n; ++i)
+        if (rcs[i] != HDG_OK) {
+            g_setup_error = "batch entry " + std::to_string(i) + ": " + hs[i]->err;
+            return rcs[i];
+        }
+    return HDG_OK;
+}
+
+void *hdg_get_stream(const hdg_handle *h) { return h ? static_cast<void *>(h->stream) : nullptr; }
 
 int hdg_destroy(hdg_handle *h) {
     free_handle(h);

@@ -49,9 +49,11 @@ struct HostLevel {
     int nv = 0, nc = 0;
     std::vector<double> X;        // [nc][3][2] local 2-D vertex coordinates
     std::vector<int32_t> cells;   // [nc][3]
-    // geometric P1 matrices, CSR with sorted columns
+    // CSR structure of the level operator (sorted columns) and its assembly data
     std::vector<int32_t> row_ptr, col, diag;
-    std::vector<double> mass, stiff;
+    std::vector<double> elem;           // [nc][27]: 3x3 mass | stiffness | skew per cell
+    std::vector<int32_t> contrib_ptr;   // [nnz+1]
+    std::vector<int32_t> contrib;       // cell*9 + a*3 + b, in cell order per entry
     // transfer to the next finer level (empty on the fine level)
     std::vector<int32_t> parent;      // [nv_finer][2]
     std::vector<int32_t> child_ptr;   // [nv + 1]  restriction: coarse vertex <- fine vertices
@@ -80,7 +82,8 @@ std::string build_host_mesh(const hdg_mesh_desc *desc, HostMesh &hm);
 struct DevLevel {
     int nv = 0, nnz = 0;
     int32_t *row_ptr = nullptr, *col = nullptr, *diag = nullptr;
-    double *mass = nullptr, *stiff = nullptr, *A = nullptr, *dinv = nullptr;
+    double *elem = nullptr, *fK = nullptr, *A = nullptr, *dinv = nullptr;
+    int32_t *contrib_ptr = nullptr, *contrib = nullptr;
     float *A32 = nullptr, *dinv32 = nullptr;
     int32_t *parent = nullptr;                         // [nv_finer][2]
     int32_t *child_ptr = nullptr, *child_idx = nullptr;
@@ -105,6 +108,7 @@ struct ReadBack {
 // levels of the single-CTA V-cycle tail (k_p1.cu)
 constexpr int kTailMaxLevels = 8;
 constexpr int kTailMaxVertices = 1024;     // default largest level run inside the tail kernel
+constexpr size_t kTailSmemMax = 226 * 1024; // dynamic shared memory limit of the tail kernel
 struct TailLevel {
     int nv, nnz, nci;
     const int32_t *rp, *col;            // CSR of the level operator
@@ -173,6 +177,7 @@ struct hdg_handle {
 
     std::vector<hdg::DevLevel> lev;
     int tail_start[2] = {0, 0};       // first P1 level of the single-CTA tail kernel (FP64, FP32)
+    int bs_facet = 256;               // threads per block of the facet-row kernels (autotuned)
     double *d_coarse_inv = nullptr;   // dense inverse of the coarsest P1 operator
     double *d_coarse_work = nullptr;
     float *d_coarse_inv32 = nullptr;
@@ -196,7 +201,7 @@ namespace hdg {
 // condense / assembly (k_condense.cu)
 cudaError_t launch_condense(hdg_handle *h);
 cudaError_t launch_assemble(hdg_handle *h);
-cudaError_t launch_p1_combine(hdg_handle *h, DevLevel &L, double tau, double ctau2);
+cudaError_t launch_p1_assemble(hdg_handle *h, DevLevel &L, double tau, double gH, int rotating);
 cudaError_t launch_dense_inverse(hdg_handle *h, const DevLevel &L, double *work, double *inv, int n);
 cudaError_t launch_to_f32(const double *x, float *y, size_t n, cudaStream_t s);
 

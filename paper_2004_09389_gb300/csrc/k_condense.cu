@@ -273,13 +273,34 @@ __global__ void assemble_kernel(AssembleArgs a) {
 }
 
 // ---------------------------------------------------------------- P1 level operator
-// A = (M + (tau c)^2 K) / tau  (Eq. coarse_problem_upwind at the scale of the
-// trace operator on smooth traces); dinv = 1 / diag(A).
-__global__ void p1_combine_kernel(int nv, int nnz, const int32_t *diag, const double *mass, const double *stiff,
-                                  double tau, double ctau2, double *A, double *dinv) {
+// The coarse problem obtained, as in Sec. 4.4 (Eq. coarse_problem_upwind), by
+// eliminating u from the time-implicit continuum equations, here with the
+// Coriolis term implicit: u = (I - tau f J)(r_u - tau g grad h)/(1 + tau^2 f^2),
+// hence per cell (f_K the cell mean of f, kappa_K = 1/(1 + tau^2 f_K^2))
+//   A = [ (phi,psi) + tau^2 g H kappa_K ((grad phi, grad psi) - tau f_K (J grad phi, grad psi)) ] / tau,
+// divided by tau to match the scale of the trace operator on smooth traces.
+// rotating = 0 drops f (the form printed in the paper).  Every CSR entry sums
+// its contributions in a fixed (cell) order.
+__global__ void p1_assemble_kernel(int nnz, const int32_t *__restrict__ cptr, const int32_t *__restrict__ contrib,
+                                   const double *__restrict__ elem, const double *__restrict__ fK, double tau,
+                                   double gH, int rotating, double *__restrict__ A) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nnz) return;
+    double acc = 0.0;
+    for (int k = cptr[q]; k < cptr[q + 1]; ++k) {
+        const int code = contrib[k], K = code / 9, ab = code % 9;
+        const double *el = elem + size_t(K) * 27;
+        const double f = rotating ? fK[K] : 0.0;
+        const double kap = 1.0 / (1.0 + tau * tau * f * f);
+        acc += (el[ab] + tau * tau * gH * kap * (el[9 + ab] - tau * f * el[18 + ab])) / tau;
+    }
+    A[q] = acc;
+}
+
+__global__ void p1_dinv_kernel(int nv, const int32_t *__restrict__ diag, const double *__restrict__ A,
+                               double *__restrict__ dinv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nnz) A[i] = (mass[i] + ctau2 * stiff[i]) / tau;
-    if (i < nv) dinv[i] = tau / (mass[diag[i]] + ctau2 * stiff[diag[i]]);
+    if (i < nv) dinv[i] = 1.0 / A[diag[i]];
 }
 
 // dense copy of a CSR matrix (n <= 1024), then in-place Gauss-Jordan inverse with
@@ -399,10 +420,12 @@ cudaError_t launch_assemble(hdg_handle *h) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_p1_combine(hdg_handle *h, DevLevel &L, double tau, double ctau2) {
-    int n = L.nnz > L.nv ? L.nnz : L.nv;
-    p1_combine_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(L.nv, L.nnz, L.diag, L.mass, L.stiff, tau, ctau2,
-                                                               L.A, L.dinv);
+cudaError_t launch_p1_assemble(hdg_handle *h, DevLevel &L, double tau, double gH, int rotating) {
+    p1_assemble_kernel<<<(L.nnz + 255) / 256, 256, 0, h->stream>>>(L.nnz, L.contrib_ptr, L.contrib, L.elem, L.fK, tau,
+                                                                    gH, rotating, L.A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    p1_dinv_kernel<<<(L.nv + 255) / 256, 256, 0, h->stream>>>(L.nv, L.diag, L.A, L.dinv);
     return cudaGetLastError();
 }
 

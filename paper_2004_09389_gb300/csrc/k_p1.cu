@@ -348,7 +348,10 @@ cudaError_t launch_p1_up(const DevLevel &fine, const DevLevel &coarse, const T *
 }
 template <typename T>
 cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(tail_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    // one fixed limit for every handle: the attribute is process-wide, so a
+    // per-handle value could be lowered by another thread between set and launch
+    if (smem > kTailSmemMax) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(tail_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTailSmemMax));
     if (e != cudaSuccess) return e;
     tail_kernel<T><<<1, 1024, smem, s>>>(a);
     return cudaGetLastError();

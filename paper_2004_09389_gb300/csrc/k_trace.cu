@@ -377,7 +377,7 @@ inline bool bf16_pre(hdg_handle *h) { return h->prm.precision == HDG_MIXED_BF16 
 
 template <typename T>
 cudaError_t launch_apply_t(hdg_handle *h, const T *x, T *y) {
-    HDG_DISPATCH_P(h->p, (apply_kernel<P, T, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, Ops<T>::S(h, false), h->d_nbr, x, y)));
+    HDG_DISPATCH_P(h->p, (apply_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, false), h->d_nbr, x, y)));
     return cudaGetLastError();
 }
 // residual / smoothing kernels serve the preconditioner (pre = true) or the
@@ -385,11 +385,11 @@ cudaError_t launch_apply_t(hdg_handle *h, const T *x, T *y) {
 template <typename T>
 cudaError_t launch_residual_t(hdg_handle *h, const T *b, const T *x, T *r, bool pre) {
     if constexpr (std::is_same<T, float>::value) if (pre && bf16_pre(h)) {
-        HDG_DISPATCH_P(h->p, (residual_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, h->d_Sval16, h->d_nbr, b, x, r)));
+        HDG_DISPATCH_P(h->p, (residual_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, h->d_nbr, b, x, r)));
         return cudaGetLastError();
     }
     {
-        HDG_DISPATCH_P(h->p, (residual_kernel<P, T, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, Ops<T>::S(h, pre), h->d_nbr, b, x, r)));
+        HDG_DISPATCH_P(h->p, (residual_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, pre), h->d_nbr, b, x, r)));
     }
     return cudaGetLastError();
 }
@@ -397,18 +397,18 @@ template <typename T>
 cudaError_t launch_smooth_t(hdg_handle *h, const T *b, const T *x, T *xout) {
     const T om = T(h->prm.omega);
     if constexpr (std::is_same<T, float>::value) if (bf16_pre(h)) {
-        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, om)));
+        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, om)));
         return cudaGetLastError();
     }
     {
-        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, om)));
+        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, om)));
     }
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_smooth_first_t(hdg_handle *h, const T *b, T *x) {
     const T om = T(h->prm.omega);
-    HDG_DISPATCH_P(h->p, (smooth_first_kernel<P, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, Ops<T>::D(h), b, x, om)));
+    HDG_DISPATCH_P(h->p, (smooth_first_kernel<P, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::D(h), b, x, om)));
     return cudaGetLastError();
 }
 template <typename T>
@@ -420,17 +420,17 @@ template <typename T>
 cudaError_t launch_smooth_prolong_t(hdg_handle *h, const T *ec, const T *b, const T *x, T *xout) {
     const T om = T(h->prm.omega);
     if constexpr (std::is_same<T, float>::value) if (bf16_pre(h)) {
-        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om)));
+        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om)));
         return cudaGetLastError();
     }
     {
-        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om)));
+        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om)));
     }
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_prolong_add_t(hdg_handle *h, const T *ec, T *x) {
-    HDG_DISPATCH_P(h->p, (prolong_add_kernel<P, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->NF, h->d_facet_verts, ec, x)));
+    HDG_DISPATCH_P(h->p, (prolong_add_kernel<P, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_facet_verts, ec, x)));
     return cudaGetLastError();
 }
 
@@ -479,7 +479,7 @@ cudaError_t launch_rhs(hdg_handle *h, const double *r_u, const double *r_h, doub
     HDG_DISPATCH_P(h->p, (rhs_cell_kernel<P><<<blocks(n, 256), 256, 0, h->stream>>>(h->N, h->d_W, r_u, r_h, ycell)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    HDG_DISPATCH_P(h->p, (rhs_gather_kernel<P><<<blocks(h->NF, 256), 256, 0, h->stream>>>(h->N, h->NF, ycell, h->d_facet_cell, h->d_facet_edge, h->d_flip, g)));
+    HDG_DISPATCH_P(h->p, (rhs_gather_kernel<P><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->N, h->NF, ycell, h->d_facet_cell, h->d_facet_edge, h->d_flip, g)));
     return cudaGetLastError();
 }
 

@@ -65,9 +65,14 @@ std::string check_level(const hdg_mesh_level &L, const char *what) {
     return "";
 }
 
-// geometric P1 mass and stiffness on one level, CSR with sorted columns
+// P1 element data on one level and the CSR structure of the level operator:
+// per cell the 3x3 mass, stiffness (grad L_b, grad L_a) and skew
+// (J grad L_b, grad L_a) matrices (J the rotation by 90 degrees in the cell's
+// plane), and for every CSR entry the list of (cell, a, b) that contribute, in
+// cell order, so the device sums each entry in a fixed order.
 void p1_matrices(HostLevel &hl) {
-    std::vector<std::vector<std::pair<int, std::pair<double, double>>>> rows(hl.nv);
+    hl.elem.assign(size_t(hl.nc) * 27, 0.0);
+    std::vector<std::vector<std::pair<int, int>>> rows(hl.nv);   // (column, contribution code)
     for (int K = 0; K < hl.nc; ++K) {
         const double *x = &hl.X[size_t(K) * 6];
         double J00 = x[2] - x[0], J01 = x[4] - x[0], J10 = x[3] - x[1], J11 = x[5] - x[1];
@@ -79,27 +84,30 @@ void p1_matrices(HostLevel &hl) {
             G[a][0] = (J11 * gref[a][0] - J10 * gref[a][1]) / det;
             G[a][1] = (-J01 * gref[a][0] + J00 * gref[a][1]) / det;
         }
+        double *el = &hl.elem[size_t(K) * 27];
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) {
-                double mv = det / 24.0 * (a == b ? 2.0 : 1.0);
-                double kv = 0.5 * det * (G[a][0] * G[b][0] + G[a][1] * G[b][1]);
-                rows[hl.cells[3 * K + a]].push_back({hl.cells[3 * K + b], {mv, kv}});
+                const int ab = a * 3 + b;
+                el[ab] = det / 24.0 * (a == b ? 2.0 : 1.0);
+                el[9 + ab] = 0.5 * det * (G[a][0] * G[b][0] + G[a][1] * G[b][1]);
+                // (J g_b) . g_a with J g = (-g_y, g_x)
+                el[18 + ab] = 0.5 * det * (G[a][0] * (-G[b][1]) + G[a][1] * G[b][0]);
+                rows[hl.cells[3 * K + a]].push_back({hl.cells[3 * K + b], K * 9 + ab});
             }
     }
     hl.row_ptr.assign(hl.nv + 1, 0);
-    hl.col.clear(); hl.mass.clear(); hl.stiff.clear(); hl.diag.assign(hl.nv, -1);
+    hl.col.clear(); hl.diag.assign(hl.nv, -1);
+    hl.contrib_ptr.assign(1, 0);
+    hl.contrib.clear();
     for (int v = 0; v < hl.nv; ++v) {
         auto &r = rows[v];
-        std::sort(r.begin(), r.end(), [](auto &a, auto &b) { return a.first < b.first; });
+        std::stable_sort(r.begin(), r.end(), [](auto &a, auto &b) { return a.first < b.first; });
         for (size_t k = 0; k < r.size();) {
             size_t k2 = k;
-            double m = 0, s = 0;
-            // sum duplicates in a fixed order (sorted by column, then cell order)
-            while (k2 < r.size() && r[k2].first == r[k].first) { m += r[k2].second.first; s += r[k2].second.second; ++k2; }
             if (r[k].first == v) hl.diag[v] = int(hl.col.size());
             hl.col.push_back(r[k].first);
-            hl.mass.push_back(m);
-            hl.stiff.push_back(s);
+            while (k2 < r.size() && r[k2].first == r[k].first) hl.contrib.push_back(r[k2++].second);
+            hl.contrib_ptr.push_back(int(hl.contrib.size()));
             k = k2;
         }
         hl.row_ptr[v + 1] = int(hl.col.size());

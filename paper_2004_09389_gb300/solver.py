@@ -25,9 +25,11 @@ class HDGSolver:
     ``cell_shift`` and an optional list ``levels`` of coarse P1 levels (each with
     ``parent``).  Keyword arguments override the fields of ``hdg_params``.
     ``stream``: a ``torch.cuda.Stream`` (or a raw ``cudaStream_t`` value) for the
-    handle's work; by default a new PyTorch stream.  ``*_dev`` calls are ordered
-    after the work already queued on PyTorch's current stream, and that stream
-    waits for them, so tensors can be used right before and after the call.
+    handle's work; by default the handle creates its own stream (PyTorch hands
+    out streams from a small pool, so many handles would share them).
+    ``*_dev`` calls are ordered after the work already queued on PyTorch's
+    current stream, and that stream waits for them, so tensors can be used
+    right before and after the call.
     """
 
     def __init__(self, mesh, p: int, tau: float, g: float = 1.0, H: float = 1.0, f_vertex=None,
@@ -47,9 +49,6 @@ class HDGSolver:
         desc = L.make_mesh_desc(mesh, self._keep)
         h = C.c_void_p()
         torch = _torch()
-        if stream is None and torch is not None:
-            stream = torch.cuda.Stream()
-        self.stream = stream
         raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
         rc = self.lib.hdg_setup(C.byref(desc), C.byref(prm), C.c_void_p(raw), C.byref(h))
         self._keep = []
@@ -57,6 +56,9 @@ class HDGSolver:
             raise L.HDGError(rc, self.lib.hdg_last_error(None).decode())
         self.h = h
         self.p = int(p)
+        if stream is None and torch is not None:
+            stream = torch.cuda.ExternalStream(self.lib.hdg_get_stream(h))
+        self.stream = stream
         sz = (C.c_int64 * 6)()
         L.check(h, self.lib.hdg_get_sizes(h, sz))
         self.n_cells, self.n_facets, self.n_trace, self.n_p, self.m, self.n_levels = (int(v) for v in sz)
@@ -136,6 +138,14 @@ class HDGSolver:
     def precond_apply_dev(self, v, z) -> None:
         L.check(self.h, self._ordered(self.lib.hdg_precond_apply_dev, L._ptr(v), L._ptr(z)))
 
+    def autotune(self) -> tuple:
+        """Time candidate launch shapes on this handle and keep the fastest;
+        returns (threads per facet-row block, Gram-Schmidt blocks, largest
+        single-CTA coarse level)."""
+        ch = np.zeros(3, dtype=np.int32)
+        L.check(self.h, self.lib.hdg_autotune(self.h, ch.ctypes.data))
+        return tuple(int(v) for v in ch)
+
     # ---------------------------------------------------------------- accounting
     def profile_enable(self, timing: bool = True) -> None:
         L.check(self.h, self.lib.hdg_profile_enable(self.h, 1 if timing else 0))
@@ -158,3 +168,28 @@ class HDGSolver:
         S = np.empty((self.n_cells, self.m, self.m))
         L.check(self.h, self.lib.hdg_get_cell_schur(self.h, S.ctypes.data))
         return S
+
+
+def solve_batch_dev(solvers, r_u, r_h, lam, n_threads: int = 0, allow_fail: bool = False):
+    """Run independent solves concurrently (``hdg_solve_batch_dev``): solver i
+    solves device tensors ``r_u[i], r_h[i]`` into ``lam[i]``.  Every solver
+    needs its own stream (the default).  Returns the list of info dicts."""
+    lib = L.load()
+    n = len(solvers)
+    torch = _torch()
+    if torch is not None:
+        cur = torch.cuda.current_stream()
+        for s in solvers:
+            s.stream.wait_stream(cur)
+    hs = (C.c_void_p * n)(*[s.h.value for s in solvers])
+    pu = (C.c_void_p * n)(*[L._ptr(t) for t in r_u])
+    ph = (C.c_void_p * n)(*[L._ptr(t) for t in r_h])
+    pl = (C.c_void_p * n)(*[L._ptr(t) for t in lam])
+    infos = (L.hdg_solve_info * n)()
+    rc = lib.hdg_solve_batch_dev(hs, n, pu, ph, pl, infos, int(n_threads))
+    if torch is not None:
+        for s in solvers:
+            cur.wait_stream(s.stream)
+    if rc != 0 and not (allow_fail and rc in (L.HDG_ENOCONV, L.HDG_EBREAKDOWN)):
+        raise L.HDGError(rc, (lib.hdg_last_error(None) or b"").decode())
+    return [infos[i].as_dict() for i in range(n)]

@@ -121,6 +121,20 @@ def test_precond_matches_oracle(kind, p, n_pre, n_post):
     s.close()
 
 
+@pytest.mark.parametrize("kind", ["flat", "sphere"])
+def test_precond_printed_coarse_form_matches_oracle(kind):
+    """coarse_mode = 1: the coarse operator exactly as printed (no rotation)."""
+    mesh, prob, (tau, g, H, f), _, _ = _case(kind, 2)
+    s = _solver(mesh, 2, tau, g, H, f, coarse_mode=1)
+    pc = TwoLevelPreconditioner(prob, mesh, prob.trace_operator(), coarse="gmg", coarse_mode="rediscretised")
+    v = np.random.default_rng(4).standard_normal(prob.n_trace)
+    z = torch.empty(prob.n_trace, dtype=torch.float64, device="cuda")
+    s.precond_apply_dev(_dev(v), z)
+    torch.cuda.synchronize()
+    assert _rel(z.cpu().numpy(), pc(v)) <= 1e-12
+    s.close()
+
+
 @pytest.mark.parametrize("kind,p", CASES)
 def test_solve_and_recover_match_oracle(kind, p):
     mesh, prob, (tau, g, H, f), ru, rh = _case(kind, p)

@@ -142,3 +142,69 @@ def test_iterative_solve_reaches_direct_solution(kind):
     assert info["converged"] and info["iters"] < 40
     assert np.linalg.norm(lam - lam0) / np.linalg.norm(lam0) < 1e-10
     assert np.linalg.norm(h - h0) / np.linalg.norm(h0) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# coarse operator with the implicit Coriolis term (reading of Sec. 4.4)
+
+def test_rotating_coarse_operator_reduces_to_the_printed_form_without_rotation():
+    from oracle.solver import p1_rotating_operator
+    mesh = I.icosahedral_sphere(2)
+    md = MeshData.of(mesh)
+    tau, g, H = 0.3, 1.7, 0.6
+    A = p1_rotating_operator(md, np.zeros(mesh.n_vertices), tau, g, H)
+    Mm, Km = p1_matrices(md)
+    B = (Mm + tau * tau * g * H * Km) / tau
+    assert np.abs((A - B).toarray()).max() <= 1e-13 * np.abs(B.toarray()).max()
+
+
+def test_rotating_coarse_operator_constant_f_has_no_skew_part():
+    """On a closed surface with constant f the skew term sums to zero for P1
+    (tangential derivatives are continuous), leaving kappa = 1/(1+tau^2 f^2)."""
+    from oracle.solver import p1_rotating_operator
+    mesh = I.periodic_square(8)
+    md = MeshData.of(mesh)
+    tau, g, H, f0 = 0.4, 1.0, 2.0, 3.0
+    A = p1_rotating_operator(md, np.full(mesh.n_vertices, f0), tau, g, H).toarray()
+    Mm, Km = p1_matrices(md)
+    kap = 1.0 / (1.0 + (tau * f0) ** 2)
+    B = ((Mm + tau * tau * g * H * kap * Km) / tau).toarray()
+    assert np.abs(A - B).max() <= 1e-12 * np.abs(B).max()
+    assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+
+
+def test_rotating_coarse_operator_fourier_symbol():
+    """A smooth Fourier mode sees the continuum symbol (1 + tau^2 g H k^2 / (1 + tau^2 f^2)) / tau."""
+    from oracle.solver import p1_rotating_operator
+    n = 64
+    mesh = I.periodic_square(n)
+    md = MeshData.of(mesh)
+    tau, g, H, f0 = 0.05, 1.0, 1.0, 25.0
+    A = p1_rotating_operator(md, np.full(mesh.n_vertices, f0), tau, g, H)
+    Mm, _ = p1_matrices(md)
+    k = 2 * np.pi
+    x = np.cos(k * mesh.vertex_xyz[:, 0])
+    ratio = (x @ A @ x) / (x @ Mm @ x)
+    expect = (1 + tau * tau * g * H * k * k / (1 + (tau * f0) ** 2)) / tau
+    assert ratio == pytest.approx(expect, rel=2e-3)
+
+
+def test_rotating_coarse_operator_helps_under_rotation():
+    """Sphere, f tau ~ 2: the coarse problem with rotation needs fewer FGMRES
+    iterations than the rotation-free one; both converge (SURVEY-style check of
+    the reading, not a value printed in the paper)."""
+    R, om = 6.371e6, 7.292e-5
+    mesh = I.sphere_hierarchy(4, R, r_coarsest=1)
+    g, H = 9.81, 7500.0
+    tau = 8.0 * mesh.h / np.sqrt(g * H)
+    f = I.coriolis_sphere(mesh, om)
+    prob = HDGProblem(mesh, 1, tau=tau, g=g, H=H, f_vertex=f)
+    rng = np.random.default_rng(3)
+    ru = rng.standard_normal((prob.N, 2, prob.np))
+    rh = rng.standard_normal((prob.N, prob.np))
+    its = {}
+    for mode in ("rotating", "rediscretised"):
+        _, _, info = solve_iterative(prob, mesh, ru, rh, rtol=1e-8, coarse_mode=mode)
+        assert info["converged"]
+        its[mode] = info["iters"]
+    assert its["rotating"] < its["rediscretised"]
