@@ -218,6 +218,10 @@ HDG_API int hdg_condensed_rhs_noalloc_dev(hdg_handle *h, const double *r_u, cons
  * with zero initial guess. */
 HDG_API int hdg_precond_apply_dev(hdg_handle *h, const double *v, double *z);
 
+/* z = V(v) in FP32 as used by the inner solves of the mixed modes (with the
+ * learned sweep when it is enabled); v, z: FP32, lambda layout. */
+HDG_API int hdg_precond_apply32_dev(hdg_handle *h, const float *v, float *z);
+
 /* Inspection (host buffers) for checking against an independent code. */
 /* sizes[0..5] = n_cells, n_facets, n_trace, n_p, 3(p+1), number of P1 levels. */
 HDG_API int hdg_get_sizes(const hdg_handle *h, int64_t *sizes);
@@ -251,6 +255,37 @@ HDG_API int hdg_get_cell_schur(hdg_handle *h, double *S);
 #define HDG_PROF_N             15
 HDG_API int hdg_profile_enable(hdg_handle *h, int timing_on);
 HDG_API int hdg_profile_read(hdg_handle *h, double *ms, int64_t *launches);
+
+/* Learned facet-patch smoother (spec extension; the paper has no learned
+ * component).  In the FP32 inner solves of the mixed modes it replaces the last
+ * post-smoothing sweep of the V-cycle by x += c(r), r = v - S x:
+ *   X_e = (r_e, r of the four facets sharing a cell with e) / s_e, s_e their RMS,
+ *   y_e = W3 tanh(W2 tanh(W1 X_e + b1) + b2) + b3 + omega X_e[0:p+1],
+ *   c_e = D_e^-1 (s_e y_e)          (zero weights: the damped block-Jacobi sweep).
+ * It is trained on the GPU by the library's own forward / backward kernels to
+ * minimise mean ||r - S c(r)||^2 / ||r||^2 over residuals that the plain solver
+ * produces before its last sweep.  While it is enabled, a solve whose residual
+ * estimate drops by less than 10 % over three iterations switches back to the
+ * plain V-cycle for the rest of that solve (hdg_solve_info.fallback_used = 1).
+ * Parameters: theta = [W1 (hidden x 5(p+1)) | b1 | W2 | b2 | W3 ((p+1) x hidden) | b3], FP32. */
+/* Allocate the network (hidden = 32 or 64), seed its weights, and room for
+ * `capacity` training residuals.  Needs hdg_condense and a mixed mode. */
+HDG_API int hdg_learned_init(hdg_handle *h, int hidden, int capacity, uint64_t seed, int32_t *n_params);
+/* Run one plain solve (device pointers) and store the normalised residual seen
+ * before the last post-smoothing sweep of every preconditioner call, up to the
+ * capacity; *n_stored receives the number stored so far. */
+HDG_API int hdg_learned_collect_dev(hdg_handle *h, const double *r_u, const double *r_h, int32_t *n_stored);
+/* Adam on minibatches of stored residuals; losses of the first and last step. */
+HDG_API int hdg_learned_train(hdg_handle *h, int steps, int batch, double lr, double *loss_first,
+                              double *loss_last);
+/* Copy the parameters out (get = 1) or in (get = 0), host buffer of n_params floats. */
+HDG_API int hdg_learned_params(hdg_handle *h, float *theta, int get);
+/* Use (1) or stop using (0) the learned sweep in later solves. */
+HDG_API int hdg_learned_enable(hdg_handle *h, int on);
+/* Loss mean_i ||r_i - S c(r_i)||^2 / ||r_i||^2 and its gradient (host buffer of
+ * n_params floats) for n residuals given on the device in the lambda layout
+ * [n][n_facets][p+1] (FP32). */
+HDG_API int hdg_learned_loss_grad_dev(hdg_handle *h, const float *R, int n, float *grad, double *loss);
 
 /* The CUDA stream (cudaStream_t) the handle runs on: the one given to
  * hdg_setup, or the non-blocking stream the handle created and owns. */

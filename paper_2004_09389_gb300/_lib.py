@@ -61,7 +61,9 @@ EXPORTS = ["hdg_default_params", "hdg_setup", "hdg_condense", "hdg_set_tau", "hd
            "hdg_recover", "hdg_recover_dev", "hdg_trace_apply_dev", "hdg_condensed_rhs_dev",
            "hdg_precond_apply_dev", "hdg_get_sizes", "hdg_get_facets", "hdg_get_cell_schur", "hdg_destroy",
            "hdg_last_error", "hdg_profile_enable", "hdg_profile_read", "hdg_condensed_rhs_noalloc_dev",
-           "hdg_solve_batch_dev", "hdg_autotune", "hdg_get_stream"]
+           "hdg_solve_batch_dev", "hdg_autotune", "hdg_get_stream", "hdg_learned_init",
+           "hdg_learned_collect_dev", "hdg_learned_train", "hdg_learned_params", "hdg_learned_enable",
+           "hdg_learned_loss_grad_dev", "hdg_precond_apply32_dev"]
 
 HDG_PROF_N = 15
 PROF_NAMES = ["apply64", "residual64", "smooth64", "smooth_first64", "apply32", "residual32", "smooth32",
@@ -91,12 +93,19 @@ def load() -> C.CDLL:
     lib.hdg_condensed_rhs_dev.argtypes = [vp, vp, vp, vp]
     lib.hdg_condensed_rhs_noalloc_dev.argtypes = [vp, vp, vp, vp]
     lib.hdg_precond_apply_dev.argtypes = [vp, vp, vp]
+    lib.hdg_precond_apply32_dev.argtypes = [vp, vp, vp]
     lib.hdg_get_sizes.argtypes = [vp, C.POINTER(C.c_int64)]
     lib.hdg_get_facets.argtypes = [vp, vp, vp, vp]
     lib.hdg_get_cell_schur.argtypes = [vp, vp]
     lib.hdg_solve_batch_dev.argtypes = [vp, C.c_int, vp, vp, vp, C.POINTER(hdg_solve_info), C.c_int]
     lib.hdg_autotune.argtypes = [vp, vp]
     lib.hdg_get_stream.argtypes = [vp]
+    lib.hdg_learned_init.argtypes = [vp, C.c_int, C.c_int, C.c_uint64, vp]
+    lib.hdg_learned_collect_dev.argtypes = [vp, vp, vp, vp]
+    lib.hdg_learned_train.argtypes = [vp, C.c_int, C.c_int, C.c_double, vp, vp]
+    lib.hdg_learned_params.argtypes = [vp, vp, C.c_int]
+    lib.hdg_learned_enable.argtypes = [vp, C.c_int]
+    lib.hdg_learned_loss_grad_dev.argtypes = [vp, vp, C.c_int, vp, vp]
     lib.hdg_get_stream.restype = vp
     lib.hdg_profile_enable.argtypes = [vp, C.c_int]
     lib.hdg_profile_read.argtypes = [vp, vp, vp]

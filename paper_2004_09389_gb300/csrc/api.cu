@@ -13,6 +13,7 @@
 #include "common.h"
 
 #include <algorithm>
+#include <type_traits>
 #include <atomic>
 #include <thread>
 #include <cmath>
@@ -56,7 +57,7 @@ struct Workspace {
     double *bnorm = nullptr;  // ||b|| of the current Krylov solve
     // CUDA graphs of one Arnoldi step per (precision, j); see arnoldi_step
     struct StepGraph { cudaGraphExec_t exec = nullptr; int64_t counts[HDG_PROF_N] = {}; };
-    std::vector<StepGraph> graphs[2];
+    std::vector<StepGraph> graphs[3];   // FP64, FP32, FP32 with the learned sweep
     bool use_graphs = true;
     double *beta = nullptr;   // refinement scale ||g - S x|| (mixed mode)
     int32_t *flags = nullptr;
@@ -240,6 +241,9 @@ size_t hdg::tail_smem_bytes(const std::vector<DevLevel> &lev, int first, size_t 
 
 namespace {
 
+template <typename T>
+cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out);
+
 // P1 V-cycle for the coarse problem (Eq. coarse_problem_upwind) with
 // right-hand side levB(level 0).  Levels above the tail: fused kernels (the
 // first pre-smoothing sweep of each level rides on the restriction that
@@ -346,15 +350,48 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z) {
         if ((e = KL(HDG_PROF_TRANSFER, 1, launch_prolong_add_t<T>(h, ec, x))) != cudaSuccess) return e;
         return cudaMemcpyAsync(z, x, sizeof(T) * NT, cudaMemcpyDeviceToDevice, s);
     }
-    T *out = (np == 1) ? z : x2;
-    if ((e = KL(cat_smooth<T>(), 1, launch_smooth_prolong_t<T>(h, ec, v, x, out))) != cudaSuccess) return e;
-    std::swap(x, x2);
-    for (int i = 1; i < np; ++i) {
-        T *o = (i == np - 1) ? z : x2;
-        if ((e = KL(cat_smooth<T>(), 1, launch_smooth_t<T>(h, v, x, o))) != cudaSuccess) return e;
-        if (i < np - 1) std::swap(x, x2);
+    bool learned = false, collect = false;
+    if constexpr (std::is_same<T, float>::value) {
+        learned = h->lc.on && !h->lc.suspended;
+        collect = h->lc.collecting && h->lc.count < h->lc.cap;
     }
-    return cudaSuccess;
+    if (!learned && !collect) {
+        T *out = (np == 1) ? z : x2;
+        if ((e = KL(cat_smooth<T>(), 1, launch_smooth_prolong_t<T>(h, ec, v, x, out))) != cudaSuccess) return e;
+        std::swap(x, x2);
+        for (int i = 1; i < np; ++i) {
+            T *o = (i == np - 1) ? z : x2;
+            if ((e = KL(cat_smooth<T>(), 1, launch_smooth_t<T>(h, v, x, o))) != cudaSuccess) return e;
+            if (i < np - 1) std::swap(x, x2);
+        }
+        return cudaSuccess;
+    }
+    // n_post - 1 ordinary sweeps, then the residual r = v - S x before the last sweep
+    if (np == 1) {
+        if ((e = KL(HDG_PROF_TRANSFER, 1, launch_prolong_add_t<T>(h, ec, x))) != cudaSuccess) return e;
+    } else {
+        if ((e = KL(cat_smooth<T>(), 1, launch_smooth_prolong_t<T>(h, ec, v, x, x2))) != cudaSuccess) return e;
+        std::swap(x, x2);
+        for (int i = 1; i < np - 1; ++i) {
+            if ((e = KL(cat_smooth<T>(), 1, launch_smooth_t<T>(h, v, x, x2))) != cudaSuccess) return e;
+            std::swap(x, x2);
+        }
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        if (learned) {
+            // the learned sweep replaces the last block-Jacobi sweep
+            if ((e = KL(cat_res<T>(), 1, launch_residual_t<T>(h, v, x, k.res, true))) != cudaSuccess) return e;
+            return KL(HDG_PROF_KRYLOV, 1, launch_learned_infer(h, k.res, x, z));
+        }
+        // collecting: store the residual (normalised), then the plain last sweep
+        if ((e = KL(cat_res<T>(), 1, launch_residual_t<T>(h, v, x, k.res, true))) != cudaSuccess) return e;
+        Workspace &W = *h->ws;
+        if ((e = dots<T>(h, k.res, 1, k.res, W.nrm2)) != cudaSuccess) return e;
+        if ((e = launch_normalize32(k.res, h->lc.buf + size_t(h->lc.count) * NT, W.nrm2, NT, s)) != cudaSuccess)
+            return e;
+        h->lc.count += 1;
+    }
+    return KL(cat_smooth<T>(), 1, launch_smooth_t<T>(h, v, x, z));
 }
 
 // ---------------------------------------------------------------- Krylov helpers
@@ -408,11 +445,12 @@ template <typename T>
 int run_arnoldi_step(hdg_handle *h, int j) {
     Workspace &W = *h->ws;
     cudaStream_t s = h->stream;
-    if (h->prof.on || !W.use_graphs) {
+    if (h->prof.on || !W.use_graphs || h->lc.collecting) {
         TRY(arnoldi_step<T>(h, j));
         return HDG_OK;
     }
-    Workspace::StepGraph &G = W.graphs[sizeof(T) == 8 ? 0 : 1][j];
+    const int gi = sizeof(T) == 8 ? 0 : ((h->lc.on && !h->lc.suspended) ? 2 : 1);
+    Workspace::StepGraph &G = W.graphs[gi][j];
     if (!G.exec) {
         int64_t before[HDG_PROF_N];
         std::memcpy(before, h->prof.launches, sizeof(before));
@@ -462,6 +500,7 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
     W.host_buf[3] = beta;
     TRY(cudaMemcpyAsync(W.sv, W.host_buf + 3, sizeof(double), cudaMemcpyHostToDevice, s));
     int j = 0;
+    double hist[72];
     for (; j < m && j < max_it; ++j) {
         int rc = run_arnoldi_step<T>(h, j);
         if (rc) return rc;
@@ -469,6 +508,17 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
         prof_flush(h);
         est_out = W.host_rb->est;
         flag_out = W.host_rb->flags;
+        hist[j] = est_out;
+        // learned sweep as preconditioner: if the residual estimate stalls (less
+        // than 10 % decrease over three iterations), fall back to the plain
+        // V-cycle for the rest of this solve (FGMRES restarts from the iterate)
+        if (std::is_same<T, float>::value && h->lc.on && !h->lc.suspended && j >= 3 && est_out > rel_target &&
+            est_out > 0.9 * hist[j - 3]) {
+            h->lc.suspended = true;
+            h->lc.fallback = true;
+            ++j;
+            break;
+        }
         if (est_out <= rel_target || (flag_out & 6)) { ++j; break; }
     }
     its_done = j;
@@ -629,6 +679,11 @@ void free_handle(hdg_handle *h) {
         if (W.host_buf) cudaFreeHost(W.host_buf);
         if (W.host_flags) cudaFreeHost(W.host_flags);
         delete h->ws;
+    }
+    {
+        Learned &L = h->lc;
+        dfree(L.theta); dfree(L.m); dfree(L.v); dfree(L.grad); dfree(L.act); dfree(L.gfac); dfree(L.rev);
+        dfree(L.buf); dfree(L.c); dfree(L.rn); dfree(L.gc); dfree(L.tmp); dfree(L.coef); dfree(L.nrm);
     }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -813,8 +868,7 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(dalloc(&W.est, 1));
     TRY(dalloc(&W.scal, 1));
     TRY(dalloc(&W.bnorm, 1));
-    W.graphs[0].resize(W.m);
-    W.graphs[1].resize(W.m);
+    for (auto &gv : W.graphs) gv.resize(W.m);
     {
         const char *ev = std::getenv("HDG_DISABLE_GRAPHS");
         W.use_graphs = !(ev && ev[0] == '1');
@@ -853,6 +907,8 @@ int require_condensed(hdg_handle *h) {
 int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solve_info &info) {
     Workspace &W = *h->ws;
     cudaStream_t s = h->stream;
+    h->lc.suspended = false;
+    h->lc.fallback = false;
     TRY(KL(HDG_PROF_RHS, 2, launch_rhs(h, r_u, r_h, W.g, W.ycell)));
     int rc;
     if (h->prm.precision == HDG_FP64) {
@@ -871,6 +927,7 @@ int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solv
         }
     }
     info.status = rc;
+    info.fallback_used = h->lc.fallback ? 1 : 0;
     TRY(cudaMemcpyAsync(W.lam_int, W.x, sizeof(double) * W.NT, cudaMemcpyDeviceToDevice, s));
     W.have_lambda = true;
     return rc;
@@ -1098,6 +1155,22 @@ int hdg_precond_apply_dev(hdg_handle *h, const double *v, double *z) {
     return HDG_OK;
 }
 
+int hdg_precond_apply32_dev(hdg_handle *h, const float *v, float *z) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    if (h->prm.precision == HDG_FP64) return fail(h, HDG_EINVAL, "the FP32 preconditioner needs a mixed precision mode");
+    if (!v || !z) return fail(h, HDG_EINVAL, "NULL pointer argument");
+    Workspace &W = *h->ws;
+    const size_t NF = h->NF, pp = h->pp;
+    // [NF][pp] <-> [pp][NF] through the FP32 Krylov work vectors
+    TRY(launch_to_internal32(h, v, W.k32.b));
+    TRY(precond<float>(h, W.k32.b, W.k32.x));
+    (void)NF;
+    (void)pp;
+    TRY(launch_to_external32(h, W.k32.x, z));
+    return HDG_OK;
+}
+
 int hdg_get_sizes(const hdg_handle *h, int64_t *sizes) {
     if (!h || !sizes) return HDG_EINVAL;
     sizes[0] = h->N;
@@ -1265,6 +1338,185 @@ int hdg_solve_batch_dev(hdg_handle *const *hs, int n, const double *const *r_u, 
 }
 
 void *hdg_get_stream(const hdg_handle *h) { return h ? static_cast<void *>(h->stream) : nullptr; }
+
+// ---------------------------------------------------------------- learned smoother
+
+static uint64_t splitmix64(uint64_t &x) {
+    uint64_t z = (x += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+int hdg_learned_init(hdg_handle *h, int hidden, int capacity, uint64_t seed, int32_t *n_params) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    if (h->prm.precision == HDG_FP64 || !h->d_Sval32)
+        return fail(h, HDG_EINVAL, "the learned smoother works in the FP32 inner solves: use a mixed precision mode");
+    if (hidden != 32 && hidden != 64) return fail(h, HDG_EINVAL, "hidden width must be 32 or 64");
+    if (capacity < 1) return fail(h, HDG_EINVAL, "capacity must be positive");
+    Learned &L = h->lc;
+    if (L.ready) return fail(h, HDG_ESTATE, "learned smoother already initialised on this handle");
+    cudaStream_t s = h->stream;
+    const size_t NF = h->NF, NT = h->NT, pp = h->pp, F = 5 * pp;
+    L.hid = hidden;
+    L.npar = learned_n_params(h->p, hidden);
+    L.cap = capacity;
+    TRY(dalloc(&L.theta, size_t(L.npar)));
+    TRY(dalloc(&L.m, size_t(L.npar)));
+    TRY(dalloc(&L.v, size_t(L.npar)));
+    TRY(dalloc(&L.grad, size_t(L.npar)));
+    TRY(dalloc(&L.act, NF * (F + 2 * hidden + 1)));
+    TRY(dalloc(&L.gfac, NF * (2 * hidden + pp)));
+    TRY(dalloc(&L.rev, 4 * NF));
+    TRY(dalloc(&L.buf, size_t(capacity) * NT));
+    TRY(dalloc(&L.c, NT));
+    TRY(dalloc(&L.rn, NT));
+    TRY(dalloc(&L.gc, NT));
+    TRY(dalloc(&L.tmp, NT));
+    TRY(dalloc(&L.coef, 1));
+    TRY(dalloc(&L.nrm, 1));
+    TRY(cudaMemsetAsync(L.m, 0, sizeof(float) * L.npar, s));
+    TRY(cudaMemsetAsync(L.v, 0, sizeof(float) * L.npar, s));
+    // reverse neighbour lists for S^T: facet e appears in the row of each of its
+    // four neighbours f, as block b
+    std::vector<int32_t> nbr(4 * NF), rev(4 * NF, -1);
+    TRY(cudaMemcpyAsync(nbr.data(), h->d_nbr, sizeof(int32_t) * nbr.size(), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    std::vector<int> fill(NF, 0);
+    for (size_t f = 0; f < NF; ++f)
+        for (int b = 1; b <= 4; ++b) {
+            const int e = nbr[size_t(b - 1) * NF + f];
+            if (fill[e] >= 4) return fail(h, HDG_EINVAL, "facet neighbour relation is not symmetric");
+            rev[size_t(fill[e]++) * NF + e] = int32_t(f) * 8 + b;
+        }
+    for (size_t e = 0; e < NF; ++e)
+        if (fill[e] != 4) return fail(h, HDG_EINVAL, "facet neighbour relation is not symmetric");
+    TRY(cudaMemcpyAsync(L.rev, rev.data(), sizeof(int32_t) * rev.size(), cudaMemcpyHostToDevice, s));
+    // weights: uniform(-a, a) with a = sqrt(3 / fan_in); the output layer 100x
+    // smaller and zero biases, so the untrained sweep is close to block-Jacobi
+    std::vector<float> th(size_t(L.npar), 0.f);
+    uint64_t st = seed;
+    auto uni = [&]() { return float((splitmix64(st) >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0); };
+    const int hid = hidden;
+    size_t k = 0;
+    for (size_t i = 0; i < size_t(hid) * F; ++i) th[k++] = uni() * std::sqrt(3.f / float(F));
+    k += hid;
+    for (size_t i = 0; i < size_t(hid) * hid; ++i) th[k++] = uni() * std::sqrt(3.f / float(hid));
+    k += hid;
+    for (size_t i = 0; i < pp * size_t(hid); ++i) th[k++] = 0.01f * uni() * std::sqrt(3.f / float(hid));
+    TRY(cudaMemcpyAsync(L.theta, th.data(), sizeof(float) * th.size(), cudaMemcpyHostToDevice, s));
+    TRY(cudaStreamSynchronize(s));
+    L.rng = seed ^ 0x5851f42d4c957f2dull;
+    L.t = 0;
+    L.count = 0;
+    L.ready = true;
+    if (n_params) *n_params = L.npar;
+    return HDG_OK;
+}
+
+int hdg_learned_collect_dev(hdg_handle *h, const double *r_u, const double *r_h, int32_t *n_stored) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    if (!h->lc.ready) return fail(h, HDG_ESTATE, "hdg_learned_init has not run");
+    const bool was_on = h->lc.on;
+    h->lc.on = false;
+    h->lc.collecting = true;
+    hdg_solve_info info{};
+    rc = solve_internal(h, r_u, r_h, info);
+    h->lc.collecting = false;
+    h->lc.on = was_on;
+    if (n_stored) *n_stored = h->lc.count;
+    return rc;
+}
+
+int hdg_learned_train(hdg_handle *h, int steps, int batch, double lr, double *loss_first, double *loss_last) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    Learned &L = h->lc;
+    if (!L.ready || L.count < 1) return fail(h, HDG_ESTATE, "no training residuals collected");
+    if (steps < 1 || batch < 1 || !(lr > 0)) return fail(h, HDG_EINVAL, "bad training arguments");
+    Workspace &W = *h->ws;
+    cudaStream_t s = h->stream;
+    const size_t NT = h->NT;
+    W.host_buf[5] = -2.0 / batch;          // stored residuals have unit norm
+    TRY(cudaMemcpyAsync(L.coef, W.host_buf + 5, sizeof(double), cudaMemcpyHostToDevice, s));
+    for (int step = 0; step < steps; ++step) {
+        TRY(cudaMemsetAsync(L.grad, 0, sizeof(float) * L.npar, s));
+        double loss = 0.0;
+        for (int b = 0; b < batch; ++b) {
+            const float *r = L.buf + size_t(splitmix64(L.rng) % uint64_t(L.count)) * NT;
+            TRY(launch_learned_forward(h, r, L.c));
+            TRY(launch_residual_t<float>(h, r, L.c, L.rn, false));
+            double nrn;
+            rc = norm_host<float>(h, L.rn, nrn);
+            if (rc) return rc;
+            loss += nrn * nrn;
+            TRY(launch_learned_applyT(h, L.rn, L.gc));
+            TRY(launch_learned_backward(h, L.gc, L.coef));
+        }
+        L.t += 1;
+        TRY(launch_adam(h, float(lr), int(std::min<long long>(L.t, 1 << 30))));
+        loss /= batch;
+        if (!std::isfinite(loss)) return fail(h, HDG_ENAN, "NaN in the training loss");
+        if (step == 0 && loss_first) *loss_first = loss;
+        if (loss_last) *loss_last = loss;
+    }
+    TRY(cudaStreamSynchronize(s));
+    return HDG_OK;
+}
+
+int hdg_learned_params(hdg_handle *h, float *theta, int get) {
+    if (!h) return HDG_EINVAL;
+    if (!h->lc.ready) return fail(h, HDG_ESTATE, "hdg_learned_init has not run");
+    if (!theta) return fail(h, HDG_EINVAL, "NULL pointer argument");
+    const size_t bytes = sizeof(float) * h->lc.npar;
+    if (get) TRY(cudaMemcpyAsync(theta, h->lc.theta, bytes, cudaMemcpyDeviceToHost, h->stream));
+    else TRY(cudaMemcpyAsync(h->lc.theta, theta, bytes, cudaMemcpyHostToDevice, h->stream));
+    TRY(cudaStreamSynchronize(h->stream));
+    return HDG_OK;
+}
+
+int hdg_learned_enable(hdg_handle *h, int on) {
+    if (!h) return HDG_EINVAL;
+    if (on && !h->lc.ready) return fail(h, HDG_ESTATE, "hdg_learned_init has not run");
+    h->lc.on = on != 0;
+    return HDG_OK;
+}
+
+int hdg_learned_loss_grad_dev(hdg_handle *h, const float *R, int n, float *grad, double *loss) {
+    int rc = require_condensed(h);
+    if (rc) return rc;
+    Learned &L = h->lc;
+    if (!L.ready) return fail(h, HDG_ESTATE, "hdg_learned_init has not run");
+    if (!R || n < 1) return fail(h, HDG_EINVAL, "bad arguments");
+    Workspace &W = *h->ws;
+    cudaStream_t s = h->stream;
+    const size_t NT = h->NT;
+    TRY(cudaMemsetAsync(L.grad, 0, sizeof(float) * L.npar, s));
+    double total = 0.0;
+    for (int i = 0; i < n; ++i) {
+        TRY(launch_to_internal32(h, R + size_t(i) * NT, L.tmp));
+        double nr;
+        rc = norm_host<float>(h, L.tmp, nr);
+        if (rc) return rc;
+        W.host_buf[6] = -2.0 / (double(n) * nr * nr);
+        TRY(cudaMemcpyAsync(L.coef, W.host_buf + 6, sizeof(double), cudaMemcpyHostToDevice, s));
+        TRY(launch_learned_forward(h, L.tmp, L.c));
+        TRY(launch_residual_t<float>(h, L.tmp, L.c, L.rn, false));
+        double nrn;
+        rc = norm_host<float>(h, L.rn, nrn);
+        if (rc) return rc;
+        total += (nrn * nrn) / (nr * nr) / n;
+        TRY(launch_learned_applyT(h, L.rn, L.gc));
+        TRY(launch_learned_backward(h, L.gc, L.coef));
+        TRY(cudaStreamSynchronize(s));
+    }
+    if (grad) TRY(cudaMemcpyAsync(grad, L.grad, sizeof(float) * L.npar, cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    if (loss) *loss = total;
+    return HDG_OK;
+}
 
 int hdg_destroy(hdg_handle *h) {
     free_handle(h);

@@ -97,6 +97,25 @@ struct DevLevel {
 
 struct Workspace;   // solver vectors, defined in api.cu
 
+// learned facet-patch smoother (k_learned.cu, spec extension)
+struct Learned {
+    int hid = 0, npar = 0;
+    bool ready = false;        // initialised
+    bool on = false;           // used by the FP32 preconditioner
+    bool suspended = false;    // switched off for the rest of a solve after a stall
+    bool collecting = false;   // plain solves store the residual before the last sweep
+    bool fallback = false;     // a stall was seen in the current solve
+    int cap = 0, count = 0;    // training residuals stored / capacity
+    long long t = 0;           // Adam steps done
+    uint64_t rng = 0;
+    float *theta = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+    float *act = nullptr, *gfac = nullptr;   // per-facet activations / gradients (training)
+    int32_t *rev = nullptr;                  // [4][NF] neighbour f*8 + block index pointing back
+    float *buf = nullptr;                    // [cap][NT] normalised training residuals
+    float *c = nullptr, *rn = nullptr, *gc = nullptr, *tmp = nullptr;
+    double *coef = nullptr, *nrm = nullptr;
+};
+
 // per-iteration readback of the Krylov driver (pinned host copy)
 struct ReadBack {
     double est;      // |s_{j+1}| / ||b||
@@ -183,6 +202,7 @@ struct hdg_handle {
     float *d_coarse_inv32 = nullptr;
     hdg::Workspace *ws = nullptr;
     hdg::Prof prof;
+    hdg::Learned lc;
 };
 
 // ---------------------------------------------------------------- error helpers
@@ -260,6 +280,15 @@ template <typename T>
 cudaError_t launch_gs_step(const T *V, size_t ld, int j, T *w, double *partial, unsigned int *counter, int nblk,
                            double *h1, double *h2, double *nrm2, double *Hm, int ldh, double *cs, double *sn,
                            double *sv, const double *bnorm, ReadBack *rb, T *vnext, cudaStream_t s);
+int learned_n_params(int p, int hid);
+cudaError_t launch_learned_infer(hdg_handle *h, const float *r, const float *x, float *xout);
+cudaError_t launch_learned_forward(hdg_handle *h, const float *r, float *c);
+cudaError_t launch_learned_applyT(hdg_handle *h, const float *x, float *y);
+cudaError_t launch_learned_backward(hdg_handle *h, const float *gc, const double *coef);
+cudaError_t launch_adam(hdg_handle *h, float lr, int t);
+cudaError_t launch_normalize32(const float *src, float *dst, const double *nrm2, size_t n, cudaStream_t s);
+cudaError_t launch_to_internal32(hdg_handle *h, const float *ext, float *in);
+cudaError_t launch_to_external32(hdg_handle *h, const float *in, float *ext);
 cudaError_t launch_axpby_mixed(double *x, const float *d, const double *scale, size_t n, cudaStream_t s);
 cudaError_t launch_d2f_scaled(const double *x, float *y, const double *scale, size_t n, cudaStream_t s);
 

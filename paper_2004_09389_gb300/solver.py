@@ -138,6 +138,9 @@ class HDGSolver:
     def precond_apply_dev(self, v, z) -> None:
         L.check(self.h, self._ordered(self.lib.hdg_precond_apply_dev, L._ptr(v), L._ptr(z)))
 
+    def precond_apply32_dev(self, v, z) -> None:
+        L.check(self.h, self._ordered(self.lib.hdg_precond_apply32_dev, L._ptr(v), L._ptr(z)))
+
     def autotune(self) -> tuple:
         """Time candidate launch shapes on this handle and keep the fastest;
         returns (threads per facet-row block, Gram-Schmidt blocks, largest
@@ -145,6 +148,45 @@ class HDGSolver:
         ch = np.zeros(3, dtype=np.int32)
         L.check(self.h, self.lib.hdg_autotune(self.h, ch.ctypes.data))
         return tuple(int(v) for v in ch)
+
+    # ---------------------------------------------------------------- learned smoother
+    def learned_init(self, hidden: int = 32, capacity: int = 256, seed: int = 0) -> int:
+        n = C.c_int32()
+        L.check(self.h, self.lib.hdg_learned_init(self.h, int(hidden), int(capacity), C.c_uint64(seed), C.byref(n)))
+        self.n_learned_params = int(n.value)
+        return self.n_learned_params
+
+    def learned_collect_dev(self, r_u, r_h) -> int:
+        n = C.c_int32()
+        L.check(self.h, self._ordered(self.lib.hdg_learned_collect_dev, L._ptr(r_u), L._ptr(r_h), C.byref(n)))
+        return int(n.value)
+
+    def learned_train(self, steps: int, batch: int = 8, lr: float = 1e-3):
+        a, b = C.c_double(), C.c_double()
+        L.check(self.h, self.lib.hdg_learned_train(self.h, int(steps), int(batch), C.c_double(lr), C.byref(a),
+                                                   C.byref(b)))
+        return a.value, b.value
+
+    def learned_params(self) -> np.ndarray:
+        th = np.empty(self.n_learned_params, dtype=np.float32)
+        L.check(self.h, self.lib.hdg_learned_params(self.h, th.ctypes.data, 1))
+        return th
+
+    def set_learned_params(self, theta) -> None:
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        assert th.size == self.n_learned_params
+        L.check(self.h, self.lib.hdg_learned_params(self.h, th.ctypes.data, 0))
+
+    def learned_enable(self, on: bool = True) -> None:
+        L.check(self.h, self.lib.hdg_learned_enable(self.h, 1 if on else 0))
+
+    def learned_loss_grad_dev(self, R):
+        """R: float32 device tensor [n, n_facets, p+1]; returns (loss, gradient)."""
+        g = np.empty(self.n_learned_params, dtype=np.float32)
+        loss = C.c_double()
+        L.check(self.h, self._ordered(self.lib.hdg_learned_loss_grad_dev, L._ptr(R), int(R.shape[0]), g.ctypes.data,
+                                      C.byref(loss)))
+        return loss.value, g
 
     # ---------------------------------------------------------------- accounting
     def profile_enable(self, timing: bool = True) -> None:
