@@ -121,6 +121,12 @@ typedef struct {
                                        - tau f_K (J grad phi,grad psi)], kappa_K = 1/(1+tau^2 f_K^2);
                                    1 = as printed in Eq. coarse_problem_upwind (no rotation).
                                    Both agree when f = 0.                                  */
+    int32_t       reorth;       /* Arnoldi orthogonalisation (GMRES, Sec. 5.1 setup):
+                                   0 = one classical Gram-Schmidt pass (the solver
+                                       configuration of the paper's experiments sets no
+                                       orthogonalisation option, i.e. the library default
+                                       of classical Gram-Schmidt without refinement);
+                                   1 = classical Gram-Schmidt twice (CGS2).              */
 } hdg_params;
 
 typedef struct {
@@ -134,7 +140,7 @@ typedef struct {
 
 /* Fill *prm with the defaults: p = 1, tau = 1, g = H = 1, tau_s = sqrt(gH),
  * FP64, rtol 1e-8, restart 30, max_iter 500, 2 + 2 sweeps, omega = 2/3,
- * 2 + 2 P1 sweeps, p1_omega = 2/3, inner_rtol 1e-4, coarse_mode 0. */
+ * 2 + 2 P1 sweeps, p1_omega = 2/3, inner_rtol 1e-4, coarse_mode 0, reorth 0. */
 HDG_API void hdg_default_params(hdg_params *prm);
 
 /* Build a handle: validate and copy the mesh (facet numbering, orientation,

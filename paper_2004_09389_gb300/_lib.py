@@ -39,7 +39,8 @@ class hdg_params(C.Structure):
                 ("tau_s", C.c_double), ("f_vertex", _dp), ("precision", C.c_int32), ("rtol", C.c_double),
                 ("restart", C.c_int32), ("max_iter", C.c_int32), ("n_pre", C.c_int32), ("n_post", C.c_int32),
                 ("omega", C.c_double), ("p1_nu_pre", C.c_int32), ("p1_nu_post", C.c_int32),
-                ("p1_omega", C.c_double), ("inner_rtol", C.c_double), ("coarse_mode", C.c_int32)]
+                ("p1_omega", C.c_double), ("inner_rtol", C.c_double), ("coarse_mode", C.c_int32),
+                ("reorth", C.c_int32)]
 
 
 class hdg_solve_info(C.Structure):

@@ -120,6 +120,7 @@ std::string check_params(const hdg_params *prm) {
     if (prm->n_pre < 0 || prm->n_post < 0 || prm->p1_nu_pre < 0 || prm->p1_nu_post < 0) return "negative sweep count";
     if (!(prm->omega > 0) || !(prm->p1_omega > 0)) return "damping factors must be positive";
     if (prm->coarse_mode != 0 && prm->coarse_mode != 1) return "coarse_mode must be 0 or 1";
+    if (prm->reorth != 0 && prm->reorth != 1) return "reorth must be 0 or 1";
     if (prm->precision != HDG_FP64 && prm->precision != HDG_MIXED_FP32 && prm->precision != HDG_MIXED_BF16)
         return "unknown precision mode";
     if (prm->precision != HDG_FP64 && !(prm->inner_rtol > 0 && prm->inner_rtol < 1)) return "inner_rtol must be in (0, 1)";
@@ -432,9 +433,11 @@ cudaError_t arnoldi_step(hdg_handle *h, int j) {
     cudaError_t e;
     if ((e = precond<T>(h, vj, zj)) != cudaSuccess) return e;
     if ((e = KL(cat_apply<T>(), 1, launch_apply_t<T>(h, zj, k.w))) != cudaSuccess) return e;
-    if ((e = KL(HDG_PROF_KRYLOV, 4, launch_gs_step<T>(k.V, ld, j, k.w, W.partial, W.counter, W.nblk_gs, W.h1, W.h2,
-                                                      W.nrm2, W.Hm, ldh, W.cs, W.sn, W.sv, W.bnorm, W.rb,
-                                                      k.V + size_t(j + 1) * ld, s))) != cudaSuccess) return e;
+    const bool reorth = h->prm.reorth != 0;
+    if ((e = KL(HDG_PROF_KRYLOV, reorth ? 4 : 3,
+                launch_gs_step<T>(k.V, ld, j, k.w, W.partial, W.counter, W.nblk_gs, W.h1, W.h2, W.nrm2, W.Hm, ldh,
+                                  W.cs, W.sn, W.sv, W.bnorm, W.rb, k.V + size_t(j + 1) * ld, reorth, s))) != cudaSuccess)
+        return e;
     (void)NT;
     return cudaMemcpyAsync(W.host_rb, W.rb, sizeof(ReadBack), cudaMemcpyDeviceToHost, s);
 }
@@ -961,6 +964,7 @@ void hdg_default_params(hdg_params *prm) {
     prm->p1_omega = 2.0 / 3.0;
     prm->inner_rtol = 1e-4;
     prm->coarse_mode = 0;
+    prm->reorth = 0;
 }
 
 int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hdg_handle **out) {

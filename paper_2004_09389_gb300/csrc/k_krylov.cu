@@ -258,7 +258,8 @@ __global__ void __launch_bounds__(256) gs_update_dots_kernel(const T *V, size_t 
     dots_and_finish<T>(V4p, ld4, k, w4, n4, partial, counter, h2, &last);
 }
 
-// w -= V h2, ||w||^2; the last block forms Hessenberg column j (h1 + h2,
+// w -= V h2 (h2 null: w -= V h1, one classical Gram-Schmidt pass), ||w||^2;
+// the last block forms Hessenberg column j (h1 + h2, or h1 alone;
 // h_{j+1,j} = ||w||), applies the previous Givens rotations, forms rotation j,
 // updates the least-squares right-hand side and writes the residual
 // estimate |s_{j+1}| / ||b|| and the flags (2: breakdown, 4: NaN/Inf) to rb.
@@ -273,12 +274,12 @@ __global__ void __launch_bounds__(256) gs_update_norm_givens_kernel(const T *V, 
     const size_t ld4 = ld / (16 / sizeof(T)), n4 = n / (16 / sizeof(T));
     const V4 *V4p = reinterpret_cast<const V4 *>(V);
     V4 *w4 = reinterpret_cast<V4 *>(w);
-    block_update<T>(V4p, ld4, k, w4, n4, h2);
+    block_update<T>(V4p, ld4, k, w4, n4, h2 ? h2 : h1);
     bool last;
     dots_and_finish<T>(w4, 0, 1, w4, n4, partial, counter, nrm2, &last);
     if (!last || threadIdx.x != 0) return;
     double *col = Hm + size_t(j) * ldh;
-    for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+    for (int i = 0; i <= j; ++i) col[i] = h2 ? h1[i] + h2[i] : h1[i];
     col[j + 1] = sqrt(nrm2[0]);
     for (int i = 0; i < j; ++i) {
         const double t = cs[i] * col[i] + sn[i] * col[i + 1];
@@ -374,22 +375,22 @@ cudaError_t launch_d2f_scaled(const double *x, float *y, const double *scale, si
 template <typename T>
 cudaError_t launch_gs_step(const T *V, size_t ld, int j, T *w, double *partial, unsigned int *counter, int nblk,
                            double *h1, double *h2, double *nrm2, double *Hm, int ldh, double *cs, double *sn,
-                           double *sv, const double *bnorm, ReadBack *rb, T *vnext, cudaStream_t s) {
+                           double *sv, const double *bnorm, ReadBack *rb, T *vnext, bool reorth, cudaStream_t s) {
     const int k = j + 1;
     gs_dots_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, partial, counter, h1);
-    gs_update_dots_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, h1, partial, counter, h2);
-    gs_update_norm_givens_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, h1, h2, partial, counter, nrm2, Hm, ldh, cs,
-                                                        sn, sv, j, bnorm, rb);
+    if (reorth) gs_update_dots_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, h1, partial, counter, h2);
+    gs_update_norm_givens_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, h1, reorth ? h2 : nullptr, partial, counter,
+                                                        nrm2, Hm, ldh, cs, sn, sv, j, bnorm, rb);
     const size_t n4 = ld / (16 / sizeof(T));
     gs_scale_kernel<T><<<blocks(n4, 256), 256, 0, s>>>(w, vnext, ld, rb);
     return cudaGetLastError();
 }
 template cudaError_t launch_gs_step<float>(const float *, size_t, int, float *, double *, unsigned int *, int, double *,
                                            double *, double *, double *, int, double *, double *, double *,
-                                           const double *, ReadBack *, float *, cudaStream_t);
+                                           const double *, ReadBack *, float *, bool, cudaStream_t);
 template cudaError_t launch_gs_step<double>(const double *, size_t, int, double *, double *, unsigned int *, int,
                                             double *, double *, double *, double *, int, double *, double *, double *,
-                                            const double *, ReadBack *, double *, cudaStream_t);
+                                            const double *, ReadBack *, double *, bool, cudaStream_t);
 
 #define HDG_KRYLOV_INST(T)                                                                                      \
     template cudaError_t launch_multidot<T>(const T *, size_t, int, const T *, size_t, double *, int,           \

@@ -152,35 +152,43 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, long long limit) {
 
 __host__ __device__ constexpr size_t pad16(size_t bytes) { return (bytes + 15) / 16 * 16; }
 
+// Shared-memory addresses and sizes of one tail level.  The table lives in
+// shared memory (filled by thread 0) so that run-time level indices never
+// put per-thread pointer arrays on the stack.
+template <typename T>
+struct TailSlot {
+    T *A, *D, *cw, *x, *x2, *b, *r;
+    int32_t *rp, *col, *cp, *ci, *par;
+    int nv, nnz, nci;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
     extern __shared__ __align__(16) unsigned char tail_smem[];
     __shared__ __align__(8) uint64_t bar;
     // per level: A[nnz], dinv[nv], cw[nci], x, x2, b, r [nv] (T); rp[nv+1], col[nnz],
     // cp[nv+1], ci[nci], par[2 nv_finer] (int32), each 16-byte aligned
-    int32_t *RP[kTailMaxLevels], *COL[kTailMaxLevels], *CP[kTailMaxLevels], *CI[kTailMaxLevels], *PAR[kTailMaxLevels];
-    T *AV[kTailMaxLevels], *DV[kTailMaxLevels], *CW[kTailMaxLevels];
-    T *X[kTailMaxLevels], *X2[kTailMaxLevels], *B[kTailMaxLevels], *R[kTailMaxLevels];
-    {
+    __shared__ TailSlot<T> L[kTailMaxLevels];
+    if (threadIdx.x == 0) {
         unsigned char *q = tail_smem;
         for (int l = 0; l < a.nlev; ++l) {
-            const TailLevel &L = a.lev[l];
+            const TailLevel &G = a.lev[l];
             const int nfin = l > 0 ? a.lev[l - 1].nv : 0;
-            AV[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nnz);
-            DV[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nv);
-            CW[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nci);
-            X[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nv);
-            X2[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nv);
-            B[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nv);
-            R[l] = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * L.nv);
-            RP[l] = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(L.nv + 1));
-            COL[l] = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(L.nnz));
-            CP[l] = reinterpret_cast<int32_t *>(q); q += l > 0 ? pad16(4 * size_t(L.nv + 1)) : 0;
-            CI[l] = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(L.nci));
-            PAR[l] = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(2 * nfin));
+            TailSlot<T> &S = L[l];
+            S.nv = G.nv; S.nnz = G.nnz; S.nci = G.nci;
+            S.A = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nnz);
+            S.D = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
+            S.cw = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nci);
+            S.x = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
+            S.x2 = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
+            S.b = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
+            S.r = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
+            S.rp = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(G.nv + 1));
+            S.col = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(G.nnz));
+            S.cp = reinterpret_cast<int32_t *>(q); q += l > 0 ? pad16(4 * size_t(G.nv + 1)) : 0;
+            S.ci = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(G.nci));
+            S.par = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(2 * nfin));
         }
-    }
-    if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -188,30 +196,33 @@ __global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
     if (threadIdx.x == 0) {
         uint32_t tx = 0;
         for (int l = 0; l < a.nlev; ++l) {
-            const TailLevel &L = a.lev[l];
-            tx += pad16(sizeof(T) * L.nnz) + pad16(sizeof(T) * L.nv) + pad16(4 * size_t(L.nv + 1)) + pad16(4 * size_t(L.nnz));
-            if (l > 0) tx += pad16(sizeof(T) * L.nci) + pad16(4 * size_t(L.nv + 1)) + pad16(4 * size_t(L.nci)) +
+            const TailLevel &G = a.lev[l];
+            tx += pad16(sizeof(T) * G.nnz) + pad16(sizeof(T) * G.nv) + pad16(4 * size_t(G.nv + 1)) + pad16(4 * size_t(G.nnz));
+            if (l > 0) tx += pad16(sizeof(T) * G.nci) + pad16(4 * size_t(G.nv + 1)) + pad16(4 * size_t(G.nci)) +
                              pad16(4 * size_t(2 * a.lev[l - 1].nv));
         }
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(&bar)), "r"(tx) : "memory");
         for (int l = 0; l < a.nlev; ++l) {
-            const TailLevel &L = a.lev[l];
-            bulk_g2s(AV[l], L.A, pad16(sizeof(T) * L.nnz), &bar);
-            bulk_g2s(DV[l], L.dinv, pad16(sizeof(T) * L.nv), &bar);
-            bulk_g2s(RP[l], L.rp, pad16(4 * size_t(L.nv + 1)), &bar);
-            bulk_g2s(COL[l], L.col, pad16(4 * size_t(L.nnz)), &bar);
+            const TailLevel &G = a.lev[l];
+            const TailSlot<T> &S = L[l];
+            bulk_g2s(S.A, G.A, pad16(sizeof(T) * G.nnz), &bar);
+            bulk_g2s(S.D, G.dinv, pad16(sizeof(T) * G.nv), &bar);
+            bulk_g2s(S.rp, G.rp, pad16(4 * size_t(G.nv + 1)), &bar);
+            bulk_g2s(S.col, G.col, pad16(4 * size_t(G.nnz)), &bar);
             if (l > 0) {
-                bulk_g2s(CW[l], L.cw, pad16(sizeof(T) * L.nci), &bar);
-                bulk_g2s(CP[l], L.cp, pad16(4 * size_t(L.nv + 1)), &bar);
-                bulk_g2s(CI[l], L.ci, pad16(4 * size_t(L.nci)), &bar);
-                bulk_g2s(PAR[l], L.parent, pad16(4 * size_t(2 * a.lev[l - 1].nv)), &bar);
+                bulk_g2s(S.cw, G.cw, pad16(sizeof(T) * G.nci), &bar);
+                bulk_g2s(S.cp, G.cp, pad16(4 * size_t(G.nv + 1)), &bar);
+                bulk_g2s(S.ci, G.ci, pad16(4 * size_t(G.nci)), &bar);
+                bulk_g2s(S.par, G.parent, pad16(4 * size_t(2 * a.lev[l - 1].nv)), &bar);
             }
         }
     }
     // right-hand side of the top level with plain loads meanwhile
     {
         const T *btop = static_cast<const T *>(a.b_top);
-        for (int i = threadIdx.x; i < a.lev[0].nv; i += blockDim.x) B[0][i] = btop[i];
+        T *b0 = L[0].b;
+        const int nv0 = L[0].nv;
+        for (int i = threadIdx.x; i < nv0; i += blockDim.x) b0[i] = btop[i];
     }
     if (!bar_wait(&bar, 1ll << 22)) {
         // the copies did not complete: record it, give them one more bounded
@@ -226,60 +237,63 @@ __global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
     const int last = a.nlev - 1;
     // ---- down
     for (int l = 0; l < last; ++l) {
-        const int nv = a.lev[l].nv;
-        const int32_t *rp = RP[l], *cl = COL[l];
-        const T *A = AV[l], *D = DV[l];
-        T *x = X[l], *x2 = X2[l];
+        const int nv = L[l].nv;
+        const int32_t *rp = L[l].rp, *cl = L[l].col;
+        const T *A = L[l].A, *D = L[l].D, *b = L[l].b;
+        T *x = L[l].x, *x2 = L[l].x2, *r = L[l].r;
         if (a.nu1 == 0) {
             for (int i = tid; i < nv; i += nt) x[i] = T(0);
         } else {
-            for (int i = tid; i < nv; i += nt) x[i] = om * D[i] * B[l][i];
+            for (int i = tid; i < nv; i += nt) x[i] = om * D[i] * b[i];
         }
         __syncthreads();
         for (int k = 1; k < a.nu1; ++k) {
             for (int i = tid; i < nv; i += nt) {
                 T ax = T(0);
                 for (int q = rp[i]; q < rp[i + 1]; ++q) ax = fma(A[q], x[cl[q]], ax);
-                x2[i] = fma(om * D[i], B[l][i] - ax, x[i]);
+                x2[i] = fma(om * D[i], b[i] - ax, x[i]);
             }
             __syncthreads();
             T *t = x; x = x2; x2 = t;
         }
-        X[l] = x; X2[l] = x2;
         for (int i = tid; i < nv; i += nt) {
             T ax = T(0);
             for (int q = rp[i]; q < rp[i + 1]; ++q) ax = fma(A[q], x[cl[q]], ax);
-            R[l][i] = B[l][i] - ax;
+            r[i] = b[i] - ax;
         }
+        if (tid == 0) { L[l].x = x; L[l].x2 = x2; }   // read again only after later barriers
         __syncthreads();
-        const int ncv = a.lev[l + 1].nv;
-        const int32_t *cp = CP[l + 1], *ci = CI[l + 1];
-        const T *cw = CW[l + 1];
+        const int ncv = L[l + 1].nv;
+        const int32_t *cp = L[l + 1].cp, *ci = L[l + 1].ci;
+        const T *cw = L[l + 1].cw;
+        T *bc = L[l + 1].b;
         for (int i = tid; i < ncv; i += nt) {
             T acc = T(0);
-            for (int k = cp[i]; k < cp[i + 1]; ++k) acc = fma(cw[k], R[l][ci[k]], acc);
-            B[l + 1][i] = acc;
+            for (int k = cp[i]; k < cp[i + 1]; ++k) acc = fma(cw[k], r[ci[k]], acc);
+            bc[i] = acc;
         }
         __syncthreads();
     }
     // ---- coarsest: dense inverse
     {
         const T *inv = static_cast<const T *>(a.inv);
-        const int n = a.lev[last].nv;
+        const int n = L[last].nv;
+        const T *b = L[last].b;
+        T *x = L[last].x;
         for (int i = tid; i < n; i += nt) {
             T acc = T(0);
-            for (int j = 0; j < n; ++j) acc = fma(inv[size_t(i) * n + j], B[last][j], acc);
-            X[last][i] = acc;
+            for (int j = 0; j < n; ++j) acc = fma(inv[size_t(i) * n + j], b[j], acc);
+            x[i] = acc;
         }
         __syncthreads();
     }
     // ---- up
+    const T *ec = L[last].x;
     for (int l = last - 1; l >= 0; --l) {
-        const int nv = a.lev[l].nv;
-        const int32_t *rp = RP[l], *cl = COL[l], *par = PAR[l + 1];
-        const T *A = AV[l], *D = DV[l];
-        T *x = X[l], *x2 = X2[l];
-        const T *ec = X[l + 1];
+        const int nv = L[l].nv;
+        const int32_t *rp = L[l].rp, *cl = L[l].col, *par = L[l + 1].par;
+        const T *A = L[l].A, *D = L[l].D, *b = L[l].b;
+        T *x = L[l].x, *x2 = L[l].x2;
         for (int i = tid; i < nv; i += nt) {
             const int p0 = par[2 * i], p1 = par[2 * i + 1];
             x[i] += (p0 == p1) ? ec[p0] : T(0.5) * (ec[p0] + ec[p1]);
@@ -289,15 +303,15 @@ __global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
             for (int i = tid; i < nv; i += nt) {
                 T ax = T(0);
                 for (int q = rp[i]; q < rp[i + 1]; ++q) ax = fma(A[q], x[cl[q]], ax);
-                x2[i] = fma(om * D[i], B[l][i] - ax, x[i]);
+                x2[i] = fma(om * D[i], b[i] - ax, x[i]);
             }
             __syncthreads();
             T *t = x; x = x2; x2 = t;
         }
-        X[l] = x; X2[l] = x2;
+        ec = x;
     }
     T *xtop = static_cast<T *>(a.x_top);
-    for (int i = tid; i < a.lev[0].nv; i += nt) xtop[i] = X[0][i];
+    for (int i = tid; i < L[0].nv; i += nt) xtop[i] = ec[i];
 }
 
 }  // namespace

@@ -58,3 +58,10 @@ def test_setup_rejects_bad_arguments_without_gpu(lib_path):
     rc = lib.hdg_setup(None, ctypes.byref(prm), None, ctypes.byref(h))
     assert rc == _lib.HDG_EINVAL and not h.value
     assert b"p must be" in lib.hdg_last_error(None)
+    # the last field of hdg_params reaches the library at the offset the binding uses
+    prm = _lib.default_params()
+    assert prm.reorth == 0
+    prm.reorth = 3
+    rc = lib.hdg_setup(None, ctypes.byref(prm), None, ctypes.byref(h))
+    assert rc == _lib.HDG_EINVAL and not h.value
+    assert b"reorth must be" in lib.hdg_last_error(None)

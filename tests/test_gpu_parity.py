@@ -136,9 +136,12 @@ def test_precond_printed_coarse_form_matches_oracle(kind):
 
 
 @pytest.mark.parametrize("kind,p", CASES)
-def test_solve_and_recover_match_oracle(kind, p):
+@pytest.mark.parametrize("reorth", [0, 1])
+def test_solve_and_recover_match_oracle(kind, p, reorth):
+    """One classical Gram-Schmidt pass (reorth 0, the default) and CGS2
+    (reorth 1) both reach the oracle's solution."""
     mesh, prob, (tau, g, H, f), ru, rh = _case(kind, p)
-    s = _solver(mesh, p, tau, g, H, f, rtol=1e-13)
+    s = _solver(mesh, p, tau, g, H, f, rtol=1e-13, reorth=reorth)
     lam, info = s.solve(ru, rh)
     u, h = s.recover()
     (u0, h0), lam0 = prob.solve_condensed(ru, rh)
@@ -153,11 +156,14 @@ def test_solve_and_recover_match_oracle(kind, p):
 
 
 @pytest.mark.parametrize("kind,p", [("flat", 2), ("sphere", 2)])
-def test_iteration_count_matches_oracle(kind, p):
-    """Same algorithm on both sides (FGMRES(30) + the same V-cycle): the
-    iteration counts to rtol 1e-8 agree within one."""
+@pytest.mark.parametrize("reorth", [0, 1])
+def test_iteration_count_matches_oracle(kind, p, reorth):
+    """Same algorithm on both sides (FGMRES(30) + the same V-cycle; the
+    oracle orthogonalises by modified Gram-Schmidt, the device by classical
+    Gram-Schmidt once or twice, equal in exact arithmetic): the iteration
+    counts to rtol 1e-8 agree within one."""
     mesh, prob, (tau, g, H, f), ru, rh = _case(kind, p)
-    s = _solver(mesh, p, tau, g, H, f, rtol=1e-8)
+    s = _solver(mesh, p, tau, g, H, f, rtol=1e-8, reorth=reorth)
     _, info = s.solve(ru, rh)
     S = prob.trace_operator()
     pc = TwoLevelPreconditioner(prob, mesh, S, coarse="gmg")
@@ -184,13 +190,14 @@ def test_device_entry_points_match_host_ones():
 
 @pytest.mark.parametrize("kind,p", [("flat", 2), ("sphere", 3), ("flat", 4), ("flat", 1)])
 @pytest.mark.parametrize("mode", [1, 2])
-def test_mixed_precision(kind, p, mode):
+@pytest.mark.parametrize("reorth", [0, 1])
+def test_mixed_precision(kind, p, mode, reorth):
     """FP32 inner FGMRES + FP32 V-cycle (mode 1) or with a BF16 operator copy in
     the smoother and V-cycle residual (mode 2), with FP64 iterative refinement,
     reaches the FP64 residual target; stated tolerance vs the oracle: 1e-8
     relative at rtol 1e-10 (the trace operator's condition number here is < 100)."""
     mesh, prob, (tau, g, H, f), ru, rh = _case(kind, p)
-    s = _solver(mesh, p, tau, g, H, f, rtol=1e-10, precision=mode)
+    s = _solver(mesh, p, tau, g, H, f, rtol=1e-10, precision=mode, reorth=reorth)
     lam, info = s.solve(ru, rh)
     u, h = s.recover()
     (u0, h0), lam0 = prob.solve_condensed(ru, rh)
@@ -232,7 +239,7 @@ def test_iteration_cap_reports_noconv():
 def test_invalid_arguments():
     from paper_2004_09389_gb300 import HDGError
     mesh, prob, (tau, g, H, f), ru, rh = _case("flat", 1)
-    for kw in ({"p": 5}, {"tau": -1.0}, {"restart": 0}):
+    for kw in ({"p": 5}, {"tau": -1.0}, {"restart": 0}, {"reorth": 2}):
         args = dict(p=1, tau=tau)
         args.update(kw)
         with pytest.raises(HDGError) as ei:
