@@ -235,7 +235,7 @@ size_t hdg::tail_smem_bytes(const std::vector<DevLevel> &lev, int first, size_t 
         const size_t nv = lev[l].nv, nnz = lev[l].nnz, nci = top ? 0 : lev[l].nci;
         const size_t nfin = top ? 0 : lev[l - 1].nv;
         bytes += pad(tsz * nnz) + pad(tsz * nv) + pad(tsz * nci) + 4 * pad(tsz * nv);
-        bytes += pad(4 * (nv + 1)) + pad(4 * nnz) + (top ? 0 : pad(4 * (nv + 1))) + pad(4 * nci) + pad(4 * 2 * nfin);
+        bytes += pad(4 * nnz) + (top ? 0 : pad(4 * (nv + 1))) + pad(4 * nci) + pad(4 * 2 * nfin);
     }
     return bytes;
 }
@@ -285,8 +285,8 @@ cudaError_t p1_cycle(hdg_handle *h, T **result) {
         for (int l = ts; l < nlev; ++l) {
             DevLevel &L = h->lev[l];
             TailLevel &t = a.lev[l - ts];
-            t.nv = L.nv; t.nnz = L.nnz; t.nci = (l > ts) ? L.nci : 0;
-            t.rp = L.row_ptr; t.col = L.col; t.A = levA<T>(L); t.dinv = levD<T>(L);
+            t.nv = L.nv; t.nnz = L.nnz; t.nci = (l > ts) ? L.nci : 0; t.width = L.width;
+            t.col = L.col; t.A = levA<T>(L); t.dinv = levD<T>(L);
             t.cp = L.child_ptr; t.ci = L.child_idx; t.parent = L.parent;
             t.cw = sizeof(T) == 4 ? static_cast<const void *>(L.child_w32) : static_cast<const void *>(L.child_w);
         }
@@ -661,7 +661,7 @@ void free_handle(hdg_handle *h) {
     dfree(h->d_Dinv); dfree(h->d_Sval32); dfree(h->d_Dinv32); dfree(h->d_Sval16); dfree(h->d_status); dfree(h->d_coarse_inv);
     dfree(h->d_coarse_inv32); dfree(h->d_coarse_work);
     for (auto &L : h->lev) {
-        dfree(L.row_ptr); dfree(L.col); dfree(L.diag); dfree(L.elem); dfree(L.fK); dfree(L.contrib_ptr); dfree(L.contrib); dfree(L.A); dfree(L.dinv);
+        dfree(L.col); dfree(L.diag); dfree(L.elem); dfree(L.fK); dfree(L.contrib_ptr); dfree(L.contrib); dfree(L.A); dfree(L.dinv);
         dfree(L.A32); dfree(L.dinv32); dfree(L.parent); dfree(L.child_ptr); dfree(L.child_idx); dfree(L.child_w); dfree(L.child_w32);
         dfree(L.x); dfree(L.x2); dfree(L.b); dfree(L.r); dfree(L.x32); dfree(L.x232); dfree(L.b32); dfree(L.r32);
     }
@@ -778,11 +778,11 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
         const HostLevel &hl = hm.levels[l];
         DevLevel &L = h->lev[l];
         L.nv = hl.nv;
+        L.width = hl.width;
         L.nnz = int(hl.col.size());
         if (L.nnz == 0 || int(hl.diag.size()) != L.nv) return fail(h, HDG_EINVAL, "empty P1 level operator");
         for (int v = 0; v < L.nv; ++v)
             if (hl.diag[v] < 0) return fail(h, HDG_EINVAL, "P1 vertex without a cell");
-        TRY(upload(&L.row_ptr, hl.row_ptr, s));
         TRY(upload(&L.col, hl.col, s));
         TRY(upload(&L.diag, hl.diag, s));
         TRY(upload(&L.elem, hl.elem, s));

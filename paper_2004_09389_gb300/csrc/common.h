@@ -49,10 +49,13 @@ struct HostLevel {
     int nv = 0, nc = 0;
     std::vector<double> X;        // [nc][3][2] local 2-D vertex coordinates
     std::vector<int32_t> cells;   // [nc][3]
-    // CSR structure of the level operator (sorted columns) and its assembly data
-    std::vector<int32_t> row_ptr, col, diag;
+    // padded row-major ELL structure of the level operator: width W (a multiple
+    // of 4), slot q of row v at v * W + q (columns increasing, unused slots
+    // point at v with value 0)
+    int width = 0;
+    std::vector<int32_t> col, diag;     // [W * nv], [nv] (slot of the diagonal)
     std::vector<double> elem;           // [nc][27]: 3x3 mass | stiffness | skew per cell
-    std::vector<int32_t> contrib_ptr;   // [nnz+1]
+    std::vector<int32_t> contrib_ptr;   // [W * nv + 1]
     std::vector<int32_t> contrib;       // cell*9 + a*3 + b, in cell order per entry
     // transfer to the next finer level (empty on the fine level)
     std::vector<int32_t> parent;      // [nv_finer][2]
@@ -80,8 +83,8 @@ std::string build_host_mesh(const hdg_mesh_desc *desc, HostMesh &hm);
 
 // ---------------------------------------------------------------- device data
 struct DevLevel {
-    int nv = 0, nnz = 0;
-    int32_t *row_ptr = nullptr, *col = nullptr, *diag = nullptr;
+    int nv = 0, nnz = 0, width = 0;                     // nnz = width * nv (padded ELL slots)
+    int32_t *col = nullptr, *diag = nullptr;
     double *elem = nullptr, *fK = nullptr, *A = nullptr, *dinv = nullptr;
     int32_t *contrib_ptr = nullptr, *contrib = nullptr;
     float *A32 = nullptr, *dinv32 = nullptr;
@@ -129,8 +132,8 @@ constexpr int kTailMaxLevels = 8;
 constexpr int kTailMaxVertices = 1024;     // default largest level run inside the tail kernel
 constexpr size_t kTailSmemMax = 226 * 1024; // dynamic shared memory limit of the tail kernel
 struct TailLevel {
-    int nv, nnz, nci;
-    const int32_t *rp, *col;            // CSR of the level operator
+    int nv, nnz, nci, width;            // nnz = width * nv
+    const int32_t *col;                 // padded ELL columns of the level operator
     const void *A, *dinv;               // values in the solve precision
     const int32_t *cp, *ci;             // restriction into this level (children in the finer level)
     const void *cw;                     // child weights in the solve precision

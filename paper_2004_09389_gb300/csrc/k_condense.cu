@@ -303,15 +303,14 @@ __global__ void p1_dinv_kernel(int nv, const int32_t *__restrict__ diag, const d
     if (i < nv) dinv[i] = 1.0 / A[diag[i]];
 }
 
-// dense copy of a CSR matrix (n <= 1024), then in-place Gauss-Jordan inverse with
-// partial pivoting by one CTA.
-__global__ void csr_to_dense_kernel(int n, const int32_t *row_ptr, const int32_t *col, const double *A,
-                                    double *D) {
+// dense copy of a padded ELL matrix (n <= 1024; unused slots add 0 to the
+// diagonal), then in-place Gauss-Jordan inverse with partial pivoting by one CTA.
+__global__ void ell_to_dense_kernel(int n, int width, const int32_t *col, const double *A, double *D) {
     const int r = blockIdx.x;
     for (int c = threadIdx.x; c < n; c += blockDim.x) D[size_t(r) * n + c] = 0.0;
     __syncthreads();
     if (threadIdx.x == 0)
-        for (int k = row_ptr[r]; k < row_ptr[r + 1]; ++k) D[size_t(r) * n + col[k]] = A[k];
+        for (int q = 0; q < width; ++q) D[size_t(r) * n + col[size_t(r) * width + q]] += A[size_t(r) * width + q];
 }
 
 __global__ void dense_inverse_kernel(int n, double *Aw, double *inv, int32_t *status) {
@@ -430,7 +429,7 @@ cudaError_t launch_p1_assemble(hdg_handle *h, DevLevel &L, double tau, double gH
 }
 
 cudaError_t launch_dense_inverse(hdg_handle *h, const DevLevel &L, double *work, double *inv, int n) {
-    csr_to_dense_kernel<<<n, 128, 0, h->stream>>>(n, L.row_ptr, L.col, L.A, work);
+    ell_to_dense_kernel<<<n, 128, 0, h->stream>>>(n, L.width, L.col, L.A, work);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dense_inverse_kernel<<<1, 1024, 0, h->stream>>>(n, work, inv, h->d_status);

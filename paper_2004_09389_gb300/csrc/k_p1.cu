@@ -1,7 +1,9 @@
 // Geometric V-cycle on the nested P1 levels for the coarse problem of the
 // two-level method (Eq. coarse_problem_upwind): damped Jacobi smoothing with
-// CSR operators, restriction by the transpose of the midpoint prolongation,
-// and a dense inverse on the coarsest level.
+// the level operators in padded row-major ELL form (width W a multiple of 4,
+// slot q of row i at i * W + q), restriction by the transpose of the midpoint
+// prolongation, and a dense inverse on the coarsest level.  A row's columns
+// and values load as 16-byte vectors; its W products are summed in slot order.
 #include "common.h"
 
 namespace hdg {
@@ -11,30 +13,56 @@ namespace {
 inline unsigned blocks(size_t n, int bs) { return unsigned((n + bs - 1) / bs); }
 
 // x_out = x + omega D^-1 (b - A x); first sweep (x = 0): x_out = omega D^-1 b
+// four consecutive values of a row as one 16-byte load (two for FP64)
+__device__ __forceinline__ void load4(const float *p, float v[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double *p, double v[4]) {
+    const double2 t0 = reinterpret_cast<const double2 *>(p)[0], t1 = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+}
+
+// (A x)_i for a padded row-major ELL operator of width W (a multiple of 4)
 template <typename T>
-__global__ void jacobi_kernel(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                              const T *__restrict__ A, const T *__restrict__ dinv, const T *__restrict__ b,
-                              const T *__restrict__ x, T *__restrict__ xout, T omega, int first) {
+__device__ __forceinline__ T ell_row(int i, int W, const int32_t *__restrict__ col, const T *__restrict__ A,
+                                     const T *__restrict__ x) {
+    const int32_t *c = col + size_t(i) * W;
+    const T *a = A + size_t(i) * W;
+    T ax = T(0);
+#pragma unroll 2
+    for (int q = 0; q < W; q += 4) {
+        const int4 cc = *reinterpret_cast<const int4 *>(c + q);
+        T av[4];
+        load4(a + q, av);
+        ax = fma(av[0], x[cc.x], ax);
+        ax = fma(av[1], x[cc.y], ax);
+        ax = fma(av[2], x[cc.z], ax);
+        ax = fma(av[3], x[cc.w], ax);
+    }
+    return ax;
+}
+
+template <typename T>
+__global__ void jacobi_kernel(int n, int W, const int32_t *__restrict__ col, const T *__restrict__ A,
+                              const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x,
+                              T *__restrict__ xout, T omega, int first) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (first) {
         xout[i] = omega * dinv[i] * b[i];
         return;
     }
-    T ax = T(0);
-    for (int k = rp[i]; k < rp[i + 1]; ++k) ax = fma(A[k], x[col[k]], ax);
+    const T ax = ell_row(i, W, col, A, x);
     xout[i] = fma(omega * dinv[i], b[i] - ax, x[i]);
 }
 
 template <typename T>
-__global__ void residual_kernel(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                const T *__restrict__ A, const T *__restrict__ b, const T *__restrict__ x,
-                                T *__restrict__ r) {
+__global__ void residual_kernel(int n, int W, const int32_t *__restrict__ col, const T *__restrict__ A,
+                                const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ r) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    T ax = T(0);
-    for (int k = rp[i]; k < rp[i + 1]; ++k) ax = fma(A[k], x[col[k]], ax);
-    r[i] = b[i] - ax;
+    r[i] = b[i] - ell_row(i, W, col, A, x);
 }
 
 template <typename T>
@@ -77,7 +105,7 @@ __global__ void dense_apply_kernel(const T *__restrict__ inv, int n, const T *__
 template <typename T>
 __global__ void __launch_bounds__(256) down_kernel(int nc, const int32_t *__restrict__ cp,
                                                    const int32_t *__restrict__ ci, const T *__restrict__ cw,
-                                                   const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                                   int nf, int W, const int32_t *__restrict__ col,
                                                    const T *__restrict__ A, const T *__restrict__ bf,
                                                    const T *__restrict__ xf, const T *__restrict__ dinv_c, T omega,
                                                    T *__restrict__ bc, T *__restrict__ xc) {
@@ -87,9 +115,7 @@ __global__ void __launch_bounds__(256) down_kernel(int nc, const int32_t *__rest
     if (valid) {
         for (int k = cp[gid] + lane; k < cp[gid + 1]; k += 8) {
             const int f = ci[k];
-            T ax = T(0);
-            for (int q = rp[f]; q < rp[f + 1]; ++q) ax = fma(A[q], xf[col[q]], ax);
-            acc = fma(cw[k], bf[f] - ax, acc);
+            acc = fma(cw[k], bf[f] - ell_row(f, W, col, A, xf), acc);
         }
     }
     acc += __shfl_xor_sync(0xffffffffu, acc, 4);
@@ -104,17 +130,27 @@ __global__ void __launch_bounds__(256) down_kernel(int nc, const int32_t *__rest
 // Going up one level, fused: x' = x + P e_c (midpoint prolongation, formed on
 // the fly for every column) followed by one damped Jacobi sweep on x'.
 template <typename T>
-__global__ void up_kernel(int nf, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                          const T *__restrict__ A, const T *__restrict__ dinv, const T *__restrict__ b,
-                          const T *__restrict__ x, const int32_t *__restrict__ parent, const T *__restrict__ ec,
-                          T *__restrict__ xout, T omega) {
+__global__ void up_kernel(int nf, int W, const int32_t *__restrict__ col, const T *__restrict__ A,
+                          const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x,
+                          const int32_t *__restrict__ parent, const T *__restrict__ ec, T *__restrict__ xout,
+                          T omega) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
     T ax = T(0);
-    for (int q = rp[i]; q < rp[i + 1]; ++q) {
-        const int j = col[q], a = parent[2 * j], bb = parent[2 * j + 1];
-        const T pj = (a == bb) ? ec[a] : T(0.5) * (ec[a] + ec[bb]);
-        ax = fma(A[q], x[j] + pj, ax);
+    const int32_t *c = col + size_t(i) * W;
+    const T *arow = A + size_t(i) * W;
+#pragma unroll 2
+    for (int q = 0; q < W; q += 4) {
+        const int4 cc = *reinterpret_cast<const int4 *>(c + q);
+        T av[4];
+        load4(arow + q, av);
+        const int js[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = js[u], a = parent[2 * j], bb = parent[2 * j + 1];
+            const T pj = (a == bb) ? ec[a] : T(0.5) * (ec[a] + ec[bb]);
+            ax = fma(av[u], x[j] + pj, ax);
+        }
     }
     const int a = parent[2 * i], bb = parent[2 * i + 1];
     const T xi = x[i] + ((a == bb) ? ec[a] : T(0.5) * (ec[a] + ec[bb]));
@@ -158,15 +194,15 @@ __host__ __device__ constexpr size_t pad16(size_t bytes) { return (bytes + 15) /
 template <typename T>
 struct TailSlot {
     T *A, *D, *cw, *x, *x2, *b, *r;
-    int32_t *rp, *col, *cp, *ci, *par;
-    int nv, nnz, nci;
+    int32_t *col, *cp, *ci, *par;
+    int nv, nnz, nci, W;
 };
 
 template <typename T>
-__global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
+__global__ void __launch_bounds__(1024, 1) tail_kernel(TailArgs a) {
     extern __shared__ __align__(16) unsigned char tail_smem[];
     __shared__ __align__(8) uint64_t bar;
-    // per level: A[nnz], dinv[nv], cw[nci], x, x2, b, r [nv] (T); rp[nv+1], col[nnz],
+    // per level: A[nnz], dinv[nv], cw[nci], x, x2, b, r [nv] (T); col[nnz],
     // cp[nv+1], ci[nci], par[2 nv_finer] (int32), each 16-byte aligned
     __shared__ TailSlot<T> L[kTailMaxLevels];
     if (threadIdx.x == 0) {
@@ -175,7 +211,7 @@ __global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
             const TailLevel &G = a.lev[l];
             const int nfin = l > 0 ? a.lev[l - 1].nv : 0;
             TailSlot<T> &S = L[l];
-            S.nv = G.nv; S.nnz = G.nnz; S.nci = G.nci;
+            S.nv = G.nv; S.nnz = G.nnz; S.nci = G.nci; S.W = G.width;
             S.A = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nnz);
             S.D = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
             S.cw = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nci);
@@ -183,7 +219,6 @@ __global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
             S.x2 = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
             S.b = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
             S.r = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
-            S.rp = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(G.nv + 1));
             S.col = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(G.nnz));
             S.cp = reinterpret_cast<int32_t *>(q); q += l > 0 ? pad16(4 * size_t(G.nv + 1)) : 0;
             S.ci = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(G.nci));
@@ -197,7 +232,7 @@ __global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
         uint32_t tx = 0;
         for (int l = 0; l < a.nlev; ++l) {
             const TailLevel &G = a.lev[l];
-            tx += pad16(sizeof(T) * G.nnz) + pad16(sizeof(T) * G.nv) + pad16(4 * size_t(G.nv + 1)) + pad16(4 * size_t(G.nnz));
+            tx += pad16(sizeof(T) * G.nnz) + pad16(sizeof(T) * G.nv) + pad16(4 * size_t(G.nnz));
             if (l > 0) tx += pad16(sizeof(T) * G.nci) + pad16(4 * size_t(G.nv + 1)) + pad16(4 * size_t(G.nci)) +
                              pad16(4 * size_t(2 * a.lev[l - 1].nv));
         }
@@ -207,7 +242,6 @@ __global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
             const TailSlot<T> &S = L[l];
             bulk_g2s(S.A, G.A, pad16(sizeof(T) * G.nnz), &bar);
             bulk_g2s(S.D, G.dinv, pad16(sizeof(T) * G.nv), &bar);
-            bulk_g2s(S.rp, G.rp, pad16(4 * size_t(G.nv + 1)), &bar);
             bulk_g2s(S.col, G.col, pad16(4 * size_t(G.nnz)), &bar);
             if (l > 0) {
                 bulk_g2s(S.cw, G.cw, pad16(sizeof(T) * G.nci), &bar);
@@ -237,8 +271,8 @@ __global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
     const int last = a.nlev - 1;
     // ---- down
     for (int l = 0; l < last; ++l) {
-        const int nv = L[l].nv;
-        const int32_t *rp = L[l].rp, *cl = L[l].col;
+        const int nv = L[l].nv, W = L[l].W;
+        const int32_t *cl = L[l].col;
         const T *A = L[l].A, *D = L[l].D, *b = L[l].b;
         T *x = L[l].x, *x2 = L[l].x2, *r = L[l].r;
         if (a.nu1 == 0) {
@@ -248,19 +282,11 @@ __global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
         }
         __syncthreads();
         for (int k = 1; k < a.nu1; ++k) {
-            for (int i = tid; i < nv; i += nt) {
-                T ax = T(0);
-                for (int q = rp[i]; q < rp[i + 1]; ++q) ax = fma(A[q], x[cl[q]], ax);
-                x2[i] = fma(om * D[i], b[i] - ax, x[i]);
-            }
+            for (int i = tid; i < nv; i += nt) x2[i] = fma(om * D[i], b[i] - ell_row(i, W, cl, A, x), x[i]);
             __syncthreads();
             T *t = x; x = x2; x2 = t;
         }
-        for (int i = tid; i < nv; i += nt) {
-            T ax = T(0);
-            for (int q = rp[i]; q < rp[i + 1]; ++q) ax = fma(A[q], x[cl[q]], ax);
-            r[i] = b[i] - ax;
-        }
+        for (int i = tid; i < nv; i += nt) r[i] = b[i] - ell_row(i, W, cl, A, x);
         if (tid == 0) { L[l].x = x; L[l].x2 = x2; }   // read again only after later barriers
         __syncthreads();
         const int ncv = L[l + 1].nv;
@@ -290,8 +316,8 @@ __global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
     // ---- up
     const T *ec = L[last].x;
     for (int l = last - 1; l >= 0; --l) {
-        const int nv = L[l].nv;
-        const int32_t *rp = L[l].rp, *cl = L[l].col, *par = L[l + 1].par;
+        const int nv = L[l].nv, W = L[l].W;
+        const int32_t *cl = L[l].col, *par = L[l + 1].par;
         const T *A = L[l].A, *D = L[l].D, *b = L[l].b;
         T *x = L[l].x, *x2 = L[l].x2;
         for (int i = tid; i < nv; i += nt) {
@@ -300,11 +326,7 @@ __global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
         }
         __syncthreads();
         for (int k = 0; k < a.nu2; ++k) {
-            for (int i = tid; i < nv; i += nt) {
-                T ax = T(0);
-                for (int q = rp[i]; q < rp[i + 1]; ++q) ax = fma(A[q], x[cl[q]], ax);
-                x2[i] = fma(om * D[i], b[i] - ax, x[i]);
-            }
+            for (int i = tid; i < nv; i += nt) x2[i] = fma(om * D[i], b[i] - ell_row(i, W, cl, A, x), x[i]);
             __syncthreads();
             T *t = x; x = x2; x2 = t;
         }
@@ -319,12 +341,12 @@ __global__ void __launch_bounds__(1024) tail_kernel(TailArgs a) {
 template <typename T>
 cudaError_t launch_p1_jacobi(const DevLevel &L, const T *A, const T *dinv, const T *b, const T *x, T *xout, T omega,
                              bool first, cudaStream_t s) {
-    jacobi_kernel<T><<<blocks(L.nv, 256), 256, 0, s>>>(L.nv, L.row_ptr, L.col, A, dinv, b, x, xout, omega, first ? 1 : 0);
+    jacobi_kernel<T><<<blocks(L.nv, 256), 256, 0, s>>>(L.nv, L.width, L.col, A, dinv, b, x, xout, omega, first ? 1 : 0);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_p1_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, cudaStream_t s) {
-    residual_kernel<T><<<blocks(L.nv, 256), 256, 0, s>>>(L.nv, L.row_ptr, L.col, A, b, x, r);
+    residual_kernel<T><<<blocks(L.nv, 256), 256, 0, s>>>(L.nv, L.width, L.col, A, b, x, r);
     return cudaGetLastError();
 }
 template <typename T>
@@ -349,14 +371,14 @@ cudaError_t launch_p1_down(const DevLevel &fine, const DevLevel &coarse, const T
                            const T *dinv_c, T omega, T *b_c, T *x_c, cudaStream_t s) {
     const T *cw = sizeof(T) == 4 ? reinterpret_cast<const T *>(coarse.child_w32) : reinterpret_cast<const T *>(coarse.child_w);
     down_kernel<T><<<blocks(size_t(coarse.nv) * 8, 256), 256, 0, s>>>(coarse.nv, coarse.child_ptr, coarse.child_idx, cw,
-                                                                      fine.row_ptr, fine.col, A_f, b_f, x_f, dinv_c,
+                                                                      fine.nv, fine.width, fine.col, A_f, b_f, x_f, dinv_c,
                                                                       omega, b_c, x_c);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_p1_up(const DevLevel &fine, const DevLevel &coarse, const T *A_f, const T *dinv_f, const T *b_f,
                          const T *x_f, const T *ec, T *xout, T omega, cudaStream_t s) {
-    up_kernel<T><<<blocks(fine.nv, 256), 256, 0, s>>>(fine.nv, fine.row_ptr, fine.col, A_f, dinv_f, b_f, x_f,
+    up_kernel<T><<<blocks(fine.nv, 256), 256, 0, s>>>(fine.nv, fine.width, fine.col, A_f, dinv_f, b_f, x_f,
                                                       coarse.parent, ec, xout, omega);
     return cudaGetLastError();
 }

@@ -65,11 +65,16 @@ std::string check_level(const hdg_mesh_level &L, const char *what) {
     return "";
 }
 
-// P1 element data on one level and the CSR structure of the level operator:
+// P1 element data on one level and the structure of the level operator:
 // per cell the 3x3 mass, stiffness (grad L_b, grad L_a) and skew
 // (J grad L_b, grad L_a) matrices (J the rotation by 90 degrees in the cell's
-// plane), and for every CSR entry the list of (cell, a, b) that contribute, in
-// cell order, so the device sums each entry in a fixed order.
+// plane).  The operator is stored in a padded row-major ELL layout: width W =
+// the longest row rounded up to a multiple of 4 (rows start on 16-byte
+// boundaries and load as 16-byte vectors); slot q of row v sits at v * W + q;
+// row v lists its columns in increasing order in slots 0..len-1 and points the
+// remaining slots at v itself with no contributions (value 0).  Every slot has
+// the list of (cell, a, b) that contribute to it, in cell order, so the device
+// sums each entry in a fixed order.
 void p1_matrices(HostLevel &hl) {
     hl.elem.assign(size_t(hl.nc) * 27, 0.0);
     std::vector<std::vector<std::pair<int, int>>> rows(hl.nv);   // (column, contribution code)
@@ -95,23 +100,40 @@ void p1_matrices(HostLevel &hl) {
                 rows[hl.cells[3 * K + a]].push_back({hl.cells[3 * K + b], K * 9 + ab});
             }
     }
-    hl.row_ptr.assign(hl.nv + 1, 0);
-    hl.col.clear(); hl.diag.assign(hl.nv, -1);
-    hl.contrib_ptr.assign(1, 0);
-    hl.contrib.clear();
+    // merge equal columns: per row the distinct columns and their contribution ranges
+    std::vector<std::vector<int>> cols(hl.nv);
+    std::vector<std::vector<std::vector<int>>> codes(hl.nv);
+    int W = 1;
     for (int v = 0; v < hl.nv; ++v) {
         auto &r = rows[v];
         std::stable_sort(r.begin(), r.end(), [](auto &a, auto &b) { return a.first < b.first; });
         for (size_t k = 0; k < r.size();) {
             size_t k2 = k;
-            if (r[k].first == v) hl.diag[v] = int(hl.col.size());
-            hl.col.push_back(r[k].first);
-            while (k2 < r.size() && r[k2].first == r[k].first) hl.contrib.push_back(r[k2++].second);
-            hl.contrib_ptr.push_back(int(hl.contrib.size()));
+            cols[v].push_back(r[k].first);
+            codes[v].emplace_back();
+            while (k2 < r.size() && r[k2].first == r[k].first) codes[v].back().push_back(r[k2++].second);
             k = k2;
         }
-        hl.row_ptr[v + 1] = int(hl.col.size());
+        W = std::max(W, int(cols[v].size()));
     }
+    W = (W + 3) / 4 * 4;
+    hl.width = W;
+    hl.col.assign(size_t(W) * hl.nv, 0);
+    hl.diag.assign(hl.nv, -1);
+    hl.contrib_ptr.assign(1, 0);
+    hl.contrib.clear();
+    for (int v = 0; v < hl.nv; ++v)
+        for (int q = 0; q < W; ++q) {
+            const size_t slot = size_t(v) * W + q;
+            if (q < int(cols[v].size())) {
+                hl.col[slot] = cols[v][q];
+                if (cols[v][q] == v) hl.diag[v] = int(slot);
+                for (int c : codes[v][q]) hl.contrib.push_back(c);
+            } else {
+                hl.col[slot] = v;
+            }
+            hl.contrib_ptr.push_back(int(hl.contrib.size()));
+        }
 }
 
 }  // namespace
