@@ -534,9 +534,11 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
 
 // Full FGMRES(m) on S x = b in precision T; stops on the true residual (FP64
 // mode) or on the Arnoldi estimate (inner FP32 solves).  x must hold the
-// initial guess.
+// initial guess; with x_zero (x = 0 on entry) the first residual is b itself
+// and its norm is ||b||, so neither is recomputed.
 template <typename T>
-int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_residual, hdg_solve_info &info) {
+int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_residual, bool x_zero,
+           hdg_solve_info &info) {
     Workspace &W = *h->ws;
     KSpace<T> &k = kspace<T>(h);
     cudaStream_t s = h->stream;
@@ -556,12 +558,17 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
     TRY(cudaMemcpyAsync(W.bnorm, W.host_buf + 4, sizeof(double), cudaMemcpyHostToDevice, s));
     TRY(cudaStreamSynchronize(s));
     int total = 0;
-    for (;;) {
-        // r = b - S x into V[0]
-        TRY(KL(cat_res<T>(), 1, launch_residual_t<T>(h, b, x, k.V, false)));
-        double beta;
-        rc = norm_host<T>(h, k.V, beta);
-        if (rc) return rc;
+    for (bool first = true;; first = false) {
+        // r = b - S x into V[0] (r = b for a zero initial guess)
+        const T *r0 = k.V;
+        double beta = bnorm;
+        if (first && x_zero) {
+            r0 = b;
+        } else {
+            TRY(KL(cat_res<T>(), 1, launch_residual_t<T>(h, b, x, k.V, false)));
+            rc = norm_host<T>(h, k.V, beta);
+            if (rc) return rc;
+        }
         const double rel = beta / bnorm;
         info.true_rel_res = rel;
         if (!std::isfinite(rel)) return fail(h, HDG_ENAN, "NaN or Inf in the Krylov iteration");
@@ -569,7 +576,7 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
         if (total >= max_it) return fail(h, HDG_ENOCONV, "maximum number of iterations reached");
         W.host_buf[1] = beta;
         TRY(cudaMemcpyAsync(W.scal, W.host_buf + 1, sizeof(double), cudaMemcpyHostToDevice, s));
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_scale_copy<T>(k.V, k.V, W.scal, W.NT, s)));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_scale_copy<T>(r0, k.V, W.scal, W.NT, s)));
         int done, flag;
         double est;
         rc = fgmres_cycle<T>(h, x, beta, bnorm, rtol, max_it - total, done, est, flag);
@@ -611,10 +618,16 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info)
     if (bnorm == 0.0) return HDG_OK;
     int total = 0;
     for (int outer = 0;; ++outer) {
-        TRY(KL(HDG_PROF_RESIDUAL64, 1, launch_residual_t<double>(h, g, x, W.r, false)));
-        double beta;
-        rc = norm_host<double>(h, W.r, beta);
-        if (rc) return rc;
+        // r = g - S x in FP64 (r = g while x is still zero)
+        const double *r = W.r;
+        double beta = bnorm;
+        if (outer == 0) {
+            r = g;
+        } else {
+            TRY(KL(HDG_PROF_RESIDUAL64, 1, launch_residual_t<double>(h, g, x, W.r, false)));
+            rc = norm_host<double>(h, W.r, beta);
+            if (rc) return rc;
+        }
         info.true_rel_res = beta / bnorm;
         info.outer = outer;
         if (!std::isfinite(beta)) return fail(h, HDG_ENAN, "NaN or Inf in the refinement");
@@ -624,11 +637,11 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info)
         // b32 = r / ||r||, solve S d = b32 in FP32, x += ||r|| d
         W.host_buf[2] = beta;
         TRY(cudaMemcpyAsync(W.beta, W.host_buf + 2, sizeof(double), cudaMemcpyHostToDevice, s));
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_d2f_scaled(W.r, k.b, W.beta, W.NT, s)));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_d2f_scaled(r, k.b, W.beta, W.NT, s)));
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<float>(k.x, 0.0f, W.NT, s)));
         hdg_solve_info inner{};
         const double inner_tol = std::max(h->prm.inner_rtol, 0.5 * h->prm.rtol * bnorm / beta);
-        rc = fgmres<float>(h, k.b, k.x, inner_tol, h->prm.max_iter - total, false, inner);
+        rc = fgmres<float>(h, k.b, k.x, inner_tol, h->prm.max_iter - total, false, true, inner);
         if (rc && rc != HDG_ENOCONV) return rc;
         total += inner.iters;
         info.iters = total;
@@ -836,7 +849,9 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(dalloc(&W.ycell, N * m));
     const size_t mm = W.m;
     W.ld = (W.NT + 3) / 4 * 4;
-    W.nblk_gs = int(std::min<size_t>(std::max<size_t>((W.ld / 4 + 1023) / 1024, 1), 304));
+    // one 16-byte group of w per thread (enough loads in flight for the few-vector
+    // steps at the start of a cycle), at most 8 blocks of 256 per SM of a GB300
+    W.nblk_gs = int(std::min<size_t>(std::max<size_t>((W.ld / 4 + 255) / 256, 1), kMaxGsBlocks));
     if (!mixed) {
         TRY(dalloc(&W.k64.V, (mm + 1) * W.ld));
         TRY(dalloc(&W.k64.Z, mm * W.ld));
@@ -878,7 +893,9 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     }
     TRY(dalloc(&W.beta, 1));
     TRY(dalloc(&W.y, mm + 1));
-    TRY(dalloc(&W.partial, (mm + 1) * size_t(std::max(W.nchunk, 608))));
+    // partial sums: (m + 1) vectors x the largest grid of the multi-dot (nchunk) or
+    // of the Gram-Schmidt kernels (nblk_gs, or up to 1216 blocks after autotuning)
+    TRY(dalloc(&W.partial, (mm + 1) * size_t(std::max({W.nchunk, W.nblk_gs, kMaxGsBlocks}))));
     TRY(dalloc(&W.counter, 1));
     TRY(cudaMemsetAsync(W.counter, 0, sizeof(unsigned int), s));
     TRY(dalloc(&W.rb, 1));
@@ -916,7 +933,7 @@ int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solv
     int rc;
     if (h->prm.precision == HDG_FP64) {
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<double>(W.x, 0.0, W.NT, s)));
-        rc = fgmres<double>(h, W.g, W.x, h->prm.rtol, h->prm.max_iter, true, info);
+        rc = fgmres<double>(h, W.g, W.x, h->prm.rtol, h->prm.max_iter, true, true, info);
     } else {
         rc = solve_mixed(h, W.g, W.x, info);
     }
@@ -1274,7 +1291,7 @@ int hdg_autotune(hdg_handle *h, int32_t *choice) {
     // blocks of the fused Gram-Schmidt kernels
     int best_nb = W.nblk_gs;
     best_t = 1e30f;
-    for (int nb : {152, 304, 608}) {
+    for (int nb : {152, 304, 608, kMaxGsBlocks}) {
         W.nblk_gs = nb;
         if ((rc = time_step(t))) return rc;
         if (t < best_t) { best_t = t; best_nb = nb; }

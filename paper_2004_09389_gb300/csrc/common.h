@@ -128,6 +128,7 @@ struct ReadBack {
 };
 
 // levels of the single-CTA V-cycle tail (k_p1.cu)
+constexpr int kMaxGsBlocks = 1216;     // largest grid of the fused Gram-Schmidt kernels (8 x 152 SMs)
 constexpr int kTailMaxLevels = 8;
 constexpr int kTailMaxVertices = 1024;     // default largest level run inside the tail kernel
 constexpr size_t kTailSmemMax = 226 * 1024; // dynamic shared memory limit of the tail kernel

@@ -63,12 +63,22 @@ __global__ void __launch_bounds__(256) multi_axpy_kernel(T *__restrict__ w, cons
     w[idx] = acc;
 }
 
+// 1 / d[0] in FP64, formed once per block (FP64 division is slow on this part;
+// every thread reaches the barrier, so call it before any early return)
+__device__ __forceinline__ double block_recip(const double *d) {
+    __shared__ double r;
+    if (threadIdx.x == 0) r = 1.0 / d[0];
+    __syncthreads();
+    return r;
+}
+
 template <typename T>
 __global__ void scale_copy_kernel(const T *__restrict__ w, T *__restrict__ v, const double *__restrict__ denom,
                                   size_t n) {
+    const double inv = block_recip(denom);
     const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (idx >= n) return;
-    v[idx] = w[idx] * T(1.0 / denom[0]);
+    v[idx] = w[idx] * T(inv);
 }
 
 // Hessenberg column j from the two Gram-Schmidt passes; h[j+1] = ||w||
@@ -130,8 +140,9 @@ __global__ void axpby_mixed_kernel(double *x, const float *d, const double *scal
 
 // y = float(x / scale[0])
 __global__ void d2f_scaled_kernel(const double *x, float *y, const double *scale, size_t n) {
+    const double inv = block_recip(scale);
     const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx < n) y[idx] = float(x[idx] * (1.0 / scale[0]));
+    if (idx < n) y[idx] = float(x[idx] * inv);
 }
 
 
@@ -312,9 +323,9 @@ template <typename T>
 __global__ void gs_scale_kernel(const T *w, T *v, size_t n, const ReadBack *rb) {
     using V4 = typename V16<T>::type;
     const size_t n4 = n / (16 / sizeof(T));
+    const T inv = T(block_recip(&rb->hnext));
     const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (idx >= n4) return;
-    const T inv = T(1.0 / rb->hnext);
     reinterpret_cast<V4 *>(v)[idx] = V16<T>::scale(reinterpret_cast<const V4 *>(w)[idx], inv);
 }
 
