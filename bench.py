@@ -469,7 +469,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": mx["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 inner + f64 refinement", "data": "synthetic",
+        "dtype": "f32 inner + f32x2 (two-float, ~48-bit) refinement, RHS and recovery", "data": "synthetic",
         "config": {"workload": name, "n_cells": mx["n_cells"], "n_trace_dofs": mx["NF"] * mx["pp"],
                    "rtol": args.rtol, "inner_rtol": args.inner_rtol, "restart": args.restart,
                    "smoother": "2+2 block-Jacobi omega=2/3", "coarse": "P1 geometric V-cycle 256->4",

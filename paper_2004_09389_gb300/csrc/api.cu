@@ -48,6 +48,7 @@ struct Workspace {
     unsigned int *counter = nullptr;
     ReadBack *rb = nullptr, *host_rb = nullptr;
     double *g = nullptr, *x = nullptr, *r = nullptr, *ycell = nullptr;
+    float2 *x2 = nullptr;  // mixed modes: split copy of the FP64 iterate x (two-float residual)
     KSpace<double> k64;
     KSpace<float> k32;
     // small device arrays
@@ -624,7 +625,8 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info)
         if (outer == 0) {
             r = g;
         } else {
-            TRY(KL(HDG_PROF_RESIDUAL64, 1, launch_residual_t<double>(h, g, x, W.r, false)));
+            // in two-float arithmetic from the split copy of x kept by the update below
+            TRY(KL(HDG_PROF_RESIDUAL64, 1, launch_residual_ff(h, g, W.x2, W.r)));
             rc = norm_host<double>(h, W.r, beta);
             if (rc) return rc;
         }
@@ -647,7 +649,7 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info)
         info.iters = total;
         info.est_rel_res = inner.est_rel_res;
         // x += beta * d
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_axpby_mixed(x, k.x, W.beta, W.NT, s)));
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_axpby_split(x, W.x2, k.x, W.beta, W.NT, s)));
     }
 }
 
@@ -671,6 +673,7 @@ void free_handle(hdg_handle *h) {
     dfree(h->d_ref); dfree(h->d_X); dfree(h->d_fcell); dfree(h->d_facet_of); dfree(h->d_flip);
     dfree(h->d_facet_cell); dfree(h->d_facet_edge); dfree(h->d_facet_verts); dfree(h->d_v2f_ptr); dfree(h->d_v2f);
     dfree(h->d_nbr); dfree(h->d_Xb); dfree(h->d_Rm); dfree(h->d_W); dfree(h->d_Scell); dfree(h->d_Sval);
+    dfree(h->d_Xb2); dfree(h->d_Rm2); dfree(h->d_W2); dfree(h->d_Sval2);
     dfree(h->d_Dinv); dfree(h->d_Sval32); dfree(h->d_Dinv32); dfree(h->d_Sval16); dfree(h->d_status); dfree(h->d_coarse_inv);
     dfree(h->d_coarse_inv32); dfree(h->d_coarse_work);
     for (auto &L : h->lev) {
@@ -680,7 +683,7 @@ void free_handle(hdg_handle *h) {
     }
     if (h->ws) {
         Workspace &W = *h->ws;
-        dfree(W.g); dfree(W.x); dfree(W.r); dfree(W.ycell);
+        dfree(W.g); dfree(W.x); dfree(W.r); dfree(W.ycell); dfree(W.x2);
         dfree(W.k64.V); dfree(W.k64.Z); dfree(W.k64.w); dfree(W.k64.t0); dfree(W.k64.t1); dfree(W.k64.res);
         dfree(W.k32.V); dfree(W.k32.Z); dfree(W.k32.w); dfree(W.k32.t0); dfree(W.k32.t1); dfree(W.k32.res);
         dfree(W.k32.b); dfree(W.k32.x);
@@ -764,6 +767,10 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     if (mixed) {
         TRY(dalloc(&h->d_Sval32, packed(5 * pp * pp, 4)));
         TRY(dalloc(&h->d_Dinv32, packed(pp * pp, 4)));
+        TRY(dalloc(&h->d_Xb2, nK * m * N));
+        TRY(dalloc(&h->d_Rm2, nK * nK * N));
+        TRY(dalloc(&h->d_W2, m * nK * N));
+        TRY(dalloc(&h->d_Sval2, packed(5 * pp * pp, 2)));
         if (prm->precision == HDG_MIXED_BF16) TRY(dalloc(&h->d_Sval16, packed(5 * pp * pp, 8)));
     }
     // Coriolis parameter per cell (mean of its vertices) on every P1 level; on a
@@ -847,6 +854,7 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(dalloc(&W.r, W.NT));
     TRY(dalloc(&W.lam_int, W.NT));
     TRY(dalloc(&W.ycell, N * m));
+    if (h->prm.precision != HDG_FP64) TRY(dalloc(&W.x2, W.NT));
     const size_t mm = W.m;
     W.ld = (W.NT + 3) / 4 * 4;
     // one 16-byte group of w per thread (enough loads in flight for the few-vector
@@ -929,7 +937,8 @@ int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solv
     cudaStream_t s = h->stream;
     h->lc.suspended = false;
     h->lc.fallback = false;
-    TRY(KL(HDG_PROF_RHS, 2, launch_rhs(h, r_u, r_h, W.g, W.ycell)));
+    if (h->prm.precision == HDG_FP64) TRY(KL(HDG_PROF_RHS, 2, launch_rhs(h, r_u, r_h, W.g, W.ycell)));
+    else TRY(KL(HDG_PROF_RHS, 2, launch_rhs_ff(h, r_u, r_h, W.g, W.ycell)));
     int rc;
     if (h->prm.precision == HDG_FP64) {
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<double>(W.x, 0.0, W.NT, s)));
@@ -1047,6 +1056,12 @@ int hdg_condense(hdg_handle *h) {
             TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(L.dinv, L.dinv32, size_t(L.nv), s)));
         }
         TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(h->d_coarse_inv, h->d_coarse_inv32, size_t(Lc.nv) * Lc.nv, s)));
+        // (hi, lo) float pairs for the two-float FP64 steps
+        const size_t N = h->N, nK = h->nK, m = h->m, pp = h->pp, NS = 5 * pp * pp;
+        TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Xb, h->d_Xb2, nK * m * N, s)));
+        TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Rm, h->d_Rm2, nK * nK * N, s)));
+        TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_W, h->d_W2, m * nK * N, s)));
+        TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Sval, h->d_Sval2, (NS + 1) / 2 * 2 * size_t(h->NF), s)));
     }
     int rc = check_status(h);
     if (rc) return rc;
@@ -1114,7 +1129,8 @@ int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h, const d
     } else if (!W.have_lambda) {
         return fail(h, HDG_ESTATE, "no lambda given and no previous solve");
     }
-    TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, r_u, r_h, lam, u, h_out)));
+    if (h->prm.precision == HDG_FP64) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, r_u, r_h, lam, u, h_out)));
+    else TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, r_u, r_h, lam, u, h_out)));
     return HDG_OK;
 }
 
@@ -1140,7 +1156,8 @@ int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, const doubl
     } else if (!W.have_lambda) {
         return fail(h, HDG_ESTATE, "no lambda given and no previous solve");
     }
-    TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, W.ru, W.rh, lam, W.u, W.hh)));
+    if (h->prm.precision == HDG_FP64) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, W.ru, W.rh, lam, W.u, W.hh)));
+    else TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, W.ru, W.rh, lam, W.u, W.hh)));
     TRY(cudaMemcpyAsync(u, W.u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyDeviceToHost, s));
     TRY(cudaMemcpyAsync(h_out, W.hh, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));

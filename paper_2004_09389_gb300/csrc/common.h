@@ -190,6 +190,9 @@ struct hdg_handle {
     double *d_Xb = nullptr;         // A^-1 B        [nK*m][N]
     double *d_Rm = nullptr;         // A^-1 Mass     [nK*nK][N]
     double *d_W = nullptr;          // C A^-1 Mass   [m*nK][N]
+    // mixed modes: the same three matrices and the FP64 trace operator as
+    // (hi, lo) float pairs for the two-float FP64 steps (k_ff.cu)
+    float2 *d_Xb2 = nullptr, *d_Rm2 = nullptr, *d_W2 = nullptr, *d_Sval2 = nullptr;
     double *d_Scell = nullptr;      // S_K           [N][m][m]
     // facet-row trace operator
     double *d_Sval = nullptr;       // 5(p+1)^2 values per facet, packed in 16-byte groups
@@ -223,6 +226,16 @@ namespace hdg {
 
 // ---------------------------------------------------------------- kernel launchers
 // condense / assembly (k_condense.cu)
+// dispatch a launch on the polynomial degree p (1..4) as a compile-time P
+#define HDG_DISPATCH_P(p, CALL) \
+    switch (p) {                \
+        case 1: { constexpr int P = 1; CALL; } break; \
+        case 2: { constexpr int P = 2; CALL; } break; \
+        case 3: { constexpr int P = 3; CALL; } break; \
+        case 4: { constexpr int P = 4; CALL; } break; \
+        default: return cudaErrorInvalidValue;        \
+    }
+
 cudaError_t launch_condense(hdg_handle *h);
 cudaError_t launch_assemble(hdg_handle *h);
 cudaError_t launch_p1_assemble(hdg_handle *h, DevLevel &L, double tau, double gH, int rotating);
@@ -238,6 +251,14 @@ inline __host__ __device__ size_t packed_index(size_t j, size_t e, size_t NF, si
 }
 cudaError_t launch_to_external(hdg_handle *h, const double *in, double *ext);
 cudaError_t launch_rhs(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell);
+cudaError_t launch_rhs_gather(hdg_handle *h, const double *ycell, double *g);
+// two-float versions of the FP64 steps (mixed modes, k_ff.cu)
+cudaError_t launch_split(const double *a, float2 *out, size_t n, cudaStream_t s);
+cudaError_t launch_axpby_split(double *x, float2 *x2, const float *d, const double *scale, size_t n, cudaStream_t s);
+cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2, double *res);
+cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell);
+cudaError_t launch_recover_ff(hdg_handle *h, const double *r_u, const double *r_h, const double *lam, double *u,
+                              double *hout);
 cudaError_t launch_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lam,
                            double *u, double *hout);
 

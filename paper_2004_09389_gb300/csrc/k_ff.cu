@@ -1,0 +1,210 @@
+// Two-float arithmetic for the FP64 steps of the mixed-precision path: the
+// condensed right-hand side (step 1 of the Schur-complement solve, Sec. 3.3),
+// the refinement residual g - S lambda (Eq. schur_system) and the recovery of
+// the cell unknowns (step 3).  GB300's FP64 pipe is far slower than its FP32
+// one, and these steps are FP64-FMA bound there, not HBM bound.
+//
+// Every stored FP64 matrix entry a is kept as a pair (hi, lo) = (rn(a),
+// rn(a - hi)) of floats (8 bytes, like the double), every FP64 input is split
+// the same way once per use, and a sum of products is carried as
+//   s + c:  s the running sum of the rounded leading products hi_a*hi_x, added
+//           by error-free TwoSum steps; c the float sum of the exact product
+//           errors (by FMA), the cross terms hi_a*lo_x + lo_a*hi_x and the
+//           TwoSum errors.
+// The dropped lo_a*lo_x and the rounding of c leave a relative error of about
+// n * 2^-48 of sum |a_i x_i| (FP64: n * 2^-53), at a dozen FP32 operations per
+// term.  Values must lie in the FP32 range (|v| < 3e38); an overflow shows up
+// as Inf/NaN in the refinement residual, which the solver reports.
+#include "common.h"
+
+namespace hdg {
+
+namespace {
+
+inline unsigned blocks(size_t n, int bs) { return unsigned((n + bs - 1) / bs); }
+
+__device__ __forceinline__ float2 split(double a) {
+    const float hi = __double2float_rn(a);
+    return make_float2(hi, __double2float_rn(a - double(hi)));
+}
+
+struct FFAcc {
+    float s = 0.f, c = 0.f;
+    // s + c += a * x (a, x split pairs); intrinsics keep the compiler from
+    // contracting or reassociating the error-free steps
+    __device__ __forceinline__ void add(const float2 a, const float2 x) {
+        const float p = __fmul_rn(a.x, x.x);
+        const float e = __fmaf_rn(a.x, x.x, -p);
+        c = __fmaf_rn(a.x, x.y, c);
+        c = __fmaf_rn(a.y, x.x, c);
+        c = __fadd_rn(c, e);
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
+__global__ void split_kernel(const double *__restrict__ a, float2 *__restrict__ out, size_t n) {
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = split(a[i]);
+}
+
+// x += scale * d (refinement correction, FP32 -> FP64) and its split copy
+__global__ void axpby_split_kernel(double *__restrict__ x, float2 *__restrict__ x2, const float *__restrict__ d,
+                                   const double *__restrict__ scale, size_t n) {
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = fma(scale[0], double(d[i]), x[i]);
+    x[i] = v;
+    x2[i] = split(v);
+}
+
+// r = b - S x with x given split; S split in the packed FP64 layout (element
+// j of facet e in 16-byte group (j / 2, e), lane j % 2, here two float pairs)
+template <int P>
+__global__ void __launch_bounds__(256) residual_ff_kernel(int NF, const float4 *__restrict__ S2,
+                                                          const int32_t *__restrict__ nbr, const double *__restrict__ b,
+                                                          const float2 *__restrict__ x2, double *__restrict__ res) {
+    constexpr int PP = P + 1, NS = 5 * PP * PP, NQ = (NS + 1) / 2;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= NF) return;
+    int src[5];
+    src[0] = e;
+#pragma unroll
+    for (int q = 1; q < 5; ++q) src[q] = __ldg(nbr + size_t(q - 1) * NF + e);
+    float2 xs[5][PP];
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+        for (int c = 0; c < PP; ++c) xs[q][c] = x2[size_t(c) * NF + src[q]];
+    FFAcc acc[PP];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const float4 v = __ldg(S2 + size_t(q) * NF + e);
+        const float2 a[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const int j = 2 * q + g;
+            if (j < NS) {
+                const int r = j / (5 * PP), rem = j % (5 * PP);
+                acc[r].add(a[g], xs[rem / PP][rem % PP]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < PP; ++r) res[size_t(r) * NF + e] = b[size_t(r) * NF + e] - acc[r].value();
+}
+
+// The cell kernels take 32 consecutive cells per block (lane = cell): the
+// cells' right-hand sides r_K = (r_u, r_h) are read as contiguous chunks,
+// split once into shared memory and shared by the warps, which take the output
+// rows in turn; per-cell matrices [row*ncol + col][N] load coalesced.
+constexpr int kCells = 32;
+
+template <int NP>
+__device__ __forceinline__ void stage_cell_rhs(int N, int K0, const double *__restrict__ r_u,
+                                               const double *__restrict__ r_h, float2 (*sIn)[kCells + 1]) {
+    const int nc = min(kCells, N - K0);
+    for (int j = threadIdx.x; j < nc * 2 * NP; j += blockDim.x)
+        sIn[j % (2 * NP)][j / (2 * NP)] = split(r_u[size_t(K0) * 2 * NP + j]);
+    for (int j = threadIdx.x; j < nc * NP; j += blockDim.x)
+        sIn[2 * NP + j % NP][j / NP] = split(r_h[size_t(K0) * NP + j]);
+}
+
+// step 1, cell part: ycell[t][K] = sum_kappa W[t*NK + kappa][K] r_K[kappa]
+template <int P>
+__global__ void __launch_bounds__(128) rhs_cell_ff_kernel(int N, const float2 *__restrict__ W2,
+                                                          const double *__restrict__ r_u,
+                                                          const double *__restrict__ r_h, double *__restrict__ ycell) {
+    constexpr int PP = P + 1, NP = (P + 1) * (P + 2) / 2, NK = 3 * NP, M = 3 * PP, NW = 4;
+    __shared__ float2 sIn[NK][kCells + 1];
+    const int K0 = blockIdx.x * kCells, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    stage_cell_rhs<NP>(N, K0, r_u, r_h, sIn);
+    __syncthreads();
+    const int K = K0 + lane;
+    if (K >= N) return;
+    for (int t = w; t < M; t += NW) {
+        FFAcc acc;
+#pragma unroll 6
+        for (int kap = 0; kap < NK; ++kap) acc.add(__ldg(W2 + size_t(t * NK + kap) * N + K), sIn[kap][lane]);
+        ycell[size_t(t) * N + K] = acc.value();
+    }
+}
+
+// step 3: q_K = R_M r_K - X_B lambda_K, written in the caller's u / h layout
+template <int P>
+__global__ void __launch_bounds__(256) recover_ff_kernel(int N, int NF, const float2 *__restrict__ Rm2,
+                                                         const float2 *__restrict__ Xb2, const double *__restrict__ r_u,
+                                                         const double *__restrict__ r_h, const double *__restrict__ lam,
+                                                         const int32_t *__restrict__ facet_of,
+                                                         const int32_t *__restrict__ flip, double *__restrict__ u,
+                                                         double *__restrict__ hout) {
+    constexpr int PP = P + 1, NP = (P + 1) * (P + 2) / 2, NK = 3 * NP, M = 3 * PP, NW = 8;
+    __shared__ float2 sIn[NK + M][kCells + 1];   // r_K, then lambda on the cell's three facets
+    __shared__ double sOut[NK][kCells + 1];
+    const int K0 = blockIdx.x * kCells, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nc = min(kCells, N - K0);
+    stage_cell_rhs<NP>(N, K0, r_u, r_h, sIn);
+    for (int j = threadIdx.x; j < nc * M; j += blockDim.x) {
+        const int cell = j / M, q = j % M, i = q / PP, jj = q % PP, K = K0 + cell;
+        const int f = facet_of[3 * K + i], fl = flip[3 * K + i];
+        sIn[NK + q][cell] = split(lam[size_t(fl ? P - jj : jj) * NF + f]);
+    }
+    __syncthreads();
+    const int K = K0 + lane;
+    if (K < N) {
+        for (int rho = w; rho < NK; rho += NW) {
+            FFAcc acc;
+#pragma unroll 6
+            for (int kap = 0; kap < NK; ++kap) acc.add(__ldg(Rm2 + size_t(rho * NK + kap) * N + K), sIn[kap][lane]);
+#pragma unroll
+            for (int q = 0; q < M; ++q) {
+                const float2 a = __ldg(Xb2 + size_t(rho * M + q) * N + K);
+                acc.add(make_float2(-a.x, -a.y), sIn[NK + q][lane]);
+            }
+            sOut[rho][lane] = acc.value();
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nc * 2 * NP; j += blockDim.x)
+        u[size_t(K0) * 2 * NP + j] = sOut[j % (2 * NP)][j / (2 * NP)];
+    for (int j = threadIdx.x; j < nc * NP; j += blockDim.x) hout[size_t(K0) * NP + j] = sOut[2 * NP + j % NP][j / NP];
+}
+
+}  // namespace
+
+cudaError_t launch_split(const double *a, float2 *out, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    split_kernel<<<blocks(n, 256), 256, 0, s>>>(a, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpby_split(double *x, float2 *x2, const float *d, const double *scale, size_t n, cudaStream_t s) {
+    axpby_split_kernel<<<blocks(n, 256), 256, 0, s>>>(x, x2, d, scale, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2, double *res) {
+    HDG_DISPATCH_P(h->p, (residual_ff_kernel<P><<<blocks(h->NF, 256), 256, 0, h->stream>>>(
+                             h->NF, reinterpret_cast<const float4 *>(h->d_Sval2), h->d_nbr, b, x2, res)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell) {
+    HDG_DISPATCH_P(h->p, (rhs_cell_ff_kernel<P><<<blocks(h->N, kCells), 128, 0, h->stream>>>(h->N, h->d_W2, r_u, r_h,
+                                                                                               ycell)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_rhs_gather(h, ycell, g);
+}
+
+cudaError_t launch_recover_ff(hdg_handle *h, const double *r_u, const double *r_h, const double *lam, double *u,
+                              double *hout) {
+    HDG_DISPATCH_P(h->p, (recover_ff_kernel<P><<<blocks(h->N, kCells), 256, 0, h->stream>>>(
+                             h->N, h->NF, h->d_Rm2, h->d_Xb2, r_u, r_h, lam, h->d_facet_of, h->d_flip, u, hout)));
+    return cudaGetLastError();
+}
+
+}  // namespace hdg

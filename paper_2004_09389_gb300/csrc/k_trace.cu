@@ -351,14 +351,6 @@ __global__ void prolong_add_kernel(int NF, const int32_t *__restrict__ fverts, c
 
 inline unsigned blocks(size_t n, int bs) { return unsigned((n + bs - 1) / bs); }
 
-#define HDG_DISPATCH_P(p, CALL) \
-    switch (p) {                \
-        case 1: { constexpr int P = 1; CALL; } break; \
-        case 2: { constexpr int P = 2; CALL; } break; \
-        case 3: { constexpr int P = 3; CALL; } break; \
-        case 4: { constexpr int P = 4; CALL; } break; \
-        default: return cudaErrorInvalidValue;        \
-    }
 
 }  // namespace
 
@@ -474,13 +466,17 @@ cudaError_t launch_to_external(hdg_handle *h, const double *in, double *ext) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_rhs_gather(hdg_handle *h, const double *ycell, double *g) {
+    HDG_DISPATCH_P(h->p, (rhs_gather_kernel<P><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->N, h->NF, ycell, h->d_facet_cell, h->d_facet_edge, h->d_flip, g)));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rhs(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell) {
     size_t n = size_t(h->N) * h->m;
     HDG_DISPATCH_P(h->p, (rhs_cell_kernel<P><<<blocks(n, 256), 256, 0, h->stream>>>(h->N, h->d_W, r_u, r_h, ycell)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    HDG_DISPATCH_P(h->p, (rhs_gather_kernel<P><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->N, h->NF, ycell, h->d_facet_cell, h->d_facet_edge, h->d_flip, g)));
-    return cudaGetLastError();
+    return launch_rhs_gather(h, ycell, g);
 }
 
 cudaError_t launch_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lam, double *u,

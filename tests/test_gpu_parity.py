@@ -207,6 +207,44 @@ def test_mixed_precision(kind, p, mode, reorth):
     s.close()
 
 
+@pytest.mark.parametrize("kind,p", [("flat", 1), ("flat", 3), ("flat", 4), ("sphere", 3)])
+def test_two_float_steps_match_fp64(kind, p):
+    """Mixed modes do the FP64 steps (recovery, condensed right-hand side,
+    refinement residual) in two-float arithmetic (about 48 significant bits):
+    recovery from the same lambda agrees with the FP64 kernel to 1e-12, and a
+    mixed solve to rtol 1e-11 meets it when its residual is measured with the
+    FP64 operator.  The flat case (200 cells, 300 facets) leaves a ragged last
+    block in both the 32-cell and the 256-facet kernels."""
+    if kind == "flat":
+        mesh = I.periodic_square_hierarchy(10, n_coarsest=5)       # 200 cells, 300 facets
+        g, H, f = 1.3, 0.7, I.coriolis_flat(mesh, 1.0)
+        tau = 8 * mesh.h / np.sqrt(g * H)
+        n_p = (p + 1) * (p + 2) // 2
+        rng = np.random.default_rng(1)
+        ru = rng.standard_normal((mesh.n_cells, 2, n_p))
+        rh = rng.standard_normal((mesh.n_cells, n_p))
+        assert mesh.n_cells % 32 != 0
+    else:
+        mesh, prob, (tau, g, H, f), ru, rh = _case(kind, p)
+    s64 = _solver(mesh, p, tau, g, H, f, rtol=1e-12)
+    s32 = _solver(mesh, p, tau, g, H, f, rtol=1e-11, precision=1)
+    lam, _ = s64.solve(ru, rh)
+    u64, h64 = s64.recover(ru, rh, lam)
+    u32, h32 = s32.recover(ru, rh, lam)
+    assert _rel(u32, u64) <= 1e-12 and _rel(h32, h64) <= 1e-12
+    lam2, info = s32.solve(ru, rh)
+    assert info["true_rel_res"] <= 1e-11
+    gd = torch.empty(lam2.shape, dtype=torch.float64, device="cuda")
+    yd = torch.empty_like(gd)
+    s64.condensed_rhs_dev(_dev(ru), _dev(rh), gd)
+    s64.trace_apply_dev(_dev(lam2), yd)
+    torch.cuda.synchronize()
+    gh, yh = gd.cpu().numpy(), yd.cpu().numpy()
+    assert np.linalg.norm(gh - yh) / np.linalg.norm(gh) <= 1.5e-11
+    s64.close()
+    s32.close()
+
+
 def test_zero_rhs_and_nan_rhs():
     from paper_2004_09389_gb300 import HDGError
     mesh, prob, (tau, g, H, f), ru, rh = _case("flat", 1)
