@@ -74,14 +74,20 @@ def trace_bytes(cat: str, NF: int, pp: int, s_width: int | None = None) -> float
 
 
 # ---------------------------------------------------------------- clocks
-CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+CLOCK_QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
 class ClockSampler:
+    """nvidia-smi sampling every 50 ms.  Started before the warm-up: a cold
+    nvidia-smi start costs CPU time that would otherwise fall into the timed
+    region; wait_ready() holds until it has run for 1.5 s.  Each sample carries
+    nvidia-smi's own timestamp; stop(t0, t1) keeps those inside the timed window."""
+
     def __init__(self, gpu_index: int):
         self.proc = None
+        self.t_start = time.time()
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -92,7 +98,11 @@ class ClockSampler:
         except (OSError, FileNotFoundError):
             self.proc = None
 
-    def stop(self) -> dict:
+    def wait_ready(self, seconds: float = 1.5) -> None:
+        if self.proc is not None:
+            time.sleep(max(0.0, self.t_start + seconds - time.time()))
+
+    def stop(self, t0: float = None, t1: float = None) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -101,18 +111,26 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
+        import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
+        if t0 is not None and t1 is not None:
+            inside = [r for r in rows if t0 - 0.06 <= r[0] <= t1 + 0.06]
+            rows = inside or rows
+        sm, smax, reasons = [], [], set()
+        for _, a, b, flags in rows:
+            sm.append(a)
+            smax.append(b)
+            for nm, v in zip(names, flags):
                 if v.lower() == "active":
                     reasons.add(nm)
         sm.sort()
@@ -202,22 +220,26 @@ def gpu_arm(args, rank: int, world: int):
             infos.append(s.solve_dev(ru_d, rh_d, lam_d))
             s.recover_dev(ru_d, rh_d, lam_d, u_d, h_d)
 
+        clocks = ClockSampler(dev.index) if arm == "mixed" else None
         for _ in range(args.warmup):
             step()
         infos.clear()
         s.profile_enable(timing=False)          # launch counters only
         stream = s.stream                        # the handle's stream: every kernel of the solve runs on it
+        if clocks:
+            clocks.wait_ready()
         barrier()
-        clocks = ClockSampler(dev.index) if arm == "mixed" else None
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_wall0 = time.time()
         e0.record(stream)
         for _ in range(args.steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
+        t_wall1 = time.time()
         barrier()
         ms = e0.elapsed_time(e1)
-        clk = clocks.stop() if clocks else None
+        clk = clocks.stop(t_wall0, t_wall1) if clocks else None
         launches = sum(n for _, n in s.profile_read().values())
         if dist is not None:
             t = torch.tensor([ms], device=dev)

@@ -111,6 +111,24 @@ void dfree(T *&p) {
     p = nullptr;
 }
 
+// Device address under which kernels may access a host buffer in place
+// (page-locked memory from cudaHostAlloc / cudaHostRegister on this device;
+// on Grace-Blackwell such accesses cross the coherent NVLink-C2C link), or
+// nullptr for other memory, which goes through staged copies.  The caller's
+// buffer must span the documented size, as for the copies.
+template <typename T>
+T *host_alias(T *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer || a.device != dev) return nullptr;
+    return static_cast<T *>(a.devicePointer);
+}
+
 std::string check_params(const hdg_params *prm) {
     if (!prm) return "params is NULL";
     if (prm->p < 1 || prm->p > 4) return "p must be in 1..4";
@@ -932,13 +950,16 @@ int require_condensed(hdg_handle *h) {
     return HDG_OK;
 }
 
-int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solve_info &info) {
+// copy_u / copy_h (mixed modes, optional): device buffers that receive r_u, r_h
+// as the right-hand-side kernel reads them (used when those are host memory)
+int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solve_info &info,
+                   double *copy_u = nullptr, double *copy_h = nullptr) {
     Workspace &W = *h->ws;
     cudaStream_t s = h->stream;
     h->lc.suspended = false;
     h->lc.fallback = false;
     if (h->prm.precision == HDG_FP64) TRY(KL(HDG_PROF_RHS, 2, launch_rhs(h, r_u, r_h, W.g, W.ycell)));
-    else TRY(KL(HDG_PROF_RHS, 2, launch_rhs_ff(h, r_u, r_h, W.g, W.ycell)));
+    else TRY(KL(HDG_PROF_RHS, 2, launch_rhs_ff(h, r_u, r_h, W.g, W.ycell, copy_u, copy_h)));
     int rc;
     if (h->prm.precision == HDG_FP64) {
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<double>(W.x, 0.0, W.NT, s)));
@@ -1100,16 +1121,27 @@ int hdg_solve(hdg_handle *h, const double *r_u, const double *r_h, double *lambd
     if (rc) return rc;
     Workspace &W = *h->ws;
     cudaStream_t s = h->stream;
-    TRY(cudaMemcpyAsync(W.ru, r_u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyHostToDevice, s));
-    TRY(cudaMemcpyAsync(W.rh, r_h, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyHostToDevice, s));
     hdg_solve_info loc{};
-    rc = solve_internal(h, W.ru, W.rh, loc);
+    // page-locked inputs of a mixed handle: the right-hand-side kernel reads them
+    // in place (and keeps device copies for hdg_recover); otherwise staged copies
+    const double *ru_a = host_alias(r_u), *rh_a = host_alias(r_h);
+    if (h->prm.precision != HDG_FP64 && ru_a && rh_a) {
+        rc = solve_internal(h, ru_a, rh_a, loc, W.ru, W.rh);
+    } else {
+        TRY(cudaMemcpyAsync(W.ru, r_u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyHostToDevice, s));
+        TRY(cudaMemcpyAsync(W.rh, r_h, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyHostToDevice, s));
+        rc = solve_internal(h, W.ru, W.rh, loc);
+    }
     if (rc == HDG_ECUDA) {
         if (info) *info = loc;
         return rc;
     }
-    TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_external(h, W.x, W.lam_ext)));
-    TRY(cudaMemcpyAsync(lambda, W.lam_ext, sizeof(double) * W.NT, cudaMemcpyDeviceToHost, s));
+    if (double *lam_a = host_alias(lambda)) {
+        TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_external(h, W.x, lam_a)));
+    } else {
+        TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_external(h, W.x, W.lam_ext)));
+        TRY(cudaMemcpyAsync(lambda, W.lam_ext, sizeof(double) * W.NT, cudaMemcpyDeviceToHost, s));
+    }
     TRY(cudaStreamSynchronize(s));
     W.have_rhs = true;
     if (info) *info = loc;
@@ -1156,10 +1188,16 @@ int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, const doubl
     } else if (!W.have_lambda) {
         return fail(h, HDG_ESTATE, "no lambda given and no previous solve");
     }
-    if (h->prm.precision == HDG_FP64) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, W.ru, W.rh, lam, W.u, W.hh)));
-    else TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, W.ru, W.rh, lam, W.u, W.hh)));
-    TRY(cudaMemcpyAsync(u, W.u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyDeviceToHost, s));
-    TRY(cudaMemcpyAsync(h_out, W.hh, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyDeviceToHost, s));
+    double *u_a = host_alias(u), *h_a = host_alias(h_out);
+    if (h->prm.precision != HDG_FP64 && u_a && h_a) {
+        // page-locked outputs of a mixed handle: the recovery kernel writes them in place
+        TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, W.ru, W.rh, lam, u_a, h_a)));
+    } else {
+        if (h->prm.precision == HDG_FP64) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, W.ru, W.rh, lam, W.u, W.hh)));
+        else TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, W.ru, W.rh, lam, W.u, W.hh)));
+        TRY(cudaMemcpyAsync(u, W.u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyDeviceToHost, s));
+        TRY(cudaMemcpyAsync(h_out, W.hh, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyDeviceToHost, s));
+    }
     TRY(cudaStreamSynchronize(s));
     return HDG_OK;
 }

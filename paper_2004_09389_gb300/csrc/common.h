@@ -256,7 +256,10 @@ cudaError_t launch_rhs_gather(hdg_handle *h, const double *ycell, double *g);
 cudaError_t launch_split(const double *a, float2 *out, size_t n, cudaStream_t s);
 cudaError_t launch_axpby_split(double *x, float2 *x2, const float *d, const double *scale, size_t n, cudaStream_t s);
 cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2, double *res);
-cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell);
+// (r_u, r_h may be device aliases of page-locked host memory; copy_u / copy_h,
+// if non-null, receive a device copy of them)
+cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell,
+                          double *copy_u = nullptr, double *copy_h = nullptr);
 cudaError_t launch_recover_ff(hdg_handle *h, const double *r_u, const double *r_h, const double *lam, double *u,
                               double *hout);
 cudaError_t launch_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lam,

@@ -103,25 +103,37 @@ __global__ void __launch_bounds__(256) residual_ff_kernel(int NF, const float4 *
 // rows in turn; per-cell matrices [row*ncol + col][N] load coalesced.
 constexpr int kCells = 32;
 
+// (r_u, r_h may live in page-locked host memory read over the C2C link; with
+// cu, ch non-null each value read is also stored there, in HBM)
 template <int NP>
 __device__ __forceinline__ void stage_cell_rhs(int N, int K0, const double *__restrict__ r_u,
-                                               const double *__restrict__ r_h, float2 (*sIn)[kCells + 1]) {
+                                               const double *__restrict__ r_h, float2 (*sIn)[kCells + 1],
+                                               double *__restrict__ cu = nullptr, double *__restrict__ ch = nullptr) {
     const int nc = min(kCells, N - K0);
-    for (int j = threadIdx.x; j < nc * 2 * NP; j += blockDim.x)
-        sIn[j % (2 * NP)][j / (2 * NP)] = split(r_u[size_t(K0) * 2 * NP + j]);
-    for (int j = threadIdx.x; j < nc * NP; j += blockDim.x)
-        sIn[2 * NP + j % NP][j / NP] = split(r_h[size_t(K0) * NP + j]);
+    for (int j = threadIdx.x; j < nc * 2 * NP; j += blockDim.x) {
+        const size_t k = size_t(K0) * 2 * NP + j;
+        const double v = r_u[k];
+        if (cu) cu[k] = v;
+        sIn[j % (2 * NP)][j / (2 * NP)] = split(v);
+    }
+    for (int j = threadIdx.x; j < nc * NP; j += blockDim.x) {
+        const size_t k = size_t(K0) * NP + j;
+        const double v = r_h[k];
+        if (ch) ch[k] = v;
+        sIn[2 * NP + j % NP][j / NP] = split(v);
+    }
 }
 
 // step 1, cell part: ycell[t][K] = sum_kappa W[t*NK + kappa][K] r_K[kappa]
 template <int P>
 __global__ void __launch_bounds__(128) rhs_cell_ff_kernel(int N, const float2 *__restrict__ W2,
                                                           const double *__restrict__ r_u,
-                                                          const double *__restrict__ r_h, double *__restrict__ ycell) {
+                                                          const double *__restrict__ r_h, double *__restrict__ ycell,
+                                                          double *__restrict__ cu, double *__restrict__ ch) {
     constexpr int PP = P + 1, NP = (P + 1) * (P + 2) / 2, NK = 3 * NP, M = 3 * PP, NW = 4;
     __shared__ float2 sIn[NK][kCells + 1];
     const int K0 = blockIdx.x * kCells, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    stage_cell_rhs<NP>(N, K0, r_u, r_h, sIn);
+    stage_cell_rhs<NP>(N, K0, r_u, r_h, sIn, cu, ch);
     __syncthreads();
     const int K = K0 + lane;
     if (K >= N) return;
@@ -192,9 +204,10 @@ cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2,
     return cudaGetLastError();
 }
 
-cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell) {
+cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell,
+                          double *copy_u, double *copy_h) {
     HDG_DISPATCH_P(h->p, (rhs_cell_ff_kernel<P><<<blocks(h->N, kCells), 128, 0, h->stream>>>(h->N, h->d_W2, r_u, r_h,
-                                                                                               ycell)));
+                                                                                               ycell, copy_u, copy_h)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_rhs_gather(h, ycell, g);

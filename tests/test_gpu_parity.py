@@ -245,6 +245,33 @@ def test_two_float_steps_match_fp64(kind, p):
     s32.close()
 
 
+@pytest.mark.parametrize("kind,p", [("flat", 3), ("sphere", 2)])
+def test_page_locked_host_buffers_match_staged_path(kind, p):
+    """Mixed handles read page-locked right-hand sides and write page-locked
+    lambda / u / h in place (no staged copies); pageable numpy buffers take
+    the staged path.  Same kernels and arithmetic: the results are identical,
+    and hdg_recover(NULL, ...) afterwards still uses the solve's inputs."""
+    import ctypes
+    from paper_2004_09389_gb300 import _lib
+    mesh, prob, (tau, g, H, f), ru, rh = _case(kind, p)
+    s = _solver(mesh, p, tau, g, H, f, rtol=1e-10, precision=1)
+    lam0, _ = s.solve(ru, rh)
+    u0, h0 = s.recover()
+    ru_p = torch.from_numpy(ru.copy()).pin_memory()
+    rh_p = torch.from_numpy(rh.copy()).pin_memory()
+    lam_p = torch.empty(lam0.shape, dtype=torch.float64).pin_memory()
+    u_p = torch.empty(u0.shape, dtype=torch.float64).pin_memory()
+    h_p = torch.empty(h0.shape, dtype=torch.float64).pin_memory()
+    info = _lib.hdg_solve_info()
+    _lib.check(s.h, s.lib.hdg_solve(s.h, ru_p.data_ptr(), rh_p.data_ptr(), lam_p.data_ptr(), ctypes.byref(info)))
+    ru_p.zero_()                     # the recovery below must not read the caller's buffers
+    rh_p.zero_()
+    _lib.check(s.h, s.lib.hdg_recover(s.h, None, None, None, u_p.data_ptr(), h_p.data_ptr()))
+    assert np.array_equal(lam_p.numpy(), lam0)
+    assert np.array_equal(u_p.numpy(), u0) and np.array_equal(h_p.numpy(), h0)
+    s.close()
+
+
 def test_zero_rhs_and_nan_rhs():
     from paper_2004_09389_gb300 import HDGError
     mesh, prob, (tau, g, H, f), ru, rh = _case("flat", 1)
