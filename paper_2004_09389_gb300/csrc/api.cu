@@ -26,7 +26,12 @@ namespace hdg {
 template <typename T> cudaError_t launch_apply_t(hdg_handle *, const T *, T *);
 template <typename T> cudaError_t launch_residual_t(hdg_handle *, const T *, const T *, T *, bool);
 template <typename T> cudaError_t launch_smooth_t(hdg_handle *, const T *, const T *, T *);
-template <typename T> cudaError_t launch_smooth_first_t(hdg_handle *, const T *, T *);
+template <typename T>
+cudaError_t launch_smooth_first_t(hdg_handle *, const T *, T *, const T * = nullptr, const double * = nullptr,
+                                  T * = nullptr);
+template <typename T>
+cudaError_t launch_apply_dots_t(hdg_handle *, const T *, T *, const T *, size_t, int, double *, unsigned int *,
+                                double *);
 template <typename T> cudaError_t launch_restrict_t(hdg_handle *, const T *, T *, const T *, T, T *);
 template <typename T> cudaError_t launch_smooth_prolong_t(hdg_handle *, const T *, const T *, const T *, T *);
 template <typename T> cudaError_t launch_prolong_add_t(hdg_handle *, const T *, T *);
@@ -337,9 +342,11 @@ cudaError_t p1_cycle(hdg_handle *h, T **result) {
     return cudaSuccess;
 }
 
-// z = V(v), Alg. twolevel_vcycle with zero initial guess (internal layout)
+// z = V(v), Alg. twolevel_vcycle with zero initial guess (internal layout).
+// With w_src (Arnoldi steps j >= 1, n_pre >= 1), v is first formed as
+// w_src / h_{j+1,j} by the first smoothing sweep, which stores it to v.
 template <typename T>
-cudaError_t precond(hdg_handle *h, const T *v, T *z) {
+cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr) {
     KSpace<T> &k = kspace<T>(h);
     cudaStream_t s = h->stream;
     const size_t NT = h->NT;
@@ -349,7 +356,10 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z) {
     if (h->prm.n_pre == 0) {
         if ((e = KL(HDG_PROF_KRYLOV, 1, launch_fill<T>(x, T(0), NT, s))) != cudaSuccess) return e;
     } else {
-        if ((e = KL(cat_first<T>(), 1, launch_smooth_first_t<T>(h, v, x))) != cudaSuccess) return e;
+        if ((e = KL(cat_first<T>(), 1,
+                    launch_smooth_first_t<T>(h, v, x, w_src, w_src ? &h->ws->rb->hnext : nullptr,
+                                             const_cast<T *>(v)))) != cudaSuccess)
+            return e;
         for (int i = 1; i < h->prm.n_pre; ++i) {
             if ((e = KL(cat_smooth<T>(), 1, launch_smooth_t<T>(h, v, x, x2))) != cudaSuccess) return e;
             std::swap(x, x2);
@@ -450,12 +460,18 @@ cudaError_t arnoldi_step(hdg_handle *h, int j) {
     const size_t ld = W.ld;
     T *vj = k.V + size_t(j) * ld, *zj = k.Z + size_t(j) * ld;
     cudaError_t e;
-    if ((e = precond<T>(h, vj, zj)) != cudaSuccess) return e;
-    if ((e = KL(cat_apply<T>(), 1, launch_apply_t<T>(h, zj, k.w))) != cudaSuccess) return e;
+    // v_j = w / h_{j,j-1} rides on the first smoothing sweep (w and h from step j-1)
+    const bool fuse_scale = h->prm.n_pre >= 1;
+    if ((e = precond<T>(h, vj, zj, (fuse_scale && j > 0) ? k.w : nullptr)) != cudaSuccess) return e;
+    // w = S z_j with the first Gram-Schmidt pass h1 = V^T w in the same kernel
+    if ((e = KL(cat_apply<T>(), 1, launch_apply_dots_t<T>(h, zj, k.w, k.V, ld, j + 1, W.partial, W.counter, W.h1))) !=
+        cudaSuccess)
+        return e;
     const bool reorth = h->prm.reorth != 0;
-    if ((e = KL(HDG_PROF_KRYLOV, reorth ? 4 : 3,
+    if ((e = KL(HDG_PROF_KRYLOV, 1 + (reorth ? 1 : 0) + (fuse_scale ? 0 : 1),
                 launch_gs_step<T>(k.V, ld, j, k.w, W.partial, W.counter, W.nblk_gs, W.h1, W.h2, W.nrm2, W.Hm, ldh,
-                                  W.cs, W.sn, W.sv, W.bnorm, W.rb, k.V + size_t(j + 1) * ld, reorth, s))) != cudaSuccess)
+                                  W.cs, W.sn, W.sv, W.bnorm, W.rb, k.V + size_t(j + 1) * ld, reorth, !fuse_scale,
+                                  s))) != cudaSuccess)
         return e;
     (void)NT;
     return cudaMemcpyAsync(W.host_rb, W.rb, sizeof(ReadBack), cudaMemcpyDeviceToHost, s);
@@ -921,7 +937,7 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(dalloc(&W.y, mm + 1));
     // partial sums: (m + 1) vectors x the largest grid of the multi-dot (nchunk) or
     // of the Gram-Schmidt kernels (nblk_gs, or up to 1216 blocks after autotuning)
-    TRY(dalloc(&W.partial, (mm + 1) * size_t(std::max({W.nchunk, W.nblk_gs, kMaxGsBlocks}))));
+    TRY(dalloc(&W.partial, (mm + 1) * size_t(std::max({W.nchunk, W.nblk_gs, kMaxGsBlocks, int((h->NF + 255) / 256)}))));
     TRY(dalloc(&W.counter, 1));
     TRY(cudaMemsetAsync(W.counter, 0, sizeof(unsigned int), s));
     TRY(dalloc(&W.rb, 1));
@@ -1369,6 +1385,13 @@ int hdg_autotune(hdg_handle *h, int32_t *choice) {
     cudaEventDestroy(e1);
     h->prof.on = was_on;
     drop_graphs(h);
+    // the timing filled basis vectors over their padded length; the padding
+    // beyond N_T must be zero again for the Gram-Schmidt kernels
+    if (f32) {
+        TRY(cudaMemsetAsync(W.k32.V, 0, sizeof(float) * ld * size_t(W.m + 1), s));
+    } else {
+        TRY(cudaMemsetAsync(W.k64.V, 0, sizeof(double) * ld * size_t(W.m + 1), s));
+    }
     if (choice) {
         choice[0] = h->bs_facet;
         choice[1] = W.nblk_gs;

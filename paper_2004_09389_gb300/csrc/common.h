@@ -307,7 +307,8 @@ cudaError_t launch_fill(T *x, T v, size_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_gs_step(const T *V, size_t ld, int j, T *w, double *partial, unsigned int *counter, int nblk,
                            double *h1, double *h2, double *nrm2, double *Hm, int ldh, double *cs, double *sn,
-                           double *sv, const double *bnorm, ReadBack *rb, T *vnext, bool reorth, cudaStream_t s);
+                           double *sv, const double *bnorm, ReadBack *rb, T *vnext, bool reorth, bool scale,
+                           cudaStream_t s);
 int learned_n_params(int p, int hid);
 cudaError_t launch_learned_infer(hdg_handle *h, const float *r, const float *x, float *xout);
 cudaError_t launch_learned_forward(hdg_handle *h, const float *r, float *c);

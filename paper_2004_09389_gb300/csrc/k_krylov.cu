@@ -245,16 +245,6 @@ __device__ void block_update(const typename V16<T>::type *__restrict__ V, size_t
     __syncthreads();
 }
 
-// pass 1: h1 = V^T w
-template <typename T>
-__global__ void __launch_bounds__(256) gs_dots_kernel(const T *V, size_t ld, int k, const T *w, size_t n,
-                                                      double *partial, unsigned int *counter, double *h1) {
-    using V4 = typename V16<T>::type;
-    bool last;
-    dots_and_finish<T>(reinterpret_cast<const V4 *>(V), ld / (16 / sizeof(T)), k, reinterpret_cast<const V4 *>(w),
-                       n / (16 / sizeof(T)), partial, counter, h1, &last);
-}
-
 // w -= V h1, then pass 2: h2 = V^T w
 template <typename T>
 __global__ void __launch_bounds__(256) gs_update_dots_kernel(const T *V, size_t ld, int k, T *w, size_t n,
@@ -386,22 +376,25 @@ cudaError_t launch_d2f_scaled(const double *x, float *y, const double *scale, si
 template <typename T>
 cudaError_t launch_gs_step(const T *V, size_t ld, int j, T *w, double *partial, unsigned int *counter, int nblk,
                            double *h1, double *h2, double *nrm2, double *Hm, int ldh, double *cs, double *sn,
-                           double *sv, const double *bnorm, ReadBack *rb, T *vnext, bool reorth, cudaStream_t s) {
+                           double *sv, const double *bnorm, ReadBack *rb, T *vnext, bool reorth, bool scale,
+                           cudaStream_t s) {
+    // h1 = V^T w comes with w from the operator kernel (apply_dots_kernel)
     const int k = j + 1;
-    gs_dots_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, partial, counter, h1);
     if (reorth) gs_update_dots_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, h1, partial, counter, h2);
     gs_update_norm_givens_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, h1, reorth ? h2 : nullptr, partial, counter,
                                                         nrm2, Hm, ldh, cs, sn, sv, j, bnorm, rb);
-    const size_t n4 = ld / (16 / sizeof(T));
-    gs_scale_kernel<T><<<blocks(n4, 256), 256, 0, s>>>(w, vnext, ld, rb);
+    if (scale) {   // otherwise the next step's first smoothing sweep forms v_{j+1}
+        const size_t n4 = ld / (16 / sizeof(T));
+        gs_scale_kernel<T><<<blocks(n4, 256), 256, 0, s>>>(w, vnext, ld, rb);
+    }
     return cudaGetLastError();
 }
 template cudaError_t launch_gs_step<float>(const float *, size_t, int, float *, double *, unsigned int *, int, double *,
                                            double *, double *, double *, int, double *, double *, double *,
-                                           const double *, ReadBack *, float *, bool, cudaStream_t);
+                                           const double *, ReadBack *, float *, bool, bool, cudaStream_t);
 template cudaError_t launch_gs_step<double>(const double *, size_t, int, double *, double *, unsigned int *, int,
                                             double *, double *, double *, double *, int, double *, double *, double *,
-                                            const double *, ReadBack *, double *, bool, cudaStream_t);
+                                            const double *, ReadBack *, double *, bool, bool, cudaStream_t);
 
 #define HDG_KRYLOV_INST(T)                                                                                      \
     template cudaError_t launch_multidot<T>(const T *, size_t, int, const T *, size_t, double *, int,           \

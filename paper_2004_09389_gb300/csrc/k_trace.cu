@@ -135,6 +135,75 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) apply_kernel(int NF,
     for (int r = 0; r <= P; ++r) y[size_t(r) * NF + e] = v[r];
 }
 
+// y = S x (as apply_kernel) and h = V^T y over the first k basis vectors (the
+// first Gram-Schmidt pass of an Arnoldi step): each block sums its facets'
+// rows, four vectors at a time, into per-block partials; the last block to
+// finish adds the partials in block order (deterministic) into h.
+template <int P, typename T, typename ST>
+__global__ void __launch_bounds__(256, 4) apply_dots_kernel(int NF, const ST *__restrict__ Sval,
+                                                          const int32_t *__restrict__ nbr, const T *__restrict__ x,
+                                                          T *__restrict__ y, const T *__restrict__ V, size_t ld,
+                                                          int k, double *__restrict__ partial,
+                                                          unsigned int *__restrict__ counter, double *__restrict__ h) {
+    using A = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+    constexpr int PP = P + 1, G = 4;
+    __shared__ A red[G][8];
+    __shared__ bool last;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = e < NF;
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nwarp = blockDim.x / 32;
+    T v[PP];
+    if (valid) {
+        T xs[5][PP];
+        gather_x<P, T>(nbr, x, e, NF, xs);
+        facet_rows_packed<P, T, ST>(Sval, e, NF, xs, v);
+#pragma unroll
+        for (int r = 0; r < PP; ++r) y[size_t(r) * NF + e] = v[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < PP; ++r) v[r] = T(0);
+    }
+    for (int i0 = 0; i0 < k; i0 += G) {
+        A acc[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            A a = A(0);
+            if (valid && i0 + g < k) {
+#pragma unroll
+                for (int r = 0; r < PP; ++r) a = fma(A(V[size_t(i0 + g) * ld + size_t(r) * NF + e]), A(v[r]), a);
+            }
+            acc[g] = a;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            A t = acc[g];
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+            if (lane == 0) red[g][warp] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < G && i0 + int(threadIdx.x) < k) {
+            A t = A(0);
+            for (int q = 0; q < nwarp; ++q) t += red[threadIdx.x][q];
+            partial[size_t(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = double(t);
+        }
+        __syncthreads();
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int i = warp; i < k; i += nwarp) {
+        double t = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32) t += partial[size_t(i) * gridDim.x + b];
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0) h[i] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
 template <int P, typename T, typename ST>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value) residual_kernel(int NF, const ST *__restrict__ Sval,
                                                        const int32_t *__restrict__ nbr, const T *__restrict__ b,
@@ -202,13 +271,31 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_prolong_kerne
 // first sweep from a zero initial guess: x = omega D^-1 b
 template <int P, typename T>
 __global__ void smooth_first_kernel(int NF, const T *__restrict__ Dinv, const T *__restrict__ b, T *__restrict__ xout,
-                                    T omega) {
+                                    T omega, const T *__restrict__ w, const double *__restrict__ hnext,
+                                    T *__restrict__ bout) {
+    // with w: the right-hand side is the next Arnoldi vector b = w / h_{j+1,j}
+    // (the last Gram-Schmidt step of the previous iteration), also stored to
+    // bout; the FP64 reciprocal is formed once per block
+    __shared__ double inv_h;
+    if (w != nullptr) {
+        if (threadIdx.x == 0) inv_h = 1.0 / hnext[0];
+        __syncthreads();
+    }
     constexpr int PP = P + 1;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= NF) return;
     T v[PP], d[PP];
+    if (w != nullptr) {
+        const T inv = T(inv_h);
 #pragma unroll
-    for (int c = 0; c < PP; ++c) v[c] = b[size_t(c) * NF + e];
+        for (int c = 0; c < PP; ++c) {
+            v[c] = w[size_t(c) * NF + e] * inv;
+            bout[size_t(c) * NF + e] = v[c];
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < PP; ++c) v[c] = b[size_t(c) * NF + e];
+    }
     block_solve_packed<P, T, T>(Dinv, e, NF, v, d);
 #pragma unroll
     for (int r = 0; r < PP; ++r) xout[size_t(r) * NF + e] = omega * d[r];
@@ -368,6 +455,13 @@ template <> struct Ops<float> {
 inline bool bf16_pre(hdg_handle *h) { return h->prm.precision == HDG_MIXED_BF16 && h->d_Sval16; }
 
 template <typename T>
+cudaError_t launch_apply_dots_t(hdg_handle *h, const T *x, T *y, const T *V, size_t ld, int k, double *partial,
+                                unsigned int *counter, double *hdots) {
+    HDG_DISPATCH_P(h->p, (apply_dots_kernel<P, T, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(
+                             h->NF, Ops<T>::S(h, false), h->d_nbr, x, y, V, ld, k, partial, counter, hdots)));
+    return cudaGetLastError();
+}
+template <typename T>
 cudaError_t launch_apply_t(hdg_handle *h, const T *x, T *y) {
     HDG_DISPATCH_P(h->p, (apply_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, false), h->d_nbr, x, y)));
     return cudaGetLastError();
@@ -398,9 +492,9 @@ cudaError_t launch_smooth_t(hdg_handle *h, const T *b, const T *x, T *xout) {
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_smooth_first_t(hdg_handle *h, const T *b, T *x) {
+cudaError_t launch_smooth_first_t(hdg_handle *h, const T *b, T *x, const T *w, const double *hnext, T *bout) {
     const T om = T(h->prm.omega);
-    HDG_DISPATCH_P(h->p, (smooth_first_kernel<P, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::D(h), b, x, om)));
+    HDG_DISPATCH_P(h->p, (smooth_first_kernel<P, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::D(h), b, x, om, w, hnext, bout)));
     return cudaGetLastError();
 }
 template <typename T>
@@ -441,13 +535,19 @@ cudaError_t launch_repack(hdg_handle *h) {
 }
 
 template cudaError_t launch_apply_t<double>(hdg_handle *, const double *, double *);
+template cudaError_t launch_apply_dots_t<double>(hdg_handle *, const double *, double *, const double *, size_t, int,
+                                                 double *, unsigned int *, double *);
+template cudaError_t launch_apply_dots_t<float>(hdg_handle *, const float *, float *, const float *, size_t, int,
+                                                double *, unsigned int *, double *);
 template cudaError_t launch_apply_t<float>(hdg_handle *, const float *, float *);
 template cudaError_t launch_residual_t<double>(hdg_handle *, const double *, const double *, double *, bool);
 template cudaError_t launch_residual_t<float>(hdg_handle *, const float *, const float *, float *, bool);
 template cudaError_t launch_smooth_t<double>(hdg_handle *, const double *, const double *, double *);
 template cudaError_t launch_smooth_t<float>(hdg_handle *, const float *, const float *, float *);
-template cudaError_t launch_smooth_first_t<double>(hdg_handle *, const double *, double *);
-template cudaError_t launch_smooth_first_t<float>(hdg_handle *, const float *, float *);
+template cudaError_t launch_smooth_first_t<double>(hdg_handle *, const double *, double *, const double *,
+                                                   const double *, double *);
+template cudaError_t launch_smooth_first_t<float>(hdg_handle *, const float *, float *, const float *, const double *,
+                                                  float *);
 template cudaError_t launch_restrict_t<double>(hdg_handle *, const double *, double *, const double *, double, double *);
 template cudaError_t launch_restrict_t<float>(hdg_handle *, const float *, float *, const float *, float, float *);
 template cudaError_t launch_smooth_prolong_t<double>(hdg_handle *, const double *, const double *, const double *, double *);
