@@ -33,6 +33,8 @@ if ROOT not in sys.path:
 METRIC = "HDG trace solves/s to rel.res 1e-8: mixed/learned vs plain FP64 MG, same GB300"
 SIDE, NGRID, G, DEPTH, F0 = 5.12e6, 256, 9.81, 1.0e3, 1.0e-4
 SAMPLE_N = 64            # oracle sample: 64 x 64 x 2 = 8,192 triangles of the same workload
+RADIUS, OMEGA = 6.371e6, 7.292e-5
+SPHERE_R, SAMPLE_R = 6, 4   # sphere workload: r = 6 (81,920 triangles); oracle sample r = 4 (5,120)
 
 
 def workload(n: int, p: int, courant: float, seed: int):
@@ -48,6 +50,47 @@ def workload(n: int, p: int, courant: float, seed: int):
 def workload_name(n, p, courant):
     return (f"flat periodic {n}x{n}x2 ({2 * n * n:,} triangles), HDG p={p}, acoustic Courant {courant:g}, "
             f"g={G}, H={DEPTH:g} m, f={F0:g}, k^-3 Gaussian RHS")
+
+
+def sphere_workload(r: int, p: int, courant: float, seed: int):
+    """Icosahedral sphere refined r times (20 * 4^r flat triangles), radius
+    6.371e6 m, f = 2 Omega sin(latitude) (P1), g = 9.81, H drawn from
+    U[5e3, 1e4] m by the seed, tau = Courant * h_r / c; right-hand sides are
+    random spherical-harmonic fields up to degree 64 with l^-3 variance."""
+    import numpy as np
+    import hdg_inputs as I
+    mesh = I.sphere_hierarchy(r, RADIUS, r_coarsest=max(r - 5, 1))
+    H = float(np.random.default_rng(seed).uniform(5e3, 1e4))
+    tau = courant * mesh.h / math.sqrt(G * H)
+    f = I.coriolis_sphere(mesh, OMEGA)
+    ru, rh = I.spherical_harmonic_rhs(mesh, p, seed, lmax=64)
+    return mesh, tau, f, ru, rh, H
+
+
+def workload_label(kind: str, p: int, courant: float, seed: int) -> str:
+    """Name of the full workload (without generating its right-hand sides)."""
+    if kind == "sphere":
+        import numpy as np
+        import hdg_inputs as I
+        mesh = I.sphere_hierarchy(SPHERE_R, RADIUS, r_coarsest=max(SPHERE_R - 5, 1))
+        H = float(np.random.default_rng(seed).uniform(5e3, 1e4))
+        tau = courant * mesh.h / math.sqrt(G * H)
+        fmax = float(np.abs(I.coriolis_sphere(mesh, OMEGA)).max())
+        return (f"icosahedral sphere r={SPHERE_R} ({mesh.n_cells:,} triangles), radius 6.371e6 m, HDG p={p}, "
+                f"acoustic Courant {courant:g}, g={G}, H={H:.0f} m, f=2 Omega sin(lat) (max |f| tau = "
+                f"{fmax * tau:.2f}), spherical-harmonic RHS to degree 64")
+    return workload_name(NGRID, p, courant)
+
+
+def make_workload(kind: str, full: bool, p: int, courant: float, seed: int) -> dict:
+    """The benchmark workload (full = True) or the oracle's bounded sample of it."""
+    if kind == "sphere":
+        r = SPHERE_R if full else SAMPLE_R
+        mesh, tau, f, ru, rh, H = sphere_workload(r, p, courant, seed)
+        return dict(mesh=mesh, tau=tau, f=f, ru=ru, rh=rh, g=G, H=H)
+    n = NGRID if full else SAMPLE_N
+    mesh, tau, f, ru, rh = workload(n, p, courant, seed)
+    return dict(mesh=mesh, tau=tau, f=f, ru=ru, rh=rh, g=G, H=DEPTH)
 
 
 # ---------------------------------------------------------------- algorithmic bytes per launch
@@ -139,14 +182,15 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_sample(p: int, courant: float, steps: int, seed: int = 0) -> dict:
+def oracle_sample(p: int, courant: float, steps: int, seed: int = 0, kind: str = "flat") -> dict:
     """Time the oracle (plain FP64 FGMRES + V-cycle, as it stands) on the
     sample mesh; run in a spawned single-threaded process."""
     import numpy as np
     from oracle.hdg import HDGProblem
     from oracle.solver import TwoLevelPreconditioner, gmres
-    mesh, tau, f, ru, rh = workload(SAMPLE_N, p, courant, seed)
-    prob = HDGProblem(mesh, p, tau=tau, g=G, H=DEPTH, f_vertex=f)
+    wl = make_workload(kind, False, p, courant, seed)
+    mesh, tau, f, ru, rh = wl["mesh"], wl["tau"], wl["f"], wl["ru"], wl["rh"]
+    prob = HDGProblem(mesh, p, tau=tau, g=wl["g"], H=wl["H"], f_vertex=f)
     S = prob.trace_operator()
     pc = TwoLevelPreconditioner(prob, mesh, S, coarse="gmg")
     times, iters = [], []
@@ -160,24 +204,31 @@ def oracle_sample(p: int, courant: float, steps: int, seed: int = 0) -> dict:
     return {"sec_per_solve": float(np.median(times)), "iters": iters, "n_cells": mesh.n_cells}
 
 
-def run_oracle_subprocess(p: int, courant: float, steps: int) -> dict:
+def run_oracle_subprocess(p: int, courant: float, steps: int, kind: str = "flat") -> dict:
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--p", str(p), "--courant", str(courant),
-           "--steps", str(steps)]
+           "--steps", str(steps), "--workload", kind]
     res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
     if res.returncode != 0:
         raise RuntimeError(f"oracle sample failed: {res.stderr[-2000:]}")
     return json.loads(res.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline_entry(p, courant, steps):
+def sample_text(kind: str) -> tuple:
+    """(sample description, cells of the full workload)"""
+    if kind == "sphere":
+        return f"icosahedral sphere r={SAMPLE_R}", 20 * 4 ** SPHERE_R
+    return f"{SAMPLE_N}x{SAMPLE_N}x2", 2 * NGRID * NGRID
+
+
+def cpu_baseline_entry(p, courant, steps, kind="flat"):
     t0 = time.perf_counter()
-    r = run_oracle_subprocess(p, courant, steps)
-    n_full = 2 * NGRID * NGRID
+    r = run_oracle_subprocess(p, courant, steps, kind)
+    desc, n_full = sample_text(kind)
     val = (1.0 / r["sec_per_solve"]) * (r["n_cells"] / n_full)
     return {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"{SAMPLE_N}x{SAMPLE_N}x2 = {r['n_cells']} triangles of the same workload (same p, Courant, "
-                       f"RHS generator), {steps} solves, median time per solve scaled to 131,072 triangles by the "
+            "sample": (f"{desc} = {r['n_cells']} triangles of the same workload (same p, Courant, "
+                       f"RHS generator), {steps} solves, median time per solve scaled to {n_full:,} triangles by the "
                        f"cell ratio; single-threaded NumPy/SciPy"),
             "sec_per_solve_sample": r["sec_per_solve"], "iters": r["iters"],
             "wall_s": time.perf_counter() - t0}
@@ -201,14 +252,15 @@ def gpu_arm(args, rank: int, world: int):
             dist.barrier()
         torch.cuda.synchronize()
 
-    mesh, tau, f, ru, rh = workload(NGRID, args.p, args.courant, args.seed + rank)
+    wl = make_workload(args.workload, True, args.p, args.courant, args.seed + rank)
+    mesh, tau, f, ru, rh, g_, H_ = wl["mesh"], wl["tau"], wl["f"], wl["ru"], wl["rh"], wl["g"], wl["H"]
     ru_d = torch.from_numpy(ru).to(dev)
     rh_d = torch.from_numpy(rh).to(dev)
     out = {}
     arms = [(a, p) for a, p in (("mixed", HDG_MIXED_FP32), ("mixed_bf16", HDG_MIXED_BF16), ("fp64", HDG_FP64))
             if a in args.arms.split(",")]
     for arm, prec in arms:
-        s = HDGSolver(mesh, args.p, tau, G, DEPTH, f_vertex=f, rtol=args.rtol, precision=prec,
+        s = HDGSolver(mesh, args.p, tau, g_, H_, f_vertex=f, rtol=args.rtol, precision=prec,
                       inner_rtol=args.inner_rtol, restart=args.restart, reorth=args.reorth)
         NF, pp = s.n_facets, args.p + 1
         lam_d = torch.empty((NF, pp), dtype=torch.float64, device=dev)
@@ -279,8 +331,13 @@ def gpu_arm(args, rank: int, world: int):
             e2e_s = float(t.item())
         h2d = ru.nbytes + rh.nbytes
         d2h = lam_h.numel() * 8 + u_h.numel() * 8 + hh_h.numel() * 8
+        levels = [mesh] + list(mesh.levels)
+        nK, m = 3 * s.n_p, 3 * pp
         out[arm] = dict(ms=ms, infos=infos, clocks=clk, launches=launches, prof=prof, e2e_s=e2e_s,
-                        h2d=h2d, d2h=d2h, NF=NF, pp=pp, n_cells=s.n_cells)
+                        h2d=h2d, d2h=d2h, NF=NF, pp=pp, n_cells=s.n_cells,
+                        coarse=(f"P1 geometric V-cycle over {len(levels)} levels, {levels[0].n_vertices:,} -> "
+                                f"{levels[-1].n_vertices} vertices (dense coarsest solve)"),
+                        data_gb=(8.0 * s.n_cells * (nK * nK + 2 * nK * m) + 8.0 * NF * 5 * pp * pp) / 1e9)
         s.close()
         torch.cuda.empty_cache()
     if dist is not None:
@@ -419,6 +476,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--workload", default="flat", choices=["flat", "sphere"],
+                    help="flat: periodic 256x256x2 square (the headline); sphere: icosahedral sphere r=6")
     ap.add_argument("--courant", type=float, default=8.0)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--inner-rtol", dest="inner_rtol", type=float, default=1e-4)
@@ -439,28 +498,28 @@ def main():
         return
 
     if args.oracle_sample:
-        print(json.dumps(oracle_sample(args.p, args.courant, args.steps)))
+        print(json.dumps(oracle_sample(args.p, args.courant, args.steps, kind=args.workload)))
         return
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
-    name = workload_name(NGRID, args.p, args.courant)
+    name = workload_label(args.workload, args.p, args.courant, args.seed)
+    desc, n_full = sample_text(args.workload)
 
     if args.impl == "reference":
         if rank != 0:
             return
         steps = args.warmup + args.steps
         t0 = time.perf_counter()
-        r = run_oracle_subprocess(args.p, args.courant, max(steps, 1))
-        n_full = 2 * NGRID * NGRID
+        r = run_oracle_subprocess(args.p, args.courant, max(steps, 1), args.workload)
         val = (1.0 / r["sec_per_solve"]) * (r["n_cells"] / n_full)
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / val, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": name, "rtol": args.rtol},
                 "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                 "sample": f"{SAMPLE_N}x{SAMPLE_N}x2 = {r['n_cells']} triangles per step, median "
-                                           f"time per solve scaled to 131,072 triangles by the cell ratio"},
+                                 "sample": f"{desc} = {r['n_cells']} triangles per step, median "
+                                           f"time per solve scaled to {n_full:,} triangles by the cell ratio"},
                 "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "iters": r["iters"], "wall_s": time.perf_counter() - t0}
         print(json.dumps(line))
@@ -469,7 +528,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # spawned before the first CUDA call
-        cpu = cpu_baseline_entry(args.p, args.courant, args.oracle_steps)
+        cpu = cpu_baseline_entry(args.p, args.courant, args.oracle_steps, args.workload)
     res = gpu_arm(args, rank, world)
     if rank != 0:
         return
@@ -494,9 +553,10 @@ def main():
         "dtype": "f32 inner + f32x2 (two-float, ~48-bit) refinement, RHS and recovery", "data": "synthetic",
         "config": {"workload": name, "n_cells": mx["n_cells"], "n_trace_dofs": mx["NF"] * mx["pp"],
                    "rtol": args.rtol, "inner_rtol": args.inner_rtol, "restart": args.restart,
-                   "smoother": "2+2 block-Jacobi omega=2/3", "coarse": "P1 geometric V-cycle 256->4",
+                   "smoother": "2+2 block-Jacobi omega=2/3", "coarse": mx["coarse"],
                    "orthogonalisation": "CGS2" if args.reorth else "CGS (one pass)",
-                   "l2": "inputs larger than L2 (operator data ~1.8 GB resident in HBM), no flush",
+                   "l2": (f"inputs larger than L2 (per-cell matrices and trace operator {mx['data_gb']:.2f} GB "
+                          f"resident in HBM, L2 129 MB), no flush"),
                    "parallelism": f"replicas x{world}"},
         "iters": it_mx, "true_rel_res": [i["true_rel_res"] for i in mx["infos"]],
         "plain_fp64": {"value": fp_value, "unit": "solves/s", "ms_per_step": fp["ms"] / K, "iters": it_fp,

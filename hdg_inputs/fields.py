@@ -138,39 +138,53 @@ def gaussian_field_rhs(mesh: Mesh, p: int, seed: int, grid: int = 1024,
 # random spherical-harmonic fields (sphere)
 # --------------------------------------------------------------------------
 
-def _sh_sum(lon: np.ndarray, colat: np.ndarray, rng, lmax: int, slope: float) -> np.ndarray:
-    """Sum of real, fully normalised spherical harmonics 1 <= l <= lmax with
-    random coefficients of variance ``l^slope``.  Associated Legendre values
-    come from the standard three-term recurrences in l at fixed m."""
-    x = np.cos(colat)
-    s = np.sin(colat)
-    out = np.zeros_like(x)
-    pmm = np.ones_like(x)              # \bar P_0^0
+def _sh_coefficients(rng, lmax: int, slope: float) -> np.ndarray:
+    """Random coefficients of one field, drawn in the order (m = 0..lmax, then
+    l = max(m, 1)..lmax; cos then sin term): array [lmax + 1 (m), lmax + 1 (l), 2],
+    zero where unused; standard deviation l^(slope / 2)."""
+    c = np.zeros((lmax + 1, lmax + 1, 2))
     for m in range(0, lmax + 1):
-        if m == 1:
-            pmm = math.sqrt(3.0) * s
-        elif m > 1:
-            pmm = math.sqrt((2.0 * m + 1.0) / (2.0 * m)) * s * pmm
-        cm, sm = np.cos(m * lon), np.sin(m * lon)
-        p_lm2, p_lm1 = None, pmm       # l = m
-        for l in range(m, lmax + 1):
-            if l == m:
-                plm = pmm
-            elif l == m + 1:
-                plm = math.sqrt(2.0 * m + 3.0) * x * pmm
-            else:
-                a = math.sqrt((2.0 * l - 1.0) * (2.0 * l + 1.0) / ((l - m) * (l + m)))
-                b = math.sqrt((2.0 * l + 1.0) * (l + m - 1.0) * (l - m - 1.0)
-                              / ((l - m) * (l + m) * (2.0 * l - 3.0)))
-                plm = a * x * p_lm1 - b * p_lm2
-            if l >= m + 1:
-                p_lm2, p_lm1 = p_lm1, plm
-            if l >= 1:
-                sd = l ** (slope / 2.0)
-                out += sd * rng.standard_normal() * plm * cm
-                if m > 0:
-                    out += sd * rng.standard_normal() * plm * sm
-    return out
+        for l in range(max(m, 1), lmax + 1):
+            sd = l ** (slope / 2.0)
+            c[m, l, 0] = sd * rng.standard_normal()
+            if m > 0:
+                c[m, l, 1] = sd * rng.standard_normal()
+    return c
+
+
+def _sh_sums(lon: np.ndarray, colat: np.ndarray, coefs: list, chunk: int = 65536) -> list:
+    """Sums of real, fully normalised spherical harmonics 1 <= l <= lmax, one
+    per coefficient array of ``_sh_coefficients``, at the given directions.
+    Associated Legendre values come from the standard three-term recurrences in
+    l at fixed m, evaluated once per order for all the fields."""
+    lmax = coefs[0].shape[0] - 1
+    C = np.stack(coefs)                                  # [F, m, l, 2]
+    flat_lon, flat_colat = lon.ravel(), colat.ravel()
+    outs = np.zeros((len(coefs), flat_lon.size))
+    for a in range(0, flat_lon.size, chunk):
+        x = np.cos(flat_colat[a:a + chunk])
+        s = np.sin(flat_colat[a:a + chunk])
+        ln = flat_lon[a:a + chunk]
+        pmm = np.ones_like(x)                            # \bar P_0^0
+        for m in range(0, lmax + 1):
+            if m == 1:
+                pmm = math.sqrt(3.0) * s
+            elif m > 1:
+                pmm = math.sqrt((2.0 * m + 1.0) / (2.0 * m)) * s * pmm
+            P = np.empty((lmax + 1 - m, x.size))       # rows l = m .. lmax
+            P[0] = pmm
+            if m + 1 <= lmax:
+                P[1] = math.sqrt(2.0 * m + 3.0) * x * pmm
+            for l in range(m + 2, lmax + 1):
+                a_ = math.sqrt((2.0 * l - 1.0) * (2.0 * l + 1.0) / ((l - m) * (l + m)))
+                b_ = math.sqrt((2.0 * l + 1.0) * (l + m - 1.0) * (l - m - 1.0)
+                               / ((l - m) * (l + m) * (2.0 * l - 3.0)))
+                P[l - m] = a_ * x * P[l - m - 1] - b_ * P[l - m - 2]
+            A = C[:, m, m:, 0] @ P                       # [F, chunk]
+            outs[:, a:a + chunk] += A * np.cos(m * ln)
+            if m > 0:
+                outs[:, a:a + chunk] += (C[:, m, m:, 1] @ P) * np.sin(m * ln)
+    return [o.reshape(lon.shape) for o in outs]
 
 
 def spherical_harmonic_rhs(mesh: Mesh, p: int, seed: int, lmax: int = 64, slope: float = -3.0):
@@ -185,12 +199,10 @@ def spherical_harmonic_rhs(mesh: Mesh, p: int, seed: int, lmax: int = 64, slope:
     colat = np.arccos(np.clip(xyz[..., 2] / rr, -1.0, 1.0))
     lon = np.arctan2(xyz[..., 1], xyz[..., 0])
 
-    def one():
-        v = _sh_sum(lon, colat, rng, lmax, slope)
-        return v / np.sqrt(np.mean(v ** 2))
-
-    rh = one()
-    vec = np.stack([one(), one(), one()], axis=-1)     # [N, n_p, 3]
+    coefs = [_sh_coefficients(rng, lmax, slope) for _ in range(4)]
+    fields = [v / np.sqrt(np.mean(v ** 2)) for v in _sh_sums(lon, colat, coefs)]
+    rh = fields[0]
+    vec = np.stack(fields[1:], axis=-1)                  # [N, n_p, 3]
     e1, e2, _ = cell_frames(mesh)
     ru = np.stack([np.einsum("kpd,kd->kp", vec, e1), np.einsum("kpd,kd->kp", vec, e2)], axis=1)
     return ru, rh

@@ -1,12 +1,14 @@
-"""Parity at the benchmark's full size, in the benchmark's launch configuration.
+"""Parity at the benchmark's full sizes, in the benchmark's launch configuration.
 
-Workload: flat periodic 256 x 256 x 2 (131,072 triangles), p = 3, acoustic
-Courant 8, g = 9.81, H = 1e3, f = 1e-4, k^-3 Gaussian right-hand sides.  The
-oracle cannot solve this size in seconds, so it checks sampled outputs one by
-one (trace-operator rows, condensed right-hand side, recovered cells) and the
-solve is checked through properties that hold at any size: the true relative
-residual of the returned lambda, and discrete mass conservation up to the
-bound the residual implies.
+Workloads: flat periodic 256 x 256 x 2 (131,072 triangles), p = 3, acoustic
+Courant 8, g = 9.81, H = 1e3, f = 1e-4, k^-3 Gaussian right-hand sides; and
+the icosahedral sphere r = 6 (81,920 triangles, radius 6.371e6 m, f =
+2 Omega sin(latitude), p = 3, Courant 8, spherical-harmonic right-hand sides).
+The oracle cannot solve these sizes in seconds, so it checks sampled outputs
+one by one (trace-operator rows, condensed right-hand side, recovered cells)
+and the solve is checked through properties that hold at any size: the true
+relative residual of the returned lambda, and discrete mass conservation up
+to the bound the residual implies.
 """
 import math
 
@@ -18,20 +20,24 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.fixture(scope="module")
-def setup():
+@pytest.fixture(scope="module", params=["flat", "sphere"])
+def setup(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2004_09389_gb300 import build, HDGSolver, HDG_FP64, HDG_MIXED_FP32
-    from oracle.hdg import HDGProblem
+    from oracle.hdg import HDGProblem, MeshData, local_coordinates
     import bench
     build.build()
     p = 3
-    mesh, tau, f, ru, rh = bench.workload(bench.NGRID, p, 8.0, 0)
-    prob = HDGProblem(mesh, p, tau=tau, g=bench.G, H=bench.DEPTH, f_vertex=f, lazy=True)
-    s64 = HDGSolver(mesh, p, tau, bench.G, bench.DEPTH, f_vertex=f, precision=HDG_FP64, rtol=1e-8)
-    s32 = HDGSolver(mesh, p, tau, bench.G, bench.DEPTH, f_vertex=f, precision=HDG_MIXED_FP32, rtol=1e-8)
-    yield dict(mesh=mesh, tau=tau, f=f, ru=ru, rh=rh, prob=prob, s64=s64, s32=s32, p=p)
+    wl = bench.make_workload(request.param, True, p, 8.0, 0)
+    mesh, tau, f, ru, rh, g, H = wl["mesh"], wl["tau"], wl["f"], wl["ru"], wl["rh"], wl["g"], wl["H"]
+    prob = HDGProblem(mesh, p, tau=tau, g=g, H=H, f_vertex=f, lazy=True)
+    s64 = HDGSolver(mesh, p, tau, g, H, f_vertex=f, precision=HDG_FP64, rtol=1e-8)
+    s32 = HDGSolver(mesh, p, tau, g, H, f_vertex=f, precision=HDG_MIXED_FP32, rtol=1e-8)
+    X = local_coordinates(MeshData.of(mesh))
+    detJ = np.abs((X[:, 1, 0] - X[:, 0, 0]) * (X[:, 2, 1] - X[:, 0, 1])
+                  - (X[:, 2, 0] - X[:, 0, 0]) * (X[:, 1, 1] - X[:, 0, 1]))
+    yield dict(mesh=mesh, tau=tau, f=f, ru=ru, rh=rh, prob=prob, s64=s64, s32=s32, p=p, detJ=detJ)
     s64.close()
     s32.close()
 
@@ -87,19 +93,16 @@ def test_solve_properties_and_sampled_recovery(setup, arm):
     res = (g - Sl).cpu().numpy()
     rel = np.linalg.norm(res) / np.linalg.norm(g.cpu().numpy())
     assert rel <= 1.5e-8
-    # mass conservation: int h - int r_h = -tau * sum of the facet residuals (mu = 1)
+    # mass conservation: int h - int r_h = -tau * sum of the facet residuals (mu = 1);
+    # int_K phi_i = |det J_K| times its reference-triangle integral
     prob_w = np.asarray(__import__("oracle.reference", fromlist=["x"]).reference_matrices(setup["p"])["M"]).sum(0)
-    area = (bench_side() / 256) ** 2 / 2
-    mass_h = area * 2 * (h @ prob_w).sum()
-    mass_r = area * 2 * (rh @ prob_w).sum()
-    assert abs((mass_h - mass_r) + setup["tau"] * res.sum()) <= 1e-9 * area * 2 * np.abs(rh @ prob_w).sum()
+    dj = setup["detJ"]
+    mass_h = (dj * (h @ prob_w)).sum()
+    mass_r = (dj * (rh @ prob_w)).sum()
+    assert abs((mass_h - mass_r) + setup["tau"] * res.sum()) <= 1e-9 * (dj * np.abs(rh @ prob_w)).sum()
     # sampled cells recovered exactly from this lambda
     cells = _samples(prob.N, seed=3)
     q0 = prob.local_cells(cells, ru, rh, lam.reshape(-1))
     q = np.concatenate([u[cells, 0], u[cells, 1], h[cells]], axis=1)
     assert np.abs(q - q0).max() <= 1e-11 * np.abs(q0).max()
 
-
-def bench_side():
-    import bench
-    return bench.SIDE
