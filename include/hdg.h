@@ -76,6 +76,9 @@ extern "C" {
 #define HDG_MIXED_FP32  1   /* FP32 inner FGMRES + V-cycle, FP64 iterative refinement         */
 #define HDG_MIXED_BF16  2   /* as HDG_MIXED_FP32, with a BF16 copy of the trace operator for the
                                smoother and V-cycle residual (FP32 accumulation)              */
+#define HDG_MIXED_FGMRES64 3 /* FP64 FGMRES (basis, orthogonalisation, residual, update, RHS and
+                               recovery in FP64) preconditioned by the two-level V-cycle in FP32
+                               (FP32 operator copies; the coarsest P1 solve stays FP64)       */
 
 typedef struct hdg_handle hdg_handle;
 
@@ -105,7 +108,7 @@ typedef struct {
     double        g, H;         /* gravity and mean depth (> 0)                          */
     double        tau_s;        /* upwind stabilisation; <= 0 selects sqrt(g H)          */
     const double *f_vertex;     /* Coriolis parameter at fine vertices, P1 per cell; NULL = 0 */
-    int32_t       precision;    /* HDG_FP64, HDG_MIXED_FP32 or HDG_MIXED_BF16             */
+    int32_t       precision;    /* HDG_FP64, HDG_MIXED_FP32, HDG_MIXED_BF16 or HDG_MIXED_FGMRES64 */
     double        rtol;         /* stop at ||g - S lambda|| <= rtol ||g|| (FP64 residual) */
     int32_t       restart;      /* FGMRES restart length m (1..64)                        */
     int32_t       max_iter;     /* total Krylov iterations allowed                        */

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libhdg.so")
 
 HDG_OK, HDG_EINVAL, HDG_ESINGULAR, HDG_ENOCONV = 0, -1, -2, -3
 HDG_EBREAKDOWN, HDG_ENAN, HDG_ECUDA, HDG_ETIMEOUT, HDG_ENOMEM, HDG_ESTATE = -4, -5, -6, -7, -8, -9
-HDG_FP64, HDG_MIXED_FP32, HDG_MIXED_BF16 = 0, 1, 2
+HDG_FP64, HDG_MIXED_FP32, HDG_MIXED_BF16, HDG_MIXED_FGMRES64 = 0, 1, 2, 3
 
 ERROR_NAMES = {0: "HDG_OK", -1: "HDG_EINVAL", -2: "HDG_ESINGULAR", -3: "HDG_ENOCONV",
                -4: "HDG_EBREAKDOWN", -5: "HDG_ENAN", -6: "HDG_ECUDA", -7: "HDG_ETIMEOUT",

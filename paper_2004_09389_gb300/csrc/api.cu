@@ -145,9 +145,12 @@ std::string check_params(const hdg_params *prm) {
     if (!(prm->omega > 0) || !(prm->p1_omega > 0)) return "damping factors must be positive";
     if (prm->coarse_mode != 0 && prm->coarse_mode != 1) return "coarse_mode must be 0 or 1";
     if (prm->reorth != 0 && prm->reorth != 1) return "reorth must be 0 or 1";
-    if (prm->precision != HDG_FP64 && prm->precision != HDG_MIXED_FP32 && prm->precision != HDG_MIXED_BF16)
+    if (prm->precision != HDG_FP64 && prm->precision != HDG_MIXED_FP32 && prm->precision != HDG_MIXED_BF16 &&
+        prm->precision != HDG_MIXED_FGMRES64)
         return "unknown precision mode";
-    if (prm->precision != HDG_FP64 && !(prm->inner_rtol > 0 && prm->inner_rtol < 1)) return "inner_rtol must be in (0, 1)";
+    if ((prm->precision == HDG_MIXED_FP32 || prm->precision == HDG_MIXED_BF16) &&
+        !(prm->inner_rtol > 0 && prm->inner_rtol < 1))
+        return "inner_rtol must be in (0, 1)";
     return "";
 }
 
@@ -237,12 +240,6 @@ double *levR<double>(DevLevel &L) { return L.r; }
 template <>
 float *levR<float>(DevLevel &L) { return L.r32; }
 template <typename T>
-const T *coarse_inv(hdg_handle *h);
-template <>
-const double *coarse_inv<double>(hdg_handle *h) { return h->d_coarse_inv; }
-template <>
-const float *coarse_inv<float>(hdg_handle *h) { return h->d_coarse_inv32; }
-template <typename T>
 KSpace<T> &kspace(hdg_handle *h);
 template <>
 KSpace<double> &kspace<double>(hdg_handle *h) { return h->ws->k64; }
@@ -315,7 +312,7 @@ cudaError_t p1_cycle(hdg_handle *h, T **result) {
             t.cw = sizeof(T) == 4 ? static_cast<const void *>(L.child_w32) : static_cast<const void *>(L.child_w);
         }
         smem = tail_smem_bytes(h->lev, ts, sizeof(T));
-        a.inv = coarse_inv<T>(h);
+        a.inv = h->d_coarse_inv;          // the coarsest solve stays FP64 in every precision
         a.status = h->d_status;
         a.b_top = levB<T>(h->lev[ts]);
         a.x_top = levX<T>(h->lev[ts]);
@@ -460,9 +457,24 @@ cudaError_t arnoldi_step(hdg_handle *h, int j) {
     const size_t ld = W.ld;
     T *vj = k.V + size_t(j) * ld, *zj = k.Z + size_t(j) * ld;
     cudaError_t e;
-    // v_j = w / h_{j,j-1} rides on the first smoothing sweep (w and h from step j-1)
-    const bool fuse_scale = h->prm.n_pre >= 1;
-    if ((e = precond<T>(h, vj, zj, (fuse_scale && j > 0) ? k.w : nullptr)) != cudaSuccess) return e;
+    bool fuse_scale = h->prm.n_pre >= 1;
+    if (std::is_same<T, double>::value && mode_pre32(h->prm)) {
+        // FP64 FGMRES, FP32 preconditioner: v_j = w / h_{j,j-1} formed in FP64 and
+        // rounded to FP32 in one pass, z_j widened back to FP64
+        KSpace<float> &k32 = h->ws->k32;
+        const double *wsrc = reinterpret_cast<const double *>(j > 0 ? k.w : vj);
+        if ((e = KL(HDG_PROF_KRYLOV, 1, launch_scale_round(wsrc, j > 0 ? &W.rb->hnext : nullptr,
+                                                            reinterpret_cast<double *>(vj), k32.b, NT, s))) !=
+            cudaSuccess)
+            return e;
+        if ((e = precond<float>(h, k32.b, k32.x)) != cudaSuccess) return e;
+        if ((e = KL(HDG_PROF_KRYLOV, 1, launch_widen(k32.x, reinterpret_cast<double *>(zj), NT, s))) != cudaSuccess)
+            return e;
+        fuse_scale = true;
+    } else {
+        // v_j = w / h_{j,j-1} rides on the first smoothing sweep (w and h from step j-1)
+        if ((e = precond<T>(h, vj, zj, (fuse_scale && j > 0) ? k.w : nullptr)) != cudaSuccess) return e;
+    }
     // w = S z_j with the first Gram-Schmidt pass h1 = V^T w in the same kernel
     if ((e = KL(cat_apply<T>(), 1, launch_apply_dots_t<T>(h, zj, k.w, k.V, ld, j + 1, W.partial, W.counter, W.h1))) !=
         cudaSuccess)
@@ -709,7 +721,7 @@ void free_handle(hdg_handle *h) {
     dfree(h->d_nbr); dfree(h->d_Xb); dfree(h->d_Rm); dfree(h->d_W); dfree(h->d_Scell); dfree(h->d_Sval);
     dfree(h->d_Xb2); dfree(h->d_Rm2); dfree(h->d_W2); dfree(h->d_Sval2);
     dfree(h->d_Dinv); dfree(h->d_Sval32); dfree(h->d_Dinv32); dfree(h->d_Sval16); dfree(h->d_status); dfree(h->d_coarse_inv);
-    dfree(h->d_coarse_inv32); dfree(h->d_coarse_work);
+    dfree(h->d_coarse_work);
     for (auto &L : h->lev) {
         dfree(L.col); dfree(L.diag); dfree(L.elem); dfree(L.fK); dfree(L.contrib_ptr); dfree(L.contrib); dfree(L.A); dfree(L.dinv);
         dfree(L.A32); dfree(L.dinv32); dfree(L.parent); dfree(L.child_ptr); dfree(L.child_idx); dfree(L.child_w); dfree(L.child_w32);
@@ -801,10 +813,12 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     if (mixed) {
         TRY(dalloc(&h->d_Sval32, packed(5 * pp * pp, 4)));
         TRY(dalloc(&h->d_Dinv32, packed(pp * pp, 4)));
-        TRY(dalloc(&h->d_Xb2, nK * m * N));
-        TRY(dalloc(&h->d_Rm2, nK * nK * N));
-        TRY(dalloc(&h->d_W2, m * nK * N));
-        TRY(dalloc(&h->d_Sval2, packed(5 * pp * pp, 2)));
+        if (mode_ff(*prm)) {
+            TRY(dalloc(&h->d_Xb2, nK * m * N));
+            TRY(dalloc(&h->d_Rm2, nK * nK * N));
+            TRY(dalloc(&h->d_W2, m * nK * N));
+            TRY(dalloc(&h->d_Sval2, packed(5 * pp * pp, 2)));
+        }
         if (prm->precision == HDG_MIXED_BF16) TRY(dalloc(&h->d_Sval16, packed(5 * pp * pp, 8)));
     }
     // Coriolis parameter per cell (mean of its vertices) on every P1 level; on a
@@ -876,7 +890,6 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     const size_t nc = h->lev.back().nv;
     TRY(dalloc(&h->d_coarse_inv, nc * nc));
     TRY(dalloc(&h->d_coarse_work, nc * nc));
-    if (mixed) TRY(dalloc(&h->d_coarse_inv32, nc * nc));
 
     h->ws = new Workspace();
     Workspace &W = *h->ws;
@@ -888,18 +901,26 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(dalloc(&W.r, W.NT));
     TRY(dalloc(&W.lam_int, W.NT));
     TRY(dalloc(&W.ycell, N * m));
-    if (h->prm.precision != HDG_FP64) TRY(dalloc(&W.x2, W.NT));
+    if (mode_ff(h->prm)) TRY(dalloc(&W.x2, W.NT));
     const size_t mm = W.m;
     W.ld = (W.NT + 3) / 4 * 4;
     // one 16-byte group of w per thread (enough loads in flight for the few-vector
     // steps at the start of a cycle), at most 8 blocks of 256 per SM of a GB300
     W.nblk_gs = int(std::min<size_t>(std::max<size_t>((W.ld / 4 + 255) / 256, 1), kMaxGsBlocks));
-    if (!mixed) {
+    if (mode_krylov64(h->prm)) {
         TRY(dalloc(&W.k64.V, (mm + 1) * W.ld));
         TRY(dalloc(&W.k64.Z, mm * W.ld));
         TRY(dalloc(&W.k64.w, W.ld));
         TRY(cudaMemsetAsync(W.k64.V, 0, sizeof(double) * (mm + 1) * W.ld, s));
         TRY(cudaMemsetAsync(W.k64.w, 0, sizeof(double) * W.ld, s));
+        if (mode_pre32(h->prm)) {
+            // the FP32 preconditioner's work vectors, its input and its output
+            TRY(dalloc(&W.k32.t0, W.NT));
+            TRY(dalloc(&W.k32.t1, W.NT));
+            TRY(dalloc(&W.k32.res, W.NT));
+            TRY(dalloc(&W.k32.b, W.NT));
+            TRY(dalloc(&W.k32.x, W.NT));
+        }
     } else {
         // FP64 vectors still needed by the FP64 operator entry points
         TRY(dalloc(&W.k64.V, W.ld));
@@ -974,10 +995,10 @@ int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solv
     cudaStream_t s = h->stream;
     h->lc.suspended = false;
     h->lc.fallback = false;
-    if (h->prm.precision == HDG_FP64) TRY(KL(HDG_PROF_RHS, 2, launch_rhs(h, r_u, r_h, W.g, W.ycell)));
+    if (!mode_ff(h->prm)) TRY(KL(HDG_PROF_RHS, 2, launch_rhs(h, r_u, r_h, W.g, W.ycell)));
     else TRY(KL(HDG_PROF_RHS, 2, launch_rhs_ff(h, r_u, r_h, W.g, W.ycell, copy_u, copy_h)));
     int rc;
-    if (h->prm.precision == HDG_FP64) {
+    if (mode_krylov64(h->prm)) {
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<double>(W.x, 0.0, W.NT, s)));
         rc = fgmres<double>(h, W.g, W.x, h->prm.rtol, h->prm.max_iter, true, true, info);
     } else {
@@ -1092,13 +1113,14 @@ int hdg_condense(hdg_handle *h) {
             TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(L.A, L.A32, size_t(L.nnz), s)));
             TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(L.dinv, L.dinv32, size_t(L.nv), s)));
         }
-        TRY(KL(HDG_PROF_CONDENSE, 1, launch_to_f32(h->d_coarse_inv, h->d_coarse_inv32, size_t(Lc.nv) * Lc.nv, s)));
-        // (hi, lo) float pairs for the two-float FP64 steps
-        const size_t N = h->N, nK = h->nK, m = h->m, pp = h->pp, NS = 5 * pp * pp;
-        TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Xb, h->d_Xb2, nK * m * N, s)));
-        TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Rm, h->d_Rm2, nK * nK * N, s)));
-        TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_W, h->d_W2, m * nK * N, s)));
-        TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Sval, h->d_Sval2, (NS + 1) / 2 * 2 * size_t(h->NF), s)));
+        if (mode_ff(h->prm)) {
+            // (hi, lo) float pairs for the two-float FP64 steps
+            const size_t N = h->N, nK = h->nK, m = h->m, pp = h->pp, NS = 5 * pp * pp;
+            TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Xb, h->d_Xb2, nK * m * N, s)));
+            TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Rm, h->d_Rm2, nK * nK * N, s)));
+            TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_W, h->d_W2, m * nK * N, s)));
+            TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Sval, h->d_Sval2, (NS + 1) / 2 * 2 * size_t(h->NF), s)));
+        }
     }
     int rc = check_status(h);
     if (rc) return rc;
@@ -1141,7 +1163,7 @@ int hdg_solve(hdg_handle *h, const double *r_u, const double *r_h, double *lambd
     // page-locked inputs of a mixed handle: the right-hand-side kernel reads them
     // in place (and keeps device copies for hdg_recover); otherwise staged copies
     const double *ru_a = host_alias(r_u), *rh_a = host_alias(r_h);
-    if (h->prm.precision != HDG_FP64 && ru_a && rh_a) {
+    if (mode_ff(h->prm) && ru_a && rh_a) {
         rc = solve_internal(h, ru_a, rh_a, loc, W.ru, W.rh);
     } else {
         TRY(cudaMemcpyAsync(W.ru, r_u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyHostToDevice, s));
@@ -1177,7 +1199,7 @@ int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h, const d
     } else if (!W.have_lambda) {
         return fail(h, HDG_ESTATE, "no lambda given and no previous solve");
     }
-    if (h->prm.precision == HDG_FP64) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, r_u, r_h, lam, u, h_out)));
+    if (!mode_ff(h->prm)) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, r_u, r_h, lam, u, h_out)));
     else TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, r_u, r_h, lam, u, h_out)));
     return HDG_OK;
 }
@@ -1205,11 +1227,11 @@ int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, const doubl
         return fail(h, HDG_ESTATE, "no lambda given and no previous solve");
     }
     double *u_a = host_alias(u), *h_a = host_alias(h_out);
-    if (h->prm.precision != HDG_FP64 && u_a && h_a) {
+    if (mode_ff(h->prm) && u_a && h_a) {
         // page-locked outputs of a mixed handle: the recovery kernel writes them in place
         TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, W.ru, W.rh, lam, u_a, h_a)));
     } else {
-        if (h->prm.precision == HDG_FP64) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, W.ru, W.rh, lam, W.u, W.hh)));
+        if (!mode_ff(h->prm)) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, W.ru, W.rh, lam, W.u, W.hh)));
         else TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, W.ru, W.rh, lam, W.u, W.hh)));
         TRY(cudaMemcpyAsync(u, W.u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyDeviceToHost, s));
         TRY(cudaMemcpyAsync(h_out, W.hh, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyDeviceToHost, s));
@@ -1320,7 +1342,7 @@ int hdg_autotune(hdg_handle *h, int32_t *choice) {
     if (rc) return rc;
     Workspace &W = *h->ws;
     cudaStream_t s = h->stream;
-    const bool f32 = h->prm.precision != HDG_FP64;
+    const bool f32 = mode_ff(h->prm);   // the Krylov space the Arnoldi steps run in
     const size_t ld = W.ld;
     const int jt = std::min(4, W.m - 1);
     // basis vectors with arbitrary finite content for timing
@@ -1450,8 +1472,8 @@ static uint64_t splitmix64(uint64_t &x) {
 int hdg_learned_init(hdg_handle *h, int hidden, int capacity, uint64_t seed, int32_t *n_params) {
     int rc = require_condensed(h);
     if (rc) return rc;
-    if (h->prm.precision == HDG_FP64 || !h->d_Sval32)
-        return fail(h, HDG_EINVAL, "the learned smoother works in the FP32 inner solves: use a mixed precision mode");
+    if (!mode_ff(h->prm) || !h->d_Sval32)
+        return fail(h, HDG_EINVAL, "the learned smoother works in the FP32 inner solves: use HDG_MIXED_FP32 or HDG_MIXED_BF16");
     if (hidden != 32 && hidden != 64) return fail(h, HDG_EINVAL, "hidden width must be 32 or 64");
     if (capacity < 1) return fail(h, HDG_EINVAL, "capacity must be positive");
     Learned &L = h->lc;

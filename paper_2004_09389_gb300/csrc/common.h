@@ -147,7 +147,7 @@ struct TailArgs {
     double omega;
     TailLevel lev[kTailMaxLevels];
     int32_t *status;                    // device error flags (8: shared-memory staging timed out)
-    const void *inv;                    // dense inverse of the last level
+    const double *inv;                  // dense FP64 inverse of the last level
     const void *b_top;                  // right-hand side of the first tail level (global)
     void *x_top;                        // its solution (global)
 };
@@ -206,7 +206,6 @@ struct hdg_handle {
     int bs_facet = 256;               // threads per block of the facet-row kernels (autotuned)
     double *d_coarse_inv = nullptr;   // dense inverse of the coarsest P1 operator
     double *d_coarse_work = nullptr;
-    float *d_coarse_inv32 = nullptr;
     hdg::Workspace *ws = nullptr;
     hdg::Prof prof;
     hdg::Learned lc;
@@ -226,6 +225,14 @@ namespace hdg {
 
 // ---------------------------------------------------------------- kernel launchers
 // condense / assembly (k_condense.cu)
+// What a precision mode uses: two-float FP64 steps around FP32 inner FGMRES
+// solves (HDG_MIXED_FP32 / _BF16); an FP64 Krylov space (HDG_FP64 and
+// HDG_MIXED_FGMRES64); an FP32 preconditioner under the FP64 FGMRES
+// (HDG_MIXED_FGMRES64).
+inline bool mode_ff(const hdg_params &p) { return p.precision == HDG_MIXED_FP32 || p.precision == HDG_MIXED_BF16; }
+inline bool mode_krylov64(const hdg_params &p) { return p.precision == HDG_FP64 || p.precision == HDG_MIXED_FGMRES64; }
+inline bool mode_pre32(const hdg_params &p) { return p.precision == HDG_MIXED_FGMRES64; }
+
 // dispatch a launch on the polynomial degree p (1..4) as a compile-time P
 #define HDG_DISPATCH_P(p, CALL) \
     switch (p) {                \
@@ -319,6 +326,9 @@ cudaError_t launch_normalize32(const float *src, float *dst, const double *nrm2,
 cudaError_t launch_to_internal32(hdg_handle *h, const float *ext, float *in);
 cudaError_t launch_to_external32(hdg_handle *h, const float *in, float *ext);
 cudaError_t launch_axpby_mixed(double *x, const float *d, const double *scale, size_t n, cudaStream_t s);
+cudaError_t launch_scale_round(const double *w, const double *hnext, double *v64, float *v32, size_t n,
+                               cudaStream_t s);
+cudaError_t launch_widen(const float *a, double *b, size_t n, cudaStream_t s);
 cudaError_t launch_d2f_scaled(const double *x, float *y, const double *scale, size_t n, cudaStream_t s);
 
 }  // namespace hdg

@@ -72,6 +72,33 @@ __device__ __forceinline__ double block_recip(const double *d) {
     return r;
 }
 
+// FP64 FGMRES with the FP32 preconditioner: v = w / h (h from the Givens step
+// of the previous Arnoldi step, reciprocal once per block) stored as the next
+// FP64 basis vector, and rounded to FP32 as the preconditioner's input; with
+// hnext null, w is the basis vector itself and is only rounded.
+__global__ void scale_round_kernel(const double *__restrict__ w, const double *__restrict__ hnext,
+                                   double *__restrict__ v64, float *__restrict__ v32, size_t n) {
+    __shared__ double inv_h;
+    if (hnext != nullptr) {
+        if (threadIdx.x == 0) inv_h = 1.0 / hnext[0];
+        __syncthreads();
+    }
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = w[i];
+    if (hnext != nullptr) {
+        v = v * inv_h;
+        v64[i] = v;
+    }
+    v32[i] = float(v);
+}
+
+// the FP32 preconditioner's output widened to the FP64 basis Z
+__global__ void widen_kernel(const float *__restrict__ a, double *__restrict__ b, size_t n) {
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = double(a[i]);
+}
+
 template <typename T>
 __global__ void scale_copy_kernel(const T *__restrict__ w, T *__restrict__ v, const double *__restrict__ denom,
                                   size_t n) {
@@ -336,6 +363,15 @@ template <typename T>
 cudaError_t launch_multi_axpy(T *w, const T *V, size_t ld, int k, const double *coef, double sign, size_t n,
                               cudaStream_t s) {
     multi_axpy_kernel<T><<<blocks(n, 256), 256, 0, s>>>(w, V, ld, k, coef, sign, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_scale_round(const double *w, const double *hnext, double *v64, float *v32, size_t n,
+                               cudaStream_t s) {
+    scale_round_kernel<<<blocks(n, 256), 256, 0, s>>>(w, hnext, v64, v32, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_widen(const float *a, double *b, size_t n, cudaStream_t s) {
+    widen_kernel<<<blocks(n, 256), 256, 0, s>>>(a, b, n);
     return cudaGetLastError();
 }
 template <typename T>

@@ -300,16 +300,16 @@ __global__ void __launch_bounds__(1024, 1) tail_kernel(TailArgs a) {
         }
         __syncthreads();
     }
-    // ---- coarsest: dense inverse
+    // ---- coarsest: dense FP64 inverse, FP64 sums in every precision
     {
-        const T *inv = static_cast<const T *>(a.inv);
+        const double *inv = static_cast<const double *>(a.inv);
         const int n = L[last].nv;
         const T *b = L[last].b;
         T *x = L[last].x;
         for (int i = tid; i < n; i += nt) {
-            T acc = T(0);
-            for (int j = 0; j < n; ++j) acc = fma(inv[size_t(i) * n + j], b[j], acc);
-            x[i] = acc;
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) acc = fma(inv[size_t(i) * n + j], double(b[j]), acc);
+            x[i] = T(acc);
         }
         __syncthreads();
     }

@@ -272,6 +272,36 @@ def test_page_locked_host_buffers_match_staged_path(kind, p):
     s.close()
 
 
+@pytest.mark.parametrize("kind,p", [("flat", 2), ("sphere", 3), ("flat", 4), ("flat", 1)])
+def test_fp64_fgmres_with_fp32_preconditioner(kind, p):
+    """HDG_MIXED_FGMRES64: FP64 FGMRES (basis, orthogonalisation, residual,
+    update, right-hand side and recovery in FP64) preconditioned by the FP32
+    two-level V-cycle with an FP64 coarsest solve.  It reaches the FP64 residual
+    target; stated tolerance vs the oracle: 1e-8 relative at rtol 1e-10; the
+    FP32 preconditioner costs at most one iteration against the FP64 one."""
+    from paper_2004_09389_gb300 import HDG_MIXED_FGMRES64
+    mesh, prob, (tau, g, H, f), ru, rh = _case(kind, p)
+    s = _solver(mesh, p, tau, g, H, f, rtol=1e-10, precision=HDG_MIXED_FGMRES64)
+    lam, info = s.solve(ru, rh)
+    u, h = s.recover()
+    (u0, h0), lam0 = prob.solve_condensed(ru, rh)
+    assert info["true_rel_res"] <= 1e-10
+    assert _rel(lam, lam0) <= 1e-8 and _rel(u, u0) <= 1e-8 and _rel(h, h0) <= 1e-8
+    s64 = _solver(mesh, p, tau, g, H, f, rtol=1e-10)
+    _, info64 = s64.solve(ru, rh)
+    assert abs(info["iters"] - info64["iters"]) <= 1
+    # the residual measured with the FP64 operator of the FP64 handle
+    gd = torch.empty(lam.shape, dtype=torch.float64, device="cuda")
+    yd = torch.empty_like(gd)
+    s64.condensed_rhs_dev(_dev(ru), _dev(rh), gd)
+    s64.trace_apply_dev(_dev(lam), yd)
+    torch.cuda.synchronize()
+    gh, yh = gd.cpu().numpy(), yd.cpu().numpy()
+    assert np.linalg.norm(gh - yh) / np.linalg.norm(gh) <= 1.5e-10
+    s.close()
+    s64.close()
+
+
 def test_zero_rhs_and_nan_rhs():
     from paper_2004_09389_gb300 import HDGError
     mesh, prob, (tau, g, H, f), ru, rh = _case("flat", 1)
