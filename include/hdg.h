@@ -289,7 +289,10 @@ HDG_API int hdg_learned_train(hdg_handle *h, int steps, int batch, double lr, do
                               double *loss_last);
 /* Copy the parameters out (get = 1) or in (get = 0), host buffer of n_params floats. */
 HDG_API int hdg_learned_params(hdg_handle *h, float *theta, int get);
-/* Use (1) or stop using (0) the learned sweep in later solves. */
+/* Use the learned sweep in later solves: 0 = off; 1 = FP32 network on the CUDA
+ * cores; 2 = the network's three layers as tcgen05 GEMMs over tiles of 128 facets
+ * (BF16 weights and activations, FP32 accumulation in tensor memory; the damped
+ * block-Jacobi part, the scale and the D^-1 solve stay FP32). */
 HDG_API int hdg_learned_enable(hdg_handle *h, int on);
 /* Loss mean_i ||r_i - S c(r_i)||^2 / ||r_i||^2 and its gradient (host buffer of
  * n_params floats) for n residuals given on the device in the lambda layout

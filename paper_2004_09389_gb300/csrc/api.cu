@@ -408,7 +408,8 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr) {
         if (learned) {
             // the learned sweep replaces the last block-Jacobi sweep
             if ((e = KL(cat_res<T>(), 1, launch_residual_t<T>(h, v, x, k.res, true))) != cudaSuccess) return e;
-            return KL(HDG_PROF_KRYLOV, 1, launch_learned_infer(h, k.res, x, z));
+            return KL(HDG_PROF_KRYLOV, 1, h->lc.tc ? launch_learned_infer_tc(h, k.res, x, z)
+                                                   : launch_learned_infer(h, k.res, x, z));
         }
         // collecting: store the residual (normalised), then the plain last sweep
         if ((e = KL(cat_res<T>(), 1, launch_residual_t<T>(h, v, x, k.res, true))) != cudaSuccess) return e;
@@ -748,6 +749,7 @@ void free_handle(hdg_handle *h) {
     {
         Learned &L = h->lc;
         dfree(L.theta); dfree(L.m); dfree(L.v); dfree(L.grad); dfree(L.act); dfree(L.gfac); dfree(L.rev);
+        dfree(L.wimg);
         dfree(L.buf); dfree(L.c); dfree(L.rn); dfree(L.gc); dfree(L.tmp); dfree(L.coef); dfree(L.nrm);
     }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -1484,6 +1486,7 @@ int hdg_learned_init(hdg_handle *h, int hidden, int capacity, uint64_t seed, int
     L.npar = learned_n_params(h->p, hidden);
     L.cap = capacity;
     TRY(dalloc(&L.theta, size_t(L.npar)));
+    TRY(dalloc(&L.wimg, learned_tc_image_elems(h->p, hidden)));
     TRY(dalloc(&L.m, size_t(L.npar)));
     TRY(dalloc(&L.v, size_t(L.npar)));
     TRY(dalloc(&L.grad, size_t(L.npar)));
@@ -1527,6 +1530,7 @@ int hdg_learned_init(hdg_handle *h, int hidden, int capacity, uint64_t seed, int
     k += hid;
     for (size_t i = 0; i < pp * size_t(hid); ++i) th[k++] = 0.01f * uni() * std::sqrt(3.f / float(hid));
     TRY(cudaMemcpyAsync(L.theta, th.data(), sizeof(float) * th.size(), cudaMemcpyHostToDevice, s));
+    TRY(launch_learned_tc_weights(h));
     TRY(cudaStreamSynchronize(s));
     L.rng = seed ^ 0x5851f42d4c957f2dull;
     L.t = 0;
@@ -1578,6 +1582,7 @@ int hdg_learned_train(hdg_handle *h, int steps, int batch, double lr, double *lo
         }
         L.t += 1;
         TRY(launch_adam(h, float(lr), int(std::min<long long>(L.t, 1 << 30))));
+        TRY(launch_learned_tc_weights(h));
         loss /= batch;
         if (!std::isfinite(loss)) return fail(h, HDG_ENAN, "NaN in the training loss");
         if (step == 0 && loss_first) *loss_first = loss;
@@ -1593,15 +1598,22 @@ int hdg_learned_params(hdg_handle *h, float *theta, int get) {
     if (!theta) return fail(h, HDG_EINVAL, "NULL pointer argument");
     const size_t bytes = sizeof(float) * h->lc.npar;
     if (get) TRY(cudaMemcpyAsync(theta, h->lc.theta, bytes, cudaMemcpyDeviceToHost, h->stream));
-    else TRY(cudaMemcpyAsync(h->lc.theta, theta, bytes, cudaMemcpyHostToDevice, h->stream));
+    else {
+        TRY(cudaMemcpyAsync(h->lc.theta, theta, bytes, cudaMemcpyHostToDevice, h->stream));
+        TRY(launch_learned_tc_weights(h));
+    }
     TRY(cudaStreamSynchronize(h->stream));
     return HDG_OK;
 }
 
 int hdg_learned_enable(hdg_handle *h, int on) {
     if (!h) return HDG_EINVAL;
+    if (on < 0 || on > 2) return fail(h, HDG_EINVAL, "on must be 0, 1 or 2");
     if (on && !h->lc.ready) return fail(h, HDG_ESTATE, "hdg_learned_init has not run");
+    // the choice of inference kernel is baked into the captured Arnoldi steps
+    if (h->lc.tc != (on == 2)) drop_graphs(h);
     h->lc.on = on != 0;
+    h->lc.tc = on == 2;
     return HDG_OK;
 }
 

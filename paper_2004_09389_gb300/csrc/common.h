@@ -105,6 +105,8 @@ struct Learned {
     int hid = 0, npar = 0;
     bool ready = false;        // initialised
     bool on = false;           // used by the FP32 preconditioner
+    bool tc = false;           // inference on the tensor cores (BF16 weights, FP32 accumulation)
+    __nv_bfloat16 *wimg = nullptr;   // BF16 weight images for the tensor-core inference
     bool suspended = false;    // switched off for the rest of a solve after a stall
     bool collecting = false;   // plain solves store the residual before the last sweep
     bool fallback = false;     // a stall was seen in the current solve
@@ -318,6 +320,9 @@ cudaError_t launch_gs_step(const T *V, size_t ld, int j, T *w, double *partial, 
                            cudaStream_t s);
 int learned_n_params(int p, int hid);
 cudaError_t launch_learned_infer(hdg_handle *h, const float *r, const float *x, float *xout);
+cudaError_t launch_learned_infer_tc(hdg_handle *h, const float *r, const float *x, float *xout);
+cudaError_t launch_learned_tc_weights(hdg_handle *h);
+size_t learned_tc_image_elems(int p, int hid);
 cudaError_t launch_learned_forward(hdg_handle *h, const float *r, float *c);
 cudaError_t launch_learned_applyT(hdg_handle *h, const float *x, float *y);
 cudaError_t launch_learned_backward(hdg_handle *h, const float *gc, const double *coef);

@@ -119,6 +119,257 @@ __global__ void __launch_bounds__(128) infer_kernel(int NF, const int32_t *__res
     for (int j = 0; j < L::PP; ++j) xout[size_t(j) * NF + e] = x[size_t(j) * NF + e] + c[j];
 }
 
+// ---------------------------------------------------------------- tensor cores
+// The same network on the 5th-generation tensor cores: the three layers are
+// GEMMs of a tile of 128 facets (rows) against weights shared by all facets,
+// BF16 operands in shared memory, FP32 accumulators in tensor memory,
+//   H1 = tanh(X W1^T + b1),  H2 = tanh(H1 W2^T + b2),  Y = H2 W3^T + b3,
+// one tcgen05.mma per 16-wide K step issued by one thread, completion signalled
+// on an mbarrier (bounded wait).  The damped block-Jacobi part omega X_self,
+// the scale s and the D^-1 solve stay FP32, so only the learned correction
+// passes through BF16.  Operands use the canonical no-swizzle K-major layout:
+// 8-row x 16-byte core matrices, element (row, k) at byte
+//   (row / 8) * (K / 8) * 128 + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2,
+// i.e. leading (K-direction) core stride 128 B, stride (row-group) K / 8 * 128 B.
+template <int P>
+struct TC {
+    static constexpr int PP = P + 1, F = 5 * PP, K1 = (F + 15) / 16 * 16, N3 = 16;
+};
+
+__device__ __forceinline__ int canon(int row, int k, int K) {
+    return (row / 8) * (K / 8) * 64 + (k / 8) * 64 + (row % 8) * 8 + (k % 8);   // in bf16 elements
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared-memory matrix descriptor (no swizzle, K-major): start, leading and
+// stride byte offsets (>> 4), descriptor version 1
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t K) {
+    uint64_t d = uint64_t((addr & 0x3FFFF) >> 4);
+    d |= uint64_t(128 >> 4) << 16;
+    d |= uint64_t(((K / 8) * 128) >> 4) << 32;
+    d |= uint64_t(1) << 46;
+    return d;
+}
+
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+// D (tensor memory) = sum over K steps of A (128 x K) B^T (N x K)
+__device__ __forceinline__ void umma_gemm(uint32_t tmem, const void *A, const void *B, int K, uint32_t idesc) {
+    for (int ks = 0; ks < K / 16; ++ks) {
+        const uint64_t ad = umma_desc(smem_addr(A) + ks * 256, K), bd = umma_desc(smem_addr(B) + ks * 256, K);
+        const uint32_t acc = ks > 0 ? 1u : 0u;
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                     :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+    }
+}
+
+// thread 0: commit the issued MMAs to the barrier and wait (bounded) for the
+// given phase; the outcome is published to the CTA
+__device__ __forceinline__ bool umma_wait(uint64_t *bar, uint32_t phase, int *flag, int32_t *status) {
+    if (threadIdx.x == 0) {
+        int ok = 0;
+        for (long long it = 0; it < (1ll << 24) && !ok; ++it) {
+            uint32_t d;
+            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                         "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(d) : "r"(smem_addr(bar)), "r"(phase) : "memory");
+            ok = int(d);
+        }
+        if (!ok) {
+            // record it and give the MMAs one more bounded wait before the
+            // tensor memory they write is freed
+            atomicOr(status, 8);
+            for (long long it = 0; it < (1ll << 24); ++it) {
+                uint32_t d;
+                asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                             "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(d) : "r"(smem_addr(bar)), "r"(phase) : "memory");
+                if (d) break;
+            }
+        }
+        *flag = ok;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return *flag != 0;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// the hardware tanh approximation (about 11 significant bits): its result is
+// rounded to BF16 (8 bits) right after
+__device__ __forceinline__ float tanh_hw(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// own row of a layer: tanh(acc + bias) in BF16, written in the canonical layout
+template <int HID>
+__device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *bias, __nv_bfloat16 *sH) {
+    const int row = threadIdx.x;
+#pragma unroll
+    for (int c0 = 0; c0 < HID; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem_row + uint32_t(c0), v);
+#pragma unroll
+        for (int g = 0; g < 16; g += 8) {
+            __align__(16) __nv_bfloat16 h8[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) h8[t] = __float2bfloat16_rn(tanh_hw(v[g + t] + bias[c0 + g + t]));
+            *reinterpret_cast<uint4 *>(sH + canon(row, c0 + g, HID)) = *reinterpret_cast<const uint4 *>(h8);
+        }
+    }
+}
+
+// x_out = x + c(r) for 128 facets per CTA
+template <int P, int HID>
+__global__ void __launch_bounds__(128) infer_tc_kernel(int NF, const int32_t *__restrict__ nbr,
+                                                       const float *__restrict__ r, const float *__restrict__ Dinv,
+                                                       const float *__restrict__ theta,
+                                                       const __nv_bfloat16 *__restrict__ wimg, float omega,
+                                                       const float *__restrict__ x, float *__restrict__ xout,
+                                                       int32_t *status) {
+    using L = LN<P, HID>;
+    using T = TC<P>;
+    constexpr int PP = T::PP, F = T::F, K1 = T::K1, N3 = T::N3;
+    constexpr int NW1 = HID * K1, NW2 = HID * HID, NW3 = N3 * HID;
+    __shared__ __align__(128) __nv_bfloat16 sX[128 * K1];
+    __shared__ __align__(128) __nv_bfloat16 sH[128 * HID];
+    __shared__ __align__(128) __nv_bfloat16 sW[NW1 + NW2 + NW3];
+    __shared__ float sb[2 * HID + PP];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int flag;
+    const int tid = threadIdx.x, warp = tid / 32;
+    const int e = blockIdx.x * 128 + tid;
+    const bool valid = e < NF;
+    // weights (BF16 images, canonical layout) and biases
+    for (int i = tid; i < (NW1 + NW2 + NW3) / 8; i += 128)
+        reinterpret_cast<uint4 *>(sW)[i] = reinterpret_cast<const uint4 *>(wimg)[i];
+    for (int i = tid; i < HID; i += 128) {
+        sb[i] = theta[L::ob1 + i];
+        sb[HID + i] = theta[L::ob2 + i];
+    }
+    if (tid < PP) sb[2 * HID + tid] = theta[L::ob3 + tid];
+    // features of the own facet (FP32), rounded to BF16 for the first GEMM
+    float X[F];
+    float s = 1.f;
+    if (valid) {
+        s = patch_features<P>(nbr, r, e, NF, X);
+    } else {
+#pragma unroll
+        for (int i = 0; i < F; ++i) X[i] = 0.f;
+    }
+#pragma unroll
+    for (int k0 = 0; k0 < K1; k0 += 8) {
+        __align__(16) __nv_bfloat16 x8[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) x8[t] = __float2bfloat16_rn(k0 + t < F ? X[k0 + t] : 0.f);
+        *reinterpret_cast<uint4 *>(sX + canon(tid, k0, K1)) = *reinterpret_cast<const uint4 *>(x8);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(&tmem_base)), "r"(HID) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t tmem_row = tmem + (uint32_t(warp * 32) << 16);
+    bool ok = true;
+    // layer 1
+    if (tid == 0) {
+        umma_gemm(tmem, sX, sW, K1, umma_idesc(128, HID));
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(smem_addr(&bar)) : "memory");
+    }
+    ok = umma_wait(&bar, 0, &flag, status);
+    if (ok) hidden_epilogue<HID>(tmem_row, sb, sH);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // layer 2 (same tensor-memory columns, read above)
+    if (ok) {
+        if (tid == 0) {
+            umma_gemm(tmem, sH, sW + NW1, HID, umma_idesc(128, HID));
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_addr(&bar)) : "memory");
+        }
+        ok = umma_wait(&bar, 1, &flag, status);
+        if (ok) hidden_epilogue<HID>(tmem_row, sb + HID, sH);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // layer 3 and the FP32 output
+    if (ok) {
+        if (tid == 0) {
+            umma_gemm(tmem, sH, sW + NW1 + NW2, HID, umma_idesc(128, N3));
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_addr(&bar)) : "memory");
+        }
+        ok = umma_wait(&bar, 0, &flag, status);
+        if (ok) {
+            float acc[16];
+            tmem_ld16(tmem_row, acc);
+            if (valid) {
+                float y[PP], c[PP];
+#pragma unroll
+                for (int j = 0; j < PP; ++j) y[j] = (acc[j] + sb[2 * HID + j] + omega * X[j]) * s;
+                dinv_apply<P, false>(Dinv, e, NF, y, c);
+#pragma unroll
+                for (int j = 0; j < PP; ++j) xout[size_t(j) * NF + e] = x[size_t(j) * NF + e] + c[j];
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(HID) : "memory");
+}
+
+// theta -> BF16 images of W1, W2, W3 in the canonical layout (zero padding)
+template <int P, int HID>
+__global__ void tc_weights_kernel(const float *__restrict__ theta, __nv_bfloat16 *__restrict__ img) {
+    using L = LN<P, HID>;
+    using T = TC<P>;
+    constexpr int F = T::F, K1 = T::K1, N3 = T::N3, PP = T::PP;
+    constexpr int NW1 = HID * K1, NW2 = HID * HID, NW3 = N3 * HID;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < NW1) {
+        const int j = i / K1, k = i % K1;
+        img[canon(j, k, K1)] = __float2bfloat16_rn(k < F ? theta[L::oW1 + j * F + k] : 0.f);
+    } else if (i < NW1 + NW2) {
+        const int q = i - NW1, j = q / HID, k = q % HID;
+        img[NW1 + canon(j, k, HID)] = __float2bfloat16_rn(theta[L::oW2 + j * HID + k]);
+    } else if (i < NW1 + NW2 + NW3) {
+        const int q = i - NW1 - NW2, j = q / HID, k = q % HID;
+        img[NW1 + NW2 + canon(j, k, HID)] = __float2bfloat16_rn(j < PP ? theta[L::oW3 + j * HID + k] : 0.f);
+    }
+}
+
 // training forward for one residual: c (internal layout) and the per-facet
 // activations kept for the backward pass: act[e] = X (F) | h1 (HID) | h2 (HID) | s
 template <int P, int HID>
@@ -329,6 +580,26 @@ cudaError_t launch_learned_infer(hdg_handle *h, const float *r, const float *x, 
                     (infer_kernel<P, HID><<<blocks(h->NF, 128), 128, 0, h->stream>>>(h->NF, h->d_nbr, r, h->d_Dinv32,
                                                                                       h->lc.theta, float(h->prm.omega), x,
                                                                                       xout)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_learned_infer_tc(hdg_handle *h, const float *r, const float *x, float *xout) {
+    HDG_LN_DISPATCH(h->p, h->lc.hid,
+                    (infer_tc_kernel<P, HID><<<blocks(h->NF, 128), 128, 0, h->stream>>>(
+                        h->NF, h->d_nbr, r, h->d_Dinv32, h->lc.theta, h->lc.wimg, float(h->prm.omega), x, xout,
+                        h->d_status)));
+    return cudaGetLastError();
+}
+
+size_t learned_tc_image_elems(int p, int hid) {
+    const int F = 5 * (p + 1), K1 = (F + 15) / 16 * 16;
+    return size_t(hid) * K1 + size_t(hid) * hid + size_t(16) * hid;
+}
+
+cudaError_t launch_learned_tc_weights(hdg_handle *h) {
+    const size_t n = learned_tc_image_elems(h->p, h->lc.hid);
+    HDG_LN_DISPATCH(h->p, h->lc.hid,
+                    (tc_weights_kernel<P, HID><<<blocks(n, 256), 256, 0, h->stream>>>(h->lc.theta, h->lc.wimg)));
     return cudaGetLastError();
 }
 

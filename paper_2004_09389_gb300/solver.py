@@ -177,8 +177,10 @@ class HDGSolver:
         assert th.size == self.n_learned_params
         L.check(self.h, self.lib.hdg_learned_params(self.h, th.ctypes.data, 0))
 
-    def learned_enable(self, on: bool = True) -> None:
-        L.check(self.h, self.lib.hdg_learned_enable(self.h, 1 if on else 0))
+    def learned_enable(self, on: bool = True, tensor_cores: bool = False) -> None:
+        """Use the learned sweep in later solves; tensor_cores runs its network
+        as BF16 tcgen05 GEMMs (FP32 accumulation) instead of FP32 on the CUDA cores."""
+        L.check(self.h, self.lib.hdg_learned_enable(self.h, (2 if tensor_cores else 1) if on else 0))
 
     def learned_loss_grad_dev(self, R):
         """R: float32 device tensor [n, n_facets, p+1]; returns (loss, gradient)."""

@@ -152,3 +152,58 @@ def test_training_improves_the_preconditioner():
     assert learned <= plain
     s.close()
     s64.close()
+
+
+@pytest.mark.parametrize("p,hid,n", [(1, 32, 8), (3, 64, 8), (2, 64, 32), (4, 32, 32)])
+def test_tensor_core_network_matches_fp32(p, hid, n):
+    """The network's three layers as tcgen05 GEMMs over tiles of 128 facets
+    (BF16 weights and activations, FP32 accumulation in tensor memory) against
+    the FP32 network on the CUDA cores, one preconditioner application with the
+    learned sweep: the difference is at most 3 % of the learned part (the FP32
+    output minus the output with the network's output layer zeroed; BF16 keeps
+    8 significant bits per rounding, three layers deep); the learned sweep is
+    the last post-smoothing sweep, so that part is a small share of the output.  n = 8 leaves a ragged
+    last tile (192 facets), n = 32 fills 24 tiles.  A full solve with the
+    tensor-core sweep still reaches its tolerance."""
+    from paper_2004_09389_gb300 import HDGSolver
+    mesh, tau, g, H, f = _flat(n, p)
+    s = HDGSolver(mesh, p, tau, g, H, f_vertex=f, precision=1, rtol=1e-8)
+    npar = s.learned_init(hidden=hid, capacity=4)
+    rng = np.random.default_rng(1)
+    theta = (0.3 * rng.standard_normal(npar)).astype(np.float32)
+    s.set_learned_params(theta)
+    pp = p + 1
+    nt = s.n_facets * pp
+    v = torch.from_numpy(np.random.default_rng(2).standard_normal(nt).astype(np.float32)).cuda()
+
+    def z_of(tc):
+        s.learned_enable(True, tensor_cores=tc)
+        z = torch.empty_like(v)
+        s.precond_apply32_dev(v, z)
+        torch.cuda.synchronize()
+        return z.cpu().numpy().astype(np.float64)
+
+    z32 = z_of(False)
+    ztc = z_of(True)
+    shapes = LN.param_shapes(5 * pp, hid, pp)
+    n_out = int(np.prod(shapes[-2][1])) + int(np.prod(shapes[-1][1]))
+    theta0 = theta.copy()
+    theta0[-n_out:] = 0.0                       # W3 and b3: the learned part off
+    s.set_learned_params(theta0)
+    zlin = z_of(False)
+    part = np.linalg.norm(z32 - zlin)
+    # the learned sweep is the last post-smoothing sweep: its share of the
+    # preconditioner's output is small but well above rounding
+    assert part > 1e-3 * np.linalg.norm(z32)
+    assert np.all(np.isfinite(ztc))
+    ratio = np.linalg.norm(ztc - z32) / part
+    print(f"p={p} hidden={hid} n={n}: |z_tc - z_fp32| / |learned part| = {ratio:.2e}")
+    assert ratio <= 0.03
+    # a full solve with the tensor-core sweep (the stall fallback may take over)
+    s.set_learned_params(theta)
+    s.learned_enable(True, tensor_cores=True)
+    ru = np.random.default_rng(3).standard_normal((mesh.n_cells, 2, (p + 1) * (p + 2) // 2))
+    rh = np.random.default_rng(4).standard_normal((mesh.n_cells, (p + 1) * (p + 2) // 2))
+    _, info = s.solve(ru, rh)
+    assert info["true_rel_res"] <= 1e-8
+    s.close()
