@@ -264,6 +264,7 @@ def gpu_arm(args, rank: int, world: int):
         s = HDGSolver(mesh, args.p, tau, g_, H_, f_vertex=f, rtol=args.rtol, precision=prec,
                       inner_rtol=args.inner_rtol, restart=args.restart, reorth=args.reorth)
         NF, pp = s.n_facets, args.p + 1
+        tuned = s.autotune() if args.autotune else None
         # condensation (step 0, once per operator), timed warm and apart from the solves
         torch.cuda.synchronize()
         t_c = time.perf_counter()
@@ -341,7 +342,7 @@ def gpu_arm(args, rank: int, world: int):
         levels = [mesh] + list(mesh.levels)
         nK, m = 3 * s.n_p, 3 * pp
         out[arm] = dict(ms=ms, infos=infos, clocks=clk, launches=launches, prof=prof, e2e_s=e2e_s,
-                        condense_ms=condense_ms, n_p=s.n_p, prof_steps=max(1, min(args.steps, 3)),
+                        condense_ms=condense_ms, n_p=s.n_p, prof_steps=max(1, min(args.steps, 3)), tuned=tuned,
                         h2d=h2d, d2h=d2h, NF=NF, pp=pp, n_cells=s.n_cells,
                         coarse=(f"P1 geometric V-cycle over {len(levels)} levels, {levels[0].n_vertices:,} -> "
                                 f"{levels[-1].n_vertices} vertices (dense coarsest solve)"),
@@ -524,7 +525,7 @@ def main():
                     help="solver arms to run (profiling runs may pick one)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--batch", type=int, default=0, help="run the batched-solve benchmark with this many problems")
-    ap.add_argument("--autotune", action="store_true", help="autotune launch shapes per handle (batch mode)")
+    ap.add_argument("--autotune", action="store_true", help="autotune launch shapes per handle (off by default: on the 256x256x2 workload the defaults measured faster)")
     args = ap.parse_args()
     if args.batch:
         batch_main(args)
