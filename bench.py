@@ -234,6 +234,23 @@ def cpu_baseline_entry(p, courant, steps, kind="flat"):
             "wall_s": time.perf_counter() - t0}
 
 
+# ---------------------------------------------------------------- replicas
+def max_over_ranks(dist, x: float, device) -> float:
+    """Largest x over the ranks of the process group (x itself without one).
+    The replicas share nothing on the data path; only their timings meet here."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, steps: int, ms_max: float) -> float:
+    """Whole-job solves/s: every rank solves `steps` problems; the slowest rank's time counts."""
+    return world * steps / (ms_max * 1e-3)
+
+
 # ---------------------------------------------------------------- GPU arms
 def gpu_arm(args, rank: int, world: int):
     import numpy as np
@@ -301,10 +318,7 @@ def gpu_arm(args, rank: int, world: int):
         ms = e0.elapsed_time(e1)
         clk = clocks.stop(t_wall0, t_wall1) if clocks else None
         launches = sum(n for _, n in s.profile_read().values())
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(dist, ms, dev)
         # second pass with per-kernel event timing for the roofline
         s.profile_enable(timing=True)
         for _ in range(max(1, min(args.steps, 3))):
@@ -333,10 +347,7 @@ def gpu_arm(args, rank: int, world: int):
             host_step()
         barrier()
         e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(dist, e2e_s, dev)
         h2d = ru.nbytes + rh.nbytes
         d2h = lam_h.numel() * 8 + u_h.numel() * 8 + hh_h.numel() * 8
         levels = [mesh] + list(mesh.levels)
@@ -577,8 +588,8 @@ def main():
         peaks = json.load(open(ppath))
     mx, fp, mb, fg = res["mixed"], res["fp64"], res["mixed_bf16"], res["fgmres64"]
     K = args.steps
-    value = world * K / (mx["ms"] * 1e-3)
-    fp_value = world * K / (fp["ms"] * 1e-3)
+    value = replica_value(world, K, mx["ms"])
+    fp_value = replica_value(world, K, fp["ms"])
     it_mx = [i["iters"] for i in mx["infos"]]
     it_fp = [i["iters"] for i in fp["infos"]]
     line = {
