@@ -470,6 +470,110 @@ def batch_workload(n_problems: int, seed: int):
     return out
 
 
+def sequence_main(args):
+    """Learned sweep over a sequence of solves: icosahedral sphere r = 7 (327,680
+    triangles), p = 2, Courant 8, f = 2 Omega sin(lat), H drawn by the seed; a
+    50-step sequence r^(s+1) = 0.98 r^(s) + 0.2 xi^(s) (normalised), each xi a
+    seeded random combination of a pool of 12 spherical-harmonic fields up to
+    degree 32 (generated once).  The network (hidden 64, inference on the tensor
+    cores) is trained on the r = 5 sphere (same p, physics and Courant number) on
+    residuals that plain solves of spherical-harmonic right-hand sides produce,
+    and its parameters are copied to the r = 7 handle; the sequence is timed
+    with the learned sweep off and on (mixed precision both times), every step
+    one solve + recovery."""
+    import numpy as np
+    import torch
+    import hdg_inputs as I
+    from paper_2004_09389_gb300 import HDGSolver, HDG_MIXED_FP32, build
+    build.build()
+    dev = torch.device("cuda", 0)
+    r, p, steps = 7, 2, 50
+    mesh = I.sphere_hierarchy(r, RADIUS, r_coarsest=max(r - 5, 1))
+    H = float(np.random.default_rng(args.seed).uniform(5e3, 1e4))
+    tau = args.courant * mesh.h / math.sqrt(G * H)
+    f = I.coriolis_sphere(mesh, OMEGA)
+    t0 = time.perf_counter()
+    pool = [I.spherical_harmonic_rhs(mesh, p, args.seed + 100 + k, lmax=32) for k in range(12)]
+    t_gen = time.perf_counter() - t0
+    PU = np.stack([a for a, _ in pool])
+    PH = np.stack([b for _, b in pool])
+    rng = np.random.default_rng(args.seed + 7)
+
+    def combo():
+        c = rng.standard_normal(len(pool))
+        u, h = np.tensordot(c, PU, 1), np.tensordot(c, PH, 1)
+        nrm = math.sqrt((np.sum(u * u) + np.sum(h * h)) / (u.size + h.size))
+        return u / nrm, h / nrm
+
+    # training on the r = 5 sphere (same p, physics and Courant number): the
+    # network sees RMS-normalised facet patches, so its parameters carry over
+    rt = 5
+    mesh_t = I.sphere_hierarchy(rt, RADIUS, r_coarsest=1)
+    tau_t = args.courant * mesh_t.h / math.sqrt(G * H)
+    st = HDGSolver(mesh_t, p, tau_t, G, H, f_vertex=I.coriolis_sphere(mesh_t, OMEGA), precision=HDG_MIXED_FP32,
+                   rtol=args.rtol)
+    npar = st.learned_init(hidden=64, capacity=256, seed=args.seed)
+    n_stored = 0
+    for k in range(8):
+        u_t, h_t = I.spherical_harmonic_rhs(mesh_t, p, args.seed + 500 + k, lmax=32)
+        n_stored = st.learned_collect_dev(torch.from_numpy(u_t).to(dev), torch.from_numpy(h_t).to(dev))
+    t0 = time.perf_counter()
+    l0, l1 = st.learned_train(steps=400, batch=8, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    theta = st.learned_params()
+    st.close()
+    s = HDGSolver(mesh, p, tau, G, H, f_vertex=f, precision=HDG_MIXED_FP32, rtol=args.rtol)
+    s.learned_init(hidden=64, capacity=1, seed=args.seed)
+    s.set_learned_params(theta)
+    # the sequence, resident on the device
+    u, h = combo()
+    seq = []
+    for k in range(steps):
+        seq.append((torch.from_numpy(u).to(dev), torch.from_numpy(h).to(dev)))
+        xu, xh = combo()
+        u, h = 0.98 * u + 0.2 * xu, 0.98 * h + 0.2 * xh
+        nrm = math.sqrt((np.sum(u * u) + np.sum(h * h)) / (u.size + h.size))
+        u, h = u / nrm, h / nrm
+    lam = torch.empty((s.n_facets, p + 1), dtype=torch.float64, device=dev)
+    uo = torch.empty((s.n_cells, 2, s.n_p), dtype=torch.float64, device=dev)
+    ho = torch.empty((s.n_cells, s.n_p), dtype=torch.float64, device=dev)
+
+    def run(on):
+        s.learned_enable(on, tensor_cores=True)
+        for k in range(3):                                   # warm-up (graph capture)
+            s.solve_dev(*seq[k], lam)
+        torch.cuda.synchronize()
+        infos = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        for ru_d, rh_d in seq:
+            infos.append(s.solve_dev(ru_d, rh_d, lam))
+            s.recover_dev(ru_d, rh_d, lam, uo, ho)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return {"value": steps / (ms * 1e-3), "unit": "solves/s", "ms_per_step": ms / steps,
+                "iters": [i["iters"] for i in infos], "fallbacks": int(sum(i["fallback_used"] for i in infos)),
+                "max_true_rel_res": max(i["true_rel_res"] for i in infos)}
+
+    plain = run(False)
+    learned = run(True)
+    line = {"metric": METRIC + " (learned sequence)", "value": learned["value"], "unit": "solves/s",
+            "n_gpus": 1, "steps": steps, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": (f"icosahedral sphere r={r} ({mesh.n_cells:,} triangles), HDG p={p}, Courant "
+                                    f"{args.courant:g}, H={H:.0f} m, 50-step sequence r <- 0.98 r + 0.2 xi over a "
+                                    f"pool of 12 spherical-harmonic fields to degree 32"),
+                       "network": f"facet patch, hidden 64, {npar} parameters, tcgen05 inference (BF16 x BF16 -> FP32)",
+                       "training": {"mesh": f"icosahedral sphere r={rt}", "residuals": n_stored, "plain_solves": 8,
+                                    "steps": 400, "batch": 8,
+                                    "loss_first": l0, "loss_last": l1, "seconds": t_train},
+                       "field_generation_s": t_gen},
+            "learned": learned, "plain_mixed": plain,
+            "learned_vs_plain": learned["value"] / plain["value"]}
+    s.close()
+    print(json.dumps(line))
+
+
 def batch_main(args):
     import numpy as np
     import torch
@@ -521,8 +625,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--p", type=int, default=3)
-    ap.add_argument("--workload", default="flat", choices=["flat", "sphere"],
-                    help="flat: periodic 256x256x2 square (the headline); sphere: icosahedral sphere r=6")
+    ap.add_argument("--workload", default="flat", choices=["flat", "sphere", "sequence"],
+                    help="flat: periodic 256x256x2 square (the headline); sphere: icosahedral sphere r=6; "
+                         "sequence: learned sweep over a 50-step sequence on the r=7 sphere")
     ap.add_argument("--courant", type=float, default=8.0)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--inner-rtol", dest="inner_rtol", type=float, default=1e-4)
@@ -540,6 +645,9 @@ def main():
     args = ap.parse_args()
     if args.batch:
         batch_main(args)
+        return
+    if args.workload == "sequence":
+        sequence_main(args)
         return
 
     if args.oracle_sample:
