@@ -749,7 +749,7 @@ void free_handle(hdg_handle *h) {
     {
         Learned &L = h->lc;
         dfree(L.theta); dfree(L.m); dfree(L.v); dfree(L.grad); dfree(L.act); dfree(L.gfac); dfree(L.rev);
-        dfree(L.wimg);
+        dfree(L.wimg); dfree(L.gpart);
         dfree(L.buf); dfree(L.c); dfree(L.rn); dfree(L.gc); dfree(L.tmp); dfree(L.coef); dfree(L.nrm);
     }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -1492,6 +1492,7 @@ int hdg_learned_init(hdg_handle *h, int hidden, int capacity, uint64_t seed, int
     TRY(dalloc(&L.grad, size_t(L.npar)));
     TRY(dalloc(&L.act, NF * (F + 2 * hidden + 1)));
     TRY(dalloc(&L.gfac, NF * (2 * hidden + pp)));
+    TRY(dalloc(&L.gpart, (NF + 1023) / 1024 * size_t(L.npar)));
     TRY(dalloc(&L.rev, 4 * NF));
     TRY(dalloc(&L.buf, size_t(capacity) * NT));
     TRY(dalloc(&L.c, NT));

@@ -115,6 +115,7 @@ struct Learned {
     uint64_t rng = 0;
     float *theta = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     float *act = nullptr, *gfac = nullptr;   // per-facet activations / gradients (training)
+    float *gpart = nullptr;                  // per-block partial weight gradients [ceil(NF/1024)][npar]
     int32_t *rev = nullptr;                  // [4][NF] neighbour f*8 + block index pointing back
     float *buf = nullptr;                    // [cap][NT] normalised training residuals
     float *c = nullptr, *rn = nullptr, *gc = nullptr, *tmp = nullptr;

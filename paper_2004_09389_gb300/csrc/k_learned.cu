@@ -480,30 +480,71 @@ __global__ void __launch_bounds__(128) train_backward_kernel(int NF, const float
     for (int j = 0; j < L::PP; ++j) go[2 * HID + j] = gy[j];
 }
 
-// grad[out_off + i * nb + j] += sum_e A[e][ao + i] * B[e][bo + j] (B = 1 when nb = 0: bias,
-// written at out_off + i).  One block per i, threads over facets, fixed-order
-// tree reduction per j: deterministic.
-__global__ void outer_reduce_kernel(int NF, const float *__restrict__ A, int lda, int ao,
-                                    const float *__restrict__ Bm, int ldb, int bo, int nb, float *__restrict__ grad,
-                                    int out_off) {
-    __shared__ float red[256];
-    const int i = blockIdx.x;
-    const int ncol = nb > 0 ? nb : 1;
-    for (int j = 0; j < ncol; ++j) {
-        float acc = 0.f;
-        for (int e = threadIdx.x; e < NF; e += blockDim.x) {
-            const float av = A[size_t(e) * lda + ao + i];
-            acc = fmaf(av, nb > 0 ? Bm[size_t(e) * ldb + bo + j] : 1.f, acc);
-        }
-        red[threadIdx.x] = acc;
+// Weight gradients: every parameter is a sum over facets of a gradient column
+// (gfac = [ga1 | ga2 | gy], NG per facet) times an activation column (act =
+// [X | h1 | h2 | s], NA per facet) or 1 for a bias.  A block takes kGradChunk
+// facets, staged 32 rows at a time in shared memory (coalesced rows); each
+// thread accumulates its parameters (tid, tid + 256, ...) and writes one
+// partial per parameter; grad_reduce_kernel adds the partials in block order.
+constexpr int kGradChunk = 1024, kGradRows = 32, kGradMaxPer = 25;   // 256 x 25 >= 6149 (p = 4, hidden 64)
+
+__device__ __forceinline__ void grad_param_cols(int idx, int hid, int F, int pp, int &q, int &a) {
+    const int n1 = hid * F, n2 = n1 + hid, n3 = n2 + hid * hid, n4 = n3 + hid, n5 = n4 + pp * hid;
+    if (idx < n1) { q = idx / F; a = idx % F; }
+    else if (idx < n2) { q = idx - n1; a = -1; }
+    else if (idx < n3) { q = hid + (idx - n2) / hid; a = F + (idx - n2) % hid; }
+    else if (idx < n4) { q = hid + (idx - n3); a = -1; }
+    else if (idx < n5) { q = 2 * hid + (idx - n4) / hid; a = F + hid + (idx - n4) % hid; }
+    else { q = 2 * hid + (idx - n5); a = -1; }
+}
+
+__global__ void __launch_bounds__(256) grad_partial_kernel(int NF, int hid, int F, int pp, int npar,
+                                                           const float *__restrict__ gfac,
+                                                           const float *__restrict__ act,
+                                                           float *__restrict__ partial) {
+    extern __shared__ float sm[];
+    const int NG = 2 * hid + pp, NA = F + 2 * hid + 1;
+    float *sG = sm, *sA = sm + kGradRows * NG;
+    float acc[kGradMaxPer];
+    int qc[kGradMaxPer], ac[kGradMaxPer];
+#pragma unroll
+    for (int t = 0; t < kGradMaxPer; ++t) {
+        acc[t] = 0.f;
+        const int idx = threadIdx.x + t * blockDim.x;
+        qc[t] = 0;
+        ac[t] = -1;
+        if (idx < npar) grad_param_cols(idx, hid, F, pp, qc[t], ac[t]);
+    }
+    const int e0 = blockIdx.x * kGradChunk, e1 = min(NF, e0 + kGradChunk);
+    for (int eb = e0; eb < e1; eb += kGradRows) {
+        const int nr = min(kGradRows, e1 - eb);
+        for (int i = threadIdx.x; i < nr * NG; i += blockDim.x) sG[i] = gfac[size_t(eb) * NG + i];
+        for (int i = threadIdx.x; i < nr * NA; i += blockDim.x) sA[i] = act[size_t(eb) * NA + i];
         __syncthreads();
-        for (int sft = blockDim.x / 2; sft > 0; sft >>= 1) {
-            if (threadIdx.x < sft) red[threadIdx.x] += red[threadIdx.x + sft];
-            __syncthreads();
+#pragma unroll
+        for (int t = 0; t < kGradMaxPer; ++t) {
+            if (threadIdx.x + t * blockDim.x < npar) {
+                float v = acc[t];
+                for (int r = 0; r < nr; ++r)
+                    v = fmaf(sG[r * NG + qc[t]], ac[t] >= 0 ? sA[r * NA + ac[t]] : 1.f, v);
+                acc[t] = v;
+            }
         }
-        if (threadIdx.x == 0) grad[out_off + (nb > 0 ? i * nb + j : i)] += red[0];
         __syncthreads();
     }
+#pragma unroll
+    for (int t = 0; t < kGradMaxPer; ++t) {
+        const int idx = threadIdx.x + t * blockDim.x;
+        if (idx < npar) partial[size_t(blockIdx.x) * npar + idx] = acc[t];
+    }
+}
+
+__global__ void grad_reduce_kernel(int nblk, int npar, const float *__restrict__ partial, float *__restrict__ grad) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= npar) return;
+    float v = 0.f;
+    for (int b = 0; b < nblk; ++b) v += partial[size_t(b) * npar + idx];
+    grad[idx] += v;
 }
 
 __global__ void adam_kernel(int n, float *__restrict__ theta, float *__restrict__ m, float *__restrict__ v,
@@ -630,15 +671,16 @@ cudaError_t launch_learned_backward(hdg_handle *h, const float *gc, const double
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int NA = F + 2 * hid + 1, NG = 2 * hid + pp;
-    const int oW1 = 0, ob1 = hid * F, oW2 = ob1 + hid, ob2 = oW2 + hid * hid, oW3 = ob2 + hid, ob3 = oW3 + pp * hid;
-    float *gr = h->lc.grad;
     // dW1 = ga1 X^T, db1 = sum ga1; dW2 = ga2 h1^T, db2; dW3 = gy h2^T, db3
-    outer_reduce_kernel<<<hid, 256, 0, h->stream>>>(h->NF, h->lc.gfac, NG, 0, h->lc.act, NA, 0, F, gr, oW1);
-    outer_reduce_kernel<<<hid, 256, 0, h->stream>>>(h->NF, h->lc.gfac, NG, 0, nullptr, 0, 0, 0, gr, ob1);
-    outer_reduce_kernel<<<hid, 256, 0, h->stream>>>(h->NF, h->lc.gfac, NG, hid, h->lc.act, NA, F, hid, gr, oW2);
-    outer_reduce_kernel<<<hid, 256, 0, h->stream>>>(h->NF, h->lc.gfac, NG, hid, nullptr, 0, 0, 0, gr, ob2);
-    outer_reduce_kernel<<<pp, 256, 0, h->stream>>>(h->NF, h->lc.gfac, NG, 2 * hid, h->lc.act, NA, F + hid, hid, gr, oW3);
-    outer_reduce_kernel<<<pp, 256, 0, h->stream>>>(h->NF, h->lc.gfac, NG, 2 * hid, nullptr, 0, 0, 0, gr, ob3);
+    const int npar = h->lc.npar;
+    if (npar > 256 * kGradMaxPer) return cudaErrorInvalidValue;
+    const int nblk = int((h->NF + kGradChunk - 1) / kGradChunk);
+    const size_t smem = sizeof(float) * kGradRows * size_t(NG + NA);
+    grad_partial_kernel<<<nblk, 256, smem, h->stream>>>(int(h->NF), hid, F, pp, npar, h->lc.gfac, h->lc.act,
+                                                         h->lc.gpart);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    grad_reduce_kernel<<<blocks(npar, 256), 256, 0, h->stream>>>(nblk, npar, h->lc.gpart, h->lc.grad);
     return cudaGetLastError();
 }
 
