@@ -175,8 +175,10 @@ HDG_API int hdg_solve_dev(hdg_handle *h, const double *r_u, const double *r_h, d
                   hdg_solve_info *info);
 
 /* Step 3 with host buffers: (u, h) from lambda and the right-hand side.
- * lambda may be NULL to use the handle's last solution; r_u / r_h may be NULL
- * to use the right-hand side of the handle's last solve. */
+ * lambda may be NULL to use the handle's last solution; r_u and r_h may both
+ * be NULL to use the right-hand side of the handle's last hdg_solve (one NULL
+ * and one not: HDG_EINVAL).  Explicit inputs serve this call only: a later
+ * call with NULLs still selects the last solve's data. */
 HDG_API int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lambda,
                 double *u, double *h_out);
 HDG_API int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h, const double *lambda,

@@ -72,6 +72,7 @@ struct Workspace {
     int32_t *host_flags = nullptr;
     // staging for host-pointer entry points and for recover defaults
     double *ru = nullptr, *rh = nullptr, *lam_ext = nullptr, *u = nullptr, *hh = nullptr;
+    double *ru_x = nullptr, *rh_x = nullptr;   // explicit hdg_recover inputs (ru/rh keep the last solve's)
     bool have_rhs = false, have_lambda = false;
     double *lam_int = nullptr;    // last solution, internal layout
 };
@@ -742,6 +743,7 @@ void free_handle(hdg_handle *h) {
             for (auto &G : gv)
                 if (G.exec) cudaGraphExecDestroy(G.exec); dfree(W.beta); dfree(W.y); dfree(W.partial); dfree(W.flags);
         dfree(W.ru); dfree(W.rh); dfree(W.lam_ext); dfree(W.u); dfree(W.hh); dfree(W.lam_int);
+        dfree(W.ru_x); dfree(W.rh_x);
         if (W.host_buf) cudaFreeHost(W.host_buf);
         if (W.host_flags) cudaFreeHost(W.host_flags);
         delete h->ws;
@@ -1210,13 +1212,29 @@ int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, const doubl
     int rc = require_condensed(h);
     if (rc) return rc;
     if (!u || !h_out) return fail(h, HDG_EINVAL, "NULL output pointer");
+    if (!r_u != !r_h) return fail(h, HDG_EINVAL, "r_u and r_h must both be given or both be NULL");
     rc = ensure_staging(h);
     if (rc) return rc;
     Workspace &W = *h->ws;
     cudaStream_t s = h->stream;
-    if (r_u && r_h) {
-        TRY(cudaMemcpyAsync(W.ru, r_u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyHostToDevice, s));
-        TRY(cudaMemcpyAsync(W.rh, r_h, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyHostToDevice, s));
+    // explicit inputs never overwrite the last solve's right-hand side, which a
+    // later call with r_u = r_h = NULL still selects
+    const double *ru = W.ru, *rh = W.rh;
+    if (r_u) {
+        const double *ru_a = host_alias(r_u), *rh_a = host_alias(r_h);
+        if (mode_ff(h->prm) && ru_a && rh_a) {
+            ru = ru_a;
+            rh = rh_a;
+        } else {
+            if (!W.ru_x) {
+                TRY(dalloc(&W.ru_x, size_t(h->N) * 2 * h->np));
+                TRY(dalloc(&W.rh_x, size_t(h->N) * h->np));
+            }
+            TRY(cudaMemcpyAsync(W.ru_x, r_u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyHostToDevice, s));
+            TRY(cudaMemcpyAsync(W.rh_x, r_h, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyHostToDevice, s));
+            ru = W.ru_x;
+            rh = W.rh_x;
+        }
     } else if (!W.have_rhs) {
         return fail(h, HDG_ESTATE, "no right-hand side given and none kept from hdg_solve");
     }
@@ -1231,10 +1249,10 @@ int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, const doubl
     double *u_a = host_alias(u), *h_a = host_alias(h_out);
     if (mode_ff(h->prm) && u_a && h_a) {
         // page-locked outputs of a mixed handle: the recovery kernel writes them in place
-        TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, W.ru, W.rh, lam, u_a, h_a)));
+        TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, ru, rh, lam, u_a, h_a)));
     } else {
-        if (!mode_ff(h->prm)) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, W.ru, W.rh, lam, W.u, W.hh)));
-        else TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, W.ru, W.rh, lam, W.u, W.hh)));
+        if (!mode_ff(h->prm)) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, ru, rh, lam, W.u, W.hh)));
+        else TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, ru, rh, lam, W.u, W.hh)));
         TRY(cudaMemcpyAsync(u, W.u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyDeviceToHost, s));
         TRY(cudaMemcpyAsync(h_out, W.hh, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyDeviceToHost, s));
     }

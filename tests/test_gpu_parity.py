@@ -272,6 +272,39 @@ def test_page_locked_host_buffers_match_staged_path(kind, p):
     s.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_explicit_recover_inputs_leave_the_last_solve_selected(precision):
+    """hdg_recover with explicit r_u, r_h (pageable, and page-locked on a
+    mixed handle) serves that call only: a following hdg_recover with NULLs
+    still uses the last solve's right-hand side.  One of r_u / r_h NULL is
+    rejected."""
+    import ctypes
+    from paper_2004_09389_gb300 import _lib, HDGError
+    mesh, prob, (tau, g, H, f), ru, rh = _case("flat", 2)
+    s = _solver(mesh, 2, tau, g, H, f, rtol=1e-10, precision=precision)
+    lam, _ = s.solve(ru, rh)
+    u0, h0 = s.recover()
+    rng = np.random.default_rng(7)
+    ru2, rh2 = rng.standard_normal(ru.shape), rng.standard_normal(rh.shape)
+    u2_ref, h2_ref = prob.recover(lam.reshape(-1), ru2, rh2)
+    u2, h2 = s.recover(ru2, rh2, lam)
+    assert _rel(u2, u2_ref) <= 1e-12 and _rel(h2, h2_ref) <= 1e-12
+    u1, h1 = s.recover()
+    assert np.array_equal(u1, u0) and np.array_equal(h1, h0)
+    ru_p = torch.from_numpy(ru2.copy()).pin_memory()
+    rh_p = torch.from_numpy(rh2.copy()).pin_memory()
+    u_p = torch.empty(u0.shape, dtype=torch.float64).pin_memory()
+    h_p = torch.empty(h0.shape, dtype=torch.float64).pin_memory()
+    _lib.check(s.h, s.lib.hdg_recover(s.h, ru_p.data_ptr(), rh_p.data_ptr(), None, u_p.data_ptr(), h_p.data_ptr()))
+    assert np.array_equal(u_p.numpy(), u2) and np.array_equal(h_p.numpy(), h2)
+    u1, h1 = s.recover()
+    assert np.array_equal(u1, u0) and np.array_equal(h1, h0)
+    with pytest.raises(HDGError) as ei:
+        s.recover(ru2, None)
+    assert ei.value.code == -1
+    s.close()
+
+
 @pytest.mark.parametrize("kind,p", [("flat", 2), ("sphere", 3), ("flat", 4), ("flat", 1)])
 def test_fp64_fgmres_with_fp32_preconditioner(kind, p):
     """HDG_MIXED_FGMRES64: FP64 FGMRES (basis, orthogonalisation, residual,
