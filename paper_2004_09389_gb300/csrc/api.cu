@@ -251,7 +251,7 @@ KSpace<float> &kspace<float>(hdg_handle *h) { return h->ws->k32; }
 
 size_t hdg::tail_smem_bytes(const std::vector<DevLevel> &lev, int first, size_t tsz) {
     auto pad = [](size_t b) { return (b + 15) / 16 * 16; };
-    size_t bytes = 0;
+    size_t bytes = pad(sizeof(TailHdr) * (lev.size() - first));
     for (size_t l = first; l < lev.size(); ++l) {
         const bool top = int(l) == first;
         const size_t nv = lev[l].nv, nnz = lev[l].nnz, nci = top ? 0 : lev[l].nci;
@@ -298,25 +298,25 @@ cudaError_t p1_cycle(hdg_handle *h, T **result) {
                                                       fuse ? levX<T>(C) : nullptr, s))) != cudaSuccess) return e;
     }
     {
+        const TailImage &im = h->tail_img[sizeof(T) == 8 ? 0 : 1];
+        if (im.ts != ts || !im.d) return cudaErrorInvalidValue;   // image not built for this tail start
         TailArgs a{};
         a.nlev = nlev - ts;
         a.nu1 = nu1;
         a.nu2 = nu2;
         a.omega = h->prm.p1_omega;
-        size_t smem = 0;
-        for (int l = ts; l < nlev; ++l) {
-            DevLevel &L = h->lev[l];
-            TailLevel &t = a.lev[l - ts];
-            t.nv = L.nv; t.nnz = L.nnz; t.nci = (l > ts) ? L.nci : 0; t.width = L.width;
-            t.col = L.col; t.A = levA<T>(L); t.dinv = levD<T>(L);
-            t.cp = L.child_ptr; t.ci = L.child_idx; t.parent = L.parent;
-            t.cw = sizeof(T) == 4 ? static_cast<const void *>(L.child_w32) : static_cast<const void *>(L.child_w);
-        }
-        smem = tail_smem_bytes(h->lev, ts, sizeof(T));
+        a.img = im.d;
+        a.img_bytes = im.img_bytes;
+        a.inv_off = im.inv_off;
+        a.nv0 = h->lev[ts].nv;
+        a.ob0 = im.ob0;
+        a.ox0 = im.ox0;
+        a.dinv0 = levD<T>(h->lev[ts]);
         a.inv = h->d_coarse_inv;          // the coarsest solve stays FP64 in every precision
         a.status = h->d_status;
         a.b_top = levB<T>(h->lev[ts]);
         a.x_top = levX<T>(h->lev[ts]);
+        const size_t smem = im.smem_bytes;
         if ((e = KL(HDG_PROF_P1, 1, launch_p1_tail<T>(a, smem, s))) != cudaSuccess) return e;
         res[ts] = levX<T>(h->lev[ts]);
     }
@@ -723,6 +723,7 @@ void free_handle(hdg_handle *h) {
     dfree(h->d_nbr); dfree(h->d_Xb); dfree(h->d_Rm); dfree(h->d_W); dfree(h->d_Scell); dfree(h->d_Sval);
     dfree(h->d_Xb2); dfree(h->d_Rm2); dfree(h->d_W2); dfree(h->d_Sval2);
     dfree(h->d_Dinv); dfree(h->d_Sval32); dfree(h->d_Dinv32); dfree(h->d_Sval16); dfree(h->d_status); dfree(h->d_coarse_inv);
+    dfree(h->tail_img[0].d); dfree(h->tail_img[1].d);
     dfree(h->d_coarse_work);
     for (auto &L : h->lev) {
         dfree(L.col); dfree(L.diag); dfree(L.elem); dfree(L.fK); dfree(L.contrib_ptr); dfree(L.contrib); dfree(L.A); dfree(L.dinv);
@@ -758,6 +759,88 @@ void free_handle(hdg_handle *h) {
     delete h;
 }
 
+void drop_graphs(hdg_handle *h);
+
+// The tail image of precision pi (0: FP64, 1: FP32) for the current tail
+// start: header table, every level's staged arrays and, when it fits, the
+// coarsest FP64 inverse, copied device to device into one buffer.  Needs the
+// assembled level operators (hdg_condense).
+int build_tail_image(hdg_handle *h, int pi) {
+    if (pi == 1 && !h->lev[0].A32) return HDG_OK;          // no FP32 levels on this handle
+    auto pad = [](size_t b) { return (b + 15) / 16 * 16; };
+    const size_t tsz = pi == 0 ? sizeof(double) : sizeof(float);
+    const int nlev = int(h->lev.size()), ts = h->tail_start[pi], n = nlev - ts;
+    std::vector<TailHdr> hdr(n);
+    struct Piece { size_t off; const void *src; size_t bytes; };
+    std::vector<Piece> pieces;
+    size_t off = pad(sizeof(TailHdr) * n);
+    auto put = [&](int32_t &o, const void *src, size_t bytes) {
+        o = int32_t(off);
+        if (bytes) pieces.push_back({off, src, pad(bytes)});
+        off += pad(bytes);
+    };
+    for (int k = 0; k < n; ++k) {
+        const DevLevel &L = h->lev[ts + k];
+        const bool top = k == 0;
+        TailHdr &H = hdr[k];
+        H = TailHdr{};
+        H.nv = L.nv; H.nnz = L.nnz; H.nci = top ? 0 : L.nci; H.W = L.width;
+        put(H.oA, pi == 0 ? static_cast<const void *>(L.A) : static_cast<const void *>(L.A32), tsz * L.nnz);
+        put(H.oD, pi == 0 ? static_cast<const void *>(L.dinv) : static_cast<const void *>(L.dinv32), tsz * L.nv);
+        put(H.ocol, L.col, 4 * size_t(L.nnz));
+        if (!top) {
+            put(H.ocw, pi == 0 ? static_cast<const void *>(L.child_w) : static_cast<const void *>(L.child_w32),
+                tsz * L.nci);
+            put(H.ocp, L.child_ptr, 4 * size_t(L.nv + 1));
+            put(H.oci, L.child_idx, 4 * size_t(L.nci));
+            put(H.opar, L.parent, 4 * size_t(2 * h->lev[ts + k - 1].nv));
+        }
+    }
+    const size_t data_end = off;
+    size_t scratch = 0;
+    for (int k = 0; k < n; ++k) scratch += 4 * pad(tsz * h->lev[ts + k].nv);
+    const size_t nc = h->lev.back().nv, inv_bytes = pad(sizeof(double) * nc * nc);
+    int32_t inv_off = -1;
+    if (inv_bytes <= kTailInvSmemMax && data_end + inv_bytes + scratch <= kTailSmemMax) {
+        inv_off = int32_t(off);
+        pieces.push_back({off, h->d_coarse_inv, inv_bytes});
+        off += inv_bytes;
+    }
+    const size_t img_bytes = off;
+    for (int k = 0; k < n; ++k) {
+        const size_t v = pad(tsz * h->lev[ts + k].nv);
+        hdr[k].ox = int32_t(off); off += v;
+        hdr[k].ox2 = int32_t(off); off += v;
+        hdr[k].ob = int32_t(off); off += v;
+        hdr[k].orr = int32_t(off); off += v;
+    }
+    if (off > kTailSmemMax)
+        return fail(h, HDG_EINVAL, "coarsest P1 levels too large for the single-CTA coarse cycle");
+    TailImage &im = h->tail_img[pi];
+    if (im.cap < img_bytes) {
+        dfree(im.d);
+        im.cap = 0;
+        TRY(dalloc(&im.d, img_bytes));
+        im.cap = img_bytes;
+        if (h->ws) drop_graphs(h);                         // captured launches hold the old address
+    }
+    cudaStream_t s = h->stream;
+    TRY(cudaMemcpyAsync(im.d, hdr.data(), sizeof(TailHdr) * n, cudaMemcpyHostToDevice, s));
+    for (const Piece &q : pieces)
+        TRY(cudaMemcpyAsync(im.d + q.off, q.src, q.bytes, cudaMemcpyDeviceToDevice, s));
+    TRY(cudaStreamSynchronize(s));                         // hdr is host memory on this stack
+    if (im.ts != ts || im.img_bytes != img_bytes) {
+        if (h->ws) drop_graphs(h);
+    }
+    im.ts = ts;
+    im.img_bytes = uint32_t(img_bytes);
+    im.smem_bytes = uint32_t(off);
+    im.inv_off = inv_off;
+    im.ob0 = hdr[0].ob;
+    im.ox0 = hdr[0].ox;
+    return HDG_OK;
+}
+
 // First level of the single-CTA coarse cycle, per precision: the largest
 // suffix of P1 levels whose levels have at most tail_max vertices and whose
 // operators, transfers and vectors fit in one CTA's shared memory.
@@ -772,6 +855,10 @@ int set_tail_start(hdg_handle *h, int tail_max) {
         if (tail_smem_bytes(h->lev, ts, tsz) > kTailSmemMax)
             return fail(h, HDG_EINVAL, "coarsest P1 level too large for the single-CTA coarse cycle");
         h->tail_start[pi] = ts;
+        if (h->condensed) {
+            int rc = build_tail_image(h, pi);
+            if (rc) return rc;
+        }
     }
     return HDG_OK;
 }
@@ -1125,6 +1212,10 @@ int hdg_condense(hdg_handle *h) {
             TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_W, h->d_W2, m * nK * N, s)));
             TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Sval, h->d_Sval2, (NS + 1) / 2 * 2 * size_t(h->NF), s)));
         }
+    }
+    for (int pi = 0; pi < 2; ++pi) {
+        int rc = build_tail_image(h, pi);
+        if (rc) return rc;
     }
     int rc = check_status(h);
     if (rc) return rc;

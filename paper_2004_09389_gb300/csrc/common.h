@@ -135,22 +135,42 @@ constexpr int kMaxGsBlocks = 1216;     // largest grid of the fused Gram-Schmidt
 constexpr int kTailMaxLevels = 8;
 constexpr int kTailMaxVertices = 1024;     // default largest level run inside the tail kernel
 constexpr size_t kTailSmemMax = 226 * 1024; // dynamic shared memory limit of the tail kernel
-struct TailLevel {
-    int nv, nnz, nci, width;            // nnz = width * nv
-    const int32_t *col;                 // padded ELL columns of the level operator
-    const void *A, *dinv;               // values in the solve precision
-    const int32_t *cp, *ci;             // restriction into this level (children in the finer level)
-    const void *cw;                     // child weights in the solve precision
-    const int32_t *parent;              // prolongation from this level to the finer one
+constexpr size_t kTailInvSmemMax = 64 * 1024; // largest coarsest-level inverse staged in shared memory
+// One level of the single-CTA tail as laid out in shared memory: sizes and
+// byte offsets from the start of the dynamic shared memory.  The table sits
+// at offset 0 of the tail image; arrays that the bulk copy does not fill
+// (x, x2, b, r) lie after the image.
+struct TailHdr {
+    int32_t nv, nnz, nci, W;            // nnz = W * nv; nci = 0 on the first tail level
+    int32_t oA, oD, ocw, ocol, ocp, oci, opar;   // staged: values, inverse diagonal, transfers
+    int32_t ox, ox2, ob, orr, pad;      // scratch vectors
 };
-// shared-memory bytes of the tail kernel for levels [first, levels.size()) in precision of size tsz
+static_assert(sizeof(TailHdr) == 64, "tail header entries are 64 bytes");
+// The tail's shared-memory image in global memory for one precision:
+// [TailHdr per level][level arrays, each 16-byte padded][coarsest inverse
+// when it fits], filled at condensation, staged by bulk copies per launch.
+struct TailImage {
+    unsigned char *d = nullptr;
+    size_t cap = 0;
+    int ts = -1;                        // first level the image was built for
+    uint32_t img_bytes = 0;             // bytes staged by the bulk copies
+    uint32_t smem_bytes = 0;            // image plus scratch vectors
+    int32_t inv_off = -1;               // offset of the staged inverse, -1: read from global memory
+    int32_t ob0 = 0, ox0 = 0;           // scratch b and x of the first tail level
+};
+// shared-memory bytes of the tail kernel for levels [first, levels.size()) in
+// precision of size tsz (header table, level arrays, scratch; no inverse)
 size_t tail_smem_bytes(const std::vector<DevLevel> &lev, int first, size_t tsz);
 struct TailArgs {
     int nlev, nu1, nu2;
     double omega;
-    TailLevel lev[kTailMaxLevels];
+    const unsigned char *img;           // tail image (global), 16-byte aligned
+    uint32_t img_bytes;                 // bytes to stage, a multiple of 16
+    int32_t inv_off;                    // staged inverse offset, -1: use inv
+    int32_t nv0, ob0, ox0;              // first tail level: size, scratch offsets of b and x
+    const void *dinv0;                  // its inverse diagonal (global, the solve precision)
     int32_t *status;                    // device error flags (8: shared-memory staging timed out)
-    const double *inv;                  // dense FP64 inverse of the last level
+    const double *inv;                  // dense FP64 inverse of the last level (n x n, row-major)
     const void *b_top;                  // right-hand side of the first tail level (global)
     void *x_top;                        // its solution (global)
 };
@@ -208,6 +228,7 @@ struct hdg_handle {
     int tail_start[2] = {0, 0};       // first P1 level of the single-CTA tail kernel (FP64, FP32)
     int bs_facet = 256;               // threads per block of the facet-row kernels (autotuned)
     double *d_coarse_inv = nullptr;   // dense inverse of the coarsest P1 operator
+    hdg::TailImage tail_img[2];       // shared-memory images of the tail levels (FP64, FP32)
     double *d_coarse_work = nullptr;
     hdg::Workspace *ws = nullptr;
     hdg::Prof prof;

@@ -157,14 +157,15 @@ __global__ void up_kernel(int nf, int W, const int32_t *__restrict__ col, const 
     xout[i] = fma(omega * dinv[i], b[i] - ax, xi);
 }
 
-// The V-cycle over the small levels in one CTA.  Every level's operator
-// (CSR, values, inverse diagonal) and transfer lists are first copied into
-// shared memory by TMA bulk copies (cp.async.bulk, one mbarrier with a
-// transaction count), then the steps run with __syncthreads between them.
-// Level 0 of the tail takes b from global memory and returns x there; the last
-// level is solved with its dense inverse (read from global memory).
-// Every staged array starts 16-byte aligned in global memory (separate
-// allocations padded to 16 bytes) and in shared memory (offsets rounded up).
+// The V-cycle over the small levels in one CTA.  The levels' operators
+// (ELL values and columns, inverse diagonals), transfer lists and, when it
+// fits, the coarsest level's FP64 inverse were packed at condensation into one
+// image laid out exactly as this kernel's shared memory, headed by a table of
+// sizes and offsets; a few bulk copies (cp.async.bulk, one mbarrier with a
+// transaction count) stage it, then the steps run with __syncthreads between
+// them.  Level 0 of the tail takes b from global memory and returns x there;
+// the last level is solved with its dense inverse.  The image and every
+// chunk of it start 16-byte aligned.
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -189,8 +190,8 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, long long limit) {
 __host__ __device__ constexpr size_t pad16(size_t bytes) { return (bytes + 15) / 16 * 16; }
 
 // Shared-memory addresses and sizes of one tail level.  The table lives in
-// shared memory (filled by thread 0) so that run-time level indices never
-// put per-thread pointer arrays on the stack.
+// shared memory (filled from the staged header, one thread per level) so that
+// run-time level indices never put per-thread pointer arrays on the stack.
 template <typename T>
 struct TailSlot {
     T *A, *D, *cw, *x, *x2, *b, *r;
@@ -198,89 +199,82 @@ struct TailSlot {
     int nv, nnz, nci, W;
 };
 
+// x_j + (P e_c)_j: the midpoint prolongation of the coarse correction added on the fly
+template <typename T>
+__device__ __forceinline__ T prolonged(const int32_t *par, const T *x, const T *ec, int j) {
+    const int p0 = par[2 * j], p1 = par[2 * j + 1];
+    return x[j] + ((p0 == p1) ? ec[p0] : T(0.5) * (ec[p0] + ec[p1]));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024, 1) tail_kernel(TailArgs a) {
     extern __shared__ __align__(16) unsigned char tail_smem[];
     __shared__ __align__(8) uint64_t bar;
-    // per level: A[nnz], dinv[nv], cw[nci], x, x2, b, r [nv] (T); col[nnz],
-    // cp[nv+1], ci[nci], par[2 nv_finer] (int32), each 16-byte aligned
     __shared__ TailSlot<T> L[kTailMaxLevels];
-    if (threadIdx.x == 0) {
-        unsigned char *q = tail_smem;
-        for (int l = 0; l < a.nlev; ++l) {
-            const TailLevel &G = a.lev[l];
-            const int nfin = l > 0 ? a.lev[l - 1].nv : 0;
-            TailSlot<T> &S = L[l];
-            S.nv = G.nv; S.nnz = G.nnz; S.nci = G.nci; S.W = G.width;
-            S.A = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nnz);
-            S.D = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
-            S.cw = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nci);
-            S.x = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
-            S.x2 = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
-            S.b = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
-            S.r = reinterpret_cast<T *>(q); q += pad16(sizeof(T) * G.nv);
-            S.col = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(G.nnz));
-            S.cp = reinterpret_cast<int32_t *>(q); q += l > 0 ? pad16(4 * size_t(G.nv + 1)) : 0;
-            S.ci = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(G.nci));
-            S.par = reinterpret_cast<int32_t *>(q); q += pad16(4 * size_t(2 * nfin));
-        }
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t tx = 0;
-        for (int l = 0; l < a.nlev; ++l) {
-            const TailLevel &G = a.lev[l];
-            tx += pad16(sizeof(T) * G.nnz) + pad16(sizeof(T) * G.nv) + pad16(4 * size_t(G.nnz));
-            if (l > 0) tx += pad16(sizeof(T) * G.nci) + pad16(4 * size_t(G.nv + 1)) + pad16(4 * size_t(G.nci)) +
-                             pad16(4 * size_t(2 * a.lev[l - 1].nv));
-        }
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(&bar)), "r"(tx) : "memory");
-        for (int l = 0; l < a.nlev; ++l) {
-            const TailLevel &G = a.lev[l];
-            const TailSlot<T> &S = L[l];
-            bulk_g2s(S.A, G.A, pad16(sizeof(T) * G.nnz), &bar);
-            bulk_g2s(S.D, G.dinv, pad16(sizeof(T) * G.nv), &bar);
-            bulk_g2s(S.col, G.col, pad16(4 * size_t(G.nnz)), &bar);
-            if (l > 0) {
-                bulk_g2s(S.cw, G.cw, pad16(sizeof(T) * G.nci), &bar);
-                bulk_g2s(S.cp, G.cp, pad16(4 * size_t(G.nv + 1)), &bar);
-                bulk_g2s(S.ci, G.ci, pad16(4 * size_t(G.nci)), &bar);
-                bulk_g2s(S.par, G.parent, pad16(4 * size_t(2 * a.lev[l - 1].nv)), &bar);
-            }
-        }
+    // the image (level table, operators, transfers, inverse) in chunks of at
+    // most 64 KB, one per lane of warp 0, after lane 0 has set the byte count
+    if (tid < 32) {
+        if (tid == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         :: "r"(smem_u32(&bar)), "r"(a.img_bytes) : "memory");
+        __syncwarp();
+        constexpr uint32_t kChunk = 64 * 1024;
+        const uint32_t o = uint32_t(tid) * kChunk;
+        if (o < a.img_bytes) bulk_g2s(tail_smem + o, a.img + o, min(kChunk, a.img_bytes - o), &bar);
     }
-    // right-hand side of the top level with plain loads meanwhile
+    const T om = T(a.omega);
+    // meanwhile, with plain loads into the scratch space after the image: the
+    // first level's right-hand side and its first pre-smoothing sweep from
+    // zero, x = omega D^-1 b (the inverse diagonal read from global memory)
     {
         const T *btop = static_cast<const T *>(a.b_top);
-        T *b0 = L[0].b;
-        const int nv0 = L[0].nv;
-        for (int i = threadIdx.x; i < nv0; i += blockDim.x) b0[i] = btop[i];
+        const T *d0 = static_cast<const T *>(a.dinv0);
+        T *b0 = reinterpret_cast<T *>(tail_smem + a.ob0), *x0 = reinterpret_cast<T *>(tail_smem + a.ox0);
+        for (int i = tid; i < a.nv0; i += nt) {
+            const T bi = btop[i];
+            b0[i] = bi;
+            x0[i] = a.nu1 == 0 ? T(0) : om * d0[i] * bi;
+        }
     }
     if (!bar_wait(&bar, 1ll << 22)) {
         // the copies did not complete: record it, give them one more bounded
         // wait so none is left writing into this CTA's shared memory, return
-        if (threadIdx.x == 0) atomicOr(a.status, 8);
+        if (tid == 0) atomicOr(a.status, 8);
         bar_wait(&bar, 1ll << 22);
         return;
     }
+    if (tid < a.nlev) {
+        const TailHdr H = reinterpret_cast<const TailHdr *>(tail_smem)[tid];
+        TailSlot<T> &S = L[tid];
+        S.nv = H.nv; S.nnz = H.nnz; S.nci = H.nci; S.W = H.W;
+        S.A = reinterpret_cast<T *>(tail_smem + H.oA);
+        S.D = reinterpret_cast<T *>(tail_smem + H.oD);
+        S.cw = reinterpret_cast<T *>(tail_smem + H.ocw);
+        S.col = reinterpret_cast<int32_t *>(tail_smem + H.ocol);
+        S.cp = reinterpret_cast<int32_t *>(tail_smem + H.ocp);
+        S.ci = reinterpret_cast<int32_t *>(tail_smem + H.oci);
+        S.par = reinterpret_cast<int32_t *>(tail_smem + H.opar);
+        S.x = reinterpret_cast<T *>(tail_smem + H.ox);
+        S.x2 = reinterpret_cast<T *>(tail_smem + H.ox2);
+        S.b = reinterpret_cast<T *>(tail_smem + H.ob);
+        S.r = reinterpret_cast<T *>(tail_smem + H.orr);
+    }
     __syncthreads();
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const T om = T(a.omega);
+    const int nc = L[a.nlev - 1].nv;
+    const double *sinv = a.inv_off >= 0 ? reinterpret_cast<const double *>(tail_smem + a.inv_off) : nullptr;
     const int last = a.nlev - 1;
-    // ---- down
+    // ---- down: x holds the first sweep (or zero) on entry to each level
     for (int l = 0; l < last; ++l) {
         const int nv = L[l].nv, W = L[l].W;
         const int32_t *cl = L[l].col;
         const T *A = L[l].A, *D = L[l].D, *b = L[l].b;
         T *x = L[l].x, *x2 = L[l].x2, *r = L[l].r;
-        if (a.nu1 == 0) {
-            for (int i = tid; i < nv; i += nt) x[i] = T(0);
-        } else {
-            for (int i = tid; i < nv; i += nt) x[i] = om * D[i] * b[i];
-        }
-        __syncthreads();
         for (int k = 1; k < a.nu1; ++k) {
             for (int i = tid; i < nv; i += nt) x2[i] = fma(om * D[i], b[i] - ell_row(i, W, cl, A, x), x[i]);
             __syncthreads();
@@ -289,41 +283,48 @@ __global__ void __launch_bounds__(1024, 1) tail_kernel(TailArgs a) {
         for (int i = tid; i < nv; i += nt) r[i] = b[i] - ell_row(i, W, cl, A, x);
         if (tid == 0) { L[l].x = x; L[l].x2 = x2; }   // read again only after later barriers
         __syncthreads();
+        // restriction, with the coarse level's first sweep from zero
         const int ncv = L[l + 1].nv;
         const int32_t *cp = L[l + 1].cp, *ci = L[l + 1].ci;
-        const T *cw = L[l + 1].cw;
-        T *bc = L[l + 1].b;
+        const T *cw = L[l + 1].cw, *Dc = L[l + 1].D;
+        T *bc = L[l + 1].b, *xc = L[l + 1].x;
+        const bool smooth_c = l + 1 < last;
         for (int i = tid; i < ncv; i += nt) {
             T acc = T(0);
             for (int k = cp[i]; k < cp[i + 1]; ++k) acc = fma(cw[k], r[ci[k]], acc);
             bc[i] = acc;
+            if (smooth_c) xc[i] = a.nu1 == 0 ? T(0) : om * Dc[i] * acc;
         }
         __syncthreads();
     }
-    // ---- coarsest: dense FP64 inverse, FP64 sums in every precision
+    // ---- coarsest: dense FP64 inverse, FP64 sums in every precision; four
+    // lanes per row (FP64 arithmetic is a narrow pipe: few adds in the tree),
+    // each summing every fourth column, combined by a fixed two-step shuffle
     {
-        const double *inv = static_cast<const double *>(a.inv);
-        const int n = L[last].nv;
+        const double *inv = sinv ? sinv : a.inv;
         const T *b = L[last].b;
         T *x = L[last].x;
-        for (int i = tid; i < n; i += nt) {
+        const int sub = tid & 3, ng = nt >> 2;
+        // whole warps take part in every shuffle: the row loop runs to a multiple of 8
+        for (int i = tid >> 2; i < ((nc + 7) & ~7); i += ng) {
             double acc = 0.0;
-            for (int j = 0; j < n; ++j) acc = fma(inv[size_t(i) * n + j], double(b[j]), acc);
-            x[i] = T(acc);
+            if (i < nc)
+                for (int j = sub; j < nc; j += 4) acc = fma(inv[size_t(i) * nc + j], double(b[j]), acc);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            if (i < nc && sub == 0) x[i] = T(acc);
         }
         __syncthreads();
     }
-    // ---- up
+    // ---- up: x += P e_c in place (a separate step: forming it on the fly in
+    // the sweep multiplies the shared-memory gathers), then post-smoothing
     const T *ec = L[last].x;
     for (int l = last - 1; l >= 0; --l) {
         const int nv = L[l].nv, W = L[l].W;
         const int32_t *cl = L[l].col, *par = L[l + 1].par;
         const T *A = L[l].A, *D = L[l].D, *b = L[l].b;
         T *x = L[l].x, *x2 = L[l].x2;
-        for (int i = tid; i < nv; i += nt) {
-            const int p0 = par[2 * i], p1 = par[2 * i + 1];
-            x[i] += (p0 == p1) ? ec[p0] : T(0.5) * (ec[p0] + ec[p1]);
-        }
+        for (int i = tid; i < nv; i += nt) x[i] = prolonged(par, x, ec, i);
         __syncthreads();
         for (int k = 0; k < a.nu2; ++k) {
             for (int i = tid; i < nv; i += nt) x2[i] = fma(om * D[i], b[i] - ell_row(i, W, cl, A, x), x[i]);
