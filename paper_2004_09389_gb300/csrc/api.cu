@@ -286,16 +286,25 @@ cudaError_t p1_cycle(hdg_handle *h, T **result) {
     for (int l = 0; l < ts; ++l) {
         DevLevel &L = h->lev[l];
         T *x = levX<T>(L), *x2 = levX2<T>(L);
+        DevLevel &C = h->lev[l + 1];
+        const bool fuse = (l + 1 < ts) && nu1 >= 1;
+        // with two or more sweeps, the last one shares the patch kernel of the restriction
+        const bool patch = h->p1_fused && p1_patch_ok<T>(L) && nu1 >= 2;
         if (nu1 == 0 && (e = KL(HDG_PROF_P1, 1, launch_fill<T>(x, T(0), L.nv, s))) != cudaSuccess) return e;
-        for (int k = 1; k < nu1; ++k) {
+        for (int k = patch ? 2 : 1; k < nu1; ++k) {
             if ((e = KL(HDG_PROF_P1, 1, launch_p1_jacobi<T>(L, levA<T>(L), levD<T>(L), levB<T>(L), x, x2, om, false, s))) != cudaSuccess) return e;
             std::swap(x, x2);
         }
+        if (patch) {
+            if ((e = KL(HDG_PROF_P1, 1, launch_p1_down_fused<T>(L, C, levA<T>(L), levD<T>(L), levB<T>(L), x, x2,
+                                                                levD<T>(C), om, levB<T>(C),
+                                                                fuse ? levX<T>(C) : nullptr, s))) != cudaSuccess) return e;
+            std::swap(x, x2);
+        } else {
+            if ((e = KL(HDG_PROF_P1, 1, launch_p1_down<T>(L, C, levA<T>(L), levB<T>(L), x, levD<T>(C), om, levB<T>(C),
+                                                          fuse ? levX<T>(C) : nullptr, s))) != cudaSuccess) return e;
+        }
         cur[l] = x; oth[l] = x2;
-        DevLevel &C = h->lev[l + 1];
-        const bool fuse = (l + 1 < ts) && nu1 >= 1;
-        if ((e = KL(HDG_PROF_P1, 1, launch_p1_down<T>(L, C, levA<T>(L), levB<T>(L), x, levD<T>(C), om, levB<T>(C),
-                                                      fuse ? levX<T>(C) : nullptr, s))) != cudaSuccess) return e;
     }
     {
         const TailImage &im = h->tail_img[sizeof(T) == 8 ? 0 : 1];
@@ -326,6 +335,14 @@ cudaError_t p1_cycle(hdg_handle *h, T **result) {
         T *x = cur[l], *x2 = oth[l];
         if (nu2 == 0) {
             if ((e = KL(HDG_PROF_P1, 1, launch_p1_prolong_add<T>(C, L.nv, res[l + 1], x, s))) != cudaSuccess) return e;
+        } else if (h->p1_fused && p1_patch_ok<T>(L) && nu2 >= 2) {
+            // the prolongation and the first two post-smoothing sweeps in one patch kernel
+            if ((e = KL(HDG_PROF_P1, 1, launch_p1_up_fused<T>(L, C, levA<T>(L), levD<T>(L), levB<T>(L), x, res[l + 1], x2, om, s))) != cudaSuccess) return e;
+            std::swap(x, x2);
+            for (int k = 2; k < nu2; ++k) {
+                if ((e = KL(HDG_PROF_P1, 1, launch_p1_jacobi<T>(L, levA<T>(L), levD<T>(L), levB<T>(L), x, x2, om, false, s))) != cudaSuccess) return e;
+                std::swap(x, x2);
+            }
         } else {
             if ((e = KL(HDG_PROF_P1, 1, launch_p1_up<T>(L, C, levA<T>(L), levD<T>(L), levB<T>(L), x, res[l + 1], x2, om, s))) != cudaSuccess) return e;
             std::swap(x, x2);
@@ -728,6 +745,10 @@ void free_handle(hdg_handle *h) {
     for (auto &L : h->lev) {
         dfree(L.col); dfree(L.diag); dfree(L.elem); dfree(L.fK); dfree(L.contrib_ptr); dfree(L.contrib); dfree(L.A); dfree(L.dinv);
         dfree(L.A32); dfree(L.dinv32); dfree(L.parent); dfree(L.child_ptr); dfree(L.child_idx); dfree(L.child_w); dfree(L.child_w32);
+        dfree(L.pf_ptr); dfree(L.pf_n0); dfree(L.pf_ids); dfree(L.pf0_base); dfree(L.plcol);
+        dfree(L.pc_ptr); dfree(L.pc_ids); dfree(L.pcc_ptr); dfree(L.pcc_slot); dfree(L.pcc_w); dfree(L.pcc_w32);
+        dfree(L.pg_ptr); dfree(L.pg_nown); dfree(L.pg_ids); dfree(L.pg0_base); dfree(L.pglcol);
+        dfree(L.pfcol); dfree(L.pgcol); dfree(L.pgpar); dfree(L.pgrow_par);
         dfree(L.x); dfree(L.x2); dfree(L.b); dfree(L.r); dfree(L.x32); dfree(L.x232); dfree(L.b32); dfree(L.r32);
     }
     if (h->ws) {
@@ -959,6 +980,21 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
             TRY(upload(&L.child_w32, w32, s));
             L.nci = int(hl.child_idx.size());
         }
+        if (hl.patch.nb > 0) {
+            const HostPatches &P = hl.patch;
+            L.nb = P.nb; L.max_f1 = P.max_f1; L.max_f0 = P.max_f0; L.max_g1 = P.max_g1;
+            TRY(upload(&L.pf_ptr, P.f_ptr, s)); TRY(upload(&L.pf_n0, P.f_n0, s)); TRY(upload(&L.pf_ids, P.f_ids, s));
+            TRY(upload(&L.pf0_base, P.f0_base, s)); TRY(upload(&L.plcol, P.lcol, s));
+            TRY(upload(&L.pc_ptr, P.c_ptr, s)); TRY(upload(&L.pc_ids, P.c_ids, s));
+            TRY(upload(&L.pcc_ptr, P.cc_ptr, s)); TRY(upload(&L.pcc_slot, P.cc_slot, s));
+            TRY(upload(&L.pcc_w, P.cc_w, s));
+            std::vector<float> cw32(P.cc_w.begin(), P.cc_w.end());
+            TRY(upload(&L.pcc_w32, cw32, s));
+            TRY(upload(&L.pg_ptr, P.g_ptr, s)); TRY(upload(&L.pg_nown, P.g_nown, s)); TRY(upload(&L.pg_ids, P.g_ids, s));
+            TRY(upload(&L.pg0_base, P.g0_base, s)); TRY(upload(&L.pglcol, P.glcol, s));
+            TRY(upload(&L.pfcol, P.fcol, s)); TRY(upload(&L.pgcol, P.gcol, s));
+            TRY(upload(&L.pgpar, P.gpar, s)); TRY(upload(&L.pgrow_par, P.grow_par, s));
+        }
         TRY(dalloc(&L.x, size_t(L.nv)));
         TRY(dalloc(&L.x2, size_t(L.nv)));
         TRY(dalloc(&L.b, size_t(L.nv)));
@@ -975,6 +1011,8 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     {
         int tail_max = kTailMaxVertices;
         if (const char *ev = std::getenv("HDG_TAIL_MAX_VERTICES")) tail_max = std::max(16, std::min(4096, std::atoi(ev)));
+        // HDG_P1_FUSED=0 selects the unfused P1 kernels (same arithmetic; for timing comparisons)
+        if (const char *ev = std::getenv("HDG_P1_FUSED")) h->p1_fused = std::atoi(ev) != 0;
         int rc = set_tail_start(h, tail_max);
         if (rc) return rc;
     }

@@ -45,8 +45,31 @@ inline RefOffsets ref_offsets(int p) {
 }
 
 // ---------------------------------------------------------------- host mesh data
+// Patches of the fused P1 smoothing kernels between a level (fine) and the
+// next coarser one.  The coarse vertices are split into nb spatially compact
+// patches (recursive coordinate bisection).  Going down, patch b takes its
+// coarse vertices' children F0 (slots [0, n0)) and their ELL neighbours (the
+// rest of F1); going up, it owns the fine vertices whose first parent is in
+// it (slots [0, nown)) plus their neighbours.  Every ELL column of a row in
+// the first part maps to a slot of the same patch.
+struct HostPatches {
+    int nb = 0, max_f1 = 0, max_f0 = 0, max_g1 = 0;
+    std::vector<int32_t> f_ptr, f_n0, f_ids, f0_base, lcol;        // down: F1 ids per patch, F0 rows' local columns
+    std::vector<int32_t> c_ptr, c_ids, cc_ptr, cc_slot;            // down: coarse vertices, their children's slots
+    std::vector<double> cc_w;                                      //       and weights (order of child_idx)
+    std::vector<int32_t> g_ptr, g_nown, g_ids, g0_base, glcol;     // up: owned + neighbour ids, owned rows' local columns
+    // copies of static structure indexed by patch row (no index indirection in the kernels)
+    std::vector<int32_t> fcol;        // [f_ids.size()][W] global columns of the F1 rows
+    std::vector<int32_t> gcol;        // [g_ids.size()][W] global columns of the up rows
+    std::vector<int32_t> gpar;        // [g_ids.size()][W][2] parents (coarse) of each column
+    std::vector<int32_t> grow_par;    // [g_ids.size()][2] parents of the row vertex
+};
+
 struct HostLevel {
     int nv = 0, nc = 0;
+    int vdim = 0;
+    std::vector<double> vxyz;     // [nv][vdim] vertex coordinates (coarse levels)
+    HostPatches patch;            // fused-kernel patches towards the next coarser level
     std::vector<double> X;        // [nc][3][2] local 2-D vertex coordinates
     std::vector<int32_t> cells;   // [nc][3]
     // padded row-major ELL structure of the level operator: width W (a multiple
@@ -80,6 +103,9 @@ struct HostMesh {
 
 // Returns empty string on success, else the reason.
 std::string build_host_mesh(const hdg_mesh_desc *desc, HostMesh &hm);
+// Patches of level l towards level l + 1 (needs both levels' ELL structure,
+// the transfers and level l + 1's coordinates); about target_blocks patches.
+void build_p1_patches(HostMesh &hm, int l, int target_blocks);
 
 // ---------------------------------------------------------------- device data
 struct DevLevel {
@@ -96,6 +122,15 @@ struct DevLevel {
     // work vectors
     double *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;
     float *x32 = nullptr, *x232 = nullptr, *b32 = nullptr, *r32 = nullptr;
+    // patches of the fused smoothing kernels towards the next coarser level
+    // (HostPatches; nb = 0 on the coarsest level)
+    int nb = 0, max_f1 = 0, max_f0 = 0, max_g1 = 0;
+    int32_t *pf_ptr = nullptr, *pf_n0 = nullptr, *pf_ids = nullptr, *pf0_base = nullptr, *plcol = nullptr;
+    int32_t *pc_ptr = nullptr, *pc_ids = nullptr, *pcc_ptr = nullptr, *pcc_slot = nullptr;
+    double *pcc_w = nullptr;
+    float *pcc_w32 = nullptr;
+    int32_t *pg_ptr = nullptr, *pg_nown = nullptr, *pg_ids = nullptr, *pg0_base = nullptr, *pglcol = nullptr;
+    int32_t *pfcol = nullptr, *pgcol = nullptr, *pgpar = nullptr, *pgrow_par = nullptr;
 };
 
 struct Workspace;   // solver vectors, defined in api.cu
@@ -136,6 +171,7 @@ constexpr int kTailMaxLevels = 8;
 constexpr int kTailMaxVertices = 1024;     // default largest level run inside the tail kernel
 constexpr size_t kTailSmemMax = 226 * 1024; // dynamic shared memory limit of the tail kernel
 constexpr size_t kTailInvSmemMax = 64 * 1024; // largest coarsest-level inverse staged in shared memory
+constexpr int kPatchMaxVertices = 32768;      // largest P1 level smoothed by the fused patch kernels
 // One level of the single-CTA tail as laid out in shared memory: sizes and
 // byte offsets from the start of the dynamic shared memory.  The table sits
 // at offset 0 of the tail image; arrays that the bulk copy does not fill
@@ -226,6 +262,7 @@ struct hdg_handle {
 
     std::vector<hdg::DevLevel> lev;
     int tail_start[2] = {0, 0};       // first P1 level of the single-CTA tail kernel (FP64, FP32)
+    bool p1_fused = true;             // patch-fused P1 smoothing kernels on the levels above the tail
     int bs_facet = 256;               // threads per block of the facet-row kernels (autotuned)
     double *d_coarse_inv = nullptr;   // dense inverse of the coarsest P1 operator
     hdg::TailImage tail_img[2];       // shared-memory images of the tail levels (FP64, FP32)
@@ -314,6 +351,17 @@ cudaError_t launch_p1_down(const DevLevel &fine, const DevLevel &coarse, const T
 template <typename T>
 cudaError_t launch_p1_up(const DevLevel &fine, const DevLevel &coarse, const T *A_f, const T *dinv_f, const T *b_f,
                          const T *x_f, const T *ec, T *xout, T omega, cudaStream_t s);
+// one launch per patch: the last pre-smoothing sweep, the residual and the
+// restriction (down); the prolongation with both post-smoothing sweeps (up)
+template <typename T>
+bool p1_patch_ok(const DevLevel &L);   // the level's patches suit these kernels in precision T
+template <typename T>
+cudaError_t launch_p1_down_fused(const DevLevel &fine, const DevLevel &coarse, const T *A_f, const T *dinv_f,
+                                 const T *b_f, const T *x_f, T *xout_f, const T *dinv_c, T omega, T *b_c, T *x_c,
+                                 cudaStream_t s);
+template <typename T>
+cudaError_t launch_p1_up_fused(const DevLevel &fine, const DevLevel &coarse, const T *A_f, const T *dinv_f,
+                               const T *b_f, const T *x_f, const T *ec, T *xout, T omega, cudaStream_t s);
 template <typename T>
 cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s);
 

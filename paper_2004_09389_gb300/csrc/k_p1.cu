@@ -157,6 +157,183 @@ __global__ void up_kernel(int nf, int W, const int32_t *__restrict__ col, const 
     xout[i] = fma(omega * dinv[i], b[i] - ax, xi);
 }
 
+// x_j + (P e_c)_j: the midpoint prolongation of the coarse correction added on the fly
+template <typename T>
+__device__ __forceinline__ T prolonged(const int32_t *par, const T *x, const T *ec, int j) {
+    const int p0 = par[2 * j], p1 = par[2 * j + 1];
+    return x[j] + ((p0 == p1) ? ec[p0] : T(0.5) * (ec[p0] + ec[p1]));
+}
+
+// Fused steps over patches (HostPatches): one block per patch, one thread per
+// patch row, the one-ring halo recomputed by every patch that needs it, so
+// that a smoothing sweep and the step that consumes it share one launch.
+// Every index a thread needs (its row's columns, local columns, the parents
+// of its columns, its coarse vertex's children) is read from per-patch copies
+// before the first barrier, and its row's operator values stay in registers:
+// after the first phase only shared-memory gathers remain.  Every value is
+// formed with the arithmetic of the unfused kernels (rows in ELL slot order).
+__device__ __forceinline__ int4 load_cols(const int32_t *p) { return *reinterpret_cast<const int4 *>(p); }
+__device__ __forceinline__ int cget(const int4 &c, int u) { return u == 0 ? c.x : u == 1 ? c.y : u == 2 ? c.z : c.w; }
+
+// threads per patch block: FP32 rows fit 64 registers (1024 threads), FP64 rows 84 (768)
+template <typename T>
+constexpr int kPatchThreads = sizeof(T) == 4 ? 1024 : 768;
+constexpr int kChildPrefetch = 8;     // children of a coarse vertex held in registers
+
+// Going down one level, fused with the last pre-smoothing sweep.  Row s of
+// patch F1: x' = x + omega D^-1 (b - A x) (x from global memory) into shared
+// memory, and to xout for F0 rows (the pre-smoothed iterate; F0 sets of
+// neighbouring patches overlap and write identical values); r = b - A x' on
+// F0; b_c = R r for the patch's coarse vertices and, when xc is given, the
+// coarse level's first sweep from zero, x_c = omega D_c^-1 b_c.
+template <typename T, int WQ>
+__global__ void __launch_bounds__(kPatchThreads<T>, 1) down_fused_kernel(
+    const int32_t *__restrict__ f_ptr, const int32_t *__restrict__ f_n0, const int32_t *__restrict__ f_ids,
+    const int32_t *__restrict__ f0_base, const int32_t *__restrict__ lcol, const int32_t *__restrict__ fcol,
+    const int32_t *__restrict__ c_ptr, const int32_t *__restrict__ c_ids, const int32_t *__restrict__ cc_ptr,
+    const int32_t *__restrict__ cc_slot, const T *__restrict__ cc_w, const T *__restrict__ A,
+    const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ xout,
+    const T *__restrict__ dinv_c, T omega, T *__restrict__ bc, T *__restrict__ xc, int max_f1) {
+    constexpr int W = 4 * WQ;
+    extern __shared__ __align__(16) unsigned char patch_smem[];
+    T *xs = reinterpret_cast<T *>(patch_smem);
+    T *rs = xs + max_f1;
+    const int blk = blockIdx.x, s = threadIdx.x;
+    const int s0 = f_ptr[blk], n1 = f_ptr[blk + 1] - s0, n0 = f_n0[blk];
+    const int c = c_ptr[blk] + s;
+    const bool row = s < n1, row0 = s < n0, crow = c < c_ptr[blk + 1];
+    int v = 0;
+    int4 cols[WQ], lcs[WQ];
+    if (row) {
+        v = f_ids[s0 + s];
+#pragma unroll
+        for (int g = 0; g < WQ; ++g) cols[g] = load_cols(fcol + size_t(s0 + s) * W + 4 * g);
+    }
+    if (row0) {
+        const int r0 = f0_base[blk];
+#pragma unroll
+        for (int g = 0; g < WQ; ++g) lcs[g] = load_cols(lcol + size_t(r0 + s) * W + 4 * g);
+    }
+    int cid = 0, k0 = 0, k1 = 0;
+    int cs[kChildPrefetch];
+    T cwv[kChildPrefetch];
+    if (crow) {
+        cid = c_ids[c];
+        k0 = cc_ptr[c];
+        k1 = cc_ptr[c + 1];
+#pragma unroll
+        for (int j = 0; j < kChildPrefetch; ++j) {
+            cs[j] = k0 + j < k1 ? cc_slot[k0 + j] : 0;
+            cwv[j] = k0 + j < k1 ? cc_w[k0 + j] : T(0);
+        }
+    }
+    T av[W];
+    T bv = T(0);
+    if (row) {
+#pragma unroll
+        for (int g = 0; g < WQ; ++g) load4(A + size_t(v) * W + 4 * g, av + 4 * g);
+        bv = b[v];
+        T ax = T(0);
+#pragma unroll
+        for (int g = 0; g < WQ; ++g)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ax = fma(av[4 * g + u], x[cget(cols[g], u)], ax);
+        const T xn = fma(omega * dinv[v], bv - ax, x[v]);
+        xs[s] = xn;
+        if (row0) xout[v] = xn;
+    }
+    __syncthreads();
+    if (row0) {
+        T ax = T(0);
+#pragma unroll
+        for (int g = 0; g < WQ; ++g)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ax = fma(av[4 * g + u], xs[cget(lcs[g], u)], ax);
+        rs[s] = bv - ax;
+    }
+    __syncthreads();
+    if (crow) {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < kChildPrefetch; ++j)
+            if (k0 + j < k1) acc = fma(cwv[j], rs[cs[j]], acc);
+        for (int k = k0 + kChildPrefetch; k < k1; ++k) acc = fma(cc_w[k], rs[cc_slot[k]], acc);
+        bc[cid] = acc;
+        if (xc) xc[cid] = omega * dinv_c[cid] * acc;
+    }
+}
+
+// (P e_c) at a vertex with parents (pa, pb): the midpoint prolongation
+template <typename T>
+__device__ __forceinline__ T prolong_at(const T *__restrict__ ec, int pa, int pb) {
+    return (pa == pb) ? ec[pa] : T(0.5) * (ec[pa] + ec[pb]);
+}
+
+// Going up one level, fused with the second post-smoothing sweep.  Row s of
+// the patch (owned vertices, then their neighbours): x' = (x + P e_c) +
+// omega D^-1 (b - A (x + P e_c)) into shared memory (the prolongation formed
+// on the fly, as up_kernel does); then x'' = x' + omega D^-1 (b - A x') on the
+// owned rows to xout.
+template <typename T, int WQ>
+__global__ void __launch_bounds__(kPatchThreads<T>, 1) up_fused_kernel(
+    const int32_t *__restrict__ g_ptr, const int32_t *__restrict__ g_nown, const int32_t *__restrict__ g_ids,
+    const int32_t *__restrict__ g0_base, const int32_t *__restrict__ glcol, const int32_t *__restrict__ gcol,
+    const int32_t *__restrict__ gpar, const int32_t *__restrict__ grow_par, const T *__restrict__ A,
+    const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x, const T *__restrict__ ec,
+    T *__restrict__ xout, T omega) {
+    constexpr int W = 4 * WQ;
+    extern __shared__ __align__(16) unsigned char patch_smem[];
+    T *xs = reinterpret_cast<T *>(patch_smem);
+    const int blk = blockIdx.x, s = threadIdx.x;
+    const int s0 = g_ptr[blk], n1 = g_ptr[blk + 1] - s0, nown = g_nown[blk];
+    const bool row = s < n1, own = s < nown;
+    int v = 0;
+    int4 cols[WQ], lcs[WQ], par[2 * WQ];
+    int2 rp = make_int2(0, 0);
+    if (row) {
+        v = g_ids[s0 + s];
+#pragma unroll
+        for (int g = 0; g < WQ; ++g) cols[g] = load_cols(gcol + size_t(s0 + s) * W + 4 * g);
+#pragma unroll
+        for (int g = 0; g < 2 * WQ; ++g) par[g] = load_cols(gpar + size_t(s0 + s) * 2 * W + 4 * g);
+        rp = *reinterpret_cast<const int2 *>(grow_par + 2 * size_t(s0 + s));
+    }
+    if (own) {
+        const int r0 = g0_base[blk];
+#pragma unroll
+        for (int g = 0; g < WQ; ++g) lcs[g] = load_cols(glcol + size_t(r0 + s) * W + 4 * g);
+    }
+    T av[W];
+    T bv = T(0), wv = T(0), x3 = T(0);
+    if (row) {
+#pragma unroll
+        for (int g = 0; g < WQ; ++g) load4(A + size_t(v) * W + 4 * g, av + 4 * g);
+        bv = b[v];
+        wv = omega * dinv[v];
+        T ax = T(0);
+#pragma unroll
+        for (int g = 0; g < WQ; ++g)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = 4 * g + u;
+                const int4 pq = par[q / 2];
+                const int pa = (q & 1) ? pq.z : pq.x, pb = (q & 1) ? pq.w : pq.y;
+                ax = fma(av[q], x[cget(cols[g], u)] + prolong_at(ec, pa, pb), ax);
+            }
+        x3 = fma(wv, bv - ax, x[v] + prolong_at(ec, rp.x, rp.y));
+        xs[s] = x3;
+    }
+    __syncthreads();
+    if (own) {
+        T ax = T(0);
+#pragma unroll
+        for (int g = 0; g < WQ; ++g)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ax = fma(av[4 * g + u], xs[cget(lcs[g], u)], ax);
+        xout[v] = fma(wv, bv - ax, x3);
+    }
+}
+
 // The V-cycle over the small levels in one CTA.  The levels' operators
 // (ELL values and columns, inverse diagonals), transfer lists and, when it
 // fits, the coarsest level's FP64 inverse were packed at condensation into one
@@ -187,30 +364,30 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, long long limit) {
     return false;
 }
 
-__host__ __device__ constexpr size_t pad16(size_t bytes) { return (bytes + 15) / 16 * 16; }
-
-// Shared-memory addresses and sizes of one tail level.  The table lives in
-// shared memory (filled from the staged header, one thread per level) so that
-// run-time level indices never put per-thread pointer arrays on the stack.
+// dense FP64 product x = inv b of the coarsest level (n rows): four lanes per
+// row (FP64 arithmetic is a narrow pipe: few adds in the tree), each summing
+// every fourth column, combined by a fixed two-step shuffle.  Whole warps take
+// part in every shuffle: the row loop runs to a multiple of 8.
 template <typename T>
-struct TailSlot {
-    T *A, *D, *cw, *x, *x2, *b, *r;
-    int32_t *col, *cp, *ci, *par;
-    int nv, nnz, nci, W;
-};
-
-// x_j + (P e_c)_j: the midpoint prolongation of the coarse correction added on the fly
-template <typename T>
-__device__ __forceinline__ T prolonged(const int32_t *par, const T *x, const T *ec, int j) {
-    const int p0 = par[2 * j], p1 = par[2 * j + 1];
-    return x[j] + ((p0 == p1) ? ec[p0] : T(0.5) * (ec[p0] + ec[p1]));
+__device__ __forceinline__ void coarse_product(const double *inv, int n, const T *b, T *x) {
+    const int sub = threadIdx.x & 3, ng = blockDim.x >> 2;
+    for (int i = threadIdx.x >> 2; i < ((n + 7) & ~7); i += ng) {
+        double acc = 0.0;
+        if (i < n)
+            for (int j = sub; j < n; j += 4) acc = fma(inv[size_t(i) * n + j], double(b[j]), acc);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (i < n && sub == 0) x[i] = T(acc);
+    }
 }
 
+
+// Every array pointer below is the shared-memory base plus an offset from the
+// level table, so that the compiler addresses shared memory directly.
 template <typename T>
 __global__ void __launch_bounds__(1024, 1) tail_kernel(TailArgs a) {
     extern __shared__ __align__(16) unsigned char tail_smem[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ TailSlot<T> L[kTailMaxLevels];
     const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar)) : "memory");
@@ -229,13 +406,15 @@ __global__ void __launch_bounds__(1024, 1) tail_kernel(TailArgs a) {
         if (o < a.img_bytes) bulk_g2s(tail_smem + o, a.img + o, min(kChunk, a.img_bytes - o), &bar);
     }
     const T om = T(a.omega);
+    auto PT = [&](int32_t o) { return reinterpret_cast<T *>(tail_smem + o); };
+    auto PI = [&](int32_t o) { return reinterpret_cast<int32_t *>(tail_smem + o); };
     // meanwhile, with plain loads into the scratch space after the image: the
     // first level's right-hand side and its first pre-smoothing sweep from
     // zero, x = omega D^-1 b (the inverse diagonal read from global memory)
     {
         const T *btop = static_cast<const T *>(a.b_top);
         const T *d0 = static_cast<const T *>(a.dinv0);
-        T *b0 = reinterpret_cast<T *>(tail_smem + a.ob0), *x0 = reinterpret_cast<T *>(tail_smem + a.ox0);
+        T *b0 = PT(a.ob0), *x0 = PT(a.ox0);
         for (int i = tid; i < a.nv0; i += nt) {
             const T bi = btop[i];
             b0[i] = bi;
@@ -249,47 +428,36 @@ __global__ void __launch_bounds__(1024, 1) tail_kernel(TailArgs a) {
         bar_wait(&bar, 1ll << 22);
         return;
     }
-    if (tid < a.nlev) {
-        const TailHdr H = reinterpret_cast<const TailHdr *>(tail_smem)[tid];
-        TailSlot<T> &S = L[tid];
-        S.nv = H.nv; S.nnz = H.nnz; S.nci = H.nci; S.W = H.W;
-        S.A = reinterpret_cast<T *>(tail_smem + H.oA);
-        S.D = reinterpret_cast<T *>(tail_smem + H.oD);
-        S.cw = reinterpret_cast<T *>(tail_smem + H.ocw);
-        S.col = reinterpret_cast<int32_t *>(tail_smem + H.ocol);
-        S.cp = reinterpret_cast<int32_t *>(tail_smem + H.ocp);
-        S.ci = reinterpret_cast<int32_t *>(tail_smem + H.oci);
-        S.par = reinterpret_cast<int32_t *>(tail_smem + H.opar);
-        S.x = reinterpret_cast<T *>(tail_smem + H.ox);
-        S.x2 = reinterpret_cast<T *>(tail_smem + H.ox2);
-        S.b = reinterpret_cast<T *>(tail_smem + H.ob);
-        S.r = reinterpret_cast<T *>(tail_smem + H.orr);
-    }
     __syncthreads();
-    const int nc = L[a.nlev - 1].nv;
-    const double *sinv = a.inv_off >= 0 ? reinterpret_cast<const double *>(tail_smem + a.inv_off) : nullptr;
+    TailHdr *H = reinterpret_cast<TailHdr *>(tail_smem);   // staged level table (ox/ox2 rewritten below)
     const int last = a.nlev - 1;
     // ---- down: x holds the first sweep (or zero) on entry to each level
     for (int l = 0; l < last; ++l) {
-        const int nv = L[l].nv, W = L[l].W;
-        const int32_t *cl = L[l].col;
-        const T *A = L[l].A, *D = L[l].D, *b = L[l].b;
-        T *x = L[l].x, *x2 = L[l].x2, *r = L[l].r;
+        const TailHdr h = H[l], hc = H[l + 1];
+        const int nv = h.nv, W = h.W;
+        const int32_t *cl = PI(h.ocol);
+        const T *A = PT(h.oA), *D = PT(h.oD), *b = PT(h.ob);
+        T *r = PT(h.orr);
+        int32_t ox = h.ox, ox2 = h.ox2;
         for (int k = 1; k < a.nu1; ++k) {
+            const T *x = PT(ox);
+            T *x2 = PT(ox2);
             for (int i = tid; i < nv; i += nt) x2[i] = fma(om * D[i], b[i] - ell_row(i, W, cl, A, x), x[i]);
             __syncthreads();
-            T *t = x; x = x2; x2 = t;
+            const int32_t t = ox; ox = ox2; ox2 = t;
         }
-        for (int i = tid; i < nv; i += nt) r[i] = b[i] - ell_row(i, W, cl, A, x);
-        if (tid == 0) { L[l].x = x; L[l].x2 = x2; }   // read again only after later barriers
+        {
+            const T *x = PT(ox);
+            for (int i = tid; i < nv; i += nt) r[i] = b[i] - ell_row(i, W, cl, A, x);
+        }
+        if (tid == 0) { H[l].ox = ox; H[l].ox2 = ox2; }   // read again only after later barriers
         __syncthreads();
         // restriction, with the coarse level's first sweep from zero
-        const int ncv = L[l + 1].nv;
-        const int32_t *cp = L[l + 1].cp, *ci = L[l + 1].ci;
-        const T *cw = L[l + 1].cw, *Dc = L[l + 1].D;
-        T *bc = L[l + 1].b, *xc = L[l + 1].x;
+        const int32_t *cp = PI(hc.ocp), *ci = PI(hc.oci);
+        const T *cw = PT(hc.ocw), *Dc = PT(hc.oD);
+        T *bc = PT(hc.ob), *xc = PT(hc.ox);
         const bool smooth_c = l + 1 < last;
-        for (int i = tid; i < ncv; i += nt) {
+        for (int i = tid; i < hc.nv; i += nt) {
             T acc = T(0);
             for (int k = cp[i]; k < cp[i + 1]; ++k) acc = fma(cw[k], r[ci[k]], acc);
             bc[i] = acc;
@@ -297,44 +465,40 @@ __global__ void __launch_bounds__(1024, 1) tail_kernel(TailArgs a) {
         }
         __syncthreads();
     }
-    // ---- coarsest: dense FP64 inverse, FP64 sums in every precision; four
-    // lanes per row (FP64 arithmetic is a narrow pipe: few adds in the tree),
-    // each summing every fourth column, combined by a fixed two-step shuffle
+    // ---- coarsest: dense FP64 inverse, FP64 sums in every precision
     {
-        const double *inv = sinv ? sinv : a.inv;
-        const T *b = L[last].b;
-        T *x = L[last].x;
-        const int sub = tid & 3, ng = nt >> 2;
-        // whole warps take part in every shuffle: the row loop runs to a multiple of 8
-        for (int i = tid >> 2; i < ((nc + 7) & ~7); i += ng) {
-            double acc = 0.0;
-            if (i < nc)
-                for (int j = sub; j < nc; j += 4) acc = fma(inv[size_t(i) * nc + j], double(b[j]), acc);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            if (i < nc && sub == 0) x[i] = T(acc);
-        }
+        const TailHdr h = H[last];
+        if (a.inv_off >= 0) coarse_product<T>(reinterpret_cast<const double *>(tail_smem + a.inv_off), h.nv, PT(h.ob), PT(h.ox));
+        else coarse_product<T>(a.inv, h.nv, PT(h.ob), PT(h.ox));
         __syncthreads();
     }
     // ---- up: x += P e_c in place (a separate step: forming it on the fly in
     // the sweep multiplies the shared-memory gathers), then post-smoothing
-    const T *ec = L[last].x;
+    int32_t oec = H[last].ox;
     for (int l = last - 1; l >= 0; --l) {
-        const int nv = L[l].nv, W = L[l].W;
-        const int32_t *cl = L[l].col, *par = L[l + 1].par;
-        const T *A = L[l].A, *D = L[l].D, *b = L[l].b;
-        T *x = L[l].x, *x2 = L[l].x2;
-        for (int i = tid; i < nv; i += nt) x[i] = prolonged(par, x, ec, i);
+        const TailHdr h = H[l];
+        const int nv = h.nv, W = h.W;
+        const int32_t *cl = PI(h.ocol), *par = PI(H[l + 1].opar);
+        const T *A = PT(h.oA), *D = PT(h.oD), *b = PT(h.ob);
+        int32_t ox = h.ox, ox2 = h.ox2;
+        {
+            const T *ec = PT(oec);
+            T *x = PT(ox);
+            for (int i = tid; i < nv; i += nt) x[i] = prolonged(par, x, ec, i);
+        }
         __syncthreads();
         for (int k = 0; k < a.nu2; ++k) {
+            const T *x = PT(ox);
+            T *x2 = PT(ox2);
             for (int i = tid; i < nv; i += nt) x2[i] = fma(om * D[i], b[i] - ell_row(i, W, cl, A, x), x[i]);
             __syncthreads();
-            T *t = x; x = x2; x2 = t;
+            const int32_t t = ox; ox = ox2; ox2 = t;
         }
-        ec = x;
+        oec = ox;
     }
     T *xtop = static_cast<T *>(a.x_top);
-    for (int i = tid; i < L[0].nv; i += nt) xtop[i] = ec[i];
+    const T *ec = PT(oec);
+    for (int i = tid; i < a.nv0; i += nt) xtop[i] = ec[i];
 }
 
 }  // namespace
@@ -383,6 +547,42 @@ cudaError_t launch_p1_up(const DevLevel &fine, const DevLevel &coarse, const T *
                                                       coarse.parent, ec, xout, omega);
     return cudaGetLastError();
 }
+// The patch kernels run one thread per row of the largest patch and hold a
+// row's operator values in registers: ELL widths 4 and 8.
+template <typename T>
+bool p1_patch_ok(const DevLevel &L) {
+    return L.nb > 0 && (L.width == 4 || L.width == 8) && L.max_f1 <= kPatchThreads<T> &&
+           L.max_g1 <= kPatchThreads<T> && sizeof(T) * size_t(L.max_f1 + L.max_f0) <= 48 * 1024;
+}
+inline unsigned patch_threads(int rows) { return unsigned(std::max(64, (rows + 31) / 32 * 32)); }
+
+template <typename T>
+cudaError_t launch_p1_down_fused(const DevLevel &fine, const DevLevel &coarse, const T *A_f, const T *dinv_f,
+                                 const T *b_f, const T *x_f, T *xout_f, const T *dinv_c, T omega, T *b_c, T *x_c,
+                                 cudaStream_t s) {
+    if (!p1_patch_ok<T>(fine)) return cudaErrorInvalidValue;
+    const T *ccw = sizeof(T) == 4 ? reinterpret_cast<const T *>(fine.pcc_w32) : reinterpret_cast<const T *>(fine.pcc_w);
+    const size_t smem = sizeof(T) * size_t(fine.max_f1 + fine.max_f0);
+    auto k = fine.width == 4 ? down_fused_kernel<T, 1> : down_fused_kernel<T, 2>;
+    k<<<fine.nb, patch_threads(fine.max_f1), smem, s>>>(fine.pf_ptr, fine.pf_n0, fine.pf_ids, fine.pf0_base, fine.plcol,
+                                                        fine.pfcol, fine.pc_ptr, fine.pc_ids, fine.pcc_ptr,
+                                                        fine.pcc_slot, ccw, A_f, dinv_f, b_f, x_f, xout_f, dinv_c,
+                                                        omega, b_c, x_c, fine.max_f1);
+    (void)coarse;
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_p1_up_fused(const DevLevel &fine, const DevLevel &coarse, const T *A_f, const T *dinv_f,
+                               const T *b_f, const T *x_f, const T *ec, T *xout, T omega, cudaStream_t s) {
+    if (!p1_patch_ok<T>(fine)) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(T) * size_t(fine.max_g1);
+    auto k = fine.width == 4 ? up_fused_kernel<T, 1> : up_fused_kernel<T, 2>;
+    k<<<fine.nb, patch_threads(fine.max_g1), smem, s>>>(fine.pg_ptr, fine.pg_nown, fine.pg_ids, fine.pg0_base,
+                                                        fine.pglcol, fine.pgcol, fine.pgpar, fine.pgrow_par, A_f,
+                                                        dinv_f, b_f, x_f, ec, xout, omega);
+    (void)coarse;
+    return cudaGetLastError();
+}
 template <typename T>
 cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s) {
     // one fixed limit for every handle: the attribute is process-wide, so a
@@ -406,6 +606,11 @@ cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s) {
                                            const T *, T, T *, T *, cudaStream_t);                               \
     template cudaError_t launch_p1_up<T>(const DevLevel &, const DevLevel &, const T *, const T *, const T *,    \
                                          const T *, const T *, T *, T, cudaStream_t);                           \
+    template cudaError_t launch_p1_down_fused<T>(const DevLevel &, const DevLevel &, const T *, const T *,        \
+                                                 const T *, const T *, T *, const T *, T, T *, T *, cudaStream_t); \
+    template cudaError_t launch_p1_up_fused<T>(const DevLevel &, const DevLevel &, const T *, const T *, const T *, \
+                                               const T *, const T *, T *, T, cudaStream_t);                        \
+    template bool p1_patch_ok<T>(const DevLevel &);                                                          \
     template cudaError_t launch_p1_tail<T>(const TailArgs &, size_t, cudaStream_t);
 HDG_P1_INST(double)
 HDG_P1_INST(float)

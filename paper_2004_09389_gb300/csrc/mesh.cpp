@@ -236,6 +236,8 @@ std::string build_host_mesh(const hdg_mesh_desc *desc, HostMesh &hm) {
         HostLevel hl;
         hl.nv = C.n_vertices;
         hl.nc = C.n_cells;
+        hl.vdim = C.dim;
+        hl.vxyz.assign(C.vertex_xyz, C.vertex_xyz + size_t(C.n_vertices) * C.dim);
         hl.cells.assign(C.cell_vertices, C.cell_vertices + 3 * size_t(C.n_cells));
         e = local_coords(C, hl.X);
         if (!e.empty()) return what + ": " + e;
@@ -260,7 +262,130 @@ std::string build_host_mesh(const hdg_mesh_desc *desc, HostMesh &hm) {
     }
     if (hm.levels.back().nv > 1024)
         return "the coarsest P1 level has more than 1024 vertices; pass more coarse levels";
+    // patches only where their per-row copies stay small (a few MB): on larger
+    // levels the copies displace the facet operator from L2 and the unfused
+    // kernels measured faster
+    for (int l = 0; l + 1 < int(hm.levels.size()); ++l)
+        if (hm.levels[l].nv <= kPatchMaxVertices) build_p1_patches(hm, l, 128);
     return "";
+}
+
+namespace {
+
+// recursive coordinate bisection of ids[lo, hi) into parts of at most maxsz
+// vertices: split at the median of the coordinate with the largest extent
+// (ties by vertex id, so the result is deterministic)
+void rcb(std::vector<int> &ids, int lo, int hi, const std::vector<double> &xyz, int dim, int maxsz,
+         std::vector<int> &part, int &np) {
+    if (hi - lo <= maxsz) {
+        for (int i = lo; i < hi; ++i) part[ids[i]] = np;
+        ++np;
+        return;
+    }
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int i = lo; i < hi; ++i)
+        for (int d = 0; d < dim; ++d) {
+            const double x = xyz[size_t(ids[i]) * dim + d];
+            mn[d] = std::min(mn[d], x);
+            mx[d] = std::max(mx[d], x);
+        }
+    int ax = 0;
+    for (int d = 1; d < dim; ++d)
+        if (mx[d] - mn[d] > mx[ax] - mn[ax]) ax = d;
+    const int mid = lo + (hi - lo) / 2;
+    std::nth_element(ids.begin() + lo, ids.begin() + mid, ids.begin() + hi, [&](int a, int b) {
+        const double xa = xyz[size_t(a) * dim + ax], xb = xyz[size_t(b) * dim + ax];
+        return xa < xb || (xa == xb && a < b);
+    });
+    rcb(ids, lo, mid, xyz, dim, maxsz, part, np);
+    rcb(ids, mid, hi, xyz, dim, maxsz, part, np);
+}
+
+}  // namespace
+
+void build_p1_patches(HostMesh &hm, int l, int target_blocks) {
+    HostLevel &F = hm.levels[l];
+    const HostLevel &C = hm.levels[l + 1];
+    HostPatches &P = F.patch;
+    P = HostPatches{};
+    const int W = F.width, nf = F.nv, nc = C.nv;
+    // about target_blocks patches, each of 16 to 128 coarse vertices (so that a
+    // patch's rows fit one block of at most 1024 threads)
+    const int maxsz = std::min(128, std::max(16, (nc + target_blocks - 1) / target_blocks));
+    std::vector<int> ids(nc), part(nc, -1);
+    for (int c = 0; c < nc; ++c) ids[c] = c;
+    int nb = 0;
+    rcb(ids, 0, nc, C.vxyz, C.vdim, maxsz, part, nb);
+    P.nb = nb;
+    std::vector<std::vector<int>> members(nb);
+    for (int c = 0; c < nc; ++c) members[part[c]].push_back(c);            // ascending ids per patch
+    std::vector<std::vector<int>> owned(nb);
+    for (int v = 0; v < nf; ++v) owned[part[C.parent[2 * v]]].push_back(v);
+    std::vector<int> slot(nf, -1);
+    // rows first (ascending), then their neighbours not among them (ascending)
+    auto ring = [&](const std::vector<int> &rows, std::vector<int> &out) {
+        out = rows;
+        for (size_t i = 0; i < rows.size(); ++i) slot[rows[i]] = int(i);
+        std::vector<int> halo;
+        for (int v : rows)
+            for (int q = 0; q < W; ++q) {
+                const int u = F.col[size_t(v) * W + q];
+                if (slot[u] < 0) { slot[u] = -2; halo.push_back(u); }
+            }
+        std::sort(halo.begin(), halo.end());
+        for (size_t i = 0; i < halo.size(); ++i) slot[halo[i]] = int(rows.size() + i);
+        out.insert(out.end(), halo.begin(), halo.end());
+    };
+    P.f_ptr.push_back(0); P.c_ptr.push_back(0); P.cc_ptr.push_back(0); P.g_ptr.push_back(0);
+    std::vector<int> set;
+    for (int b = 0; b < nb; ++b) {
+        // going down: children of the patch's coarse vertices, then their neighbours
+        std::vector<int> f0;
+        for (int c : members[b])
+            for (int k = C.child_ptr[c]; k < C.child_ptr[c + 1]; ++k) f0.push_back(C.child_idx[k]);
+        std::sort(f0.begin(), f0.end());
+        f0.erase(std::unique(f0.begin(), f0.end()), f0.end());
+        ring(f0, set);
+        P.f0_base.push_back(int(P.lcol.size() / W));
+        for (int v : f0)
+            for (int q = 0; q < W; ++q) P.lcol.push_back(slot[F.col[size_t(v) * W + q]]);
+        for (int c : members[b]) {
+            P.c_ids.push_back(c);
+            for (int k = C.child_ptr[c]; k < C.child_ptr[c + 1]; ++k) {
+                P.cc_slot.push_back(slot[C.child_idx[k]]);
+                P.cc_w.push_back(C.child_w[k]);
+            }
+            P.cc_ptr.push_back(int(P.cc_slot.size()));
+        }
+        P.c_ptr.push_back(int(P.c_ids.size()));
+        P.f_n0.push_back(int(f0.size()));
+        P.f_ids.insert(P.f_ids.end(), set.begin(), set.end());
+        for (int v : set) P.fcol.insert(P.fcol.end(), F.col.begin() + size_t(v) * W, F.col.begin() + size_t(v + 1) * W);
+        P.f_ptr.push_back(int(P.f_ids.size()));
+        P.max_f0 = std::max(P.max_f0, int(f0.size()));
+        P.max_f1 = std::max(P.max_f1, int(set.size()));
+        for (int v : set) slot[v] = -1;
+        // going up: owned fine vertices, then their neighbours
+        ring(owned[b], set);
+        P.g0_base.push_back(int(P.glcol.size() / W));
+        for (int v : owned[b])
+            for (int q = 0; q < W; ++q) P.glcol.push_back(slot[F.col[size_t(v) * W + q]]);
+        P.g_nown.push_back(int(owned[b].size()));
+        P.g_ids.insert(P.g_ids.end(), set.begin(), set.end());
+        for (int v : set) {
+            for (int q = 0; q < W; ++q) {
+                const int j = F.col[size_t(v) * W + q];
+                P.gcol.push_back(j);
+                P.gpar.push_back(C.parent[2 * j]);
+                P.gpar.push_back(C.parent[2 * j + 1]);
+            }
+            P.grow_par.push_back(C.parent[2 * v]);
+            P.grow_par.push_back(C.parent[2 * v + 1]);
+        }
+        P.g_ptr.push_back(int(P.g_ids.size()));
+        P.max_g1 = std::max(P.max_g1, int(set.size()));
+        for (int v : set) slot[v] = -1;
+    }
 }
 
 }  // namespace hdg

@@ -386,3 +386,42 @@ def test_invalid_arguments():
         s.solve(ru, rh)
     assert ei.value.code == -9
     s.close()
+
+
+@pytest.mark.parametrize("kind", ["flat", "sphere"])
+@pytest.mark.parametrize("p1_nu", [(2, 2), (3, 3), (1, 1)])
+def test_precond_multi_block_p1_levels_match_oracle(kind, p1_nu, monkeypatch):
+    """The P1 levels above the single-CTA tail: with the tail limited to 16
+    vertices every other level runs in multi-block kernels, the patch-fused
+    ones (sweep + residual + restriction going down, prolongation + two
+    sweeps going up, ragged patches on three levels) where a level takes two
+    or more sweeps.  FP64 matches the oracle; FP64 and FP32 match the unfused
+    kernels up to summation order."""
+    if kind == "flat":
+        mesh = I.periodic_square_hierarchy(24, n_coarsest=3)       # P1 levels 576, 144, 36, 9
+        g, H, f = 1.3, 0.7, I.coriolis_flat(mesh, 1.0)
+    else:
+        mesh = I.sphere_hierarchy(3, 1.0, r_coarsest=0)            # P1 levels 642, 162, 42, 12
+        g, H, f = 1.0, 1.0, I.coriolis_sphere(mesh, 0.5)
+    p = 1
+    tau = 8 * mesh.h / np.sqrt(g * H)
+    prob = HDGProblem(mesh, p, tau=tau, g=g, H=H, f_vertex=f)
+    v = np.random.default_rng(5).standard_normal(prob.n_trace)
+    monkeypatch.setenv("HDG_TAIL_MAX_VERTICES", "16")
+    out = {}
+    for fused in ("1", "0"):
+        monkeypatch.setenv("HDG_P1_FUSED", fused)
+        s = _solver(mesh, p, tau, g, H, f, precision=1, p1_nu_pre=p1_nu[0], p1_nu_post=p1_nu[1])
+        z = torch.empty(prob.n_trace, dtype=torch.float64, device="cuda")
+        z32 = torch.empty(prob.n_trace, dtype=torch.float32, device="cuda")
+        s.precond_apply_dev(_dev(v), z)
+        s.precond_apply32_dev(_dev(v.astype(np.float32)), z32)
+        torch.cuda.synchronize()
+        out[fused] = (z.cpu().numpy(), z32.cpu().numpy().astype(np.float64))
+        s.close()
+    pc = TwoLevelPreconditioner(prob, mesh, prob.trace_operator(), coarse="gmg", p1_nu=p1_nu)
+    z0 = pc(v)
+    assert _rel(out["1"][0], z0) <= 1e-12
+    assert _rel(out["1"][0], out["0"][0]) <= 1e-14
+    assert _rel(out["1"][1], out["0"][1]) <= 1e-6
+    assert _rel(out["1"][1], z0) <= 1e-5
