@@ -618,6 +618,36 @@ def batch_main(args):
         s.close()
 
 
+def profile_solve_main(args):
+    """One warm solve + recovery inside cudaProfilerStart/Stop: the launch list of a
+    solve as it runs in the timed loop (caches warm from the previous solves)."""
+    import torch
+    from paper_2004_09389_gb300 import HDGSolver, HDG_FP64, HDG_MIXED_FP32, HDG_MIXED_BF16, HDG_MIXED_FGMRES64, build
+    build.build()
+    prec = {"mixed": HDG_MIXED_FP32, "mixed_bf16": HDG_MIXED_BF16, "fgmres64": HDG_MIXED_FGMRES64,
+            "fp64": HDG_FP64}[args.profile_solve]
+    wl = make_workload(args.workload, True, args.p, args.courant, args.seed)
+    s = HDGSolver(wl["mesh"], args.p, wl["tau"], wl["g"], wl["H"], f_vertex=wl["f"], rtol=args.rtol, precision=prec,
+                  inner_rtol=args.inner_rtol, restart=args.restart, reorth=args.reorth)
+    ru_d, rh_d = torch.from_numpy(wl["ru"]).cuda(), torch.from_numpy(wl["rh"]).cuda()
+    lam = torch.empty((s.n_facets, args.p + 1), dtype=torch.float64, device="cuda")
+    u = torch.empty((s.n_cells, 2, s.n_p), dtype=torch.float64, device="cuda")
+    h = torch.empty((s.n_cells, s.n_p), dtype=torch.float64, device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        s.solve_dev(ru_d, rh_d, lam)
+        s.recover_dev(ru_d, rh_d, lam, u, h)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    info = s.solve_dev(ru_d, rh_d, lam)
+    s.recover_dev(ru_d, rh_d, lam, u, h)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profile_solve": args.profile_solve, "workload": workload_label(args.workload, args.p,
+                                                                                       args.courant, args.seed),
+                      "iters": info["iters"], "true_rel_res": info["true_rel_res"]}))
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -642,7 +672,14 @@ def main():
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--batch", type=int, default=0, help="run the batched-solve benchmark with this many problems")
     ap.add_argument("--autotune", action="store_true", help="autotune launch shapes per handle (off by default: on the 256x256x2 workload the defaults measured faster)")
+    ap.add_argument("--profile-solve", dest="profile_solve", default="",
+                    choices=["", "mixed", "mixed_bf16", "fgmres64", "fp64"],
+                    help="warm up, then run one solve and recovery of this arm between profiler start and stop "
+                         "(for ncu --profile-from-start off); prints the iteration count, no bench line")
     args = ap.parse_args()
+    if args.profile_solve:
+        profile_solve_main(args)
+        return
     if args.batch:
         batch_main(args)
         return

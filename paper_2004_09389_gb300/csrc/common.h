@@ -165,6 +165,35 @@ struct ReadBack {
     int32_t pad;
 };
 
+#ifdef __CUDACC__
+// The last block of a grid-wide reduction: out[i] = sum over b < nb of
+// partial[i * nb + b] for i < k, in a fixed order.  The warps are shared out
+// among the vectors (all of them for one vector, half each for two, ...);
+// a warp's lanes take every 32 * (warps per vector)-th partial, then a
+// shuffle tree, then the vector's warps in order.  Every thread of the block
+// must call it.
+__device__ __forceinline__ void finish_partials(const double *partial, int nb, int k, double *out) {
+    __shared__ double red[32];
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nwarp = blockDim.x / 32;
+    const int wpv = nwarp / k > 1 ? nwarp / k : 1, vpr = nwarp / wpv;
+    for (int i0 = 0; i0 < k; i0 += vpr) {
+        const int i = i0 + warp / wpv, sub = warp % wpv;
+        double v = 0.0;
+        if (warp < vpr * wpv && i < k)
+            for (int b = sub * 32 + lane; b < nb; b += wpv * 32) v += partial[size_t(i) * nb + b];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        if (int(threadIdx.x) < vpr && i0 + int(threadIdx.x) < k) {
+            double t = 0.0;
+            for (int q = 0; q < wpv; ++q) t += red[threadIdx.x * wpv + q];
+            out[i0 + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+#endif
+
 // levels of the single-CTA V-cycle tail (k_p1.cu)
 constexpr int kMaxGsBlocks = 1216;     // largest grid of the fused Gram-Schmidt kernels (8 x 152 SMs)
 constexpr int kTailMaxLevels = 8;

@@ -203,8 +203,8 @@ template <> struct V16<double> {
 
 // Partial sums of V_i . w for i < k over this block's grid-stride range, in
 // groups of kGroup vectors (one pass over w per group, kGroup accumulators per
-// thread), then the last block to finish adds the partials in block order,
-// one warp per vector (deterministic).
+// thread), then the last block to finish adds the partials in a fixed order
+// (finish_partials: deterministic).
 constexpr int kGroup = 16;
 
 template <typename T>
@@ -239,20 +239,14 @@ __device__ void dots_and_finish(const typename V16<T>::type *__restrict__ V, siz
         }
         __syncthreads();
     }
-    __threadfence();
+    if (threadIdx.x < kGroup) __threadfence();  // the writers' partials are visible before the count
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     __syncthreads();
     *is_last = last;
     if (!last) return;
     __threadfence();
-    for (int i = warp; i < k; i += nwarp) {
-        double v = 0.0;
-        for (unsigned b = lane; b < gridDim.x; b += 32) v += partial[size_t(i) * gridDim.x + b];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) out[i] = v;
-    }
-    __syncthreads();
+    finish_partials(partial, int(gridDim.x), k, out);
     if (threadIdx.x == 0) *counter = 0u;
 }
 
@@ -286,8 +280,9 @@ __global__ void __launch_bounds__(256) gs_update_dots_kernel(const T *V, size_t 
     dots_and_finish<T>(V4p, ld4, k, w4, n4, partial, counter, h2, &last);
 }
 
-// w -= V h2 (h2 null: w -= V h1, one classical Gram-Schmidt pass), ||w||^2;
-// the last block forms Hessenberg column j (h1 + h2, or h1 alone;
+// w -= V h2 (h2 null: w -= V h1, one classical Gram-Schmidt pass) and
+// ||w||^2 in the same pass; the last block adds the per-block partials and
+// forms Hessenberg column j (h1 + h2, or h1 alone;
 // h_{j+1,j} = ||w||), applies the previous Givens rotations, forms rotation j,
 // updates the least-squares right-hand side and writes the residual
 // estimate |s_{j+1}| / ||b|| and the flags (2: breakdown, 4: NaN/Inf) to rb.
@@ -299,36 +294,87 @@ __global__ void __launch_bounds__(256) gs_update_norm_givens_kernel(const T *V, 
                                                                     double *sn, double *sv, int j,
                                                                     const double *bnorm, ReadBack *rb) {
     using V4 = typename V16<T>::type;
+    using A = typename V16<T>::acc;
     const size_t ld4 = ld / (16 / sizeof(T)), n4 = n / (16 / sizeof(T));
     const V4 *V4p = reinterpret_cast<const V4 *>(V);
     V4 *w4 = reinterpret_cast<V4 *>(w);
-    block_update<T>(V4p, ld4, k, w4, n4, h2 ? h2 : h1);
-    bool last;
-    dots_and_finish<T>(w4, 0, 1, w4, n4, partial, counter, nrm2, &last);
-    if (!last || threadIdx.x != 0) return;
-    double *col = Hm + size_t(j) * ldh;
-    for (int i = 0; i <= j; ++i) col[i] = h2 ? h1[i] + h2[i] : h1[i];
-    col[j + 1] = sqrt(nrm2[0]);
-    for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-        col[i] = t;
+    const double *c = h2 ? h2 : h1;
+    __shared__ T cs_[66];
+    __shared__ A red[32];
+    __shared__ double redd[32];
+    __shared__ bool last;
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nwarp = blockDim.x / 32;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) cs_[i] = T(-c[i]);
+    __syncthreads();
+    // the update and ||w||^2 in one pass: each updated value is squared from registers
+    A nrm = A(0);
+    for (size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < n4; idx += size_t(gridDim.x) * blockDim.x) {
+        V4 acc = w4[idx];
+        for (int i = 0; i < k; ++i) acc = V16<T>::axpy(cs_[i], V4p[size_t(i) * ld4 + idx], acc);
+        w4[idx] = acc;
+        nrm += V16<T>::dot(acc, acc);
     }
-    const double a = col[j], b = col[j + 1];
+    for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
+    if (lane == 0) red[warp] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        A t = A(0);
+        for (int q = 0; q < nwarp; ++q) t += red[q];
+        partial[blockIdx.x] = double(t);
+        __threadfence();                       // the partial is visible before the count
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // the Hessenberg column and the previous rotations into shared memory (one
+    // load per thread, alongside the partials), so that the sequential
+    // rotations below touch no global memory
+    __shared__ double colS[66], csS[66], snS[66];
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) colS[i] = h2 ? h1[i] + h2[i] : h1[i];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        csS[i] = cs[i];
+        snS[i] = sn[i];
+    }
+    // the last block adds the partials with all its threads, in a fixed order
+    // (thread t: partials t, t + blockDim, ...; then the warp tree; then the warps)
+    double v = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) v += partial[b];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) redd[warp] = v;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double svj = sv[j], bn = bnorm[0];
+    double ww = 0.0;
+    for (int q = 0; q < nwarp; ++q) ww += redd[q];
+    *counter = 0u;
+    nrm2[0] = ww;
+    colS[j + 1] = sqrt(ww);
+    for (int i = 0; i < j; ++i) {
+        const double t = csS[i] * colS[i] + snS[i] * colS[i + 1];
+        colS[i + 1] = -snS[i] * colS[i] + csS[i] * colS[i + 1];
+        colS[i] = t;
+    }
+    double *col = Hm + size_t(j) * ldh;
+    for (int i = 0; i < j; ++i) col[i] = colS[i];
+    const double a = colS[j], b = colS[j + 1];
     const double den = hypot(a, b);
     int32_t fl = 0;
+    double cj = 1.0, sj = 0.0;
     if (!(den > 0.0)) {
-        cs[j] = 1.0; sn[j] = 0.0;
         fl |= 2;
     } else {
-        cs[j] = a / den; sn[j] = b / den;
+        cj = a / den;
+        sj = b / den;
     }
+    cs[j] = cj;
+    sn[j] = sj;
     if (!(fabs(b) > 1e-300 * (fabs(a) + 1e-300))) fl |= 2;
     col[j] = (den > 0.0) ? den : a;
     col[j + 1] = 0.0;
-    sv[j + 1] = -sn[j] * sv[j];
-    sv[j] = cs[j] * sv[j];
-    const double est = fabs(sv[j + 1]) / bnorm[0];
+    sv[j + 1] = -sj * svj;
+    sv[j] = cj * svj;
+    const double est = fabs(-sj * svj) / bn;
     if (!isfinite(est) || !isfinite(den)) fl |= 4;
     rb->est = est;
     rb->flags = fl;

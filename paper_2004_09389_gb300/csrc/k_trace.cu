@@ -188,19 +188,13 @@ __global__ void __launch_bounds__(256, 4) apply_dots_kernel(int NF, const ST *__
         }
         __syncthreads();
     }
-    __threadfence();
+    if (threadIdx.x < G) __threadfence();      // the writers' partials are visible before the count
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int i = warp; i < k; i += nwarp) {
-        double t = 0.0;
-        for (unsigned b = lane; b < gridDim.x; b += 32) t += partial[size_t(i) * gridDim.x + b];
-        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-        if (lane == 0) h[i] = t;
-    }
-    __syncthreads();
+    finish_partials(partial, int(gridDim.x), k, h);
     if (threadIdx.x == 0) *counter = 0u;
 }
 
