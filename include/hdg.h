@@ -150,7 +150,12 @@ HDG_API void hdg_default_params(hdg_params *prm);
  * cell frames, P1 hierarchy and its geometric mass / stiffness matrices) to
  * the device.  stream: a cudaStream_t to run on, or NULL for a new
  * non-blocking stream owned by the handle.  On failure *out is NULL and the
- * error text is available from hdg_last_error(NULL). */
+ * error text is available from hdg_last_error(NULL).
+ * Two environment variables, read here, select equivalent launch structures
+ * (for timing comparisons; results agree up to summation order):
+ * HDG_TAIL_MAX_VERTICES (16..4096, default 1024) bounds the P1 levels run by
+ * the single-block coarse cycle; HDG_P1_FUSED=0 replaces the patch-fused P1
+ * kernels by one launch per smoothing / transfer step. */
 HDG_API int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hdg_handle **out);
 
 /* (Re)build the cell operators for the handle's parameters: for every cell the
