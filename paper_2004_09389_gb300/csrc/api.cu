@@ -52,6 +52,7 @@ struct Workspace {
     int nblk_gs = 1;      // blocks of the fused Gram-Schmidt kernels
     unsigned int *counter = nullptr;
     ReadBack *rb = nullptr, *host_rb = nullptr;
+    ReadBack *host_rb_dev = nullptr;   // device address of host_rb (page-locked, written by the Gram-Schmidt kernel)
     double *g = nullptr, *x = nullptr, *r = nullptr, *ycell = nullptr;
     float2 *x2 = nullptr;  // mixed modes: split copy of the FP64 iterate x (two-float residual)
     KSpace<double> k64;
@@ -501,11 +502,32 @@ cudaError_t arnoldi_step(hdg_handle *h, int j) {
     const bool reorth = h->prm.reorth != 0;
     if ((e = KL(HDG_PROF_KRYLOV, 1 + (reorth ? 1 : 0) + (fuse_scale ? 0 : 1),
                 launch_gs_step<T>(k.V, ld, j, k.w, W.partial, W.counter, W.nblk_gs, W.h1, W.h2, W.nrm2, W.Hm, ldh,
-                                  W.cs, W.sn, W.sv, W.bnorm, W.rb, k.V + size_t(j + 1) * ld, reorth, !fuse_scale,
-                                  s))) != cudaSuccess)
+                                  W.cs, W.sn, W.sv, W.bnorm, W.rb, W.host_rb_dev, k.V + size_t(j + 1) * ld, reorth,
+                                  !fuse_scale, s))) != cudaSuccess)
         return e;
     (void)NT;
-    return cudaMemcpyAsync(W.host_rb, W.rb, sizeof(ReadBack), cudaMemcpyDeviceToHost, s);
+    return cudaSuccess;
+}
+
+// Wait for Arnoldi step j's readback: spin on the step number that the
+// Gram-Schmidt kernel writes last into the page-locked copy, checking the
+// stream every 256 polls (an error, or a finished stream without the number,
+// ends the wait with HDG_ECUDA).
+int wait_readback(hdg_handle *h, int j) {
+    Workspace &W = *h->ws;
+    const volatile int32_t *seq = &W.host_rb->seq;
+    for (uint64_t it = 1;; ++it) {
+        if (*seq == j + 1) break;
+        if ((it & 255) == 0) {
+            const cudaError_t q = cudaStreamQuery(h->stream);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) return fail(h, HDG_ECUDA, std::string("Arnoldi step: ") + cudaGetErrorString(q));
+            if (*seq == j + 1) break;
+            return fail(h, HDG_ECUDA, "Arnoldi step finished without its readback");
+        }
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    return HDG_OK;
 }
 
 // Run Arnoldi step j: directly while kernel timing is on, otherwise through
@@ -571,10 +593,15 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
     int j = 0;
     double hist[72];
     for (; j < m && j < max_it; ++j) {
+        W.host_rb->seq = 0;   // the previous step's number was seen, so no write to it is in flight
         int rc = run_arnoldi_step<T>(h, j);
         if (rc) return rc;
-        TRY(cudaStreamSynchronize(s));
-        prof_flush(h);
+        if (h->prof.on) {
+            TRY(cudaStreamSynchronize(s));
+            prof_flush(h);
+        } else if ((rc = wait_readback(h, j))) {
+            return rc;
+        }
         est_out = W.host_rb->est;
         flag_out = W.host_rb->flags;
         hist[j] = est_out;
@@ -1092,6 +1119,8 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(cudaMemsetAsync(W.counter, 0, sizeof(unsigned int), s));
     TRY(dalloc(&W.rb, 1));
     TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_rb), sizeof(ReadBack)));
+    std::memset(W.host_rb, 0, sizeof(ReadBack));
+    TRY(cudaHostGetDevicePointer(reinterpret_cast<void **>(&W.host_rb_dev), W.host_rb, 0));
     TRY(dalloc(&W.flags, 1));
     TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_buf), 8 * sizeof(double)));
     TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_flags), 4 * sizeof(int32_t)));

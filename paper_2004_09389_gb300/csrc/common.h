@@ -162,7 +162,7 @@ struct ReadBack {
     double est;      // |s_{j+1}| / ||b||
     double hnext;    // h_{j+1,j} before rotation
     int32_t flags;   // 2: breakdown, 4: NaN/Inf
-    int32_t pad;
+    int32_t seq;     // page-locked copy only: j + 1, written last (after the other fields) by step j
 };
 
 #ifdef __CUDACC__
@@ -415,7 +415,7 @@ cudaError_t launch_fill(T *x, T v, size_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_gs_step(const T *V, size_t ld, int j, T *w, double *partial, unsigned int *counter, int nblk,
                            double *h1, double *h2, double *nrm2, double *Hm, int ldh, double *cs, double *sn,
-                           double *sv, const double *bnorm, ReadBack *rb, T *vnext, bool reorth, bool scale,
+                           double *sv, const double *bnorm, ReadBack *rb, ReadBack *host_rb, T *vnext, bool reorth, bool scale,
                            cudaStream_t s);
 int learned_n_params(int p, int hid);
 cudaError_t launch_learned_infer(hdg_handle *h, const float *r, const float *x, float *xout);

@@ -292,7 +292,8 @@ __global__ void __launch_bounds__(256) gs_update_norm_givens_kernel(const T *V, 
                                                                     double *partial, unsigned int *counter,
                                                                     double *nrm2, double *Hm, int ldh, double *cs,
                                                                     double *sn, double *sv, int j,
-                                                                    const double *bnorm, ReadBack *rb) {
+                                                                    const double *bnorm, ReadBack *rb,
+                                                                    ReadBack *host_rb) {
     using V4 = typename V16<T>::type;
     using A = typename V16<T>::acc;
     const size_t ld4 = ld / (16 / sizeof(T)), n4 = n / (16 / sizeof(T));
@@ -379,6 +380,15 @@ __global__ void __launch_bounds__(256) gs_update_norm_givens_kernel(const T *V, 
     rb->est = est;
     rb->flags = fl;
     rb->hnext = b;
+    if (host_rb) {
+        // the page-locked copy the host polls: the fields, a system-scope fence,
+        // then the step number, so that the host may read the fields once it sees it
+        host_rb->est = est;
+        host_rb->flags = fl;
+        host_rb->hnext = b;
+        __threadfence_system();
+        *reinterpret_cast<volatile int32_t *>(&host_rb->seq) = j + 1;
+    }
 }
 
 // v_{j+1} = w / h_{j+1,j}  (the unrotated norm kept in rb->hnext)
@@ -458,13 +468,13 @@ cudaError_t launch_d2f_scaled(const double *x, float *y, const double *scale, si
 template <typename T>
 cudaError_t launch_gs_step(const T *V, size_t ld, int j, T *w, double *partial, unsigned int *counter, int nblk,
                            double *h1, double *h2, double *nrm2, double *Hm, int ldh, double *cs, double *sn,
-                           double *sv, const double *bnorm, ReadBack *rb, T *vnext, bool reorth, bool scale,
+                           double *sv, const double *bnorm, ReadBack *rb, ReadBack *host_rb, T *vnext, bool reorth, bool scale,
                            cudaStream_t s) {
     // h1 = V^T w comes with w from the operator kernel (apply_dots_kernel)
     const int k = j + 1;
     if (reorth) gs_update_dots_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, h1, partial, counter, h2);
     gs_update_norm_givens_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, h1, reorth ? h2 : nullptr, partial, counter,
-                                                        nrm2, Hm, ldh, cs, sn, sv, j, bnorm, rb);
+                                                        nrm2, Hm, ldh, cs, sn, sv, j, bnorm, rb, host_rb);
     if (scale) {   // otherwise the next step's first smoothing sweep forms v_{j+1}
         const size_t n4 = ld / (16 / sizeof(T));
         gs_scale_kernel<T><<<blocks(n4, 256), 256, 0, s>>>(w, vnext, ld, rb);
@@ -473,10 +483,10 @@ cudaError_t launch_gs_step(const T *V, size_t ld, int j, T *w, double *partial, 
 }
 template cudaError_t launch_gs_step<float>(const float *, size_t, int, float *, double *, unsigned int *, int, double *,
                                            double *, double *, double *, int, double *, double *, double *,
-                                           const double *, ReadBack *, float *, bool, bool, cudaStream_t);
+                                           const double *, ReadBack *, ReadBack *, float *, bool, bool, cudaStream_t);
 template cudaError_t launch_gs_step<double>(const double *, size_t, int, double *, double *, unsigned int *, int,
                                             double *, double *, double *, double *, int, double *, double *, double *,
-                                            const double *, ReadBack *, double *, bool, bool, cudaStream_t);
+                                            const double *, ReadBack *, ReadBack *, double *, bool, bool, cudaStream_t);
 
 #define HDG_KRYLOV_INST(T)                                                                                      \
     template cudaError_t launch_multidot<T>(const T *, size_t, int, const T *, size_t, double *, int,           \
