@@ -204,7 +204,7 @@ HDG_API int hdg_solve_batch_dev(hdg_handle *const *hs, int n, const double *cons
 /* Pick launch shapes for this handle by timing one Arnoldi step (preconditioner,
  * operator application, Gram-Schmidt) for each candidate: threads per block of
  * the facet-row kernels (64 / 128 / 256), blocks of the fused Gram-Schmidt
- * kernels (152 / 304 / 608) and the largest level of the single-CTA coarse
+ * kernels (152 / 304 / 608 / 1216) and the largest level of the single-CTA coarse
  * cycle (256 / 1024 / 4096 vertices), one parameter at a time.  Needs
  * hdg_condense.  choice[0..2] (may be NULL) receives the three picks.  Results
  * do not depend on the choice beyond floating-point summation order. */

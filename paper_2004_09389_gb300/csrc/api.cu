@@ -53,6 +53,8 @@ struct Workspace {
     unsigned int *counter = nullptr;
     ReadBack *rb = nullptr, *host_rb = nullptr;
     ReadBack *host_rb_dev = nullptr;   // device address of host_rb (page-locked, written by the Gram-Schmidt kernel)
+    HostValue *host_val = nullptr, *host_val_dev = nullptr;   // norms handed to the host
+    int32_t val_seq = 0;
     double *g = nullptr, *x = nullptr, *r = nullptr, *ycell = nullptr;
     float2 *x2 = nullptr;  // mixed modes: split copy of the FP64 iterate x (two-float residual)
     KSpace<double> k64;
@@ -266,7 +268,8 @@ size_t hdg::tail_smem_bytes(const std::vector<DevLevel> &lev, int first, size_t 
 namespace {
 
 template <typename T>
-cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out);
+cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out, HostValue *pub = nullptr,
+                 int32_t seq = 0);
 
 // P1 V-cycle for the coarse problem (Eq. coarse_problem_upwind) with
 // right-hand side levB(level 0).  Levels above the tail: fused kernels (the
@@ -444,21 +447,47 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr) {
 // ---------------------------------------------------------------- Krylov helpers
 
 template <typename T>
-cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out) {
+cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out, HostValue *pub, int32_t seq) {
     Workspace &W = *h->ws;
     cudaError_t e = KL(HDG_PROF_KRYLOV, 1, launch_multidot<T>(V, W.NT, k, w, W.NT, W.partial, W.nchunk, h->stream));
     if (e != cudaSuccess) return e;
-    return KL(HDG_PROF_KRYLOV, 1, launch_reduce_partials(W.partial, k, W.nchunk, out, h->stream));
+    return KL(HDG_PROF_KRYLOV, 1, launch_reduce_partials(W.partial, k, W.nchunk, out, h->stream, pub, seq));
 }
 
+// Wait until the page-locked HostValue carries sequence number want: spin,
+// checking the stream every 256 polls (an error, or a finished stream
+// without the number, ends the wait with HDG_ECUDA).
+int wait_host_value(hdg_handle *h, int32_t want) {
+    Workspace &W = *h->ws;
+    const volatile int32_t *seq = &W.host_val->seq;
+    for (uint64_t it = 1;; ++it) {
+        if (*seq == want) break;
+        if ((it & 255) == 0) {
+            const cudaError_t q = cudaStreamQuery(h->stream);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) return fail(h, HDG_ECUDA, std::string("norm: ") + cudaGetErrorString(q));
+            if (*seq == want) break;
+            return fail(h, HDG_ECUDA, "norm kernel finished without handing over its value");
+        }
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    return HDG_OK;
+}
+
+// ||v||: the reduction kernel hands the squared norm to the host through
+// page-locked memory (no copy, no stream synchronisation)
 template <typename T>
 int norm_host(hdg_handle *h, const T *v, double &out) {
     Workspace &W = *h->ws;
-    TRY(dots<T>(h, v, 1, v, W.nrm2));
-    TRY(cudaMemcpyAsync(W.host_buf, W.nrm2, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    TRY(cudaStreamSynchronize(h->stream));
-    prof_flush(h);
-    out = std::sqrt(W.host_buf[0]);
+    const int32_t want = W.val_seq = W.val_seq % 1000000000 + 1;
+    TRY(dots<T>(h, v, 1, v, W.nrm2, W.host_val_dev, want));
+    if (h->prof.on) {
+        TRY(cudaStreamSynchronize(h->stream));
+        prof_flush(h);
+    }
+    int rc = wait_host_value(h, want);
+    if (rc) return rc;
+    out = std::sqrt(W.host_val->v);
     return HDG_OK;
 }
 
@@ -647,9 +676,10 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<T>(x, T(0), W.NT, s)));
         return HDG_OK;
     }
+    // host_buf[4] is written again only after the next norm, whose hand-over
+    // follows this copy in the stream
     W.host_buf[4] = bnorm;
     TRY(cudaMemcpyAsync(W.bnorm, W.host_buf + 4, sizeof(double), cudaMemcpyHostToDevice, s));
-    TRY(cudaStreamSynchronize(s));
     int total = 0;
     for (bool first = true;; first = false) {
         // r = b - S x into V[0] (r = b for a zero initial guess)
@@ -787,6 +817,7 @@ void free_handle(hdg_handle *h) {
         dfree(W.Hm); dfree(W.cs); dfree(W.sn); dfree(W.sv); dfree(W.h1); dfree(W.h2); dfree(W.nrm2);
         dfree(W.est); dfree(W.counter); dfree(W.rb);
         if (W.host_rb) cudaFreeHost(W.host_rb);
+        if (W.host_val) cudaFreeHost(W.host_val);
         dfree(W.scal); dfree(W.bnorm);
         for (auto &gv : W.graphs)
             for (auto &G : gv)
@@ -1121,6 +1152,9 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_rb), sizeof(ReadBack)));
     std::memset(W.host_rb, 0, sizeof(ReadBack));
     TRY(cudaHostGetDevicePointer(reinterpret_cast<void **>(&W.host_rb_dev), W.host_rb, 0));
+    TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_val), sizeof(HostValue)));
+    std::memset(W.host_val, 0, sizeof(HostValue));
+    TRY(cudaHostGetDevicePointer(reinterpret_cast<void **>(&W.host_val_dev), W.host_val, 0));
     TRY(dalloc(&W.flags, 1));
     TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_buf), 8 * sizeof(double)));
     TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_flags), 4 * sizeof(int32_t)));

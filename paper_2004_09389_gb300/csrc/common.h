@@ -158,6 +158,14 @@ struct Learned {
 };
 
 // per-iteration readback of the Krylov driver (pinned host copy)
+// a scalar handed to the host through page-locked memory: the value, then
+// (after a system-scope fence) a sequence number the host waits for
+struct HostValue {
+    double v;
+    int32_t seq;
+    int32_t pad;
+};
+
 struct ReadBack {
     double est;      // |s_{j+1}| / ||b||
     double hnext;    // h_{j+1,j} before rotation
@@ -398,7 +406,8 @@ cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s);
 template <typename T>
 cudaError_t launch_multidot(const T *V, size_t ld, int k, const T *w, size_t n, double *partial,
                             int nchunk, cudaStream_t s);
-cudaError_t launch_reduce_partials(const double *partial, int k, int nchunk, double *out, cudaStream_t s);
+cudaError_t launch_reduce_partials(const double *partial, int k, int nchunk, double *out, cudaStream_t s,
+                                   HostValue *pub = nullptr, int32_t seq = 0);
 template <typename T>
 cudaError_t launch_multi_axpy(T *w, const T *V, size_t ld, int k, const double *coef, double sign,
                               size_t n, cudaStream_t s);

@@ -41,12 +41,22 @@ __global__ void __launch_bounds__(256) multidot_kernel(const T *__restrict__ V, 
     if (threadIdx.x == 0) partial[size_t(i) * nchunk + c] = tot;
 }
 
-__global__ void reduce_partials_kernel(const double *__restrict__ partial, int nchunk, double *__restrict__ out) {
+// out[i] = sum of the partials of vector i; with pub, block 0 also hands its
+// sum to the host (page-locked HostValue: the value, a system fence, seq)
+__global__ void reduce_partials_kernel(const double *__restrict__ partial, int nchunk, double *__restrict__ out,
+                                       HostValue *pub, int32_t seq) {
     const int i = blockIdx.x;
     double acc = 0.0;
     for (int c = threadIdx.x; c < nchunk; c += blockDim.x) acc += partial[size_t(i) * nchunk + c];
     acc = block_sum(acc);
-    if (threadIdx.x == 0) out[i] = acc;
+    if (threadIdx.x == 0) {
+        out[i] = acc;
+        if (pub && i == 0) {
+            pub->v = acc;
+            __threadfence_system();
+            *reinterpret_cast<volatile int32_t *>(&pub->seq) = seq;
+        }
+    }
 }
 
 // w += sign * sum_i coef[i] V_i
@@ -411,8 +421,9 @@ cudaError_t launch_multidot(const T *V, size_t ld, int k, const T *w, size_t n, 
     multidot_kernel<T><<<grid, 256, 0, s>>>(V, ld, w, n, partial, nchunk);
     return cudaGetLastError();
 }
-cudaError_t launch_reduce_partials(const double *partial, int k, int nchunk, double *out, cudaStream_t s) {
-    reduce_partials_kernel<<<k, 256, 0, s>>>(partial, nchunk, out);
+cudaError_t launch_reduce_partials(const double *partial, int k, int nchunk, double *out, cudaStream_t s,
+                                   HostValue *pub, int32_t seq) {
+    reduce_partials_kernel<<<k, 256, 0, s>>>(partial, nchunk, out, pub, seq);
     return cudaGetLastError();
 }
 template <typename T>
