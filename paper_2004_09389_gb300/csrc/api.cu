@@ -269,7 +269,7 @@ namespace {
 
 template <typename T>
 cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out, HostValue *pub = nullptr,
-                 int32_t seq = 0);
+                 int32_t seq = 0, double *root_a = nullptr, double *root_b = nullptr);
 
 // P1 V-cycle for the coarse problem (Eq. coarse_problem_upwind) with
 // right-hand side levB(level 0).  Levels above the tail: fused kernels (the
@@ -447,11 +447,13 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr) {
 // ---------------------------------------------------------------- Krylov helpers
 
 template <typename T>
-cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out, HostValue *pub, int32_t seq) {
+cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out, HostValue *pub, int32_t seq,
+                 double *root_a, double *root_b) {
     Workspace &W = *h->ws;
     cudaError_t e = KL(HDG_PROF_KRYLOV, 1, launch_multidot<T>(V, W.NT, k, w, W.NT, W.partial, W.nchunk, h->stream));
     if (e != cudaSuccess) return e;
-    return KL(HDG_PROF_KRYLOV, 1, launch_reduce_partials(W.partial, k, W.nchunk, out, h->stream, pub, seq));
+    return KL(HDG_PROF_KRYLOV, 1, launch_reduce_partials(W.partial, k, W.nchunk, out, h->stream, pub, seq, root_a,
+                                                         root_b));
 }
 
 // Wait until the page-locked HostValue carries sequence number want: spin,
@@ -605,7 +607,7 @@ int run_arnoldi_step(hdg_handle *h, int j) {
 // Returns the number of iterations; x is updated.
 template <typename T>
 int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_target, int max_it, int &its_done,
-                 double &est_out, int &flag_out) {
+                 double &est_out, int &flag_out, bool beta_on_device = false) {
     Workspace &W = *h->ws;
     KSpace<T> &k = kspace<T>(h);
     cudaStream_t s = h->stream;
@@ -617,8 +619,13 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
     // s = [beta, 0, ...]
     TRY(cudaMemsetAsync(W.sv, 0, sizeof(double) * (m + 1), s));
     TRY(cudaMemsetAsync(W.Hm, 0, sizeof(double) * (m + 1) * m, s));
-    W.host_buf[3] = beta;
-    TRY(cudaMemcpyAsync(W.sv, W.host_buf + 3, sizeof(double), cudaMemcpyHostToDevice, s));
+    if (beta_on_device) {
+        // s_0 = ||b|| as the norm kernel left it in W.bnorm (first cycle, zero guess)
+        TRY(cudaMemcpyAsync(W.sv, W.bnorm, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+        W.host_buf[3] = beta;
+        TRY(cudaMemcpyAsync(W.sv, W.host_buf + 3, sizeof(double), cudaMemcpyHostToDevice, s));
+    }
     int j = 0;
     double hist[72];
     for (; j < m && j < max_it; ++j) {
@@ -657,29 +664,40 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
 // Full FGMRES(m) on S x = b in precision T; stops on the true residual (FP64
 // mode) or on the Arnoldi estimate (inner FP32 solves).  x must hold the
 // initial guess; with x_zero (x = 0 on entry) the first residual is b itself
-// and its norm is ||b||, so neither is recomputed.
+// and its norm is ||b||, so neither is recomputed.  unit_rhs (with x_zero):
+// b = r / ||r|| by construction, finite with norm 1 up to rounding; its
+// exact norm goes from the reduction kernel straight into the device scalars
+// that use it (the estimate's denominator, the first basis vector's scale and
+// s_0), and the host keeps the nominal 1 for its bookkeeping, so the solve
+// starts without waiting for the GPU.
 template <typename T>
 int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_residual, bool x_zero,
-           hdg_solve_info &info) {
+           hdg_solve_info &info, bool unit_rhs = false) {
     Workspace &W = *h->ws;
     KSpace<T> &k = kspace<T>(h);
     cudaStream_t s = h->stream;
-    double bnorm;
-    int rc = norm_host<T>(h, b, bnorm);
-    if (rc) return rc;
+    double bnorm = 1.0;
+    int rc = HDG_OK;
+    unit_rhs = unit_rhs && x_zero;
     info.iters = 0;
     info.outer = 0;
     info.est_rel_res = 0;
     info.true_rel_res = 0;
-    if (!std::isfinite(bnorm)) return fail(h, HDG_ENAN, "NaN or Inf in the right-hand side");
-    if (bnorm == 0.0) {
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<T>(x, T(0), W.NT, s)));
-        return HDG_OK;
+    if (unit_rhs) {
+        TRY(dots<T>(h, b, 1, b, W.nrm2, nullptr, 0, W.bnorm, W.scal));
+    } else {
+        rc = norm_host<T>(h, b, bnorm);
+        if (rc) return rc;
+        if (!std::isfinite(bnorm)) return fail(h, HDG_ENAN, "NaN or Inf in the right-hand side");
+        if (bnorm == 0.0) {
+            TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<T>(x, T(0), W.NT, s)));
+            return HDG_OK;
+        }
+        // host_buf[4] is written again only after the next norm, whose hand-over
+        // follows this copy in the stream
+        W.host_buf[4] = bnorm;
+        TRY(cudaMemcpyAsync(W.bnorm, W.host_buf + 4, sizeof(double), cudaMemcpyHostToDevice, s));
     }
-    // host_buf[4] is written again only after the next norm, whose hand-over
-    // follows this copy in the stream
-    W.host_buf[4] = bnorm;
-    TRY(cudaMemcpyAsync(W.bnorm, W.host_buf + 4, sizeof(double), cudaMemcpyHostToDevice, s));
     int total = 0;
     for (bool first = true;; first = false) {
         // r = b - S x into V[0] (r = b for a zero initial guess)
@@ -697,12 +715,15 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
         if (!std::isfinite(rel)) return fail(h, HDG_ENAN, "NaN or Inf in the Krylov iteration");
         if (rel <= rtol) return HDG_OK;
         if (total >= max_it) return fail(h, HDG_ENOCONV, "maximum number of iterations reached");
-        W.host_buf[1] = beta;
-        TRY(cudaMemcpyAsync(W.scal, W.host_buf + 1, sizeof(double), cudaMemcpyHostToDevice, s));
+        const bool beta_dev = first && unit_rhs;     // W.scal and W.bnorm already hold ||b||
+        if (!beta_dev) {
+            W.host_buf[1] = beta;
+            TRY(cudaMemcpyAsync(W.scal, W.host_buf + 1, sizeof(double), cudaMemcpyHostToDevice, s));
+        }
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_scale_copy<T>(r0, k.V, W.scal, W.NT, s)));
         int done, flag;
         double est;
-        rc = fgmres_cycle<T>(h, x, beta, bnorm, rtol, max_it - total, done, est, flag);
+        rc = fgmres_cycle<T>(h, x, beta, bnorm, rtol, max_it - total, done, est, flag, beta_dev);
         if (rc) return rc;
         total += done;
         info.iters = total;
@@ -765,7 +786,7 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info)
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<float>(k.x, 0.0f, W.NT, s)));
         hdg_solve_info inner{};
         const double inner_tol = std::max(h->prm.inner_rtol, 0.5 * h->prm.rtol * bnorm / beta);
-        rc = fgmres<float>(h, k.b, k.x, inner_tol, h->prm.max_iter - total, false, true, inner);
+        rc = fgmres<float>(h, k.b, k.x, inner_tol, h->prm.max_iter - total, false, true, inner, true);
         if (rc && rc != HDG_ENOCONV) return rc;
         total += inner.iters;
         info.iters = total;

@@ -407,7 +407,8 @@ template <typename T>
 cudaError_t launch_multidot(const T *V, size_t ld, int k, const T *w, size_t n, double *partial,
                             int nchunk, cudaStream_t s);
 cudaError_t launch_reduce_partials(const double *partial, int k, int nchunk, double *out, cudaStream_t s,
-                                   HostValue *pub = nullptr, int32_t seq = 0);
+                                   HostValue *pub = nullptr, int32_t seq = 0, double *root_a = nullptr,
+                                   double *root_b = nullptr);
 template <typename T>
 cudaError_t launch_multi_axpy(T *w, const T *V, size_t ld, int k, const double *coef, double sign,
                               size_t n, cudaStream_t s);

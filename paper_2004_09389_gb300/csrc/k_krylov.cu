@@ -42,15 +42,21 @@ __global__ void __launch_bounds__(256) multidot_kernel(const T *__restrict__ V, 
 }
 
 // out[i] = sum of the partials of vector i; with pub, block 0 also hands its
-// sum to the host (page-locked HostValue: the value, a system fence, seq)
+// sum to the host (page-locked HostValue: the value, a system fence, seq);
+// root_a / root_b (may be null) receive the square root of block 0's sum
 __global__ void reduce_partials_kernel(const double *__restrict__ partial, int nchunk, double *__restrict__ out,
-                                       HostValue *pub, int32_t seq) {
+                                       HostValue *pub, int32_t seq, double *root_a, double *root_b) {
     const int i = blockIdx.x;
     double acc = 0.0;
     for (int c = threadIdx.x; c < nchunk; c += blockDim.x) acc += partial[size_t(i) * nchunk + c];
     acc = block_sum(acc);
     if (threadIdx.x == 0) {
         out[i] = acc;
+        if (i == 0 && (root_a || root_b)) {
+            const double r = sqrt(acc);
+            if (root_a) *root_a = r;
+            if (root_b) *root_b = r;
+        }
         if (pub && i == 0) {
             pub->v = acc;
             __threadfence_system();
@@ -422,8 +428,8 @@ cudaError_t launch_multidot(const T *V, size_t ld, int k, const T *w, size_t n, 
     return cudaGetLastError();
 }
 cudaError_t launch_reduce_partials(const double *partial, int k, int nchunk, double *out, cudaStream_t s,
-                                   HostValue *pub, int32_t seq) {
-    reduce_partials_kernel<<<k, 256, 0, s>>>(partial, nchunk, out, pub, seq);
+                                   HostValue *pub, int32_t seq, double *root_a, double *root_b) {
+    reduce_partials_kernel<<<k, 256, 0, s>>>(partial, nchunk, out, pub, seq, root_a, root_b);
     return cudaGetLastError();
 }
 template <typename T>
