@@ -1005,9 +1005,10 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
         TRY(dalloc(&h->d_Sval32, packed(5 * pp * pp, 4)));
         TRY(dalloc(&h->d_Dinv32, packed(pp * pp, 4)));
         if (mode_ff(*prm)) {
-            TRY(dalloc(&h->d_Xb2, nK * m * N));
-            TRY(dalloc(&h->d_Rm2, nK * nK * N));
-            TRY(dalloc(&h->d_W2, m * nK * N));
+            // pairs of row entries (odd rows padded by one zero entry)
+            TRY(dalloc(&h->d_Xb2, nK * ((m + 1) / 2 * 2) * N));
+            TRY(dalloc(&h->d_Rm2, nK * ((nK + 1) / 2 * 2) * N));
+            TRY(dalloc(&h->d_W2, m * ((nK + 1) / 2 * 2) * N));
             TRY(dalloc(&h->d_Sval2, packed(5 * pp * pp, 2)));
         }
         if (prm->precision == HDG_MIXED_BF16) TRY(dalloc(&h->d_Sval16, packed(5 * pp * pp, 8)));
@@ -1329,9 +1330,9 @@ int hdg_condense(hdg_handle *h) {
         if (mode_ff(h->prm)) {
             // (hi, lo) float pairs for the two-float FP64 steps
             const size_t N = h->N, nK = h->nK, m = h->m, pp = h->pp, NS = 5 * pp * pp;
-            TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Xb, h->d_Xb2, nK * m * N, s)));
-            TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Rm, h->d_Rm2, nK * nK * N, s)));
-            TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_W, h->d_W2, m * nK * N, s)));
+            TRY(KL(HDG_PROF_CONDENSE, 1, launch_split_pairs(h->d_Xb, h->d_Xb2, int(nK), int(m), N, s)));
+            TRY(KL(HDG_PROF_CONDENSE, 1, launch_split_pairs(h->d_Rm, h->d_Rm2, int(nK), int(nK), N, s)));
+            TRY(KL(HDG_PROF_CONDENSE, 1, launch_split_pairs(h->d_W, h->d_W2, int(m), int(nK), N, s)));
             TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Sval, h->d_Sval2, (NS + 1) / 2 * 2 * size_t(h->NF), s)));
         }
     }

@@ -23,6 +23,14 @@ namespace {
 
 inline unsigned blocks(size_t n, int bs) { return unsigned((n + bs - 1) / bs); }
 
+// The cell kernels take 32 consecutive cells per block (lane = cell): the
+// cells' right-hand sides r_K = (r_u, r_h) are read as contiguous chunks,
+// split once into shared memory and shared by the warps, which take the output
+// rows in turn; per-cell matrices, split into pairs of row entries
+// ([row][col pair][N], split_pairs_kernel), load coalesced, 16 bytes per lane.
+constexpr int kCells = 32;
+constexpr int kCellsPad = kCells + 1;
+
 __device__ __forceinline__ float2 split(double a) {
     const float hi = __double2float_rn(a);
     return make_float2(hi, __double2float_rn(a - double(hi)));
@@ -49,6 +57,40 @@ struct FFAcc {
 __global__ void split_kernel(const double *__restrict__ a, float2 *__restrict__ out, size_t n) {
     const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i < n) out[i] = split(a[i]);
+}
+
+// A per-cell matrix a[(row * cols + col) * N + K] split into pairs of
+// consecutive row entries: out[(row * CP + cp) * N + K] = (pair of col 2cp,
+// pair of col 2cp + 1, or zeros past the row's end), CP = (cols + 1) / 2, so
+// that one 16-byte load per lane brings two entries of a row
+__global__ void split_pairs_kernel(const double *__restrict__ a, float4 *__restrict__ out, int rows, int cols,
+                                   size_t N) {
+    const int CP = (cols + 1) / 2;
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= size_t(rows) * CP * N) return;
+    const size_t K = i % N, pc = i / N;
+    const int row = int(pc / CP), c0 = 2 * int(pc % CP);
+    const float2 lo = split(a[(size_t(row) * cols + c0) * N + K]);
+    const float2 hi = c0 + 1 < cols ? split(a[(size_t(row) * cols + c0 + 1) * N + K]) : make_float2(0.f, 0.f);
+    out[i] = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// acc += sum over the n entries of one row (pairs p[cp * N], cp < (n + 1) / 2)
+// times x[col][lane], in column order
+template <int NCOL>
+__device__ __forceinline__ void row_pairs(FFAcc &acc, const float4 *__restrict__ p, size_t N,
+                                          const float2 (*x)[kCellsPad], int lane, bool negate = false) {
+    constexpr int CP = (NCOL + 1) / 2;
+#pragma unroll 3
+    for (int cp = 0; cp < CP; ++cp) {
+        const float4 v = __ldg(p + size_t(cp) * N);
+        const float2 a0 = negate ? make_float2(-v.x, -v.y) : make_float2(v.x, v.y);
+        acc.add(a0, x[2 * cp][lane]);
+        if (2 * cp + 1 < NCOL) {
+            const float2 a1 = negate ? make_float2(-v.z, -v.w) : make_float2(v.z, v.w);
+            acc.add(a1, x[2 * cp + 1][lane]);
+        }
+    }
 }
 
 // x += scale * d (refinement correction, FP32 -> FP64) and its split copy
@@ -97,17 +139,11 @@ __global__ void __launch_bounds__(256) residual_ff_kernel(int NF, const float4 *
     for (int r = 0; r < PP; ++r) res[size_t(r) * NF + e] = b[size_t(r) * NF + e] - acc[r].value();
 }
 
-// The cell kernels take 32 consecutive cells per block (lane = cell): the
-// cells' right-hand sides r_K = (r_u, r_h) are read as contiguous chunks,
-// split once into shared memory and shared by the warps, which take the output
-// rows in turn; per-cell matrices [row*ncol + col][N] load coalesced.
-constexpr int kCells = 32;
-
 // (r_u, r_h may live in page-locked host memory read over the C2C link; with
 // cu, ch non-null each value read is also stored there, in HBM)
 template <int NP>
 __device__ __forceinline__ void stage_cell_rhs(int N, int K0, const double *__restrict__ r_u,
-                                               const double *__restrict__ r_h, float2 (*sIn)[kCells + 1],
+                                               const double *__restrict__ r_h, float2 (*sIn)[kCellsPad],
                                                double *__restrict__ cu = nullptr, double *__restrict__ ch = nullptr) {
     const int nc = min(kCells, N - K0);
     for (int j = threadIdx.x; j < nc * 2 * NP; j += blockDim.x) {
@@ -126,12 +162,13 @@ __device__ __forceinline__ void stage_cell_rhs(int N, int K0, const double *__re
 
 // step 1, cell part: ycell[t][K] = sum_kappa W[t*NK + kappa][K] r_K[kappa]
 template <int P>
-__global__ void __launch_bounds__(128) rhs_cell_ff_kernel(int N, const float2 *__restrict__ W2,
+__global__ void __launch_bounds__(128, 8) rhs_cell_ff_kernel(int N, const float4 *__restrict__ W2,
                                                           const double *__restrict__ r_u,
                                                           const double *__restrict__ r_h, double *__restrict__ ycell,
                                                           double *__restrict__ cu, double *__restrict__ ch) {
     constexpr int PP = P + 1, NP = (P + 1) * (P + 2) / 2, NK = 3 * NP, M = 3 * PP, NW = 4;
-    __shared__ float2 sIn[NK][kCells + 1];
+    constexpr int KP = (NK + 1) / 2;
+    __shared__ float2 sIn[NK][kCellsPad];
     const int K0 = blockIdx.x * kCells, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     stage_cell_rhs<NP>(N, K0, r_u, r_h, sIn, cu, ch);
     __syncthreads();
@@ -139,23 +176,23 @@ __global__ void __launch_bounds__(128) rhs_cell_ff_kernel(int N, const float2 *_
     if (K >= N) return;
     for (int t = w; t < M; t += NW) {
         FFAcc acc;
-#pragma unroll 6
-        for (int kap = 0; kap < NK; ++kap) acc.add(__ldg(W2 + size_t(t * NK + kap) * N + K), sIn[kap][lane]);
+        row_pairs<NK>(acc, W2 + size_t(t) * KP * N + K, N, sIn, lane);
         ycell[size_t(t) * N + K] = acc.value();
     }
 }
 
 // step 3: q_K = R_M r_K - X_B lambda_K, written in the caller's u / h layout
 template <int P>
-__global__ void __launch_bounds__(256) recover_ff_kernel(int N, int NF, const float2 *__restrict__ Rm2,
-                                                         const float2 *__restrict__ Xb2, const double *__restrict__ r_u,
+__global__ void __launch_bounds__(256) recover_ff_kernel(int N, int NF, const float4 *__restrict__ Rm2,
+                                                         const float4 *__restrict__ Xb2, const double *__restrict__ r_u,
                                                          const double *__restrict__ r_h, const double *__restrict__ lam,
                                                          const int32_t *__restrict__ facet_of,
                                                          const int32_t *__restrict__ flip, double *__restrict__ u,
                                                          double *__restrict__ hout) {
     constexpr int PP = P + 1, NP = (P + 1) * (P + 2) / 2, NK = 3 * NP, M = 3 * PP, NW = 8;
-    __shared__ float2 sIn[NK + M][kCells + 1];   // r_K, then lambda on the cell's three facets
-    __shared__ double sOut[NK][kCells + 1];
+    constexpr int KP = (NK + 1) / 2, MP = (M + 1) / 2;
+    __shared__ float2 sIn[NK + M][kCellsPad];   // r_K, then lambda on the cell's three facets
+    __shared__ double sOut[NK][kCellsPad];
     const int K0 = blockIdx.x * kCells, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nc = min(kCells, N - K0);
     stage_cell_rhs<NP>(N, K0, r_u, r_h, sIn);
@@ -169,13 +206,8 @@ __global__ void __launch_bounds__(256) recover_ff_kernel(int N, int NF, const fl
     if (K < N) {
         for (int rho = w; rho < NK; rho += NW) {
             FFAcc acc;
-#pragma unroll 6
-            for (int kap = 0; kap < NK; ++kap) acc.add(__ldg(Rm2 + size_t(rho * NK + kap) * N + K), sIn[kap][lane]);
-#pragma unroll
-            for (int q = 0; q < M; ++q) {
-                const float2 a = __ldg(Xb2 + size_t(rho * M + q) * N + K);
-                acc.add(make_float2(-a.x, -a.y), sIn[NK + q][lane]);
-            }
+            row_pairs<NK>(acc, Rm2 + size_t(rho) * KP * N + K, N, sIn, lane);
+            row_pairs<M>(acc, Xb2 + size_t(rho) * MP * N + K, N, sIn + NK, lane, true);
             sOut[rho][lane] = acc.value();
         }
     }
@@ -193,6 +225,13 @@ cudaError_t launch_split(const double *a, float2 *out, size_t n, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_split_pairs(const double *a, float2 *out, int rows, int cols, size_t N, cudaStream_t s) {
+    const size_t n = size_t(rows) * ((cols + 1) / 2) * N;
+    if (n == 0) return cudaSuccess;
+    split_pairs_kernel<<<blocks(n, 256), 256, 0, s>>>(a, reinterpret_cast<float4 *>(out), rows, cols, N);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_axpby_split(double *x, float2 *x2, const float *d, const double *scale, size_t n, cudaStream_t s) {
     axpby_split_kernel<<<blocks(n, 256), 256, 0, s>>>(x, x2, d, scale, n);
     return cudaGetLastError();
@@ -206,7 +245,7 @@ cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2,
 
 cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell,
                           double *copy_u, double *copy_h) {
-    HDG_DISPATCH_P(h->p, (rhs_cell_ff_kernel<P><<<blocks(h->N, kCells), 128, 0, h->stream>>>(h->N, h->d_W2, r_u, r_h,
+    HDG_DISPATCH_P(h->p, (rhs_cell_ff_kernel<P><<<blocks(h->N, kCells), 128, 0, h->stream>>>(h->N, reinterpret_cast<const float4 *>(h->d_W2), r_u, r_h,
                                                                                                ycell, copy_u, copy_h)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -216,7 +255,9 @@ cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, d
 cudaError_t launch_recover_ff(hdg_handle *h, const double *r_u, const double *r_h, const double *lam, double *u,
                               double *hout) {
     HDG_DISPATCH_P(h->p, (recover_ff_kernel<P><<<blocks(h->N, kCells), 256, 0, h->stream>>>(
-                             h->N, h->NF, h->d_Rm2, h->d_Xb2, r_u, r_h, lam, h->d_facet_of, h->d_flip, u, hout)));
+                             h->N, h->NF, reinterpret_cast<const float4 *>(h->d_Rm2),
+                             reinterpret_cast<const float4 *>(h->d_Xb2), r_u, r_h, lam, h->d_facet_of, h->d_flip, u,
+                             hout)));
     return cudaGetLastError();
 }
 
