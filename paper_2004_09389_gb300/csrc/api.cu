@@ -1005,10 +1005,11 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
         TRY(dalloc(&h->d_Sval32, packed(5 * pp * pp, 4)));
         TRY(dalloc(&h->d_Dinv32, packed(pp * pp, 4)));
         if (mode_ff(*prm)) {
-            // pairs of row entries (odd rows padded by one zero entry)
-            TRY(dalloc(&h->d_Xb2, nK * ((m + 1) / 2 * 2) * N));
-            TRY(dalloc(&h->d_Rm2, nK * ((nK + 1) / 2 * 2) * N));
-            TRY(dalloc(&h->d_W2, m * ((nK + 1) / 2 * 2) * N));
+            // pairs of row entries (odd rows padded by one zero entry), tiles of 32 cells
+            const size_t Nt = (N + 31) / 32 * 32;
+            TRY(dalloc(&h->d_Xb2, nK * ((m + 1) / 2 * 2) * Nt));
+            TRY(dalloc(&h->d_Rm2, nK * ((nK + 1) / 2 * 2) * Nt));
+            TRY(dalloc(&h->d_W2, m * ((nK + 1) / 2 * 2) * Nt));
             TRY(dalloc(&h->d_Sval2, packed(5 * pp * pp, 2)));
         }
         if (prm->precision == HDG_MIXED_BF16) TRY(dalloc(&h->d_Sval16, packed(5 * pp * pp, 8)));

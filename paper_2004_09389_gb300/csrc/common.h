@@ -359,7 +359,8 @@ cudaError_t launch_rhs(hdg_handle *h, const double *r_u, const double *r_h, doub
 cudaError_t launch_rhs_gather(hdg_handle *h, const double *ycell, double *g);
 // two-float versions of the FP64 steps (mixed modes, k_ff.cu)
 cudaError_t launch_split(const double *a, float2 *out, size_t n, cudaStream_t s);
-// a per-cell matrix [rows][cols][N] split into pairs of row entries [rows][(cols+1)/2][N] (float4)
+// a per-cell matrix [rows][cols][N] split into pairs of row entries, tiled by 32 cells:
+// [ceil(N/32)][rows][(cols+1)/2][32] (float4)
 cudaError_t launch_split_pairs(const double *a, float2 *out, int rows, int cols, size_t N, cudaStream_t s);
 cudaError_t launch_axpby_split(double *x, float2 *x2, const float *d, const double *scale, size_t n, cudaStream_t s);
 cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2, double *res);

@@ -60,30 +60,34 @@ __global__ void split_kernel(const double *__restrict__ a, float2 *__restrict__ 
 }
 
 // A per-cell matrix a[(row * cols + col) * N + K] split into pairs of
-// consecutive row entries: out[(row * CP + cp) * N + K] = (pair of col 2cp,
-// pair of col 2cp + 1, or zeros past the row's end), CP = (cols + 1) / 2, so
-// that one 16-byte load per lane brings two entries of a row
+// consecutive row entries, in tiles of kCells cells: the pair (col 2cp, col
+// 2cp + 1, or zeros past the row's end) of plane pc = row * CP + cp, CP =
+// (cols + 1) / 2, for cell K sits at out[((K / kCells) * rows * CP + pc) *
+// kCells + K % kCells].  One 16-byte load per lane brings two entries of a row,
+// a warp's loads are coalesced, and a block of kCells cells streams one
+// contiguous tile.
 __global__ void split_pairs_kernel(const double *__restrict__ a, float4 *__restrict__ out, int rows, int cols,
                                    size_t N) {
     const int CP = (cols + 1) / 2;
+    const size_t np = size_t(rows) * CP;
     const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= size_t(rows) * CP * N) return;
+    if (i >= np * N) return;
     const size_t K = i % N, pc = i / N;
     const int row = int(pc / CP), c0 = 2 * int(pc % CP);
     const float2 lo = split(a[(size_t(row) * cols + c0) * N + K]);
     const float2 hi = c0 + 1 < cols ? split(a[(size_t(row) * cols + c0 + 1) * N + K]) : make_float2(0.f, 0.f);
-    out[i] = make_float4(lo.x, lo.y, hi.x, hi.y);
+    out[((K / kCells) * np + pc) * kCells + K % kCells] = make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
-// acc += sum over the n entries of one row (pairs p[cp * N], cp < (n + 1) / 2)
-// times x[col][lane], in column order
+// acc += sum over the NCOL entries of one row (pairs p[cp * kCells], cp <
+// (NCOL + 1) / 2, within the cell's tile) times x[col][lane], in column order
 template <int NCOL>
-__device__ __forceinline__ void row_pairs(FFAcc &acc, const float4 *__restrict__ p, size_t N,
-                                          const float2 (*x)[kCellsPad], int lane, bool negate = false) {
+__device__ __forceinline__ void row_pairs(FFAcc &acc, const float4 *__restrict__ p, const float2 (*x)[kCellsPad],
+                                          int lane, bool negate = false) {
     constexpr int CP = (NCOL + 1) / 2;
 #pragma unroll 3
     for (int cp = 0; cp < CP; ++cp) {
-        const float4 v = __ldg(p + size_t(cp) * N);
+        const float4 v = __ldg(p + size_t(cp) * kCells);
         const float2 a0 = negate ? make_float2(-v.x, -v.y) : make_float2(v.x, v.y);
         acc.add(a0, x[2 * cp][lane]);
         if (2 * cp + 1 < NCOL) {
@@ -176,7 +180,7 @@ __global__ void __launch_bounds__(128, 8) rhs_cell_ff_kernel(int N, const float4
     if (K >= N) return;
     for (int t = w; t < M; t += NW) {
         FFAcc acc;
-        row_pairs<NK>(acc, W2 + size_t(t) * KP * N + K, N, sIn, lane);
+        row_pairs<NK>(acc, W2 + (size_t(blockIdx.x) * M * KP + size_t(t) * KP) * kCells + lane, sIn, lane);
         ycell[size_t(t) * N + K] = acc.value();
     }
 }
@@ -206,8 +210,9 @@ __global__ void __launch_bounds__(256) recover_ff_kernel(int N, int NF, const fl
     if (K < N) {
         for (int rho = w; rho < NK; rho += NW) {
             FFAcc acc;
-            row_pairs<NK>(acc, Rm2 + size_t(rho) * KP * N + K, N, sIn, lane);
-            row_pairs<M>(acc, Xb2 + size_t(rho) * MP * N + K, N, sIn + NK, lane, true);
+            row_pairs<NK>(acc, Rm2 + (size_t(blockIdx.x) * NK * KP + size_t(rho) * KP) * kCells + lane, sIn, lane);
+            row_pairs<M>(acc, Xb2 + (size_t(blockIdx.x) * NK * MP + size_t(rho) * MP) * kCells + lane, sIn + NK,
+                         lane, true);
             sOut[rho][lane] = acc.value();
         }
     }
