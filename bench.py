@@ -128,12 +128,20 @@ class ClockSampler:
     region; wait_ready() holds until it has run for 1.5 s.  Each sample carries
     nvidia-smi's own timestamp; stop(t0, t1) keeps those inside the timed window."""
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, path: str = ""):
         self.proc = None
+        self.fh = None
         self.t_start = time.time()
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to path when given (--clocks-csv), else to a temporary file
+        self.tmp = not path
+        if self.tmp:
+            import tempfile
+            fd, path = tempfile.mkstemp(prefix=f"clocks_{os.getpid()}_", suffix=".csv")
+            os.close(fd)
+        self.path = path
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            if os.path.dirname(self.path):
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={CLOCK_QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
@@ -147,6 +155,10 @@ class ClockSampler:
 
     def stop(self, t0: float = None, t1: float = None) -> dict:
         if self.proc is None:
+            if getattr(self, "fh", None) is not None:
+                self.fh.close()
+            if self.tmp and os.path.exists(self.path):
+                os.remove(self.path)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:
@@ -157,7 +169,11 @@ class ClockSampler:
         import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         rows = []
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        if self.tmp:
+            os.remove(self.path)
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 10:
                 continue
@@ -297,7 +313,7 @@ def gpu_arm(args, rank: int, world: int):
             infos.append(s.solve_dev(ru_d, rh_d, lam_d))
             s.recover_dev(ru_d, rh_d, lam_d, u_d, h_d)
 
-        clocks = ClockSampler(dev.index) if arm == "mixed" else None
+        clocks = ClockSampler(dev.index, args.clocks_csv) if arm == "mixed" else None
         for _ in range(args.warmup):
             step()
         infos.clear()
@@ -672,6 +688,8 @@ def main():
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--batch", type=int, default=0, help="run the batched-solve benchmark with this many problems")
     ap.add_argument("--autotune", action="store_true", help="autotune launch shapes per handle (off by default: on the 256x256x2 workload the defaults measured faster)")
+    ap.add_argument("--clocks-csv", dest="clocks_csv", default="",
+                    help="keep the raw nvidia-smi clock samples of the timed region in this CSV file")
     ap.add_argument("--profile-solve", dest="profile_solve", default="",
                     choices=["", "mixed", "mixed_bf16", "fgmres64", "fp64"],
                     help="warm up, then run one solve and recovery of this arm between profiler start and stop "
