@@ -378,13 +378,7 @@ template <typename T>
 cudaError_t launch_p1_jacobi(const DevLevel &L, const T *A, const T *dinv, const T *b, const T *x,
                              T *xout, T omega, bool first, cudaStream_t s);
 template <typename T>
-cudaError_t launch_p1_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, cudaStream_t s);
-template <typename T>
-cudaError_t launch_p1_restrict(const DevLevel &coarse, const T *rf, T *bc, cudaStream_t s);
-template <typename T>
 cudaError_t launch_p1_prolong_add(const DevLevel &coarse, int nv_fine, const T *ec, T *xf, cudaStream_t s);
-template <typename T>
-cudaError_t launch_dense_apply(const T *inv, int n, const T *b, T *x, cudaStream_t s);
 template <typename T>
 cudaError_t launch_p1_down(const DevLevel &fine, const DevLevel &coarse, const T *A_f, const T *b_f, const T *x_f,
                            const T *dinv_c, T omega, T *b_c, T *x_c, cudaStream_t s);
@@ -417,10 +411,6 @@ cudaError_t launch_multi_axpy(T *w, const T *V, size_t ld, int k, const double *
                               size_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_scale_copy(const T *w, T *v, const double *denom, size_t n, cudaStream_t s);
-cudaError_t launch_arnoldi_finish(double *Hcol, const double *h1, const double *h2, const double *nrm2,
-                                  int j, cudaStream_t s);
-cudaError_t launch_givens(double *Hm, int ldh, double *cs, double *sn, double *sv, int j, const double *bnorm,
-                          double *est, int32_t *flags, cudaStream_t s);
 cudaError_t launch_hessenberg_solve(const double *Hm, int ldh, const double *sv, int k, double *y,
                                     cudaStream_t s);
 template <typename T>
@@ -442,7 +432,6 @@ cudaError_t launch_adam(hdg_handle *h, float lr, int t);
 cudaError_t launch_normalize32(const float *src, float *dst, const double *nrm2, size_t n, cudaStream_t s);
 cudaError_t launch_to_internal32(hdg_handle *h, const float *ext, float *in);
 cudaError_t launch_to_external32(hdg_handle *h, const float *in, float *ext);
-cudaError_t launch_axpby_mixed(double *x, const float *d, const double *scale, size_t n, cudaStream_t s);
 cudaError_t launch_scale_round(const double *w, const double *hnext, double *v64, float *v32, size_t n,
                                cudaStream_t s);
 cudaError_t launch_widen(const float *a, double *b, size_t n, cudaStream_t s);

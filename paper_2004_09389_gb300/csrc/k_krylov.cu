@@ -124,48 +124,24 @@ __global__ void scale_copy_kernel(const T *__restrict__ w, T *__restrict__ v, co
     v[idx] = w[idx] * T(inv);
 }
 
-// Hessenberg column j from the two Gram-Schmidt passes; h[j+1] = ||w||
-__global__ void arnoldi_finish_kernel(double *Hcol, const double *h1, const double *h2, const double *nrm2, int j) {
-    for (int i = 0; i <= j; ++i) Hcol[i] = h1[i] + h2[i];
-    Hcol[j + 1] = sqrt(nrm2[0]);
-}
-
-// Apply the previous rotations to column j, form rotation j, update the RHS of
-// the least-squares problem; est = |s_{j+1}| / ||b||.  flags: 2 = breakdown,
-// 4 = NaN/Inf.
-__global__ void givens_kernel(double *Hm, int ldh, double *cs, double *sn, double *sv, int j, const double *bnorm_p,
-                              double *est, int32_t *flags) {
-    const double bnorm = bnorm_p[0];
-    double *col = Hm + size_t(j) * ldh;
-    for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-        col[i] = t;
-    }
-    const double a = col[j], b = col[j + 1];
-    const double den = hypot(a, b);
-    int32_t fl = 0;
-    if (!(den > 0.0)) {
-        cs[j] = 1.0; sn[j] = 0.0;
-        fl |= 2;
-    } else {
-        cs[j] = a / den; sn[j] = b / den;
-    }
-    if (!(fabs(b) > 1e-300 * (fabs(a) + 1e-300))) fl |= 2;
-    col[j] = (den > 0.0) ? den : a;
-    col[j + 1] = 0.0;
-    sv[j + 1] = -sn[j] * sv[j];
-    sv[j] = cs[j] * sv[j];
-    est[0] = fabs(sv[j + 1]) / bnorm;
-    if (!isfinite(est[0]) || !isfinite(den)) fl |= 4;
-    flags[0] = fl;
-}
-
+// y = R^-1 s for the leading k x k upper triangle R of the rotated Hessenberg
+// matrix (column-major, leading dimension ldh): the triangle and s are first
+// loaded into shared memory by the whole block, then one thread substitutes
+// backwards (k <= 64)
 __global__ void hessenberg_solve_kernel(const double *Hm, int ldh, const double *sv, int k, double *y) {
+    __shared__ double R[64][65], sS[64], yS[64];
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+        const int l = t / k, i = t % k;            // column l, row i
+        if (i <= l) R[i][l] = Hm[size_t(l) * ldh + i];
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) sS[i] = sv[i];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     for (int i = k - 1; i >= 0; --i) {
-        double s = sv[i];
-        for (int l = i + 1; l < k; ++l) s -= Hm[size_t(l) * ldh + i] * y[l];
-        y[i] = s / Hm[size_t(i) * ldh + i];
+        double s = sS[i];
+        for (int l = i + 1; l < k; ++l) s -= R[i][l] * yS[l];
+        yS[i] = s / R[i][i];
+        y[i] = yS[i];
     }
 }
 
@@ -173,12 +149,6 @@ template <typename T>
 __global__ void fill_kernel(T *x, T v, size_t n) {
     const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (idx < n) x[idx] = v;
-}
-
-// x += scale * d (refinement correction, FP32 -> FP64)
-__global__ void axpby_mixed_kernel(double *x, const float *d, const double *scale, size_t n) {
-    const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx < n) x[idx] = fma(scale[0], double(d[idx]), x[idx]);
 }
 
 // y = float(x / scale[0])
@@ -452,28 +422,14 @@ cudaError_t launch_scale_copy(const T *w, T *v, const double *denom, size_t n, c
     scale_copy_kernel<T><<<blocks(n, 256), 256, 0, s>>>(w, v, denom, n);
     return cudaGetLastError();
 }
-cudaError_t launch_arnoldi_finish(double *Hcol, const double *h1, const double *h2, const double *nrm2, int j,
-                                  cudaStream_t s) {
-    arnoldi_finish_kernel<<<1, 1, 0, s>>>(Hcol, h1, h2, nrm2, j);
-    return cudaGetLastError();
-}
-cudaError_t launch_givens(double *Hm, int ldh, double *cs, double *sn, double *sv, int j, const double *bnorm, double *est,
-                          int32_t *flags, cudaStream_t s) {
-    givens_kernel<<<1, 1, 0, s>>>(Hm, ldh, cs, sn, sv, j, bnorm, est, flags);
-    return cudaGetLastError();
-}
 cudaError_t launch_hessenberg_solve(const double *Hm, int ldh, const double *sv, int k, double *y, cudaStream_t s) {
-    hessenberg_solve_kernel<<<1, 1, 0, s>>>(Hm, ldh, sv, k, y);
+    hessenberg_solve_kernel<<<1, 128, 0, s>>>(Hm, ldh, sv, k, y);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_fill(T *x, T v, size_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     fill_kernel<T><<<blocks(n, 256), 256, 0, s>>>(x, v, n);
-    return cudaGetLastError();
-}
-cudaError_t launch_axpby_mixed(double *x, const float *d, const double *scale, size_t n, cudaStream_t s) {
-    axpby_mixed_kernel<<<blocks(n, 256), 256, 0, s>>>(x, d, scale, n);
     return cudaGetLastError();
 }
 cudaError_t launch_d2f_scaled(const double *x, float *y, const double *scale, size_t n, cudaStream_t s) {

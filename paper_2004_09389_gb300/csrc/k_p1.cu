@@ -58,24 +58,6 @@ __global__ void jacobi_kernel(int n, int W, const int32_t *__restrict__ col, con
 }
 
 template <typename T>
-__global__ void residual_kernel(int n, int W, const int32_t *__restrict__ col, const T *__restrict__ A,
-                                const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ r) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    r[i] = b[i] - ell_row(i, W, col, A, x);
-}
-
-template <typename T>
-__global__ void restrict_kernel(int nc, const int32_t *__restrict__ cp, const int32_t *__restrict__ ci,
-                                const double *__restrict__ cw, const T *__restrict__ rf, T *__restrict__ bc) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc) return;
-    T acc = T(0);
-    for (int k = cp[c]; k < cp[c + 1]; ++k) acc = fma(T(cw[k]), rf[ci[k]], acc);
-    bc[c] = acc;
-}
-
-template <typename T>
 __global__ void prolong_add_kernel(int nf, const int32_t *__restrict__ parent, const T *__restrict__ ec,
                                    T *__restrict__ xf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -84,17 +66,6 @@ __global__ void prolong_add_kernel(int nf, const int32_t *__restrict__ parent, c
     xf[i] += (a == b) ? ec[a] : T(0.5) * (ec[a] + ec[b]);
 }
 
-// x = inv b, one warp per row (inv row-major, n <= 1024)
-template <typename T>
-__global__ void dense_apply_kernel(const T *__restrict__ inv, int n, const T *__restrict__ b, T *__restrict__ x) {
-    const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    const int lane = threadIdx.x % 32;
-    if (row >= n) return;
-    double acc = 0.0;
-    for (int c = lane; c < n; c += 32) acc += double(inv[size_t(row) * n + c]) * double(b[c]);
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) x[row] = T(acc);
-}
 
 
 // Going down one level, fused: b_c = R (b_f - A_f x_f) with the fine residual
@@ -510,24 +481,8 @@ cudaError_t launch_p1_jacobi(const DevLevel &L, const T *A, const T *dinv, const
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_p1_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, cudaStream_t s) {
-    residual_kernel<T><<<blocks(L.nv, 256), 256, 0, s>>>(L.nv, L.width, L.col, A, b, x, r);
-    return cudaGetLastError();
-}
-template <typename T>
-cudaError_t launch_p1_restrict(const DevLevel &coarse, const T *rf, T *bc, cudaStream_t s) {
-    restrict_kernel<T><<<blocks(coarse.nv, 256), 256, 0, s>>>(coarse.nv, coarse.child_ptr, coarse.child_idx,
-                                                              coarse.child_w, rf, bc);
-    return cudaGetLastError();
-}
-template <typename T>
 cudaError_t launch_p1_prolong_add(const DevLevel &coarse, int nv_fine, const T *ec, T *xf, cudaStream_t s) {
     prolong_add_kernel<T><<<blocks(nv_fine, 256), 256, 0, s>>>(nv_fine, coarse.parent, ec, xf);
-    return cudaGetLastError();
-}
-template <typename T>
-cudaError_t launch_dense_apply(const T *inv, int n, const T *b, T *x, cudaStream_t s) {
-    dense_apply_kernel<T><<<blocks(size_t(n) * 32, 256), 256, 0, s>>>(inv, n, b, x);
     return cudaGetLastError();
 }
 
@@ -597,11 +552,7 @@ cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s) {
 #define HDG_P1_INST(T)                                                                                         \
     template cudaError_t launch_p1_jacobi<T>(const DevLevel &, const T *, const T *, const T *, const T *, T *, \
                                              T, bool, cudaStream_t);                                           \
-    template cudaError_t launch_p1_residual<T>(const DevLevel &, const T *, const T *, const T *, T *,           \
-                                               cudaStream_t);                                                  \
-    template cudaError_t launch_p1_restrict<T>(const DevLevel &, const T *, T *, cudaStream_t);                 \
     template cudaError_t launch_p1_prolong_add<T>(const DevLevel &, int, const T *, T *, cudaStream_t);         \
-    template cudaError_t launch_dense_apply<T>(const T *, int, const T *, T *, cudaStream_t);                  \
     template cudaError_t launch_p1_down<T>(const DevLevel &, const DevLevel &, const T *, const T *, const T *,  \
                                            const T *, T, T *, T *, cudaStream_t);                               \
     template cudaError_t launch_p1_up<T>(const DevLevel &, const DevLevel &, const T *, const T *, const T *,    \
