@@ -450,6 +450,9 @@ template <typename T>
 cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out, HostValue *pub, int32_t seq,
                  double *root_a, double *root_b) {
     Workspace &W = *h->ws;
+    if (k == 1)
+        return KL(HDG_PROF_KRYLOV, 1, launch_dot1<T>(V, w, W.NT, W.partial, W.nchunk, W.counter, out, pub, seq, root_a,
+                                                     root_b, h->stream));
     cudaError_t e = KL(HDG_PROF_KRYLOV, 1, launch_multidot<T>(V, W.NT, k, w, W.NT, W.partial, W.nchunk, h->stream));
     if (e != cudaSuccess) return e;
     return KL(HDG_PROF_KRYLOV, 1, launch_reduce_partials(W.partial, k, W.nchunk, out, h->stream, pub, seq, root_a,

@@ -403,6 +403,11 @@ cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s);
 template <typename T>
 cudaError_t launch_multidot(const T *V, size_t ld, int k, const T *w, size_t n, double *partial,
                             int nchunk, cudaStream_t s);
+// v . w in one launch (partials per chunk, then the last block adds them; the
+// same order and result as multidot + reduce_partials with k = 1)
+template <typename T>
+cudaError_t launch_dot1(const T *v, const T *w, size_t n, double *partial, int nchunk, unsigned int *counter,
+                        double *out, HostValue *pub, int32_t seq, double *root_a, double *root_b, cudaStream_t s);
 cudaError_t launch_reduce_partials(const double *partial, int k, int nchunk, double *out, cudaStream_t s,
                                    HostValue *pub = nullptr, int32_t seq = 0, double *root_a = nullptr,
                                    double *root_b = nullptr);

@@ -41,6 +41,49 @@ __global__ void __launch_bounds__(256) multidot_kernel(const T *__restrict__ V, 
     if (threadIdx.x == 0) partial[size_t(i) * nchunk + c] = tot;
 }
 
+// v . w in one launch: block c sums chunk c (as multidot_kernel), the last
+// block to finish adds the nchunk partials (as reduce_partials_kernel: the
+// same order, the same result) into out[0], optionally its square root into
+// root_a / root_b and a hand-over to the host (pub, seq)
+template <typename T>
+__global__ void __launch_bounds__(256) dot1_kernel(const T *__restrict__ v, const T *__restrict__ w, size_t n,
+                                                   double *__restrict__ partial, int nchunk,
+                                                   unsigned int *__restrict__ counter, double *__restrict__ out,
+                                                   HostValue *pub, int32_t seq, double *root_a, double *root_b) {
+    __shared__ bool last;
+    const int c = blockIdx.x;
+    const size_t len = (n + nchunk - 1) / nchunk;
+    const size_t beg = size_t(c) * len, end = beg + len < n ? beg + len : n;
+    T acc = T(0);
+    for (size_t k = beg + threadIdx.x; k < end; k += blockDim.x) acc = fma(v[k], w[k], acc);
+    const double tot = block_sum(double(acc));
+    if (threadIdx.x == 0) {
+        partial[c] = tot;
+        __threadfence();                       // the partial is visible before the count
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nchunk; i += blockDim.x) a += partial[i];
+    a = block_sum(a);
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        out[0] = a;
+        if (root_a || root_b) {
+            const double r = sqrt(a);
+            if (root_a) *root_a = r;
+            if (root_b) *root_b = r;
+        }
+        if (pub) {
+            pub->v = a;
+            __threadfence_system();
+            *reinterpret_cast<volatile int32_t *>(&pub->seq) = seq;
+        }
+    }
+}
+
 // out[i] = sum of the partials of vector i; with pub, block 0 also hands its
 // sum to the host (page-locked HostValue: the value, a system fence, seq);
 // root_a / root_b (may be null) receive the square root of block 0's sum
@@ -397,6 +440,16 @@ cudaError_t launch_multidot(const T *V, size_t ld, int k, const T *w, size_t n, 
     multidot_kernel<T><<<grid, 256, 0, s>>>(V, ld, w, n, partial, nchunk);
     return cudaGetLastError();
 }
+template <typename T>
+cudaError_t launch_dot1(const T *v, const T *w, size_t n, double *partial, int nchunk, unsigned int *counter,
+                        double *out, HostValue *pub, int32_t seq, double *root_a, double *root_b, cudaStream_t s) {
+    dot1_kernel<T><<<nchunk, 256, 0, s>>>(v, w, n, partial, nchunk, counter, out, pub, seq, root_a, root_b);
+    return cudaGetLastError();
+}
+template cudaError_t launch_dot1<double>(const double *, const double *, size_t, double *, int, unsigned int *,
+                                         double *, HostValue *, int32_t, double *, double *, cudaStream_t);
+template cudaError_t launch_dot1<float>(const float *, const float *, size_t, double *, int, unsigned int *, double *,
+                                        HostValue *, int32_t, double *, double *, cudaStream_t);
 cudaError_t launch_reduce_partials(const double *partial, int k, int nchunk, double *out, cudaStream_t s,
                                    HostValue *pub, int32_t seq, double *root_a, double *root_b) {
     reduce_partials_kernel<<<k, 256, 0, s>>>(partial, nchunk, out, pub, seq, root_a, root_b);
