@@ -272,11 +272,14 @@ cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out, Host
                  int32_t seq = 0, double *root_a = nullptr, double *root_b = nullptr);
 
 // P1 V-cycle for the coarse problem (Eq. coarse_problem_upwind) with
-// right-hand side levB(level 0).  Levels above the tail: fused kernels (the
-// first pre-smoothing sweep of each level rides on the restriction that
-// produced its right-hand side; the prolongation rides on the first
-// post-smoothing sweep); levels from tail_start down: one single-CTA kernel.
-// Returns the device vector that holds the level-0 result.  The first
+// right-hand side levB(level 0).  Levels above the tail: the first
+// pre-smoothing sweep of each level rides on the restriction that produced
+// its right-hand side; on levels with patches (at most 32,768 vertices) the
+// last pre-sweep, the residual and the restriction share one patch kernel, and
+// so do the prolongation and the first two post-sweeps; elsewhere one kernel
+// per sweep, with the residual inside the restriction and the prolongation
+// inside the first post-sweep.  Levels from tail_start down: one single-CTA
+// kernel.  Returns the device vector that holds the level-0 result.  The first
 // pre-smoothing sweep of level 0 (when it is above the tail) was done by the
 // trace-to-P1 restriction.
 template <typename T>

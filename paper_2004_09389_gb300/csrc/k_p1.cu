@@ -4,6 +4,10 @@
 // slot q of row i at i * W + q), restriction by the transpose of the midpoint
 // prolongation, and a dense inverse on the coarsest level.  A row's columns
 // and values load as 16-byte vectors; its W products are summed in slot order.
+// Three launch structures, all with that arithmetic: one kernel per step
+// (large levels), patch kernels that recompute a one-ring halo so that a
+// sweep and the step consuming it share a launch (mid-size levels), and one
+// CTA for the small levels, staged from a pre-packed shared-memory image.
 #include "common.h"
 
 namespace hdg {
