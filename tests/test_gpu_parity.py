@@ -425,3 +425,38 @@ def test_precond_multi_block_p1_levels_match_oracle(kind, p1_nu, monkeypatch):
     assert _rel(out["1"][0], out["0"][0]) <= 1e-14
     assert _rel(out["1"][1], out["0"][1]) <= 1e-6
     assert _rel(out["1"][1], z0) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_set_tau_recondenses_in_place(precision, monkeypatch):
+    """hdg_set_tau re-condenses the handle: operators, P1 levels and the
+    single-CTA cycle's shared-memory image are rebuilt in place under the
+    step graphs captured by the first solve.  The next solve equals that of a
+    fresh handle built with the new tau (same kernels, same data: bit for bit)
+    and the oracle's solution.  The coarse cycle is limited to 16 vertices so
+    that the patch-fused P1 kernels run too."""
+    monkeypatch.setenv("HDG_TAIL_MAX_VERTICES", "16")
+    mesh = I.periodic_square_hierarchy(24, n_coarsest=3)
+    g, H, f = 1.3, 0.7, I.coriolis_flat(mesh, 1.0)
+    p = 2
+    tau1 = 8 * mesh.h / np.sqrt(g * H)
+    tau2 = 2.5 * tau1
+    prob2 = HDGProblem(mesh, p, tau=tau2, g=g, H=H, f_vertex=f)
+    rng = np.random.default_rng(11)
+    ru = rng.standard_normal((mesh.n_cells, 2, prob2.np))
+    rh = rng.standard_normal((mesh.n_cells, prob2.np))
+    s = _solver(mesh, p, tau1, g, H, f, precision=precision, rtol=1e-10)
+    s.solve(ru, rh)
+    s.set_tau(tau2)
+    lam, info = s.solve(ru, rh)
+    u, h = s.recover()
+    fresh = _solver(mesh, p, tau2, g, H, f, precision=precision, rtol=1e-10)
+    lam_f, info_f = fresh.solve(ru, rh)
+    u_f, h_f = fresh.recover()
+    assert info["iters"] == info_f["iters"]
+    assert np.array_equal(lam, lam_f) and np.array_equal(u, u_f) and np.array_equal(h, h_f)
+    (u0, h0), lam0 = prob2.solve_condensed(ru, rh)
+    tol = 1e-8 if precision else 1e-9
+    assert _rel(lam, lam0.reshape(lam.shape)) <= tol and _rel(u, u0) <= tol and _rel(h, h0) <= tol
+    s.close()
+    fresh.close()
