@@ -460,3 +460,25 @@ def test_set_tau_recondenses_in_place(precision, monkeypatch):
     assert _rel(lam, lam0.reshape(lam.shape)) <= tol and _rel(u, u0) <= tol and _rel(h, h0) <= tol
     s.close()
     fresh.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_kernel_accounting_keeps_the_result(precision):
+    """With timing on, every launch is bracketed by CUDA events and the
+    Arnoldi steps run as direct launches instead of replayed graphs: the
+    solution is bit-identical, the per-category launch counts equal those the
+    graphs report, and every category the solve uses gets time."""
+    mesh, prob, (tau, g, H, f), ru, rh = _case("flat", 2)
+    s = _solver(mesh, 2, tau, g, H, f, precision=precision, rtol=1e-10)
+    s.solve(ru, rh)                       # step graphs captured
+    s.profile_enable(False)               # counters reset, timing off
+    lam_g, info_g = s.solve(ru, rh)
+    counts_g = {k: v[1] for k, v in s.profile_read().items()}
+    s.profile_enable(True)
+    lam_t, info_t = s.solve(ru, rh)
+    prof = s.profile_read()
+    s.close()
+    assert info_g["iters"] == info_t["iters"] and np.array_equal(lam_g, lam_t)
+    assert {k: v[1] for k, v in prof.items()} == counts_g
+    for k in ("apply64" if precision == 0 else "apply32", "p1", "krylov", "rhs", "layout"):
+        assert prof[k][1] > 0 and prof[k][0] > 0.0, (k, prof[k])
