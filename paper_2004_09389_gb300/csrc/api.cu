@@ -252,17 +252,20 @@ KSpace<float> &kspace<float>(hdg_handle *h) { return h->ws->k32; }
 
 }  // namespace
 
-size_t hdg::tail_smem_bytes(const std::vector<DevLevel> &lev, int first, size_t tsz) {
-    auto pad = [](size_t b) { return (b + 15) / 16 * 16; };
-    size_t bytes = pad(sizeof(TailHdr) * (lev.size() - first));
-    for (size_t l = first; l < lev.size(); ++l) {
+// sizes of the single-CTA levels [first, lev.size()) for their layout
+static std::vector<TailLevelSize> tail_sizes(const std::vector<DevLevel> &lev, int first) {
+    std::vector<TailLevelSize> lv;
+    for (size_t l = size_t(first); l < lev.size(); ++l) {
         const bool top = int(l) == first;
-        const size_t nv = lev[l].nv, nnz = lev[l].nnz, nci = top ? 0 : lev[l].nci;
-        const size_t nfin = top ? 0 : lev[l - 1].nv;
-        bytes += pad(tsz * nnz) + pad(tsz * nv) + pad(tsz * nci) + 4 * pad(tsz * nv);
-        bytes += pad(4 * nnz) + (top ? 0 : pad(4 * (nv + 1))) + pad(4 * nci) + pad(4 * 2 * nfin);
+        lv.push_back({lev[l].nv, lev[l].nnz, lev[l].width, top ? 0 : lev[l].nci, top ? 0 : lev[l - 1].nv});
     }
-    return bytes;
+    return lv;
+}
+
+size_t hdg::tail_smem_bytes(const std::vector<DevLevel> &lev, int first, size_t tsz) {
+    TailLayout lay;
+    tail_layout(tail_sizes(lev, first), tsz, 0, lay);
+    return lay.smem_bytes;
 }
 
 namespace {
@@ -873,55 +876,28 @@ void drop_graphs(hdg_handle *h);
 // assembled level operators (hdg_condense).
 int build_tail_image(hdg_handle *h, int pi) {
     if (pi == 1 && !h->lev[0].A32) return HDG_OK;          // no FP32 levels on this handle
-    auto pad = [](size_t b) { return (b + 15) / 16 * 16; };
     const size_t tsz = pi == 0 ? sizeof(double) : sizeof(float);
-    const int nlev = int(h->lev.size()), ts = h->tail_start[pi], n = nlev - ts;
-    std::vector<TailHdr> hdr(n);
-    struct Piece { size_t off; const void *src; size_t bytes; };
-    std::vector<Piece> pieces;
-    size_t off = pad(sizeof(TailHdr) * n);
-    auto put = [&](int32_t &o, const void *src, size_t bytes) {
-        o = int32_t(off);
-        if (bytes) pieces.push_back({off, src, pad(bytes)});
-        off += pad(bytes);
-    };
-    for (int k = 0; k < n; ++k) {
-        const DevLevel &L = h->lev[ts + k];
-        const bool top = k == 0;
-        TailHdr &H = hdr[k];
-        H = TailHdr{};
-        H.nv = L.nv; H.nnz = L.nnz; H.nci = top ? 0 : L.nci; H.W = L.width;
-        put(H.oA, pi == 0 ? static_cast<const void *>(L.A) : static_cast<const void *>(L.A32), tsz * L.nnz);
-        put(H.oD, pi == 0 ? static_cast<const void *>(L.dinv) : static_cast<const void *>(L.dinv32), tsz * L.nv);
-        put(H.ocol, L.col, 4 * size_t(L.nnz));
-        if (!top) {
-            put(H.ocw, pi == 0 ? static_cast<const void *>(L.child_w) : static_cast<const void *>(L.child_w32),
-                tsz * L.nci);
-            put(H.ocp, L.child_ptr, 4 * size_t(L.nv + 1));
-            put(H.oci, L.child_idx, 4 * size_t(L.nci));
-            put(H.opar, L.parent, 4 * size_t(2 * h->lev[ts + k - 1].nv));
-        }
-    }
-    const size_t data_end = off;
-    size_t scratch = 0;
-    for (int k = 0; k < n; ++k) scratch += 4 * pad(tsz * h->lev[ts + k].nv);
-    const size_t nc = h->lev.back().nv, inv_bytes = pad(sizeof(double) * nc * nc);
-    int32_t inv_off = -1;
-    if (inv_bytes <= kTailInvSmemMax && data_end + inv_bytes + scratch <= kTailSmemMax) {
-        inv_off = int32_t(off);
-        pieces.push_back({off, h->d_coarse_inv, inv_bytes});
-        off += inv_bytes;
-    }
-    const size_t img_bytes = off;
-    for (int k = 0; k < n; ++k) {
-        const size_t v = pad(tsz * h->lev[ts + k].nv);
-        hdr[k].ox = int32_t(off); off += v;
-        hdr[k].ox2 = int32_t(off); off += v;
-        hdr[k].ob = int32_t(off); off += v;
-        hdr[k].orr = int32_t(off); off += v;
-    }
-    if (off > kTailSmemMax)
+    const int ts = h->tail_start[pi], n = int(h->lev.size()) - ts;
+    TailLayout lay;
+    if (!tail_layout(tail_sizes(h->lev, ts), tsz, size_t(h->lev.back().nv), lay))
         return fail(h, HDG_EINVAL, "coarsest P1 levels too large for the single-CTA coarse cycle");
+    const std::vector<TailHdr> &hdr = lay.hdr;
+    const size_t img_bytes = lay.img_bytes;
+    const int32_t inv_off = lay.inv_off;
+    const size_t off = lay.smem_bytes;
+    auto source = [&](const TailPiece &q) -> const void * {
+        const DevLevel &L = h->lev[size_t(ts + q.level)];
+        switch (q.kind) {
+        case kTailA: return pi == 0 ? static_cast<const void *>(L.A) : static_cast<const void *>(L.A32);
+        case kTailD: return pi == 0 ? static_cast<const void *>(L.dinv) : static_cast<const void *>(L.dinv32);
+        case kTailCol: return L.col;
+        case kTailCw: return pi == 0 ? static_cast<const void *>(L.child_w) : static_cast<const void *>(L.child_w32);
+        case kTailCp: return L.child_ptr;
+        case kTailCi: return L.child_idx;
+        case kTailPar: return L.parent;
+        default: return h->d_coarse_inv;
+        }
+    };
     TailImage &im = h->tail_img[pi];
     if (im.cap < img_bytes) {
         dfree(im.d);
@@ -932,8 +908,8 @@ int build_tail_image(hdg_handle *h, int pi) {
     }
     cudaStream_t s = h->stream;
     TRY(cudaMemcpyAsync(im.d, hdr.data(), sizeof(TailHdr) * n, cudaMemcpyHostToDevice, s));
-    for (const Piece &q : pieces)
-        TRY(cudaMemcpyAsync(im.d + q.off, q.src, q.bytes, cudaMemcpyDeviceToDevice, s));
+    for (const TailPiece &q : lay.pieces)
+        TRY(cudaMemcpyAsync(im.d + q.off, source(q), q.bytes, cudaMemcpyDeviceToDevice, s));
     TRY(cudaStreamSynchronize(s));                         // hdr is host memory on this stack
     if (im.ts != ts || im.img_bytes != img_bytes) {
         if (h->ws) drop_graphs(h);

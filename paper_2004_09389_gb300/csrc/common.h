@@ -234,6 +234,32 @@ struct TailImage {
 // shared-memory bytes of the tail kernel for levels [first, levels.size()) in
 // precision of size tsz (header table, level arrays, scratch; no inverse)
 size_t tail_smem_bytes(const std::vector<DevLevel> &lev, int first, size_t tsz);
+
+// Host-side layout of the tail image (csrc/layout.cpp).  Sizes of one tail
+// level: vertices, ELL slots and width, restriction entries into it and the
+// finer level's vertex count (both 0 on the first tail level).
+struct TailLevelSize {
+    int nv, nnz, W, nci, nfin;
+};
+enum TailPieceKind : int { kTailA = 0, kTailD, kTailCol, kTailCw, kTailCp, kTailCi, kTailPar, kTailInv };
+// one array copied into the image: byte offset and (16-byte padded) size,
+// the tail level it belongs to and what it is
+struct TailPiece {
+    size_t off, bytes;
+    int level, kind;
+};
+struct TailLayout {
+    std::vector<TailHdr> hdr;         // one per level, at offset 0 of the image
+    std::vector<TailPiece> pieces;    // in offset order, after the table
+    size_t img_bytes = 0;             // table + pieces: what the bulk copies stage
+    size_t smem_bytes = 0;            // plus the scratch vectors x, x2, b, r of every level
+    int32_t inv_off = -1;             // offset of the coarsest FP64 inverse, -1: not staged
+};
+// The layout for levels lv (first tail level first), values of tsz bytes and
+// a coarsest level of nc vertices whose FP64 inverse is staged when it fits
+// (nc = 0: never).  Every offset and size is a multiple of 16 bytes.  Returns
+// false when the shared memory would exceed kTailSmemMax.
+bool tail_layout(const std::vector<TailLevelSize> &lv, size_t tsz, size_t nc, TailLayout &out);
 struct TailArgs {
     int nlev, nu1, nu2;
     double omega;
