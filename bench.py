@@ -664,6 +664,48 @@ def profile_solve_main(args):
     s.close()
 
 
+def profile_learned_main(args):
+    """The learned facet-patch sweep inside one FP32 preconditioner application on
+    the benchmark workload: off, FP32 network on the CUDA cores, network on the
+    tensor cores (hidden 64, parameters 0.3 N(0, 1) from seed 1), 50 applications
+    each timed by CUDA events on the handle's stream; then one application with
+    each network between profiler start and stop (for ncu --profile-from-start off)."""
+    import numpy as np
+    import torch
+    from paper_2004_09389_gb300 import HDGSolver, HDG_MIXED_FP32, build
+    build.build()
+    wl = make_workload("flat", True, args.p, args.courant, args.seed)
+    s = HDGSolver(wl["mesh"], args.p, wl["tau"], wl["g"], wl["H"], f_vertex=wl["f"], precision=HDG_MIXED_FP32)
+    npar = s.learned_init(hidden=64, capacity=4)
+    s.set_learned_params((0.3 * np.random.default_rng(1).standard_normal(npar)).astype(np.float32))
+    v = torch.randn(s.n_facets * (args.p + 1), device="cuda")
+    z = torch.empty_like(v)
+    out = {}
+    for name, tc in (("off", None), ("fp32", False), ("tensor_cores", True)):
+        if tc is None:
+            s.learned_enable(False)
+        else:
+            s.learned_enable(True, tensor_cores=tc)
+        for _ in range(3):
+            s.precond_apply32_dev(v, z)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        for _ in range(50):
+            s.precond_apply32_dev(v, z)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / 50 * 1e3
+    torch.cuda.profiler.start()
+    for tc in (False, True):
+        s.learned_enable(True, tensor_cores=tc)
+        s.precond_apply32_dev(v, z)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    s.close()
+    print(json.dumps({"profile_learned": "precond application us", **{k: round(t, 1) for k, t in out.items()}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -690,6 +732,10 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="autotune launch shapes per handle (off by default: on the 256x256x2 workload the defaults measured faster)")
     ap.add_argument("--clocks-csv", dest="clocks_csv", default="",
                     help="keep the raw nvidia-smi clock samples of the timed region in this CSV file")
+    ap.add_argument("--profile-learned", dest="profile_learned", action="store_true",
+                    help="time one FP32 preconditioner application with the learned sweep off, on the CUDA cores "
+                         "and on the tensor cores (hidden 64, random parameters), then run one of each between "
+                         "profiler start and stop; prints the times, no bench line")
     ap.add_argument("--profile-solve", dest="profile_solve", default="",
                     choices=["", "mixed", "mixed_bf16", "fgmres64", "fp64"],
                     help="warm up, then run one solve and recovery of this arm between profiler start and stop "
@@ -697,6 +743,9 @@ def main():
     args = ap.parse_args()
     if args.profile_solve:
         profile_solve_main(args)
+        return
+    if args.profile_learned:
+        profile_learned_main(args)
         return
     if args.batch:
         batch_main(args)
