@@ -1,4 +1,4 @@
-"""Mesh validation in hdg_setup, on the CPU: every check runs on the host
+"""Argument and mesh validation in hdg_setup, on the CPU: every check runs on the host
 before the first CUDA call, so each malformed input is rejected with
 HDG_EINVAL, no handle and a message naming the fault, without a GPU."""
 import copy
@@ -132,3 +132,51 @@ def test_bad_coarse_level_list_is_rejected_on_the_host():
         rc = lib.hdg_setup(ctypes.byref(desc), ctypes.byref(prm), None, ctypes.byref(h))
         assert rc == _lib.HDG_EINVAL and not h.value
         assert "bad coarse level list" in lib.hdg_last_error(None).decode()
+
+
+PARAM_FAULTS = [
+    ({"p": 0}, "p must be in 1..4"), ({"p": 5}, "p must be in 1..4"),
+    ({"tau": 0.0}, "tau, g and H must be positive"), ({"g": -1.0}, "tau, g and H must be positive"),
+    ({"H": float("nan")}, "tau, g and H must be positive"),
+    ({"rtol": 0.0}, "rtol must be positive"),
+    ({"restart": 0}, "restart must be in 1..64"), ({"restart": 65}, "restart must be in 1..64"),
+    ({"max_iter": 0}, "max_iter must be positive"),
+    ({"n_pre": -1}, "negative sweep count"), ({"p1_nu_post": -2}, "negative sweep count"),
+    ({"omega": 0.0}, "damping factors must be positive"), ({"p1_omega": -0.5}, "damping factors must be positive"),
+    ({"coarse_mode": 2}, "coarse_mode must be 0 or 1"),
+    ({"reorth": -1}, "reorth must be 0 or 1"),
+    ({"precision": 7}, "unknown precision mode"),
+    ({"precision": 1, "inner_rtol": 1.0}, "inner_rtol must be in (0, 1)"),
+    ({"precision": 2, "inner_rtol": 0.0}, "inner_rtol must be in (0, 1)"),
+]
+
+
+@pytest.mark.parametrize("fields,text", PARAM_FAULTS)
+def test_bad_parameters_are_rejected_on_the_host(fields, text):
+    """Each parameter fault is reported before the mesh is even looked at."""
+    from paper_2004_09389_gb300 import _lib
+    lib = _lib.load()
+    prm = _lib.default_params()
+    prm.tau, prm.g, prm.H = 0.1, 1.0, 1.0
+    for k, v in fields.items():
+        setattr(prm, k, v)
+    keep = []
+    desc = _lib.make_mesh_desc(_mesh(), keep)
+    h = ctypes.c_void_p()
+    rc = lib.hdg_setup(ctypes.byref(desc), ctypes.byref(prm), None, ctypes.byref(h))
+    assert rc == _lib.HDG_EINVAL and not h.value
+    assert text in lib.hdg_last_error(None).decode()
+
+
+def test_null_params_and_out_are_rejected():
+    from paper_2004_09389_gb300 import _lib
+    lib = _lib.load()
+    keep = []
+    desc = _lib.make_mesh_desc(_mesh(), keep)
+    h = ctypes.c_void_p()
+    assert lib.hdg_setup(ctypes.byref(desc), None, None, ctypes.byref(h)) == _lib.HDG_EINVAL and not h.value
+    assert "params is NULL" in lib.hdg_last_error(None).decode()
+    prm = _lib.default_params()
+    prm.tau, prm.g, prm.H = 0.1, 1.0, 1.0
+    assert lib.hdg_setup(ctypes.byref(desc), ctypes.byref(prm), None, None) == _lib.HDG_EINVAL
+    assert "out is NULL" in lib.hdg_last_error(None).decode()
