@@ -172,7 +172,11 @@ HDG_API int hdg_set_tau(hdg_handle *h, double tau);
 
 /* Steps 1 and 2 with host buffers: r_u, r_h in, lambda out ([n_facets][p+1]).
  * info may be NULL.  Returns HDG_ENOCONV / HDG_EBREAKDOWN / HDG_ENAN with the
- * last iterate in lambda. */
+ * last iterate in lambda.  Step 2 (Sec. 4.2) is driven from the calling
+ * thread: after each Arnoldi step it spins on a word the GPU writes to
+ * page-locked memory (the residual estimate decides whether to go on), so the
+ * calling thread keeps one CPU core busy for the length of the solve; the same
+ * holds for hdg_solve_dev and each thread of hdg_solve_batch_dev. */
 HDG_API int hdg_solve(hdg_handle *h, const double *r_u, const double *r_h, double *lambda,
               hdg_solve_info *info);
 /* The same with device pointers. */
