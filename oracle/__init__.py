@@ -18,6 +18,11 @@ What it computes, and where each piece comes from in the paper:
 * ``stddg``      - the standard (non-hybridised) upwind DG system obtained by
   eliminating the trace, used only to cross-check the HDG solution
   (the equivalence stated after Eq. linear_hybridized).
+* ``imex``       - time stepping around the implicit solve (Sec. 3 "Time
+  discretisation", Eqs. theta_method, IMEX_HDG_I, IMEX_HDG_II; the ARS2(2,3,2)
+  tableau of Sec. "Timestepping methods"): the theta method and ARS2 with
+  the Coriolis term explicit, each implicit stage solved directly or by the
+  HDG route (tau = alpha dt, f = 0).
 * ``solver``     - right-preconditioned (F)GMRES and the non-nested two-level
   V-cycle of Alg. twolevel_vcycle: damped block-Jacobi facet smoothing,
   P1 restriction/prolongation (Sec. 4.4, upwind coarse space), and the

@@ -44,6 +44,15 @@ def _cross_edge_matrix(p: int, i: int, i2: int) -> np.ndarray:
 
 def solve_standard_dg(prob: HDGProblem, r_u: np.ndarray, r_h: np.ndarray):
     """Assemble and solve the standard upwind DG system; returns (u, h)."""
+    Amat = assemble_standard_dg(prob)
+    rhs = prob.load(r_u, r_h).ravel()
+    q = spla.splu(Amat.tocsc()).solve(rhs).reshape(prob.N, -1)
+    return prob.split(q)
+
+
+def assemble_standard_dg(prob: HDGProblem) -> sp.csr_matrix:
+    """The matrix of the standard upwind DG system (cell unknowns ordered
+    cell, then u_x, u_y, h, then node), so that A q = M r."""
     p = prob.prm.p
     tau, g, H, ts = prob.prm.tau, prob.prm.g, prob.prm.H, prob.prm.tau_s
     R = ref.reference_matrices(p)
@@ -99,8 +108,5 @@ def solve_standard_dg(prob: HDGProblem, r_u: np.ndarray, r_h: np.ndarray):
                 put(tau * g * nx * blk, K, UX, Kc, sc)     # tau g <lambda, w.n>
                 put(tau * g * ny * blk, K, UY, Kc, sc)
                 put(-tau * ts * blk, K, HH, Kc, sc)        # -tau tau_s <lambda, psi>
-    Amat = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                          shape=(N * nK, N * nK))
-    rhs = prob.load(r_u, r_h).ravel()
-    q = spla.splu(Amat.tocsc()).solve(rhs).reshape(N, nK)
-    return prob.split(q)
