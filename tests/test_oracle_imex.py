@@ -133,3 +133,19 @@ def test_temporal_order(mesh, ops, ops0, case, order):
     ratio = np.linalg.norm(q16 - q32) / np.linalg.norm(q32 - q64)
     lo, hi = (1.5, 2.6) if order == 1 else (3.3, 4.8)
     assert lo <= ratio <= hi, ratio
+
+
+@pytest.mark.parametrize("scheme", ["theta", "ars2"])
+def test_sphere_routes_and_mass(scheme):
+    """The same two pins on an icosahedral sphere (cells in their own tangent
+    frames, f = 2 Omega sin(latitude))."""
+    sph = I.sphere_hierarchy(1, 1.0, r_coarsest=0)
+    ops_s = imex.IMEXOperators(sph, P, G, H, I.coriolis_sphere(sph, 0.8))
+    q, dt = _random_state(ops_s, 5), 0.04
+    m0 = ops_s.integral_of_h(q)
+    if scheme == "theta":
+        a, b = imex.theta_step(ops_s, q, dt, 0.5, "direct"), imex.theta_step(ops_s, q, dt, 0.5, "hdg")
+    else:
+        a, b = imex.ars2_step(ops_s, q, dt, "direct"), imex.ars2_step(ops_s, q, dt, "hdg")
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+    assert abs(ops_s.integral_of_h(a) - m0) <= 1e-12 * abs(m0)
