@@ -190,6 +190,9 @@ HDG_API int hdg_solve_dev(hdg_handle *h, const double *r_u, const double *r_h, d
  * call with NULLs still selects the last solve's data. */
 HDG_API int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lambda,
                 double *u, double *h_out);
+/* The same with device pointers on the handle's stream: r_u, r_h, u and h_out
+ * are required (HDG_EINVAL if NULL); lambda may be NULL to use the handle's
+ * last solution.  Results are complete once the stream has been synchronised. */
 HDG_API int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h, const double *lambda,
                     double *u, double *h_out);
 
