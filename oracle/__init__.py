@@ -20,7 +20,8 @@ What it computes, and where each piece comes from in the paper:
   (the equivalence stated after Eq. linear_hybridized).
 * ``imex``       - time stepping around the implicit solve (Sec. 3 "Time
   discretisation", Eqs. theta_method, IMEX_HDG_I, IMEX_HDG_II; the ARS2(2,3,2)
-  tableau of Sec. "Timestepping methods"): the theta method and ARS2 with
+  tableaux of Sec. "Timestepping methods"): the theta method and a general
+  IMEX Runge-Kutta stage driver (ARS2(2,3,2), SSP2(3,2,2), ARS3(4,4,3)) with
   the Coriolis term explicit, each implicit stage solved directly or by the
   HDG route (tau = alpha dt, f = 0).
 * ``solver``     - right-preconditioned (F)GMRES and the non-nested two-level

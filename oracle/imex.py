@@ -118,3 +118,50 @@ def ars2_step(ops: IMEXOperators, q0: np.ndarray, dt: float, route: str = "direc
     Q3 = ops.stage_solve(g * dt, Mq0 + dt * (d * N1 + (1.0 - d) * N2) + dt * (1.0 - g) * L2, route)
     N3, L3 = -(ops.C @ Q3), -(ops.K0 @ Q3)
     return ops.mass_solve(Mq0 + dt * ((1.0 - g) * (N2 + L2) + g * (N3 + L3)))
+
+
+# Butcher tableaux (explicit a, implicit a~, weights b, b~) of the IMEX methods
+# listed in the paper's section "Timestepping methods": ARS2(2,3,2),
+# SSP2(3,2,2) and ARS3(4,4,3).
+def _ars2():
+    g, d = ARS2_GAMMA, ARS2_DELTA
+    return ([[0, 0, 0], [g, 0, 0], [d, 1 - d, 0]], [[0, 0, 0], [0, g, 0], [0, 1 - g, g]],
+            [0, 1 - g, g], [0, 1 - g, g])
+
+
+TABLEAUX = {
+    "ARS2": _ars2(),
+    "SSP2": ([[0, 0, 0], [0, 0, 0], [0, 1, 0]], [[0.5, 0, 0], [-0.5, 0.5, 0], [0, 0.5, 0.5]],
+             [0, 0.5, 0.5], [0, 0.5, 0.5]),
+    "ARS3": ([[0, 0, 0, 0, 0], [1 / 2, 0, 0, 0, 0], [11 / 18, 1 / 18, 0, 0, 0], [5 / 6, -5 / 6, 1 / 2, 0, 0],
+              [1 / 4, 7 / 4, 3 / 4, -7 / 4, 0]],
+             [[0, 0, 0, 0, 0], [0, 1 / 2, 0, 0, 0], [0, 1 / 6, 1 / 2, 0, 0], [0, -1 / 2, 1 / 2, 1 / 2, 0],
+              [0, 3 / 2, -3 / 2, 1 / 2, 1 / 2]],
+             [1 / 4, 7 / 4, 3 / 4, -7 / 4, 0], [0, 3 / 2, -3 / 2, 1 / 2, 1 / 2]),
+}
+
+
+def imex_rk_step(ops: IMEXOperators, q0: np.ndarray, dt: float, tableau: str, route: str = "direct") -> np.ndarray:
+    """One step of an s-stage IMEX method (Eqs. IMEX_HDG_I, IMEX_HDG_II):
+    stage i solves M Q_i - a~_ii dt L(Q_i) = M q0 + dt sum_{j<i} (a_ij N(Q_j)
+    + a~_ij L(Q_j)) (a plain mass solve where a~_ii = 0; stage 1 is q0 when
+    nothing precedes it), then M q1 = M q0 + dt sum_i (b_i N(Q_i) + b~_i L(Q_i))."""
+    a, at, b, bt = (np.asarray(x, dtype=float) for x in TABLEAUX[tableau])
+    Mq0 = ops.mass(q0)
+    Ns, Ls = [], []
+    for i in range(len(b)):
+        rhs = Mq0.copy()
+        for j in range(i):
+            rhs += dt * (a[i, j] * Ns[j] + at[i, j] * Ls[j])
+        if at[i, i] != 0.0:
+            Q = ops.stage_solve(at[i, i] * dt, rhs, route)
+        elif i == 0:
+            Q = q0
+        else:
+            Q = ops.mass_solve(rhs)
+        Ns.append(-(ops.C @ Q))
+        Ls.append(-(ops.K0 @ Q))
+    upd = Mq0.copy()
+    for i in range(len(b)):
+        upd += dt * (b[i] * Ns[i] + bt[i] * Ls[i])
+    return ops.mass_solve(upd)

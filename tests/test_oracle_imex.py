@@ -149,3 +149,45 @@ def test_sphere_routes_and_mass(scheme):
         a, b = imex.ars2_step(ops_s, q, dt, "direct"), imex.ars2_step(ops_s, q, dt, "hdg")
     assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
     assert abs(ops_s.integral_of_h(a) - m0) <= 1e-12 * abs(m0)
+
+
+def test_general_driver_reproduces_ars2(ops):
+    q, dt = _random_state(ops, 6), 0.05
+    a = imex.ars2_step(ops, q, dt)
+    b = imex.imex_rk_step(ops, q, dt, "ARS2")
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("name", ["ARS2", "SSP2", "ARS3"])
+def test_tableau_order_conditions(name):
+    """Weights sum to one and the second-order conditions hold for both parts
+    and their coupling (b.c = b.c~ = b~.c = b~.c~ = 1/2)."""
+    a, at, b, bt = (np.asarray(x, float) for x in imex.TABLEAUX[name])
+    c, ct = a.sum(1), at.sum(1)
+    assert abs(b.sum() - 1) < 1e-14 and abs(bt.sum() - 1) < 1e-14
+    for u in (b, bt):
+        for v in (c, ct):
+            assert abs(u @ v - 0.5) < 1e-14
+    assert np.allclose(np.triu(a), 0) and np.allclose(np.triu(at, 1), 0)    # explicit / diagonally implicit
+
+
+@pytest.mark.parametrize("name,order", [("SSP2", 2), ("ARS3", 3)])
+def test_general_driver_orders_and_mass(mesh, ops, name, order):
+    T = 0.4
+    q0 = _smooth_state(mesh, ops)
+
+    def run(n):
+        q = q0.copy()
+        for _ in range(n):
+            q = imex.imex_rk_step(ops, q, T / n, name)
+        return q
+
+    q16, q32, q64 = run(16), run(32), run(64)
+    ratio = np.linalg.norm(q16 - q32) / np.linalg.norm(q32 - q64)
+    lo, hi = {2: (3.3, 4.8), 3: (6.5, 9.6)}[order]
+    assert lo <= ratio <= hi, ratio
+    qr = _random_state(ops, 7)
+    q1 = imex.imex_rk_step(ops, qr, 0.05, name)
+    q1h = imex.imex_rk_step(ops, qr, 0.05, name, route="hdg")
+    assert np.abs(q1 - q1h).max() <= 1e-12 * np.abs(q1).max()
+    assert abs(ops.integral_of_h(q1) - ops.integral_of_h(qr)) <= 1e-12 * abs(ops.integral_of_h(qr))
