@@ -57,7 +57,7 @@ def test_monolithic_equals_condensed(kind, p):
     assert np.abs(l1 - l2).max() <= 1e-12 * np.abs(l1).max()
 
 
-@pytest.mark.parametrize("kind,p", [("flat", 1), ("flat", 2), ("sphere", 2)])
+@pytest.mark.parametrize("kind,p", [("flat", 1), ("flat", 2), ("flat", 3), ("flat", 4), ("sphere", 2)])
 def test_hdg_equals_standard_dg(kind, p):
     mesh, prob = _problem(kind, p)
     ru, rh = _rand_rhs(prob, 2)
@@ -81,7 +81,8 @@ def _edge_mismatch2(prob, K, hK, lamK):
 
 
 @pytest.mark.parametrize("kind,p,f0", [("flat", 1, 0.0), ("flat", 2, 0.0), ("sphere", 2, 0.0),
-                                        ("flat", 2, 1.0), ("sphere", 1, 3.0)])
+                                        ("flat", 2, 1.0), ("sphere", 1, 3.0), ("flat", 3, 0.0),
+                                        ("flat", 3, 1.0), ("sphere", 3, 0.0), ("flat", 4, 0.0)])
 def test_energy_identity(kind, p, f0):
     """lambda^T S lambda = (1/tau)((H/g)||u||^2 + ||h||^2) + tau_s sum_K ||h - lambda||^2_dK
     for the local responses (u, h) to lambda with zero RHS; holds for any f
@@ -125,7 +126,7 @@ def test_asymmetry_scales_with_rotation():
     assert vals[2] / vals[1] == pytest.approx(2.0, rel=0.01)
 
 
-@pytest.mark.parametrize("kind,p", [("flat", 2), ("sphere", 2)])
+@pytest.mark.parametrize("kind,p", [("flat", 2), ("sphere", 2), ("flat", 3), ("sphere", 3), ("flat", 4)])
 def test_mass_conservation(kind, p):
     """psi = 1 on every cell plus mu = 1 on every facet: the facet fluxes cancel,
     so int h = int r_h exactly (up to roundoff) for the direct solve."""
@@ -150,7 +151,7 @@ def _l2_error(prob, mesh, u, h, exact):
     return math.sqrt(eu), math.sqrt(eh)
 
 
-@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_manufactured_convergence(p):
     """Sec. 7.3: L2 errors decrease at least like h^(p+1/2); p+1 is expected."""
     g, H, f0 = 1.0, 1.0, 1.0
@@ -167,11 +168,12 @@ def test_manufactured_convergence(p):
     assert (rates[-1] >= p + 0.5).all(), rates
 
 
-def test_fourier_closed_form():
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_fourier_closed_form(p):
     """Single Fourier mode on the periodic square with constant f: the
     continuous solution is a 3x3 complex solve per mode; the discrete error
     converges at order >= p + 1/2."""
-    p, g, H, f0, tau = 2, 1.0, 2.0, 0.7, 0.05
+    g, H, f0, tau = 1.0, 2.0, 0.7, 0.05
     kv = 2 * math.pi * np.array([1.0, 2.0])
     Mc = np.array([[1, -tau * f0, 1j * tau * g * kv[0]],
                    [tau * f0, 1, 1j * tau * g * kv[1]],
