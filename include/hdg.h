@@ -41,7 +41,9 @@
  * copies what it keeps.  The handle owns its device memory.  Every function
  * returns HDG_OK (0) or a negative HDG_E* code; hdg_last_error() describes
  * the last failure on a handle.  A handle must not be used by two host
- * threads at once.  Host-pointer entry points copy to and from the device
+ * threads at once.  A handle belongs to the CUDA device that was current at
+ * hdg_setup: make that device current for every call on it; a device reset
+ * invalidates every handle on that device.  Host-pointer entry points copy to and from the device
  * and synchronise; *_dev entry points take device pointers, run on the
  * handle's stream and return once the work is enqueued (they synchronise only
  * where a result decides the control flow, e.g. the convergence test).
@@ -223,19 +225,22 @@ HDG_API int hdg_trace_apply_dev(hdg_handle *h, const double *x, double *y);
 /* g = sum_K P_K^T C_K A_K^-1 F_K, the condensed right-hand side of step 1. */
 HDG_API int hdg_condensed_rhs_dev(hdg_handle *h, const double *r_u, const double *r_h, double *g);
 /* Same result as hdg_condensed_rhs_dev, for callers that must not cause any
- * device allocation once the handle exists (e.g. an application that gives
- * all device memory to its own pool up front, or code that records a CUDA
- * graph, during which allocation calls are not allowed).  The paper has no
- * counterpart: this is an engineering variant.  Its scratch is a fixed
- * 32 MiB array inside the library's device image, shared by every call on
- * the device and kept by every GPU that loads the library until the process
- * exits; sizes needing more than 2^22 doubles (n_cells * 3(p+1) +
- * n_facets * (p+1)) return HDG_EINVAL.  It calls no cudaMalloc / cudaFree and
- * no allocating library routine.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current, so
- * make that first call before any stream capture.  The array keeps the last
- * call's contents; calls whose GPU work overlaps (two streams, two handles on
- * one device) race on it and must be serialised by the caller. */
+ * device allocation once their handles exist: an application that hands all
+ * device memory to its own pool at start-up (a late allocation by a library
+ * would fail or force the pool to give memory back), or one that cannot
+ * afford the device-wide synchronisation that cudaMalloc / cudaFree may
+ * impose on its other streams.  The paper has no counterpart: this is an
+ * engineering variant.  Its scratch is a fixed 32 MiB array (2^22 doubles)
+ * inside the library's device image, shared by every call on the device;
+ * sizes needing more (n_cells * 3(p+1), rounded up to 32, plus
+ * n_facets * (p+1) doubles) return HDG_EINVAL.  hdg_setup places the array on
+ * the handle's device and looks up its device address there; from then on
+ * the device keeps it until the process exits, and this call allocates
+ * nothing: no cudaMalloc / cudaFree, no allocating library routine, no
+ * module load.  The array keeps the last call's contents (nothing in it has
+ * to start at zero: every entry a call reads, that call wrote first); calls
+ * whose GPU work overlaps (two streams, two handles on one device) race on it
+ * and must be serialised by the caller.  HDG_ESTATE before hdg_condense. */
 HDG_API int hdg_condensed_rhs_noalloc_dev(hdg_handle *h, const double *r_u, const double *r_h, double *g);
 /* z = V(v): one application of the two-level V-cycle (Alg. twolevel_vcycle)
  * with zero initial guess. */

@@ -200,6 +200,14 @@ cudaError_t klaunch(hdg_handle *h, int cat, int nk, F &&f) {
 }
 #define KL(cat, nk, expr) klaunch(h, (cat), (nk), [&]() { return (expr); })
 
+}  // namespace
+
+cudaError_t hdg::account_launch(hdg_handle *h, int cat, int nk, const std::function<cudaError_t()> &fn) {
+    return klaunch(h, cat, nk, fn);
+}
+
+namespace {
+
 template <typename T> constexpr int cat_apply() { return sizeof(T) == 8 ? HDG_PROF_APPLY64 : HDG_PROF_APPLY32; }
 template <typename T> constexpr int cat_res() { return sizeof(T) == 8 ? HDG_PROF_RESIDUAL64 : HDG_PROF_RESIDUAL32; }
 template <typename T> constexpr int cat_smooth() { return sizeof(T) == 8 ? HDG_PROF_SMOOTH64 : HDG_PROF_SMOOTH32; }
@@ -467,7 +475,11 @@ cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out, Host
 
 // Wait until the page-locked HostValue carries sequence number want: spin,
 // checking the stream every 256 polls (an error, or a finished stream
-// without the number, ends the wait with HDG_ECUDA).
+// without the number, ends the wait with HDG_ECUDA).  There is no host-side
+// time limit: the loop ends because the stream ends, and the stream ends
+// because every wait inside the library's kernels is bounded by an iteration
+// count (the coarse-cycle staging and the learned sweep's MMA waits set a
+// status bit and return when theirs runs out).
 int wait_host_value(hdg_handle *h, int32_t want) {
     Workspace &W = *h->ws;
     const volatile int32_t *seq = &W.host_val->seq;
@@ -552,7 +564,8 @@ cudaError_t arnoldi_step(hdg_handle *h, int j) {
 // Wait for Arnoldi step j's readback: spin on the step number that the
 // Gram-Schmidt kernel writes last into the page-locked copy, checking the
 // stream every 256 polls (an error, or a finished stream without the number,
-// ends the wait with HDG_ECUDA).
+// ends the wait with HDG_ECUDA).  Like wait_host_value, it relies on every
+// device-side wait of the library being bounded.
 int wait_readback(hdg_handle *h, int j) {
     Workspace &W = *h->ws;
     const volatile int32_t *seq = &W.host_rb->seq;
@@ -1205,8 +1218,10 @@ int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solv
         int32_t st = 0;
         TRY(cudaMemcpyAsync(&st, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         TRY(cudaStreamSynchronize(s));
-        if (st & 8) {
-            rc = fail(h, HDG_ETIMEOUT, "a bounded device-side wait ran out (coarse-cycle staging)");
+        if (st & (8 | 16)) {
+            rc = fail(h, HDG_ETIMEOUT, (st & 8) ? "a bounded device-side wait ran out (coarse-cycle staging)"
+                                                : "a bounded device-side wait ran out (tensor-core MMA of the "
+                                                  "learned sweep)");
             TRY(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), s));
         }
     }
@@ -1283,6 +1298,13 @@ int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hd
         h->own_stream = true;
     }
     int rc = setup_device(h, prm);
+    if (!rc) {
+        // the device this handle lives on, and the no-allocation scratch array
+        // loaded onto it now rather than inside a later call
+        cudaError_t ce = cudaGetDevice(&h->device);
+        if (ce == cudaSuccess) ce = noalloc_prepare(h);
+        if (ce != cudaSuccess) rc = fail(h, HDG_ECUDA, std::string("no-allocation scratch: ") + cudaGetErrorString(ce));
+    }
     if (rc) {
         std::string msg = h->err;
         free_handle(h);

@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -321,7 +322,11 @@ struct hdg_handle {
     double *d_Dinv = nullptr;       // (p+1)^2 values per facet, packed likewise
     float *d_Sval32 = nullptr, *d_Dinv32 = nullptr;
     __nv_bfloat16 *d_Sval16 = nullptr;   // preconditioner copy (HDG_MIXED_BF16)
-    int32_t *d_status = nullptr;    // device error flags
+    int32_t *d_status = nullptr;    // device error flags: 1 zero pivot in A_K, 2 singular facet block,
+                                    // 4 singular coarsest P1 operator, 8 coarse-cycle staging wait ran
+                                    // out, 16 learned-sweep MMA wait ran out
+    int device = -1;                // CUDA device current at hdg_setup
+    double *noalloc_scratch = nullptr;   // device address of the fixed scratch array (noalloc.cu)
 
     std::vector<hdg::DevLevel> lev;
     int tail_start[2] = {0, 0};       // first P1 level of the single-CTA tail kernel (FP64, FP32)
@@ -366,6 +371,14 @@ inline bool mode_pre32(const hdg_params &p) { return p.precision == HDG_MIXED_FG
         case 4: { constexpr int P = 4; CALL; } break; \
         default: return cudaErrorInvalidValue;        \
     }
+
+// Kernel accounting for entry points defined outside api.cu: counts nk
+// launches in category cat and, with timing on, brackets what fn enqueues
+// with events on the handle's stream (see hdg_profile_enable).
+cudaError_t account_launch(hdg_handle *h, int cat, int nk, const std::function<cudaError_t()> &fn);
+// Look up the device address of the no-allocation scratch array on the
+// current device and keep it in the handle (noalloc.cu; called by hdg_setup).
+cudaError_t noalloc_prepare(hdg_handle *h);
 
 cudaError_t launch_condense(hdg_handle *h);
 cudaError_t launch_assemble(hdg_handle *h);

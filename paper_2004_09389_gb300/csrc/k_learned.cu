@@ -184,7 +184,7 @@ __device__ __forceinline__ bool umma_wait(uint64_t *bar, uint32_t phase, int *fl
         if (!ok) {
             // record it and give the MMAs one more bounded wait before the
             // tensor memory they write is freed
-            atomicOr(status, 8);
+            atomicOr(status, 16);
             for (long long it = 0; it < (1ll << 24); ++it) {
                 uint32_t d;
                 asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"

@@ -85,8 +85,6 @@ __device__ __forceinline__ void facet_rows_packed(const ST *__restrict__ Sval, i
         Pack<ST>::unpack(v, o);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            constexpr int dummy = 0;
-            (void)dummy;
             const int j = q * G + g;
             if (j < NS) {
                 const int r = j / (5 * PP), rem = j % (5 * PP), b = rem / PP, c = rem % PP;

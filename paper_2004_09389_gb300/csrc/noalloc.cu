@@ -4,39 +4,34 @@
 // solver workspace.  hdg_condensed_rhs_noalloc_dev computes exactly the same
 // thing with that scratch in a fixed array that lives in this library's
 // device image instead, so the call itself never allocates.
+//
+// The library is linked from separate objects, so this file is a module of
+// its own; under lazy module loading the array is only placed on a device
+// when something first touches the module.  hdg_setup does that
+// (noalloc_prepare), so that the entry point never triggers the load.
 #include "common.h"
-
-#include <mutex>
 
 namespace {
 
-// Scratch: the per-cell products W_K r_K (n_cells * 3(p+1) doubles) followed by
-// the right-hand side in the internal node-major layout (n_facets * (p+1)).
+// Scratch: the per-cell products W_K r_K (n_cells * 3(p+1) doubles, rounded
+// up to 32) followed by the right-hand side in the internal node-major layout
+// (n_facets * (p+1)).
 constexpr size_t kScratchDoubles = size_t(1) << 22;      // 32 MiB
 static __device__ __align__(256) double g_rhs_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-double *g_scratch_addr[kMaxDevices] = {};
+}  // namespace
 
-// Device address of g_rhs_scratch on the current device (looked up once per device).
-cudaError_t scratch_address(double **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+// Called by hdg_setup with the handle's device current: loads this module on
+// that device (if it is not loaded yet) and keeps the array's device address
+// in the handle.  In host code g_rhs_scratch is only a host-side stand-in, so
+// the address must come from cudaGetSymbolAddress.
+cudaError_t hdg::noalloc_prepare(hdg_handle *h) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_rhs_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_rhs_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_addr[dev];
+    h->noalloc_scratch = static_cast<double *>(p);
     return cudaSuccess;
 }
-
-}  // namespace
 
 extern "C" int hdg_condensed_rhs_noalloc_dev(hdg_handle *h, const double *r_u, const double *r_h, double *g) {
     if (!h) return HDG_EINVAL;
@@ -56,17 +51,16 @@ extern "C" int hdg_condensed_rhs_noalloc_dev(hdg_handle *h, const double *r_u, c
         h->err = "hdg_condense has not run on this handle";
         return HDG_ESTATE;
     }
-    double *scratch = nullptr;
-    cudaError_t e = scratch_address(&scratch);
-    if (e != cudaSuccess) {
-        h->err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-        return HDG_ECUDA;
+    if (!h->noalloc_scratch) {
+        h->err = "hdg_condensed_rhs_noalloc_dev: the scratch address was not resolved at set-up";
+        return HDG_ESTATE;
     }
-    // every scratch entry read by the gather is written first by the cell kernel:
-    // nothing has to start at zero
-    double *ycell = scratch, *g_int = scratch + cell_part;
-    e = hdg::launch_rhs(h, r_u, r_h, g_int, ycell);
-    if (e == cudaSuccess) e = hdg::launch_to_external(h, g_int, g);
+    // every scratch entry read by the gather is written first by the cell kernel
+    // of the same call: nothing has to start at zero
+    double *ycell = h->noalloc_scratch, *g_int = h->noalloc_scratch + cell_part;
+    cudaError_t e = hdg::account_launch(h, HDG_PROF_RHS, 2, [&]() { return hdg::launch_rhs(h, r_u, r_h, g_int, ycell); });
+    if (e == cudaSuccess)
+        e = hdg::account_launch(h, HDG_PROF_LAYOUT, 1, [&]() { return hdg::launch_to_external(h, g_int, g); });
     if (e != cudaSuccess) {
         h->err = std::string("hdg_condensed_rhs_noalloc_dev: ") + cudaGetErrorString(e);
         return HDG_ECUDA;

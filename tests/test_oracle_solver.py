@@ -191,8 +191,8 @@ def test_rotating_coarse_operator_fourier_symbol():
 
 def test_rotating_coarse_operator_helps_under_rotation():
     """Sphere, f tau ~ 2: the coarse problem with rotation needs fewer FGMRES
-    iterations than the rotation-free one; both converge (SURVEY-style check of
-    the reading, not a value printed in the paper)."""
+    iterations than the rotation-free one; both converge (a check of the
+    reading, not a value printed in the paper)."""
     R, om = 6.371e6, 7.292e-5
     mesh = I.sphere_hierarchy(4, R, r_coarsest=1)
     g, H = 9.81, 7500.0
