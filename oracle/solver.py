@@ -203,13 +203,13 @@ class TwoLevelPreconditioner:
         self.prob, self.S = prob, S
         self.n_pre, self.n_post, self.omega = n_pre, n_post, omega
         pp = prob.prm.p + 1
-        # facet diagonal blocks D_e and their inverses
+        # facet diagonal blocks D_e (rows and columns e(p+1) .. e(p+1)+p of S)
+        # and their inverses, block-diagonal
         Sd = S.tocsr()
-        blocks = []
-        for e in range(prob.n_facets):
-            idx = np.arange(e * pp, (e + 1) * pp)
-            blocks.append(np.linalg.inv(Sd[idx][:, idx].toarray()))
-        self.Dinv = sp.block_diag(blocks, format="csr")
+        nf = prob.n_facets
+        idx = np.arange(nf)[:, None] * pp + np.arange(pp)[None, :]
+        D = np.asarray(Sd[np.repeat(idx, pp, axis=1).ravel(), np.tile(idx, (1, pp)).ravel()]).reshape(nf, pp, pp)
+        self.Dinv = sp.bsr_matrix((np.linalg.inv(D), np.arange(nf), np.arange(nf + 1)), shape=S.shape).tocsr()
         nv = mesh.n_vertices
         self.Pi = injection(prob, nv)
         tau, g, H = prob.prm.tau, prob.prm.g, prob.prm.H
