@@ -198,56 +198,106 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_sample(p: int, courant: float, steps: int, seed: int = 0, kind: str = "flat") -> dict:
+def host_threads() -> dict:
+    """Host cores and the thread settings the oracle process runs with."""
+    try:
+        avail = len(os.sched_getaffinity(0))
+    except AttributeError:
+        avail = os.cpu_count()
+    return {"nproc": avail, "cpu_count": os.cpu_count(),
+            **{k: os.environ.get(k, "unset") for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}}
+
+
+def oracle_run(p: int, courant: float, warmup: int, steps: int, seed: int = 0, kind: str = "flat",
+               full: bool = True, direct: bool = False) -> dict:
     """Time the oracle (plain FP64 FGMRES + V-cycle, as it stands) on the
-    sample mesh; run in a spawned single-threaded process."""
+    benchmark workload (full = True) or its small sample: set-up (cell
+    operators, trace operator, preconditioner) once and untimed, then `warmup`
+    untimed and `steps` timed solves, each one condensed right-hand side,
+    FGMRES(30) to 1e-8 and recovery.  direct = True also times SciPy's sparse
+    LU of the trace operator (factor and solve), the analogue of the paper's
+    direct-solver comparison."""
     import numpy as np
     from oracle.hdg import HDGProblem
     from oracle.solver import TwoLevelPreconditioner, gmres
-    wl = make_workload(kind, False, p, courant, seed)
+    t_all = time.perf_counter()
+    wl = make_workload(kind, full, p, courant, seed)
     mesh, tau, f, ru, rh = wl["mesh"], wl["tau"], wl["f"], wl["ru"], wl["rh"]
+    t0 = time.perf_counter()
     prob = HDGProblem(mesh, p, tau=tau, g=wl["g"], H=wl["H"], f_vertex=f)
     S = prob.trace_operator()
     pc = TwoLevelPreconditioner(prob, mesh, S, coarse="gmg")
-    times, iters = [], []
-    for _ in range(steps):
+    setup_s = time.perf_counter() - t0
+    times, iters, res = [], [], []
+    for k in range(warmup + steps):
         t0 = time.perf_counter()
         gvec = prob.condensed_rhs(ru, rh)
         lam, info = gmres(lambda v: S @ v, gvec, pc, restart=30, rtol=1e-8)
         prob.recover(lam, ru, rh)
-        times.append(time.perf_counter() - t0)
-        iters.append(info["iters"])
-    return {"sec_per_solve": float(np.median(times)), "iters": iters, "n_cells": mesh.n_cells}
+        if k >= warmup:
+            times.append(time.perf_counter() - t0)
+            iters.append(info["iters"])
+            res.append(float(info["true_rel_res"]))
+    out = {"sec_per_solve": float(np.median(times)), "sec_total": float(np.sum(times)), "times": times,
+           "iters": iters, "true_rel_res": res, "n_cells": mesh.n_cells, "setup_s": setup_s, **host_threads()}
+    if direct:
+        import scipy.sparse.linalg as spla
+        gvec = prob.condensed_rhs(ru, rh)
+        t0 = time.perf_counter()
+        lu = spla.splu(S.tocsc())
+        t1 = time.perf_counter()
+        x = lu.solve(gvec)
+        t2 = time.perf_counter()
+        out["direct"] = {"factor_s": t1 - t0, "solve_s": t2 - t1, "lu_nnz": int(lu.L.nnz + lu.U.nnz),
+                         "true_rel_res": float(np.linalg.norm(gvec - S @ x) / np.linalg.norm(gvec))}
+    out["wall_s"] = time.perf_counter() - t_all
+    return out
 
 
-def run_oracle_subprocess(p: int, courant: float, steps: int, kind: str = "flat") -> dict:
+def oracle_command(p: int, courant: float, warmup: int, steps: int, kind: str = "flat", direct: bool = False):
+    """The oracle runs in a process of its own, single-threaded (SciPy's sparse
+    products are single-threaded anyway; BLAS pinned to one thread)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--p", str(p), "--courant", str(courant),
-           "--steps", str(steps), "--workload", kind]
-    res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
-    if res.returncode != 0:
-        raise RuntimeError(f"oracle sample failed: {res.stderr[-2000:]}")
-    return json.loads(res.stdout.strip().splitlines()[-1])
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-run", "--p", str(p), "--courant", str(courant),
+           "--warmup", str(warmup), "--steps", str(steps), "--workload", kind] + (["--cpu-direct"] if direct else [])
+    return cmd, env
 
 
-def sample_text(kind: str) -> tuple:
-    """(sample description, cells of the full workload)"""
-    if kind == "sphere":
-        return f"icosahedral sphere r={SAMPLE_R}", 20 * 4 ** SPHERE_R
-    return f"{SAMPLE_N}x{SAMPLE_N}x2", 2 * NGRID * NGRID
+def oracle_start(p, courant, warmup, steps, kind="flat", direct=False):
+    """Start the oracle process now (before any CUDA call); collect it with oracle_wait."""
+    import tempfile
+    cmd, env = oracle_command(p, courant, warmup, steps, kind, direct)
+    out = tempfile.TemporaryFile(mode="w+")
+    err = tempfile.TemporaryFile(mode="w+")
+    return subprocess.Popen(cmd, stdout=out, stderr=err, env=env, text=True), out, err
 
 
-def cpu_baseline_entry(p, courant, steps, kind="flat"):
-    t0 = time.perf_counter()
-    r = run_oracle_subprocess(p, courant, steps, kind)
-    desc, n_full = sample_text(kind)
-    val = (1.0 / r["sec_per_solve"]) * (r["n_cells"] / n_full)
-    return {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"{desc} = {r['n_cells']} triangles of the same workload (same p, Courant, "
-                       f"RHS generator), {steps} solves, median time per solve scaled to {n_full:,} triangles by the "
-                       f"cell ratio; single-threaded NumPy/SciPy"),
-            "sec_per_solve_sample": r["sec_per_solve"], "iters": r["iters"],
-            "wall_s": time.perf_counter() - t0}
+def oracle_wait(handle, timeout=3600) -> dict:
+    proc, out, err = handle
+    rc = proc.wait(timeout=timeout)
+    out.seek(0)
+    err.seek(0)
+    if rc != 0:
+        raise RuntimeError(f"oracle run failed: {err.read()[-2000:]}")
+    return json.loads(out.read().strip().splitlines()[-1])
+
+
+def oracle_sample_text(r: dict, kind: str, name: str) -> str:
+    return (f"the full workload ({name}): {len(r['times'])} timed solve(s) after {r['setup_s']:.0f} s of untimed "
+            f"set-up, each one condensed RHS, FGMRES(30) + V-cycle to 1e-8 and recovery (median per solve); "
+            f"single-threaded NumPy/SciPy oracle, as it stands")
+
+
+def cpu_baseline_entry(r: dict, kind: str, name: str) -> dict:
+    val = 1.0 / r["sec_per_solve"]
+    entry = {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+             "sample": oracle_sample_text(r, kind, name), "sec_per_solve": r["sec_per_solve"],
+             "iters": r["iters"], "setup_s": r["setup_s"], "wall_s": r["wall_s"],
+             "host": {k: r[k] for k in ("nproc", "cpu_count", "OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                        "MKL_NUM_THREADS")}}
+    if "direct" in r:
+        entry["direct_splu"] = r["direct"]
+    return entry
 
 
 # ---------------------------------------------------------------- replicas
@@ -285,6 +335,9 @@ def gpu_arm(args, rank: int, world: int):
             dist.barrier()
         torch.cuda.synchronize()
 
+    from paper_2004_09389_gb300 import _lib as hdglib
+    fma = {"fp64_tflops": hdglib.fma_rate(8), "fp32_tflops": hdglib.fma_rate(4),
+           "how": "hdg_fma_rate: 8 independent FMA chains per thread, 8 x 256 threads per SM, CUDA events, best of 3"}
     wl = make_workload(args.workload, True, args.p, args.courant, args.seed + rank)
     mesh, tau, f, ru, rh, g_, H_ = wl["mesh"], wl["tau"], wl["f"], wl["ru"], wl["rh"], wl["g"], wl["H"]
     ru_d = torch.from_numpy(ru).to(dev)
@@ -335,11 +388,18 @@ def gpu_arm(args, rank: int, world: int):
         clk = clocks.stop(t_wall0, t_wall1) if clocks else None
         launches = sum(n for _, n in s.profile_read().values())
         ms = max_over_ranks(dist, ms, dev)
-        # second pass with per-kernel event timing for the roofline
+        # second pass with per-kernel event timing for the roofline (caches as the
+        # solve leaves them), third pass with L2 evicted before every timed launch
+        # (operands from DRAM: the HBM figure)
+        nprof = max(1, min(args.steps, 3))
         s.profile_enable(timing=True)
-        for _ in range(max(1, min(args.steps, 3))):
+        for _ in range(nprof):
             step()
         prof = s.profile_read()
+        s.profile_enable(timing=True, cold=True)
+        for _ in range(nprof):
+            step()
+        prof_cold = s.profile_read()
         s.profile_enable(timing=False)           # per-kernel events off again for the end-to-end pass
         # end to end through the host-pointer C-ABI calls (pinned host buffers)
         ru_h = torch.from_numpy(ru).pin_memory()
@@ -368,8 +428,9 @@ def gpu_arm(args, rank: int, world: int):
         d2h = lam_h.numel() * 8 + u_h.numel() * 8 + hh_h.numel() * 8
         levels = [mesh] + list(mesh.levels)
         nK, m = 3 * s.n_p, 3 * pp
-        out[arm] = dict(ms=ms, infos=infos, clocks=clk, launches=launches, prof=prof, e2e_s=e2e_s,
-                        condense_ms=condense_ms, n_p=s.n_p, prof_steps=max(1, min(args.steps, 3)), tuned=tuned,
+        out[arm] = dict(ms=ms, infos=infos, clocks=clk, launches=launches, prof=prof, prof_cold=prof_cold,
+                        e2e_s=e2e_s, levels_nv=[lv.n_vertices for lv in levels],
+                        condense_ms=condense_ms, n_p=s.n_p, prof_steps=nprof, tuned=tuned,
                         h2d=h2d, d2h=d2h, NF=NF, pp=pp, n_cells=s.n_cells,
                         coarse=(f"P1 geometric V-cycle over {len(levels)} levels, {levels[0].n_vertices:,} -> "
                                 f"{levels[-1].n_vertices} vertices (dense coarsest solve)"),
@@ -378,7 +439,7 @@ def gpu_arm(args, rank: int, world: int):
         torch.cuda.empty_cache()
     if dist is not None:
         dist.destroy_process_group()
-    return out
+    return out, fma
 
 
 def whole_solve(arm: dict, peaks: dict, steps: int) -> dict:
@@ -404,29 +465,121 @@ def whole_solve(arm: dict, peaks: dict, steps: int) -> dict:
             "counted": "facet-row kernels, condensed RHS, recovery (P1 V-cycle and Krylov vectors not counted)"}
 
 
-def roofline(arm: dict, peaks: dict, bf16_pre: bool = False) -> dict:
-    prof, NF, pp = arm["prof"], arm["NF"], arm["pp"]
-    cats = [c for c in prof if c.startswith(("apply", "residual", "smooth"))]
+def fp64_fmas_per_facet(cat: str, pp: int) -> int:
+    """FMAs per facet of an FP64 facet-row kernel (operator blocks, inverse block)."""
+    base = cat[:-2]
+    return {"apply": 5 * pp * pp, "residual": 5 * pp * pp, "smooth": 6 * pp * pp, "smooth_first": pp * pp}[base]
+
+
+def p1_cycle_bytes(levels_nv: list, w: int, width: int = 8) -> float:
+    """Algorithmic bytes of one P1 V-cycle (2 + 2 Jacobi sweeps per level): each
+    sweep reads the padded ELL values and columns, the inverse diagonal, b and x
+    and writes x; the residual reads the operator, b and x and writes r; the
+    transfers read and write each level's vector once; the coarsest level reads
+    its dense FP64 inverse."""
+    total = 0.0
+    for nv in levels_nv[:-1]:
+        sweep = nv * (width * (4 + w) + 4 * w)
+        total += 4 * sweep + nv * (width * (4 + w) + 3 * w) + 4 * nv * w
+    nc = levels_nv[-1]
+    return total + 8.0 * nc * nc + 16.0 * nc
+
+
+def _kernel_entry(name, prof, cold, cat, bytes_per_launch, peak, total_w, note=None):
+    ms_w, n_w = prof[cat]
+    ms_c, n_c = cold[cat]
+    if not n_w:
+        return None
+    e = {"kernel": name, "share_of_kernel_time": ms_w / total_w if total_w else None,
+         "launches": n_w, "avg_us_warm": ms_w * 1e3 / n_w, "avg_us_cold": ms_c * 1e3 / max(n_c, 1)}
+    if bytes_per_launch:
+        e.update({"algorithmic_bytes_per_launch": bytes_per_launch,
+                  "achieved_cold": bytes_per_launch * n_c / (ms_c * 1e-3) / 1e9 if ms_c > 0 else None,
+                  "achieved_warm": bytes_per_launch * n_w / (ms_w * 1e-3) / 1e9 if ms_w > 0 else None})
+        e["frac_cold"] = e["achieved_cold"] / peak if e["achieved_cold"] else None
+    if note:
+        e["note"] = note
+    return e
+
+
+def roofline(arm: dict, peaks: dict, fma: dict | None = None, bf16_pre: bool = False) -> dict:
+    """Roofline of the facet-row kernel with the largest share of the solve's
+    kernel time: algorithmic bytes per launch x launches over its CUDA-event
+    time with L2 evicted before every launch (cold: operands from DRAM), against
+    the measured HBM copy bandwidth; the same in the running solve (warm) as a
+    second figure.  FP64 facet-row kernels also get their FP64-pipe fraction
+    against the measured FMA rate.  `others` lists the remaining kernel
+    families with their shares."""
+    prof, cold, NF, pp = arm["prof"], arm["prof_cold"], arm["NF"], arm["pp"]
+    cats = [c for c in prof if c.startswith(("apply", "residual", "smooth")) and prof[c][1]]
     total = sum(ms for ms, _ in prof.values())
     best = max(cats, key=lambda c: prof[c][0])
-    ms, n = prof[best]
-    per_launch = trace_bytes(best, NF, pp, 2 if (bf16_pre and best.startswith("smooth") and best.endswith("32")
-                                                 and not best.startswith("smooth_first")) else None)
-    achieved = per_launch * n / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    bf16_op = bf16_pre and best.startswith("smooth") and best.endswith("32") and not best.startswith("smooth_first")
+    per_launch = trace_bytes(best, NF, pp, 2 if bf16_op else None)
+    ms_c, n_c = cold[best]
+    ms_w, n_w = prof[best]
+    achieved = per_launch * n_c / (ms_c * 1e-3) / 1e9 if ms_c > 0 else 0.0
+    warm = per_launch * n_w / (ms_w * 1e-3) / 1e9 if ms_w > 0 else 0.0
     peak = peaks.get("hbm_gbs", 6800.0)
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        tr = json.load(open(tpath))
-        ent = tr.get(f"{best}_p{pp - 1}")
-        if ent and ent.get("source_sha") == source_sha():
-            traffic = ent["bytes_per_launch"]
+    traffic = stored_traffic(best, pp - 1, "bf16" if bf16_op else ("fp64" if best.endswith("64") else "fp32"))
     family_ms = sum(prof[c][0] for c in cats)
-    return {"bound": "hbm", "kernel": best, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes_per_launch": per_launch,
-            "launches": n, "avg_us": ms * 1e3 / max(n, 1), "share_of_kernel_time": ms / total if total else None,
-            "facet_row_family_share": family_ms / total if total else None,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback"}
+    out = {"bound": "hbm", "kernel": best, "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes_per_launch": per_launch,
+           "launches": n_c, "avg_us": ms_c * 1e3 / max(n_c, 1),
+           "timing": "CUDA events on the handle's stream; L2 evicted (3 x L2 read) before every launch",
+           "warm": {"achieved": warm, "frac": warm / peak, "avg_us": ms_w * 1e3 / max(n_w, 1),
+                    "timing": "CUDA events in the running solve (part of the operator L2-resident)"},
+           "share_of_kernel_time": ms_w / total if total else None,
+           "facet_row_family_share": family_ms / total if total else None,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
+    if best.endswith("64") and fma:
+        fl = 2.0 * fp64_fmas_per_facet(best, pp) * NF * n_c / (ms_c * 1e-3) / 1e12
+        out["fp64_pipe"] = {"achieved_tflops": fl, "peak_tflops": fma["fp64_tflops"],
+                            "frac": fl / fma["fp64_tflops"], "peak_source": "hdg_fma_rate (of measured)"}
+    # the other kernel families of the solve
+    N, nK, m = arm["n_cells"], 3 * arm["n_p"], 3 * pp
+    w32 = 4 if (prof["smooth32"][1] or prof["smooth_first32"][1]) else 8
+    ncyc = max(prof["smooth_first32"][1] + prof["smooth_first64"][1], 1)
+    others = [
+        _kernel_entry("P1 V-cycle (all P1 kernels)", prof, cold, "p1",
+                      p1_cycle_bytes(arm["levels_nv"], w32) * ncyc / max(prof["p1"][1], 1), peak, total,
+                      "levels up to 32,768 vertices are L2-resident in the running solve: latency-bound"),
+        _kernel_entry("recover", prof, cold, "recover", 8.0 * N * (nK * nK + nK * m + 3 * nK + m), peak, total),
+        _kernel_entry("condensed RHS (cell + gather kernels)", prof, cold, "rhs",
+                      8.0 * N * (m * nK + nK + m) / 2, peak, total),
+        _kernel_entry("Krylov (Gram-Schmidt update with norm and Givens, dots, scalings)", prof, cold, "krylov",
+                      None, peak, total, "reductions of (j+1) values per iteration: latency of the grid-wide sum"),
+        _kernel_entry("restriction / prolongation", prof, cold, "transfer", None, peak, total),
+    ]
+    out["others"] = [e for e in others if e]
+    return out
+
+
+def condense_rate(arm: dict, fma: dict) -> dict:
+    """FP64 flop rate of the condensation against the measured FP64 FMA rate.
+    Per cell: Gauss-Jordan elimination of [A_K | B_K | Mass_K] (n_K x (2 n_K + m),
+    sum over pivots k of n_K (2 n_K + m - k - 1) FMAs), then S_K = Mt_K + C_K X_B
+    (m^2 n_K) and W_K = C_K R_M (m n_K^2)."""
+    nK, m, N = 3 * arm["n_p"], 3 * arm["pp"], arm["n_cells"]
+    lda = 2 * nK + m
+    fmas = sum(nK * (lda - k - 1) for k in range(nK)) + m * m * nK + m * nK * nK
+    tf = 2.0 * fmas * N / (arm["condense_ms"] * 1e-3) / 1e12
+    return {"flops_per_cell": 2 * fmas, "achieved_tflops": tf, "peak_tflops": fma["fp64_tflops"],
+            "frac": tf / fma["fp64_tflops"], "timing": "host wall clock around hdg_condense (one call, synchronised)",
+            "note": "includes the facet-row assembly, the P1 operators and the dense coarsest inverse"}
+
+
+def stored_traffic(cat: str, p: int, op: str):
+    """DRAM bytes per launch from an ncu capture (profiles/traffic.json), keyed by
+    kernel category, degree and operator type; None unless it was taken on the
+    current source of the facet-row kernels."""
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(tpath):
+        return None
+    ent = json.load(open(tpath)).get(f"{cat}_{op}_p{p}")
+    if ent and ent.get("source_sha") == source_sha():
+        return ent["bytes_per_launch"]
+    return None
 
 
 def source_sha() -> str:
@@ -723,11 +876,14 @@ def main():
     ap.add_argument("--reorth", type=int, default=0, choices=[0, 1],
                     help="Arnoldi orthogonalisation: 0 one classical Gram-Schmidt pass, 1 two passes")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--oracle-steps", type=int, default=3)
+    ap.add_argument("--oracle-steps", type=int, default=2,
+                    help="timed oracle solves for cpu_baseline (full workload, after one untimed set-up)")
+    ap.add_argument("--cpu-direct", dest="cpu_direct", action="store_true",
+                    help="also time SciPy's sparse LU of the trace operator in the oracle process")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--arms", default="mixed,mixed_bf16,fgmres64,fp64",
                     help="solver arms to run (profiling runs may pick one)")
-    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-run", dest="oracle_run", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--batch", type=int, default=0, help="run the batched-solve benchmark with this many problems")
     ap.add_argument("--autotune", action="store_true", help="autotune launch shapes per handle (off by default: on the 256x256x2 workload the defaults measured faster)")
     ap.add_argument("--clocks-csv", dest="clocks_csv", default="",
@@ -754,39 +910,44 @@ def main():
         sequence_main(args)
         return
 
-    if args.oracle_sample:
-        print(json.dumps(oracle_sample(args.p, args.courant, args.steps, kind=args.workload)))
+    if args.oracle_run:
+        print(json.dumps(oracle_run(args.p, args.courant, args.warmup, args.steps, kind=args.workload,
+                                    direct=args.cpu_direct)))
         return
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     name = workload_label(args.workload, args.p, args.courant, args.seed)
-    desc, n_full = sample_text(args.workload)
 
     if args.impl == "reference":
         if rank != 0:
             return
-        steps = args.warmup + args.steps
         t0 = time.perf_counter()
-        r = run_oracle_subprocess(args.p, args.courant, max(steps, 1), args.workload)
-        val = (1.0 / r["sec_per_solve"]) * (r["n_cells"] / n_full)
+        cmd, env = oracle_command(args.p, args.courant, args.warmup, args.steps, args.workload, args.cpu_direct)
+        res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=3600)
+        if res.returncode != 0:
+            raise RuntimeError(f"oracle run failed: {res.stderr[-2000:]}")
+        r = json.loads(res.stdout.strip().splitlines()[-1])
+        val = args.steps / r["sec_total"]
+        cb = cpu_baseline_entry(r, args.workload, name)
+        cb["value"] = val
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / val, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["sec_total"] / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": name, "rtol": args.rtol},
-                "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                 "sample": f"{desc} = {r['n_cells']} triangles per step, median "
-                                           f"time per solve scaled to {n_full:,} triangles by the cell ratio"},
+                "cpu_baseline": cb,
                 "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "iters": r["iters"], "wall_s": time.perf_counter() - t0}
         print(json.dumps(line))
         return
 
+    res, fma = gpu_arm(args, rank, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # spawned before the first CUDA call
-        cpu = cpu_baseline_entry(args.p, args.courant, args.oracle_steps, args.workload)
-    res = gpu_arm(args, rank, world)
+        # the oracle runs in a process of its own (exec'd, so it inherits no CUDA
+        # state) after the GPU arms: run beside them, it cost them a few per cent
+        cpu = cpu_baseline_entry(oracle_wait(oracle_start(args.p, args.courant, 0, args.oracle_steps, args.workload,
+                                                          args.cpu_direct)), args.workload, name)
     if rank != 0:
         return
     if set(res) != {"mixed", "mixed_bf16", "fgmres64", "fp64"}:
@@ -818,20 +979,22 @@ def main():
         "iters": it_mx, "true_rel_res": [i["true_rel_res"] for i in mx["infos"]],
         "plain_fp64": {"value": fp_value, "unit": "solves/s", "ms_per_step": fp["ms"] / K, "iters": it_fp,
                        "true_rel_res": [i["true_rel_res"] for i in fp["infos"]],
-                       "roofline": roofline(fp, peaks)},
+                       "roofline": roofline(fp, peaks, fma)},
         "mixed_bf16_smoother": {"value": world * K / (mb["ms"] * 1e-3), "unit": "solves/s",
                                 "ms_per_step": mb["ms"] / K, "iters": [i["iters"] for i in mb["infos"]],
                                 "true_rel_res": [i["true_rel_res"] for i in mb["infos"]],
-                                "roofline": roofline(mb, peaks, bf16_pre=True)},
+                                "roofline": roofline(mb, peaks, fma, bf16_pre=True)},
         "fp64_fgmres_fp32_preconditioner": {
             "value": world * K / (fg["ms"] * 1e-3), "unit": "solves/s", "ms_per_step": fg["ms"] / K,
             "iters": [i["iters"] for i in fg["infos"]], "true_rel_res": [i["true_rel_res"] for i in fg["infos"]],
             "e2e": {"value": world * K / fg["e2e_s"], "unit": "solves/s"},
             "precision": "FP64 FGMRES, orthogonalisation, residual, RHS, recovery; FP32 V-cycle, FP64 coarsest solve"},
         "speedup_vs_plain_fp64": value / fp_value,
-        "roofline": roofline(mx, peaks),
+        "roofline": roofline(mx, peaks, fma),
         "whole_solve": whole_solve(mx, peaks, K),
         "condense_ms": {"mixed": mx["condense_ms"], "fp64": fp["condense_ms"]},
+        "condense_fp64_pipe": condense_rate(fp, fma),
+        "measured_fma": fma,
         "kernel_ms": {k: v[0] for k, v in mx["prof"].items() if v[1]},
         "gpu_launches": mx["launches"],
         "clocks": mx["clocks"],

@@ -264,6 +264,11 @@ HDG_API int hdg_get_cell_schur(hdg_handle *h, double *S);
  * timing enabled every launch is bracketed by CUDA events on the handle's
  * stream and the elapsed times are summed per category (read at the
  * library's own synchronisation points).  hdg_profile_enable resets both.
+ * timing_on: 0 = counts only; 1 = event timing (caches as the solve leaves
+ * them); 2 = event timing with the L2 cache evicted before every timed launch
+ * (a buffer of three times the L2 size, allocated here, is read outside the
+ * events), so each kernel's operands come from DRAM.  While timing is on the
+ * Arnoldi steps run as direct launches instead of replayed graphs.
  * ms / launches: arrays of HDG_PROF_N entries (either may be NULL). */
 #define HDG_PROF_APPLY64        0   /* y = S x, FP64                         */
 #define HDG_PROF_RESIDUAL64     1   /* r = b - S x, FP64                     */
@@ -280,9 +285,17 @@ HDG_API int hdg_get_cell_schur(hdg_handle *h, double *S);
 #define HDG_PROF_RECOVER       12   /* step 3                                */
 #define HDG_PROF_LAYOUT        13   /* lambda layout conversions             */
 #define HDG_PROF_CONDENSE      14   /* condensation and assembly             */
-#define HDG_PROF_N             15
+#define HDG_PROF_IMEX          15   /* IMEX stage rates and combinations     */
+#define HDG_PROF_N             16
 HDG_API int hdg_profile_enable(hdg_handle *h, int timing_on);
 HDG_API int hdg_profile_read(hdg_handle *h, double *ms, int64_t *launches);
+
+/* Measured FMA throughput of this GPU in TFLOP/s (2 flops per FMA) for
+ * bytes = 8 (FP64) or 4 (FP32): independent FMA chains on every SM of the
+ * current device, timed by CUDA events (best of three launches).  The paper
+ * has no counterpart; it is the arithmetic roof the FP64 kernels are measured
+ * against.  HDG_EINVAL for other sizes. */
+HDG_API int hdg_fma_rate(int bytes, double *tflops);
 
 /* Learned facet-patch smoother (spec extension; the paper has no learned
  * component).  In the FP32 inner solves of the mixed modes it replaces the last
@@ -317,6 +330,47 @@ HDG_API int hdg_learned_enable(hdg_handle *h, int on);
  * n_params floats) for n residuals given on the device in the lambda layout
  * [n][n_facets][p+1] (FP32). */
 HDG_API int hdg_learned_loss_grad_dev(hdg_handle *h, const float *R, int n, float *grad, double *loss);
+
+/* IMEX time stepping around the solve (Sec. 3.3: Eq. theta_method and the
+ * IMEX Runge-Kutta form of Eqs. IMEX_HDG_I / IMEX_HDG_II; the tableaux of
+ * Sec. 5.1).  The semi-discrete system M dq/dt = N(q) + L(q) splits into the
+ * gravity-wave terms with the upwind stabilisation, L (implicit), and the
+ * Coriolis term, N (explicit, as in the paper):
+ *   L_u(q).w = g (h, div w) - g <lambda, w.n>_dK,
+ *   L_h(q) psi = -H (div u, psi) - tau_s <h - lambda, psi>_dK,
+ *   N_u(q).w = -(f u_perp, w),  N_h = 0,
+ * with lambda = {h} + H / (2 tau_s) (u_1.n_1 + u_2.n_2) on each facet (the
+ * transmission condition solved pointwise).  An implicit stage
+ * M Q - a_ii dt L(Q) = M r is this library's solve with f = 0 and
+ * tau = a_ii dt (re-condensed by hdg_set_tau when tau changes) followed by
+ * the recovery; explicit parts act through the inverse cell mass matrices on
+ * nodal function values.  The handle must have been set up with
+ * f_vertex = NULL (its implicit operator has no Coriolis term). */
+#define HDG_IMEX_THETA 0   /* (M + theta dt K) q1 = M q0 + dt (N(q0) - (1 - theta) K q0), K = -L    */
+#define HDG_IMEX_ARS2  1   /* ARS2(2,3,2): gamma = 1 - 1/sqrt(2), delta = -2 sqrt(2)/3, two solves     */
+#define HDG_IMEX_SSP2  2   /* SSP2(3,2,2): three implicit stages with a_ii = 1/2                       */
+#define HDG_IMEX_ARS3  3   /* ARS3(4,4,3): four implicit stages with a_ii = 1/2                        */
+/* Store the Coriolis field of the explicit term (host array [n_vertices], P1
+ * per cell like hdg_params.f_vertex; NULL: no rotation) and allocate the
+ * stage buffers (3 + 10 state vectors of n_cells * 3 n_p doubles).
+ * HDG_EINVAL if the handle was set up with a non-zero f_vertex. */
+HDG_API int hdg_imex_init(hdg_handle *h, const double *f_vertex);
+/* The stage rates of a state (device pointers, caller layouts u [N][2][n_p],
+ * h [N][n_p]): (nu, nh) = M^-1 N(q) (both NULL to skip) and (lu, lh) =
+ * M^-1 L(q), as nodal values.  Needs hdg_imex_init. */
+HDG_API int hdg_imex_rates_dev(hdg_handle *h, const double *u, const double *hh, double *nu, double *nh,
+                               double *lu, double *lh);
+/* Advance (u, h) (device pointers, updated in place) by one step of length dt
+ * of the scheme: for each stage i, r_i = q0 + dt sum_{j<i} (a_ij n~_j +
+ * a~_ij l~_j); Q_i = q0 for an explicit first stage, the stage solve of r_i
+ * where a~_ii != 0; then q1 = q0 + dt sum_i (b_i n~_i + b~_i l~_i), with
+ * n~ = M^-1 N, l~ = M^-1 L.  theta is used by HDG_IMEX_THETA only (0 < theta
+ * <= 1).  info (may be NULL) sums the stage solves' iterations and keeps the
+ * largest residual; the return value is the first non-OK stage status (the
+ * step is still completed unless it is HDG_ECUDA or HDG_ENAN).  Synchronises
+ * once per stage solve (the convergence test). */
+HDG_API int hdg_imex_step_dev(hdg_handle *h, int scheme, double theta, double dt, double *u, double *hh,
+                              hdg_solve_info *info);
 
 /* The CUDA stream (cudaStream_t) the handle runs on: the one given to
  * hdg_setup, or the non-blocking stream the handle created and owns. */

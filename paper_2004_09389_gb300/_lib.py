@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(HERE, "lib", "libhdg.so")
 HDG_OK, HDG_EINVAL, HDG_ESINGULAR, HDG_ENOCONV = 0, -1, -2, -3
 HDG_EBREAKDOWN, HDG_ENAN, HDG_ECUDA, HDG_ETIMEOUT, HDG_ENOMEM, HDG_ESTATE = -4, -5, -6, -7, -8, -9
 HDG_FP64, HDG_MIXED_FP32, HDG_MIXED_BF16, HDG_MIXED_FGMRES64 = 0, 1, 2, 3
+HDG_IMEX_THETA, HDG_IMEX_ARS2, HDG_IMEX_SSP2, HDG_IMEX_ARS3 = 0, 1, 2, 3
+IMEX_SCHEMES = {"theta": HDG_IMEX_THETA, "ARS2": HDG_IMEX_ARS2, "SSP2": HDG_IMEX_SSP2, "ARS3": HDG_IMEX_ARS3}
 
 ERROR_NAMES = {0: "HDG_OK", -1: "HDG_EINVAL", -2: "HDG_ESINGULAR", -3: "HDG_ENOCONV",
                -4: "HDG_EBREAKDOWN", -5: "HDG_ENAN", -6: "HDG_ECUDA", -7: "HDG_ETIMEOUT",
@@ -64,11 +66,12 @@ EXPORTS = ["hdg_default_params", "hdg_setup", "hdg_condense", "hdg_set_tau", "hd
            "hdg_last_error", "hdg_profile_enable", "hdg_profile_read", "hdg_condensed_rhs_noalloc_dev",
            "hdg_solve_batch_dev", "hdg_autotune", "hdg_get_stream", "hdg_learned_init",
            "hdg_learned_collect_dev", "hdg_learned_train", "hdg_learned_params", "hdg_learned_enable",
-           "hdg_learned_loss_grad_dev", "hdg_precond_apply32_dev"]
+           "hdg_learned_loss_grad_dev", "hdg_precond_apply32_dev", "hdg_fma_rate",
+           "hdg_imex_init", "hdg_imex_rates_dev", "hdg_imex_step_dev"]
 
-HDG_PROF_N = 15
+HDG_PROF_N = 16
 PROF_NAMES = ["apply64", "residual64", "smooth64", "smooth_first64", "apply32", "residual32", "smooth32",
-              "smooth_first32", "transfer", "p1", "krylov", "rhs", "recover", "layout", "condense"]
+              "smooth_first32", "transfer", "p1", "krylov", "rhs", "recover", "layout", "condense", "imex"]
 
 
 def load() -> C.CDLL:
@@ -110,6 +113,10 @@ def load() -> C.CDLL:
     lib.hdg_get_stream.restype = vp
     lib.hdg_profile_enable.argtypes = [vp, C.c_int]
     lib.hdg_profile_read.argtypes = [vp, vp, vp]
+    lib.hdg_fma_rate.argtypes = [C.c_int, vp]
+    lib.hdg_imex_init.argtypes = [vp, vp]
+    lib.hdg_imex_rates_dev.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.hdg_imex_step_dev.argtypes = [vp, C.c_int, C.c_double, C.c_double, vp, vp, C.POINTER(hdg_solve_info)]
     lib.hdg_last_error.argtypes = [vp]
     lib.hdg_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -166,3 +173,10 @@ def check(handle, rc: int, allow=()) -> int:
         msg = load().hdg_last_error(handle)
         raise HDGError(rc, msg.decode() if msg else "")
     return rc
+
+
+def fma_rate(nbytes: int) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current GPU for FP64 (8) or FP32 (4)."""
+    out = C.c_double(0.0)
+    check(None, load().hdg_fma_rate(int(nbytes), C.byref(out)))
+    return out.value

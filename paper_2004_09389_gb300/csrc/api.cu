@@ -192,6 +192,7 @@ cudaError_t klaunch(hdg_handle *h, int cat, int nk, F &&f) {
     P.launches[cat] += nk;
     if (!P.on) return f();
     cudaEvent_t a = prof_event(h), b = prof_event(h);
+    if (P.evict_buf) launch_l2_evict(P.evict_buf, P.evict_bytes, P.evict_sink, h->stream);
     cudaEventRecord(a, h->stream);
     cudaError_t e = f();
     cudaEventRecord(b, h->stream);
@@ -835,6 +836,9 @@ void free_handle(hdg_handle *h) {
     prof_flush(h);
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     h->prof.pool.clear();
+    imex_release(h);
+    if (h->prof.evict_buf) cudaFree(h->prof.evict_buf);
+    if (h->prof.evict_sink) cudaFree(h->prof.evict_sink);
     dfree(h->d_ref); dfree(h->d_X); dfree(h->d_fcell); dfree(h->d_facet_of); dfree(h->d_flip);
     dfree(h->d_facet_cell); dfree(h->d_facet_edge); dfree(h->d_facet_verts); dfree(h->d_v2f_ptr); dfree(h->d_v2f);
     dfree(h->d_nbr); dfree(h->d_Xb); dfree(h->d_Rm); dfree(h->d_W); dfree(h->d_Scell); dfree(h->d_Sval);
@@ -976,7 +980,10 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     std::vector<double> fcell(size_t(h->N) * 3, 0.0);
     if (prm->f_vertex)
         for (int K = 0; K < h->N; ++K)
-            for (int i = 0; i < 3; ++i) fcell[size_t(K) * 3 + i] = prm->f_vertex[hm.cells[3 * K + i]];
+            for (int i = 0; i < 3; ++i) {
+                fcell[size_t(K) * 3 + i] = prm->f_vertex[hm.cells[3 * K + i]];
+                if (fcell[size_t(K) * 3 + i] != 0.0) h->has_f = true;
+            }
     TRY(upload(&h->d_fcell, fcell, s));
     TRY(upload(&h->d_facet_of, hm.facet_of, s));
     TRY(upload(&h->d_flip, hm.flip, s));
@@ -1555,8 +1562,26 @@ int hdg_get_cell_schur(hdg_handle *h, double *S) {
 
 int hdg_profile_enable(hdg_handle *h, int timing_on) {
     if (!h) return HDG_EINVAL;
+    if (timing_on < 0 || timing_on > 2) return fail(h, HDG_EINVAL, "timing_on must be 0, 1 or 2");
     TRY(cudaStreamSynchronize(h->stream));
     prof_flush(h);
+    Prof &P = h->prof;
+    if (timing_on == 2 && !P.evict_buf) {
+        int dev = 0, l2 = 0;
+        TRY(cudaGetDevice(&dev));
+        TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+        P.evict_bytes = (size_t(3) * size_t(l2) + 15) / 16 * 16;
+        TRY(cudaMalloc(&P.evict_buf, P.evict_bytes));
+        TRY(cudaMalloc(reinterpret_cast<void **>(&P.evict_sink), sizeof(uint32_t)));
+        TRY(cudaMemsetAsync(P.evict_buf, 0x5a, P.evict_bytes, h->stream));
+        TRY(cudaStreamSynchronize(h->stream));
+    } else if (timing_on != 2 && P.evict_buf) {
+        cudaFree(P.evict_buf);
+        cudaFree(P.evict_sink);
+        P.evict_buf = nullptr;
+        P.evict_sink = nullptr;
+        P.evict_bytes = 0;
+    }
     h->prof.on = timing_on != 0;
     for (int i = 0; i < HDG_PROF_N; ++i) {
         h->prof.ms[i] = 0.0;

@@ -158,6 +158,19 @@ struct Learned {
     double *coef = nullptr, *nrm = nullptr;
 };
 
+// IMEX time stepping state (k_imex.cu)
+constexpr int kImexMaxStages = 5;
+struct Imex {
+    bool ready = false;
+    bool has_f = false;          // explicit Coriolis term present
+    size_t nq = 0;               // doubles of one state vector: N * 3 * n_p (u part, then h part)
+    double *fcell = nullptr;     // [N][3] Coriolis at the cell vertices (explicit term)
+    double *minv = nullptr;      // [n_p][n_p] inverse of the reference mass matrix
+    double *lam = nullptr;       // [PP][NF] upwind trace of the DG state
+    double *lam_out = nullptr;   // [NF][PP] trace solution of a stage solve
+    double *buf = nullptr;       // (3 + 2 kImexMaxStages) state vectors
+};
+
 // per-iteration readback of the Krylov driver (pinned host copy)
 // a scalar handed to the host through page-locked memory: the value, then
 // (after a system-scope fence) a sequence number the host waits for
@@ -278,6 +291,11 @@ struct TailArgs {
 // per-category kernel accounting (see hdg_profile_enable)
 struct Prof {
     bool on = false;
+    // cold-cache timing (hdg_profile_enable(h, 2)): a buffer of three times
+    // the L2 size read before every bracketed launch
+    void *evict_buf = nullptr;
+    size_t evict_bytes = 0;
+    uint32_t *evict_sink = nullptr;
     double ms[HDG_PROF_N] = {};
     int64_t launches[HDG_PROF_N] = {};
     struct Pending { int cat; cudaEvent_t a, b; };
@@ -338,6 +356,8 @@ struct hdg_handle {
     hdg::Workspace *ws = nullptr;
     hdg::Prof prof;
     hdg::Learned lc;
+    hdg::Imex imex;
+    bool has_f = false;               // a non-zero Coriolis field was given to hdg_setup
 };
 
 // ---------------------------------------------------------------- error helpers
@@ -379,6 +399,15 @@ cudaError_t account_launch(hdg_handle *h, int cat, int nk, const std::function<c
 // Look up the device address of the no-allocation scratch array on the
 // current device and keep it in the handle (noalloc.cu; called by hdg_setup).
 cudaError_t noalloc_prepare(hdg_handle *h);
+
+// read a buffer larger than L2 so that the next kernel's data comes from DRAM (k_measure.cu)
+cudaError_t launch_l2_evict(const void *buf, size_t bytes, uint32_t *sink, cudaStream_t s);
+
+// IMEX rates (k_imex.cu): upwind trace of the state, then M^-1 N(q) (nu, nh;
+// skipped when null) and M^-1 L(q) (lu, lh) per cell
+cudaError_t launch_imex_rates(hdg_handle *h, const double *u, const double *hh, double *nu, double *nh, double *lu,
+                              double *lh);
+void imex_release(hdg_handle *h);
 
 cudaError_t launch_condense(hdg_handle *h);
 cudaError_t launch_assemble(hdg_handle *h);

@@ -190,9 +190,31 @@ class HDGSolver:
                                       C.byref(loss)))
         return loss.value, g
 
+    # ---------------------------------------------------------------- IMEX time stepping
+    def imex_init(self, f_vertex=None) -> None:
+        """Explicit Coriolis field (host, [n_vertices]) for hdg_imex_step_dev."""
+        fv = None if f_vertex is None else np.ascontiguousarray(f_vertex, dtype=np.float64)
+        L.check(self.h, self.lib.hdg_imex_init(self.h, None if fv is None else fv.ctypes.data))
+
+    def imex_rates_dev(self, u, h, nu, nh, lu, lh) -> None:
+        """(nu, nh) = M^-1 N(q) (both None to skip), (lu, lh) = M^-1 L(q)."""
+        L.check(self.h, self._ordered(self.lib.hdg_imex_rates_dev, L._ptr(u), L._ptr(h), L._ptr(nu), L._ptr(nh),
+                                      L._ptr(lu), L._ptr(lh)))
+
+    def imex_step_dev(self, scheme, dt: float, u, h, theta: float = 0.5, allow_fail: bool = False) -> dict:
+        """One step of an IMEX scheme ("theta", "ARS2", "SSP2", "ARS3") on device (u, h), in place."""
+        info = L.hdg_solve_info()
+        code = L.IMEX_SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        rc = self._ordered(self.lib.hdg_imex_step_dev, code, C.c_double(theta), C.c_double(dt), L._ptr(u), L._ptr(h),
+                           C.byref(info))
+        L.check(self.h, rc, allow=(L.HDG_ENOCONV, L.HDG_EBREAKDOWN) if allow_fail else ())
+        return info.as_dict()
+
     # ---------------------------------------------------------------- accounting
-    def profile_enable(self, timing: bool = True) -> None:
-        L.check(self.h, self.lib.hdg_profile_enable(self.h, 1 if timing else 0))
+    def profile_enable(self, timing: bool = True, cold: bool = False) -> None:
+        """Launch counts always; with timing, per-category CUDA-event times; with
+        cold, the L2 cache is evicted before every timed launch."""
+        L.check(self.h, self.lib.hdg_profile_enable(self.h, (2 if cold else 1) if timing else 0))
 
     def profile_read(self) -> dict:
         ms = np.zeros(L.HDG_PROF_N)
