@@ -7,7 +7,8 @@ Test infrastructure only (see the package docstring).
   one call to the next is allowed), modified Gram-Schmidt Arnoldi, Givens
   rotations, stop on the *true* relative residual ``||b - A x|| / ||b||``.
 * ``TwoLevelPreconditioner``: Alg. twolevel_vcycle with initial guess zero:
-  n_pre damped block-Jacobi sweeps on the facet blocks, residual, restriction
+  n_pre damped block-Jacobi sweeps on the facet blocks (or n_pre steps of the
+  block-Jacobi-preconditioned Chebyshev iteration, "chebyshev"), residual, restriction
   ``r_c = pi^T r`` (pi = the natural injection of P1 into the trace space,
   Sec. 4.4, upwind), coarse solve, ``x += pi e_c``, n_post sweeps.
 * Coarse problem: the weak form of the second-order problem that the
@@ -196,12 +197,95 @@ class P1Multigrid:
         return x
 
 
+# ------------------------------------------------------------------ Chebyshev smoother
+#
+# The paper smooths with a Chebyshev iteration (Sec. 5.2.1 and the solver
+# configuration in the appendix: two Chebyshev steps, block-Jacobi/SOR
+# preconditioned).  Here it is the Chebyshev iteration for D^-1 S (D the
+# facet diagonal blocks) on an ellipse in the complex plane, centre theta on
+# the real axis and focal half-distance delta (delta^2 < 0 when the ellipse
+# is taller than wide, as under strong rotation).  With s_0 = 1/theta and
+# s_k = 1 / (2 theta - delta^2 s_{k-1}),
+#     x_1 = x_0 + s_0 D^-1 r_0,
+#     x_{k+1} = x_k + 2 s_k D^-1 r_k + delta^2 s_k s_{k-1} (x_k - x_{k-1}),
+# the error after n steps is T_n((theta - D^-1 S)/delta) / T_n(theta/delta)
+# applied to the initial error; only delta^2 enters, so everything stays real.
+# The ellipse is fitted to Ritz values of a few Arnoldi steps on D^-1 S:
+# real extent [lower b, b] with b = grow * max Re(ritz) (PETSc's default
+# Chebyshev bounds are 0.1 and 1.1 times the largest estimate), imaginary
+# semi-axis grown until it holds every Ritz value with Re >= lower b.
+
+def chebyshev_start_vector(n: int) -> np.ndarray:
+    """Deterministic Arnoldi start vector: v_i = 1 + ((37 i) mod 101) / 101 for
+    trace dof i in the lambda layout (facet-major, p+1 nodes per facet)."""
+    i = np.arange(n, dtype=np.int64)
+    return 1.0 + ((37 * i) % 101) / 101.0
+
+
+def arnoldi_ritz(apply_op, v0: np.ndarray, k: int) -> np.ndarray:
+    """Ritz values of k Arnoldi steps (modified Gram-Schmidt) from v0: the
+    eigenvalues of the leading k x k block of the Hessenberg matrix."""
+    n = v0.shape[0]
+    k = min(k, n)
+    V = np.zeros((k + 1, n))
+    Hm = np.zeros((k + 1, k))
+    V[0] = v0 / np.linalg.norm(v0)
+    m = k
+    for j in range(k):
+        w = apply_op(V[j])
+        for i in range(j + 1):
+            Hm[i, j] = w @ V[i]
+            w = w - Hm[i, j] * V[i]
+        Hm[j + 1, j] = np.linalg.norm(w)
+        if Hm[j + 1, j] <= 1e-14 * np.abs(Hm[:j + 1, j]).max():
+            m = j + 1                      # invariant subspace: the Ritz values are exact
+            break
+        V[j + 1] = w / Hm[j + 1, j]
+    return np.linalg.eigvals(Hm[:m, :m])
+
+
+def chebyshev_ellipse(ritz: np.ndarray, lower: float = 0.1, grow: float = 1.1):
+    """(theta, delta^2) of the ellipse fitted to the Ritz values (see above)."""
+    b = grow * float(np.max(ritz.real))
+    a = lower * b
+    d, A = 0.5 * (a + b), 0.5 * (b - a)
+    B2 = 0.0
+    for z in ritz:
+        if z.real >= a:
+            q = 1.0 - ((z.real - d) / A) ** 2
+            if q > 1e-3:
+                B2 = max(B2, z.imag ** 2 / q)
+    B2 *= grow * grow
+    return d, A * A - B2
+
+
+def chebyshev_polynomial(mu, theta: float, delta2: float, n: int):
+    """Error-reduction factor T_n((theta - mu)/delta) / T_n(theta/delta) of n
+    Chebyshev steps at the eigenvalue(s) mu of D^-1 S (closed form, complex)."""
+    dl = np.sqrt(complex(delta2))
+    if dl == 0:
+        return (1.0 - np.asarray(mu, dtype=complex) / theta) ** n
+
+    def T(z):
+        t0, t1 = np.ones_like(z), z
+        if n == 0:
+            return t0
+        for _ in range(n - 1):
+            t0, t1 = t1, 2 * z * t1 - t0
+        return t1
+
+    mu = np.asarray(mu, dtype=complex)
+    return T((theta - mu) / dl) / T(np.full_like(mu, theta / dl))
+
+
 class TwoLevelPreconditioner:
     def __init__(self, prob: HDGProblem, mesh, S: sp.csr_matrix, n_pre: int = 2, n_post: int = 2,
                  omega: float = 2.0 / 3.0, coarse: str = "gmg", coarse_mode: str = "rotating",
-                 p1_nu: tuple = (2, 2), p1_omega: float = 2.0 / 3.0):
+                 p1_nu: tuple = (2, 2), p1_omega: float = 2.0 / 3.0, smoother: str = "jacobi",
+                 cheb: tuple | None = None, cheb_steps: int = 20):
         self.prob, self.S = prob, S
         self.n_pre, self.n_post, self.omega = n_pre, n_post, omega
+        self.smoother = smoother
         pp = prob.prm.p + 1
         # facet diagonal blocks D_e (rows and columns e(p+1) .. e(p+1)+p of S)
         # and their inverses, block-diagonal
@@ -210,6 +294,13 @@ class TwoLevelPreconditioner:
         idx = np.arange(nf)[:, None] * pp + np.arange(pp)[None, :]
         D = np.asarray(Sd[np.repeat(idx, pp, axis=1).ravel(), np.tile(idx, (1, pp)).ravel()]).reshape(nf, pp, pp)
         self.Dinv = sp.bsr_matrix((np.linalg.inv(D), np.arange(nf), np.arange(nf + 1)), shape=S.shape).tocsr()
+        if smoother == "chebyshev":
+            if cheb is None:
+                ritz = arnoldi_ritz(lambda v: self.Dinv @ (S @ v), chebyshev_start_vector(S.shape[0]), cheb_steps)
+                cheb = chebyshev_ellipse(ritz)
+            self.cheb = (float(cheb[0]), float(cheb[1]))
+        elif smoother != "jacobi":
+            raise ValueError(smoother)
         nv = mesh.n_vertices
         self.Pi = injection(prob, nv)
         tau, g, H = prob.prm.tau, prob.prm.g, prob.prm.H
@@ -249,8 +340,21 @@ class TwoLevelPreconditioner:
             raise ValueError(coarse)
 
     def smooth(self, b: np.ndarray, x: np.ndarray, n: int) -> np.ndarray:
-        for _ in range(n):
-            x = x + self.omega * (self.Dinv @ (b - self.S @ x))
+        if self.smoother == "jacobi":
+            for _ in range(n):
+                x = x + self.omega * (self.Dinv @ (b - self.S @ x))
+            return x
+        if n == 0:
+            return x
+        theta, delta2 = self.cheb
+        s_prev = 1.0 / theta
+        d = s_prev * (self.Dinv @ (b - self.S @ x))
+        x = x + d
+        for _ in range(1, n):
+            s = 1.0 / (2.0 * theta - delta2 * s_prev)
+            d = delta2 * s * s_prev * d + 2.0 * s * (self.Dinv @ (b - self.S @ x))
+            x = x + d
+            s_prev = s
         return x
 
     def __call__(self, b: np.ndarray) -> np.ndarray:
