@@ -132,6 +132,17 @@ typedef struct {
                                        orthogonalisation option, i.e. the library default
                                        of classical Gram-Schmidt without refinement);
                                    1 = classical Gram-Schmidt twice (CGS2).              */
+    int32_t       smoother;     /* facet smoother of Alg. twolevel_vcycle (lines 1 and 6):
+                                   0 = damped block-Jacobi (omega);
+                                   1 = Chebyshev iteration preconditioned by block-Jacobi
+                                       (the paper's smoother is a Chebyshev iteration,
+                                       Sec. 5.2.1), tuned to an ellipse around the spectrum
+                                       of D^-1 S: stays contractive under strong rotation  */
+    double        cheb_theta;   /* smoother 1: ellipse centre; <= 0 selects the estimate
+                                   made at condensation (Arnoldi on D^-1 S)               */
+    double        cheb_delta2;  /* smoother 1: squared focal half-distance of the ellipse
+                                   (used only when cheb_theta > 0; < 0 for a tall ellipse) */
+    int32_t       cheb_steps;   /* smoother 1: Arnoldi steps of the estimate (2..64)      */
 } hdg_params;
 
 typedef struct {
@@ -145,7 +156,8 @@ typedef struct {
 
 /* Fill *prm with the defaults: p = 1, tau = 1, g = H = 1, tau_s = sqrt(gH),
  * FP64, rtol 1e-8, restart 30, max_iter 500, 2 + 2 sweeps, omega = 2/3,
- * 2 + 2 P1 sweeps, p1_omega = 2/3, inner_rtol 1e-4, coarse_mode 0, reorth 0. */
+ * 2 + 2 P1 sweeps, p1_omega = 2/3, inner_rtol 1e-4, coarse_mode 0, reorth 0,
+ * smoother 0 (cheb_theta 0: estimated, cheb_steps 20). */
 HDG_API void hdg_default_params(hdg_params *prm);
 
 /* Build a handle: validate and copy the mesh (facet numbering, orientation,
@@ -259,6 +271,17 @@ HDG_API int hdg_get_facets(const hdg_handle *h, int32_t *facet_of, int32_t *flip
 /* Per-cell S_K in the local trace order (edge i, node j along the edge from
  * local vertex (i+1)%3 to (i+2)%3), [n_cells][3(p+1)][3(p+1)].  Needs condense. */
 HDG_API int hdg_get_cell_schur(hdg_handle *h, double *S);
+
+/* The Chebyshev smoother's ellipse (smoother 1, after hdg_condense):
+ * ellipse[0] = theta, ellipse[1] = delta^2.  The estimate runs cheb_steps
+ * Arnoldi steps on D^-1 S (FP64 operator, classical Gram-Schmidt twice) from
+ * the start vector v_i = 1 + ((37 i) mod 101) / 101, i the index in the
+ * lambda layout; the ellipse spans [0.1 b, b] on the real axis with
+ * b = 1.1 max Re(Ritz) and is 1.1 times as tall as needed to hold every Ritz
+ * value in that range.  ritz (may be NULL) receives up to 64 Ritz values as
+ * (re, im) pairs, *n_ritz their number (0 when the ellipse was given).
+ * HDG_ESTATE if the handle does not use smoother 1 or is not condensed. */
+HDG_API int hdg_get_chebyshev(const hdg_handle *h, double *ellipse, double *ritz, int32_t *n_ritz);
 
 /* Kernel accounting.  Launch counts per category are always kept; with
  * timing enabled every launch is bracketed by CUDA events on the handle's

@@ -28,12 +28,15 @@ template <typename T> cudaError_t launch_residual_t(hdg_handle *, const T *, con
 template <typename T> cudaError_t launch_smooth_t(hdg_handle *, const T *, const T *, T *);
 template <typename T>
 cudaError_t launch_smooth_first_t(hdg_handle *, const T *, T *, const T * = nullptr, const double * = nullptr,
-                                  T * = nullptr);
+                                  T * = nullptr, double = 0.0);
+template <typename T>
+cudaError_t launch_smooth_cheb_t(hdg_handle *, const T *, const T *, T *, double, double, const T *);
 template <typename T>
 cudaError_t launch_apply_dots_t(hdg_handle *, const T *, T *, const T *, size_t, int, double *, unsigned int *,
                                 double *);
 template <typename T> cudaError_t launch_restrict_t(hdg_handle *, const T *, T *, const T *, T, T *);
-template <typename T> cudaError_t launch_smooth_prolong_t(hdg_handle *, const T *, const T *, const T *, T *);
+template <typename T>
+cudaError_t launch_smooth_prolong_t(hdg_handle *, const T *, const T *, const T *, T *, double = 0.0, T * = nullptr);
 template <typename T> cudaError_t launch_prolong_add_t(hdg_handle *, const T *, T *);
 
 // Krylov vectors of one precision
@@ -149,6 +152,12 @@ std::string check_params(const hdg_params *prm) {
     if (!(prm->omega > 0) || !(prm->p1_omega > 0)) return "damping factors must be positive";
     if (prm->coarse_mode != 0 && prm->coarse_mode != 1) return "coarse_mode must be 0 or 1";
     if (prm->reorth != 0 && prm->reorth != 1) return "reorth must be 0 or 1";
+    if (prm->smoother != 0 && prm->smoother != 1) return "smoother must be 0 or 1";
+    if (prm->smoother == 1 && prm->cheb_theta <= 0 && (prm->cheb_steps < 2 || prm->cheb_steps > 64))
+        return "cheb_steps must be in 2..64";
+    if (prm->smoother == 1 && prm->cheb_theta > 0 && !(std::isfinite(prm->cheb_delta2) &&
+                                                       prm->cheb_delta2 < prm->cheb_theta * prm->cheb_theta))
+        return "cheb_delta2 must be finite and below cheb_theta^2";
     if (prm->precision != HDG_FP64 && prm->precision != HDG_MIXED_FP32 && prm->precision != HDG_MIXED_BF16 &&
         prm->precision != HDG_MIXED_FGMRES64)
         return "unknown precision mode";
@@ -386,8 +395,26 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr) {
     const size_t NT = h->NT;
     T *x = k.t0, *x2 = k.t1;
     cudaError_t e;
+    const bool cheb = h->prm.smoother == 1;
     // lines 1-2: pre-smoothing and residual
-    if (h->prm.n_pre == 0) {
+    if (cheb && h->prm.n_pre > 0) {
+        // Chebyshev iteration from zero: x_1 = s_0 D^-1 v, then x_{k+1} = x_k +
+        // 2 s_k D^-1 (v - S x_k) + delta^2 s_k s_{k-1} (x_k - x_{k-1})
+        if ((e = KL(cat_first<T>(), 1,
+                    launch_smooth_first_t<T>(h, v, x, w_src, w_src ? &h->ws->rb->hnext : nullptr,
+                                             const_cast<T *>(v), h->cheb_omega[0]))) != cudaSuccess)
+            return e;
+        T *prev = nullptr;
+        for (int i = 1; i < h->prm.n_pre; ++i) {
+            T *o = prev ? prev : x2;
+            if ((e = KL(cat_smooth<T>(), 1, launch_smooth_cheb_t<T>(h, v, x, o, h->cheb_omega[i], h->cheb_beta[i],
+                                                                     prev))) != cudaSuccess)
+                return e;
+            prev = x;
+            x = o;
+        }
+        x2 = (x == k.t0) ? k.t1 : k.t0;
+    } else if (h->prm.n_pre == 0) {
         if ((e = KL(HDG_PROF_KRYLOV, 1, launch_fill<T>(x, T(0), NT, s))) != cudaSuccess) return e;
     } else {
         if ((e = KL(cat_first<T>(), 1,
@@ -418,6 +445,23 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr) {
     if constexpr (std::is_same<T, float>::value) {
         learned = h->lc.on && !h->lc.suspended;
         collect = h->lc.collecting && h->lc.count < h->lc.cap;
+    }
+    if (cheb && !learned && !collect) {
+        // Chebyshev iteration from x_0 = x + pi e_c: the first step rides on the
+        // prolongation and keeps x_0 (in k.res, free after the restriction)
+        T *cur = (np == 1) ? z : x2, *prev = (np == 1) ? nullptr : k.res;
+        if ((e = KL(cat_smooth<T>(), 1, launch_smooth_prolong_t<T>(h, ec, v, x, cur, h->cheb_omega[0], prev))) !=
+            cudaSuccess)
+            return e;
+        for (int i = 1; i < np; ++i) {
+            T *o = (i == np - 1) ? z : prev;
+            if ((e = KL(cat_smooth<T>(), 1, launch_smooth_cheb_t<T>(h, v, cur, o, h->cheb_omega[i], h->cheb_beta[i],
+                                                                     prev))) != cudaSuccess)
+                return e;
+            prev = cur;
+            cur = o;
+        }
+        return cudaSuccess;
     }
     if (!learned && !collect) {
         T *out = (np == 1) ? z : x2;
@@ -1198,6 +1242,98 @@ int check_status(hdg_handle *h) {
     return HDG_OK;
 }
 
+// The Chebyshev smoother's ellipse: Ritz values of cheb_steps Arnoldi steps on
+// D^-1 S (FP64 operator; classical Gram-Schmidt twice) from the start vector
+// v_i = 1 + ((37 i) mod 101) / 101 (i = facet * (p+1) + node), then the fit
+// of spectrum.cpp; or the ellipse given in the parameters.  Then the sweep
+// coefficients: s_0 = 1/theta, s_k = 1 / (2 theta - delta^2 s_{k-1}),
+// omega_0 = s_0, omega_k = 2 s_k, beta_k = delta^2 s_k s_{k-1}.
+int chebyshev_setup(hdg_handle *h) {
+    h->cheb_ritz.clear();
+    if (h->prm.cheb_theta > 0) {
+        h->cheb_theta = h->prm.cheb_theta;
+        h->cheb_delta2 = h->prm.cheb_delta2;
+    } else {
+        Workspace &W = *h->ws;
+        cudaStream_t s = h->stream;
+        const int k = h->prm.cheb_steps;
+        const size_t NT = h->NT, ld = (NT + 3) / 4 * 4, NF = h->NF, pp = h->pp;
+        double *V = nullptr, *tmp = nullptr, *w = nullptr, *part = nullptr, *dh = nullptr;
+        auto release = [&]() {
+            dfree(V); dfree(tmp); dfree(w); dfree(part); dfree(dh);
+        };
+        cudaError_t e = dalloc(&V, size_t(k + 1) * ld);
+        if (e == cudaSuccess) e = dalloc(&tmp, NT);
+        if (e == cudaSuccess) e = dalloc(&w, ld);
+        if (e == cudaSuccess) e = dalloc(&part, size_t(k + 2) * size_t(W.nchunk));
+        if (e == cudaSuccess) e = dalloc(&dh, size_t(k + 2));
+        std::vector<double> v0(NT);
+        double nrm = 0.0;
+        for (size_t e_ = 0; e_ < NF; ++e_)
+            for (size_t r = 0; r < pp; ++r) {
+                const double val = 1.0 + double((37 * (e_ * pp + r)) % 101) / 101.0;
+                v0[r * NF + e_] = val;
+                nrm += val * val;
+            }
+        nrm = std::sqrt(nrm);
+        for (double &x : v0) x /= nrm;
+        if (e == cudaSuccess) e = cudaMemsetAsync(V, 0, sizeof(double) * size_t(k + 1) * ld, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w, 0, sizeof(double) * ld, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(V, v0.data(), sizeof(double) * NT, cudaMemcpyHostToDevice, s);
+        std::vector<double> Hm(size_t(k + 1) * k, 0.0), hc(size_t(k + 2));
+        int m = k;
+        for (int j = 0; j < k && e == cudaSuccess; ++j) {
+            e = launch_apply_t<double>(h, V + size_t(j) * ld, tmp);
+            if (e == cudaSuccess) e = launch_smooth_first_t<double>(h, tmp, w, nullptr, nullptr, nullptr, 1.0);
+            for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+                e = launch_multidot<double>(V, ld, j + 1, w, NT, part, W.nchunk, s);
+                if (e == cudaSuccess) e = launch_reduce_partials(part, j + 1, W.nchunk, dh, s);
+                if (e == cudaSuccess) e = launch_multi_axpy<double>(w, V, ld, j + 1, dh, -1.0, NT, s);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), dh, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                for (int i = 0; i <= j; ++i) Hm[size_t(i) * k + j] += hc[size_t(i)];
+            }
+            // ||w|| into dh[k + 1] (the square root written by the reduction)
+            if (e == cudaSuccess) e = launch_multidot<double>(w, ld, 1, w, NT, part, W.nchunk, s);
+            if (e == cudaSuccess) e = launch_reduce_partials(part, 1, W.nchunk, dh, s, nullptr, 0, dh + k + 1);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), dh + k + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) break;
+            double colmax = 0.0;
+            for (int i = 0; i <= j; ++i) colmax = std::max(colmax, std::fabs(Hm[size_t(i) * k + j]));
+            if (!(hc[0] > 1e-14 * colmax)) {
+                m = j + 1;                     // invariant subspace: the Ritz values are exact
+                break;
+            }
+            if (j + 1 < k) Hm[size_t(j + 1) * k + j] = hc[0];
+            e = launch_scale_copy<double>(w, V + size_t(j + 1) * ld, dh + k + 1, NT, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        release();
+        if (e != cudaSuccess) return fail(h, HDG_ECUDA, std::string("Chebyshev estimate: ") + cudaGetErrorString(e));
+        std::vector<double> Hs(size_t(m) * m);
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) Hs[size_t(i) * m + j] = Hm[size_t(i) * k + j];
+        for (double x : Hs)
+            if (!std::isfinite(x)) return fail(h, HDG_ENAN, "Chebyshev estimate: non-finite Arnoldi entry");
+        h->cheb_ritz = hessenberg_eigenvalues(Hs, m);
+        chebyshev_ellipse(h->cheb_ritz, 0.1, 1.1, h->cheb_theta, h->cheb_delta2);
+        if (!(h->cheb_theta > 0)) return fail(h, HDG_EBREAKDOWN, "Chebyshev estimate: no eigenvalue with Re > 0");
+    }
+    const int n = std::max({h->prm.n_pre, h->prm.n_post, 1});
+    h->cheb_omega.assign(size_t(n), 0.0);
+    h->cheb_beta.assign(size_t(n), 0.0);
+    double sp = 1.0 / h->cheb_theta;
+    h->cheb_omega[0] = sp;
+    for (int i = 1; i < n; ++i) {
+        const double si = 1.0 / (2.0 * h->cheb_theta - h->cheb_delta2 * sp);
+        h->cheb_omega[size_t(i)] = 2.0 * si;
+        h->cheb_beta[size_t(i)] = h->cheb_delta2 * si * sp;
+        sp = si;
+    }
+    return HDG_OK;
+}
+
 int require_condensed(hdg_handle *h) {
     if (!h) return HDG_EINVAL;
     if (!h->condensed) return fail(h, HDG_ESTATE, "hdg_condense has not run on this handle");
@@ -1268,6 +1404,10 @@ void hdg_default_params(hdg_params *prm) {
     prm->inner_rtol = 1e-4;
     prm->coarse_mode = 0;
     prm->reorth = 0;
+    prm->smoother = 0;
+    prm->cheb_theta = 0.0;
+    prm->cheb_delta2 = 0.0;
+    prm->cheb_steps = 20;
 }
 
 int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hdg_handle **out) {
@@ -1354,7 +1494,27 @@ int hdg_condense(hdg_handle *h) {
     }
     int rc = check_status(h);
     if (rc) return rc;
+    if (h->prm.smoother == 1 && (rc = chebyshev_setup(h)) != HDG_OK) return rc;
     h->condensed = true;
+    return HDG_OK;
+}
+
+int hdg_get_chebyshev(const hdg_handle *hc, double *ellipse, double *ritz, int32_t *n_ritz) {
+    hdg_handle *h = const_cast<hdg_handle *>(hc);
+    if (!h) return HDG_EINVAL;
+    if (h->prm.smoother != 1) return fail(h, HDG_ESTATE, "the handle does not use the Chebyshev smoother");
+    if (!h->condensed) return fail(h, HDG_ESTATE, "hdg_condense has not run on this handle");
+    if (ellipse) {
+        ellipse[0] = h->cheb_theta;
+        ellipse[1] = h->cheb_delta2;
+    }
+    const int n = int(std::min<size_t>(h->cheb_ritz.size(), 64));
+    if (ritz)
+        for (int i = 0; i < n; ++i) {
+            ritz[2 * i] = h->cheb_ritz[size_t(i)].real();
+            ritz[2 * i + 1] = h->cheb_ritz[size_t(i)].imag();
+        }
+    if (n_ritz) *n_ritz = n;
     return HDG_OK;
 }
 

@@ -3,6 +3,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <complex>
 #include <cstdint>
 #include <functional>
 #include <string>
@@ -358,6 +359,12 @@ struct hdg_handle {
     hdg::Learned lc;
     hdg::Imex imex;
     bool has_f = false;               // a non-zero Coriolis field was given to hdg_setup
+    // Chebyshev smoother (smoother 1): the ellipse, the Ritz values it was
+    // fitted to, and per step k the sweep coefficients omega_k (of D^-1 r)
+    // and beta_k (of x_k - x_{k-1})
+    double cheb_theta = 0.0, cheb_delta2 = 0.0;
+    std::vector<std::complex<double>> cheb_ritz;
+    std::vector<double> cheb_omega, cheb_beta;
 };
 
 // ---------------------------------------------------------------- error helpers
@@ -391,6 +398,14 @@ inline bool mode_pre32(const hdg_params &p) { return p.precision == HDG_MIXED_FG
         case 4: { constexpr int P = 4; CALL; } break; \
         default: return cudaErrorInvalidValue;        \
     }
+
+// Spectral estimate for the Chebyshev smoother (spectrum.cpp, host): the
+// eigenvalues of an n x n upper Hessenberg matrix (row-major), and the
+// ellipse (centre theta, squared focal half-distance delta2) fitted to Ritz
+// values with real extent [lower b, b], b = grow * max Re.
+std::vector<std::complex<double>> hessenberg_eigenvalues(const std::vector<double> &H, int n);
+void chebyshev_ellipse(const std::vector<std::complex<double>> &ritz, double lower, double grow, double &theta,
+                       double &delta2);
 
 // Kernel accounting for entry points defined outside api.cu: counts nk
 // launches in category cat and, with timing on, brackets what fn enqueues

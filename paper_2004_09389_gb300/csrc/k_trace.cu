@@ -209,10 +209,15 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) residual_kernel(int 
     for (int r = 0; r <= P; ++r) res[size_t(r) * NF + e] = b[size_t(r) * NF + e] - v[r];
 }
 
-template <int P, typename T, typename ST>
+// One sweep x_out = x + omega D_e^-1 (b - S x)_e; with CHEB, a step of the
+// Chebyshev iteration x_out = x + omega D_e^-1 (b - S x)_e + beta (x - x_prev)
+// (x_prev null: the previous iterate is zero).  x_out may alias x_prev: each
+// thread reads x_prev only at its own facet before writing it.
+template <int P, typename T, typename ST, bool CHEB = false>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_kernel(int NF, const ST *__restrict__ Sval, const T *__restrict__ Dinv,
                                                      const int32_t *__restrict__ nbr, const T *__restrict__ b,
-                                                     const T *__restrict__ x, T *__restrict__ xout, T omega) {
+                                                     const T *__restrict__ x, T *xout, T omega, T beta,
+                                                     const T *xprev) {
     constexpr int PP = P + 1;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= NF) return;
@@ -222,19 +227,30 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_kernel(int NF
 #pragma unroll
     for (int r = 0; r < PP; ++r) v[r] = b[size_t(r) * NF + e] - v[r];
     block_solve_packed<P, T, T>(Dinv, e, NF, v, d);
+    if constexpr (CHEB) {
 #pragma unroll
-    for (int r = 0; r < PP; ++r) xout[size_t(r) * NF + e] = fma(omega, d[r], xs[0][r]);
+        for (int r = 0; r < PP; ++r) {
+            const T xp = xprev ? xprev[size_t(r) * NF + e] : T(0);
+            xout[size_t(r) * NF + e] = fma(beta, xs[0][r] - xp, fma(omega, d[r], xs[0][r]));
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < PP; ++r) xout[size_t(r) * NF + e] = fma(omega, d[r], xs[0][r]);
+    }
 }
 
 // First post-smoothing sweep with the coarse correction folded in:
 // x' = x + pi e_c is formed on the fly for the five facets the rows touch,
 // then x_out = x' + omega D_e^-1 (b - S x')_e.
-template <int P, typename T, typename ST>
+// With X0, x' on the facet itself is also stored to x0out (the previous
+// iterate of the Chebyshev step that follows).
+template <int P, typename T, typename ST, bool X0 = false>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_prolong_kernel(int NF, const ST *__restrict__ Sval,
                                                              const T *__restrict__ Dinv, const int32_t *__restrict__ nbr,
                                                              const int32_t *__restrict__ fverts,
                                                              const T *__restrict__ ec, const T *__restrict__ b,
-                                                             const T *__restrict__ x, T *__restrict__ xout, T omega) {
+                                                             const T *__restrict__ x, T *__restrict__ xout, T omega,
+                                                             T *__restrict__ x0out) {
     constexpr int PP = P + 1;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= NF) return;
@@ -258,6 +274,10 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_prolong_kerne
     block_solve_packed<P, T, T>(Dinv, e, NF, v, d);
 #pragma unroll
     for (int r = 0; r < PP; ++r) xout[size_t(r) * NF + e] = fma(omega, d[r], xs[0][r]);
+    if constexpr (X0) {
+#pragma unroll
+        for (int r = 0; r < PP; ++r) x0out[size_t(r) * NF + e] = xs[0][r];
+    }
 }
 
 // first sweep from a zero initial guess: x = omega D^-1 b
@@ -475,17 +495,31 @@ template <typename T>
 cudaError_t launch_smooth_t(hdg_handle *h, const T *b, const T *x, T *xout) {
     const T om = T(h->prm.omega);
     if constexpr (std::is_same<T, float>::value) if (bf16_pre(h)) {
-        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, om)));
+        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, om, T(0), nullptr)));
         return cudaGetLastError();
     }
     {
-        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, om)));
+        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, om, T(0), nullptr)));
+    }
+    return cudaGetLastError();
+}
+// a step of the Chebyshev iteration: xout = x + omega D^-1 (b - S x) + beta (x - xprev)
+template <typename T>
+cudaError_t launch_smooth_cheb_t(hdg_handle *h, const T *b, const T *x, T *xout, double omega, double beta,
+                                 const T *xprev) {
+    if constexpr (std::is_same<T, float>::value) if (bf16_pre(h)) {
+        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, __nv_bfloat16, true><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, T(omega), T(beta), xprev)));
+        return cudaGetLastError();
+    }
+    {
+        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, T, true><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, T(omega), T(beta), xprev)));
     }
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_smooth_first_t(hdg_handle *h, const T *b, T *x, const T *w, const double *hnext, T *bout) {
-    const T om = T(h->prm.omega);
+cudaError_t launch_smooth_first_t(hdg_handle *h, const T *b, T *x, const T *w, const double *hnext, T *bout,
+                                  double omega) {
+    const T om = T(omega > 0 ? omega : h->prm.omega);
     HDG_DISPATCH_P(h->p, (smooth_first_kernel<P, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::D(h), b, x, om, w, hnext, bout)));
     return cudaGetLastError();
 }
@@ -495,14 +529,21 @@ cudaError_t launch_restrict_t(hdg_handle *h, const T *r, T *rc, const T *dinv0, 
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_smooth_prolong_t(hdg_handle *h, const T *ec, const T *b, const T *x, T *xout) {
-    const T om = T(h->prm.omega);
+cudaError_t launch_smooth_prolong_t(hdg_handle *h, const T *ec, const T *b, const T *x, T *xout, double omega,
+                                    T *x0out) {
+    const T om = T(omega > 0 ? omega : h->prm.omega);
     if constexpr (std::is_same<T, float>::value) if (bf16_pre(h)) {
-        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om)));
+        if (x0out) {
+            HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, __nv_bfloat16, true><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om, x0out)));
+        } else {
+            HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om, nullptr)));
+        }
         return cudaGetLastError();
     }
-    {
-        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om)));
+    if (x0out) {
+        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, T, true><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om, x0out)));
+    } else {
+        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om, nullptr)));
     }
     return cudaGetLastError();
 }
@@ -536,14 +577,20 @@ template cudaError_t launch_residual_t<double>(hdg_handle *, const double *, con
 template cudaError_t launch_residual_t<float>(hdg_handle *, const float *, const float *, float *, bool);
 template cudaError_t launch_smooth_t<double>(hdg_handle *, const double *, const double *, double *);
 template cudaError_t launch_smooth_t<float>(hdg_handle *, const float *, const float *, float *);
+template cudaError_t launch_smooth_cheb_t<double>(hdg_handle *, const double *, const double *, double *, double,
+                                                  double, const double *);
+template cudaError_t launch_smooth_cheb_t<float>(hdg_handle *, const float *, const float *, float *, double, double,
+                                                 const float *);
 template cudaError_t launch_smooth_first_t<double>(hdg_handle *, const double *, double *, const double *,
-                                                   const double *, double *);
+                                                   const double *, double *, double);
 template cudaError_t launch_smooth_first_t<float>(hdg_handle *, const float *, float *, const float *, const double *,
-                                                  float *);
+                                                  float *, double);
 template cudaError_t launch_restrict_t<double>(hdg_handle *, const double *, double *, const double *, double, double *);
 template cudaError_t launch_restrict_t<float>(hdg_handle *, const float *, float *, const float *, float, float *);
-template cudaError_t launch_smooth_prolong_t<double>(hdg_handle *, const double *, const double *, const double *, double *);
-template cudaError_t launch_smooth_prolong_t<float>(hdg_handle *, const float *, const float *, const float *, float *);
+template cudaError_t launch_smooth_prolong_t<double>(hdg_handle *, const double *, const double *, const double *, double *,
+                                                     double, double *);
+template cudaError_t launch_smooth_prolong_t<float>(hdg_handle *, const float *, const float *, const float *, float *,
+                                                    double, float *);
 template cudaError_t launch_prolong_add_t<double>(hdg_handle *, const double *, double *);
 template cudaError_t launch_prolong_add_t<float>(hdg_handle *, const float *, float *);
 

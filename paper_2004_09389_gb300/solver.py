@@ -190,6 +190,14 @@ class HDGSolver:
                                       C.byref(loss)))
         return loss.value, g
 
+    def chebyshev(self):
+        """The Chebyshev smoother's ellipse (theta, delta^2) and the Ritz values it was fitted to."""
+        ell = np.zeros(2)
+        ritz = np.zeros(128)
+        n = C.c_int32(0)
+        L.check(self.h, self.lib.hdg_get_chebyshev(self.h, ell.ctypes.data, ritz.ctypes.data, C.byref(n)))
+        return (float(ell[0]), float(ell[1])), ritz[:2 * n.value:2] + 1j * ritz[1:2 * n.value:2]
+
     # ---------------------------------------------------------------- IMEX time stepping
     def imex_init(self, f_vertex=None) -> None:
         """Explicit Coriolis field (host, [n_vertices]) for hdg_imex_step_dev."""
