@@ -125,7 +125,10 @@ typedef struct {
                                        (phi,psi) + tau^2 g H kappa_K [(grad phi,grad psi)
                                        - tau f_K (J grad phi,grad psi)], kappa_K = 1/(1+tau^2 f_K^2);
                                    1 = as printed in Eq. coarse_problem_upwind (no rotation).
-                                   Both agree when f = 0.                                  */
+                                   Both agree when f = 0.
+                                   2 = the Galerkin choice of the Sec. 4.4 footnote:
+                                       pi^T S pi on the fine P1 level, P^T A P on the
+                                       coarser ones (P linear interpolation)             */
     int32_t       reorth;       /* Arnoldi orthogonalisation (GMRES, Sec. 5.1 setup):
                                    0 = one classical Gram-Schmidt pass (the solver
                                        configuration of the paper's experiments sets no

@@ -150,7 +150,7 @@ std::string check_params(const hdg_params *prm) {
     if (prm->max_iter < 1) return "max_iter must be positive";
     if (prm->n_pre < 0 || prm->n_post < 0 || prm->p1_nu_pre < 0 || prm->p1_nu_post < 0) return "negative sweep count";
     if (!(prm->omega > 0) || !(prm->p1_omega > 0)) return "damping factors must be positive";
-    if (prm->coarse_mode != 0 && prm->coarse_mode != 1) return "coarse_mode must be 0 or 1";
+    if (prm->coarse_mode < 0 || prm->coarse_mode > 2) return "coarse_mode must be 0, 1 or 2";
     if (prm->reorth != 0 && prm->reorth != 1) return "reorth must be 0 or 1";
     if (prm->smoother != 0 && prm->smoother != 1) return "smoother must be 0 or 1";
     if (prm->smoother == 1 && prm->cheb_theta <= 0 && (prm->cheb_steps < 2 || prm->cheb_steps > 64))
@@ -881,6 +881,11 @@ void free_handle(hdg_handle *h) {
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     h->prof.pool.clear();
     imex_release(h);
+    dfree(h->gal.ptr0);
+    dfree(h->gal.code0);
+    for (auto *p_ : h->gal.ptr) cudaFree(p_);
+    for (auto *p_ : h->gal.idx) cudaFree(p_);
+    for (auto *p_ : h->gal.w) cudaFree(p_);
     if (h->prof.evict_buf) cudaFree(h->prof.evict_buf);
     if (h->prof.evict_sink) cudaFree(h->prof.evict_sink);
     dfree(h->d_ref); dfree(h->d_X); dfree(h->d_fcell); dfree(h->d_facet_of); dfree(h->d_flip);
@@ -1142,6 +1147,24 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
         if (const char *ev = std::getenv("HDG_P1_FUSED")) h->p1_fused = std::atoi(ev) != 0;
         int rc = set_tail_start(h, tail_max);
         if (rc) return rc;
+    }
+    if (prm->coarse_mode == 2) {
+        GalerkinHost gh;
+        const std::string ge = build_galerkin_lists(hm, gh);
+        if (!ge.empty()) return fail(h, HDG_EINVAL, ge);
+        TRY(upload(&h->gal.ptr0, gh.ptr0, s));
+        TRY(upload(&h->gal.code0, gh.code0, s));
+        for (size_t l = 0; l < gh.ptr.size(); ++l) {
+            int32_t *pp_ = nullptr, *ii = nullptr;
+            double *ww = nullptr;
+            TRY(upload(&pp_, gh.ptr[l], s));
+            h->gal.ptr.push_back(pp_);
+            TRY(upload(&ii, gh.idx[l], s));
+            h->gal.idx.push_back(ii);
+            TRY(upload(&ww, gh.w[l], s));
+            h->gal.w.push_back(ww);
+        }
+        TRY(cudaStreamSynchronize(s));      // the host vectors go out of scope
     }
     const size_t nc = h->lev.back().nv;
     TRY(dalloc(&h->d_coarse_inv, nc * nc));
@@ -1469,8 +1492,12 @@ int hdg_condense(hdg_handle *h) {
     TRY(KL(HDG_PROF_CONDENSE, 1, launch_condense(h)));
     TRY(KL(HDG_PROF_CONDENSE, 1, launch_assemble(h)));
     const double tau = h->prm.tau, gH = h->prm.g * h->prm.H;
-    for (auto &L : h->lev)
-        TRY(KL(HDG_PROF_CONDENSE, 2, launch_p1_assemble(h, L, tau, gH, h->prm.coarse_mode == 0 ? 1 : 0)));
+    if (h->prm.coarse_mode == 2) {
+        TRY(KL(HDG_PROF_CONDENSE, int(2 * h->lev.size()), launch_p1_galerkin(h)));
+    } else {
+        for (auto &L : h->lev)
+            TRY(KL(HDG_PROF_CONDENSE, 2, launch_p1_assemble(h, L, tau, gH, h->prm.coarse_mode == 0 ? 1 : 0)));
+    }
     const DevLevel &Lc = h->lev.back();
     TRY(KL(HDG_PROF_CONDENSE, 2, launch_dense_inverse(h, Lc, h->d_coarse_work, h->d_coarse_inv, Lc.nv)));
     if (h->prm.precision != HDG_FP64) {

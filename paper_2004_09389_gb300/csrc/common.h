@@ -159,6 +159,21 @@ struct Learned {
     double *coef = nullptr, *nrm = nullptr;
 };
 
+// Galerkin coarse operators (k_galerkin.cu, coarse_mode 2): per ELL slot of
+// level 0 the codes e*20 + b*4 + sv*2 + sw of its facet-row contributions;
+// per slot of level l+1 the (slot of level l, weight) pairs
+struct GalerkinHost {
+    std::vector<int32_t> ptr0, code0;
+    std::vector<std::vector<int32_t>> ptr, idx;
+    std::vector<std::vector<double>> w;
+};
+struct GalerkinDev {
+    int32_t *ptr0 = nullptr, *code0 = nullptr;
+    std::vector<int32_t *> ptr, idx;
+    std::vector<double *> w;
+};
+std::string build_galerkin_lists(const HostMesh &hm, GalerkinHost &g);
+
 // IMEX time stepping state (k_imex.cu)
 constexpr int kImexMaxStages = 5;
 struct Imex {
@@ -358,6 +373,7 @@ struct hdg_handle {
     hdg::Prof prof;
     hdg::Learned lc;
     hdg::Imex imex;
+    hdg::GalerkinDev gal;
     bool has_f = false;               // a non-zero Coriolis field was given to hdg_setup
     // Chebyshev smoother (smoother 1): the ellipse, the Ritz values it was
     // fitted to, and per step k the sweep coefficients omega_k (of D^-1 r)
@@ -427,6 +443,8 @@ void imex_release(hdg_handle *h);
 cudaError_t launch_condense(hdg_handle *h);
 cudaError_t launch_assemble(hdg_handle *h);
 cudaError_t launch_p1_assemble(hdg_handle *h, DevLevel &L, double tau, double gH, int rotating);
+// every P1 level operator as the Galerkin product of the trace operator (k_galerkin.cu)
+cudaError_t launch_p1_galerkin(hdg_handle *h);
 cudaError_t launch_dense_inverse(hdg_handle *h, const DevLevel &L, double *work, double *inv, int n);
 cudaError_t launch_to_f32(const double *x, float *y, size_t n, cudaStream_t s);
 

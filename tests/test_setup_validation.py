@@ -143,7 +143,10 @@ PARAM_FAULTS = [
     ({"max_iter": 0}, "max_iter must be positive"),
     ({"n_pre": -1}, "negative sweep count"), ({"p1_nu_post": -2}, "negative sweep count"),
     ({"omega": 0.0}, "damping factors must be positive"), ({"p1_omega": -0.5}, "damping factors must be positive"),
-    ({"coarse_mode": 2}, "coarse_mode must be 0 or 1"),
+    ({"coarse_mode": 3}, "coarse_mode must be 0, 1 or 2"), ({"coarse_mode": -1}, "coarse_mode must be 0, 1 or 2"),
+    ({"smoother": 2}, "smoother must be 0 or 1"),
+    ({"smoother": 1, "cheb_steps": 1}, "cheb_steps must be in 2..64"),
+    ({"smoother": 1, "cheb_theta": 1.0, "cheb_delta2": 1.5}, "cheb_delta2 must be finite and below cheb_theta^2"),
     ({"reorth": -1}, "reorth must be 0 or 1"),
     ({"precision": 7}, "unknown precision mode"),
     ({"precision": 1, "inner_rtol": 1.0}, "inner_rtol must be in (0, 1)"),
