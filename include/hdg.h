@@ -172,7 +172,9 @@ HDG_API void hdg_default_params(hdg_params *prm);
  * (for timing comparisons; results agree up to summation order):
  * HDG_TAIL_MAX_VERTICES (16..4096, default 1024) bounds the P1 levels run by
  * the single-block coarse cycle; HDG_P1_FUSED=0 replaces the patch-fused P1
- * kernels by one launch per smoothing / transfer step. */
+ * kernels by one launch per smoothing / transfer step; HDG_FACET_BLOCK
+ * (64, 128 or 256; default 128 for HDG_FP64 handles, 256 otherwise) sets the
+ * threads per block of the facet-row kernels. */
 HDG_API int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hdg_handle **out);
 
 /* (Re)build the cell operators for the handle's parameters: for every cell the

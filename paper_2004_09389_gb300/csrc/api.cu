@@ -475,8 +475,28 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr) {
         return cudaSuccess;
     }
     // n_post - 1 ordinary sweeps, then the residual r = v - S x before the last sweep
+    T *cheb_prev = nullptr, *spare = k.res;   // Chebyshev: x_{n-2} for the last step; a free vector
     if (np == 1) {
         if ((e = KL(HDG_PROF_TRANSFER, 1, launch_prolong_add_t<T>(h, ec, x))) != cudaSuccess) return e;
+    } else if (cheb) {
+        // the first n_post - 1 steps of the Chebyshev iteration from x_0 = x + pi e_c,
+        // rotating three vectors (x is free once x_0 is stored)
+        T *cur = x2, *prev = k.res, *free_ = x;
+        if ((e = KL(cat_smooth<T>(), 1, launch_smooth_prolong_t<T>(h, ec, v, x, cur, h->cheb_omega[0], prev))) !=
+            cudaSuccess)
+            return e;
+        for (int i = 1; i < np - 1; ++i) {
+            if ((e = KL(cat_smooth<T>(), 1, launch_smooth_cheb_t<T>(h, v, cur, free_, h->cheb_omega[i],
+                                                                     h->cheb_beta[i], prev))) != cudaSuccess)
+                return e;
+            T *t = free_;
+            free_ = prev;
+            prev = cur;
+            cur = t;
+        }
+        x = cur;
+        cheb_prev = prev;
+        spare = free_;
     } else {
         if ((e = KL(cat_smooth<T>(), 1, launch_smooth_prolong_t<T>(h, ec, v, x, x2))) != cudaSuccess) return e;
         std::swap(x, x2);
@@ -487,19 +507,22 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr) {
     }
     if constexpr (std::is_same<T, float>::value) {
         if (learned) {
-            // the learned sweep replaces the last block-Jacobi sweep
-            if ((e = KL(cat_res<T>(), 1, launch_residual_t<T>(h, v, x, k.res, true))) != cudaSuccess) return e;
-            return KL(HDG_PROF_KRYLOV, 1, h->lc.tc ? launch_learned_infer_tc(h, k.res, x, z)
-                                                   : launch_learned_infer(h, k.res, x, z));
+            // the learned sweep replaces the last smoothing step
+            if ((e = KL(cat_res<T>(), 1, launch_residual_t<T>(h, v, x, spare, true))) != cudaSuccess) return e;
+            return KL(HDG_PROF_KRYLOV, 1, h->lc.tc ? launch_learned_infer_tc(h, spare, x, z)
+                                                   : launch_learned_infer(h, spare, x, z));
         }
-        // collecting: store the residual (normalised), then the plain last sweep
-        if ((e = KL(cat_res<T>(), 1, launch_residual_t<T>(h, v, x, k.res, true))) != cudaSuccess) return e;
+        // collecting: store the residual (normalised), then the plain last step
+        T *slot = h->lc.buf + size_t(h->lc.count) * NT;
+        if ((e = KL(cat_res<T>(), 1, launch_residual_t<T>(h, v, x, slot, true))) != cudaSuccess) return e;
         Workspace &W = *h->ws;
-        if ((e = dots<T>(h, k.res, 1, k.res, W.nrm2)) != cudaSuccess) return e;
-        if ((e = launch_normalize32(k.res, h->lc.buf + size_t(h->lc.count) * NT, W.nrm2, NT, s)) != cudaSuccess)
-            return e;
+        if ((e = dots<T>(h, slot, 1, slot, W.nrm2)) != cudaSuccess) return e;
+        if ((e = launch_normalize32(slot, slot, W.nrm2, NT, s)) != cudaSuccess) return e;
         h->lc.count += 1;
     }
+    if (cheb_prev)
+        return KL(cat_smooth<T>(), 1, launch_smooth_cheb_t<T>(h, v, x, z, h->cheb_omega[size_t(np - 1)],
+                                                              h->cheb_beta[size_t(np - 1)], cheb_prev));
     return KL(cat_smooth<T>(), 1, launch_smooth_t<T>(h, v, x, z));
 }
 
@@ -1145,6 +1168,12 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
         if (const char *ev = std::getenv("HDG_TAIL_MAX_VERTICES")) tail_max = std::max(16, std::min(4096, std::atoi(ev)));
         // HDG_P1_FUSED=0 selects the unfused P1 kernels (same arithmetic; for timing comparisons)
         if (const char *ev = std::getenv("HDG_P1_FUSED")) h->p1_fused = std::atoi(ev) != 0;
+        // HDG_FACET_BLOCK = 64 / 128 / 256: threads per block of the facet-row kernels
+        // (one of the autotuner's candidates; same arithmetic)
+        if (const char *ev = std::getenv("HDG_FACET_BLOCK")) {
+            const int bs = std::atoi(ev);
+            if (bs == 64 || bs == 128 || bs == 256) h->bs_facet = bs;
+        }
         int rc = set_tail_start(h, tail_max);
         if (rc) return rc;
     }
@@ -1457,6 +1486,9 @@ int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hd
     h->nv = h->hm.nv;
     h->dim = h->hm.dim;
     h->tau_s = prm->tau_s > 0 ? prm->tau_s : std::sqrt(prm->g * prm->H);
+    // FP64 facet-row kernels need ~240 registers per thread (one 256-thread block
+    // per SM); blocks of 128 measured faster for them (smooth64 65 -> 53 us)
+    h->bs_facet = prm->precision == HDG_FP64 ? 128 : 256;
     if (stream) {
         h->stream = static_cast<cudaStream_t>(stream);
     } else {

@@ -574,7 +574,7 @@ __global__ void adam_kernel(int n, float *__restrict__ theta, float *__restrict_
     }
 
 // dst = src / sqrt(nrm2[0])
-__global__ void normalize_kernel(const float *__restrict__ src, float *__restrict__ dst, const double *nrm2, size_t n) {
+__global__ void normalize_kernel(const float *src, float *dst, const double *nrm2, size_t n) {
     const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = float(double(src[i]) / sqrt(nrm2[0]));
 }
