@@ -146,6 +146,16 @@ typedef struct {
     double        cheb_delta2;  /* smoother 1: squared focal half-distance of the ellipse
                                    (used only when cheb_theta > 0; < 0 for a tall ellipse) */
     int32_t       cheb_steps;   /* smoother 1: Arnoldi steps of the estimate (2..64)      */
+    int32_t       flux;         /* 0 = upwind (Eq. bilinear_HDG_upwind: scalar trace, P1 coarse
+                                       space);
+                                   1 = Lax-Friedrichs (Eq. bilinear_HDG_lax: vector trace
+                                       u_hat in [P^p(e)]^2, Cartesian components, 2(p+1) dofs
+                                       per facet (component-major, nodes lo -> hi); RT0 coarse
+                                       space with the grad-div operator of
+                                       Eq. coarse_problem_LF divided by tau, solved
+                                       approximately by n_coarse Chebyshev steps).  Flat
+                                       meshes, HDG_FP64, p = 1 or 2, coarse_mode 0 or 1.   */
+    int32_t       n_coarse;     /* flux 1: Chebyshev steps of the RT0 coarse solve (1..200) */
 } hdg_params;
 
 typedef struct {
@@ -160,7 +170,7 @@ typedef struct {
 /* Fill *prm with the defaults: p = 1, tau = 1, g = H = 1, tau_s = sqrt(gH),
  * FP64, rtol 1e-8, restart 30, max_iter 500, 2 + 2 sweeps, omega = 2/3,
  * 2 + 2 P1 sweeps, p1_omega = 2/3, inner_rtol 1e-4, coarse_mode 0, reorth 0,
- * smoother 0 (cheb_theta 0: estimated, cheb_steps 20). */
+ * smoother 0 (cheb_theta 0: estimated, cheb_steps 20), flux 0, n_coarse 20. */
 HDG_API void hdg_default_params(hdg_params *prm);
 
 /* Build a handle: validate and copy the mesh (facet numbering, orientation,
@@ -287,6 +297,12 @@ HDG_API int hdg_get_cell_schur(hdg_handle *h, double *S);
  * (re, im) pairs, *n_ritz their number (0 when the ellipse was given).
  * HDG_ESTATE if the handle does not use smoother 1 or is not condensed. */
 HDG_API int hdg_get_chebyshev(const hdg_handle *h, double *ellipse, double *ritz, int32_t *n_ritz);
+/* The same for the Chebyshev coarse solve of the Lax-Friedrichs solver
+ * (flux 1): the ellipse of D_c^-1 S_c (S_c the RT0 coarse operator, D_c its
+ * diagonal) fitted to cheb_steps Arnoldi Ritz values from the start vector
+ * v_f = 1 + ((37 f) mod 101) / 101 over the facets.  HDG_ESTATE unless the
+ * handle uses flux 1 and is condensed. */
+HDG_API int hdg_get_rt0_chebyshev(const hdg_handle *h, double *ellipse, double *ritz, int32_t *n_ritz);
 
 /* Kernel accounting.  Launch counts per category are always kept; with
  * timing enabled every launch is bracketed by CUDA events on the handle's

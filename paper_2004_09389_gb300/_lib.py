@@ -43,7 +43,8 @@ class hdg_params(C.Structure):
                 ("omega", C.c_double), ("p1_nu_pre", C.c_int32), ("p1_nu_post", C.c_int32),
                 ("p1_omega", C.c_double), ("inner_rtol", C.c_double), ("coarse_mode", C.c_int32),
                 ("reorth", C.c_int32), ("smoother", C.c_int32), ("cheb_theta", C.c_double),
-                ("cheb_delta2", C.c_double), ("cheb_steps", C.c_int32)]
+                ("cheb_delta2", C.c_double), ("cheb_steps", C.c_int32), ("flux", C.c_int32),
+                ("n_coarse", C.c_int32)]
 
 
 class hdg_solve_info(C.Structure):
@@ -68,7 +69,8 @@ EXPORTS = ["hdg_default_params", "hdg_setup", "hdg_condense", "hdg_set_tau", "hd
            "hdg_solve_batch_dev", "hdg_autotune", "hdg_get_stream", "hdg_learned_init",
            "hdg_learned_collect_dev", "hdg_learned_train", "hdg_learned_params", "hdg_learned_enable",
            "hdg_learned_loss_grad_dev", "hdg_precond_apply32_dev", "hdg_fma_rate",
-           "hdg_imex_init", "hdg_imex_rates_dev", "hdg_imex_step_dev", "hdg_get_chebyshev"]
+           "hdg_imex_init", "hdg_imex_rates_dev", "hdg_imex_step_dev", "hdg_get_chebyshev",
+           "hdg_get_rt0_chebyshev"]
 
 HDG_PROF_N = 16
 PROF_NAMES = ["apply64", "residual64", "smooth64", "smooth_first64", "apply32", "residual32", "smooth32",
@@ -116,6 +118,7 @@ def load() -> C.CDLL:
     lib.hdg_profile_read.argtypes = [vp, vp, vp]
     lib.hdg_fma_rate.argtypes = [C.c_int, vp]
     lib.hdg_get_chebyshev.argtypes = [vp, vp, vp, vp]
+    lib.hdg_get_rt0_chebyshev.argtypes = [vp, vp, vp, vp]
     lib.hdg_imex_init.argtypes = [vp, vp]
     lib.hdg_imex_rates_dev.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.hdg_imex_step_dev.argtypes = [vp, C.c_int, C.c_double, C.c_double, vp, vp, C.POINTER(hdg_solve_info)]

@@ -153,6 +153,14 @@ std::string check_params(const hdg_params *prm) {
     if (prm->coarse_mode < 0 || prm->coarse_mode > 2) return "coarse_mode must be 0, 1 or 2";
     if (prm->reorth != 0 && prm->reorth != 1) return "reorth must be 0 or 1";
     if (prm->smoother != 0 && prm->smoother != 1) return "smoother must be 0 or 1";
+    if (prm->flux != 0 && prm->flux != 1) return "flux must be 0 or 1";
+    if (prm->flux == 1) {
+        if (prm->precision != HDG_FP64) return "the Lax-Friedrichs solver runs in HDG_FP64";
+        if (prm->p < 1 || prm->p > 2) return "the Lax-Friedrichs solver supports p = 1 and 2";
+        if (prm->coarse_mode == 2) return "the Lax-Friedrichs solver uses coarse_mode 0 or 1";
+        if (prm->n_coarse < 1 || prm->n_coarse > 200) return "n_coarse must be in 1..200";
+        if (prm->cheb_steps < 2 || prm->cheb_steps > 64) return "cheb_steps must be in 2..64";
+    }
     if (prm->smoother == 1 && prm->cheb_theta <= 0 && (prm->cheb_steps < 2 || prm->cheb_steps > 64))
         return "cheb_steps must be in 2..64";
     if (prm->smoother == 1 && prm->cheb_theta > 0 && !(std::isfinite(prm->cheb_delta2) &&
@@ -386,10 +394,96 @@ cudaError_t p1_cycle(hdg_handle *h, T **result) {
 }
 
 // z = V(v), Alg. twolevel_vcycle with zero initial guess (internal layout).
+// The same algorithm for the Lax-Friedrichs trace system (FP64): block-Jacobi
+// or Chebyshev smoothing on the 2(p+1) x 2(p+1) facet blocks, restriction
+// pi^T to RT0, n_coarse Chebyshev steps on the RT0 coarse problem from zero,
+// x += pi e_c, post-smoothing.
+cudaError_t precond_lf(hdg_handle *h, const double *v, double *z, const double *w_src) {
+    KSpace<double> &k = h->ws->k64;
+    cudaStream_t s = h->stream;
+    const size_t NT = h->NT;
+    const bool cheb = h->prm.smoother == 1;
+    double *x = k.t0, *x2 = k.t1;
+    cudaError_t e;
+    // pre-smoothing from zero
+    if (h->prm.n_pre == 0) {
+        if ((e = KL(HDG_PROF_KRYLOV, 1, launch_fill<double>(x, 0.0, NT, s))) != cudaSuccess) return e;
+    } else {
+        if ((e = KL(HDG_PROF_SMOOTH_FIRST64, 1,
+                    launch_smooth_first_t<double>(h, v, x, w_src, w_src ? &h->ws->rb->hnext : nullptr,
+                                                  const_cast<double *>(v), cheb ? h->cheb_omega[0] : 0.0))) !=
+            cudaSuccess)
+            return e;
+        double *prev = nullptr;
+        for (int i = 1; i < h->prm.n_pre; ++i) {
+            double *o = cheb ? (prev ? prev : x2) : x2;
+            e = cheb ? KL(HDG_PROF_SMOOTH64, 1, launch_smooth_cheb_t<double>(h, v, x, o, h->cheb_omega[i],
+                                                                             h->cheb_beta[i], prev))
+                     : KL(HDG_PROF_SMOOTH64, 1, launch_smooth_t<double>(h, v, x, o));
+            if (e != cudaSuccess) return e;
+            if (cheb) {
+                prev = x;
+                x = o;
+            } else {
+                std::swap(x, x2);
+            }
+        }
+        x2 = (x == k.t0) ? k.t1 : k.t0;
+    }
+    // residual, restriction to RT0, coarse Chebyshev steps, prolongation
+    if ((e = KL(HDG_PROF_RESIDUAL64, 1, launch_residual_t<double>(h, v, x, k.res, true))) != cudaSuccess) return e;
+    Rt0Dev &R = h->rt0;
+    if ((e = KL(HDG_PROF_TRANSFER, 1, launch_rt0_restrict(h, k.res, R.rc))) != cudaSuccess) return e;
+    double *cur = R.e0, *prev = nullptr, *spare[2] = {R.e1, R.e2};
+    if ((e = KL(HDG_PROF_P1, 1, launch_rt0_cheb(h, R.rc, nullptr, nullptr, cur, h->cheb_c_omega[0], 0.0))) !=
+        cudaSuccess)
+        return e;
+    for (int i = 1; i < h->prm.n_coarse; ++i) {
+        double *o = prev ? prev : spare[0];
+        if (o == cur) o = spare[1];
+        if ((e = KL(HDG_PROF_P1, 1, launch_rt0_cheb(h, R.rc, cur, prev, o, h->cheb_c_omega[size_t(i)],
+                                                      h->cheb_c_beta[size_t(i)]))) != cudaSuccess)
+            return e;
+        prev = cur;
+        cur = o;
+    }
+    if ((e = KL(HDG_PROF_TRANSFER, 1, launch_rt0_prolong_add(h, cur, x))) != cudaSuccess) return e;
+    // post-smoothing from x
+    const int np = h->prm.n_post;
+    if (np == 0) return cudaMemcpyAsync(z, x, sizeof(double) * NT, cudaMemcpyDeviceToDevice, s);
+    if (!cheb) {
+        for (int i = 0; i < np; ++i) {
+            double *o = (i == np - 1) ? z : x2;
+            if ((e = KL(HDG_PROF_SMOOTH64, 1, launch_smooth_t<double>(h, v, x, o))) != cudaSuccess) return e;
+            if (i < np - 1) std::swap(x, x2);
+        }
+        return cudaSuccess;
+    }
+    // Chebyshev from x_0 = x: three vectors x, x2, k.res (free after the restriction)
+    double *buf[3] = {x, x2, k.res};
+    int cur_i = 0, prev_i = -1;
+    for (int i = 0; i < np; ++i) {
+        int out_i = 0;
+        while (out_i == cur_i || out_i == prev_i) ++out_i;
+        double *o = (i == np - 1) ? z : buf[out_i];
+        if ((e = KL(HDG_PROF_SMOOTH64, 1, launch_smooth_cheb_t<double>(h, v, buf[cur_i], o, h->cheb_omega[size_t(i)],
+                                                                         i ? h->cheb_beta[size_t(i)] : 0.0,
+                                                                         i ? buf[prev_i] : nullptr))) != cudaSuccess)
+            return e;
+        prev_i = cur_i;
+        cur_i = out_i;
+    }
+    return cudaSuccess;
+}
+
 // With w_src (Arnoldi steps j >= 1, n_pre >= 1), v is first formed as
 // w_src / h_{j+1,j} by the first smoothing sweep, which stores it to v.
 template <typename T>
 cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr) {
+    if (h->prm.flux == 1) {
+        if constexpr (std::is_same<T, double>::value) return precond_lf(h, v, z, w_src);
+        return cudaErrorInvalidValue;
+    }
     KSpace<T> &k = kspace<T>(h);
     cudaStream_t s = h->stream;
     const size_t NT = h->NT;
@@ -904,6 +998,9 @@ void free_handle(hdg_handle *h) {
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     h->prof.pool.clear();
     imex_release(h);
+    dfree(h->rt0.nbr); dfree(h->rt0.rev); dfree(h->rt0.ptr); dfree(h->rt0.code); dfree(h->rt0.piw);
+    dfree(h->rt0.loc); dfree(h->rt0.fK); dfree(h->rt0.Sc); dfree(h->rt0.dinv);
+    dfree(h->rt0.rc); dfree(h->rt0.e0); dfree(h->rt0.e1); dfree(h->rt0.e2);
     dfree(h->gal.ptr0);
     dfree(h->gal.code0);
     for (auto *p_ : h->gal.ptr) cudaFree(p_);
@@ -1177,6 +1274,20 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
         int rc = set_tail_start(h, tail_max);
         if (rc) return rc;
     }
+    if (prm->flux == 1) {
+        Rt0Host rh;
+        const std::string re_ = build_rt0(hm, h->p, rh);
+        if (!re_.empty()) return fail(h, HDG_EINVAL, re_);
+        for (int K = 0; K < h->N; ++K)
+            rh.fK[size_t(K)] = (fcell[size_t(K) * 3] + fcell[size_t(K) * 3 + 1] + fcell[size_t(K) * 3 + 2]) / 3.0;
+        Rt0Dev &R = h->rt0;
+        TRY(upload(&R.nbr, rh.nbr, s)); TRY(upload(&R.rev, rh.rev, s));
+        TRY(upload(&R.ptr, rh.ptr, s)); TRY(upload(&R.code, rh.code, s));
+        TRY(upload(&R.piw, rh.piw, s)); TRY(upload(&R.loc, rh.loc, s)); TRY(upload(&R.fK, rh.fK, s));
+        TRY(dalloc(&R.Sc, 5 * NF)); TRY(dalloc(&R.dinv, NF));
+        TRY(dalloc(&R.rc, NF)); TRY(dalloc(&R.e0, NF)); TRY(dalloc(&R.e1, NF)); TRY(dalloc(&R.e2, NF));
+        TRY(cudaStreamSynchronize(s));      // the host vectors go out of scope
+    }
     if (prm->coarse_mode == 2) {
         GalerkinHost gh;
         const std::string ge = build_galerkin_lists(hm, gh);
@@ -1294,95 +1405,125 @@ int check_status(hdg_handle *h) {
     return HDG_OK;
 }
 
+// Ritz values of k Arnoldi steps (classical Gram-Schmidt twice, FP64) on the
+// operator apply(x, y, tmp) of n entries, from the host start vector v0 (in
+// device order), normalised here.  Stops early at an invariant subspace.
+int arnoldi_ritz_dev(hdg_handle *h, const std::vector<double> &v0_in, int k,
+                     const std::function<cudaError_t(const double *, double *, double *)> &apply,
+                     std::vector<std::complex<double>> &ritz, const char *what) {
+    Workspace &W = *h->ws;
+    cudaStream_t s = h->stream;
+    const size_t n = v0_in.size(), ld = (n + 3) / 4 * 4;
+    std::vector<double> v0(v0_in);
+    double nrm = 0.0;
+    for (double x : v0) nrm += x * x;
+    nrm = std::sqrt(nrm);
+    for (double &x : v0) x /= nrm;
+    double *V = nullptr, *tmp = nullptr, *w = nullptr, *part = nullptr, *dh = nullptr;
+    cudaError_t e = dalloc(&V, size_t(k + 1) * ld);
+    if (e == cudaSuccess) e = dalloc(&tmp, ld);
+    if (e == cudaSuccess) e = dalloc(&w, ld);
+    if (e == cudaSuccess) e = dalloc(&part, size_t(k + 2) * size_t(W.nchunk));
+    if (e == cudaSuccess) e = dalloc(&dh, size_t(k + 2));
+    if (e == cudaSuccess) e = cudaMemsetAsync(V, 0, sizeof(double) * size_t(k + 1) * ld, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w, 0, sizeof(double) * ld, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(V, v0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
+    std::vector<double> Hm(size_t(k + 1) * k, 0.0), hc(size_t(k + 2));
+    int m = k;
+    for (int j = 0; j < k && e == cudaSuccess; ++j) {
+        e = apply(V + size_t(j) * ld, w, tmp);
+        for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+            e = launch_multidot<double>(V, ld, j + 1, w, n, part, W.nchunk, s);
+            if (e == cudaSuccess) e = launch_reduce_partials(part, j + 1, W.nchunk, dh, s);
+            if (e == cudaSuccess) e = launch_multi_axpy<double>(w, V, ld, j + 1, dh, -1.0, n, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), dh, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            for (int i = 0; i <= j; ++i) Hm[size_t(i) * k + j] += hc[size_t(i)];
+        }
+        // ||w|| into dh[k + 1] (the square root written by the reduction)
+        if (e == cudaSuccess) e = launch_multidot<double>(w, ld, 1, w, n, part, W.nchunk, s);
+        if (e == cudaSuccess) e = launch_reduce_partials(part, 1, W.nchunk, dh, s, nullptr, 0, dh + k + 1);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), dh + k + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        double colmax = 0.0;
+        for (int i = 0; i <= j; ++i) colmax = std::max(colmax, std::fabs(Hm[size_t(i) * k + j]));
+        if (!(hc[0] > 1e-14 * colmax)) {
+            m = j + 1;                     // invariant subspace: the Ritz values are exact
+            break;
+        }
+        if (j + 1 < k) Hm[size_t(j + 1) * k + j] = hc[0];
+        e = launch_scale_copy<double>(w, V + size_t(j + 1) * ld, dh + k + 1, n, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dfree(V); dfree(tmp); dfree(w); dfree(part); dfree(dh);
+    if (e != cudaSuccess) return fail(h, HDG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    std::vector<double> Hs(size_t(m) * m);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) Hs[size_t(i) * m + j] = Hm[size_t(i) * k + j];
+    for (double x : Hs)
+        if (!std::isfinite(x)) return fail(h, HDG_ENAN, std::string(what) + ": non-finite Arnoldi entry");
+    ritz = hessenberg_eigenvalues(Hs, m);
+    return HDG_OK;
+}
+
+// Step coefficients of n Chebyshev steps on the ellipse (theta, delta2):
+// s_0 = 1/theta, s_k = 1 / (2 theta - delta^2 s_{k-1}), omega_0 = s_0,
+// omega_k = 2 s_k, beta_k = delta^2 s_k s_{k-1}.
+void chebyshev_coefficients(double theta, double delta2, int n, std::vector<double> &omega, std::vector<double> &beta) {
+    omega.assign(size_t(n), 0.0);
+    beta.assign(size_t(n), 0.0);
+    double sp = 1.0 / theta;
+    omega[0] = sp;
+    for (int i = 1; i < n; ++i) {
+        const double si = 1.0 / (2.0 * theta - delta2 * sp);
+        omega[size_t(i)] = 2.0 * si;
+        beta[size_t(i)] = delta2 * si * sp;
+        sp = si;
+    }
+}
+
+// The Chebyshev start vector v_i = 1 + ((37 i) mod 101) / 101 for index i.
+inline double cheb_start(size_t i) { return 1.0 + double((37 * i) % 101) / 101.0; }
+
 // The Chebyshev smoother's ellipse: Ritz values of cheb_steps Arnoldi steps on
-// D^-1 S (FP64 operator; classical Gram-Schmidt twice) from the start vector
-// v_i = 1 + ((37 i) mod 101) / 101 (i = facet * (p+1) + node), then the fit
-// of spectrum.cpp; or the ellipse given in the parameters.  Then the sweep
-// coefficients: s_0 = 1/theta, s_k = 1 / (2 theta - delta^2 s_{k-1}),
-// omega_0 = s_0, omega_k = 2 s_k, beta_k = delta^2 s_k s_{k-1}.
+// D^-1 S (i = facet * pp + node in the lambda layout), then the fit of
+// spectrum.cpp; or the ellipse given in the parameters.
 int chebyshev_setup(hdg_handle *h) {
     h->cheb_ritz.clear();
     if (h->prm.cheb_theta > 0) {
         h->cheb_theta = h->prm.cheb_theta;
         h->cheb_delta2 = h->prm.cheb_delta2;
     } else {
-        Workspace &W = *h->ws;
-        cudaStream_t s = h->stream;
-        const int k = h->prm.cheb_steps;
-        const size_t NT = h->NT, ld = (NT + 3) / 4 * 4, NF = h->NF, pp = h->pp;
-        double *V = nullptr, *tmp = nullptr, *w = nullptr, *part = nullptr, *dh = nullptr;
-        auto release = [&]() {
-            dfree(V); dfree(tmp); dfree(w); dfree(part); dfree(dh);
-        };
-        cudaError_t e = dalloc(&V, size_t(k + 1) * ld);
-        if (e == cudaSuccess) e = dalloc(&tmp, NT);
-        if (e == cudaSuccess) e = dalloc(&w, ld);
-        if (e == cudaSuccess) e = dalloc(&part, size_t(k + 2) * size_t(W.nchunk));
-        if (e == cudaSuccess) e = dalloc(&dh, size_t(k + 2));
-        std::vector<double> v0(NT);
-        double nrm = 0.0;
+        const size_t NF = h->NF, pp = h->pp;
+        std::vector<double> v0(h->NT);
         for (size_t e_ = 0; e_ < NF; ++e_)
-            for (size_t r = 0; r < pp; ++r) {
-                const double val = 1.0 + double((37 * (e_ * pp + r)) % 101) / 101.0;
-                v0[r * NF + e_] = val;
-                nrm += val * val;
-            }
-        nrm = std::sqrt(nrm);
-        for (double &x : v0) x /= nrm;
-        if (e == cudaSuccess) e = cudaMemsetAsync(V, 0, sizeof(double) * size_t(k + 1) * ld, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(w, 0, sizeof(double) * ld, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(V, v0.data(), sizeof(double) * NT, cudaMemcpyHostToDevice, s);
-        std::vector<double> Hm(size_t(k + 1) * k, 0.0), hc(size_t(k + 2));
-        int m = k;
-        for (int j = 0; j < k && e == cudaSuccess; ++j) {
-            e = launch_apply_t<double>(h, V + size_t(j) * ld, tmp);
-            if (e == cudaSuccess) e = launch_smooth_first_t<double>(h, tmp, w, nullptr, nullptr, nullptr, 1.0);
-            for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
-                e = launch_multidot<double>(V, ld, j + 1, w, NT, part, W.nchunk, s);
-                if (e == cudaSuccess) e = launch_reduce_partials(part, j + 1, W.nchunk, dh, s);
-                if (e == cudaSuccess) e = launch_multi_axpy<double>(w, V, ld, j + 1, dh, -1.0, NT, s);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), dh, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-                for (int i = 0; i <= j; ++i) Hm[size_t(i) * k + j] += hc[size_t(i)];
-            }
-            // ||w|| into dh[k + 1] (the square root written by the reduction)
-            if (e == cudaSuccess) e = launch_multidot<double>(w, ld, 1, w, NT, part, W.nchunk, s);
-            if (e == cudaSuccess) e = launch_reduce_partials(part, 1, W.nchunk, dh, s, nullptr, 0, dh + k + 1);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), dh + k + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) break;
-            double colmax = 0.0;
-            for (int i = 0; i <= j; ++i) colmax = std::max(colmax, std::fabs(Hm[size_t(i) * k + j]));
-            if (!(hc[0] > 1e-14 * colmax)) {
-                m = j + 1;                     // invariant subspace: the Ritz values are exact
-                break;
-            }
-            if (j + 1 < k) Hm[size_t(j + 1) * k + j] = hc[0];
-            e = launch_scale_copy<double>(w, V + size_t(j + 1) * ld, dh + k + 1, NT, s);
-        }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        release();
-        if (e != cudaSuccess) return fail(h, HDG_ECUDA, std::string("Chebyshev estimate: ") + cudaGetErrorString(e));
-        std::vector<double> Hs(size_t(m) * m);
-        for (int i = 0; i < m; ++i)
-            for (int j = 0; j < m; ++j) Hs[size_t(i) * m + j] = Hm[size_t(i) * k + j];
-        for (double x : Hs)
-            if (!std::isfinite(x)) return fail(h, HDG_ENAN, "Chebyshev estimate: non-finite Arnoldi entry");
-        h->cheb_ritz = hessenberg_eigenvalues(Hs, m);
+            for (size_t r = 0; r < pp; ++r) v0[r * NF + e_] = cheb_start(e_ * pp + r);
+        int rc = arnoldi_ritz_dev(h, v0, h->prm.cheb_steps, [&](const double *x, double *y, double *tmp) {
+            cudaError_t e = launch_apply_t<double>(h, x, tmp);
+            return e == cudaSuccess ? launch_smooth_first_t<double>(h, tmp, y, nullptr, nullptr, nullptr, 1.0) : e;
+        }, h->cheb_ritz, "Chebyshev estimate");
+        if (rc) return rc;
         chebyshev_ellipse(h->cheb_ritz, 0.1, 1.1, h->cheb_theta, h->cheb_delta2);
         if (!(h->cheb_theta > 0)) return fail(h, HDG_EBREAKDOWN, "Chebyshev estimate: no eigenvalue with Re > 0");
     }
-    const int n = std::max({h->prm.n_pre, h->prm.n_post, 1});
-    h->cheb_omega.assign(size_t(n), 0.0);
-    h->cheb_beta.assign(size_t(n), 0.0);
-    double sp = 1.0 / h->cheb_theta;
-    h->cheb_omega[0] = sp;
-    for (int i = 1; i < n; ++i) {
-        const double si = 1.0 / (2.0 * h->cheb_theta - h->cheb_delta2 * sp);
-        h->cheb_omega[size_t(i)] = 2.0 * si;
-        h->cheb_beta[size_t(i)] = h->cheb_delta2 * si * sp;
-        sp = si;
-    }
+    chebyshev_coefficients(h->cheb_theta, h->cheb_delta2, std::max({h->prm.n_pre, h->prm.n_post, 1}), h->cheb_omega,
+                           h->cheb_beta);
+    return HDG_OK;
+}
+
+// The Lax-Friedrichs coarse solve: ellipse of D_c^-1 S_c from cheb_steps
+// Arnoldi steps (start vector over the facets), n_coarse step coefficients.
+int lf_coarse_setup(hdg_handle *h) {
+    std::vector<double> v0(size_t(h->NF));
+    for (size_t f = 0; f < v0.size(); ++f) v0[f] = cheb_start(f);
+    int rc = arnoldi_ritz_dev(h, v0, h->prm.cheb_steps, [&](const double *x, double *y, double *) {
+        return launch_rt0_apply_dinv(h, x, y);
+    }, h->cheb_c_ritz, "RT0 coarse estimate");
+    if (rc) return rc;
+    chebyshev_ellipse(h->cheb_c_ritz, 0.1, 1.1, h->cheb_c_theta, h->cheb_c_delta2);
+    if (!(h->cheb_c_theta > 0)) return fail(h, HDG_EBREAKDOWN, "RT0 coarse estimate: no eigenvalue with Re > 0");
+    chebyshev_coefficients(h->cheb_c_theta, h->cheb_c_delta2, h->prm.n_coarse, h->cheb_c_omega, h->cheb_c_beta);
     return HDG_OK;
 }
 
@@ -1460,6 +1601,8 @@ void hdg_default_params(hdg_params *prm) {
     prm->cheb_theta = 0.0;
     prm->cheb_delta2 = 0.0;
     prm->cheb_steps = 20;
+    prm->flux = 0;
+    prm->n_coarse = 20;
 }
 
 int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hdg_handle **out) {
@@ -1475,8 +1618,13 @@ int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hd
         delete h;
         return fail(nullptr, HDG_EINVAL, e);
     }
+    if (prm->flux == 1 && h->hm.dim != 2) {
+        delete h;
+        return fail(nullptr, HDG_EINVAL, "the Lax-Friedrichs solver handles flat (dim = 2) meshes");
+    }
     h->p = prm->p;
-    h->pp = prm->p + 1;
+    h->pp = (prm->flux == 1 ? 2 : 1) * (prm->p + 1);     // trace dofs per facet
+    h->pf = h->pp - 1;
     h->np = n_cell_nodes(prm->p);
     h->nK = 3 * h->np;
     h->m = 3 * h->pp;
@@ -1521,6 +1669,18 @@ int hdg_condense(hdg_handle *h) {
     cudaStream_t s = h->stream;
     h->condensed = false;
     TRY(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), s));
+    if (h->prm.flux == 1) {
+        // Lax-Friedrichs: cell operators and the facet-row operator on 2(p+1) blocks,
+        // the RT0 coarse operator and its Chebyshev coarse solve
+        TRY(KL(HDG_PROF_CONDENSE, 2, launch_condense_lf(h)));
+        TRY(KL(HDG_PROF_CONDENSE, 2, launch_rt0_assemble(h)));
+        int rc = check_status(h);
+        if (rc) return rc;
+        if ((rc = lf_coarse_setup(h)) != HDG_OK) return rc;
+        if (h->prm.smoother == 1 && (rc = chebyshev_setup(h)) != HDG_OK) return rc;
+        h->condensed = true;
+        return HDG_OK;
+    }
     TRY(KL(HDG_PROF_CONDENSE, 1, launch_condense(h)));
     TRY(KL(HDG_PROF_CONDENSE, 1, launch_assemble(h)));
     const double tau = h->prm.tau, gH = h->prm.g * h->prm.H;
@@ -1555,6 +1715,25 @@ int hdg_condense(hdg_handle *h) {
     if (rc) return rc;
     if (h->prm.smoother == 1 && (rc = chebyshev_setup(h)) != HDG_OK) return rc;
     h->condensed = true;
+    return HDG_OK;
+}
+
+int hdg_get_rt0_chebyshev(const hdg_handle *hc, double *ellipse, double *ritz, int32_t *n_ritz) {
+    hdg_handle *h = const_cast<hdg_handle *>(hc);
+    if (!h) return HDG_EINVAL;
+    if (h->prm.flux != 1) return fail(h, HDG_ESTATE, "the handle does not use the Lax-Friedrichs solver");
+    if (!h->condensed) return fail(h, HDG_ESTATE, "hdg_condense has not run on this handle");
+    if (ellipse) {
+        ellipse[0] = h->cheb_c_theta;
+        ellipse[1] = h->cheb_c_delta2;
+    }
+    const int n = int(std::min<size_t>(h->cheb_c_ritz.size(), 64));
+    if (ritz)
+        for (int i = 0; i < n; ++i) {
+            ritz[2 * i] = h->cheb_c_ritz[size_t(i)].real();
+            ritz[2 * i + 1] = h->cheb_c_ritz[size_t(i)].imag();
+        }
+    if (n_ritz) *n_ritz = n;
     return HDG_OK;
 }
 
@@ -1823,6 +2002,7 @@ int hdg_profile_read(hdg_handle *h, double *ms, int64_t *launches) {
 int hdg_autotune(hdg_handle *h, int32_t *choice) {
     int rc = require_condensed(h);
     if (rc) return rc;
+    if (h->prm.flux == 1) return fail(h, HDG_EINVAL, "hdg_autotune serves the upwind solver");
     Workspace &W = *h->ws;
     cudaStream_t s = h->stream;
     const bool f32 = mode_ff(h->prm);   // the Krylov space the Arnoldi steps run in

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <functional>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/hdg.h"
@@ -174,6 +175,22 @@ struct GalerkinDev {
 };
 std::string build_galerkin_lists(const HostMesh &hm, GalerkinHost &g);
 
+// RT0 coarse space of the Lax-Friedrichs solver (k_lf.cu): facet-row
+// neighbours, prolongation weights piw [(b TB + q) NF + e], the reverse
+// neighbour map rev [(b'-1) NF + f], per-cell 3 x 3 matrices [N][M | R | D],
+// cell means of f, and per ELL slot (b NF + f) the contribution codes K*9 + i*3 + j
+struct Rt0Host {
+    std::vector<int32_t> nbr, rev, ptr, code;
+    std::vector<double> piw, loc, fK;
+};
+struct Rt0Dev {
+    int32_t *nbr = nullptr, *rev = nullptr, *ptr = nullptr, *code = nullptr;
+    double *piw = nullptr, *loc = nullptr, *fK = nullptr;
+    double *Sc = nullptr, *dinv = nullptr;       // [5][NF] coarse operator, [NF] inverse diagonal
+    double *rc = nullptr, *e0 = nullptr, *e1 = nullptr, *e2 = nullptr;   // coarse vectors
+};
+std::string build_rt0(const HostMesh &hm, int p, Rt0Host &o);
+
 // IMEX time stepping state (k_imex.cu)
 constexpr int kImexMaxStages = 5;
 struct Imex {
@@ -326,6 +343,8 @@ struct hdg_handle {
     std::string err;
     hdg_params prm{};
     int p = 0, pp = 0, np = 0, nK = 0, m = 0;
+    int pf = 0;          // the facet-row kernels' block degree: trace dofs per facet pp = pf + 1
+                         // (upwind: pp = p + 1; Lax-Friedrichs: pp = 2(p + 1))
     int N = 0, NF = 0, NT = 0, nv = 0, dim = 0;
     double tau_s = 0;
     cudaStream_t stream = nullptr;
@@ -374,6 +393,11 @@ struct hdg_handle {
     hdg::Learned lc;
     hdg::Imex imex;
     hdg::GalerkinDev gal;
+    hdg::Rt0Dev rt0;
+    // Lax-Friedrichs coarse solve: Chebyshev ellipse of D_c^-1 S_c, its Ritz values, step coefficients
+    double cheb_c_theta = 0.0, cheb_c_delta2 = 0.0;
+    std::vector<std::complex<double>> cheb_c_ritz;
+    std::vector<double> cheb_c_omega, cheb_c_beta;
     bool has_f = false;               // a non-zero Coriolis field was given to hdg_setup
     // Chebyshev smoother (smoother 1): the ellipse, the Ritz values it was
     // fitted to, and per step k the sweep coefficients omega_k (of D^-1 r)
@@ -439,6 +463,31 @@ cudaError_t launch_l2_evict(const void *buf, size_t bytes, uint32_t *sink, cudaS
 cudaError_t launch_imex_rates(hdg_handle *h, const double *u, const double *hh, double *nu, double *nh, double *lu,
                               double *lh);
 void imex_release(hdg_handle *h);
+
+// dispatch a facet-row kernel on the degree of its trace blocks (h->pf: the
+// blocks are (pf+1) x (pf+1)); pf = 5 (the vector trace at p = 2) exists in FP64 only
+#define HDG_DISPATCH_PF(pf, T, CALL) \
+    switch (pf) {                    \
+        case 1: { constexpr int P = 1; CALL; } break; \
+        case 2: { constexpr int P = 2; CALL; } break; \
+        case 3: { constexpr int P = 3; CALL; } break; \
+        case 4: { constexpr int P = 4; CALL; } break; \
+        case 5: if constexpr (std::is_same<T, double>::value) { constexpr int P = 5; CALL; } \
+                else { return cudaErrorInvalidValue; } break;                             \
+        default: return cudaErrorInvalidValue;        \
+    }
+
+// Lax-Friedrichs variant (k_lf.cu)
+cudaError_t launch_condense_lf(hdg_handle *h);
+cudaError_t launch_rhs_lf(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell);
+cudaError_t launch_recover_lf(hdg_handle *h, const double *r_u, const double *r_h, const double *lam, double *u,
+                              double *hout);
+cudaError_t launch_rt0_assemble(hdg_handle *h);
+cudaError_t launch_rt0_apply_dinv(hdg_handle *h, const double *x, double *y);
+cudaError_t launch_rt0_cheb(hdg_handle *h, const double *r, const double *x, const double *xprev, double *out,
+                            double omega, double beta);
+cudaError_t launch_rt0_restrict(hdg_handle *h, const double *r, double *rc);
+cudaError_t launch_rt0_prolong_add(hdg_handle *h, const double *ec, double *x);
 
 cudaError_t launch_condense(hdg_handle *h);
 cudaError_t launch_assemble(hdg_handle *h);

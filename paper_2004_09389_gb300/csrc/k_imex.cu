@@ -327,6 +327,8 @@ void hdg::imex_release(hdg_handle *h) { imex_free(h->imex); }
 
 extern "C" int hdg_imex_init(hdg_handle *h, const double *f_vertex) {
     if (!h) return HDG_EINVAL;
+    if (h->prm.flux != 0)
+        return imex_fail(h, HDG_EINVAL, "hdg_imex_init: the IMEX stages use the upwind solver");
     if (h->has_f)
         return imex_fail(h, HDG_EINVAL,
                          "hdg_imex_init: the implicit stages have no Coriolis term; set the handle up with "

@@ -469,13 +469,13 @@ inline bool bf16_pre(hdg_handle *h) { return h->prm.precision == HDG_MIXED_BF16 
 template <typename T>
 cudaError_t launch_apply_dots_t(hdg_handle *h, const T *x, T *y, const T *V, size_t ld, int k, double *partial,
                                 unsigned int *counter, double *hdots) {
-    HDG_DISPATCH_P(h->p, (apply_dots_kernel<P, T, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(
+    HDG_DISPATCH_PF(h->pf, T, (apply_dots_kernel<P, T, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(
                              h->NF, Ops<T>::S(h, false), h->d_nbr, x, y, V, ld, k, partial, counter, hdots)));
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_apply_t(hdg_handle *h, const T *x, T *y) {
-    HDG_DISPATCH_P(h->p, (apply_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, false), h->d_nbr, x, y)));
+    HDG_DISPATCH_PF(h->pf, T, (apply_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, false), h->d_nbr, x, y)));
     return cudaGetLastError();
 }
 // residual / smoothing kernels serve the preconditioner (pre = true) or the
@@ -483,11 +483,11 @@ cudaError_t launch_apply_t(hdg_handle *h, const T *x, T *y) {
 template <typename T>
 cudaError_t launch_residual_t(hdg_handle *h, const T *b, const T *x, T *r, bool pre) {
     if constexpr (std::is_same<T, float>::value) if (pre && bf16_pre(h)) {
-        HDG_DISPATCH_P(h->p, (residual_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, h->d_nbr, b, x, r)));
+        HDG_DISPATCH_PF(h->pf, T, (residual_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, h->d_nbr, b, x, r)));
         return cudaGetLastError();
     }
     {
-        HDG_DISPATCH_P(h->p, (residual_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, pre), h->d_nbr, b, x, r)));
+        HDG_DISPATCH_PF(h->pf, T, (residual_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, pre), h->d_nbr, b, x, r)));
     }
     return cudaGetLastError();
 }
@@ -495,11 +495,11 @@ template <typename T>
 cudaError_t launch_smooth_t(hdg_handle *h, const T *b, const T *x, T *xout) {
     const T om = T(h->prm.omega);
     if constexpr (std::is_same<T, float>::value) if (bf16_pre(h)) {
-        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, om, T(0), nullptr)));
+        HDG_DISPATCH_PF(h->pf, T, (smooth_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, om, T(0), nullptr)));
         return cudaGetLastError();
     }
     {
-        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, om, T(0), nullptr)));
+        HDG_DISPATCH_PF(h->pf, T, (smooth_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, om, T(0), nullptr)));
     }
     return cudaGetLastError();
 }
@@ -508,11 +508,11 @@ template <typename T>
 cudaError_t launch_smooth_cheb_t(hdg_handle *h, const T *b, const T *x, T *xout, double omega, double beta,
                                  const T *xprev) {
     if constexpr (std::is_same<T, float>::value) if (bf16_pre(h)) {
-        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, __nv_bfloat16, true><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, T(omega), T(beta), xprev)));
+        HDG_DISPATCH_PF(h->pf, T, (smooth_kernel<P, T, __nv_bfloat16, true><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, T(omega), T(beta), xprev)));
         return cudaGetLastError();
     }
     {
-        HDG_DISPATCH_P(h->p, (smooth_kernel<P, T, T, true><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, T(omega), T(beta), xprev)));
+        HDG_DISPATCH_PF(h->pf, T, (smooth_kernel<P, T, T, true><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, T(omega), T(beta), xprev)));
     }
     return cudaGetLastError();
 }
@@ -520,7 +520,7 @@ template <typename T>
 cudaError_t launch_smooth_first_t(hdg_handle *h, const T *b, T *x, const T *w, const double *hnext, T *bout,
                                   double omega) {
     const T om = T(omega > 0 ? omega : h->prm.omega);
-    HDG_DISPATCH_P(h->p, (smooth_first_kernel<P, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::D(h), b, x, om, w, hnext, bout)));
+    HDG_DISPATCH_PF(h->pf, T, (smooth_first_kernel<P, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::D(h), b, x, om, w, hnext, bout)));
     return cudaGetLastError();
 }
 template <typename T>
@@ -611,6 +611,7 @@ cudaError_t launch_rhs_gather(hdg_handle *h, const double *ycell, double *g) {
 }
 
 cudaError_t launch_rhs(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell) {
+    if (h->prm.flux == 1) return launch_rhs_lf(h, r_u, r_h, g, ycell);
     size_t n = size_t(h->N) * h->m;
     HDG_DISPATCH_P(h->p, (rhs_cell_kernel<P><<<blocks(n, 256), 256, 0, h->stream>>>(h->N, h->d_W, r_u, r_h, ycell)));
     cudaError_t e = cudaGetLastError();
@@ -620,6 +621,7 @@ cudaError_t launch_rhs(hdg_handle *h, const double *r_u, const double *r_h, doub
 
 cudaError_t launch_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lam, double *u,
                            double *hout) {
+    if (h->prm.flux == 1) return launch_recover_lf(h, r_u, r_h, lam, u, hout);
     size_t n = size_t(h->N) * h->nK;
     HDG_DISPATCH_P(h->p, (recover_kernel<P><<<blocks(n, 256), 256, 0, h->stream>>>(h->N, h->NF, h->d_Rm, h->d_Xb, r_u, r_h, lam, h->d_facet_of, h->d_flip, u, hout)));
     return cudaGetLastError();

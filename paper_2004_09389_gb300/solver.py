@@ -89,7 +89,7 @@ class HDGSolver:
         ru = np.ascontiguousarray(r_u, dtype=np.float64)
         rh = np.ascontiguousarray(r_h, dtype=np.float64)
         assert ru.shape == (self.n_cells, 2, self.n_p) and rh.shape == (self.n_cells, self.n_p)
-        lam = np.empty((self.n_facets, self.p + 1))
+        lam = np.empty((self.n_facets, self.n_trace // self.n_facets))   # p+1 (upwind) or 2(p+1) (Lax-Friedrichs)
         info = L.hdg_solve_info()
         rc = self.lib.hdg_solve(self.h, ru.ctypes.data, rh.ctypes.data, lam.ctypes.data, C.byref(info))
         L.check(self.h, rc, allow=(L.HDG_ENOCONV, L.HDG_EBREAKDOWN) if allow_fail else ())
@@ -190,12 +190,14 @@ class HDGSolver:
                                       C.byref(loss)))
         return loss.value, g
 
-    def chebyshev(self):
-        """The Chebyshev smoother's ellipse (theta, delta^2) and the Ritz values it was fitted to."""
+    def chebyshev(self, coarse: bool = False):
+        """The Chebyshev smoother's ellipse (theta, delta^2) and the Ritz values it was
+        fitted to; coarse=True: those of the Lax-Friedrichs RT0 coarse solve."""
         ell = np.zeros(2)
         ritz = np.zeros(128)
         n = C.c_int32(0)
-        L.check(self.h, self.lib.hdg_get_chebyshev(self.h, ell.ctypes.data, ritz.ctypes.data, C.byref(n)))
+        fn = self.lib.hdg_get_rt0_chebyshev if coarse else self.lib.hdg_get_chebyshev
+        L.check(self.h, fn(self.h, ell.ctypes.data, ritz.ctypes.data, C.byref(n)))
         return (float(ell[0]), float(ell[1])), ritz[:2 * n.value:2] + 1j * ritz[1:2 * n.value:2]
 
     # ---------------------------------------------------------------- IMEX time stepping
