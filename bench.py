@@ -805,6 +805,57 @@ def imex_main(args):
     print(json.dumps(line))
 
 
+def lf_main(args):
+    """Lax-Friedrichs solver (vector trace, RT0 coarse space; flat meshes, FP64):
+    the benchmark's flat 256 x 256 x 2 workload (side 5.12e6 m, g = 9.81,
+    H = 1e3 m, f = 1e-4, k^-3 Gaussian RHS) at p = 1 and 2 with a shorter time
+    step (acoustic Courant 2: the Lax-Friedrichs two-level method needs many
+    more iterations than the upwind one at Courant 8); solves/s to rel.res 1e-8
+    (condensed RHS + FGMRES + recovery), the upwind FP64 solver on the same
+    workload beside it."""
+    import torch
+    from paper_2004_09389_gb300 import HDGSolver, HDG_FP64, build
+    build.build()
+    out = {}
+    for p in (1, 2):
+        wl = make_workload("flat", True, p, args.courant, args.seed)
+        ru_d, rh_d = torch.from_numpy(wl["ru"]).cuda(), torch.from_numpy(wl["rh"]).cuda()
+        row = {}
+        for name, flux in (("lax_friedrichs", 1), ("upwind", 0)):
+            s = HDGSolver(wl["mesh"], p, wl["tau"], wl["g"], wl["H"], f_vertex=wl["f"], rtol=args.rtol,
+                          precision=HDG_FP64, flux=flux, max_iter=3000, restart=args.restart)
+            tb = s.n_trace // s.n_facets
+            lam = torch.empty((s.n_facets, tb), dtype=torch.float64, device="cuda")
+            u = torch.empty((s.n_cells, 2, s.n_p), dtype=torch.float64, device="cuda")
+            h = torch.empty((s.n_cells, s.n_p), dtype=torch.float64, device="cuda")
+            for _ in range(args.warmup):
+                s.solve_dev(ru_d, rh_d, lam)
+                s.recover_dev(ru_d, rh_d, lam, u, h)
+            torch.cuda.synchronize()
+            infos = []
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
+            for _ in range(args.steps):
+                infos.append(s.solve_dev(ru_d, rh_d, lam))
+                s.recover_dev(ru_d, rh_d, lam, u, h)
+            e1.record(s.stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            row[name] = {"value": args.steps / (ms * 1e-3), "unit": "solves/s", "ms_per_step": ms / args.steps,
+                         "iters": infos[-1]["iters"], "true_rel_res": infos[-1]["true_rel_res"],
+                         "trace_dofs": s.n_trace}
+            s.close()
+        out[f"p{p}"] = row
+    line = {"metric": "HDG trace solves/s to rel.res 1e-8, Lax-Friedrichs vector trace with RT0 coarse space (FP64)",
+            "value": out["p1"]["lax_friedrichs"]["value"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": workload_name(NGRID, 1, args.courant) + "; also p=2",
+                       "precond": "2+2 block-Jacobi on 2(p+1) facet blocks, RT0 grad-div coarse problem by 20 "
+                                  "Chebyshev steps"},
+            **out}
+    print(json.dumps(line))
+
+
 def batch_main(args):
     import numpy as np
     import torch
@@ -932,7 +983,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--imex-scheme", dest="imex_scheme", default="ARS2", choices=["theta", "ARS2", "SSP2", "ARS3"])
-    ap.add_argument("--workload", default="flat", choices=["flat", "sphere", "sequence", "imex"],
+    ap.add_argument("--workload", default="flat", choices=["flat", "sphere", "sequence", "imex", "lf"],
                     help="flat: periodic 256x256x2 square (the headline); sphere: icosahedral sphere r=6; "
                          "sequence: learned sweep over a 50-step sequence on the r=7 sphere")
     ap.add_argument("--courant", type=float, default=8.0)
@@ -977,6 +1028,9 @@ def main():
         return
     if args.workload == "imex":
         imex_main(args)
+        return
+    if args.workload == "lf":
+        lf_main(args)
         return
 
     if args.oracle_run:
