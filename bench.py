@@ -857,9 +857,14 @@ def lf_main(args):
 
 
 def batch_main(args):
+    """The uneven batch two ways: merged (one host thread; the launches of all
+    problems merged into multi-problem kernels, one CUDA graph per wave; the
+    headline value) and threaded (hdg_solve_batch_dev: one stream per problem,
+    per-problem step graphs, a pool of host threads); then the same solves one
+    after another for the per-solve latency."""
     import numpy as np
     import torch
-    from paper_2004_09389_gb300 import HDGSolver, HDG_MIXED_FP32, build, solve_batch_dev
+    from paper_2004_09389_gb300 import HDGSolver, HDG_MIXED_FP32, MergedBatch, build, solve_batch_dev
     build.build()
     probs = batch_workload(args.batch, args.seed)
     solvers = [HDGSolver(x["mesh"], x["p"], x["tau"], x["g"], x["H"], f_vertex=x["f"], rtol=args.rtol,
@@ -869,15 +874,24 @@ def batch_main(args):
     ru = [torch.from_numpy(x["ru"]).cuda() for x in probs]
     rh = [torch.from_numpy(x["rh"]).cuda() for x in probs]
     lam = [torch.zeros((s.n_facets, s.p + 1), dtype=torch.float64, device="cuda") for s in solvers]
-    torch.cuda.synchronize()
-    for _ in range(args.warmup):
-        solve_batch_dev(solvers, ru, rh, lam)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        infos = solve_batch_dev(solvers, ru, rh, lam)
-    torch.cuda.synchronize()
-    t_batch = (time.perf_counter() - t0) / args.steps
+    n = len(solvers)
+
+    def timed(run):
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            run()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            out = run()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / args.steps, out
+
+    batch = MergedBatch(solvers)
+    t_merged, infos = timed(lambda: batch.solve_dev(ru, rh, lam))
+    st = batch.stats()
+    batch.close()
+    t_threaded, infos_t = timed(lambda: solve_batch_dev(solvers, ru, rh, lam))
     # the same solves one after another, for the per-solve latency
     lat = []
     for s, a, b, l in zip(solvers, ru, rh, lam):
@@ -886,12 +900,21 @@ def batch_main(args):
         s.solve_dev(a, b, l)
         torch.cuda.synchronize()
         lat.append(time.perf_counter() - t1)
-    n = len(solvers)
     line = {"metric": "batched HDG trace solves/s to rel.res 1e-8 (uneven problems, mixed precision)",
-            "value": n / t_batch, "unit": "solves/s", "n_problems": n, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_batch": t_batch * 1e3, "sequential_solves_per_s": n / sum(lat),
+            "value": n / t_merged, "unit": "solves/s", "n_problems": n, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_batch": t_merged * 1e3, "host_threads": 1,
+            "merged": {"waves_per_batch": st["waves"] / (args.steps + args.warmup),
+                       "launches_per_wave": st["launches"] / max(st["waves"], 1),
+                       "problem_launches_per_wave": st["records"] / max(st["waves"], 1),
+                       "graph_replays": st["replays"], "graph_builds": st["builds"],
+                       "groups": os.environ.get("HDG_BATCH_GROUPS", "4"),
+                       "host_ms_per_batch": {k[8:]: st[k] / 1e6 / (args.steps + args.warmup)
+                                             for k in ("host_ns_fibers", "host_ns_launch", "host_ns_wait")}},
+            "threaded_solves_per_s": n / t_threaded, "threaded_ms_per_batch": t_threaded * 1e3,
+            "sequential_solves_per_s": n / sum(lat),
             "latency_ms": {"median": float(np.median(lat)) * 1e3, "max": float(np.max(lat)) * 1e3},
             "iters": [i["iters"] for i in infos], "max_true_rel_res": max(i["true_rel_res"] for i in infos),
+            "same_iters_threaded": [i["iters"] for i in infos] == [i["iters"] for i in infos_t],
             "cells": [s.n_cells for s in solvers], "p": [s.p for s in solvers],
             "autotune": tuned, "data": "synthetic",
             "max_ftau": max(x["ftau"] for x in probs), "chebyshev_problems": sum(x["smoother"] for x in probs),

@@ -232,10 +232,53 @@ HDG_API int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h,
  * solves; every Arnoldi step is a replayed CUDA graph.  infos (may be NULL)
  * gets one entry per handle; the return value is the first non-OK status in
  * handle order.  Like hdg_solve_dev, results are complete once each handle's
- * stream has been synchronised.  (North-star batching; the paper solves one
+ * stream has been synchronised.  (Batching beyond the paper, which solves one
  * system at a time.) */
 HDG_API int hdg_solve_batch_dev(hdg_handle *const *hs, int n, const double *const *r_u, const double *const *r_h,
                                 double *const *lambda, hdg_solve_info *infos, int n_threads);
+
+/* Merged batched solves: one host thread drives n independent solves whose
+ * kernels run as merged launches.  Every problem follows exactly the steps of
+ * hdg_solve_dev (the same kernels with the same arguments, so the same
+ * results bit for bit); the launches that the problems issue between two
+ * decisions of their host logic (a residual estimate or a norm read back)
+ * form one wave.  Within a wave, the launches of different problems that run
+ * the same kernel with the same block size become one launch whose blocks
+ * cover all of them (at most 64 problems per launch; each problem's
+ * arguments travel in the kernel's parameter block), ordered as a DAG of
+ * per-problem chains and run as a CUDA graph; a graph is kept and replayed
+ * whenever the same wave recurs (same kernels, shapes and arguments).  The
+ * number of launches per wave therefore depends on the kernels in play (the
+ * degrees, the coarse-level structures), not on the number of problems.
+ *
+ * hdg_batch_create checks and records the handles (n >= 1, distinct, on the
+ * current device, condensed; upwind flux; precision HDG_MIXED_FP32 or
+ * HDG_MIXED_BF16; reorth = 0): HDG_EINVAL / HDG_ESTATE otherwise, with the
+ * reason in hdg_last_error(NULL).  hdg_batch_solve_dev solves r_u[i], r_h[i]
+ * (device pointers) into lambda[i] for every handle i, on a stream of the
+ * batch ordered after each handle's stream, and each handle's stream is
+ * ordered after the batch on return (the host also waits for the last wave,
+ * so the results are complete on return).  The handles must not be used
+ * elsewhere during the call, kernel timing (hdg_profile_enable) must be off
+ * and the learned smoother not enabled (HDG_ESTATE).  infos (may be NULL) gets
+ * one entry per handle; the return value is the first non-OK status in handle
+ * order, with its message in hdg_last_error(NULL).  hdg_batch_stats fills
+ * stats[0..7] = waves, merged launches, per-problem launches they carried,
+ * graphs replayed, graphs built, and host nanoseconds spent running the
+ * problems' host logic, merging and launching waves, and waiting for the
+ * last waves (totals since creation).  hdg_batch_destroy(NULL) is a no-op;
+ * destroy the batch before its handles.
+ *
+ * The problems are dealt into groups, each with its own stream, waves and
+ * graphs: while one group's wave runs, the host prepares another's.
+ * HDG_BATCH_GROUPS = G (1..64, default 4) deals them, largest first, round
+ * robin into G groups; 0 groups them by degree. */
+typedef struct hdg_batch hdg_batch;
+HDG_API int hdg_batch_create(hdg_handle *const *hs, int n, hdg_batch **out);
+HDG_API int hdg_batch_solve_dev(hdg_batch *b, const double *const *r_u, const double *const *r_h,
+                                double *const *lambda, hdg_solve_info *infos);
+HDG_API int hdg_batch_stats(const hdg_batch *b, int64_t *stats);
+HDG_API int hdg_batch_destroy(hdg_batch *b);
 
 /* Pick launch shapes for this handle by timing one Arnoldi step (preconditioner,
  * operator application, Gram-Schmidt) for each candidate: threads per block of
@@ -341,7 +384,7 @@ HDG_API int hdg_profile_read(hdg_handle *h, double *ms, int64_t *launches);
  * against.  HDG_EINVAL for other sizes. */
 HDG_API int hdg_fma_rate(int bytes, double *tflops);
 
-/* Learned facet-patch smoother (spec extension; the paper has no learned
+/* Learned facet-patch smoother (an extension beyond the paper, which has no learned
  * component).  In the FP32 inner solves of the mixed modes it replaces the last
  * post-smoothing sweep of the V-cycle by x += c(r), r = v - S x:
  *   X_e = (r_e, r of the four facets sharing a cell with e) / s_e, s_e their RMS,

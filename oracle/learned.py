@@ -1,7 +1,7 @@
 """Learned facet-patch smoother of the oracle (reference for the GPU kernels).
 
 Test infrastructure only (see the package docstring).  The paper has no
-learned component; this is the spec extension, written plainly so the
+learned component; this extends the method beyond the paper, written plainly so the
 GPU forward and backward kernels can be checked against it.
 
 For a trace residual r, every facet e gets the features

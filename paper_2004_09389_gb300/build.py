@@ -19,7 +19,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libhdg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["refelem.cpp", "mesh.cpp", "layout.cpp", "k_condense.cu", "k_trace.cu", "k_p1.cu", "k_krylov.cu",
-           "api.cu", "noalloc.cu", "k_learned.cu", "k_ff.cu", "k_measure.cu", "k_imex.cu", "spectrum.cpp", "k_galerkin.cu", "k_lf.cu"]
+           "api.cu", "noalloc.cu", "k_learned.cu", "k_ff.cu", "k_measure.cu", "k_imex.cu", "spectrum.cpp", "k_galerkin.cu", "k_lf.cu", "batch.cu"]
 
 
 def nvcc() -> str:

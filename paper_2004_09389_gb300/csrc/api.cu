@@ -21,6 +21,9 @@
 #include <cstring>
 #include <memory>
 
+#include <chrono>
+#include <ucontext.h>
+
 namespace hdg {
 
 template <typename T> cudaError_t launch_apply_t(hdg_handle *, const T *, T *);
@@ -75,6 +78,7 @@ struct Workspace {
     int32_t *flags = nullptr;
     // pinned readback
     double *host_buf = nullptr;   // [8]: 0 readback, 1 restart scale, 2 refinement scale, 3 s_0, 4 ||b||
+    double *host_buf_dev = nullptr;   // its device address (read by recorded copies in batched solves)
     int32_t *host_flags = nullptr;
     // staging for host-pointer entry points and for recover defaults
     double *ru = nullptr, *rh = nullptr, *lam_ext = nullptr, *u = nullptr, *hh = nullptr;
@@ -230,6 +234,32 @@ template <typename T> constexpr int cat_apply() { return sizeof(T) == 8 ? HDG_PR
 template <typename T> constexpr int cat_res() { return sizeof(T) == 8 ? HDG_PROF_RESIDUAL64 : HDG_PROF_RESIDUAL32; }
 template <typename T> constexpr int cat_smooth() { return sizeof(T) == 8 ? HDG_PROF_SMOOTH64 : HDG_PROF_SMOOTH32; }
 template <typename T> constexpr int cat_first() { return sizeof(T) == 8 ? HDG_PROF_SMOOTH_FIRST64 : HDG_PROF_SMOOTH_FIRST32; }
+
+// Stream-ordered copy of bytes on the handle's stream.  Inside a batched
+// solve it is recorded as a copy kernel; a host source (only the page-locked
+// scalar buffer is used as one) is then read through its device address.
+cudaError_t dcopy(hdg_handle *h, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
+    if (batch_recorder()) {
+        const Workspace &W = *h->ws;
+        if (kind == cudaMemcpyHostToDevice) {
+            const double *p = static_cast<const double *>(src);
+            if (!(p >= W.host_buf && p < W.host_buf + 8)) return cudaErrorInvalidValue;
+            src = W.host_buf_dev + (p - W.host_buf);
+        }
+        return launch_copy(dst, src, bytes, h->stream);
+    }
+    return cudaMemcpyAsync(dst, src, bytes, kind, h->stream);
+}
+// Stream-ordered zero fill (recorded inside a batched solve, as dcopy)
+cudaError_t dzero(hdg_handle *h, void *dst, size_t bytes) {
+    if (batch_recorder()) return launch_copy(dst, nullptr, bytes, h->stream);
+    return cudaMemsetAsync(dst, 0, bytes, h->stream);
+}
+
+// Inside a batched solve: give control back to the batch until the word at
+// addr (page-locked, written by a recorded kernel) holds want (defined with
+// the batch entry points)
+int batch_yield(hdg_handle *h, const volatile int32_t *addr, int32_t want);
 
 // ---------------------------------------------------------------- preconditioner
 
@@ -533,7 +563,7 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr) {
     const int np = h->prm.n_post;
     if (np == 0) {
         if ((e = KL(HDG_PROF_TRANSFER, 1, launch_prolong_add_t<T>(h, ec, x))) != cudaSuccess) return e;
-        return cudaMemcpyAsync(z, x, sizeof(T) * NT, cudaMemcpyDeviceToDevice, s);
+        return dcopy(h, z, x, sizeof(T) * NT, cudaMemcpyDeviceToDevice);
     }
     bool learned = false, collect = false;
     if constexpr (std::is_same<T, float>::value) {
@@ -644,6 +674,10 @@ cudaError_t dots(hdg_handle *h, const T *V, int k, const T *w, double *out, Host
 // status bit and return when theirs runs out).
 int wait_host_value(hdg_handle *h, int32_t want) {
     Workspace &W = *h->ws;
+    if (batch_recorder()) {
+        const int rc = batch_yield(h, &W.host_val->seq, want);
+        if (rc) return rc;
+    }
     const volatile int32_t *seq = &W.host_val->seq;
     for (uint64_t it = 1;; ++it) {
         if (*seq == want) break;
@@ -664,7 +698,10 @@ int wait_host_value(hdg_handle *h, int32_t want) {
 template <typename T>
 int norm_host(hdg_handle *h, const T *v, double &out) {
     Workspace &W = *h->ws;
-    const int32_t want = W.val_seq = W.val_seq % 1000000000 + 1;
+    // the previous hand-over was seen, so no write to the word is in flight;
+    // one fixed number keeps the launch arguments the same from call to call
+    W.host_val->seq = 0;
+    const int32_t want = 1;
     TRY(dots<T>(h, v, 1, v, W.nrm2, W.host_val_dev, want));
     if (h->prof.on) {
         TRY(cudaStreamSynchronize(h->stream));
@@ -730,6 +767,10 @@ cudaError_t arnoldi_step(hdg_handle *h, int j) {
 // device-side wait of the library being bounded.
 int wait_readback(hdg_handle *h, int j) {
     Workspace &W = *h->ws;
+    if (batch_recorder()) {
+        const int rc = batch_yield(h, &W.host_rb->seq, j + 1);
+        if (rc) return rc;
+    }
     const volatile int32_t *seq = &W.host_rb->seq;
     for (uint64_t it = 1;; ++it) {
         if (*seq == j + 1) break;
@@ -751,7 +792,7 @@ template <typename T>
 int run_arnoldi_step(hdg_handle *h, int j) {
     Workspace &W = *h->ws;
     cudaStream_t s = h->stream;
-    if (h->prof.on || !W.use_graphs || h->lc.collecting) {
+    if (h->prof.on || !W.use_graphs || h->lc.collecting || batch_recorder()) {
         TRY(arnoldi_step<T>(h, j));
         return HDG_OK;
     }
@@ -801,14 +842,14 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
     flag_out = 0;
     est_out = beta / bnorm;
     // s = [beta, 0, ...]
-    TRY(cudaMemsetAsync(W.sv, 0, sizeof(double) * (m + 1), s));
-    TRY(cudaMemsetAsync(W.Hm, 0, sizeof(double) * (m + 1) * m, s));
+    TRY(dzero(h, W.sv, sizeof(double) * (m + 1)));
+    TRY(dzero(h, W.Hm, sizeof(double) * (m + 1) * m));
     if (beta_on_device) {
         // s_0 = ||b|| as the norm kernel left it in W.bnorm (first cycle, zero guess)
-        TRY(cudaMemcpyAsync(W.sv, W.bnorm, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        TRY(dcopy(h, W.sv, W.bnorm, sizeof(double), cudaMemcpyDeviceToDevice));
     } else {
         W.host_buf[3] = beta;
-        TRY(cudaMemcpyAsync(W.sv, W.host_buf + 3, sizeof(double), cudaMemcpyHostToDevice, s));
+        TRY(dcopy(h, W.sv, W.host_buf + 3, sizeof(double), cudaMemcpyHostToDevice));
     }
     int j = 0;
     double hist[72];
@@ -880,7 +921,7 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
         // host_buf[4] is written again only after the next norm, whose hand-over
         // follows this copy in the stream
         W.host_buf[4] = bnorm;
-        TRY(cudaMemcpyAsync(W.bnorm, W.host_buf + 4, sizeof(double), cudaMemcpyHostToDevice, s));
+        TRY(dcopy(h, W.bnorm, W.host_buf + 4, sizeof(double), cudaMemcpyHostToDevice));
     }
     int total = 0;
     for (bool first = true;; first = false) {
@@ -902,7 +943,7 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
         const bool beta_dev = first && unit_rhs;     // W.scal and W.bnorm already hold ||b||
         if (!beta_dev) {
             W.host_buf[1] = beta;
-            TRY(cudaMemcpyAsync(W.scal, W.host_buf + 1, sizeof(double), cudaMemcpyHostToDevice, s));
+            TRY(dcopy(h, W.scal, W.host_buf + 1, sizeof(double), cudaMemcpyHostToDevice));
         }
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_scale_copy<T>(r0, k.V, W.scal, W.NT, s)));
         int done, flag;
@@ -965,7 +1006,7 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info)
             return fail(h, HDG_ENOCONV, "maximum number of iterations reached");
         // b32 = r / ||r||, solve S d = b32 in FP32, x += ||r|| d
         W.host_buf[2] = beta;
-        TRY(cudaMemcpyAsync(W.beta, W.host_buf + 2, sizeof(double), cudaMemcpyHostToDevice, s));
+        TRY(dcopy(h, W.beta, W.host_buf + 2, sizeof(double), cudaMemcpyHostToDevice));
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_d2f_scaled(r, k.b, W.beta, W.NT, s)));
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<float>(k.x, 0.0f, W.NT, s)));
         hdg_solve_info inner{};
@@ -1389,6 +1430,7 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(cudaHostGetDevicePointer(reinterpret_cast<void **>(&W.host_val_dev), W.host_val, 0));
     TRY(dalloc(&W.flags, 1));
     TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_buf), 8 * sizeof(double)));
+    TRY(cudaHostGetDevicePointer(reinterpret_cast<void **>(&W.host_buf_dev), W.host_buf, 0));
     TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_flags), 4 * sizeof(int32_t)));
     TRY(cudaStreamSynchronize(s));
     return HDG_OK;
@@ -1550,7 +1592,7 @@ int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solv
     } else {
         rc = solve_mixed(h, W.g, W.x, info);
     }
-    {
+    if (!batch_recorder()) {   // a batched solve checks the status words after its last wave
         int32_t st = 0;
         TRY(cudaMemcpyAsync(&st, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         TRY(cudaStreamSynchronize(s));
@@ -1563,9 +1605,112 @@ int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solv
     }
     info.status = rc;
     info.fallback_used = h->lc.fallback ? 1 : 0;
-    TRY(cudaMemcpyAsync(W.lam_int, W.x, sizeof(double) * W.NT, cudaMemcpyDeviceToDevice, s));
+    TRY(dcopy(h, W.lam_int, W.x, sizeof(double) * W.NT, cudaMemcpyDeviceToDevice));
     W.have_lambda = true;
     return rc;
+}
+
+// ---------------------------------------------------------------- merged batches
+// Each problem of a merged batch runs the host logic of hdg_solve_dev
+// unchanged, as a fiber (a user-level context on its own stack) of the one
+// calling thread.  While a fiber runs, its launches are recorded; where the
+// host logic would wait for a value from the GPU, the fiber hands control
+// back to the batch loop.  Once every unfinished fiber of a group waits with
+// launches recorded, the loop merges and launches them as the group's next
+// wave.  A fiber is resumed as soon as the word it waits on arrives, while the
+// rest of its wave may still run, so that its next launches are recorded by
+// the time the wave ends.
+constexpr size_t kFiberStack = size_t(512) << 10;
+
+struct Fiber {
+    ucontext_t ctx;
+    std::unique_ptr<unsigned char[]> stack;
+    hdg_handle *h = nullptr;
+    const double *r_u = nullptr, *r_h = nullptr;
+    double *lambda = nullptr;
+    int32_t *status_dev = nullptr;   // device address of this problem's page-locked status word
+    hdg_solve_info info{};
+    int rc = HDG_OK;
+    bool done = false;
+    bool launched = false;           // the launches it recorded before its wait have been launched
+    const volatile int32_t *wait_addr = nullptr;
+    int32_t wait_want = 0;
+    Recorder rec;
+};
+
+thread_local Fiber *t_fiber = nullptr;            // the fiber running on this thread
+thread_local ucontext_t *t_sched = nullptr;       // the batch loop it returns to
+thread_local const char *t_wave_error = nullptr;  // set once a wave has failed
+
+int batch_yield(hdg_handle *h, const volatile int32_t *addr, int32_t want) {
+    Fiber *f = t_fiber;
+    if (!f || !t_sched) return fail(h, HDG_ESTATE, "launch recording outside a batched solve");
+    f->wait_addr = addr;
+    f->wait_want = want;
+    f->launched = false;
+    swapcontext(&f->ctx, t_sched);
+    if (t_wave_error) return fail(h, HDG_ECUDA, std::string("batched solve: ") + t_wave_error);
+    return HDG_OK;
+}
+
+// one problem: the steps of hdg_solve_dev, then its status word to the host
+void fiber_entry() {
+    Fiber *f = t_fiber;
+    hdg_handle *h = f->h;
+    f->rc = solve_internal(h, f->r_u, f->r_h, f->info);
+    if (f->rc != HDG_ECUDA) {
+        const cudaError_t e = KL(HDG_PROF_LAYOUT, 1, launch_to_external(h, h->ws->x, f->lambda));
+        if (e != cudaSuccess) f->rc = fail(h, HDG_ECUDA, std::string("launch_to_external: ") + cudaGetErrorString(e));
+        h->ws->have_rhs = false;
+    }
+    const cudaError_t e2 = launch_copy(f->status_dev, h->d_status, sizeof(int32_t), h->stream);
+    if (e2 != cudaSuccess && f->rc == HDG_OK)
+        f->rc = fail(h, HDG_ECUDA, std::string("status copy: ") + cudaGetErrorString(e2));
+    f->done = true;
+}
+
+}  // namespace
+
+struct hdg_batch {
+    // Problems are dealt into groups; each group has its own stream, its own
+    // waves and graphs, so that the host prepares one group's next wave while
+    // the waves of the others run.
+    struct Group {
+        std::vector<int> idx;                     // its problems
+        std::vector<Recorder *> recs;
+        cudaStream_t stream = nullptr;
+        cudaEvent_t ev = nullptr;                 // end of its last wave
+        bool inflight = false;
+        hdg::WaveRunner runner;
+    };
+    std::vector<hdg_handle *> hs;
+    std::vector<std::unique_ptr<Fiber>> fibers;   // never moved: a context holds pointers into itself
+    std::vector<std::unique_ptr<Group>> groups;
+    std::vector<int> group_of;                    // per problem
+    int device = 0;
+    std::vector<cudaEvent_t> ev_in;               // one per handle: its stream's work before the batch
+    int32_t *status_host = nullptr, *status_dev = nullptr;   // page-locked, one word per handle
+    int64_t ns_fibers = 0, ns_launch = 0, ns_wait = 0;       // host time: running fibers, merging/launching, waiting
+};
+
+namespace {
+
+void batch_release(hdg_batch *b) {
+    if (!b) return;
+    for (auto &g : b->groups) {
+        g->runner.clear();
+        if (g->ev) cudaEventDestroy(g->ev);
+        if (g->stream) cudaStreamDestroy(g->stream);
+    }
+    for (cudaEvent_t e : b->ev_in)
+        if (e) cudaEventDestroy(e);
+    if (b->status_host) cudaFreeHost(b->status_host);
+    delete b;
+}
+
+int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
 }
 
 }  // namespace
@@ -2118,6 +2263,289 @@ int hdg_solve_batch_dev(hdg_handle *const *hs, int n, const double *const *r_u, 
             g_setup_error = "batch entry " + std::to_string(i) + ": " + hs[i]->err;
             return rcs[i];
         }
+    return HDG_OK;
+}
+
+int hdg_batch_create(hdg_handle *const *hs, int n, hdg_batch **out) {
+    if (!out) return fail(nullptr, HDG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !hs) return fail(nullptr, HDG_EINVAL, "a batch needs at least one handle");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, HDG_ECUDA, "cudaGetDevice failed");
+    for (int i = 0; i < n; ++i) {
+        hdg_handle *h = hs[i];
+        const std::string at = "batch entry " + std::to_string(i) + ": ";
+        if (!h) return fail(nullptr, HDG_EINVAL, at + "NULL handle");
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == h) return fail(nullptr, HDG_EINVAL, at + "the same handle twice");
+        if (h->device != dev) return fail(nullptr, HDG_EINVAL, at + "handle set up on another device");
+        if (!h->condensed) return fail(nullptr, HDG_ESTATE, at + "hdg_condense has not run on this handle");
+        if (!mode_ff(h->prm))
+            return fail(nullptr, HDG_EINVAL, at + "merged batches run the precisions HDG_MIXED_FP32 and HDG_MIXED_BF16");
+        if (h->prm.flux != 0) return fail(nullptr, HDG_EINVAL, at + "merged batches run the upwind flux");
+        if (h->prm.reorth != 0) return fail(nullptr, HDG_EINVAL, at + "merged batches run with reorth = 0");
+    }
+    std::unique_ptr<hdg_batch, void (*)(hdg_batch *)> b(new hdg_batch, batch_release);
+    b->hs.assign(hs, hs + n);
+    b->device = dev;
+    auto cu = [](cudaError_t e, const char *what) {
+        return e == cudaSuccess ? HDG_OK : fail(nullptr, HDG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    int rc;
+    // groups: HDG_BATCH_GROUPS = G >= 1 deals the problems, largest first (trace
+    // unknowns NT), round-robin into G groups; 0 groups them by degree p
+    int G = 4;
+    if (const char *env = std::getenv("HDG_BATCH_GROUPS")) G = std::atoi(env);
+    if (G < 0 || G > 64) return fail(nullptr, HDG_EINVAL, "HDG_BATCH_GROUPS must be 0..64");
+    b->group_of.assign(size_t(n), 0);
+    if (G == 0) {
+        std::vector<int> ps;
+        for (int i = 0; i < n; ++i)
+            if (std::find(ps.begin(), ps.end(), hs[i]->p) == ps.end()) ps.push_back(hs[i]->p);
+        std::sort(ps.begin(), ps.end());
+        for (int i = 0; i < n; ++i)
+            b->group_of[size_t(i)] = int(std::find(ps.begin(), ps.end(), hs[i]->p) - ps.begin());
+        G = int(ps.size());
+    } else {
+        G = std::min(G, n);
+        std::vector<int> order(static_cast<size_t>(n));
+        for (int i = 0; i < n; ++i) order[size_t(i)] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hs[x]->NT > hs[y]->NT; });
+        for (int k = 0; k < n; ++k) b->group_of[size_t(order[size_t(k)])] = k % G;
+    }
+    for (int g = 0; g < G; ++g) {
+        std::unique_ptr<hdg_batch::Group> grp(new hdg_batch::Group);
+        if ((rc = cu(cudaStreamCreateWithFlags(&grp->stream, cudaStreamNonBlocking), "cudaStreamCreateWithFlags")))
+            return rc;
+        if ((rc = cu(cudaEventCreateWithFlags(&grp->ev, cudaEventDisableTiming), "cudaEventCreateWithFlags"))) return rc;
+        b->groups.push_back(std::move(grp));
+    }
+    for (int i = 0; i < n; ++i) b->groups[size_t(b->group_of[size_t(i)])]->idx.push_back(i);
+    b->ev_in.assign(size_t(n), nullptr);
+    for (auto &e : b->ev_in)
+        if ((rc = cu(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreateWithFlags"))) return rc;
+    if ((rc = cu(cudaMallocHost(reinterpret_cast<void **>(&b->status_host), sizeof(int32_t) * size_t(n)),
+                 "cudaMallocHost")))
+        return rc;
+    std::memset(b->status_host, 0, sizeof(int32_t) * size_t(n));
+    if ((rc = cu(cudaHostGetDevicePointer(reinterpret_cast<void **>(&b->status_dev), b->status_host, 0),
+                 "cudaHostGetDevicePointer")))
+        return rc;
+    for (int i = 0; i < n; ++i) {
+        std::unique_ptr<Fiber> f(new Fiber);
+        f->stack.reset(new unsigned char[kFiberStack]);
+        f->status_dev = b->status_dev + i;
+        b->fibers.push_back(std::move(f));
+    }
+    *out = b.release();
+    return HDG_OK;
+}
+
+int hdg_batch_solve_dev(hdg_batch *b, const double *const *r_u, const double *const *r_h, double *const *lambda,
+                        hdg_solve_info *infos) {
+    if (!b) return fail(nullptr, HDG_EINVAL, "batch is NULL");
+    if (!r_u || !r_h || !lambda) return fail(nullptr, HDG_EINVAL, "NULL pointer argument");
+    if (batch_recorder() || t_sched) return fail(nullptr, HDG_ESTATE, "a batched solve is already running on this thread");
+    const int n = int(b->hs.size());
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
+        return fail(nullptr, HDG_EINVAL, "the batch's device is not the current device");
+    for (int i = 0; i < n; ++i) {
+        hdg_handle *h = b->hs[i];
+        const std::string at = "batch entry " + std::to_string(i) + ": ";
+        if (!r_u[i] || !r_h[i] || !lambda[i]) return fail(nullptr, HDG_EINVAL, at + "NULL pointer argument");
+        if (!h->condensed) return fail(nullptr, HDG_ESTATE, at + "hdg_condense has not run on this handle");
+        if (!mode_ff(h->prm) || h->prm.flux != 0 || h->prm.reorth != 0)
+            return fail(nullptr, HDG_ESTATE, at + "the handle's parameters changed since hdg_batch_create");
+        if (h->prof.on) return fail(nullptr, HDG_ESTATE, at + "kernel timing is on (hdg_profile_enable)");
+        if (h->lc.on || h->lc.collecting) return fail(nullptr, HDG_ESTATE, at + "the learned smoother is enabled");
+    }
+    // each group's stream after the work already queued on its handles' streams
+    for (int i = 0; i < n; ++i) {
+        cudaError_t e = cudaEventRecord(b->ev_in[size_t(i)], b->hs[size_t(i)]->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(b->groups[size_t(b->group_of[size_t(i)])]->stream, b->ev_in[size_t(i)], 0);
+        if (e != cudaSuccess) return fail(nullptr, HDG_ECUDA, std::string("ordering the batch: ") + cudaGetErrorString(e));
+    }
+    ucontext_t sched;
+    for (int i = 0; i < n; ++i) {
+        Fiber &f = *b->fibers[size_t(i)];
+        f.h = b->hs[size_t(i)];
+        f.r_u = r_u[i];
+        f.r_h = r_h[i];
+        f.lambda = lambda[i];
+        f.info = hdg_solve_info{};
+        f.rc = HDG_OK;
+        f.done = false;
+        f.rec.clear();
+        b->status_host[i] = 0;
+        if (getcontext(&f.ctx) != 0) return fail(nullptr, HDG_EINVAL, "getcontext failed");
+        f.ctx.uc_stack.ss_sp = f.stack.get();
+        f.ctx.uc_stack.ss_size = kFiberStack;
+        f.ctx.uc_link = &sched;
+        makecontext(&f.ctx, fiber_entry, 0);
+    }
+    t_sched = &sched;
+    t_wave_error = nullptr;
+    std::string wave_err;
+    auto set_error = [&](const std::string &m) {
+        if (t_wave_error) return;
+        wave_err = m;
+        t_wave_error = wave_err.c_str();
+    };
+    // Round-robin over the groups.  In each: resume the fibers whose awaited
+    // word has arrived (or that have not started); once none of its fibers
+    // waits on a launched wave any more, launch what they recorded as the
+    // group's next wave.  A finished wave whose awaited words did not all
+    // arrive, or any CUDA error, fails the batch: every fiber is then resumed
+    // with the error and unwinds.
+    for (auto &g : b->groups) g->inflight = false;
+    for (auto &f : b->fibers) {
+        f->launched = true;            // not started: resumed on the first pass
+        f->wait_addr = nullptr;
+    }
+    auto resume = [&](Fiber &f) {
+        t_fiber = &f;
+        batch_recorder() = &f.rec;
+        swapcontext(&sched, &f.ctx);
+        batch_recorder() = nullptr;
+        t_fiber = nullptr;
+    };
+    for (;;) {
+        bool all_done = true;
+        for (auto &gp : b->groups) {
+            hdg_batch::Group &g = *gp;
+            const int64_t t0 = now_ns();
+            bool waiting = false;      // some fiber waits on a launched wave
+            bool gdone = true;
+            for (int i : g.idx) {
+                Fiber &f = *b->fibers[size_t(i)];
+                if (f.done) continue;
+                if (f.launched && (t_wave_error || !f.wait_addr || *f.wait_addr == f.wait_want)) resume(f);
+                if (!f.done) {
+                    gdone = false;
+                    if (f.launched) waiting = true;
+                }
+            }
+            if (waiting && g.inflight && !t_wave_error) {
+                // is the last wave over?  then the awaited words must be there
+                const cudaError_t q = cudaEventQuery(g.ev);
+                if (q == cudaSuccess) {
+                    g.inflight = false;
+                    std::atomic_thread_fence(std::memory_order_acquire);
+                    bool late = false;
+                    for (int i : g.idx) {
+                        Fiber &f = *b->fibers[size_t(i)];
+                        if (!f.done && f.launched && f.wait_addr && *f.wait_addr != f.wait_want) late = true;
+                    }
+                    if (late) set_error("a wave finished without the value a problem waits for");
+                } else if (q != cudaErrorNotReady) {
+                    set_error(cudaGetErrorString(q));
+                }
+            }
+            const int64_t t1 = now_ns();
+            b->ns_fibers += t1 - t0;
+            if (t_wave_error) {
+                // nothing more is launched; resume every fiber until it has unwound
+                for (int i : g.idx) {
+                    Fiber &f = *b->fibers[size_t(i)];
+                    f.rec.clear();
+                    f.launched = true;
+                }
+                if (!gdone) all_done = false;
+                continue;
+            }
+            if (!waiting) {
+                size_t nrec = 0;
+                g.recs.clear();
+                for (int i : g.idx) {
+                    g.recs.push_back(&b->fibers[size_t(i)]->rec);
+                    nrec += b->fibers[size_t(i)]->rec.recs.size();
+                }
+                if (nrec > 0) {
+                    cudaError_t e = g.runner.run(g.recs.data(), int(g.recs.size()), g.stream);
+                    if (e == cudaSuccess) e = cudaEventRecord(g.ev, g.stream);
+                    if (e == cudaSuccess) g.inflight = true;
+                    else set_error(cudaGetErrorString(e));
+                    for (int i : g.idx) {
+                        Fiber &f = *b->fibers[size_t(i)];
+                        f.rec.clear();
+                        f.launched = true;
+                    }
+                } else if (!gdone) {
+                    set_error("every problem waits and no launch was recorded");
+                }
+                b->ns_launch += now_ns() - t1;
+            }
+            if (!gdone) all_done = false;
+        }
+        if (all_done) break;
+    }
+    {
+        const int64_t t0 = now_ns();
+        for (auto &g : b->groups) {
+            const cudaError_t e = cudaStreamSynchronize(g->stream);
+            if (e != cudaSuccess) set_error(cudaGetErrorString(e));
+        }
+        b->ns_wait += now_ns() - t0;
+    }
+    const bool wave_failed = t_wave_error != nullptr;
+    t_sched = nullptr;
+    t_wave_error = nullptr;
+    int first_rc = HDG_OK;
+    std::string first_msg;
+    for (int i = 0; i < n; ++i) {
+        Fiber &f = *b->fibers[size_t(i)];
+        hdg_handle *h = f.h;
+        if (!wave_failed && f.rc != HDG_ECUDA && (b->status_host[i] & (8 | 16))) {
+            f.rc = fail(h, HDG_ETIMEOUT, (b->status_host[i] & 8)
+                                             ? "a bounded device-side wait ran out (coarse-cycle staging)"
+                                             : "a bounded device-side wait ran out (tensor-core MMA of the learned sweep)");
+            cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), h->stream);
+        }
+        if (wave_failed && f.rc == HDG_OK) f.rc = fail(h, HDG_ECUDA, "batched solve: " + wave_err);
+        f.info.status = f.rc;
+        if (infos) infos[i] = f.info;
+        if (f.rc != HDG_OK && first_rc == HDG_OK) {
+            first_rc = f.rc;
+            first_msg = "batch entry " + std::to_string(i) + ": " + h->err;
+        }
+    }
+    // every handle's stream after its group's last wave
+    cudaError_t e = cudaSuccess;
+    for (auto &g : b->groups)
+        if (e == cudaSuccess) e = cudaEventRecord(g->ev, g->stream);
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaStreamWaitEvent(b->hs[size_t(i)]->stream, b->groups[size_t(b->group_of[size_t(i)])]->ev, 0);
+    if (e != cudaSuccess && first_rc == HDG_OK) {
+        first_rc = HDG_ECUDA;
+        first_msg = std::string("ordering the handles after the batch: ") + cudaGetErrorString(e);
+    }
+    if (first_rc != HDG_OK) g_setup_error = first_msg;
+    return first_rc;
+}
+
+int hdg_batch_stats(const hdg_batch *b, int64_t *stats) {
+    if (!b || !stats) return fail(nullptr, HDG_EINVAL, "NULL pointer argument");
+    for (int k = 0; k < 8; ++k) stats[k] = 0;
+    for (const auto &g : b->groups) {
+        const WaveRunner::Stats &s = g->runner.stats;
+        stats[0] += s.waves;
+        stats[1] += s.nodes;
+        stats[2] += s.records;
+        stats[3] += s.hits;
+        stats[4] += s.misses;
+    }
+    stats[5] = b->ns_fibers;
+    stats[6] = b->ns_launch;
+    stats[7] = b->ns_wait;
+    return HDG_OK;
+}
+
+int hdg_batch_destroy(hdg_batch *b) {
+    if (!b) return HDG_OK;
+    for (auto &g : b->groups) cudaStreamSynchronize(g->stream);
+    batch_release(b);
     return HDG_OK;
 }
 

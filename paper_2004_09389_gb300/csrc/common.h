@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <complex>
 #include <cstdint>
+#include <cstring>
 #include <functional>
 #include <string>
 #include <type_traits>
@@ -138,7 +139,7 @@ struct DevLevel {
 
 struct Workspace;   // solver vectors, defined in api.cu
 
-// learned facet-patch smoother (k_learned.cu, spec extension)
+// learned facet-patch smoother (k_learned.cu; an extension beyond the paper)
 struct Learned {
     int hid = 0, npar = 0;
     bool ready = false;        // initialised
@@ -319,6 +320,114 @@ struct TailArgs {
     const double *inv;                  // dense FP64 inverse of the last level (n x n, row-major)
     const void *b_top;                  // right-hand side of the first tail level (global)
     void *x_top;                        // its solution (global)
+};
+
+// ---------------------------------------------------------------- merged launches
+// A batched solve runs the launch sequences of many independent problems at
+// once.  Each kernel that takes part exists in three forms: NAME_impl, the
+// body as a device function of (block index, grid size, arguments); NAME, the
+// ordinary kernel; and NAME_multi, one launch over several problems, whose
+// blocks start[i] .. start[i+1]-1 run problem i's blocks with problem i's
+// arguments.  The launch helper NAME_go launches NAME, or, while a Recorder is
+// installed on the calling thread, appends a record of the launch instead; the
+// batch then merges records of different problems that use the same kernel
+// and block size into one NAME_multi launch.  Every argument travels in the
+// kernel's parameter block (up to kMergeMax problems per launch).
+constexpr int kMergeMax = 64;
+
+template <class A>
+struct MultiP {
+    int n;                        // problems in this launch
+    int start[kMergeMax + 1];     // first block of problem i; start[n] = total blocks
+    A a[kMergeMax];               // arguments of problem i
+};
+
+// problem of this block (binary search of start) and the block's index within it
+__device__ __forceinline__ int merge_find(const int *start, int n, int &local) {
+    const int b = int(blockIdx.x);
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    local = b - start[lo];
+    return lo;
+}
+
+struct MergeRec {
+    const void *func;             // the merged kernel (a NAME_multi instantiation)
+    void (*pack)(void *out, int n, const int *start, const unsigned char *const *args);
+    uint32_t param_bytes;         // sizeof(MultiP<A>)
+    uint32_t args_bytes;          // sizeof(A)
+    unsigned grid, block;         // this problem's launch shape
+    size_t smem;
+    size_t off;                   // the arguments, in the recorder's arena
+};
+struct Recorder {
+    std::vector<MergeRec> recs;
+    std::vector<unsigned char> arena;
+    void clear() {
+        recs.clear();
+        arena.clear();
+    }
+};
+// the calling thread's recorder (null: launch directly)
+Recorder *&batch_recorder();
+
+template <class A>
+void merge_pack(void *out, int n, const int *start, const unsigned char *const *args) {
+    static_assert(std::is_trivially_copyable<A>::value, "merged-launch arguments are copied bytewise");
+    static_assert(sizeof(MultiP<A>) <= 32000, "merged-launch parameters exceed the kernel parameter limit");
+    MultiP<A> *M = static_cast<MultiP<A> *>(out);
+    std::memset(out, 0, sizeof(MultiP<A>));
+    M->n = n;
+    for (int i = 0; i <= n; ++i) M->start[i] = start[i];
+    for (int i = 0; i < n; ++i) std::memcpy(static_cast<void *>(&M->a[i]), args[i], sizeof(A));
+}
+// a (built in zeroed storage, so that its padding bytes are zero and two
+// records of the same launch compare equal byte for byte)
+template <class A>
+void batch_record(Recorder *r, const void *func, const A &a, unsigned grid, unsigned block, size_t smem) {
+    MergeRec m{func, &merge_pack<A>, uint32_t(sizeof(MultiP<A>)), uint32_t(sizeof(A)), grid, block, smem,
+               r->arena.size()};
+    const unsigned char *p = reinterpret_cast<const unsigned char *>(&a);
+    r->arena.insert(r->arena.end(), p, p + sizeof(A));
+    r->recs.push_back(m);
+}
+
+// stream-ordered copy of n bytes (src null: zero fill) as a kernel, so that a
+// batched solve can record it; src may be page-locked host memory
+cudaError_t launch_copy(void *dst, const void *src, size_t n, cudaStream_t s);
+
+// One wave of a batched solve: the launches that every problem records
+// between two host decisions, merged into NAME_multi launches and run as a
+// CUDA graph.  Graphs are kept, keyed by the exact records (kernels, shapes
+// and argument bytes), so a wave that recurs is replayed without rebuilding.
+class WaveRunner {
+  public:
+    struct Stats {
+        int64_t waves = 0, nodes = 0, records = 0, hits = 0, misses = 0;
+    };
+    WaveRunner() = default;
+    WaveRunner(const WaveRunner &) = delete;
+    WaveRunner &operator=(const WaveRunner &) = delete;
+    ~WaveRunner() { clear(); }
+    // merge and launch the records of recs[0 .. n) (one recorder per problem) on s
+    cudaError_t run(Recorder *const *recs, int n, cudaStream_t s);
+    void clear();
+    Stats stats;
+
+  private:
+    struct Entry {
+        std::vector<unsigned char> key;
+        cudaGraphExec_t exec = nullptr;
+        int64_t nodes = 0, records = 0;
+    };
+    std::vector<std::vector<Entry>> buckets_ = std::vector<std::vector<Entry>>(1024);
+    size_t key_bytes_ = 0;
+    std::vector<unsigned char> key_;
+    cudaError_t build(Recorder *const *recs, int n, Entry &out);
 };
 
 // per-category kernel accounting (see hdg_profile_enable)

@@ -98,23 +98,58 @@ __device__ __forceinline__ void row_pairs(FFAcc &acc, const float4 *__restrict__
 }
 
 // x += scale * d (refinement correction, FP32 -> FP64) and its split copy
-__global__ void axpby_split_kernel(double *__restrict__ x, float2 *__restrict__ x2, const float *__restrict__ d,
-                                   const double *__restrict__ scale, size_t n) {
-    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void axpby_split_kernel_impl(int bid_, int nb_, double *__restrict__ x,
+                                                        float2 *__restrict__ x2, const float *__restrict__ d,
+                                                        const double *__restrict__ scale, size_t n) {
+    const size_t i = size_t(bid_) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double v = fma(scale[0], double(d[i]), x[i]);
     x[i] = v;
     x2[i] = split(v);
 }
+__global__ void axpby_split_kernel(double *__restrict__ x, float2 *__restrict__ x2, const float *__restrict__ d,
+                                   const double *__restrict__ scale, size_t n) {
+    axpby_split_kernel_impl(blockIdx.x, gridDim.x, x, x2, d, scale, n);
+}
+struct axpby_split_kernel_args {
+    int nb_;
+    double *x;
+    float2 *x2;
+    const float *d;
+    const double *scale;
+    size_t n;
+};
+__global__ void axpby_split_kernel_multi(const __grid_constant__ MultiP<axpby_split_kernel_args> M) {
+    int b_;
+    const axpby_split_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
+    axpby_split_kernel_impl(b_, q_.nb_, q_.x, q_.x2, q_.d, q_.scale, q_.n);
+}
+void axpby_split_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, double *x, float2 *x2,
+                           const float *d, const double *scale, size_t n) {
+    if (Recorder *r_ = batch_recorder()) {
+        axpby_split_kernel_args q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.x = x;
+        q_.x2 = x2;
+        q_.d = d;
+        q_.scale = scale;
+        q_.n = n;
+        batch_record(r_, reinterpret_cast<const void *>(&axpby_split_kernel_multi), q_, grid_, block_, smem_);
+        return;
+    }
+    axpby_split_kernel<<<grid_, block_, smem_, s_>>>(x, x2, d, scale, n);
+}
+
 
 // r = b - S x with x given split; S split in the packed FP64 layout (element
 // j of facet e in 16-byte group (j / 2, e), lane j % 2, here two float pairs)
 template <int P>
-__global__ void __launch_bounds__(256) residual_ff_kernel(int NF, const float4 *__restrict__ S2,
-                                                          const int32_t *__restrict__ nbr, const double *__restrict__ b,
-                                                          const float2 *__restrict__ x2, double *__restrict__ res) {
+__device__ __forceinline__ void residual_ff_kernel_impl(int bid_, int nb_, int NF, const float4 *__restrict__ S2,
+                                                        const int32_t *__restrict__ nbr, const double *__restrict__ b,
+                                                        const float2 *__restrict__ x2, double *__restrict__ res) {
     constexpr int PP = P + 1, NS = 5 * PP * PP, NQ = (NS + 1) / 2;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = bid_ * blockDim.x + threadIdx.x;
     if (e >= NF) return;
     int src[5];
     src[0] = e;
@@ -142,6 +177,48 @@ __global__ void __launch_bounds__(256) residual_ff_kernel(int NF, const float4 *
 #pragma unroll
     for (int r = 0; r < PP; ++r) res[size_t(r) * NF + e] = b[size_t(r) * NF + e] - acc[r].value();
 }
+template <int P>
+__global__ void __launch_bounds__(256) residual_ff_kernel(int NF, const float4 *__restrict__ S2,
+                                                          const int32_t *__restrict__ nbr,
+                                                          const double *__restrict__ b, const float2 *__restrict__ x2,
+                                                          double *__restrict__ res) {
+    residual_ff_kernel_impl<P>(blockIdx.x, gridDim.x, NF, S2, nbr, b, x2, res);
+}
+template <int P>
+struct residual_ff_kernel_args {
+    int nb_;
+    int NF;
+    const float4 *S2;
+    const int32_t *nbr;
+    const double *b;
+    const float2 *x2;
+    double *res;
+};
+template <int P>
+__global__ void __launch_bounds__(256) residual_ff_kernel_multi(const __grid_constant__ MultiP<residual_ff_kernel_args<P>> M) {
+    int b_;
+    const residual_ff_kernel_args<P> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    residual_ff_kernel_impl<P>(b_, q_.nb_, q_.NF, q_.S2, q_.nbr, q_.b, q_.x2, q_.res);
+}
+template <int P>
+void residual_ff_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int NF, const float4 *S2,
+                           const int32_t *nbr, const double *b, const float2 *x2, double *res) {
+    if (Recorder *r_ = batch_recorder()) {
+        residual_ff_kernel_args<P> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.NF = NF;
+        q_.S2 = S2;
+        q_.nbr = nbr;
+        q_.b = b;
+        q_.x2 = x2;
+        q_.res = res;
+        batch_record(r_, reinterpret_cast<const void *>(&residual_ff_kernel_multi<P>), q_, grid_, block_, smem_);
+        return;
+    }
+    residual_ff_kernel<P><<<grid_, block_, smem_, s_>>>(NF, S2, nbr, b, x2, res);
+}
+
 
 // (r_u, r_h may live in page-locked host memory read over the C2C link; with
 // cu, ch non-null each value read is also stored there, in HBM)
@@ -166,24 +243,69 @@ __device__ __forceinline__ void stage_cell_rhs(int N, int K0, const double *__re
 
 // step 1, cell part: ycell[t][K] = sum_kappa W[t*NK + kappa][K] r_K[kappa]
 template <int P>
-__global__ void __launch_bounds__(128, 8) rhs_cell_ff_kernel(int N, const float4 *__restrict__ W2,
-                                                          const double *__restrict__ r_u,
-                                                          const double *__restrict__ r_h, double *__restrict__ ycell,
-                                                          double *__restrict__ cu, double *__restrict__ ch) {
+__device__ __forceinline__ void rhs_cell_ff_kernel_impl(int bid_, int nb_, int N, const float4 *__restrict__ W2,
+                                                        const double *__restrict__ r_u,
+                                                        const double *__restrict__ r_h, double *__restrict__ ycell,
+                                                        double *__restrict__ cu, double *__restrict__ ch) {
     constexpr int PP = P + 1, NP = (P + 1) * (P + 2) / 2, NK = 3 * NP, M = 3 * PP, NW = 4;
     constexpr int KP = (NK + 1) / 2;
     __shared__ float2 sIn[NK][kCellsPad];
-    const int K0 = blockIdx.x * kCells, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int K0 = bid_ * kCells, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     stage_cell_rhs<NP>(N, K0, r_u, r_h, sIn, cu, ch);
     __syncthreads();
     const int K = K0 + lane;
     if (K >= N) return;
     for (int t = w; t < M; t += NW) {
         FFAcc acc;
-        row_pairs<NK>(acc, W2 + (size_t(blockIdx.x) * M * KP + size_t(t) * KP) * kCells + lane, sIn, lane);
+        row_pairs<NK>(acc, W2 + (size_t(bid_) * M * KP + size_t(t) * KP) * kCells + lane, sIn, lane);
         ycell[size_t(t) * N + K] = acc.value();
     }
 }
+template <int P>
+__global__ void __launch_bounds__(128, 8) rhs_cell_ff_kernel(int N, const float4 *__restrict__ W2,
+                                                             const double *__restrict__ r_u,
+                                                             const double *__restrict__ r_h,
+                                                             double *__restrict__ ycell, double *__restrict__ cu,
+                                                             double *__restrict__ ch) {
+    rhs_cell_ff_kernel_impl<P>(blockIdx.x, gridDim.x, N, W2, r_u, r_h, ycell, cu, ch);
+}
+template <int P>
+struct rhs_cell_ff_kernel_args {
+    int nb_;
+    int N;
+    const float4 *W2;
+    const double *r_u;
+    const double *r_h;
+    double *ycell;
+    double *cu;
+    double *ch;
+};
+template <int P>
+__global__ void __launch_bounds__(128, 8) rhs_cell_ff_kernel_multi(const __grid_constant__ MultiP<rhs_cell_ff_kernel_args<P>> M) {
+    int b_;
+    const rhs_cell_ff_kernel_args<P> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    rhs_cell_ff_kernel_impl<P>(b_, q_.nb_, q_.N, q_.W2, q_.r_u, q_.r_h, q_.ycell, q_.cu, q_.ch);
+}
+template <int P>
+void rhs_cell_ff_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int N, const float4 *W2,
+                           const double *r_u, const double *r_h, double *ycell, double *cu, double *ch) {
+    if (Recorder *r_ = batch_recorder()) {
+        rhs_cell_ff_kernel_args<P> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.N = N;
+        q_.W2 = W2;
+        q_.r_u = r_u;
+        q_.r_h = r_h;
+        q_.ycell = ycell;
+        q_.cu = cu;
+        q_.ch = ch;
+        batch_record(r_, reinterpret_cast<const void *>(&rhs_cell_ff_kernel_multi<P>), q_, grid_, block_, smem_);
+        return;
+    }
+    rhs_cell_ff_kernel<P><<<grid_, block_, smem_, s_>>>(N, W2, r_u, r_h, ycell, cu, ch);
+}
+
 
 // step 3: q_K = R_M r_K - X_B lambda_K, written in the caller's u / h layout
 template <int P>
@@ -238,19 +360,19 @@ cudaError_t launch_split_pairs(const double *a, float2 *out, int rows, int cols,
 }
 
 cudaError_t launch_axpby_split(double *x, float2 *x2, const float *d, const double *scale, size_t n, cudaStream_t s) {
-    axpby_split_kernel<<<blocks(n, 256), 256, 0, s>>>(x, x2, d, scale, n);
+    axpby_split_kernel_go(blocks(n, 256), 256, 0, s, x, x2, d, scale, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2, double *res) {
-    HDG_DISPATCH_P(h->p, (residual_ff_kernel<P><<<blocks(h->NF, 256), 256, 0, h->stream>>>(
+    HDG_DISPATCH_P(h->p, (residual_ff_kernel_go<P>(blocks(h->NF, 256), 256, 0, h->stream, 
                              h->NF, reinterpret_cast<const float4 *>(h->d_Sval2), h->d_nbr, b, x2, res)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell,
                           double *copy_u, double *copy_h) {
-    HDG_DISPATCH_P(h->p, (rhs_cell_ff_kernel<P><<<blocks(h->N, kCells), 128, 0, h->stream>>>(h->N, reinterpret_cast<const float4 *>(h->d_W2), r_u, r_h,
+    HDG_DISPATCH_P(h->p, (rhs_cell_ff_kernel_go<P>(blocks(h->N, kCells), 128, 0, h->stream, h->N, reinterpret_cast<const float4 *>(h->d_W2), r_u, r_h,
                                                                                                ycell, copy_u, copy_h)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

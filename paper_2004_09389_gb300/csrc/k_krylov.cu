@@ -46,12 +46,12 @@ __global__ void __launch_bounds__(256) multidot_kernel(const T *__restrict__ V, 
 // same order, the same result) into out[0], optionally its square root into
 // root_a / root_b and a hand-over to the host (pub, seq)
 template <typename T>
-__global__ void __launch_bounds__(256) dot1_kernel(const T *__restrict__ v, const T *__restrict__ w, size_t n,
-                                                   double *__restrict__ partial, int nchunk,
-                                                   unsigned int *__restrict__ counter, double *__restrict__ out,
-                                                   HostValue *pub, int32_t seq, double *root_a, double *root_b) {
+__device__ __forceinline__ void dot1_kernel_impl(int bid_, int nb_, const T *__restrict__ v, const T *__restrict__ w,
+                                                 size_t n, double *__restrict__ partial, int nchunk,
+                                                 unsigned int *__restrict__ counter, double *__restrict__ out,
+                                                 HostValue *pub, int32_t seq, double *root_a, double *root_b) {
     __shared__ bool last;
-    const int c = blockIdx.x;
+    const int c = bid_;
     const size_t len = (n + nchunk - 1) / nchunk;
     const size_t beg = size_t(c) * len, end = beg + len < n ? beg + len : n;
     T acc = T(0);
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) dot1_kernel(const T *__restrict__ v, cons
     if (threadIdx.x == 0) {
         partial[c] = tot;
         __threadfence();                       // the partial is visible before the count
-        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+        last = atomicAdd(counter, 1u) == nb_ - 1;
     }
     __syncthreads();
     if (!last) return;
@@ -83,6 +83,60 @@ __global__ void __launch_bounds__(256) dot1_kernel(const T *__restrict__ v, cons
         }
     }
 }
+template <typename T>
+__global__ void __launch_bounds__(256) dot1_kernel(const T *__restrict__ v, const T *__restrict__ w, size_t n,
+                                                   double *__restrict__ partial, int nchunk,
+                                                   unsigned int *__restrict__ counter, double *__restrict__ out,
+                                                   HostValue *pub, int32_t seq, double *root_a, double *root_b) {
+    dot1_kernel_impl<T>(blockIdx.x, gridDim.x, v, w, n, partial, nchunk, counter, out, pub, seq, root_a, root_b);
+}
+template <typename T>
+struct dot1_kernel_args {
+    int nb_;
+    const T *v;
+    const T *w;
+    size_t n;
+    double *partial;
+    int nchunk;
+    unsigned int *counter;
+    double *out;
+    HostValue *pub;
+    int32_t seq;
+    double *root_a;
+    double *root_b;
+};
+template <typename T>
+__global__ void __launch_bounds__(256) dot1_kernel_multi(const __grid_constant__ MultiP<dot1_kernel_args<T>> M) {
+    int b_;
+    const dot1_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    dot1_kernel_impl<T>(b_, q_.nb_, q_.v, q_.w, q_.n, q_.partial, q_.nchunk, q_.counter, q_.out, q_.pub, q_.seq,
+        q_.root_a, q_.root_b);
+}
+template <typename T>
+void dot1_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, const T *v, const T *w, size_t n,
+                    double *partial, int nchunk, unsigned int *counter, double *out, HostValue *pub, int32_t seq,
+                    double *root_a, double *root_b) {
+    if (Recorder *r_ = batch_recorder()) {
+        dot1_kernel_args<T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.v = v;
+        q_.w = w;
+        q_.n = n;
+        q_.partial = partial;
+        q_.nchunk = nchunk;
+        q_.counter = counter;
+        q_.out = out;
+        q_.pub = pub;
+        q_.seq = seq;
+        q_.root_a = root_a;
+        q_.root_b = root_b;
+        batch_record(r_, reinterpret_cast<const void *>(&dot1_kernel_multi<T>), q_, grid_, block_, smem_);
+        return;
+    }
+    dot1_kernel<T><<<grid_, block_, smem_, s_>>>(v, w, n, partial, nchunk, counter, out, pub, seq, root_a, root_b);
+}
+
 
 // out[i] = sum of the partials of vector i; with pub, block 0 also hands its
 // sum to the host (page-locked HostValue: the value, a system fence, seq);
@@ -110,17 +164,60 @@ __global__ void reduce_partials_kernel(const double *__restrict__ partial, int n
 
 // w += sign * sum_i coef[i] V_i
 template <typename T>
-__global__ void __launch_bounds__(256) multi_axpy_kernel(T *__restrict__ w, const T *__restrict__ V, size_t ld, int k,
-                                                         const double *__restrict__ coef, double sign, size_t n) {
+__device__ __forceinline__ void multi_axpy_kernel_impl(int bid_, int nb_, T *__restrict__ w, const T *__restrict__ V,
+                                                       size_t ld, int k, const double *__restrict__ coef, double sign,
+                                                       size_t n) {
     __shared__ T cf[66];
     for (int i = threadIdx.x; i < k; i += blockDim.x) cf[i] = T(sign * coef[i]);
     __syncthreads();
-    const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t idx = size_t(bid_) * blockDim.x + threadIdx.x;
     if (idx >= n) return;
     T acc = w[idx];
     for (int i = 0; i < k; ++i) acc = fma(cf[i], V[size_t(i) * ld + idx], acc);
     w[idx] = acc;
 }
+template <typename T>
+__global__ void __launch_bounds__(256) multi_axpy_kernel(T *__restrict__ w, const T *__restrict__ V, size_t ld, int k,
+                                                         const double *__restrict__ coef, double sign, size_t n) {
+    multi_axpy_kernel_impl<T>(blockIdx.x, gridDim.x, w, V, ld, k, coef, sign, n);
+}
+template <typename T>
+struct multi_axpy_kernel_args {
+    int nb_;
+    T *w;
+    const T *V;
+    size_t ld;
+    int k;
+    const double *coef;
+    double sign;
+    size_t n;
+};
+template <typename T>
+__global__ void __launch_bounds__(256) multi_axpy_kernel_multi(const __grid_constant__ MultiP<multi_axpy_kernel_args<T>> M) {
+    int b_;
+    const multi_axpy_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    multi_axpy_kernel_impl<T>(b_, q_.nb_, q_.w, q_.V, q_.ld, q_.k, q_.coef, q_.sign, q_.n);
+}
+template <typename T>
+void multi_axpy_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, T *w, const T *V, size_t ld,
+                          int k, const double *coef, double sign, size_t n) {
+    if (Recorder *r_ = batch_recorder()) {
+        multi_axpy_kernel_args<T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.w = w;
+        q_.V = V;
+        q_.ld = ld;
+        q_.k = k;
+        q_.coef = coef;
+        q_.sign = sign;
+        q_.n = n;
+        batch_record(r_, reinterpret_cast<const void *>(&multi_axpy_kernel_multi<T>), q_, grid_, block_, smem_);
+        return;
+    }
+    multi_axpy_kernel<T><<<grid_, block_, smem_, s_>>>(w, V, ld, k, coef, sign, n);
+}
+
 
 // 1 / d[0] in FP64, formed once per block (FP64 division is slow on this part;
 // every thread reaches the barrier, so call it before any early return)
@@ -159,19 +256,56 @@ __global__ void widen_kernel(const float *__restrict__ a, double *__restrict__ b
 }
 
 template <typename T>
-__global__ void scale_copy_kernel(const T *__restrict__ w, T *__restrict__ v, const double *__restrict__ denom,
-                                  size_t n) {
+__device__ __forceinline__ void scale_copy_kernel_impl(int bid_, int nb_, const T *__restrict__ w, T *__restrict__ v,
+                                                       const double *__restrict__ denom, size_t n) {
     const double inv = block_recip(denom);
-    const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t idx = size_t(bid_) * blockDim.x + threadIdx.x;
     if (idx >= n) return;
     v[idx] = w[idx] * T(inv);
 }
+template <typename T>
+__global__ void scale_copy_kernel(const T *__restrict__ w, T *__restrict__ v, const double *__restrict__ denom,
+                                  size_t n) {
+    scale_copy_kernel_impl<T>(blockIdx.x, gridDim.x, w, v, denom, n);
+}
+template <typename T>
+struct scale_copy_kernel_args {
+    int nb_;
+    const T *w;
+    T *v;
+    const double *denom;
+    size_t n;
+};
+template <typename T>
+__global__ void scale_copy_kernel_multi(const __grid_constant__ MultiP<scale_copy_kernel_args<T>> M) {
+    int b_;
+    const scale_copy_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    scale_copy_kernel_impl<T>(b_, q_.nb_, q_.w, q_.v, q_.denom, q_.n);
+}
+template <typename T>
+void scale_copy_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, const T *w, T *v,
+                          const double *denom, size_t n) {
+    if (Recorder *r_ = batch_recorder()) {
+        scale_copy_kernel_args<T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.w = w;
+        q_.v = v;
+        q_.denom = denom;
+        q_.n = n;
+        batch_record(r_, reinterpret_cast<const void *>(&scale_copy_kernel_multi<T>), q_, grid_, block_, smem_);
+        return;
+    }
+    scale_copy_kernel<T><<<grid_, block_, smem_, s_>>>(w, v, denom, n);
+}
+
 
 // y = R^-1 s for the leading k x k upper triangle R of the rotated Hessenberg
 // matrix (column-major, leading dimension ldh): the triangle and s are first
 // loaded into shared memory by the whole block, then one thread substitutes
 // backwards (k <= 64)
-__global__ void hessenberg_solve_kernel(const double *Hm, int ldh, const double *sv, int k, double *y) {
+__device__ __forceinline__ void hessenberg_solve_kernel_impl(int bid_, int nb_, const double *Hm, int ldh,
+                                                             const double *sv, int k, double *y) {
     __shared__ double R[64][65], sS[64], yS[64];
     for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
         const int l = t / k, i = t % k;            // column l, row i
@@ -187,19 +321,116 @@ __global__ void hessenberg_solve_kernel(const double *Hm, int ldh, const double 
         y[i] = yS[i];
     }
 }
+__global__ void hessenberg_solve_kernel(const double *Hm, int ldh, const double *sv, int k, double *y) {
+    hessenberg_solve_kernel_impl(blockIdx.x, gridDim.x, Hm, ldh, sv, k, y);
+}
+struct hessenberg_solve_kernel_args {
+    int nb_;
+    const double *Hm;
+    int ldh;
+    const double *sv;
+    int k;
+    double *y;
+};
+__global__ void hessenberg_solve_kernel_multi(const __grid_constant__ MultiP<hessenberg_solve_kernel_args> M) {
+    int b_;
+    const hessenberg_solve_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
+    hessenberg_solve_kernel_impl(b_, q_.nb_, q_.Hm, q_.ldh, q_.sv, q_.k, q_.y);
+}
+void hessenberg_solve_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, const double *Hm,
+                                int ldh, const double *sv, int k, double *y) {
+    if (Recorder *r_ = batch_recorder()) {
+        hessenberg_solve_kernel_args q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.Hm = Hm;
+        q_.ldh = ldh;
+        q_.sv = sv;
+        q_.k = k;
+        q_.y = y;
+        batch_record(r_, reinterpret_cast<const void *>(&hessenberg_solve_kernel_multi), q_, grid_, block_, smem_);
+        return;
+    }
+    hessenberg_solve_kernel<<<grid_, block_, smem_, s_>>>(Hm, ldh, sv, k, y);
+}
+
 
 template <typename T>
-__global__ void fill_kernel(T *x, T v, size_t n) {
-    const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fill_kernel_impl(int bid_, int nb_, T *x, T v, size_t n) {
+    const size_t idx = size_t(bid_) * blockDim.x + threadIdx.x;
     if (idx < n) x[idx] = v;
 }
+template <typename T>
+__global__ void fill_kernel(T *x, T v, size_t n) {
+    fill_kernel_impl<T>(blockIdx.x, gridDim.x, x, v, n);
+}
+template <typename T>
+struct fill_kernel_args {
+    int nb_;
+    T *x;
+    T v;
+    size_t n;
+};
+template <typename T>
+__global__ void fill_kernel_multi(const __grid_constant__ MultiP<fill_kernel_args<T>> M) {
+    int b_;
+    const fill_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    fill_kernel_impl<T>(b_, q_.nb_, q_.x, q_.v, q_.n);
+}
+template <typename T>
+void fill_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, T *x, T v, size_t n) {
+    if (Recorder *r_ = batch_recorder()) {
+        fill_kernel_args<T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.x = x;
+        q_.v = v;
+        q_.n = n;
+        batch_record(r_, reinterpret_cast<const void *>(&fill_kernel_multi<T>), q_, grid_, block_, smem_);
+        return;
+    }
+    fill_kernel<T><<<grid_, block_, smem_, s_>>>(x, v, n);
+}
+
 
 // y = float(x / scale[0])
-__global__ void d2f_scaled_kernel(const double *x, float *y, const double *scale, size_t n) {
+__device__ __forceinline__ void d2f_scaled_kernel_impl(int bid_, int nb_, const double *x, float *y,
+                                                       const double *scale, size_t n) {
     const double inv = block_recip(scale);
-    const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t idx = size_t(bid_) * blockDim.x + threadIdx.x;
     if (idx < n) y[idx] = float(x[idx] * inv);
 }
+__global__ void d2f_scaled_kernel(const double *x, float *y, const double *scale, size_t n) {
+    d2f_scaled_kernel_impl(blockIdx.x, gridDim.x, x, y, scale, n);
+}
+struct d2f_scaled_kernel_args {
+    int nb_;
+    const double *x;
+    float *y;
+    const double *scale;
+    size_t n;
+};
+__global__ void d2f_scaled_kernel_multi(const __grid_constant__ MultiP<d2f_scaled_kernel_args> M) {
+    int b_;
+    const d2f_scaled_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
+    d2f_scaled_kernel_impl(b_, q_.nb_, q_.x, q_.y, q_.scale, q_.n);
+}
+void d2f_scaled_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, const double *x, float *y,
+                          const double *scale, size_t n) {
+    if (Recorder *r_ = batch_recorder()) {
+        d2f_scaled_kernel_args q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.x = x;
+        q_.y = y;
+        q_.scale = scale;
+        q_.n = n;
+        batch_record(r_, reinterpret_cast<const void *>(&d2f_scaled_kernel_multi), q_, grid_, block_, smem_);
+        return;
+    }
+    d2f_scaled_kernel<<<grid_, block_, smem_, s_>>>(x, y, scale, n);
+}
+
 
 
 // ---------------------------------------------------------------- fused CGS2
@@ -316,13 +547,12 @@ __global__ void __launch_bounds__(256) gs_update_dots_kernel(const T *V, size_t 
 // updates the least-squares right-hand side and writes the residual
 // estimate |s_{j+1}| / ||b|| and the flags (2: breakdown, 4: NaN/Inf) to rb.
 template <typename T>
-__global__ void __launch_bounds__(256) gs_update_norm_givens_kernel(const T *V, size_t ld, int k, T *w, size_t n,
-                                                                    const double *h1, const double *h2,
-                                                                    double *partial, unsigned int *counter,
-                                                                    double *nrm2, double *Hm, int ldh, double *cs,
-                                                                    double *sn, double *sv, int j,
-                                                                    const double *bnorm, ReadBack *rb,
-                                                                    ReadBack *host_rb) {
+__device__ __forceinline__ void gs_update_norm_givens_kernel_impl(int bid_, int nb_, const T *V, size_t ld, int k,
+                                                                  T *w, size_t n, const double *h1, const double *h2,
+                                                                  double *partial, unsigned int *counter,
+                                                                  double *nrm2, double *Hm, int ldh, double *cs,
+                                                                  double *sn, double *sv, int j, const double *bnorm,
+                                                                  ReadBack *rb, ReadBack *host_rb) {
     using V4 = typename V16<T>::type;
     using A = typename V16<T>::acc;
     const size_t ld4 = ld / (16 / sizeof(T)), n4 = n / (16 / sizeof(T));
@@ -338,7 +568,7 @@ __global__ void __launch_bounds__(256) gs_update_norm_givens_kernel(const T *V, 
     __syncthreads();
     // the update and ||w||^2 in one pass: each updated value is squared from registers
     A nrm = A(0);
-    for (size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < n4; idx += size_t(gridDim.x) * blockDim.x) {
+    for (size_t idx = size_t(bid_) * blockDim.x + threadIdx.x; idx < n4; idx += size_t(nb_) * blockDim.x) {
         V4 acc = w4[idx];
         for (int i = 0; i < k; ++i) acc = V16<T>::axpy(cs_[i], V4p[size_t(i) * ld4 + idx], acc);
         w4[idx] = acc;
@@ -350,9 +580,9 @@ __global__ void __launch_bounds__(256) gs_update_norm_givens_kernel(const T *V, 
     if (threadIdx.x == 0) {
         A t = A(0);
         for (int q = 0; q < nwarp; ++q) t += red[q];
-        partial[blockIdx.x] = double(t);
+        partial[bid_] = double(t);
         __threadfence();                       // the partial is visible before the count
-        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+        last = atomicAdd(counter, 1u) == nb_ - 1;
     }
     __syncthreads();
     if (!last) return;
@@ -369,7 +599,7 @@ __global__ void __launch_bounds__(256) gs_update_norm_givens_kernel(const T *V, 
     // the last block adds the partials with all its threads, in a fixed order
     // (thread t: partials t, t + blockDim, ...; then the warp tree; then the warps)
     double v = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) v += partial[b];
+    for (unsigned b = threadIdx.x; b < nb_; b += blockDim.x) v += partial[b];
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if (lane == 0) redd[warp] = v;
     __syncthreads();
@@ -419,17 +649,130 @@ __global__ void __launch_bounds__(256) gs_update_norm_givens_kernel(const T *V, 
         *reinterpret_cast<volatile int32_t *>(&host_rb->seq) = j + 1;
     }
 }
+template <typename T>
+__global__ void __launch_bounds__(256) gs_update_norm_givens_kernel(const T *V, size_t ld, int k, T *w, size_t n,
+                                                                    const double *h1, const double *h2,
+                                                                    double *partial, unsigned int *counter,
+                                                                    double *nrm2, double *Hm, int ldh, double *cs,
+                                                                    double *sn, double *sv, int j,
+                                                                    const double *bnorm, ReadBack *rb,
+                                                                    ReadBack *host_rb) {
+    gs_update_norm_givens_kernel_impl<T>(blockIdx.x, gridDim.x, V, ld, k, w, n, h1, h2, partial, counter, nrm2, Hm,
+        ldh, cs, sn, sv, j, bnorm, rb, host_rb);
+}
+template <typename T>
+struct gs_update_norm_givens_kernel_args {
+    int nb_;
+    const T *V;
+    size_t ld;
+    int k;
+    T *w;
+    size_t n;
+    const double *h1;
+    const double *h2;
+    double *partial;
+    unsigned int *counter;
+    double *nrm2;
+    double *Hm;
+    int ldh;
+    double *cs;
+    double *sn;
+    double *sv;
+    int j;
+    const double *bnorm;
+    ReadBack *rb;
+    ReadBack *host_rb;
+};
+template <typename T>
+__global__ void __launch_bounds__(256) gs_update_norm_givens_kernel_multi(const __grid_constant__ MultiP<gs_update_norm_givens_kernel_args<T>> M) {
+    int b_;
+    const gs_update_norm_givens_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    gs_update_norm_givens_kernel_impl<T>(b_, q_.nb_, q_.V, q_.ld, q_.k, q_.w, q_.n, q_.h1, q_.h2, q_.partial,
+        q_.counter, q_.nrm2, q_.Hm, q_.ldh, q_.cs, q_.sn, q_.sv, q_.j, q_.bnorm, q_.rb, q_.host_rb);
+}
+template <typename T>
+void gs_update_norm_givens_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, const T *V,
+                                     size_t ld, int k, T *w, size_t n, const double *h1, const double *h2,
+                                     double *partial, unsigned int *counter, double *nrm2, double *Hm, int ldh,
+                                     double *cs, double *sn, double *sv, int j, const double *bnorm, ReadBack *rb,
+                                     ReadBack *host_rb) {
+    if (Recorder *r_ = batch_recorder()) {
+        gs_update_norm_givens_kernel_args<T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.V = V;
+        q_.ld = ld;
+        q_.k = k;
+        q_.w = w;
+        q_.n = n;
+        q_.h1 = h1;
+        q_.h2 = h2;
+        q_.partial = partial;
+        q_.counter = counter;
+        q_.nrm2 = nrm2;
+        q_.Hm = Hm;
+        q_.ldh = ldh;
+        q_.cs = cs;
+        q_.sn = sn;
+        q_.sv = sv;
+        q_.j = j;
+        q_.bnorm = bnorm;
+        q_.rb = rb;
+        q_.host_rb = host_rb;
+        batch_record(r_, reinterpret_cast<const void *>(&gs_update_norm_givens_kernel_multi<T>), q_, grid_, block_, smem_);
+        return;
+    }
+    gs_update_norm_givens_kernel<T><<<grid_, block_, smem_, s_>>>(V, ld, k, w, n, h1, h2, partial, counter, nrm2, Hm,
+        ldh, cs, sn, sv, j, bnorm, rb, host_rb);
+}
+
 
 // v_{j+1} = w / h_{j+1,j}  (the unrotated norm kept in rb->hnext)
 template <typename T>
-__global__ void gs_scale_kernel(const T *w, T *v, size_t n, const ReadBack *rb) {
+__device__ __forceinline__ void gs_scale_kernel_impl(int bid_, int nb_, const T *w, T *v, size_t n,
+                                                     const ReadBack *rb) {
     using V4 = typename V16<T>::type;
     const size_t n4 = n / (16 / sizeof(T));
     const T inv = T(block_recip(&rb->hnext));
-    const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t idx = size_t(bid_) * blockDim.x + threadIdx.x;
     if (idx >= n4) return;
     reinterpret_cast<V4 *>(v)[idx] = V16<T>::scale(reinterpret_cast<const V4 *>(w)[idx], inv);
 }
+template <typename T>
+__global__ void gs_scale_kernel(const T *w, T *v, size_t n, const ReadBack *rb) {
+    gs_scale_kernel_impl<T>(blockIdx.x, gridDim.x, w, v, n, rb);
+}
+template <typename T>
+struct gs_scale_kernel_args {
+    int nb_;
+    const T *w;
+    T *v;
+    size_t n;
+    const ReadBack *rb;
+};
+template <typename T>
+__global__ void gs_scale_kernel_multi(const __grid_constant__ MultiP<gs_scale_kernel_args<T>> M) {
+    int b_;
+    const gs_scale_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    gs_scale_kernel_impl<T>(b_, q_.nb_, q_.w, q_.v, q_.n, q_.rb);
+}
+template <typename T>
+void gs_scale_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, const T *w, T *v, size_t n,
+                        const ReadBack *rb) {
+    if (Recorder *r_ = batch_recorder()) {
+        gs_scale_kernel_args<T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.w = w;
+        q_.v = v;
+        q_.n = n;
+        q_.rb = rb;
+        batch_record(r_, reinterpret_cast<const void *>(&gs_scale_kernel_multi<T>), q_, grid_, block_, smem_);
+        return;
+    }
+    gs_scale_kernel<T><<<grid_, block_, smem_, s_>>>(w, v, n, rb);
+}
+
 
 }  // namespace
 
@@ -443,7 +786,7 @@ cudaError_t launch_multidot(const T *V, size_t ld, int k, const T *w, size_t n, 
 template <typename T>
 cudaError_t launch_dot1(const T *v, const T *w, size_t n, double *partial, int nchunk, unsigned int *counter,
                         double *out, HostValue *pub, int32_t seq, double *root_a, double *root_b, cudaStream_t s) {
-    dot1_kernel<T><<<nchunk, 256, 0, s>>>(v, w, n, partial, nchunk, counter, out, pub, seq, root_a, root_b);
+    dot1_kernel_go<T>(nchunk, 256, 0, s, v, w, n, partial, nchunk, counter, out, pub, seq, root_a, root_b);
     return cudaGetLastError();
 }
 template cudaError_t launch_dot1<double>(const double *, const double *, size_t, double *, int, unsigned int *,
@@ -458,7 +801,7 @@ cudaError_t launch_reduce_partials(const double *partial, int k, int nchunk, dou
 template <typename T>
 cudaError_t launch_multi_axpy(T *w, const T *V, size_t ld, int k, const double *coef, double sign, size_t n,
                               cudaStream_t s) {
-    multi_axpy_kernel<T><<<blocks(n, 256), 256, 0, s>>>(w, V, ld, k, coef, sign, n);
+    multi_axpy_kernel_go<T>(blocks(n, 256), 256, 0, s, w, V, ld, k, coef, sign, n);
     return cudaGetLastError();
 }
 cudaError_t launch_scale_round(const double *w, const double *hnext, double *v64, float *v32, size_t n,
@@ -472,21 +815,21 @@ cudaError_t launch_widen(const float *a, double *b, size_t n, cudaStream_t s) {
 }
 template <typename T>
 cudaError_t launch_scale_copy(const T *w, T *v, const double *denom, size_t n, cudaStream_t s) {
-    scale_copy_kernel<T><<<blocks(n, 256), 256, 0, s>>>(w, v, denom, n);
+    scale_copy_kernel_go<T>(blocks(n, 256), 256, 0, s, w, v, denom, n);
     return cudaGetLastError();
 }
 cudaError_t launch_hessenberg_solve(const double *Hm, int ldh, const double *sv, int k, double *y, cudaStream_t s) {
-    hessenberg_solve_kernel<<<1, 128, 0, s>>>(Hm, ldh, sv, k, y);
+    hessenberg_solve_kernel_go(1, 128, 0, s, Hm, ldh, sv, k, y);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_fill(T *x, T v, size_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    fill_kernel<T><<<blocks(n, 256), 256, 0, s>>>(x, v, n);
+    fill_kernel_go<T>(blocks(n, 256), 256, 0, s, x, v, n);
     return cudaGetLastError();
 }
 cudaError_t launch_d2f_scaled(const double *x, float *y, const double *scale, size_t n, cudaStream_t s) {
-    d2f_scaled_kernel<<<blocks(n, 256), 256, 0, s>>>(x, y, scale, n);
+    d2f_scaled_kernel_go(blocks(n, 256), 256, 0, s, x, y, scale, n);
     return cudaGetLastError();
 }
 
@@ -499,11 +842,11 @@ cudaError_t launch_gs_step(const T *V, size_t ld, int j, T *w, double *partial, 
     // h1 = V^T w comes with w from the operator kernel (apply_dots_kernel)
     const int k = j + 1;
     if (reorth) gs_update_dots_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, h1, partial, counter, h2);
-    gs_update_norm_givens_kernel<T><<<nblk, 256, 0, s>>>(V, ld, k, w, ld, h1, reorth ? h2 : nullptr, partial, counter,
+    gs_update_norm_givens_kernel_go<T>(nblk, 256, 0, s, V, ld, k, w, ld, h1, reorth ? h2 : nullptr, partial, counter,
                                                         nrm2, Hm, ldh, cs, sn, sv, j, bnorm, rb, host_rb);
     if (scale) {   // otherwise the next step's first smoothing sweep forms v_{j+1}
         const size_t n4 = ld / (16 / sizeof(T));
-        gs_scale_kernel<T><<<blocks(n4, 256), 256, 0, s>>>(w, vnext, ld, rb);
+        gs_scale_kernel_go<T>(blocks(n4, 256), 256, 0, s, w, vnext, ld, rb);
     }
     return cudaGetLastError();
 }

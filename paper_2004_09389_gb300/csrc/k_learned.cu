@@ -1,4 +1,4 @@
-// Learned facet-patch smoother (spec extension; the paper has none).
+// Learned facet-patch smoother (an extension beyond the paper, which has none).
 //
 // For a trace residual r, facet e gets the features
 //   X_e = (r_e, r_n1, ..., r_n4) / s_e,   s_e = RMS of those 5(p+1) values

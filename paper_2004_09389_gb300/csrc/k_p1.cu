@@ -48,10 +48,11 @@ __device__ __forceinline__ T ell_row(int i, int W, const int32_t *__restrict__ c
 }
 
 template <typename T>
-__global__ void jacobi_kernel(int n, int W, const int32_t *__restrict__ col, const T *__restrict__ A,
-                              const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x,
-                              T *__restrict__ xout, T omega, int first) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void jacobi_kernel_impl(int bid_, int nb_, int n, int W, const int32_t *__restrict__ col,
+                                                   const T *__restrict__ A, const T *__restrict__ dinv,
+                                                   const T *__restrict__ b, const T *__restrict__ x,
+                                                   T *__restrict__ xout, T omega, int first) {
+    const int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (first) {
         xout[i] = omega * dinv[i] * b[i];
@@ -60,15 +61,101 @@ __global__ void jacobi_kernel(int n, int W, const int32_t *__restrict__ col, con
     const T ax = ell_row(i, W, col, A, x);
     xout[i] = fma(omega * dinv[i], b[i] - ax, x[i]);
 }
+template <typename T>
+__global__ void jacobi_kernel(int n, int W, const int32_t *__restrict__ col, const T *__restrict__ A,
+                              const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x,
+                              T *__restrict__ xout, T omega, int first) {
+    jacobi_kernel_impl<T>(blockIdx.x, gridDim.x, n, W, col, A, dinv, b, x, xout, omega, first);
+}
+template <typename T>
+struct jacobi_kernel_args {
+    int nb_;
+    int n;
+    int W;
+    const int32_t *col;
+    const T *A;
+    const T *dinv;
+    const T *b;
+    const T *x;
+    T *xout;
+    T omega;
+    int first;
+};
+template <typename T>
+__global__ void jacobi_kernel_multi(const __grid_constant__ MultiP<jacobi_kernel_args<T>> M) {
+    int b_;
+    const jacobi_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    jacobi_kernel_impl<T>(b_, q_.nb_, q_.n, q_.W, q_.col, q_.A, q_.dinv, q_.b, q_.x, q_.xout, q_.omega, q_.first);
+}
+template <typename T>
+void jacobi_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int n, int W,
+                      const int32_t *col, const T *A, const T *dinv, const T *b, const T *x, T *xout, T omega,
+                      int first) {
+    if (Recorder *r_ = batch_recorder()) {
+        jacobi_kernel_args<T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.n = n;
+        q_.W = W;
+        q_.col = col;
+        q_.A = A;
+        q_.dinv = dinv;
+        q_.b = b;
+        q_.x = x;
+        q_.xout = xout;
+        q_.omega = omega;
+        q_.first = first;
+        batch_record(r_, reinterpret_cast<const void *>(&jacobi_kernel_multi<T>), q_, grid_, block_, smem_);
+        return;
+    }
+    jacobi_kernel<T><<<grid_, block_, smem_, s_>>>(n, W, col, A, dinv, b, x, xout, omega, first);
+}
+
 
 template <typename T>
-__global__ void prolong_add_kernel(int nf, const int32_t *__restrict__ parent, const T *__restrict__ ec,
-                                   T *__restrict__ xf) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void prolong_add_kernel_impl(int bid_, int nb_, int nf, const int32_t *__restrict__ parent,
+                                                        const T *__restrict__ ec, T *__restrict__ xf) {
+    const int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= nf) return;
     const int a = parent[2 * i], b = parent[2 * i + 1];
     xf[i] += (a == b) ? ec[a] : T(0.5) * (ec[a] + ec[b]);
 }
+template <typename T>
+__global__ void prolong_add_kernel(int nf, const int32_t *__restrict__ parent, const T *__restrict__ ec,
+                                   T *__restrict__ xf) {
+    prolong_add_kernel_impl<T>(blockIdx.x, gridDim.x, nf, parent, ec, xf);
+}
+template <typename T>
+struct prolong_add_kernel_args {
+    int nb_;
+    int nf;
+    const int32_t *parent;
+    const T *ec;
+    T *xf;
+};
+template <typename T>
+__global__ void prolong_add_kernel_multi(const __grid_constant__ MultiP<prolong_add_kernel_args<T>> M) {
+    int b_;
+    const prolong_add_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    prolong_add_kernel_impl<T>(b_, q_.nb_, q_.nf, q_.parent, q_.ec, q_.xf);
+}
+template <typename T>
+void prolong_add_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int nf,
+                           const int32_t *parent, const T *ec, T *xf) {
+    if (Recorder *r_ = batch_recorder()) {
+        prolong_add_kernel_args<T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.nf = nf;
+        q_.parent = parent;
+        q_.ec = ec;
+        q_.xf = xf;
+        batch_record(r_, reinterpret_cast<const void *>(&prolong_add_kernel_multi<T>), q_, grid_, block_, smem_);
+        return;
+    }
+    prolong_add_kernel<T><<<grid_, block_, smem_, s_>>>(nf, parent, ec, xf);
+}
+
 
 
 
@@ -78,13 +165,13 @@ __global__ void prolong_add_kernel(int nf, const int32_t *__restrict__ parent, c
 // Eight lanes per coarse vertex share its children; their partial sums are
 // combined by a fixed shuffle tree (deterministic).
 template <typename T>
-__global__ void __launch_bounds__(256) down_kernel(int nc, const int32_t *__restrict__ cp,
-                                                   const int32_t *__restrict__ ci, const T *__restrict__ cw,
-                                                   int nf, int W, const int32_t *__restrict__ col,
-                                                   const T *__restrict__ A, const T *__restrict__ bf,
-                                                   const T *__restrict__ xf, const T *__restrict__ dinv_c, T omega,
-                                                   T *__restrict__ bc, T *__restrict__ xc) {
-    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 3, lane = threadIdx.x & 7;
+__device__ __forceinline__ void down_kernel_impl(int bid_, int nb_, int nc, const int32_t *__restrict__ cp,
+                                                 const int32_t *__restrict__ ci, const T *__restrict__ cw, int nf,
+                                                 int W, const int32_t *__restrict__ col, const T *__restrict__ A,
+                                                 const T *__restrict__ bf, const T *__restrict__ xf,
+                                                 const T *__restrict__ dinv_c, T omega, T *__restrict__ bc,
+                                                 T *__restrict__ xc) {
+    const int gid = (bid_ * blockDim.x + threadIdx.x) >> 3, lane = threadIdx.x & 7;
     const bool valid = gid < nc;
     T acc = T(0);
     if (valid) {
@@ -101,15 +188,78 @@ __global__ void __launch_bounds__(256) down_kernel(int nc, const int32_t *__rest
         if (xc) xc[gid] = omega * dinv_c[gid] * acc;
     }
 }
+template <typename T>
+__global__ void __launch_bounds__(256) down_kernel(int nc, const int32_t *__restrict__ cp,
+                                                   const int32_t *__restrict__ ci, const T *__restrict__ cw, int nf,
+                                                   int W, const int32_t *__restrict__ col, const T *__restrict__ A,
+                                                   const T *__restrict__ bf, const T *__restrict__ xf,
+                                                   const T *__restrict__ dinv_c, T omega, T *__restrict__ bc,
+                                                   T *__restrict__ xc) {
+    down_kernel_impl<T>(blockIdx.x, gridDim.x, nc, cp, ci, cw, nf, W, col, A, bf, xf, dinv_c, omega, bc, xc);
+}
+template <typename T>
+struct down_kernel_args {
+    int nb_;
+    int nc;
+    const int32_t *cp;
+    const int32_t *ci;
+    const T *cw;
+    int nf;
+    int W;
+    const int32_t *col;
+    const T *A;
+    const T *bf;
+    const T *xf;
+    const T *dinv_c;
+    T omega;
+    T *bc;
+    T *xc;
+};
+template <typename T>
+__global__ void __launch_bounds__(256) down_kernel_multi(const __grid_constant__ MultiP<down_kernel_args<T>> M) {
+    int b_;
+    const down_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    down_kernel_impl<T>(b_, q_.nb_, q_.nc, q_.cp, q_.ci, q_.cw, q_.nf, q_.W, q_.col, q_.A, q_.bf, q_.xf, q_.dinv_c,
+        q_.omega, q_.bc, q_.xc);
+}
+template <typename T>
+void down_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int nc, const int32_t *cp,
+                    const int32_t *ci, const T *cw, int nf, int W, const int32_t *col, const T *A, const T *bf,
+                    const T *xf, const T *dinv_c, T omega, T *bc, T *xc) {
+    if (Recorder *r_ = batch_recorder()) {
+        down_kernel_args<T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.nc = nc;
+        q_.cp = cp;
+        q_.ci = ci;
+        q_.cw = cw;
+        q_.nf = nf;
+        q_.W = W;
+        q_.col = col;
+        q_.A = A;
+        q_.bf = bf;
+        q_.xf = xf;
+        q_.dinv_c = dinv_c;
+        q_.omega = omega;
+        q_.bc = bc;
+        q_.xc = xc;
+        batch_record(r_, reinterpret_cast<const void *>(&down_kernel_multi<T>), q_, grid_, block_, smem_);
+        return;
+    }
+    down_kernel<T><<<grid_, block_, smem_, s_>>>(nc, cp, ci, cw, nf, W, col, A, bf, xf, dinv_c, omega, bc, xc);
+}
+
 
 // Going up one level, fused: x' = x + P e_c (midpoint prolongation, formed on
 // the fly for every column) followed by one damped Jacobi sweep on x'.
 template <typename T>
-__global__ void up_kernel(int nf, int W, const int32_t *__restrict__ col, const T *__restrict__ A,
-                          const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x,
-                          const int32_t *__restrict__ parent, const T *__restrict__ ec, T *__restrict__ xout,
-                          T omega) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void up_kernel_impl(int bid_, int nb_, int nf, int W, const int32_t *__restrict__ col,
+                                               const T *__restrict__ A, const T *__restrict__ dinv,
+                                               const T *__restrict__ b, const T *__restrict__ x,
+                                               const int32_t *__restrict__ parent, const T *__restrict__ ec,
+                                               T *__restrict__ xout, T omega) {
+    const int i = bid_ * blockDim.x + threadIdx.x;
     if (i >= nf) return;
     T ax = T(0);
     const int32_t *c = col + size_t(i) * W;
@@ -131,6 +281,60 @@ __global__ void up_kernel(int nf, int W, const int32_t *__restrict__ col, const 
     const T xi = x[i] + ((a == bb) ? ec[a] : T(0.5) * (ec[a] + ec[bb]));
     xout[i] = fma(omega * dinv[i], b[i] - ax, xi);
 }
+template <typename T>
+__global__ void up_kernel(int nf, int W, const int32_t *__restrict__ col, const T *__restrict__ A,
+                          const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x,
+                          const int32_t *__restrict__ parent, const T *__restrict__ ec, T *__restrict__ xout,
+                          T omega) {
+    up_kernel_impl<T>(blockIdx.x, gridDim.x, nf, W, col, A, dinv, b, x, parent, ec, xout, omega);
+}
+template <typename T>
+struct up_kernel_args {
+    int nb_;
+    int nf;
+    int W;
+    const int32_t *col;
+    const T *A;
+    const T *dinv;
+    const T *b;
+    const T *x;
+    const int32_t *parent;
+    const T *ec;
+    T *xout;
+    T omega;
+};
+template <typename T>
+__global__ void up_kernel_multi(const __grid_constant__ MultiP<up_kernel_args<T>> M) {
+    int b_;
+    const up_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    up_kernel_impl<T>(b_, q_.nb_, q_.nf, q_.W, q_.col, q_.A, q_.dinv, q_.b, q_.x, q_.parent, q_.ec, q_.xout,
+        q_.omega);
+}
+template <typename T>
+void up_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int nf, int W, const int32_t *col,
+                  const T *A, const T *dinv, const T *b, const T *x, const int32_t *parent, const T *ec, T *xout,
+                  T omega) {
+    if (Recorder *r_ = batch_recorder()) {
+        up_kernel_args<T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.nf = nf;
+        q_.W = W;
+        q_.col = col;
+        q_.A = A;
+        q_.dinv = dinv;
+        q_.b = b;
+        q_.x = x;
+        q_.parent = parent;
+        q_.ec = ec;
+        q_.xout = xout;
+        q_.omega = omega;
+        batch_record(r_, reinterpret_cast<const void *>(&up_kernel_multi<T>), q_, grid_, block_, smem_);
+        return;
+    }
+    up_kernel<T><<<grid_, block_, smem_, s_>>>(nf, W, col, A, dinv, b, x, parent, ec, xout, omega);
+}
+
 
 // x_j + (P e_c)_j: the midpoint prolongation of the coarse correction added on the fly
 template <typename T>
@@ -162,18 +366,26 @@ constexpr int kChildPrefetch = 8;     // children of a coarse vertex held in reg
 // F0; b_c = R r for the patch's coarse vertices and, when xc is given, the
 // coarse level's first sweep from zero, x_c = omega D_c^-1 b_c.
 template <typename T, int WQ>
-__global__ void __launch_bounds__(kPatchThreads<T>, 1) down_fused_kernel(
-    const int32_t *__restrict__ f_ptr, const int32_t *__restrict__ f_n0, const int32_t *__restrict__ f_ids,
-    const int32_t *__restrict__ f0_base, const int32_t *__restrict__ lcol, const int32_t *__restrict__ fcol,
-    const int32_t *__restrict__ c_ptr, const int32_t *__restrict__ c_ids, const int32_t *__restrict__ cc_ptr,
-    const int32_t *__restrict__ cc_slot, const T *__restrict__ cc_w, const T *__restrict__ A,
-    const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ xout,
-    const T *__restrict__ dinv_c, T omega, T *__restrict__ bc, T *__restrict__ xc, int max_f1) {
+__device__ __forceinline__ void down_fused_kernel_impl(int bid_, int nb_, const int32_t *__restrict__ f_ptr,
+                                                       const int32_t *__restrict__ f_n0,
+                                                       const int32_t *__restrict__ f_ids,
+                                                       const int32_t *__restrict__ f0_base,
+                                                       const int32_t *__restrict__ lcol,
+                                                       const int32_t *__restrict__ fcol,
+                                                       const int32_t *__restrict__ c_ptr,
+                                                       const int32_t *__restrict__ c_ids,
+                                                       const int32_t *__restrict__ cc_ptr,
+                                                       const int32_t *__restrict__ cc_slot,
+                                                       const T *__restrict__ cc_w, const T *__restrict__ A,
+                                                       const T *__restrict__ dinv, const T *__restrict__ b,
+                                                       const T *__restrict__ x, T *__restrict__ xout,
+                                                       const T *__restrict__ dinv_c, T omega, T *__restrict__ bc,
+                                                       T *__restrict__ xc, int max_f1) {
     constexpr int W = 4 * WQ;
     extern __shared__ __align__(16) unsigned char patch_smem[];
     T *xs = reinterpret_cast<T *>(patch_smem);
     T *rs = xs + max_f1;
-    const int blk = blockIdx.x, s = threadIdx.x;
+    const int blk = bid_, s = threadIdx.x;
     const int s0 = f_ptr[blk], n1 = f_ptr[blk + 1] - s0, n0 = f_n0[blk];
     const int c = c_ptr[blk] + s;
     const bool row = s < n1, row0 = s < n0, crow = c < c_ptr[blk + 1];
@@ -237,6 +449,100 @@ __global__ void __launch_bounds__(kPatchThreads<T>, 1) down_fused_kernel(
         if (xc) xc[cid] = omega * dinv_c[cid] * acc;
     }
 }
+template <typename T, int WQ>
+__global__ void __launch_bounds__(kPatchThreads<T>, 1) down_fused_kernel(const int32_t *__restrict__ f_ptr,
+                                                                         const int32_t *__restrict__ f_n0,
+                                                                         const int32_t *__restrict__ f_ids,
+                                                                         const int32_t *__restrict__ f0_base,
+                                                                         const int32_t *__restrict__ lcol,
+                                                                         const int32_t *__restrict__ fcol,
+                                                                         const int32_t *__restrict__ c_ptr,
+                                                                         const int32_t *__restrict__ c_ids,
+                                                                         const int32_t *__restrict__ cc_ptr,
+                                                                         const int32_t *__restrict__ cc_slot,
+                                                                         const T *__restrict__ cc_w,
+                                                                         const T *__restrict__ A,
+                                                                         const T *__restrict__ dinv,
+                                                                         const T *__restrict__ b,
+                                                                         const T *__restrict__ x,
+                                                                         T *__restrict__ xout,
+                                                                         const T *__restrict__ dinv_c, T omega,
+                                                                         T *__restrict__ bc, T *__restrict__ xc,
+                                                                         int max_f1) {
+    down_fused_kernel_impl<T, WQ>(blockIdx.x, gridDim.x, f_ptr, f_n0, f_ids, f0_base, lcol, fcol, c_ptr, c_ids,
+        cc_ptr, cc_slot, cc_w, A, dinv, b, x, xout, dinv_c, omega, bc, xc, max_f1);
+}
+template <typename T, int WQ>
+struct down_fused_kernel_args {
+    int nb_;
+    const int32_t *f_ptr;
+    const int32_t *f_n0;
+    const int32_t *f_ids;
+    const int32_t *f0_base;
+    const int32_t *lcol;
+    const int32_t *fcol;
+    const int32_t *c_ptr;
+    const int32_t *c_ids;
+    const int32_t *cc_ptr;
+    const int32_t *cc_slot;
+    const T *cc_w;
+    const T *A;
+    const T *dinv;
+    const T *b;
+    const T *x;
+    T *xout;
+    const T *dinv_c;
+    T omega;
+    T *bc;
+    T *xc;
+    int max_f1;
+};
+template <typename T, int WQ>
+__global__ void __launch_bounds__(kPatchThreads<T>, 1) down_fused_kernel_multi(const __grid_constant__ MultiP<down_fused_kernel_args<T, WQ>> M) {
+    int b_;
+    const down_fused_kernel_args<T, WQ> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    down_fused_kernel_impl<T, WQ>(b_, q_.nb_, q_.f_ptr, q_.f_n0, q_.f_ids, q_.f0_base, q_.lcol, q_.fcol, q_.c_ptr,
+        q_.c_ids, q_.cc_ptr, q_.cc_slot, q_.cc_w, q_.A, q_.dinv, q_.b, q_.x, q_.xout, q_.dinv_c, q_.omega, q_.bc,
+        q_.xc, q_.max_f1);
+}
+template <typename T, int WQ>
+void down_fused_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, const int32_t *f_ptr,
+                          const int32_t *f_n0, const int32_t *f_ids, const int32_t *f0_base, const int32_t *lcol,
+                          const int32_t *fcol, const int32_t *c_ptr, const int32_t *c_ids, const int32_t *cc_ptr,
+                          const int32_t *cc_slot, const T *cc_w, const T *A, const T *dinv, const T *b, const T *x,
+                          T *xout, const T *dinv_c, T omega, T *bc, T *xc, int max_f1) {
+    if (Recorder *r_ = batch_recorder()) {
+        down_fused_kernel_args<T, WQ> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.f_ptr = f_ptr;
+        q_.f_n0 = f_n0;
+        q_.f_ids = f_ids;
+        q_.f0_base = f0_base;
+        q_.lcol = lcol;
+        q_.fcol = fcol;
+        q_.c_ptr = c_ptr;
+        q_.c_ids = c_ids;
+        q_.cc_ptr = cc_ptr;
+        q_.cc_slot = cc_slot;
+        q_.cc_w = cc_w;
+        q_.A = A;
+        q_.dinv = dinv;
+        q_.b = b;
+        q_.x = x;
+        q_.xout = xout;
+        q_.dinv_c = dinv_c;
+        q_.omega = omega;
+        q_.bc = bc;
+        q_.xc = xc;
+        q_.max_f1 = max_f1;
+        batch_record(r_, reinterpret_cast<const void *>(&down_fused_kernel_multi<T, WQ>), q_, grid_, block_, smem_);
+        return;
+    }
+    down_fused_kernel<T, WQ><<<grid_, block_, smem_, s_>>>(f_ptr, f_n0, f_ids, f0_base, lcol, fcol, c_ptr, c_ids,
+        cc_ptr, cc_slot, cc_w, A, dinv, b, x, xout, dinv_c, omega, bc, xc, max_f1);
+}
+
 
 // (P e_c) at a vertex with parents (pa, pb): the midpoint prolongation
 template <typename T>
@@ -250,16 +556,21 @@ __device__ __forceinline__ T prolong_at(const T *__restrict__ ec, int pa, int pb
 // on the fly, as up_kernel does); then x'' = x' + omega D^-1 (b - A x') on the
 // owned rows to xout.
 template <typename T, int WQ>
-__global__ void __launch_bounds__(kPatchThreads<T>, 1) up_fused_kernel(
-    const int32_t *__restrict__ g_ptr, const int32_t *__restrict__ g_nown, const int32_t *__restrict__ g_ids,
-    const int32_t *__restrict__ g0_base, const int32_t *__restrict__ glcol, const int32_t *__restrict__ gcol,
-    const int32_t *__restrict__ gpar, const int32_t *__restrict__ grow_par, const T *__restrict__ A,
-    const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x, const T *__restrict__ ec,
-    T *__restrict__ xout, T omega) {
+__device__ __forceinline__ void up_fused_kernel_impl(int bid_, int nb_, const int32_t *__restrict__ g_ptr,
+                                                     const int32_t *__restrict__ g_nown,
+                                                     const int32_t *__restrict__ g_ids,
+                                                     const int32_t *__restrict__ g0_base,
+                                                     const int32_t *__restrict__ glcol,
+                                                     const int32_t *__restrict__ gcol,
+                                                     const int32_t *__restrict__ gpar,
+                                                     const int32_t *__restrict__ grow_par, const T *__restrict__ A,
+                                                     const T *__restrict__ dinv, const T *__restrict__ b,
+                                                     const T *__restrict__ x, const T *__restrict__ ec,
+                                                     T *__restrict__ xout, T omega) {
     constexpr int W = 4 * WQ;
     extern __shared__ __align__(16) unsigned char patch_smem[];
     T *xs = reinterpret_cast<T *>(patch_smem);
-    const int blk = blockIdx.x, s = threadIdx.x;
+    const int blk = bid_, s = threadIdx.x;
     const int s0 = g_ptr[blk], n1 = g_ptr[blk + 1] - s0, nown = g_nown[blk];
     const bool row = s < n1, own = s < nown;
     int v = 0;
@@ -308,6 +619,81 @@ __global__ void __launch_bounds__(kPatchThreads<T>, 1) up_fused_kernel(
         xout[v] = fma(wv, bv - ax, x3);
     }
 }
+template <typename T, int WQ>
+__global__ void __launch_bounds__(kPatchThreads<T>, 1) up_fused_kernel(const int32_t *__restrict__ g_ptr,
+                                                                       const int32_t *__restrict__ g_nown,
+                                                                       const int32_t *__restrict__ g_ids,
+                                                                       const int32_t *__restrict__ g0_base,
+                                                                       const int32_t *__restrict__ glcol,
+                                                                       const int32_t *__restrict__ gcol,
+                                                                       const int32_t *__restrict__ gpar,
+                                                                       const int32_t *__restrict__ grow_par,
+                                                                       const T *__restrict__ A,
+                                                                       const T *__restrict__ dinv,
+                                                                       const T *__restrict__ b,
+                                                                       const T *__restrict__ x,
+                                                                       const T *__restrict__ ec, T *__restrict__ xout,
+                                                                       T omega) {
+    up_fused_kernel_impl<T, WQ>(blockIdx.x, gridDim.x, g_ptr, g_nown, g_ids, g0_base, glcol, gcol, gpar, grow_par, A,
+        dinv, b, x, ec, xout, omega);
+}
+template <typename T, int WQ>
+struct up_fused_kernel_args {
+    int nb_;
+    const int32_t *g_ptr;
+    const int32_t *g_nown;
+    const int32_t *g_ids;
+    const int32_t *g0_base;
+    const int32_t *glcol;
+    const int32_t *gcol;
+    const int32_t *gpar;
+    const int32_t *grow_par;
+    const T *A;
+    const T *dinv;
+    const T *b;
+    const T *x;
+    const T *ec;
+    T *xout;
+    T omega;
+};
+template <typename T, int WQ>
+__global__ void __launch_bounds__(kPatchThreads<T>, 1) up_fused_kernel_multi(const __grid_constant__ MultiP<up_fused_kernel_args<T, WQ>> M) {
+    int b_;
+    const up_fused_kernel_args<T, WQ> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    up_fused_kernel_impl<T, WQ>(b_, q_.nb_, q_.g_ptr, q_.g_nown, q_.g_ids, q_.g0_base, q_.glcol, q_.gcol, q_.gpar,
+        q_.grow_par, q_.A, q_.dinv, q_.b, q_.x, q_.ec, q_.xout, q_.omega);
+}
+template <typename T, int WQ>
+void up_fused_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, const int32_t *g_ptr,
+                        const int32_t *g_nown, const int32_t *g_ids, const int32_t *g0_base, const int32_t *glcol,
+                        const int32_t *gcol, const int32_t *gpar, const int32_t *grow_par, const T *A, const T *dinv,
+                        const T *b, const T *x, const T *ec, T *xout, T omega) {
+    if (Recorder *r_ = batch_recorder()) {
+        up_fused_kernel_args<T, WQ> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.g_ptr = g_ptr;
+        q_.g_nown = g_nown;
+        q_.g_ids = g_ids;
+        q_.g0_base = g0_base;
+        q_.glcol = glcol;
+        q_.gcol = gcol;
+        q_.gpar = gpar;
+        q_.grow_par = grow_par;
+        q_.A = A;
+        q_.dinv = dinv;
+        q_.b = b;
+        q_.x = x;
+        q_.ec = ec;
+        q_.xout = xout;
+        q_.omega = omega;
+        batch_record(r_, reinterpret_cast<const void *>(&up_fused_kernel_multi<T, WQ>), q_, grid_, block_, smem_);
+        return;
+    }
+    up_fused_kernel<T, WQ><<<grid_, block_, smem_, s_>>>(g_ptr, g_nown, g_ids, g0_base, glcol, gcol, gpar, grow_par,
+        A, dinv, b, x, ec, xout, omega);
+}
+
 
 // The V-cycle over the small levels in one CTA.  The levels' operators
 // (ELL values and columns, inverse diagonals), transfer lists and, when it
@@ -360,7 +746,7 @@ __device__ __forceinline__ void coarse_product(const double *inv, int n, const T
 // Every array pointer below is the shared-memory base plus an offset from the
 // level table, so that the compiler addresses shared memory directly.
 template <typename T>
-__global__ void __launch_bounds__(1024, 1) tail_kernel(TailArgs a) {
+__device__ __forceinline__ void tail_kernel_impl(int bid_, int nb_, TailArgs a) {
     extern __shared__ __align__(16) unsigned char tail_smem[];
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -475,18 +861,46 @@ __global__ void __launch_bounds__(1024, 1) tail_kernel(TailArgs a) {
     const T *ec = PT(oec);
     for (int i = tid; i < a.nv0; i += nt) xtop[i] = ec[i];
 }
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) tail_kernel(TailArgs a) {
+    tail_kernel_impl<T>(blockIdx.x, gridDim.x, a);
+}
+template <typename T>
+struct tail_kernel_args {
+    int nb_;
+    TailArgs a;
+};
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) tail_kernel_multi(const __grid_constant__ MultiP<tail_kernel_args<T>> M) {
+    int b_;
+    const tail_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    tail_kernel_impl<T>(b_, q_.nb_, q_.a);
+}
+template <typename T>
+void tail_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, TailArgs a) {
+    if (Recorder *r_ = batch_recorder()) {
+        tail_kernel_args<T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.a = a;
+        batch_record(r_, reinterpret_cast<const void *>(&tail_kernel_multi<T>), q_, grid_, block_, smem_);
+        return;
+    }
+    tail_kernel<T><<<grid_, block_, smem_, s_>>>(a);
+}
+
 
 }  // namespace
 
 template <typename T>
 cudaError_t launch_p1_jacobi(const DevLevel &L, const T *A, const T *dinv, const T *b, const T *x, T *xout, T omega,
                              bool first, cudaStream_t s) {
-    jacobi_kernel<T><<<blocks(L.nv, 256), 256, 0, s>>>(L.nv, L.width, L.col, A, dinv, b, x, xout, omega, first ? 1 : 0);
+    jacobi_kernel_go<T>(blocks(L.nv, 256), 256, 0, s, L.nv, L.width, L.col, A, dinv, b, x, xout, omega, first ? 1 : 0);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_p1_prolong_add(const DevLevel &coarse, int nv_fine, const T *ec, T *xf, cudaStream_t s) {
-    prolong_add_kernel<T><<<blocks(nv_fine, 256), 256, 0, s>>>(nv_fine, coarse.parent, ec, xf);
+    prolong_add_kernel_go<T>(blocks(nv_fine, 256), 256, 0, s, nv_fine, coarse.parent, ec, xf);
     return cudaGetLastError();
 }
 
@@ -494,7 +908,7 @@ template <typename T>
 cudaError_t launch_p1_down(const DevLevel &fine, const DevLevel &coarse, const T *A_f, const T *b_f, const T *x_f,
                            const T *dinv_c, T omega, T *b_c, T *x_c, cudaStream_t s) {
     const T *cw = sizeof(T) == 4 ? reinterpret_cast<const T *>(coarse.child_w32) : reinterpret_cast<const T *>(coarse.child_w);
-    down_kernel<T><<<blocks(size_t(coarse.nv) * 8, 256), 256, 0, s>>>(coarse.nv, coarse.child_ptr, coarse.child_idx, cw,
+    down_kernel_go<T>(blocks(size_t(coarse.nv) * 8, 256), 256, 0, s, coarse.nv, coarse.child_ptr, coarse.child_idx, cw,
                                                                       fine.nv, fine.width, fine.col, A_f, b_f, x_f, dinv_c,
                                                                       omega, b_c, x_c);
     return cudaGetLastError();
@@ -502,7 +916,7 @@ cudaError_t launch_p1_down(const DevLevel &fine, const DevLevel &coarse, const T
 template <typename T>
 cudaError_t launch_p1_up(const DevLevel &fine, const DevLevel &coarse, const T *A_f, const T *dinv_f, const T *b_f,
                          const T *x_f, const T *ec, T *xout, T omega, cudaStream_t s) {
-    up_kernel<T><<<blocks(fine.nv, 256), 256, 0, s>>>(fine.nv, fine.width, fine.col, A_f, dinv_f, b_f, x_f,
+    up_kernel_go<T>(blocks(fine.nv, 256), 256, 0, s, fine.nv, fine.width, fine.col, A_f, dinv_f, b_f, x_f,
                                                       coarse.parent, ec, xout, omega);
     return cudaGetLastError();
 }
@@ -522,11 +936,10 @@ cudaError_t launch_p1_down_fused(const DevLevel &fine, const DevLevel &coarse, c
     if (!p1_patch_ok<T>(fine)) return cudaErrorInvalidValue;
     const T *ccw = sizeof(T) == 4 ? reinterpret_cast<const T *>(fine.pcc_w32) : reinterpret_cast<const T *>(fine.pcc_w);
     const size_t smem = sizeof(T) * size_t(fine.max_f1 + fine.max_f0);
-    auto k = fine.width == 4 ? down_fused_kernel<T, 1> : down_fused_kernel<T, 2>;
-    k<<<fine.nb, patch_threads(fine.max_f1), smem, s>>>(fine.pf_ptr, fine.pf_n0, fine.pf_ids, fine.pf0_base, fine.plcol,
-                                                        fine.pfcol, fine.pc_ptr, fine.pc_ids, fine.pcc_ptr,
-                                                        fine.pcc_slot, ccw, A_f, dinv_f, b_f, x_f, xout_f, dinv_c,
-                                                        omega, b_c, x_c, fine.max_f1);
+    auto k = fine.width == 4 ? down_fused_kernel_go<T, 1> : down_fused_kernel_go<T, 2>;
+    k(fine.nb, patch_threads(fine.max_f1), smem, s, fine.pf_ptr, fine.pf_n0, fine.pf_ids, fine.pf0_base, fine.plcol,
+      fine.pfcol, fine.pc_ptr, fine.pc_ids, fine.pcc_ptr, fine.pcc_slot, ccw, A_f, dinv_f, b_f, x_f, xout_f, dinv_c,
+      omega, b_c, x_c, fine.max_f1);
     (void)coarse;
     return cudaGetLastError();
 }
@@ -535,10 +948,9 @@ cudaError_t launch_p1_up_fused(const DevLevel &fine, const DevLevel &coarse, con
                                const T *b_f, const T *x_f, const T *ec, T *xout, T omega, cudaStream_t s) {
     if (!p1_patch_ok<T>(fine)) return cudaErrorInvalidValue;
     const size_t smem = sizeof(T) * size_t(fine.max_g1);
-    auto k = fine.width == 4 ? up_fused_kernel<T, 1> : up_fused_kernel<T, 2>;
-    k<<<fine.nb, patch_threads(fine.max_g1), smem, s>>>(fine.pg_ptr, fine.pg_nown, fine.pg_ids, fine.pg0_base,
-                                                        fine.pglcol, fine.pgcol, fine.pgpar, fine.pgrow_par, A_f,
-                                                        dinv_f, b_f, x_f, ec, xout, omega);
+    auto k = fine.width == 4 ? up_fused_kernel_go<T, 1> : up_fused_kernel_go<T, 2>;
+    k(fine.nb, patch_threads(fine.max_g1), smem, s, fine.pg_ptr, fine.pg_nown, fine.pg_ids, fine.pg0_base,
+      fine.pglcol, fine.pgcol, fine.pgpar, fine.pgrow_par, A_f, dinv_f, b_f, x_f, ec, xout, omega);
     (void)coarse;
     return cudaGetLastError();
 }
@@ -549,7 +961,7 @@ cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s) {
     if (smem > kTailSmemMax) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(tail_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTailSmemMax));
     if (e != cudaSuccess) return e;
-    tail_kernel<T><<<1, 1024, smem, s>>>(a);
+    tail_kernel_go<T>(1, 1024, smem, s, a);
     return cudaGetLastError();
 }
 

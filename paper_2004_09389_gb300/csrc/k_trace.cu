@@ -138,16 +138,16 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) apply_kernel(int NF,
 // rows, four vectors at a time, into per-block partials; the last block to
 // finish adds the partials in block order (deterministic) into h.
 template <int P, typename T, typename ST>
-__global__ void __launch_bounds__(256, 4) apply_dots_kernel(int NF, const ST *__restrict__ Sval,
-                                                          const int32_t *__restrict__ nbr, const T *__restrict__ x,
-                                                          T *__restrict__ y, const T *__restrict__ V, size_t ld,
-                                                          int k, double *__restrict__ partial,
-                                                          unsigned int *__restrict__ counter, double *__restrict__ h) {
+__device__ __forceinline__ void apply_dots_kernel_impl(int bid_, int nb_, int NF, const ST *__restrict__ Sval,
+                                                       const int32_t *__restrict__ nbr, const T *__restrict__ x,
+                                                       T *__restrict__ y, const T *__restrict__ V, size_t ld, int k,
+                                                       double *__restrict__ partial,
+                                                       unsigned int *__restrict__ counter, double *__restrict__ h) {
     using A = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
     constexpr int PP = P + 1, G = 4;
     __shared__ A red[G][8];
     __shared__ bool last;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = bid_ * blockDim.x + threadIdx.x;
     const bool valid = e < NF;
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nwarp = blockDim.x / 32;
     T v[PP];
@@ -182,25 +182,81 @@ __global__ void __launch_bounds__(256, 4) apply_dots_kernel(int NF, const ST *__
         if (threadIdx.x < G && i0 + int(threadIdx.x) < k) {
             A t = A(0);
             for (int q = 0; q < nwarp; ++q) t += red[threadIdx.x][q];
-            partial[size_t(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = double(t);
+            partial[size_t(i0 + threadIdx.x) * nb_ + bid_] = double(t);
         }
         __syncthreads();
     }
     if (threadIdx.x < G) __threadfence();      // the writers' partials are visible before the count
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == nb_ - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
-    finish_partials(partial, int(gridDim.x), k, h);
+    finish_partials(partial, int(nb_), k, h);
     if (threadIdx.x == 0) *counter = 0u;
 }
+template <int P, typename T, typename ST>
+__global__ void __launch_bounds__(256, 4) apply_dots_kernel(int NF, const ST *__restrict__ Sval,
+                                                            const int32_t *__restrict__ nbr, const T *__restrict__ x,
+                                                            T *__restrict__ y, const T *__restrict__ V, size_t ld,
+                                                            int k, double *__restrict__ partial,
+                                                            unsigned int *__restrict__ counter,
+                                                            double *__restrict__ h) {
+    apply_dots_kernel_impl<P, T, ST>(blockIdx.x, gridDim.x, NF, Sval, nbr, x, y, V, ld, k, partial, counter, h);
+}
+template <int P, typename T, typename ST>
+struct apply_dots_kernel_args {
+    int nb_;
+    int NF;
+    const ST *Sval;
+    const int32_t *nbr;
+    const T *x;
+    T *y;
+    const T *V;
+    size_t ld;
+    int k;
+    double *partial;
+    unsigned int *counter;
+    double *h;
+};
+template <int P, typename T, typename ST>
+__global__ void __launch_bounds__(256, 4) apply_dots_kernel_multi(const __grid_constant__ MultiP<apply_dots_kernel_args<P, T, ST>> M) {
+    int b_;
+    const apply_dots_kernel_args<P, T, ST> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    apply_dots_kernel_impl<P, T, ST>(b_, q_.nb_, q_.NF, q_.Sval, q_.nbr, q_.x, q_.y, q_.V, q_.ld, q_.k, q_.partial,
+        q_.counter, q_.h);
+}
+template <int P, typename T, typename ST>
+void apply_dots_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int NF, const ST *Sval,
+                          const int32_t *nbr, const T *x, T *y, const T *V, size_t ld, int k, double *partial,
+                          unsigned int *counter, double *h) {
+    if (Recorder *r_ = batch_recorder()) {
+        apply_dots_kernel_args<P, T, ST> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.NF = NF;
+        q_.Sval = Sval;
+        q_.nbr = nbr;
+        q_.x = x;
+        q_.y = y;
+        q_.V = V;
+        q_.ld = ld;
+        q_.k = k;
+        q_.partial = partial;
+        q_.counter = counter;
+        q_.h = h;
+        batch_record(r_, reinterpret_cast<const void *>(&apply_dots_kernel_multi<P, T, ST>), q_, grid_, block_, smem_);
+        return;
+    }
+    apply_dots_kernel<P, T, ST><<<grid_, block_, smem_, s_>>>(NF, Sval, nbr, x, y, V, ld, k, partial, counter, h);
+}
+
 
 template <int P, typename T, typename ST>
-__global__ void __launch_bounds__(256, MinBlocks<T>::value) residual_kernel(int NF, const ST *__restrict__ Sval,
-                                                       const int32_t *__restrict__ nbr, const T *__restrict__ b,
-                                                       const T *__restrict__ x, T *__restrict__ res) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void residual_kernel_impl(int bid_, int nb_, int NF, const ST *__restrict__ Sval,
+                                                     const int32_t *__restrict__ nbr, const T *__restrict__ b,
+                                                     const T *__restrict__ x, T *__restrict__ res) {
+    const int e = bid_ * blockDim.x + threadIdx.x;
     if (e >= NF) return;
     T xs[5][P + 1], v[P + 1];
     gather_x<P, T>(nbr, x, e, NF, xs);
@@ -208,18 +264,61 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) residual_kernel(int 
 #pragma unroll
     for (int r = 0; r <= P; ++r) res[size_t(r) * NF + e] = b[size_t(r) * NF + e] - v[r];
 }
+template <int P, typename T, typename ST>
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) residual_kernel(int NF, const ST *__restrict__ Sval,
+                                                                            const int32_t *__restrict__ nbr,
+                                                                            const T *__restrict__ b,
+                                                                            const T *__restrict__ x,
+                                                                            T *__restrict__ res) {
+    residual_kernel_impl<P, T, ST>(blockIdx.x, gridDim.x, NF, Sval, nbr, b, x, res);
+}
+template <int P, typename T, typename ST>
+struct residual_kernel_args {
+    int nb_;
+    int NF;
+    const ST *Sval;
+    const int32_t *nbr;
+    const T *b;
+    const T *x;
+    T *res;
+};
+template <int P, typename T, typename ST>
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) residual_kernel_multi(const __grid_constant__ MultiP<residual_kernel_args<P, T, ST>> M) {
+    int b_;
+    const residual_kernel_args<P, T, ST> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    residual_kernel_impl<P, T, ST>(b_, q_.nb_, q_.NF, q_.Sval, q_.nbr, q_.b, q_.x, q_.res);
+}
+template <int P, typename T, typename ST>
+void residual_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int NF, const ST *Sval,
+                        const int32_t *nbr, const T *b, const T *x, T *res) {
+    if (Recorder *r_ = batch_recorder()) {
+        residual_kernel_args<P, T, ST> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.NF = NF;
+        q_.Sval = Sval;
+        q_.nbr = nbr;
+        q_.b = b;
+        q_.x = x;
+        q_.res = res;
+        batch_record(r_, reinterpret_cast<const void *>(&residual_kernel_multi<P, T, ST>), q_, grid_, block_, smem_);
+        return;
+    }
+    residual_kernel<P, T, ST><<<grid_, block_, smem_, s_>>>(NF, Sval, nbr, b, x, res);
+}
+
 
 // One sweep x_out = x + omega D_e^-1 (b - S x)_e; with CHEB, a step of the
 // Chebyshev iteration x_out = x + omega D_e^-1 (b - S x)_e + beta (x - x_prev)
 // (x_prev null: the previous iterate is zero).  x_out may alias x_prev: each
 // thread reads x_prev only at its own facet before writing it.
 template <int P, typename T, typename ST, bool CHEB = false>
-__global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_kernel(int NF, const ST *__restrict__ Sval, const T *__restrict__ Dinv,
-                                                     const int32_t *__restrict__ nbr, const T *__restrict__ b,
-                                                     const T *__restrict__ x, T *xout, T omega, T beta,
-                                                     const T *xprev) {
+__device__ __forceinline__ void smooth_kernel_impl(int bid_, int nb_, int NF, const ST *__restrict__ Sval,
+                                                   const T *__restrict__ Dinv, const int32_t *__restrict__ nbr,
+                                                   const T *__restrict__ b, const T *__restrict__ x, T *xout, T omega,
+                                                   T beta, const T *xprev) {
     constexpr int PP = P + 1;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = bid_ * blockDim.x + threadIdx.x;
     if (e >= NF) return;
     T xs[5][PP], v[PP], d[PP];
     gather_x<P, T>(nbr, x, e, NF, xs);
@@ -238,6 +337,60 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_kernel(int NF
         for (int r = 0; r < PP; ++r) xout[size_t(r) * NF + e] = fma(omega, d[r], xs[0][r]);
     }
 }
+template <int P, typename T, typename ST, bool CHEB = false>
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_kernel(int NF, const ST *__restrict__ Sval,
+                                                                          const T *__restrict__ Dinv,
+                                                                          const int32_t *__restrict__ nbr,
+                                                                          const T *__restrict__ b,
+                                                                          const T *__restrict__ x, T *xout, T omega,
+                                                                          T beta, const T *xprev) {
+    smooth_kernel_impl<P, T, ST, CHEB>(blockIdx.x, gridDim.x, NF, Sval, Dinv, nbr, b, x, xout, omega, beta, xprev);
+}
+template <int P, typename T, typename ST, bool CHEB = false>
+struct smooth_kernel_args {
+    int nb_;
+    int NF;
+    const ST *Sval;
+    const T *Dinv;
+    const int32_t *nbr;
+    const T *b;
+    const T *x;
+    T *xout;
+    T omega;
+    T beta;
+    const T *xprev;
+};
+template <int P, typename T, typename ST, bool CHEB = false>
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_kernel_multi(const __grid_constant__ MultiP<smooth_kernel_args<P, T, ST, CHEB>> M) {
+    int b_;
+    const smooth_kernel_args<P, T, ST, CHEB> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    smooth_kernel_impl<P, T, ST, CHEB>(b_, q_.nb_, q_.NF, q_.Sval, q_.Dinv, q_.nbr, q_.b, q_.x, q_.xout, q_.omega,
+        q_.beta, q_.xprev);
+}
+template <int P, typename T, typename ST, bool CHEB = false>
+void smooth_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int NF, const ST *Sval,
+                      const T *Dinv, const int32_t *nbr, const T *b, const T *x, T *xout, T omega, T beta,
+                      const T *xprev) {
+    if (Recorder *r_ = batch_recorder()) {
+        smooth_kernel_args<P, T, ST, CHEB> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.NF = NF;
+        q_.Sval = Sval;
+        q_.Dinv = Dinv;
+        q_.nbr = nbr;
+        q_.b = b;
+        q_.x = x;
+        q_.xout = xout;
+        q_.omega = omega;
+        q_.beta = beta;
+        q_.xprev = xprev;
+        batch_record(r_, reinterpret_cast<const void *>(&smooth_kernel_multi<P, T, ST, CHEB>), q_, grid_, block_, smem_);
+        return;
+    }
+    smooth_kernel<P, T, ST, CHEB><<<grid_, block_, smem_, s_>>>(NF, Sval, Dinv, nbr, b, x, xout, omega, beta, xprev);
+}
+
 
 // First post-smoothing sweep with the coarse correction folded in:
 // x' = x + pi e_c is formed on the fly for the five facets the rows touch,
@@ -245,14 +398,15 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_kernel(int NF
 // With X0, x' on the facet itself is also stored to x0out (the previous
 // iterate of the Chebyshev step that follows).
 template <int P, typename T, typename ST, bool X0 = false>
-__global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_prolong_kernel(int NF, const ST *__restrict__ Sval,
-                                                             const T *__restrict__ Dinv, const int32_t *__restrict__ nbr,
-                                                             const int32_t *__restrict__ fverts,
-                                                             const T *__restrict__ ec, const T *__restrict__ b,
-                                                             const T *__restrict__ x, T *__restrict__ xout, T omega,
-                                                             T *__restrict__ x0out) {
+__device__ __forceinline__ void smooth_prolong_kernel_impl(int bid_, int nb_, int NF, const ST *__restrict__ Sval,
+                                                           const T *__restrict__ Dinv,
+                                                           const int32_t *__restrict__ nbr,
+                                                           const int32_t *__restrict__ fverts,
+                                                           const T *__restrict__ ec, const T *__restrict__ b,
+                                                           const T *__restrict__ x, T *__restrict__ xout, T omega,
+                                                           T *__restrict__ x0out) {
     constexpr int PP = P + 1;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = bid_ * blockDim.x + threadIdx.x;
     if (e >= NF) return;
     int src[5];
     src[0] = e;
@@ -279,12 +433,74 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_prolong_kerne
         for (int r = 0; r < PP; ++r) x0out[size_t(r) * NF + e] = xs[0][r];
     }
 }
+template <int P, typename T, typename ST, bool X0 = false>
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_prolong_kernel(int NF, const ST *__restrict__ Sval,
+                                                                                  const T *__restrict__ Dinv,
+                                                                                  const int32_t *__restrict__ nbr,
+                                                                                  const int32_t *__restrict__ fverts,
+                                                                                  const T *__restrict__ ec,
+                                                                                  const T *__restrict__ b,
+                                                                                  const T *__restrict__ x,
+                                                                                  T *__restrict__ xout, T omega,
+                                                                                  T *__restrict__ x0out) {
+    smooth_prolong_kernel_impl<P, T, ST, X0>(blockIdx.x, gridDim.x, NF, Sval, Dinv, nbr, fverts, ec, b, x, xout,
+        omega, x0out);
+}
+template <int P, typename T, typename ST, bool X0 = false>
+struct smooth_prolong_kernel_args {
+    int nb_;
+    int NF;
+    const ST *Sval;
+    const T *Dinv;
+    const int32_t *nbr;
+    const int32_t *fverts;
+    const T *ec;
+    const T *b;
+    const T *x;
+    T *xout;
+    T omega;
+    T *x0out;
+};
+template <int P, typename T, typename ST, bool X0 = false>
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_prolong_kernel_multi(const __grid_constant__ MultiP<smooth_prolong_kernel_args<P, T, ST, X0>> M) {
+    int b_;
+    const smooth_prolong_kernel_args<P, T, ST, X0> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    smooth_prolong_kernel_impl<P, T, ST, X0>(b_, q_.nb_, q_.NF, q_.Sval, q_.Dinv, q_.nbr, q_.fverts, q_.ec, q_.b,
+        q_.x, q_.xout, q_.omega, q_.x0out);
+}
+template <int P, typename T, typename ST, bool X0 = false>
+void smooth_prolong_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int NF, const ST *Sval,
+                              const T *Dinv, const int32_t *nbr, const int32_t *fverts, const T *ec, const T *b,
+                              const T *x, T *xout, T omega, T *x0out) {
+    if (Recorder *r_ = batch_recorder()) {
+        smooth_prolong_kernel_args<P, T, ST, X0> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.NF = NF;
+        q_.Sval = Sval;
+        q_.Dinv = Dinv;
+        q_.nbr = nbr;
+        q_.fverts = fverts;
+        q_.ec = ec;
+        q_.b = b;
+        q_.x = x;
+        q_.xout = xout;
+        q_.omega = omega;
+        q_.x0out = x0out;
+        batch_record(r_, reinterpret_cast<const void *>(&smooth_prolong_kernel_multi<P, T, ST, X0>), q_, grid_, block_, smem_);
+        return;
+    }
+    smooth_prolong_kernel<P, T, ST, X0><<<grid_, block_, smem_, s_>>>(NF, Sval, Dinv, nbr, fverts, ec, b, x, xout,
+        omega, x0out);
+}
+
 
 // first sweep from a zero initial guess: x = omega D^-1 b
 template <int P, typename T>
-__global__ void smooth_first_kernel(int NF, const T *__restrict__ Dinv, const T *__restrict__ b, T *__restrict__ xout,
-                                    T omega, const T *__restrict__ w, const double *__restrict__ hnext,
-                                    T *__restrict__ bout) {
+__device__ __forceinline__ void smooth_first_kernel_impl(int bid_, int nb_, int NF, const T *__restrict__ Dinv,
+                                                         const T *__restrict__ b, T *__restrict__ xout, T omega,
+                                                         const T *__restrict__ w, const double *__restrict__ hnext,
+                                                         T *__restrict__ bout) {
     // with w: the right-hand side is the next Arnoldi vector b = w / h_{j+1,j}
     // (the last Gram-Schmidt step of the previous iteration), also stored to
     // bout; the FP64 reciprocal is formed once per block
@@ -294,7 +510,7 @@ __global__ void smooth_first_kernel(int NF, const T *__restrict__ Dinv, const T 
         __syncthreads();
     }
     constexpr int PP = P + 1;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = bid_ * blockDim.x + threadIdx.x;
     if (e >= NF) return;
     T v[PP], d[PP];
     if (w != nullptr) {
@@ -312,6 +528,51 @@ __global__ void smooth_first_kernel(int NF, const T *__restrict__ Dinv, const T 
 #pragma unroll
     for (int r = 0; r < PP; ++r) xout[size_t(r) * NF + e] = omega * d[r];
 }
+template <int P, typename T>
+__global__ void smooth_first_kernel(int NF, const T *__restrict__ Dinv, const T *__restrict__ b, T *__restrict__ xout,
+                                    T omega, const T *__restrict__ w, const double *__restrict__ hnext,
+                                    T *__restrict__ bout) {
+    smooth_first_kernel_impl<P, T>(blockIdx.x, gridDim.x, NF, Dinv, b, xout, omega, w, hnext, bout);
+}
+template <int P, typename T>
+struct smooth_first_kernel_args {
+    int nb_;
+    int NF;
+    const T *Dinv;
+    const T *b;
+    T *xout;
+    T omega;
+    const T *w;
+    const double *hnext;
+    T *bout;
+};
+template <int P, typename T>
+__global__ void smooth_first_kernel_multi(const __grid_constant__ MultiP<smooth_first_kernel_args<P, T>> M) {
+    int b_;
+    const smooth_first_kernel_args<P, T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    smooth_first_kernel_impl<P, T>(b_, q_.nb_, q_.NF, q_.Dinv, q_.b, q_.xout, q_.omega, q_.w, q_.hnext, q_.bout);
+}
+template <int P, typename T>
+void smooth_first_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int NF, const T *Dinv,
+                            const T *b, T *xout, T omega, const T *w, const double *hnext, T *bout) {
+    if (Recorder *r_ = batch_recorder()) {
+        smooth_first_kernel_args<P, T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.NF = NF;
+        q_.Dinv = Dinv;
+        q_.b = b;
+        q_.xout = xout;
+        q_.omega = omega;
+        q_.w = w;
+        q_.hnext = hnext;
+        q_.bout = bout;
+        batch_record(r_, reinterpret_cast<const void *>(&smooth_first_kernel_multi<P, T>), q_, grid_, block_, smem_);
+        return;
+    }
+    smooth_first_kernel<P, T><<<grid_, block_, smem_, s_>>>(NF, Dinv, b, xout, omega, w, hnext, bout);
+}
+
 
 // Repack the FP64 operator (groups of 2) into another storage precision
 // (groups of 16 / sizeof(TO)); padding lanes are zero.
@@ -338,12 +599,44 @@ __global__ void to_internal_kernel(int NF, int PP, const double *ext, double *in
     const size_t e = i / PP, r = i % PP;
     in[r * NF + e] = ext[i];
 }
-__global__ void to_external_kernel(int NF, int PP, const double *in, double *ext) {
-    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void to_external_kernel_impl(int bid_, int nb_, int NF, int PP, const double *in,
+                                                        double *ext) {
+    const size_t i = size_t(bid_) * blockDim.x + threadIdx.x;
     if (i >= size_t(NF) * PP) return;
     const size_t e = i / PP, r = i % PP;
     ext[i] = in[r * NF + e];
 }
+__global__ void to_external_kernel(int NF, int PP, const double *in, double *ext) {
+    to_external_kernel_impl(blockIdx.x, gridDim.x, NF, PP, in, ext);
+}
+struct to_external_kernel_args {
+    int nb_;
+    int NF;
+    int PP;
+    const double *in;
+    double *ext;
+};
+__global__ void to_external_kernel_multi(const __grid_constant__ MultiP<to_external_kernel_args> M) {
+    int b_;
+    const to_external_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
+    to_external_kernel_impl(b_, q_.nb_, q_.NF, q_.PP, q_.in, q_.ext);
+}
+void to_external_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int NF, int PP,
+                           const double *in, double *ext) {
+    if (Recorder *r_ = batch_recorder()) {
+        to_external_kernel_args q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.NF = NF;
+        q_.PP = PP;
+        q_.in = in;
+        q_.ext = ext;
+        batch_record(r_, reinterpret_cast<const void *>(&to_external_kernel_multi), q_, grid_, block_, smem_);
+        return;
+    }
+    to_external_kernel<<<grid_, block_, smem_, s_>>>(NF, PP, in, ext);
+}
+
 
 // cell unknown kappa of cell K from the caller's r_u [N][2][NP], r_h [N][NP]
 template <int NP>
@@ -368,11 +661,13 @@ __global__ void rhs_cell_kernel(int N, const double *__restrict__ W, const doubl
 
 // step 1, facet part: g_{e,r} = sum over the two cells of their row of edge i_s
 template <int P>
-__global__ void rhs_gather_kernel(int N, int NF, const double *__restrict__ ycell, const int32_t *__restrict__ fcell,
-                                  const int32_t *__restrict__ fedge, const int32_t *__restrict__ flip,
-                                  double *__restrict__ g) {
+__device__ __forceinline__ void rhs_gather_kernel_impl(int bid_, int nb_, int N, int NF,
+                                                       const double *__restrict__ ycell,
+                                                       const int32_t *__restrict__ fcell,
+                                                       const int32_t *__restrict__ fedge,
+                                                       const int32_t *__restrict__ flip, double *__restrict__ g) {
     constexpr int PP = P + 1;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = bid_ * blockDim.x + threadIdx.x;
     if (e >= NF) return;
     double v[PP];
 #pragma unroll
@@ -386,6 +681,50 @@ __global__ void rhs_gather_kernel(int N, int NF, const double *__restrict__ ycel
 #pragma unroll
     for (int r = 0; r < PP; ++r) g[size_t(r) * NF + e] = v[r];
 }
+template <int P>
+__global__ void rhs_gather_kernel(int N, int NF, const double *__restrict__ ycell, const int32_t *__restrict__ fcell,
+                                  const int32_t *__restrict__ fedge, const int32_t *__restrict__ flip,
+                                  double *__restrict__ g) {
+    rhs_gather_kernel_impl<P>(blockIdx.x, gridDim.x, N, NF, ycell, fcell, fedge, flip, g);
+}
+template <int P>
+struct rhs_gather_kernel_args {
+    int nb_;
+    int N;
+    int NF;
+    const double *ycell;
+    const int32_t *fcell;
+    const int32_t *fedge;
+    const int32_t *flip;
+    double *g;
+};
+template <int P>
+__global__ void rhs_gather_kernel_multi(const __grid_constant__ MultiP<rhs_gather_kernel_args<P>> M) {
+    int b_;
+    const rhs_gather_kernel_args<P> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    rhs_gather_kernel_impl<P>(b_, q_.nb_, q_.N, q_.NF, q_.ycell, q_.fcell, q_.fedge, q_.flip, q_.g);
+}
+template <int P>
+void rhs_gather_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int N, int NF,
+                          const double *ycell, const int32_t *fcell, const int32_t *fedge, const int32_t *flip,
+                          double *g) {
+    if (Recorder *r_ = batch_recorder()) {
+        rhs_gather_kernel_args<P> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.N = N;
+        q_.NF = NF;
+        q_.ycell = ycell;
+        q_.fcell = fcell;
+        q_.fedge = fedge;
+        q_.flip = flip;
+        q_.g = g;
+        batch_record(r_, reinterpret_cast<const void *>(&rhs_gather_kernel_multi<P>), q_, grid_, block_, smem_);
+        return;
+    }
+    rhs_gather_kernel<P><<<grid_, block_, smem_, s_>>>(N, NF, ycell, fcell, fedge, flip, g);
+}
+
 
 // step 3: q_K = R_M r_K - X_B lambda_K, written in the caller's u / h layout
 template <int P>
@@ -415,10 +754,12 @@ __global__ void recover_kernel(int N, int NF, const double *__restrict__ Rm, con
 // P1 restriction rho = pi^T: r_c[v] = sum over facet ends at v of the nodal
 // weights of the linear interpolant (1 - t_r at the lower vertex, t_r at the higher)
 template <int P, typename T>
-__global__ void restrict_kernel(int nv, int NF, const int32_t *__restrict__ v2f_ptr, const int32_t *__restrict__ v2f,
-                                const T *__restrict__ r, T *__restrict__ rc, const T *__restrict__ dinv0, T omega,
-                                T *__restrict__ x0) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void restrict_kernel_impl(int bid_, int nb_, int nv, int NF,
+                                                     const int32_t *__restrict__ v2f_ptr,
+                                                     const int32_t *__restrict__ v2f, const T *__restrict__ r,
+                                                     T *__restrict__ rc, const T *__restrict__ dinv0, T omega,
+                                                     T *__restrict__ x0) {
+    const int v = bid_ * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     T acc = T(0);
     for (int k = v2f_ptr[v]; k < v2f_ptr[v + 1]; ++k) {
@@ -433,6 +774,54 @@ __global__ void restrict_kernel(int nv, int NF, const int32_t *__restrict__ v2f_
     // first damped Jacobi sweep of the P1 level from zero, fused (x0 may be null)
     if (x0) x0[v] = omega * dinv0[v] * acc;
 }
+template <int P, typename T>
+__global__ void restrict_kernel(int nv, int NF, const int32_t *__restrict__ v2f_ptr, const int32_t *__restrict__ v2f,
+                                const T *__restrict__ r, T *__restrict__ rc, const T *__restrict__ dinv0, T omega,
+                                T *__restrict__ x0) {
+    restrict_kernel_impl<P, T>(blockIdx.x, gridDim.x, nv, NF, v2f_ptr, v2f, r, rc, dinv0, omega, x0);
+}
+template <int P, typename T>
+struct restrict_kernel_args {
+    int nb_;
+    int nv;
+    int NF;
+    const int32_t *v2f_ptr;
+    const int32_t *v2f;
+    const T *r;
+    T *rc;
+    const T *dinv0;
+    T omega;
+    T *x0;
+};
+template <int P, typename T>
+__global__ void restrict_kernel_multi(const __grid_constant__ MultiP<restrict_kernel_args<P, T>> M) {
+    int b_;
+    const restrict_kernel_args<P, T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    restrict_kernel_impl<P, T>(b_, q_.nb_, q_.nv, q_.NF, q_.v2f_ptr, q_.v2f, q_.r, q_.rc, q_.dinv0, q_.omega, q_.x0);
+}
+template <int P, typename T>
+void restrict_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int nv, int NF,
+                        const int32_t *v2f_ptr, const int32_t *v2f, const T *r, T *rc, const T *dinv0, T omega,
+                        T *x0) {
+    if (Recorder *r_ = batch_recorder()) {
+        restrict_kernel_args<P, T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.nv = nv;
+        q_.NF = NF;
+        q_.v2f_ptr = v2f_ptr;
+        q_.v2f = v2f;
+        q_.r = r;
+        q_.rc = rc;
+        q_.dinv0 = dinv0;
+        q_.omega = omega;
+        q_.x0 = x0;
+        batch_record(r_, reinterpret_cast<const void *>(&restrict_kernel_multi<P, T>), q_, grid_, block_, smem_);
+        return;
+    }
+    restrict_kernel<P, T><<<grid_, block_, smem_, s_>>>(nv, NF, v2f_ptr, v2f, r, rc, dinv0, omega, x0);
+}
+
 
 // x += pi e_c (linear interpolation along each facet)
 template <int P, typename T>
@@ -469,7 +858,7 @@ inline bool bf16_pre(hdg_handle *h) { return h->prm.precision == HDG_MIXED_BF16 
 template <typename T>
 cudaError_t launch_apply_dots_t(hdg_handle *h, const T *x, T *y, const T *V, size_t ld, int k, double *partial,
                                 unsigned int *counter, double *hdots) {
-    HDG_DISPATCH_PF(h->pf, T, (apply_dots_kernel<P, T, T><<<blocks(h->NF, 256), 256, 0, h->stream>>>(
+    HDG_DISPATCH_PF(h->pf, T, (apply_dots_kernel_go<P, T, T>(blocks(h->NF, 256), 256, 0, h->stream, 
                              h->NF, Ops<T>::S(h, false), h->d_nbr, x, y, V, ld, k, partial, counter, hdots)));
     return cudaGetLastError();
 }
@@ -483,11 +872,11 @@ cudaError_t launch_apply_t(hdg_handle *h, const T *x, T *y) {
 template <typename T>
 cudaError_t launch_residual_t(hdg_handle *h, const T *b, const T *x, T *r, bool pre) {
     if constexpr (std::is_same<T, float>::value) if (pre && bf16_pre(h)) {
-        HDG_DISPATCH_PF(h->pf, T, (residual_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, h->d_nbr, b, x, r)));
+        HDG_DISPATCH_PF(h->pf, T, (residual_kernel_go<P, T, __nv_bfloat16>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->NF, h->d_Sval16, h->d_nbr, b, x, r)));
         return cudaGetLastError();
     }
     {
-        HDG_DISPATCH_PF(h->pf, T, (residual_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, pre), h->d_nbr, b, x, r)));
+        HDG_DISPATCH_PF(h->pf, T, (residual_kernel_go<P, T, T>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->NF, Ops<T>::S(h, pre), h->d_nbr, b, x, r)));
     }
     return cudaGetLastError();
 }
@@ -495,11 +884,11 @@ template <typename T>
 cudaError_t launch_smooth_t(hdg_handle *h, const T *b, const T *x, T *xout) {
     const T om = T(h->prm.omega);
     if constexpr (std::is_same<T, float>::value) if (bf16_pre(h)) {
-        HDG_DISPATCH_PF(h->pf, T, (smooth_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, om, T(0), nullptr)));
+        HDG_DISPATCH_PF(h->pf, T, (smooth_kernel_go<P, T, __nv_bfloat16>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, om, T(0), nullptr)));
         return cudaGetLastError();
     }
     {
-        HDG_DISPATCH_PF(h->pf, T, (smooth_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, om, T(0), nullptr)));
+        HDG_DISPATCH_PF(h->pf, T, (smooth_kernel_go<P, T, T>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, om, T(0), nullptr)));
     }
     return cudaGetLastError();
 }
@@ -508,11 +897,11 @@ template <typename T>
 cudaError_t launch_smooth_cheb_t(hdg_handle *h, const T *b, const T *x, T *xout, double omega, double beta,
                                  const T *xprev) {
     if constexpr (std::is_same<T, float>::value) if (bf16_pre(h)) {
-        HDG_DISPATCH_PF(h->pf, T, (smooth_kernel<P, T, __nv_bfloat16, true><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, T(omega), T(beta), xprev)));
+        HDG_DISPATCH_PF(h->pf, T, (smooth_kernel_go<P, T, __nv_bfloat16, true>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, b, x, xout, T(omega), T(beta), xprev)));
         return cudaGetLastError();
     }
     {
-        HDG_DISPATCH_PF(h->pf, T, (smooth_kernel<P, T, T, true><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, T(omega), T(beta), xprev)));
+        HDG_DISPATCH_PF(h->pf, T, (smooth_kernel_go<P, T, T, true>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, b, x, xout, T(omega), T(beta), xprev)));
     }
     return cudaGetLastError();
 }
@@ -520,12 +909,12 @@ template <typename T>
 cudaError_t launch_smooth_first_t(hdg_handle *h, const T *b, T *x, const T *w, const double *hnext, T *bout,
                                   double omega) {
     const T om = T(omega > 0 ? omega : h->prm.omega);
-    HDG_DISPATCH_PF(h->pf, T, (smooth_first_kernel<P, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::D(h), b, x, om, w, hnext, bout)));
+    HDG_DISPATCH_PF(h->pf, T, (smooth_first_kernel_go<P, T>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->NF, Ops<T>::D(h), b, x, om, w, hnext, bout)));
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_restrict_t(hdg_handle *h, const T *r, T *rc, const T *dinv0, T omega, T *x0) {
-    HDG_DISPATCH_P(h->p, (restrict_kernel<P, T><<<blocks(h->nv, 256), 256, 0, h->stream>>>(h->nv, h->NF, h->d_v2f_ptr, h->d_v2f, r, rc, dinv0, omega, x0)));
+    HDG_DISPATCH_P(h->p, (restrict_kernel_go<P, T>(blocks(h->nv, 256), 256, 0, h->stream, h->nv, h->NF, h->d_v2f_ptr, h->d_v2f, r, rc, dinv0, omega, x0)));
     return cudaGetLastError();
 }
 template <typename T>
@@ -534,16 +923,16 @@ cudaError_t launch_smooth_prolong_t(hdg_handle *h, const T *ec, const T *b, cons
     const T om = T(omega > 0 ? omega : h->prm.omega);
     if constexpr (std::is_same<T, float>::value) if (bf16_pre(h)) {
         if (x0out) {
-            HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, __nv_bfloat16, true><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om, x0out)));
+            HDG_DISPATCH_P(h->p, (smooth_prolong_kernel_go<P, T, __nv_bfloat16, true>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om, x0out)));
         } else {
-            HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, __nv_bfloat16><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om, nullptr)));
+            HDG_DISPATCH_P(h->p, (smooth_prolong_kernel_go<P, T, __nv_bfloat16>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->NF, h->d_Sval16, Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om, nullptr)));
         }
         return cudaGetLastError();
     }
     if (x0out) {
-        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, T, true><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om, x0out)));
+        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel_go<P, T, T, true>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om, x0out)));
     } else {
-        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel<P, T, T><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om, nullptr)));
+        HDG_DISPATCH_P(h->p, (smooth_prolong_kernel_go<P, T, T>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->NF, Ops<T>::S(h, true), Ops<T>::D(h), h->d_nbr, h->d_facet_verts, ec, b, x, xout, om, nullptr)));
     }
     return cudaGetLastError();
 }
@@ -601,12 +990,12 @@ cudaError_t launch_to_internal(hdg_handle *h, const double *ext, double *in) {
 }
 cudaError_t launch_to_external(hdg_handle *h, const double *in, double *ext) {
     size_t n = size_t(h->NF) * h->pp;
-    to_external_kernel<<<blocks(n, 256), 256, 0, h->stream>>>(h->NF, h->pp, in, ext);
+    to_external_kernel_go(blocks(n, 256), 256, 0, h->stream, h->NF, h->pp, in, ext);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rhs_gather(hdg_handle *h, const double *ycell, double *g) {
-    HDG_DISPATCH_P(h->p, (rhs_gather_kernel<P><<<blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream>>>(h->N, h->NF, ycell, h->d_facet_cell, h->d_facet_edge, h->d_flip, g)));
+    HDG_DISPATCH_P(h->p, (rhs_gather_kernel_go<P>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->N, h->NF, ycell, h->d_facet_cell, h->d_facet_edge, h->d_flip, g)));
     return cudaGetLastError();
 }
 

@@ -269,3 +269,61 @@ def solve_batch_dev(solvers, r_u, r_h, lam, n_threads: int = 0, allow_fail: bool
     if rc != 0 and not (allow_fail and rc in (L.HDG_ENOCONV, L.HDG_EBREAKDOWN)):
         raise L.HDGError(rc, (lib.hdg_last_error(None) or b"").decode())
     return [infos[i].as_dict() for i in range(n)]
+
+
+class MergedBatch:
+    """Merged batched solves (``hdg_batch_*``): one host thread drives the
+    solves of every solver, whose launches run as merged multi-problem
+    kernels in one CUDA graph per wave.  Solvers must use the precision
+    HDG_MIXED_FP32 or HDG_MIXED_BF16 (upwind flux, reorth = 0).  Close the
+    batch before its solvers."""
+
+    def __init__(self, solvers):
+        self.lib = L.load()
+        self.solvers = list(solvers)
+        n = len(self.solvers)
+        hs = (C.c_void_p * n)(*[s.h.value for s in self.solvers])
+        self.b = C.c_void_p()
+        L.check(None, self.lib.hdg_batch_create(hs, n, C.byref(self.b)))
+
+    def solve_dev(self, r_u, r_h, lam, allow_fail: bool = False):
+        """Solver i solves device tensors ``r_u[i], r_h[i]`` into ``lam[i]``
+        (complete on return).  Returns the list of info dicts."""
+        n = len(self.solvers)
+        torch = _torch()
+        if torch is not None:
+            cur = torch.cuda.current_stream()
+            for s in self.solvers:
+                s.stream.wait_stream(cur)
+        pu = (C.c_void_p * n)(*[L._ptr(t) for t in r_u])
+        ph = (C.c_void_p * n)(*[L._ptr(t) for t in r_h])
+        pl = (C.c_void_p * n)(*[L._ptr(t) for t in lam])
+        infos = (L.hdg_solve_info * n)()
+        rc = self.lib.hdg_batch_solve_dev(self.b, pu, ph, pl, infos)
+        if torch is not None:
+            for s in self.solvers:
+                cur.wait_stream(s.stream)
+        if rc != 0 and not (allow_fail and rc in (L.HDG_ENOCONV, L.HDG_EBREAKDOWN)):
+            raise L.HDGError(rc, (self.lib.hdg_last_error(None) or b"").decode())
+        return [infos[i].as_dict() for i in range(n)]
+
+    def stats(self) -> dict:
+        """Waves, merged launches, per-problem launches they carried, graphs
+        replayed and graphs built since creation; host nanoseconds spent
+        running the problems' host logic, merging/launching waves, and waiting
+        for the last waves."""
+        a = (C.c_int64 * 8)()
+        L.check(None, self.lib.hdg_batch_stats(self.b, a))
+        return dict(zip(("waves", "launches", "records", "replays", "builds", "host_ns_fibers", "host_ns_launch",
+                         "host_ns_wait"), list(a)))
+
+    def close(self):
+        if self.b:
+            self.lib.hdg_batch_destroy(self.b)
+            self.b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

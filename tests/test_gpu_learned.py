@@ -1,4 +1,4 @@
-"""Learned facet-patch smoother on the GPU (spec extension).
+"""Learned facet-patch smoother on the GPU (an extension beyond the paper).
 
 * loss and gradient of the library's own forward / backward kernels agree with
   the oracle's (FP64, hand-written backward pinned by finite differences) to
