@@ -184,7 +184,11 @@ HDG_API void hdg_default_params(hdg_params *prm);
  * the single-block coarse cycle; HDG_P1_FUSED=0 replaces the patch-fused P1
  * kernels by one launch per smoothing / transfer step; HDG_FACET_BLOCK
  * (64, 128 or 256; default 128 for HDG_FP64 handles, 256 otherwise) sets the
- * threads per block of the facet-row kernels. */
+ * threads per block of the facet-row kernels.  HDG_PDL (a bit mask, read once
+ * per process; default 6) selects the kernel families launched with
+ * programmatic dependent launch, so that a kernel's blocks are scheduled
+ * while its predecessor drains: 1 the facet-row kernels, 2 the P1 kernels,
+ * 4 the Krylov kernels; 0 none. */
 HDG_API int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hdg_handle **out);
 
 /* (Re)build the cell operators for the handle's parameters: for every cell the

@@ -14,10 +14,22 @@
 #include "common.h"
 
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 #include <unordered_map>
 
 namespace hdg {
+
+// launch family of this file for pdl_launch (Krylov and copy kernels)
+constexpr unsigned kPdlFamily = 4;
+
+bool pdl_enabled(unsigned family) {
+    static const unsigned mask = [] {
+        const char *e = std::getenv("HDG_PDL");
+        return e ? unsigned(std::strtoul(e, nullptr, 0)) : 6u;
+    }();
+    return (mask & family) != 0;
+}
 
 Recorder *&batch_recorder() {
     static thread_local Recorder *r = nullptr;
@@ -42,6 +54,7 @@ __device__ __forceinline__ void copy_kernel_impl(int bid_, int nb_, unsigned cha
     }
 }
 __global__ void copy_kernel(unsigned char *dst, const unsigned char *src, size_t n) {
+    pdl_wait();
     copy_kernel_impl(blockIdx.x, gridDim.x, dst, src, n);
 }
 struct copy_kernel_args {
@@ -51,6 +64,7 @@ struct copy_kernel_args {
     size_t n;
 };
 __global__ void copy_kernel_multi(const __grid_constant__ MultiP<copy_kernel_args> M) {
+    pdl_wait();
     int b_;
     const copy_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
     copy_kernel_impl(b_, q_.nb_, q_.dst, q_.src, q_.n);
@@ -67,7 +81,7 @@ void copy_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t 
         batch_record(r_, reinterpret_cast<const void *>(&copy_kernel_multi), q_, grid_, block_, smem_);
         return;
     }
-    copy_kernel<<<grid_, block_, smem_, s_>>>(dst, src, n);
+    pdl_launch(kPdlFamily, &copy_kernel, grid_, block_, smem_, s_, dst, src, n);
 }
 
 

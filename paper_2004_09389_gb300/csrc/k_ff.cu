@@ -19,6 +19,9 @@
 
 namespace hdg {
 
+// launch family of this file for pdl_launch (facet-row kernels)
+constexpr unsigned kPdlFamily = 1;
+
 namespace {
 
 inline unsigned blocks(size_t n, int bs) { return unsigned((n + bs - 1) / bs); }
@@ -109,6 +112,7 @@ __device__ __forceinline__ void axpby_split_kernel_impl(int bid_, int nb_, doubl
 }
 __global__ void axpby_split_kernel(double *__restrict__ x, float2 *__restrict__ x2, const float *__restrict__ d,
                                    const double *__restrict__ scale, size_t n) {
+    pdl_wait();
     axpby_split_kernel_impl(blockIdx.x, gridDim.x, x, x2, d, scale, n);
 }
 struct axpby_split_kernel_args {
@@ -120,6 +124,7 @@ struct axpby_split_kernel_args {
     size_t n;
 };
 __global__ void axpby_split_kernel_multi(const __grid_constant__ MultiP<axpby_split_kernel_args> M) {
+    pdl_wait();
     int b_;
     const axpby_split_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
     axpby_split_kernel_impl(b_, q_.nb_, q_.x, q_.x2, q_.d, q_.scale, q_.n);
@@ -138,7 +143,7 @@ void axpby_split_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaSt
         batch_record(r_, reinterpret_cast<const void *>(&axpby_split_kernel_multi), q_, grid_, block_, smem_);
         return;
     }
-    axpby_split_kernel<<<grid_, block_, smem_, s_>>>(x, x2, d, scale, n);
+    pdl_launch(kPdlFamily, &axpby_split_kernel, grid_, block_, smem_, s_, x, x2, d, scale, n);
 }
 
 
@@ -182,6 +187,7 @@ __global__ void __launch_bounds__(256) residual_ff_kernel(int NF, const float4 *
                                                           const int32_t *__restrict__ nbr,
                                                           const double *__restrict__ b, const float2 *__restrict__ x2,
                                                           double *__restrict__ res) {
+    pdl_wait();
     residual_ff_kernel_impl<P>(blockIdx.x, gridDim.x, NF, S2, nbr, b, x2, res);
 }
 template <int P>
@@ -196,6 +202,7 @@ struct residual_ff_kernel_args {
 };
 template <int P>
 __global__ void __launch_bounds__(256) residual_ff_kernel_multi(const __grid_constant__ MultiP<residual_ff_kernel_args<P>> M) {
+    pdl_wait();
     int b_;
     const residual_ff_kernel_args<P> &q_ = M.a[merge_find(M.start, M.n, b_)];
     residual_ff_kernel_impl<P>(b_, q_.nb_, q_.NF, q_.S2, q_.nbr, q_.b, q_.x2, q_.res);
@@ -216,7 +223,7 @@ void residual_ff_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaSt
         batch_record(r_, reinterpret_cast<const void *>(&residual_ff_kernel_multi<P>), q_, grid_, block_, smem_);
         return;
     }
-    residual_ff_kernel<P><<<grid_, block_, smem_, s_>>>(NF, S2, nbr, b, x2, res);
+    pdl_launch(kPdlFamily, &residual_ff_kernel<P>, grid_, block_, smem_, s_, NF, S2, nbr, b, x2, res);
 }
 
 
@@ -267,6 +274,7 @@ __global__ void __launch_bounds__(128, 8) rhs_cell_ff_kernel(int N, const float4
                                                              const double *__restrict__ r_h,
                                                              double *__restrict__ ycell, double *__restrict__ cu,
                                                              double *__restrict__ ch) {
+    pdl_wait();
     rhs_cell_ff_kernel_impl<P>(blockIdx.x, gridDim.x, N, W2, r_u, r_h, ycell, cu, ch);
 }
 template <int P>
@@ -282,6 +290,7 @@ struct rhs_cell_ff_kernel_args {
 };
 template <int P>
 __global__ void __launch_bounds__(128, 8) rhs_cell_ff_kernel_multi(const __grid_constant__ MultiP<rhs_cell_ff_kernel_args<P>> M) {
+    pdl_wait();
     int b_;
     const rhs_cell_ff_kernel_args<P> &q_ = M.a[merge_find(M.start, M.n, b_)];
     rhs_cell_ff_kernel_impl<P>(b_, q_.nb_, q_.N, q_.W2, q_.r_u, q_.r_h, q_.ycell, q_.cu, q_.ch);
@@ -303,7 +312,7 @@ void rhs_cell_ff_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaSt
         batch_record(r_, reinterpret_cast<const void *>(&rhs_cell_ff_kernel_multi<P>), q_, grid_, block_, smem_);
         return;
     }
-    rhs_cell_ff_kernel<P><<<grid_, block_, smem_, s_>>>(N, W2, r_u, r_h, ycell, cu, ch);
+    pdl_launch(kPdlFamily, &rhs_cell_ff_kernel<P>, grid_, block_, smem_, s_, N, W2, r_u, r_h, ycell, cu, ch);
 }
 
 

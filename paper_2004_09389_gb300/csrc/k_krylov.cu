@@ -9,6 +9,9 @@
 
 namespace hdg {
 
+// launch family of this file for pdl_launch (Krylov and copy kernels)
+constexpr unsigned kPdlFamily = 4;
+
 namespace {
 
 inline unsigned blocks(size_t n, int bs) { return unsigned((n + bs - 1) / bs); }
@@ -88,6 +91,7 @@ __global__ void __launch_bounds__(256) dot1_kernel(const T *__restrict__ v, cons
                                                    double *__restrict__ partial, int nchunk,
                                                    unsigned int *__restrict__ counter, double *__restrict__ out,
                                                    HostValue *pub, int32_t seq, double *root_a, double *root_b) {
+    pdl_wait();
     dot1_kernel_impl<T>(blockIdx.x, gridDim.x, v, w, n, partial, nchunk, counter, out, pub, seq, root_a, root_b);
 }
 template <typename T>
@@ -107,6 +111,7 @@ struct dot1_kernel_args {
 };
 template <typename T>
 __global__ void __launch_bounds__(256) dot1_kernel_multi(const __grid_constant__ MultiP<dot1_kernel_args<T>> M) {
+    pdl_wait();
     int b_;
     const dot1_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     dot1_kernel_impl<T>(b_, q_.nb_, q_.v, q_.w, q_.n, q_.partial, q_.nchunk, q_.counter, q_.out, q_.pub, q_.seq,
@@ -134,7 +139,7 @@ void dot1_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t 
         batch_record(r_, reinterpret_cast<const void *>(&dot1_kernel_multi<T>), q_, grid_, block_, smem_);
         return;
     }
-    dot1_kernel<T><<<grid_, block_, smem_, s_>>>(v, w, n, partial, nchunk, counter, out, pub, seq, root_a, root_b);
+    pdl_launch(kPdlFamily, &dot1_kernel<T>, grid_, block_, smem_, s_, v, w, n, partial, nchunk, counter, out, pub, seq, root_a, root_b);
 }
 
 
@@ -179,6 +184,7 @@ __device__ __forceinline__ void multi_axpy_kernel_impl(int bid_, int nb_, T *__r
 template <typename T>
 __global__ void __launch_bounds__(256) multi_axpy_kernel(T *__restrict__ w, const T *__restrict__ V, size_t ld, int k,
                                                          const double *__restrict__ coef, double sign, size_t n) {
+    pdl_wait();
     multi_axpy_kernel_impl<T>(blockIdx.x, gridDim.x, w, V, ld, k, coef, sign, n);
 }
 template <typename T>
@@ -194,6 +200,7 @@ struct multi_axpy_kernel_args {
 };
 template <typename T>
 __global__ void __launch_bounds__(256) multi_axpy_kernel_multi(const __grid_constant__ MultiP<multi_axpy_kernel_args<T>> M) {
+    pdl_wait();
     int b_;
     const multi_axpy_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     multi_axpy_kernel_impl<T>(b_, q_.nb_, q_.w, q_.V, q_.ld, q_.k, q_.coef, q_.sign, q_.n);
@@ -215,7 +222,7 @@ void multi_axpy_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         batch_record(r_, reinterpret_cast<const void *>(&multi_axpy_kernel_multi<T>), q_, grid_, block_, smem_);
         return;
     }
-    multi_axpy_kernel<T><<<grid_, block_, smem_, s_>>>(w, V, ld, k, coef, sign, n);
+    pdl_launch(kPdlFamily, &multi_axpy_kernel<T>, grid_, block_, smem_, s_, w, V, ld, k, coef, sign, n);
 }
 
 
@@ -266,6 +273,7 @@ __device__ __forceinline__ void scale_copy_kernel_impl(int bid_, int nb_, const 
 template <typename T>
 __global__ void scale_copy_kernel(const T *__restrict__ w, T *__restrict__ v, const double *__restrict__ denom,
                                   size_t n) {
+    pdl_wait();
     scale_copy_kernel_impl<T>(blockIdx.x, gridDim.x, w, v, denom, n);
 }
 template <typename T>
@@ -278,6 +286,7 @@ struct scale_copy_kernel_args {
 };
 template <typename T>
 __global__ void scale_copy_kernel_multi(const __grid_constant__ MultiP<scale_copy_kernel_args<T>> M) {
+    pdl_wait();
     int b_;
     const scale_copy_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     scale_copy_kernel_impl<T>(b_, q_.nb_, q_.w, q_.v, q_.denom, q_.n);
@@ -296,7 +305,7 @@ void scale_copy_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         batch_record(r_, reinterpret_cast<const void *>(&scale_copy_kernel_multi<T>), q_, grid_, block_, smem_);
         return;
     }
-    scale_copy_kernel<T><<<grid_, block_, smem_, s_>>>(w, v, denom, n);
+    pdl_launch(kPdlFamily, &scale_copy_kernel<T>, grid_, block_, smem_, s_, w, v, denom, n);
 }
 
 
@@ -322,6 +331,7 @@ __device__ __forceinline__ void hessenberg_solve_kernel_impl(int bid_, int nb_, 
     }
 }
 __global__ void hessenberg_solve_kernel(const double *Hm, int ldh, const double *sv, int k, double *y) {
+    pdl_wait();
     hessenberg_solve_kernel_impl(blockIdx.x, gridDim.x, Hm, ldh, sv, k, y);
 }
 struct hessenberg_solve_kernel_args {
@@ -333,6 +343,7 @@ struct hessenberg_solve_kernel_args {
     double *y;
 };
 __global__ void hessenberg_solve_kernel_multi(const __grid_constant__ MultiP<hessenberg_solve_kernel_args> M) {
+    pdl_wait();
     int b_;
     const hessenberg_solve_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
     hessenberg_solve_kernel_impl(b_, q_.nb_, q_.Hm, q_.ldh, q_.sv, q_.k, q_.y);
@@ -351,7 +362,7 @@ void hessenberg_solve_kernel_go(unsigned grid_, unsigned block_, size_t smem_, c
         batch_record(r_, reinterpret_cast<const void *>(&hessenberg_solve_kernel_multi), q_, grid_, block_, smem_);
         return;
     }
-    hessenberg_solve_kernel<<<grid_, block_, smem_, s_>>>(Hm, ldh, sv, k, y);
+    pdl_launch(kPdlFamily, &hessenberg_solve_kernel, grid_, block_, smem_, s_, Hm, ldh, sv, k, y);
 }
 
 
@@ -362,6 +373,7 @@ __device__ __forceinline__ void fill_kernel_impl(int bid_, int nb_, T *x, T v, s
 }
 template <typename T>
 __global__ void fill_kernel(T *x, T v, size_t n) {
+    pdl_wait();
     fill_kernel_impl<T>(blockIdx.x, gridDim.x, x, v, n);
 }
 template <typename T>
@@ -373,6 +385,7 @@ struct fill_kernel_args {
 };
 template <typename T>
 __global__ void fill_kernel_multi(const __grid_constant__ MultiP<fill_kernel_args<T>> M) {
+    pdl_wait();
     int b_;
     const fill_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     fill_kernel_impl<T>(b_, q_.nb_, q_.x, q_.v, q_.n);
@@ -389,7 +402,7 @@ void fill_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t 
         batch_record(r_, reinterpret_cast<const void *>(&fill_kernel_multi<T>), q_, grid_, block_, smem_);
         return;
     }
-    fill_kernel<T><<<grid_, block_, smem_, s_>>>(x, v, n);
+    pdl_launch(kPdlFamily, &fill_kernel<T>, grid_, block_, smem_, s_, x, v, n);
 }
 
 
@@ -401,6 +414,7 @@ __device__ __forceinline__ void d2f_scaled_kernel_impl(int bid_, int nb_, const 
     if (idx < n) y[idx] = float(x[idx] * inv);
 }
 __global__ void d2f_scaled_kernel(const double *x, float *y, const double *scale, size_t n) {
+    pdl_wait();
     d2f_scaled_kernel_impl(blockIdx.x, gridDim.x, x, y, scale, n);
 }
 struct d2f_scaled_kernel_args {
@@ -411,6 +425,7 @@ struct d2f_scaled_kernel_args {
     size_t n;
 };
 __global__ void d2f_scaled_kernel_multi(const __grid_constant__ MultiP<d2f_scaled_kernel_args> M) {
+    pdl_wait();
     int b_;
     const d2f_scaled_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
     d2f_scaled_kernel_impl(b_, q_.nb_, q_.x, q_.y, q_.scale, q_.n);
@@ -428,7 +443,7 @@ void d2f_scaled_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         batch_record(r_, reinterpret_cast<const void *>(&d2f_scaled_kernel_multi), q_, grid_, block_, smem_);
         return;
     }
-    d2f_scaled_kernel<<<grid_, block_, smem_, s_>>>(x, y, scale, n);
+    pdl_launch(kPdlFamily, &d2f_scaled_kernel, grid_, block_, smem_, s_, x, y, scale, n);
 }
 
 
@@ -657,6 +672,7 @@ __global__ void __launch_bounds__(256) gs_update_norm_givens_kernel(const T *V, 
                                                                     double *sn, double *sv, int j,
                                                                     const double *bnorm, ReadBack *rb,
                                                                     ReadBack *host_rb) {
+    pdl_wait();
     gs_update_norm_givens_kernel_impl<T>(blockIdx.x, gridDim.x, V, ld, k, w, n, h1, h2, partial, counter, nrm2, Hm,
         ldh, cs, sn, sv, j, bnorm, rb, host_rb);
 }
@@ -685,6 +701,7 @@ struct gs_update_norm_givens_kernel_args {
 };
 template <typename T>
 __global__ void __launch_bounds__(256) gs_update_norm_givens_kernel_multi(const __grid_constant__ MultiP<gs_update_norm_givens_kernel_args<T>> M) {
+    pdl_wait();
     int b_;
     const gs_update_norm_givens_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     gs_update_norm_givens_kernel_impl<T>(b_, q_.nb_, q_.V, q_.ld, q_.k, q_.w, q_.n, q_.h1, q_.h2, q_.partial,
@@ -722,7 +739,7 @@ void gs_update_norm_givens_kernel_go(unsigned grid_, unsigned block_, size_t sme
         batch_record(r_, reinterpret_cast<const void *>(&gs_update_norm_givens_kernel_multi<T>), q_, grid_, block_, smem_);
         return;
     }
-    gs_update_norm_givens_kernel<T><<<grid_, block_, smem_, s_>>>(V, ld, k, w, n, h1, h2, partial, counter, nrm2, Hm,
+    pdl_launch(kPdlFamily, &gs_update_norm_givens_kernel<T>, grid_, block_, smem_, s_, V, ld, k, w, n, h1, h2, partial, counter, nrm2, Hm,
         ldh, cs, sn, sv, j, bnorm, rb, host_rb);
 }
 
@@ -740,6 +757,7 @@ __device__ __forceinline__ void gs_scale_kernel_impl(int bid_, int nb_, const T 
 }
 template <typename T>
 __global__ void gs_scale_kernel(const T *w, T *v, size_t n, const ReadBack *rb) {
+    pdl_wait();
     gs_scale_kernel_impl<T>(blockIdx.x, gridDim.x, w, v, n, rb);
 }
 template <typename T>
@@ -752,6 +770,7 @@ struct gs_scale_kernel_args {
 };
 template <typename T>
 __global__ void gs_scale_kernel_multi(const __grid_constant__ MultiP<gs_scale_kernel_args<T>> M) {
+    pdl_wait();
     int b_;
     const gs_scale_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     gs_scale_kernel_impl<T>(b_, q_.nb_, q_.w, q_.v, q_.n, q_.rb);
@@ -770,7 +789,7 @@ void gs_scale_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStrea
         batch_record(r_, reinterpret_cast<const void *>(&gs_scale_kernel_multi<T>), q_, grid_, block_, smem_);
         return;
     }
-    gs_scale_kernel<T><<<grid_, block_, smem_, s_>>>(w, v, n, rb);
+    pdl_launch(kPdlFamily, &gs_scale_kernel<T>, grid_, block_, smem_, s_, w, v, n, rb);
 }
 
 

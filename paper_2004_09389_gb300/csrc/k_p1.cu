@@ -12,6 +12,9 @@
 
 namespace hdg {
 
+// launch family of this file for pdl_launch (P1 kernels)
+constexpr unsigned kPdlFamily = 2;
+
 namespace {
 
 inline unsigned blocks(size_t n, int bs) { return unsigned((n + bs - 1) / bs); }
@@ -65,6 +68,7 @@ template <typename T>
 __global__ void jacobi_kernel(int n, int W, const int32_t *__restrict__ col, const T *__restrict__ A,
                               const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x,
                               T *__restrict__ xout, T omega, int first) {
+    pdl_wait();
     jacobi_kernel_impl<T>(blockIdx.x, gridDim.x, n, W, col, A, dinv, b, x, xout, omega, first);
 }
 template <typename T>
@@ -83,6 +87,7 @@ struct jacobi_kernel_args {
 };
 template <typename T>
 __global__ void jacobi_kernel_multi(const __grid_constant__ MultiP<jacobi_kernel_args<T>> M) {
+    pdl_wait();
     int b_;
     const jacobi_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     jacobi_kernel_impl<T>(b_, q_.nb_, q_.n, q_.W, q_.col, q_.A, q_.dinv, q_.b, q_.x, q_.xout, q_.omega, q_.first);
@@ -108,7 +113,7 @@ void jacobi_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_
         batch_record(r_, reinterpret_cast<const void *>(&jacobi_kernel_multi<T>), q_, grid_, block_, smem_);
         return;
     }
-    jacobi_kernel<T><<<grid_, block_, smem_, s_>>>(n, W, col, A, dinv, b, x, xout, omega, first);
+    pdl_launch(kPdlFamily, &jacobi_kernel<T>, grid_, block_, smem_, s_, n, W, col, A, dinv, b, x, xout, omega, first);
 }
 
 
@@ -123,6 +128,7 @@ __device__ __forceinline__ void prolong_add_kernel_impl(int bid_, int nb_, int n
 template <typename T>
 __global__ void prolong_add_kernel(int nf, const int32_t *__restrict__ parent, const T *__restrict__ ec,
                                    T *__restrict__ xf) {
+    pdl_wait();
     prolong_add_kernel_impl<T>(blockIdx.x, gridDim.x, nf, parent, ec, xf);
 }
 template <typename T>
@@ -135,6 +141,7 @@ struct prolong_add_kernel_args {
 };
 template <typename T>
 __global__ void prolong_add_kernel_multi(const __grid_constant__ MultiP<prolong_add_kernel_args<T>> M) {
+    pdl_wait();
     int b_;
     const prolong_add_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     prolong_add_kernel_impl<T>(b_, q_.nb_, q_.nf, q_.parent, q_.ec, q_.xf);
@@ -153,7 +160,7 @@ void prolong_add_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaSt
         batch_record(r_, reinterpret_cast<const void *>(&prolong_add_kernel_multi<T>), q_, grid_, block_, smem_);
         return;
     }
-    prolong_add_kernel<T><<<grid_, block_, smem_, s_>>>(nf, parent, ec, xf);
+    pdl_launch(kPdlFamily, &prolong_add_kernel<T>, grid_, block_, smem_, s_, nf, parent, ec, xf);
 }
 
 
@@ -195,6 +202,7 @@ __global__ void __launch_bounds__(256) down_kernel(int nc, const int32_t *__rest
                                                    const T *__restrict__ bf, const T *__restrict__ xf,
                                                    const T *__restrict__ dinv_c, T omega, T *__restrict__ bc,
                                                    T *__restrict__ xc) {
+    pdl_wait();
     down_kernel_impl<T>(blockIdx.x, gridDim.x, nc, cp, ci, cw, nf, W, col, A, bf, xf, dinv_c, omega, bc, xc);
 }
 template <typename T>
@@ -217,6 +225,7 @@ struct down_kernel_args {
 };
 template <typename T>
 __global__ void __launch_bounds__(256) down_kernel_multi(const __grid_constant__ MultiP<down_kernel_args<T>> M) {
+    pdl_wait();
     int b_;
     const down_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     down_kernel_impl<T>(b_, q_.nb_, q_.nc, q_.cp, q_.ci, q_.cw, q_.nf, q_.W, q_.col, q_.A, q_.bf, q_.xf, q_.dinv_c,
@@ -247,7 +256,7 @@ void down_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t 
         batch_record(r_, reinterpret_cast<const void *>(&down_kernel_multi<T>), q_, grid_, block_, smem_);
         return;
     }
-    down_kernel<T><<<grid_, block_, smem_, s_>>>(nc, cp, ci, cw, nf, W, col, A, bf, xf, dinv_c, omega, bc, xc);
+    pdl_launch(kPdlFamily, &down_kernel<T>, grid_, block_, smem_, s_, nc, cp, ci, cw, nf, W, col, A, bf, xf, dinv_c, omega, bc, xc);
 }
 
 
@@ -286,6 +295,7 @@ __global__ void up_kernel(int nf, int W, const int32_t *__restrict__ col, const 
                           const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x,
                           const int32_t *__restrict__ parent, const T *__restrict__ ec, T *__restrict__ xout,
                           T omega) {
+    pdl_wait();
     up_kernel_impl<T>(blockIdx.x, gridDim.x, nf, W, col, A, dinv, b, x, parent, ec, xout, omega);
 }
 template <typename T>
@@ -305,6 +315,7 @@ struct up_kernel_args {
 };
 template <typename T>
 __global__ void up_kernel_multi(const __grid_constant__ MultiP<up_kernel_args<T>> M) {
+    pdl_wait();
     int b_;
     const up_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     up_kernel_impl<T>(b_, q_.nb_, q_.nf, q_.W, q_.col, q_.A, q_.dinv, q_.b, q_.x, q_.parent, q_.ec, q_.xout,
@@ -332,7 +343,7 @@ void up_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_
         batch_record(r_, reinterpret_cast<const void *>(&up_kernel_multi<T>), q_, grid_, block_, smem_);
         return;
     }
-    up_kernel<T><<<grid_, block_, smem_, s_>>>(nf, W, col, A, dinv, b, x, parent, ec, xout, omega);
+    pdl_launch(kPdlFamily, &up_kernel<T>, grid_, block_, smem_, s_, nf, W, col, A, dinv, b, x, parent, ec, xout, omega);
 }
 
 
@@ -469,6 +480,7 @@ __global__ void __launch_bounds__(kPatchThreads<T>, 1) down_fused_kernel(const i
                                                                          const T *__restrict__ dinv_c, T omega,
                                                                          T *__restrict__ bc, T *__restrict__ xc,
                                                                          int max_f1) {
+    pdl_wait();
     down_fused_kernel_impl<T, WQ>(blockIdx.x, gridDim.x, f_ptr, f_n0, f_ids, f0_base, lcol, fcol, c_ptr, c_ids,
         cc_ptr, cc_slot, cc_w, A, dinv, b, x, xout, dinv_c, omega, bc, xc, max_f1);
 }
@@ -499,6 +511,7 @@ struct down_fused_kernel_args {
 };
 template <typename T, int WQ>
 __global__ void __launch_bounds__(kPatchThreads<T>, 1) down_fused_kernel_multi(const __grid_constant__ MultiP<down_fused_kernel_args<T, WQ>> M) {
+    pdl_wait();
     int b_;
     const down_fused_kernel_args<T, WQ> &q_ = M.a[merge_find(M.start, M.n, b_)];
     down_fused_kernel_impl<T, WQ>(b_, q_.nb_, q_.f_ptr, q_.f_n0, q_.f_ids, q_.f0_base, q_.lcol, q_.fcol, q_.c_ptr,
@@ -539,7 +552,7 @@ void down_fused_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         batch_record(r_, reinterpret_cast<const void *>(&down_fused_kernel_multi<T, WQ>), q_, grid_, block_, smem_);
         return;
     }
-    down_fused_kernel<T, WQ><<<grid_, block_, smem_, s_>>>(f_ptr, f_n0, f_ids, f0_base, lcol, fcol, c_ptr, c_ids,
+    pdl_launch(kPdlFamily, &down_fused_kernel<T, WQ>, grid_, block_, smem_, s_, f_ptr, f_n0, f_ids, f0_base, lcol, fcol, c_ptr, c_ids,
         cc_ptr, cc_slot, cc_w, A, dinv, b, x, xout, dinv_c, omega, bc, xc, max_f1);
 }
 
@@ -634,6 +647,7 @@ __global__ void __launch_bounds__(kPatchThreads<T>, 1) up_fused_kernel(const int
                                                                        const T *__restrict__ x,
                                                                        const T *__restrict__ ec, T *__restrict__ xout,
                                                                        T omega) {
+    pdl_wait();
     up_fused_kernel_impl<T, WQ>(blockIdx.x, gridDim.x, g_ptr, g_nown, g_ids, g0_base, glcol, gcol, gpar, grow_par, A,
         dinv, b, x, ec, xout, omega);
 }
@@ -658,6 +672,7 @@ struct up_fused_kernel_args {
 };
 template <typename T, int WQ>
 __global__ void __launch_bounds__(kPatchThreads<T>, 1) up_fused_kernel_multi(const __grid_constant__ MultiP<up_fused_kernel_args<T, WQ>> M) {
+    pdl_wait();
     int b_;
     const up_fused_kernel_args<T, WQ> &q_ = M.a[merge_find(M.start, M.n, b_)];
     up_fused_kernel_impl<T, WQ>(b_, q_.nb_, q_.g_ptr, q_.g_nown, q_.g_ids, q_.g0_base, q_.glcol, q_.gcol, q_.gpar,
@@ -690,7 +705,7 @@ void up_fused_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStrea
         batch_record(r_, reinterpret_cast<const void *>(&up_fused_kernel_multi<T, WQ>), q_, grid_, block_, smem_);
         return;
     }
-    up_fused_kernel<T, WQ><<<grid_, block_, smem_, s_>>>(g_ptr, g_nown, g_ids, g0_base, glcol, gcol, gpar, grow_par,
+    pdl_launch(kPdlFamily, &up_fused_kernel<T, WQ>, grid_, block_, smem_, s_, g_ptr, g_nown, g_ids, g0_base, glcol, gcol, gpar, grow_par,
         A, dinv, b, x, ec, xout, omega);
 }
 
@@ -863,6 +878,7 @@ __device__ __forceinline__ void tail_kernel_impl(int bid_, int nb_, TailArgs a) 
 }
 template <typename T>
 __global__ void __launch_bounds__(1024, 1) tail_kernel(TailArgs a) {
+    pdl_wait();
     tail_kernel_impl<T>(blockIdx.x, gridDim.x, a);
 }
 template <typename T>
@@ -872,6 +888,7 @@ struct tail_kernel_args {
 };
 template <typename T>
 __global__ void __launch_bounds__(1024, 1) tail_kernel_multi(const __grid_constant__ MultiP<tail_kernel_args<T>> M) {
+    pdl_wait();
     int b_;
     const tail_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     tail_kernel_impl<T>(b_, q_.nb_, q_.a);
@@ -886,7 +903,7 @@ void tail_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t 
         batch_record(r_, reinterpret_cast<const void *>(&tail_kernel_multi<T>), q_, grid_, block_, smem_);
         return;
     }
-    tail_kernel<T><<<grid_, block_, smem_, s_>>>(a);
+    pdl_launch(kPdlFamily, &tail_kernel<T>, grid_, block_, smem_, s_, a);
 }
 
 

@@ -19,6 +19,9 @@
 
 namespace hdg {
 
+// launch family of this file for pdl_launch (facet-row kernels)
+constexpr unsigned kPdlFamily = 1;
+
 namespace {
 
 template <typename TO> __device__ __forceinline__ TO convert_to(double v);
@@ -202,6 +205,7 @@ __global__ void __launch_bounds__(256, 4) apply_dots_kernel(int NF, const ST *__
                                                             int k, double *__restrict__ partial,
                                                             unsigned int *__restrict__ counter,
                                                             double *__restrict__ h) {
+    pdl_wait();
     apply_dots_kernel_impl<P, T, ST>(blockIdx.x, gridDim.x, NF, Sval, nbr, x, y, V, ld, k, partial, counter, h);
 }
 template <int P, typename T, typename ST>
@@ -221,6 +225,7 @@ struct apply_dots_kernel_args {
 };
 template <int P, typename T, typename ST>
 __global__ void __launch_bounds__(256, 4) apply_dots_kernel_multi(const __grid_constant__ MultiP<apply_dots_kernel_args<P, T, ST>> M) {
+    pdl_wait();
     int b_;
     const apply_dots_kernel_args<P, T, ST> &q_ = M.a[merge_find(M.start, M.n, b_)];
     apply_dots_kernel_impl<P, T, ST>(b_, q_.nb_, q_.NF, q_.Sval, q_.nbr, q_.x, q_.y, q_.V, q_.ld, q_.k, q_.partial,
@@ -248,7 +253,7 @@ void apply_dots_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         batch_record(r_, reinterpret_cast<const void *>(&apply_dots_kernel_multi<P, T, ST>), q_, grid_, block_, smem_);
         return;
     }
-    apply_dots_kernel<P, T, ST><<<grid_, block_, smem_, s_>>>(NF, Sval, nbr, x, y, V, ld, k, partial, counter, h);
+    pdl_launch(kPdlFamily, &apply_dots_kernel<P, T, ST>, grid_, block_, smem_, s_, NF, Sval, nbr, x, y, V, ld, k, partial, counter, h);
 }
 
 
@@ -270,6 +275,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) residual_kernel(int 
                                                                             const T *__restrict__ b,
                                                                             const T *__restrict__ x,
                                                                             T *__restrict__ res) {
+    pdl_wait();
     residual_kernel_impl<P, T, ST>(blockIdx.x, gridDim.x, NF, Sval, nbr, b, x, res);
 }
 template <int P, typename T, typename ST>
@@ -284,6 +290,7 @@ struct residual_kernel_args {
 };
 template <int P, typename T, typename ST>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value) residual_kernel_multi(const __grid_constant__ MultiP<residual_kernel_args<P, T, ST>> M) {
+    pdl_wait();
     int b_;
     const residual_kernel_args<P, T, ST> &q_ = M.a[merge_find(M.start, M.n, b_)];
     residual_kernel_impl<P, T, ST>(b_, q_.nb_, q_.NF, q_.Sval, q_.nbr, q_.b, q_.x, q_.res);
@@ -304,7 +311,7 @@ void residual_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStrea
         batch_record(r_, reinterpret_cast<const void *>(&residual_kernel_multi<P, T, ST>), q_, grid_, block_, smem_);
         return;
     }
-    residual_kernel<P, T, ST><<<grid_, block_, smem_, s_>>>(NF, Sval, nbr, b, x, res);
+    pdl_launch(kPdlFamily, &residual_kernel<P, T, ST>, grid_, block_, smem_, s_, NF, Sval, nbr, b, x, res);
 }
 
 
@@ -344,6 +351,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_kernel(int NF
                                                                           const T *__restrict__ b,
                                                                           const T *__restrict__ x, T *xout, T omega,
                                                                           T beta, const T *xprev) {
+    pdl_wait();
     smooth_kernel_impl<P, T, ST, CHEB>(blockIdx.x, gridDim.x, NF, Sval, Dinv, nbr, b, x, xout, omega, beta, xprev);
 }
 template <int P, typename T, typename ST, bool CHEB = false>
@@ -362,6 +370,7 @@ struct smooth_kernel_args {
 };
 template <int P, typename T, typename ST, bool CHEB = false>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_kernel_multi(const __grid_constant__ MultiP<smooth_kernel_args<P, T, ST, CHEB>> M) {
+    pdl_wait();
     int b_;
     const smooth_kernel_args<P, T, ST, CHEB> &q_ = M.a[merge_find(M.start, M.n, b_)];
     smooth_kernel_impl<P, T, ST, CHEB>(b_, q_.nb_, q_.NF, q_.Sval, q_.Dinv, q_.nbr, q_.b, q_.x, q_.xout, q_.omega,
@@ -388,7 +397,7 @@ void smooth_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_
         batch_record(r_, reinterpret_cast<const void *>(&smooth_kernel_multi<P, T, ST, CHEB>), q_, grid_, block_, smem_);
         return;
     }
-    smooth_kernel<P, T, ST, CHEB><<<grid_, block_, smem_, s_>>>(NF, Sval, Dinv, nbr, b, x, xout, omega, beta, xprev);
+    pdl_launch(kPdlFamily, &smooth_kernel<P, T, ST, CHEB>, grid_, block_, smem_, s_, NF, Sval, Dinv, nbr, b, x, xout, omega, beta, xprev);
 }
 
 
@@ -443,6 +452,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_prolong_kerne
                                                                                   const T *__restrict__ x,
                                                                                   T *__restrict__ xout, T omega,
                                                                                   T *__restrict__ x0out) {
+    pdl_wait();
     smooth_prolong_kernel_impl<P, T, ST, X0>(blockIdx.x, gridDim.x, NF, Sval, Dinv, nbr, fverts, ec, b, x, xout,
         omega, x0out);
 }
@@ -463,6 +473,7 @@ struct smooth_prolong_kernel_args {
 };
 template <int P, typename T, typename ST, bool X0 = false>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value) smooth_prolong_kernel_multi(const __grid_constant__ MultiP<smooth_prolong_kernel_args<P, T, ST, X0>> M) {
+    pdl_wait();
     int b_;
     const smooth_prolong_kernel_args<P, T, ST, X0> &q_ = M.a[merge_find(M.start, M.n, b_)];
     smooth_prolong_kernel_impl<P, T, ST, X0>(b_, q_.nb_, q_.NF, q_.Sval, q_.Dinv, q_.nbr, q_.fverts, q_.ec, q_.b,
@@ -490,7 +501,7 @@ void smooth_prolong_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cud
         batch_record(r_, reinterpret_cast<const void *>(&smooth_prolong_kernel_multi<P, T, ST, X0>), q_, grid_, block_, smem_);
         return;
     }
-    smooth_prolong_kernel<P, T, ST, X0><<<grid_, block_, smem_, s_>>>(NF, Sval, Dinv, nbr, fverts, ec, b, x, xout,
+    pdl_launch(kPdlFamily, &smooth_prolong_kernel<P, T, ST, X0>, grid_, block_, smem_, s_, NF, Sval, Dinv, nbr, fverts, ec, b, x, xout,
         omega, x0out);
 }
 
@@ -532,6 +543,7 @@ template <int P, typename T>
 __global__ void smooth_first_kernel(int NF, const T *__restrict__ Dinv, const T *__restrict__ b, T *__restrict__ xout,
                                     T omega, const T *__restrict__ w, const double *__restrict__ hnext,
                                     T *__restrict__ bout) {
+    pdl_wait();
     smooth_first_kernel_impl<P, T>(blockIdx.x, gridDim.x, NF, Dinv, b, xout, omega, w, hnext, bout);
 }
 template <int P, typename T>
@@ -548,6 +560,7 @@ struct smooth_first_kernel_args {
 };
 template <int P, typename T>
 __global__ void smooth_first_kernel_multi(const __grid_constant__ MultiP<smooth_first_kernel_args<P, T>> M) {
+    pdl_wait();
     int b_;
     const smooth_first_kernel_args<P, T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     smooth_first_kernel_impl<P, T>(b_, q_.nb_, q_.NF, q_.Dinv, q_.b, q_.xout, q_.omega, q_.w, q_.hnext, q_.bout);
@@ -570,7 +583,7 @@ void smooth_first_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaS
         batch_record(r_, reinterpret_cast<const void *>(&smooth_first_kernel_multi<P, T>), q_, grid_, block_, smem_);
         return;
     }
-    smooth_first_kernel<P, T><<<grid_, block_, smem_, s_>>>(NF, Dinv, b, xout, omega, w, hnext, bout);
+    pdl_launch(kPdlFamily, &smooth_first_kernel<P, T>, grid_, block_, smem_, s_, NF, Dinv, b, xout, omega, w, hnext, bout);
 }
 
 
@@ -607,6 +620,7 @@ __device__ __forceinline__ void to_external_kernel_impl(int bid_, int nb_, int N
     ext[i] = in[r * NF + e];
 }
 __global__ void to_external_kernel(int NF, int PP, const double *in, double *ext) {
+    pdl_wait();
     to_external_kernel_impl(blockIdx.x, gridDim.x, NF, PP, in, ext);
 }
 struct to_external_kernel_args {
@@ -617,6 +631,7 @@ struct to_external_kernel_args {
     double *ext;
 };
 __global__ void to_external_kernel_multi(const __grid_constant__ MultiP<to_external_kernel_args> M) {
+    pdl_wait();
     int b_;
     const to_external_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
     to_external_kernel_impl(b_, q_.nb_, q_.NF, q_.PP, q_.in, q_.ext);
@@ -634,7 +649,7 @@ void to_external_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaSt
         batch_record(r_, reinterpret_cast<const void *>(&to_external_kernel_multi), q_, grid_, block_, smem_);
         return;
     }
-    to_external_kernel<<<grid_, block_, smem_, s_>>>(NF, PP, in, ext);
+    pdl_launch(kPdlFamily, &to_external_kernel, grid_, block_, smem_, s_, NF, PP, in, ext);
 }
 
 
@@ -685,6 +700,7 @@ template <int P>
 __global__ void rhs_gather_kernel(int N, int NF, const double *__restrict__ ycell, const int32_t *__restrict__ fcell,
                                   const int32_t *__restrict__ fedge, const int32_t *__restrict__ flip,
                                   double *__restrict__ g) {
+    pdl_wait();
     rhs_gather_kernel_impl<P>(blockIdx.x, gridDim.x, N, NF, ycell, fcell, fedge, flip, g);
 }
 template <int P>
@@ -700,6 +716,7 @@ struct rhs_gather_kernel_args {
 };
 template <int P>
 __global__ void rhs_gather_kernel_multi(const __grid_constant__ MultiP<rhs_gather_kernel_args<P>> M) {
+    pdl_wait();
     int b_;
     const rhs_gather_kernel_args<P> &q_ = M.a[merge_find(M.start, M.n, b_)];
     rhs_gather_kernel_impl<P>(b_, q_.nb_, q_.N, q_.NF, q_.ycell, q_.fcell, q_.fedge, q_.flip, q_.g);
@@ -722,7 +739,7 @@ void rhs_gather_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         batch_record(r_, reinterpret_cast<const void *>(&rhs_gather_kernel_multi<P>), q_, grid_, block_, smem_);
         return;
     }
-    rhs_gather_kernel<P><<<grid_, block_, smem_, s_>>>(N, NF, ycell, fcell, fedge, flip, g);
+    pdl_launch(kPdlFamily, &rhs_gather_kernel<P>, grid_, block_, smem_, s_, N, NF, ycell, fcell, fedge, flip, g);
 }
 
 
@@ -778,6 +795,7 @@ template <int P, typename T>
 __global__ void restrict_kernel(int nv, int NF, const int32_t *__restrict__ v2f_ptr, const int32_t *__restrict__ v2f,
                                 const T *__restrict__ r, T *__restrict__ rc, const T *__restrict__ dinv0, T omega,
                                 T *__restrict__ x0) {
+    pdl_wait();
     restrict_kernel_impl<P, T>(blockIdx.x, gridDim.x, nv, NF, v2f_ptr, v2f, r, rc, dinv0, omega, x0);
 }
 template <int P, typename T>
@@ -795,6 +813,7 @@ struct restrict_kernel_args {
 };
 template <int P, typename T>
 __global__ void restrict_kernel_multi(const __grid_constant__ MultiP<restrict_kernel_args<P, T>> M) {
+    pdl_wait();
     int b_;
     const restrict_kernel_args<P, T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     restrict_kernel_impl<P, T>(b_, q_.nb_, q_.nv, q_.NF, q_.v2f_ptr, q_.v2f, q_.r, q_.rc, q_.dinv0, q_.omega, q_.x0);
@@ -819,7 +838,7 @@ void restrict_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStrea
         batch_record(r_, reinterpret_cast<const void *>(&restrict_kernel_multi<P, T>), q_, grid_, block_, smem_);
         return;
     }
-    restrict_kernel<P, T><<<grid_, block_, smem_, s_>>>(nv, NF, v2f_ptr, v2f, r, rc, dinv0, omega, x0);
+    pdl_launch(kPdlFamily, &restrict_kernel<P, T>, grid_, block_, smem_, s_, nv, NF, v2f_ptr, v2f, r, rc, dinv0, omega, x0);
 }
 
 
