@@ -35,11 +35,27 @@ SIDE, NGRID, G, DEPTH, F0 = 5.12e6, 256, 9.81, 1.0e3, 1.0e-4
 SAMPLE_N = 64            # oracle sample: 64 x 64 x 2 = 8,192 triangles of the same workload
 RADIUS, OMEGA = 6.371e6, 7.292e-5
 SPHERE_R, SAMPLE_R = 6, 4   # sphere workload: r = 6 (81,920 triangles); oracle sample r = 4 (5,120)
+# P1 hierarchies: flat down to the 4 x 4 periodic grid (16 vertices), sphere
+# down to r - 5 (at least r = 1, 42 vertices).  Ending them at about a thousand
+# vertices (solved exactly by the multi-CTA dense product) leaves the oracle's
+# iteration counts unchanged, but measured 1 % slower on the mixed-precision
+# flat workload and costs an 18 ms larger inverse at every condensation.
+FLAT_COARSEST, SPHERE_COARSEST_DEPTH = 4, 5
+
+
+def flat_hierarchy(n: int):
+    import hdg_inputs as I
+    return I.periodic_square_hierarchy(n, side=SIDE * n / NGRID, n_coarsest=FLAT_COARSEST)
+
+
+def sphere_hierarchy(r: int):
+    import hdg_inputs as I
+    return I.sphere_hierarchy(r, RADIUS, r_coarsest=max(r - SPHERE_COARSEST_DEPTH, 1))
 
 
 def workload(n: int, p: int, courant: float, seed: int):
     import hdg_inputs as I
-    mesh = I.periodic_square_hierarchy(n, side=SIDE * n / NGRID, n_coarsest=4)
+    mesh = flat_hierarchy(n)
     c = math.sqrt(G * DEPTH)
     tau = courant * mesh.h / c
     f = I.coriolis_flat(mesh, F0)
@@ -59,7 +75,7 @@ def sphere_workload(r: int, p: int, courant: float, seed: int):
     random spherical-harmonic fields up to degree 64 with l^-3 variance."""
     import numpy as np
     import hdg_inputs as I
-    mesh = I.sphere_hierarchy(r, RADIUS, r_coarsest=max(r - 5, 1))
+    mesh = sphere_hierarchy(r)
     H = float(np.random.default_rng(seed).uniform(5e3, 1e4))
     tau = courant * mesh.h / math.sqrt(G * H)
     f = I.coriolis_sphere(mesh, OMEGA)
@@ -72,7 +88,7 @@ def workload_label(kind: str, p: int, courant: float, seed: int) -> str:
     if kind == "sphere":
         import numpy as np
         import hdg_inputs as I
-        mesh = I.sphere_hierarchy(SPHERE_R, RADIUS, r_coarsest=max(SPHERE_R - 5, 1))
+        mesh = sphere_hierarchy(SPHERE_R)
         H = float(np.random.default_rng(seed).uniform(5e3, 1e4))
         tau = courant * mesh.h / math.sqrt(G * H)
         fmax = float(np.abs(I.coriolis_sphere(mesh, OMEGA)).max())
@@ -614,9 +630,9 @@ def batch_workload(n_problems: int, seed: int):
         key = (kind, size)
         if key not in meshes:
             if kind == "flat":
-                meshes[key] = I.periodic_square_hierarchy(size, side=SIDE * size / NGRID, n_coarsest=4)
+                meshes[key] = flat_hierarchy(size)
             else:
-                meshes[key] = I.sphere_hierarchy(size, radius, r_coarsest=max(size - 5, 1))
+                meshes[key] = sphere_hierarchy(size)
         mesh = meshes[key]
         if (key, p) not in fields:
             if kind == "flat":
@@ -657,7 +673,7 @@ def sequence_main(args):
     build.build()
     dev = torch.device("cuda", 0)
     r, p, steps = 7, 2, 50
-    mesh = I.sphere_hierarchy(r, RADIUS, r_coarsest=max(r - 5, 1))
+    mesh = sphere_hierarchy(r)
     H = float(np.random.default_rng(args.seed).uniform(5e3, 1e4))
     tau = args.courant * mesh.h / math.sqrt(G * H)
     f = I.coriolis_sphere(mesh, OMEGA)
@@ -677,7 +693,7 @@ def sequence_main(args):
     # training on the r = 5 sphere (same p, physics and Courant number): the
     # network sees RMS-normalised facet patches, so its parameters carry over
     rt = 5
-    mesh_t = I.sphere_hierarchy(rt, RADIUS, r_coarsest=1)
+    mesh_t = sphere_hierarchy(rt)
     tau_t = args.courant * mesh_t.h / math.sqrt(G * H)
     st = HDGSolver(mesh_t, p, tau_t, G, H, f_vertex=I.coriolis_sphere(mesh_t, OMEGA), precision=HDG_MIXED_FP32,
                    rtol=args.rtol)
@@ -760,7 +776,7 @@ def imex_main(args):
     build.build()
     dev = torch.device("cuda", 0)
     r, p = SPHERE_R, args.p
-    mesh = I.sphere_hierarchy(r, RADIUS, r_coarsest=max(r - 5, 1))
+    mesh = sphere_hierarchy(r)
     H = float(np.random.default_rng(args.seed).uniform(5e3, 1e4))
     dt = args.courant * mesh.h / math.sqrt(G * H)
     f = I.coriolis_sphere(mesh, OMEGA)

@@ -273,10 +273,13 @@ HDG_API int hdg_solve_batch_dev(hdg_handle *const *hs, int n, const double *cons
  * last waves (totals since creation).  hdg_batch_destroy(NULL) is a no-op;
  * destroy the batch before its handles.
  *
- * The problems are dealt into groups, each with its own stream, waves and
- * graphs: while one group's wave runs, the host prepares another's.
- * HDG_BATCH_GROUPS = G (1..64, default 4) deals them, largest first, round
- * robin into G groups; 0 groups them by degree. */
+ * The problems are split into groups, each with its own stream, waves and
+ * graphs: while one group's wave runs, the host prepares another's, and the
+ * groups' launches fill each other's gaps on the GPU.  HDG_BATCH_GROUPS = G
+ * (1..64, default 4) sorts the problems by size (trace unknowns) and cuts
+ * them into G contiguous size classes of about equal total size, so that a
+ * merged launch covers problems of similar size (HDG_BATCH_DEAL=rr deals them
+ * round robin instead); 0 groups them by degree. */
 typedef struct hdg_batch hdg_batch;
 HDG_API int hdg_batch_create(hdg_handle *const *hs, int n, hdg_batch **out);
 HDG_API int hdg_batch_solve_dev(hdg_batch *b, const double *const *r_u, const double *const *r_h,

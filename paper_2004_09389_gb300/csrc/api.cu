@@ -372,7 +372,14 @@ cudaError_t p1_cycle(hdg_handle *h, T **result) {
         }
         cur[l] = x; oth[l] = x2;
     }
-    {
+    if (nlev - ts == 1 && h->lev[ts].nv > kTailDenseMax) {
+        // the coarsest level alone, too large for one CTA's dense product: the
+        // exact solve as a product with its FP64 inverse over many CTAs
+        if ((e = KL(HDG_PROF_P1, 1, launch_p1_coarse_dense<T>(h->d_coarse_inv, h->lev[ts].nv, levB<T>(h->lev[ts]),
+                                                               levX<T>(h->lev[ts]), s))) != cudaSuccess)
+            return e;
+        res[ts] = levX<T>(h->lev[ts]);
+    } else {
         const TailImage &im = h->tail_img[sizeof(T) == 8 ? 0 : 1];
         if (im.ts != ts || !im.d) return cudaErrorInvalidValue;   // image not built for this tail start
         TailArgs a{};
@@ -1056,6 +1063,7 @@ void free_handle(hdg_handle *h) {
     dfree(h->d_Dinv); dfree(h->d_Sval32); dfree(h->d_Dinv32); dfree(h->d_Sval16); dfree(h->d_status); dfree(h->d_coarse_inv);
     dfree(h->tail_img[0].d); dfree(h->tail_img[1].d);
     dfree(h->d_coarse_work);
+    dfree(h->d_coarse_fac);
     for (auto &L : h->lev) {
         dfree(L.col); dfree(L.diag); dfree(L.elem); dfree(L.fK); dfree(L.contrib_ptr); dfree(L.contrib); dfree(L.A); dfree(L.dinv);
         dfree(L.A32); dfree(L.dinv32); dfree(L.parent); dfree(L.child_ptr); dfree(L.child_idx); dfree(L.child_w); dfree(L.child_w32);
@@ -1135,8 +1143,15 @@ int build_tail_image(hdg_handle *h, int pi) {
     }
     cudaStream_t s = h->stream;
     TRY(cudaMemcpyAsync(im.d, hdr.data(), sizeof(TailHdr) * n, cudaMemcpyHostToDevice, s));
-    for (const TailPiece &q : lay.pieces)
+    for (const TailPiece &q : lay.pieces) {
+        if (q.kind == kTailCol) continue;                  // packed together with the values
+        if (q.kind == kTailA) {
+            const DevLevel &L = h->lev[size_t(ts + q.level)];
+            TRY(launch_tail_pack(L.col, source(q), tsz, L.nv, L.width, im.d + hdr[size_t(q.level)].ocol, im.d + q.off, s));
+            continue;
+        }
         TRY(cudaMemcpyAsync(im.d + q.off, source(q), q.bytes, cudaMemcpyDeviceToDevice, s));
+    }
     TRY(cudaStreamSynchronize(s));                         // hdr is host memory on this stack
     if (im.ts != ts || im.img_bytes != img_bytes) {
         if (h->ws) drop_graphs(h);
@@ -1350,6 +1365,7 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     const size_t nc = h->lev.back().nv;
     TRY(dalloc(&h->d_coarse_inv, nc * nc));
     TRY(dalloc(&h->d_coarse_work, nc * nc));
+    TRY(dalloc(&h->d_coarse_fac, nc));
 
     h->ws = new Workspace();
     Workspace &W = *h->ws;
@@ -1836,7 +1852,8 @@ int hdg_condense(hdg_handle *h) {
             TRY(KL(HDG_PROF_CONDENSE, 2, launch_p1_assemble(h, L, tau, gH, h->prm.coarse_mode == 0 ? 1 : 0)));
     }
     const DevLevel &Lc = h->lev.back();
-    TRY(KL(HDG_PROF_CONDENSE, 2, launch_dense_inverse(h, Lc, h->d_coarse_work, h->d_coarse_inv, Lc.nv)));
+    TRY(KL(HDG_PROF_CONDENSE, Lc.nv <= 256 ? 2 : 2 + 2 * Lc.nv,
+           launch_dense_inverse(h, Lc, h->d_coarse_work, h->d_coarse_inv, Lc.nv)));
     if (h->prm.precision != HDG_FP64) {
         TRY(KL(HDG_PROF_CONDENSE, h->d_Sval16 ? 3 : 2, launch_repack(h)));
         for (auto &L : h->lev) {
@@ -2292,8 +2309,9 @@ int hdg_batch_create(hdg_handle *const *hs, int n, hdg_batch **out) {
         return e == cudaSuccess ? HDG_OK : fail(nullptr, HDG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
     };
     int rc;
-    // groups: HDG_BATCH_GROUPS = G >= 1 deals the problems, largest first (trace
-    // unknowns NT), round-robin into G groups; 0 groups them by degree p
+    // groups: HDG_BATCH_GROUPS = G >= 1 splits the problems, sorted by trace
+    // unknowns NT, into G contiguous size classes of about equal total NT (or,
+    // with HDG_BATCH_DEAL=rr, deals them round robin); 0 groups them by degree p
     int G = 4;
     if (const char *env = std::getenv("HDG_BATCH_GROUPS")) G = std::atoi(env);
     if (G < 0 || G > 64) return fail(nullptr, HDG_EINVAL, "HDG_BATCH_GROUPS must be 0..64");
@@ -2311,7 +2329,24 @@ int hdg_batch_create(hdg_handle *const *hs, int n, hdg_batch **out) {
         std::vector<int> order(static_cast<size_t>(n));
         for (int i = 0; i < n; ++i) order[size_t(i)] = i;
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hs[x]->NT > hs[y]->NT; });
-        for (int k = 0; k < n; ++k) b->group_of[size_t(order[size_t(k)])] = k % G;
+        const char *deal = std::getenv("HDG_BATCH_DEAL");
+        if (!(deal && std::strcmp(deal, "rr") == 0)) {
+            // contiguous size classes of about equal total trace unknowns, so that
+            // the problems merged into one launch are of similar size
+            double total = 0.0;
+            for (int i = 0; i < n; ++i) total += double(hs[i]->NT);
+            double acc = 0.0;
+            int g = 0;
+            for (int k = 0; k < n; ++k) {
+                const int i = order[size_t(k)];
+                b->group_of[size_t(i)] = g;
+                acc += double(hs[i]->NT);
+                if (g + 1 < G && acc >= total * double(g + 1) / G && n - k - 1 >= G - g - 1) ++g;
+            }
+            G = g + 1;
+        } else {
+            for (int k = 0; k < n; ++k) b->group_of[size_t(order[size_t(k)])] = k % G;
+        }
     }
     for (int g = 0; g < G; ++g) {
         std::unique_ptr<hdg_batch::Group> grp(new hdg_batch::Group);

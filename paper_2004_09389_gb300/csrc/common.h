@@ -290,6 +290,7 @@ size_t tail_smem_bytes(const std::vector<DevLevel> &lev, int first, size_t tsz);
 struct TailLevelSize {
     int nv, nnz, W, nci, nfin;
 };
+// (kTailA: ELL values slot-major; kTailCol: ELL columns as 16-bit indices)
 enum TailPieceKind : int { kTailA = 0, kTailD, kTailCol, kTailCw, kTailCp, kTailCi, kTailPar, kTailInv };
 // one array copied into the image: byte offset and (16-byte padded) size,
 // the tail level it belongs to and what it is
@@ -532,6 +533,7 @@ struct hdg_handle {
     double *d_coarse_inv = nullptr;   // dense inverse of the coarsest P1 operator
     hdg::TailImage tail_img[2];       // shared-memory images of the tail levels (FP64, FP32)
     double *d_coarse_work = nullptr;
+    double *d_coarse_fac = nullptr;   // row factors of one elimination step (coarsest levels above 256 vertices)
     hdg::Workspace *ws = nullptr;
     hdg::Prof prof;
     hdg::Learned lc;
@@ -639,6 +641,10 @@ cudaError_t launch_p1_assemble(hdg_handle *h, DevLevel &L, double tau, double gH
 // every P1 level operator as the Galerkin product of the trace operator (k_galerkin.cu)
 cudaError_t launch_p1_galerkin(hdg_handle *h);
 cudaError_t launch_dense_inverse(hdg_handle *h, const DevLevel &L, double *work, double *inv, int n);
+// a tail level's ELL arrays in the staged layout: values (tsz bytes each)
+// slot-major into A_dst, columns as 16-bit indices into col_dst
+cudaError_t launch_tail_pack(const int32_t *col, const void *A, size_t tsz, int nv, int W, void *col_dst, void *A_dst,
+                             cudaStream_t s);
 cudaError_t launch_to_f32(const double *x, float *y, size_t n, cudaStream_t s);
 
 // trace-space kernels (k_trace.cu); vectors in the internal layout [pp][NF]
@@ -692,6 +698,11 @@ cudaError_t launch_p1_up_fused(const DevLevel &fine, const DevLevel &coarse, con
                                const T *b_f, const T *x_f, const T *ec, T *xout, T omega, cudaStream_t s);
 template <typename T>
 cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s);
+// x = inv b on the coarsest level (n vertices, FP64 inverse) over many CTAs
+template <typename T>
+cudaError_t launch_p1_coarse_dense(const double *inv, int n, const T *b, T *x, cudaStream_t s);
+// coarsest levels above this size alone in the tail take the multi-CTA product
+constexpr int kTailDenseMax = 256;
 
 // Krylov kernels (k_krylov.cu)
 template <typename T>

@@ -368,6 +368,68 @@ __global__ void dense_inverse_kernel(int n, double *Aw, double *inv, int32_t *st
     }
 }
 
+// The same elimination over many blocks, for coarsest levels too large for
+// one CTA: step k is two launches, the pivot (search as above, row swap,
+// scaling of row k, and a copy of column k as the row factors) and the
+// update of every other row, each element with the single-CTA kernel's
+// arithmetic, so that both give the same inverse bit for bit.
+__global__ void gj_pivot_kernel(int n, int k, double *Aw, double *inv, double *fac, int32_t *status) {
+    __shared__ int piv_row;
+    __shared__ double red_v[1024];
+    __shared__ int red_i[1024];
+    const int tid = threadIdx.x;
+    double best = -1.0;
+    int bi = k;
+    for (int r = k + tid; r < n; r += blockDim.x) {
+        const double v = fabs(Aw[size_t(r) * n + k]);
+        if (v > best) { best = v; bi = r; }
+    }
+    red_v[tid] = best;
+    red_i[tid] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (tid < s && red_v[tid + s] > red_v[tid]) { red_v[tid] = red_v[tid + s]; red_i[tid] = red_i[tid + s]; }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        piv_row = red_i[0];
+        if (!(red_v[0] > 1e-300)) atomicOr(status, 4);
+    }
+    __syncthreads();
+    const int pr = piv_row;
+    if (pr != k)
+        for (int c = tid; c < n; c += blockDim.x) {
+            double t = Aw[size_t(k) * n + c]; Aw[size_t(k) * n + c] = Aw[size_t(pr) * n + c]; Aw[size_t(pr) * n + c] = t;
+            t = inv[size_t(k) * n + c]; inv[size_t(k) * n + c] = inv[size_t(pr) * n + c]; inv[size_t(pr) * n + c] = t;
+        }
+    __syncthreads();
+    const double pinv = 1.0 / Aw[size_t(k) * n + k];
+    __syncthreads();
+    for (int c = tid; c < n; c += blockDim.x) {
+        Aw[size_t(k) * n + c] *= pinv;
+        inv[size_t(k) * n + c] *= pinv;
+    }
+    for (int r = tid; r < n; r += blockDim.x) fac[r] = Aw[size_t(r) * n + k];
+}
+
+// (columns left of the pivot of the working copy are skipped: their row-k
+// entries are exact zeros, so the single-CTA update leaves them unchanged)
+__global__ void gj_update_kernel(int n, int k, double *Aw, double *inv, const double *fac) {
+    const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= size_t(n) * n) return;
+    const int r = int(idx / n), c = int(idx % n);
+    if (r == k) return;
+    const double f = fac[r];
+    if (c > k) Aw[size_t(r) * n + c] -= f * Aw[size_t(k) * n + c];
+    else if (c == k) Aw[size_t(r) * n + k] = 0.0;
+    inv[size_t(r) * n + c] -= f * inv[size_t(k) * n + c];
+}
+
+__global__ void identity_kernel(int n, double *inv) {
+    const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx < size_t(n) * n) inv[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+}
+
 __global__ void to_f32_kernel(const double *x, float *y, size_t n) {
     size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i < n) y[i] = float(x[i]);
@@ -432,7 +494,21 @@ cudaError_t launch_dense_inverse(hdg_handle *h, const DevLevel &L, double *work,
     ell_to_dense_kernel<<<n, 128, 0, h->stream>>>(n, L.width, L.col, L.A, work);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dense_inverse_kernel<<<1, 1024, 0, h->stream>>>(n, work, inv, h->d_status);
+    if (n <= 256) {
+        dense_inverse_kernel<<<1, 1024, 0, h->stream>>>(n, work, inv, h->d_status);
+        return cudaGetLastError();
+    }
+    // larger coarsest levels: one pivot and one update launch per column, the
+    // row factors of each column in their own array
+    double *fac = h->d_coarse_fac;
+    if (!fac) return cudaErrorInvalidValue;
+    const size_t nn = size_t(n) * n;
+    const unsigned nb = unsigned((nn + 255) / 256);
+    identity_kernel<<<nb, 256, 0, h->stream>>>(n, inv);
+    for (int k = 0; k < n; ++k) {
+        gj_pivot_kernel<<<1, 1024, 0, h->stream>>>(n, k, work, inv, fac, h->d_status);
+        gj_update_kernel<<<nb, 256, 0, h->stream>>>(n, k, work, inv, fac);
+    }
     return cudaGetLastError();
 }
 

@@ -347,6 +347,33 @@ void up_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_
 }
 
 
+// (A x)_i on a staged tail level: the row's W columns as 16-bit indices
+// (row-major, one 16-byte load per eight), the values slot-major (slot q of
+// row i at A[q * nv + i]), so that neither read has shared-memory bank
+// conflicts across a warp of consecutive rows; the sum runs over the slots in
+// order, as ell_row's does.
+template <typename T>
+__device__ __forceinline__ T tail_row(int i, int W, int nv, const uint16_t *__restrict__ col, const T *__restrict__ A,
+                                      const T *__restrict__ x) {
+    T ax = T(0);
+    const uint16_t *c = col + size_t(i) * W;
+    if (W == 8) {
+        const uint4 cc = *reinterpret_cast<const uint4 *>(c);
+        const uint32_t w[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) ax = fma(A[q * nv + i], x[(w[q >> 1] >> (16 * (q & 1))) & 0xffffu], ax);
+        return ax;
+    }
+    for (int q = 0; q < W; q += 4) {
+        const uint2 cc = *reinterpret_cast<const uint2 *>(c + q);
+        ax = fma(A[(q + 0) * nv + i], x[cc.x & 0xffffu], ax);
+        ax = fma(A[(q + 1) * nv + i], x[cc.x >> 16], ax);
+        ax = fma(A[(q + 2) * nv + i], x[cc.y & 0xffffu], ax);
+        ax = fma(A[(q + 3) * nv + i], x[cc.y >> 16], ax);
+    }
+    return ax;
+}
+
 // x_j + (P e_c)_j: the midpoint prolongation of the coarse correction added on the fly
 template <typename T>
 __device__ __forceinline__ T prolonged(const int32_t *par, const T *x, const T *ec, int j) {
@@ -758,6 +785,73 @@ __device__ __forceinline__ void coarse_product(const double *inv, int n, const T
 }
 
 
+// x = inv b on a coarsest level too large for the single-CTA cycle (FP64
+// inverse, FP64 sums in every precision): one block of four warps per row,
+// each thread summing pairs of columns 256 apart (16-byte loads, all of a
+// thread's loads independent), then a fixed shuffle tree per warp and the
+// four warp sums in order.
+template <typename T>
+__device__ __forceinline__ void coarse_dense_kernel_impl(int bid_, int nb_, const double *__restrict__ inv, int n,
+                                                         const T *__restrict__ b, T *__restrict__ x) {
+    __shared__ double part[4];
+    const int row = bid_, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double *a = inv + size_t(row) * n;
+    double acc = 0.0;
+    if ((n & 1) == 0) {
+        // rows start on 16-byte boundaries when n is even
+#pragma unroll 4
+        for (int j = 2 * tid; j < n; j += 256) {
+            const double2 av = *reinterpret_cast<const double2 *>(a + j);
+            acc = fma(av.x, double(b[j]), acc);
+            acc = fma(av.y, double(b[j + 1]), acc);
+        }
+    } else {
+#pragma unroll 4
+        for (int j = tid; j < n; j += 128) acc = fma(a[j], double(b[j]), acc);
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) part[warp] = acc;
+    __syncthreads();
+    if (tid == 0) x[row] = T(((part[0] + part[1]) + part[2]) + part[3]);
+    (void)nb_;
+}
+template <typename T>
+__global__ void __launch_bounds__(128) coarse_dense_kernel(const double *inv, int n, const T *b, T *x) {
+    pdl_wait();
+    coarse_dense_kernel_impl<T>(blockIdx.x, gridDim.x, inv, n, b, x);
+}
+template <typename T>
+struct coarse_dense_kernel_args {
+    int nb_;
+    const double *inv;
+    int n;
+    const T *b;
+    T *x;
+};
+template <typename T>
+__global__ void __launch_bounds__(128) coarse_dense_kernel_multi(const __grid_constant__ MultiP<coarse_dense_kernel_args<T>> M) {
+    pdl_wait();
+    int b_;
+    const coarse_dense_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    coarse_dense_kernel_impl<T>(b_, q_.nb_, q_.inv, q_.n, q_.b, q_.x);
+}
+template <typename T>
+void coarse_dense_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, const double *inv, int n,
+                            const T *b, T *x) {
+    if (Recorder *r_ = batch_recorder()) {
+        coarse_dense_kernel_args<T> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.inv = inv;
+        q_.n = n;
+        q_.b = b;
+        q_.x = x;
+        batch_record(r_, reinterpret_cast<const void *>(&coarse_dense_kernel_multi<T>), q_, grid_, block_, smem_);
+        return;
+    }
+    pdl_launch(kPdlFamily, &coarse_dense_kernel<T>, grid_, block_, smem_, s_, inv, n, b, x);
+}
+
 // Every array pointer below is the shared-memory base plus an offset from the
 // level table, so that the compiler addresses shared memory directly.
 template <typename T>
@@ -811,20 +905,20 @@ __device__ __forceinline__ void tail_kernel_impl(int bid_, int nb_, TailArgs a) 
     for (int l = 0; l < last; ++l) {
         const TailHdr h = H[l], hc = H[l + 1];
         const int nv = h.nv, W = h.W;
-        const int32_t *cl = PI(h.ocol);
+        const uint16_t *cl = reinterpret_cast<const uint16_t *>(tail_smem + h.ocol);
         const T *A = PT(h.oA), *D = PT(h.oD), *b = PT(h.ob);
         T *r = PT(h.orr);
         int32_t ox = h.ox, ox2 = h.ox2;
         for (int k = 1; k < a.nu1; ++k) {
             const T *x = PT(ox);
             T *x2 = PT(ox2);
-            for (int i = tid; i < nv; i += nt) x2[i] = fma(om * D[i], b[i] - ell_row(i, W, cl, A, x), x[i]);
+            for (int i = tid; i < nv; i += nt) x2[i] = fma(om * D[i], b[i] - tail_row(i, W, nv, cl, A, x), x[i]);
             __syncthreads();
             const int32_t t = ox; ox = ox2; ox2 = t;
         }
         {
             const T *x = PT(ox);
-            for (int i = tid; i < nv; i += nt) r[i] = b[i] - ell_row(i, W, cl, A, x);
+            for (int i = tid; i < nv; i += nt) r[i] = b[i] - tail_row(i, W, nv, cl, A, x);
         }
         if (tid == 0) { H[l].ox = ox; H[l].ox2 = ox2; }   // read again only after later barriers
         __syncthreads();
@@ -854,7 +948,8 @@ __device__ __forceinline__ void tail_kernel_impl(int bid_, int nb_, TailArgs a) 
     for (int l = last - 1; l >= 0; --l) {
         const TailHdr h = H[l];
         const int nv = h.nv, W = h.W;
-        const int32_t *cl = PI(h.ocol), *par = PI(H[l + 1].opar);
+        const uint16_t *cl = reinterpret_cast<const uint16_t *>(tail_smem + h.ocol);
+        const int32_t *par = PI(H[l + 1].opar);
         const T *A = PT(h.oA), *D = PT(h.oD), *b = PT(h.ob);
         int32_t ox = h.ox, ox2 = h.ox2;
         {
@@ -866,7 +961,7 @@ __device__ __forceinline__ void tail_kernel_impl(int bid_, int nb_, TailArgs a) 
         for (int k = 0; k < a.nu2; ++k) {
             const T *x = PT(ox);
             T *x2 = PT(ox2);
-            for (int i = tid; i < nv; i += nt) x2[i] = fma(om * D[i], b[i] - ell_row(i, W, cl, A, x), x[i]);
+            for (int i = tid; i < nv; i += nt) x2[i] = fma(om * D[i], b[i] - tail_row(i, W, nv, cl, A, x), x[i]);
             __syncthreads();
             const int32_t t = ox; ox = ox2; ox2 = t;
         }
@@ -972,6 +1067,11 @@ cudaError_t launch_p1_up_fused(const DevLevel &fine, const DevLevel &coarse, con
     return cudaGetLastError();
 }
 template <typename T>
+cudaError_t launch_p1_coarse_dense(const double *inv, int n, const T *b, T *x, cudaStream_t s) {
+    coarse_dense_kernel_go<T>(unsigned(n), 128, 0, s, inv, n, b, x);
+    return cudaGetLastError();
+}
+template <typename T>
 cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s) {
     // one fixed limit for every handle: the attribute is process-wide, so a
     // per-handle value could be lowered by another thread between set and launch
@@ -979,6 +1079,35 @@ cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(tail_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTailSmemMax));
     if (e != cudaSuccess) return e;
     tail_kernel_go<T>(1, 1024, smem, s, a);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// one tail level's ELL arrays in the staged layout (see tail_row)
+template <typename T>
+__global__ void tail_pack_kernel(const int32_t *__restrict__ col, const T *__restrict__ A, int nv, int W,
+                                 uint16_t *__restrict__ col16, T *__restrict__ At) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nv * W) return;
+    const int i = k / W, q = k % W;
+    col16[k] = static_cast<uint16_t>(col[k]);
+    At[size_t(q) * nv + i] = A[k];
+}
+
+}  // namespace
+
+cudaError_t launch_tail_pack(const int32_t *col, const void *A, size_t tsz, int nv, int W, void *col_dst, void *A_dst,
+                             cudaStream_t s) {
+    if (nv > 65536 || W % 4 != 0) return cudaErrorInvalidValue;
+    const unsigned nb = unsigned((size_t(nv) * W + 255) / 256);
+    if (nb == 0) return cudaSuccess;
+    if (tsz == sizeof(double))
+        tail_pack_kernel<double><<<nb, 256, 0, s>>>(col, static_cast<const double *>(A), nv, W,
+                                                    static_cast<uint16_t *>(col_dst), static_cast<double *>(A_dst));
+    else
+        tail_pack_kernel<float><<<nb, 256, 0, s>>>(col, static_cast<const float *>(A), nv, W,
+                                                   static_cast<uint16_t *>(col_dst), static_cast<float *>(A_dst));
     return cudaGetLastError();
 }
 
@@ -995,7 +1124,8 @@ cudaError_t launch_p1_tail(const TailArgs &a, size_t smem, cudaStream_t s) {
     template cudaError_t launch_p1_up_fused<T>(const DevLevel &, const DevLevel &, const T *, const T *, const T *, \
                                                const T *, const T *, T *, T, cudaStream_t);                        \
     template bool p1_patch_ok<T>(const DevLevel &);                                                          \
-    template cudaError_t launch_p1_tail<T>(const TailArgs &, size_t, cudaStream_t);
+    template cudaError_t launch_p1_tail<T>(const TailArgs &, size_t, cudaStream_t);                           \
+    template cudaError_t launch_p1_coarse_dense<T>(const double *, int, const T *, T *, cudaStream_t);
 HDG_P1_INST(double)
 HDG_P1_INST(float)
 

@@ -3,7 +3,9 @@
 // staged arrays (ELL values, inverse diagonal, ELL columns and, below the
 // first tail level, restriction weights, child pointers, child indices and
 // parents), the coarsest level's FP64 inverse when it fits, then the scratch
-// vectors.  Kept apart from the CUDA code so that it can be checked on the CPU.
+// vectors.  The ELL values are staged slot-major (slot q of row i at
+// q * nv + i) and the ELL columns as 16-bit indices, row-major, so that the
+// kernel's shared-memory reads of a row are free of bank conflicts.  Kept apart from the CUDA code so that it can be checked on the CPU.
 #include "common.h"
 
 namespace hdg {
@@ -29,7 +31,7 @@ bool tail_layout(const std::vector<TailLevelSize> &lv, size_t tsz, size_t nc, Ta
         H.W = L.W;
         put(H.oA, k, kTailA, tsz * size_t(L.nnz));
         put(H.oD, k, kTailD, tsz * size_t(L.nv));
-        put(H.ocol, k, kTailCol, 4 * size_t(L.nnz));
+        put(H.ocol, k, kTailCol, 2 * size_t(L.nnz));      // 16-bit columns
         if (!top) {
             put(H.ocw, k, kTailCw, tsz * size_t(L.nci));
             put(H.ocp, k, kTailCp, 4 * size_t(L.nv + 1));

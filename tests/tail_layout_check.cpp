@@ -59,7 +59,7 @@ extern "C" int check_tail_layouts(const hdg_mesh_desc *d, char *out, int len) {
                 if (H.nv != L.nv || H.nnz != L.nnz || H.W != L.W || H.nci != (k ? L.nci : 0)) fail(tag + "table sizes");
                 struct Want { int kind; int32_t off; size_t bytes; };
                 std::vector<Want> want = {{kTailA, H.oA, tsz * L.nnz}, {kTailD, H.oD, tsz * L.nv},
-                                          {kTailCol, H.ocol, 4 * size_t(L.nnz)}};
+                                          {kTailCol, H.ocol, 2 * size_t(L.nnz)}};
                 if (k) {
                     want.push_back({kTailCw, H.ocw, tsz * L.nci});
                     want.push_back({kTailCp, H.ocp, 4 * size_t(L.nv + 1)});
