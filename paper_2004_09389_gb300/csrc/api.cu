@@ -1863,9 +1863,11 @@ int hdg_condense(hdg_handle *h) {
         if (mode_ff(h->prm)) {
             // (hi, lo) float pairs for the two-float FP64 steps
             const size_t N = h->N, nK = h->nK, m = h->m, pp = h->pp, NS = 5 * pp * pp;
-            TRY(KL(HDG_PROF_CONDENSE, 1, launch_split_pairs(h->d_Xb, h->d_Xb2, int(nK), int(m), N, s)));
-            TRY(KL(HDG_PROF_CONDENSE, 1, launch_split_pairs(h->d_Rm, h->d_Rm2, int(nK), int(nK), N, s)));
-            TRY(KL(HDG_PROF_CONDENSE, 1, launch_split_pairs(h->d_W, h->d_W2, int(m), int(nK), N, s)));
+            if (!condense_writes_pairs(h)) {
+                TRY(KL(HDG_PROF_CONDENSE, 1, launch_split_pairs(h->d_Xb, h->d_Xb2, int(nK), int(m), N, s)));
+                TRY(KL(HDG_PROF_CONDENSE, 1, launch_split_pairs(h->d_Rm, h->d_Rm2, int(nK), int(nK), N, s)));
+                TRY(KL(HDG_PROF_CONDENSE, 1, launch_split_pairs(h->d_W, h->d_W2, int(m), int(nK), N, s)));
+            }
             TRY(KL(HDG_PROF_CONDENSE, 1, launch_split(h->d_Sval, h->d_Sval2, (NS + 1) / 2 * 2 * size_t(h->NF), s)));
         }
     }

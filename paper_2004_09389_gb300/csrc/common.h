@@ -324,6 +324,46 @@ struct TailArgs {
     void *x_top;                        // its solution (global)
 };
 
+// ---------------------------------------------------------------- two-float arithmetic
+// An FP64 value a as the pair (hi, lo) = (rn(a), rn(a - hi)) of floats; a sum
+// of products carried as s + c: s the running sum of the rounded leading
+// products, added by error-free TwoSum steps, c the float sum of the exact
+// product errors (by FMA), the cross terms and the TwoSum errors.  About
+// n * 2^-48 relative error of sum |a_i x_i| for n terms, a dozen FP32
+// operations per term (used where GB300's FP64 pipe would be the bound).
+__device__ __forceinline__ float2 split(double a) {
+    const float hi = __double2float_rn(a);
+    return make_float2(hi, __double2float_rn(a - double(hi)));
+}
+
+// Cell tiles of the two-float per-cell matrices: a matrix a (rows x cols per
+// cell) is stored as pairs of consecutive row entries, (hi, lo) of column 2cp
+// and of column 2cp + 1 (zeros past the row's end) in one float4, pair plane
+// pc = row * CP + cp (CP = (cols + 1) / 2) of cell K at
+// ((K / kFFCells) * rows * CP + pc) * kFFCells + K % kFFCells.
+constexpr int kFFCells = 32;
+__host__ __device__ __forceinline__ size_t ff_pair_index(size_t K, size_t pc, size_t np) {
+    return ((K / kFFCells) * np + pc) * kFFCells + K % kFFCells;
+}
+
+struct FFAcc {
+    float s = 0.f, c = 0.f;
+    // s + c += a * x (a, x split pairs); intrinsics keep the compiler from
+    // contracting or reassociating the error-free steps
+    __device__ __forceinline__ void add(const float2 a, const float2 x) {
+        const float p = __fmul_rn(a.x, x.x);
+        const float e = __fmaf_rn(a.x, x.x, -p);
+        c = __fmaf_rn(a.x, x.y, c);
+        c = __fmaf_rn(a.y, x.x, c);
+        c = __fadd_rn(c, e);
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
 // ---------------------------------------------------------------- dependent launch
 // Programmatic dependent launch (sm_90 and later): a kernel launched by
 // pdl_launch may be scheduled while the previous kernel in the stream drains
@@ -641,6 +681,9 @@ cudaError_t launch_p1_assemble(hdg_handle *h, DevLevel &L, double tau, double gH
 // every P1 level operator as the Galerkin product of the trace operator (k_galerkin.cu)
 cudaError_t launch_p1_galerkin(hdg_handle *h);
 cudaError_t launch_dense_inverse(hdg_handle *h, const DevLevel &L, double *work, double *inv, int n);
+// true when launch_condense writes the mixed handles' float-pair matrices
+// (X_B, R_M, W_K) itself, so that no FP64 copy of them exists to split
+bool condense_writes_pairs(const hdg_handle *h);
 // a tail level's ELL arrays in the staged layout: values (tsz bytes each)
 // slot-major into A_dst, columns as 16-bit indices into col_dst
 cudaError_t launch_tail_pack(const int32_t *col, const void *A, size_t tsz, int nv, int W, void *col_dst, void *A_dst,

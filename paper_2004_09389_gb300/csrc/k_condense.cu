@@ -17,6 +17,8 @@
 // and R_M, X_B serve step 3 (Eq. reconstruct_solution): q = R_M r - X_B lambda_K.
 #include "common.h"
 
+#include <cstdlib>
+
 namespace hdg {
 
 namespace {
@@ -40,24 +42,20 @@ struct CondenseArgs {
     const double *fcell;    // [N][3]
     double *Xb, *Rm, *W, *Scell;
     int32_t *status;
+    float4 *Xb2, *Rm2, *W2;   // mixed-precision kernel: the float-pair copies, written directly
 };
 
+// The cell's system in shared memory: geometry (geo: detJ, J^-T, edge
+// lengths, outward normals), the vertex Coriolis values fK, the augmented rows
+// [D A | D B | D Mass] (Aug, NK x LDA; D the momentum-row scaling) and C (Cm,
+// M x NK).  Ends with a barrier.
 template <int P>
-__global__ void __launch_bounds__(kCondenseThreads) condense_kernel(CondenseArgs a) {
+__device__ __forceinline__ void cell_system(const CondenseArgs &a, int K, double *Aug, double *Cm, double *geo,
+                                            double *fK) {
     using S = Sz<P>;
     constexpr int NP = S::NP, NK = S::NK, M = S::M, PP = S::PP, LDA = S::LDA;
     constexpr int oM = 0, oML = oM + NP * NP, oDxi = oML + 3 * NP * NP, oDeta = oDxi + NP * NP,
-                  oE = oDeta + NP * NP, oN = oE + 3 * NP * NP, oM1 = oN + 3 * NP * PP;
-    extern __shared__ double smem[];
-    double *Aug = smem;                 // [NK][LDA]
-    double *Cm = Aug + NK * LDA;        // [M][NK]
-    double *prow = Cm + M * NK;         // [LDA]
-    double *fac = prow + LDA;           // [NK]
-    __shared__ double geo[16];          // detJ, Jit[4], len[3], nrm[6], pad
-    __shared__ double fK[3];
-    __shared__ int bad;
-
-    const int K = blockIdx.x;
+                  oE = oDeta + NP * NP, oN = oE + 3 * NP * NP;
     const int tid = threadIdx.x;
     const double *ref = a.ref;
     if (tid == 0) {
@@ -77,7 +75,6 @@ __global__ void __launch_bounds__(kCondenseThreads) condense_kernel(CondenseArgs
             geo[9 + 2 * i] = -tx / l;
         }
         for (int i = 0; i < 3; ++i) fK[i] = a.fcell[size_t(K) * 3 + i];
-        bad = 0;
     }
     __syncthreads();
     const double det = geo[0], j00 = geo[1], j01 = geo[2], j10 = geo[3], j11 = geo[4];
@@ -136,6 +133,30 @@ __global__ void __launch_bounds__(kCondenseThreads) condense_kernel(CondenseArgs
     }
     __syncthreads();
 
+}
+
+template <int P>
+__global__ void __launch_bounds__(kCondenseThreads) condense_kernel(CondenseArgs a) {
+    using S = Sz<P>;
+    constexpr int NP = S::NP, NK = S::NK, M = S::M, PP = S::PP, LDA = S::LDA;
+    constexpr int oM = 0, oML = oM + NP * NP, oDxi = oML + 3 * NP * NP, oDeta = oDxi + NP * NP,
+                  oE = oDeta + NP * NP, oN = oE + 3 * NP * NP, oM1 = oN + 3 * NP * PP;
+    extern __shared__ double smem[];
+    double *Aug = smem;                 // [NK][LDA]
+    double *Cm = Aug + NK * LDA;        // [M][NK]
+    double *prow = Cm + M * NK;         // [LDA]
+    double *fac = prow + LDA;           // [NK]
+    __shared__ double geo[16];          // detJ, Jit[4], len[3], nrm[6], pad
+    __shared__ double fK[3];
+    __shared__ int bad;
+
+    const int K = blockIdx.x;
+    const int tid = threadIdx.x;
+    const double *ref = a.ref;
+    const double ts = a.tau_s;
+    if (tid == 0) bad = 0;
+    cell_system<P>(a, K, Aug, Cm, geo, fK);
+
     // ---- Gauss-Jordan elimination, no pivoting (see the header comment)
     for (int k = 0; k < NK; ++k) {
         const double piv = Aug[k * LDA + k];
@@ -182,6 +203,176 @@ __global__ void __launch_bounds__(kCondenseThreads) condense_kernel(CondenseArgs
         double s = 0.0;
         for (int r = 0; r < NK; ++r) s += Cm[t * NK + r] * Aug[r * LDA + NK + M + kap];
         a.W[size_t(idx) * N + K] = s;
+    }
+}
+
+// ---------------------------------------------------------------- mixed-precision condensation
+// The same outputs for the mixed-precision handles, which use X_B, R_M, S_K
+// and W_K only as two-float pairs (and FP32 / BF16 copies): A_K is inverted in
+// FP32 (Gauss-Jordan in place, no pivoting, as above), X = A^-1 [B | Mass]
+// formed in FP32 and refined twice, each time with the residual
+// [B | Mass] - A X formed in two-float arithmetic (FFAcc) from the FP64 system
+// and the two-float X, and the correction A^-1 R added to X, kept as a
+// two-float pair.  S_K = Mt_K + C X_B and W_K = C R_M are formed in two-float
+// arithmetic too.  Each refinement step gains the factor ||I - Ainv A|| (about
+// cond(A_K) 2^-24) up to the two-float resolution (about 2^-48 relative):
+// two steps reach it for cells with a condition number well below 2^12.  No
+// FP64 product or elimination is left (GB300's FP32 rate is about 70 times its
+// FP64 rate), and with an explicit FP32 inverse every solve is a product, free
+// of the barrier per elimination step that triangular solves would take.
+// refinement steps (each costs about 60 % of the kernel's instructions)
+constexpr int kMpRefine = 2;
+
+template <int P>
+struct SzMp {
+    using S = Sz<P>;
+    static constexpr int NR = S::M + S::NK;                        // right-hand sides: B, Mass
+    static constexpr int oAi = S::NK * S::LDA + S::M * S::NK;      // in doubles: after Aug and Cm
+    static constexpr int nAi = (S::NK * S::NK + 1) / 2;            // FP32 inverse
+    static constexpr int oAp = oAi + nAi;                          // split A (float2 = one double each)
+    static constexpr int oXp = oAp + S::NK * S::NK;                // two-float X
+    static constexpr int oBp = oXp + S::NK * NR;                   // split right-hand sides
+    static constexpr int oRf = oBp + S::NK * NR;                   // FP32 residual
+    static constexpr int oFac = oRf + (S::NK * NR + 1) / 2;        // FP32 column factors
+    static constexpr int total = oFac + (S::NK + 1) / 2;           // doubles of dynamic shared memory
+};
+
+template <int P>
+__global__ void __launch_bounds__(kCondenseThreads) condense_mp_kernel(CondenseArgs a) {
+    using S = Sz<P>;
+    using Z = SzMp<P>;
+    constexpr int NP = S::NP, NK = S::NK, M = S::M, PP = S::PP, LDA = S::LDA, NR = Z::NR;
+    constexpr int oM1 = NP * NP + 3 * NP * NP + NP * NP + NP * NP + 3 * NP * NP + 3 * NP * PP;
+    extern __shared__ double smem[];
+    double *Aug = smem;                                            // [NK][LDA]
+    double *Cm = Aug + NK * LDA;                                   // [M][NK]
+    float *Ai = reinterpret_cast<float *>(smem + Z::oAi);          // [NK][NK] FP32 inverse
+    float2 *Ap = reinterpret_cast<float2 *>(smem + Z::oAp);        // [NK][NK] split A; later split C
+    float2 *Xp = reinterpret_cast<float2 *>(smem + Z::oXp);        // [NK][NR] two-float X
+    float2 *Bp = reinterpret_cast<float2 *>(smem + Z::oBp);        // [NK][NR] split [B | Mass]
+    float *Rf = reinterpret_cast<float *>(smem + Z::oRf);          // [NK][NR]
+    float *fac = reinterpret_cast<float *>(smem + Z::oFac);        // [NK]
+    __shared__ double geo[16];
+    __shared__ double fK[3];
+    __shared__ int bad;
+
+    const int K = blockIdx.x;
+    const int tid = threadIdx.x;
+    const double *ref = a.ref;
+    const double ts = a.tau_s;
+    if (tid == 0) bad = 0;
+    cell_system<P>(a, K, Aug, Cm, geo, fK);
+
+    for (int idx = tid; idx < NK * NK; idx += blockDim.x) {
+        const float2 v = split(Aug[(idx / NK) * LDA + idx % NK]);
+        Ap[idx] = v;
+        Ai[idx] = v.x;
+    }
+    __syncthreads();
+    // ---- FP32 inverse in place: step k scales row k (its pivot entry becomes
+    // 1 / pivot) and records column k, then eliminates column k from the other
+    // rows (their column-k entries become -a_ik / pivot)
+    for (int k = 0; k < NK; ++k) {
+        const float piv = Ai[k * NK + k];
+        if (tid == 0 && !(fabsf(piv) > 1e-30f)) bad = 1;
+        const float pinv = 1.0f / piv;
+        for (int i = tid; i < NK; i += blockDim.x) fac[i] = Ai[i * NK + k];
+        __syncthreads();
+        for (int c = tid; c < NK; c += blockDim.x) Ai[k * NK + c] = (c == k) ? pinv : Ai[k * NK + c] * pinv;
+        __syncthreads();
+        for (int idx = tid; idx < NK * NK; idx += blockDim.x) {
+            const int i = idx / NK, c = idx % NK;
+            if (i == k) continue;
+            Ai[idx] = (c == k) ? -fac[i] * pinv : fmaf(-fac[i], Ai[k * NK + c], Ai[idx]);
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) atomicOr(a.status, 1);
+        return;
+    }
+    // ---- X_0 = Ainv [B | Mass] in FP32, then the refinement steps
+    for (int idx = tid; idx < NK * NR; idx += blockDim.x) {
+        const float2 v = split(Aug[(idx / NR) * LDA + NK + idx % NR]);
+        Bp[idx] = v;
+        Rf[idx] = v.x;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NK * NR; idx += blockDim.x) {
+        const int i = idx / NR, c = idx % NR;
+        float x = 0.0f;
+#pragma unroll 6
+        for (int j = 0; j < NK; ++j) x = fmaf(Ai[i * NK + j], Rf[j * NR + c], x);
+        Xp[idx] = make_float2(x, 0.0f);
+    }
+    __syncthreads();
+    for (int it = 0; it < kMpRefine; ++it) {
+        for (int idx = tid; idx < NK * NR; idx += blockDim.x) {
+            const int r = idx / NR, c = idx % NR;
+            FFAcc acc;
+#pragma unroll 5
+            for (int j = 0; j < NK; ++j) acc.add(Ap[r * NK + j], Xp[j * NR + c]);
+            // r = b - A X to FP32 accuracy: the leading parts nearly cancel exactly
+            const float2 bv = Bp[idx];
+            Rf[idx] = __fadd_rn(__fsub_rn(bv.x, acc.s), __fsub_rn(bv.y, acc.c));
+        }
+        __syncthreads();
+        for (int idx = tid; idx < NK * NR; idx += blockDim.x) {
+            const int i = idx / NR, c = idx % NR;
+            float d = 0.0f;
+#pragma unroll 6
+            for (int j = 0; j < NK; ++j) d = fmaf(Ai[i * NK + j], Rf[j * NR + c], d);
+            // (hi, lo) + d: TwoSum of the leading parts, then renormalise
+            const float2 x = Xp[idx];
+            const float s1 = __fadd_rn(x.x, d);
+            const float bp = __fsub_rn(s1, x.x);
+            const float e = __fadd_rn(__fsub_rn(x.x, __fsub_rn(s1, bp)), __fsub_rn(d, bp));
+            const float lo = __fadd_rn(x.y, e);
+            const float hi = __fadd_rn(s1, lo);
+            Xp[idx] = make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s1)));
+        }
+        __syncthreads();
+    }
+    // ---- outputs: X_B, R_M and W_K as float pairs in the cell tiles of the
+    // two-float kernels, S_K in FP64 (C split into the space of the split A)
+    float2 *Cp = Ap;
+    for (int idx = tid; idx < M * NK; idx += blockDim.x) Cp[idx] = split(Cm[idx]);
+    __syncthreads();
+    {
+        constexpr int CPb = (M + 1) / 2, CPr = (NK + 1) / 2;
+        for (int idx = tid; idx < NK * CPb; idx += blockDim.x) {
+            const int rho = idx / CPb, c0 = 2 * (idx % CPb);
+            const float2 x0 = Xp[rho * NR + c0];
+            const float2 x1 = c0 + 1 < M ? Xp[rho * NR + c0 + 1] : make_float2(0.f, 0.f);
+            a.Xb2[ff_pair_index(size_t(K), size_t(idx), size_t(NK) * CPb)] = make_float4(x0.x, x0.y, x1.x, x1.y);
+        }
+        for (int idx = tid; idx < NK * CPr; idx += blockDim.x) {
+            const int rho = idx / CPr, c0 = 2 * (idx % CPr);
+            const float2 x0 = Xp[rho * NR + M + c0];
+            const float2 x1 = c0 + 1 < NK ? Xp[rho * NR + M + c0 + 1] : make_float2(0.f, 0.f);
+            a.Rm2[ff_pair_index(size_t(K), size_t(idx), size_t(NK) * CPr)] = make_float4(x0.x, x0.y, x1.x, x1.y);
+        }
+        // W_K = C R_M: each pair of columns from two two-float sums, renormalised
+        for (int idx = tid; idx < M * CPr; idx += blockDim.x) {
+            const int t = idx / CPr, c0 = 2 * (idx % CPr);
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int q = 0; q < 2 && c0 + q < NK; ++q) {
+                FFAcc acc;
+                for (int r = 0; r < NK; ++r) acc.add(Cp[t * NK + r], Xp[r * NR + M + c0 + q]);
+                const float hi = __fadd_rn(acc.s, acc.c);
+                v[2 * q] = hi;
+                v[2 * q + 1] = __fsub_rn(acc.c, __fsub_rn(hi, acc.s));
+            }
+            a.W2[ff_pair_index(size_t(K), size_t(idx), size_t(M) * CPr)] = make_float4(v[0], v[1], v[2], v[3]);
+        }
+    }
+    for (int idx = tid; idx < M * M; idx += blockDim.x) {
+        const int t = idx / M, t2 = idx % M;
+        FFAcc acc;
+        for (int kap = 0; kap < NK; ++kap) acc.add(Cp[t * NK + kap], Xp[kap * NR + t2]);
+        double v = acc.value();
+        if (t / PP == t2 / PP) v += ts * geo[5 + t / PP] * ref[oM1 + (t % PP) * PP + (t2 % PP)];
+        a.Scell[size_t(K) * M * M + idx] = v;
     }
 }
 
@@ -450,6 +641,23 @@ cudaError_t condense_p(hdg_handle *h) {
 }
 
 template <int P>
+cudaError_t condense_mp_p(hdg_handle *h) {
+    const size_t smem = sizeof(double) * SzMp<P>::total;
+    cudaError_t e = cudaFuncSetAttribute(condense_mp_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    CondenseArgs a;
+    a.N = h->N; a.tau = h->prm.tau; a.g = h->prm.g; a.H = h->prm.H; a.tau_s = h->tau_s;
+    a.ref = h->d_ref; a.X = h->d_X; a.fcell = h->d_fcell;
+    a.Xb = h->d_Xb; a.Rm = h->d_Rm; a.W = h->d_W; a.Scell = h->d_Scell; a.status = h->d_status;
+    a.Xb2 = reinterpret_cast<float4 *>(h->d_Xb2);
+    a.Rm2 = reinterpret_cast<float4 *>(h->d_Rm2);
+    a.W2 = reinterpret_cast<float4 *>(h->d_W2);
+    if (!a.Xb2 || !a.Rm2 || !a.W2) return cudaErrorInvalidValue;
+    condense_mp_kernel<P><<<h->N, kCondenseThreads, smem, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P>
 cudaError_t assemble_p(hdg_handle *h) {
     AssembleArgs a;
     a.N = h->N; a.NF = h->NF; a.Scell = h->d_Scell;
@@ -461,7 +669,31 @@ cudaError_t assemble_p(hdg_handle *h) {
 
 }  // namespace
 
+namespace {
+// HDG_CONDENSE_FP64=1: the FP64 elimination for the mixed handles too (read once)
+bool force_fp64_condense() {
+    static const bool on = [] {
+        const char *e = std::getenv("HDG_CONDENSE_FP64");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+}  // namespace
+
+bool condense_writes_pairs(const hdg_handle *h) { return mode_ff(h->prm) && !force_fp64_condense(); }
+
 cudaError_t launch_condense(hdg_handle *h) {
+    // mixed-precision handles: FP32 inverse with two-float refinement, writing
+    // the float-pair matrices directly
+    if (condense_writes_pairs(h)) {
+        switch (h->p) {
+            case 1: return condense_mp_p<1>(h);
+            case 2: return condense_mp_p<2>(h);
+            case 3: return condense_mp_p<3>(h);
+            case 4: return condense_mp_p<4>(h);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (h->p) {
         case 1: return condense_p<1>(h);
         case 2: return condense_p<2>(h);

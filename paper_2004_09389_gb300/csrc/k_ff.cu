@@ -31,31 +31,8 @@ inline unsigned blocks(size_t n, int bs) { return unsigned((n + bs - 1) / bs); }
 // split once into shared memory and shared by the warps, which take the output
 // rows in turn; per-cell matrices, split into pairs of row entries
 // ([row][col pair][N], split_pairs_kernel), load coalesced, 16 bytes per lane.
-constexpr int kCells = 32;
+constexpr int kCells = kFFCells;
 constexpr int kCellsPad = kCells + 1;
-
-__device__ __forceinline__ float2 split(double a) {
-    const float hi = __double2float_rn(a);
-    return make_float2(hi, __double2float_rn(a - double(hi)));
-}
-
-struct FFAcc {
-    float s = 0.f, c = 0.f;
-    // s + c += a * x (a, x split pairs); intrinsics keep the compiler from
-    // contracting or reassociating the error-free steps
-    __device__ __forceinline__ void add(const float2 a, const float2 x) {
-        const float p = __fmul_rn(a.x, x.x);
-        const float e = __fmaf_rn(a.x, x.x, -p);
-        c = __fmaf_rn(a.x, x.y, c);
-        c = __fmaf_rn(a.y, x.x, c);
-        c = __fadd_rn(c, e);
-        const float t = __fadd_rn(s, p);
-        const float bp = __fsub_rn(t, s);
-        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return double(s) + double(c); }
-};
 
 __global__ void split_kernel(const double *__restrict__ a, float2 *__restrict__ out, size_t n) {
     const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -79,7 +56,7 @@ __global__ void split_pairs_kernel(const double *__restrict__ a, float4 *__restr
     const int row = int(pc / CP), c0 = 2 * int(pc % CP);
     const float2 lo = split(a[(size_t(row) * cols + c0) * N + K]);
     const float2 hi = c0 + 1 < cols ? split(a[(size_t(row) * cols + c0 + 1) * N + K]) : make_float2(0.f, 0.f);
-    out[((K / kCells) * np + pc) * kCells + K % kCells] = make_float4(lo.x, lo.y, hi.x, hi.y);
+    out[ff_pair_index(K, pc, np)] = make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
 // acc += sum over the NCOL entries of one row (pairs p[cp * kCells], cp <

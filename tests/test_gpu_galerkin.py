@@ -4,8 +4,9 @@ against the oracle's Galerkin hierarchy.
 
 * One preconditioner application equals the oracle's with the same coarse
   operators (1e-12), flat and sphere, p = 1 and 3, with the coarse levels in
-  the single-CTA cycle and with them in the multi-block (patch-fused and
-  unfused) kernels.
+  the single-CTA cycle; with them in the multi-block (patch-fused and
+  unfused) kernels on a mixed-precision handle (two-float condensation),
+  1e-11 in FP64 and 1e-5 in FP32.
 * Solves reach the oracle's direct solution (1e-10 at rtol 1e-13), with the
   oracle's iteration count within one; also together with the Chebyshev
   smoother.
@@ -82,7 +83,10 @@ def test_precond_multi_block_levels_match_oracle(kind, monkeypatch):
         s.precond_apply_dev(torch.from_numpy(v).cuda(), z)
         s.precond_apply32_dev(torch.from_numpy(v.astype(np.float32)).cuda(), z32)
         torch.cuda.synchronize()
-        assert _rel(z.cpu().numpy(), z0) <= 1e-12, fused
+        # a mixed-precision handle condenses in two-float arithmetic (about
+        # 2^-48 per S_K entry), and the Galerkin coarse operator sums S_K
+        # entries with cancellation: its FP64 application agrees to 1e-11
+        assert _rel(z.cpu().numpy(), z0) <= 1e-11, fused
         assert _rel(z32.cpu().numpy().astype(np.float64), z0) <= 1e-5, fused
         s.close()
 
