@@ -942,6 +942,51 @@ def batch_main(args):
         s.close()
 
 
+def profile_condense_main(args):
+    """Set-up and condensation of one mixed-precision handle of the flat
+    n x n x 2 workload (p = 3) between cudaProfilerStart/Stop, for ncu."""
+    import torch
+    from paper_2004_09389_gb300 import HDGSolver, HDG_MIXED_FP32, build
+    build.build()
+    n = args.profile_condense
+    mesh, tau, f, ru, rh = workload(n, args.p, args.courant, args.seed)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    s = HDGSolver(mesh, args.p, tau, G, DEPTH, f_vertex=f, rtol=args.rtol, precision=HDG_MIXED_FP32)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profile_condense": f"flat {n}x{n}x2 p={args.p}", "cells": s.n_cells}))
+    s.close()
+
+
+def profile_batch_main(args):
+    """One merged batched solve of the uneven batch (after two warm-up solves)
+    between cudaProfilerStart/Stop, for an ncu launch list."""
+    import torch
+    from paper_2004_09389_gb300 import HDGSolver, HDG_MIXED_FP32, MergedBatch, build
+    build.build()
+    probs = batch_workload(args.batch or 64, args.seed)
+    solvers = [HDGSolver(x["mesh"], x["p"], x["tau"], x["g"], x["H"], f_vertex=x["f"], rtol=args.rtol,
+                         precision=HDG_MIXED_FP32, restart=args.restart, smoother=x["smoother"], max_iter=2000)
+               for x in probs]
+    ru = [torch.from_numpy(x["ru"]).cuda() for x in probs]
+    rh = [torch.from_numpy(x["rh"]).cuda() for x in probs]
+    lam = [torch.zeros((s.n_facets, s.p + 1), dtype=torch.float64, device="cuda") for s in solvers]
+    b = MergedBatch(solvers)
+    for _ in range(2):
+        b.solve_dev(ru, rh, lam)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    infos = b.solve_dev(ru, rh, lam)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    st = b.stats()
+    print(json.dumps({"profile_batch": len(solvers), "iters": sum(i["iters"] for i in infos), **st}))
+    b.close()
+    for s in solvers:
+        s.close()
+
+
 def profile_solve_main(args):
     """One warm solve + recovery inside cudaProfilerStart/Stop: the launch list of a
     solve as it runs in the timed loop (caches warm from the previous solves)."""
@@ -1048,6 +1093,10 @@ def main():
                     help="time one FP32 preconditioner application with the learned sweep off, on the CUDA cores "
                          "and on the tensor cores (hidden 64, random parameters), then run one of each between "
                          "profiler start and stop; prints the times, no bench line")
+    ap.add_argument("--profile-condense", dest="profile_condense", type=int, default=0,
+                    help="set up one mixed handle of the flat NxNx2 workload between cudaProfilerStart/Stop")
+    ap.add_argument("--profile-batch", dest="profile_batch", action="store_true",
+                    help="one merged batched solve of the --batch workload between cudaProfilerStart/Stop")
     ap.add_argument("--profile-solve", dest="profile_solve", default="",
                     choices=["", "mixed", "mixed_bf16", "fgmres64", "fp64"],
                     help="warm up, then run one solve and recovery of this arm between profiler start and stop "
@@ -1055,6 +1104,12 @@ def main():
     args = ap.parse_args()
     if args.profile_solve:
         profile_solve_main(args)
+        return
+    if args.profile_condense:
+        profile_condense_main(args)
+        return
+    if args.profile_batch:
+        profile_batch_main(args)
         return
     if args.profile_learned:
         profile_learned_main(args)
