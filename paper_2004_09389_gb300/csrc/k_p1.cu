@@ -55,20 +55,41 @@ __device__ __forceinline__ void jacobi_kernel_impl(int bid_, int nb_, int n, int
                                                    const T *__restrict__ A, const T *__restrict__ dinv,
                                                    const T *__restrict__ b, const T *__restrict__ x,
                                                    T *__restrict__ xout, T omega, int first) {
+    // the static row (operator values, columns, inverse diagonal) before the
+    // wait for the previous kernel, the vectors after it
     const int i = bid_ * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const bool ok = i < n;
+    T di = T(0), av[8];
+    int cs[8];
+    const bool pre = ok && !first && W == 8;
+    if (ok) di = dinv[i];
+    if (pre) {
+        const int4 c0 = *reinterpret_cast<const int4 *>(col + size_t(i) * 8);
+        const int4 c1 = *reinterpret_cast<const int4 *>(col + size_t(i) * 8 + 4);
+        cs[0] = c0.x; cs[1] = c0.y; cs[2] = c0.z; cs[3] = c0.w;
+        cs[4] = c1.x; cs[5] = c1.y; cs[6] = c1.z; cs[7] = c1.w;
+        load4(A + size_t(i) * 8, av);
+        load4(A + size_t(i) * 8 + 4, av + 4);
+    }
+    pdl_wait();
+    if (!ok) return;
     if (first) {
-        xout[i] = omega * dinv[i] * b[i];
+        xout[i] = omega * di * b[i];
         return;
     }
-    const T ax = ell_row(i, W, col, A, x);
-    xout[i] = fma(omega * dinv[i], b[i] - ax, x[i]);
+    T ax = T(0);
+    if (pre) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) ax = fma(av[q], x[cs[q]], ax);
+    } else {
+        ax = ell_row(i, W, col, A, x);
+    }
+    xout[i] = fma(omega * di, b[i] - ax, x[i]);
 }
 template <typename T>
 __global__ void jacobi_kernel(int n, int W, const int32_t *__restrict__ col, const T *__restrict__ A,
                               const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x,
                               T *__restrict__ xout, T omega, int first) {
-    pdl_wait();
     jacobi_kernel_impl<T>(blockIdx.x, gridDim.x, n, W, col, A, dinv, b, x, xout, omega, first);
 }
 template <typename T>
@@ -87,7 +108,6 @@ struct jacobi_kernel_args {
 };
 template <typename T>
 __global__ void jacobi_kernel_multi(const __grid_constant__ MultiP<jacobi_kernel_args<T>> M) {
-    pdl_wait();
     int b_;
     const jacobi_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     jacobi_kernel_impl<T>(b_, q_.nb_, q_.n, q_.W, q_.col, q_.A, q_.dinv, q_.b, q_.x, q_.xout, q_.omega, q_.first);
@@ -268,9 +288,44 @@ __device__ __forceinline__ void up_kernel_impl(int bid_, int nb_, int nf, int W,
                                                const T *__restrict__ b, const T *__restrict__ x,
                                                const int32_t *__restrict__ parent, const T *__restrict__ ec,
                                                T *__restrict__ xout, T omega) {
+    // the static data (row, parents of the row's columns, inverse diagonal)
+    // before the wait for the previous kernel when the row has eight slots
     const int i = bid_ * blockDim.x + threadIdx.x;
-    if (i >= nf) return;
+    const bool ok = i < nf, pre = ok && W == 8;
+    T di = T(0), av8[8];
+    int js8[8], pa8[8], pb8[8], pi0 = 0, pi1 = 0;
+    if (ok) {
+        di = dinv[i];
+        pi0 = parent[2 * i];
+        pi1 = parent[2 * i + 1];
+    }
+    if (pre) {
+        const int4 c0 = *reinterpret_cast<const int4 *>(col + size_t(i) * 8);
+        const int4 c1 = *reinterpret_cast<const int4 *>(col + size_t(i) * 8 + 4);
+        js8[0] = c0.x; js8[1] = c0.y; js8[2] = c0.z; js8[3] = c0.w;
+        js8[4] = c1.x; js8[5] = c1.y; js8[6] = c1.z; js8[7] = c1.w;
+        load4(A + size_t(i) * 8, av8);
+        load4(A + size_t(i) * 8 + 4, av8 + 4);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            pa8[q] = parent[2 * js8[q]];
+            pb8[q] = parent[2 * js8[q] + 1];
+        }
+    }
+    pdl_wait();
+    if (!ok) return;
     T ax = T(0);
+    if (pre) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int a = pa8[q], bb = pb8[q];
+            const T pj = (a == bb) ? ec[a] : T(0.5) * (ec[a] + ec[bb]);
+            ax = fma(av8[q], x[js8[q]] + pj, ax);
+        }
+        const T xi = x[i] + ((pi0 == pi1) ? ec[pi0] : T(0.5) * (ec[pi0] + ec[pi1]));
+        xout[i] = fma(omega * di, b[i] - ax, xi);
+        return;
+    }
     const int32_t *c = col + size_t(i) * W;
     const T *arow = A + size_t(i) * W;
 #pragma unroll 2
@@ -286,16 +341,14 @@ __device__ __forceinline__ void up_kernel_impl(int bid_, int nb_, int nf, int W,
             ax = fma(av[u], x[j] + pj, ax);
         }
     }
-    const int a = parent[2 * i], bb = parent[2 * i + 1];
-    const T xi = x[i] + ((a == bb) ? ec[a] : T(0.5) * (ec[a] + ec[bb]));
-    xout[i] = fma(omega * dinv[i], b[i] - ax, xi);
+    const T xi = x[i] + ((pi0 == pi1) ? ec[pi0] : T(0.5) * (ec[pi0] + ec[pi1]));
+    xout[i] = fma(omega * di, b[i] - ax, xi);
 }
 template <typename T>
 __global__ void up_kernel(int nf, int W, const int32_t *__restrict__ col, const T *__restrict__ A,
                           const T *__restrict__ dinv, const T *__restrict__ b, const T *__restrict__ x,
                           const int32_t *__restrict__ parent, const T *__restrict__ ec, T *__restrict__ xout,
                           T omega) {
-    pdl_wait();
     up_kernel_impl<T>(blockIdx.x, gridDim.x, nf, W, col, A, dinv, b, x, parent, ec, xout, omega);
 }
 template <typename T>
@@ -315,7 +368,6 @@ struct up_kernel_args {
 };
 template <typename T>
 __global__ void up_kernel_multi(const __grid_constant__ MultiP<up_kernel_args<T>> M) {
-    pdl_wait();
     int b_;
     const up_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     up_kernel_impl<T>(b_, q_.nb_, q_.nf, q_.W, q_.col, q_.A, q_.dinv, q_.b, q_.x, q_.parent, q_.ec, q_.xout,
@@ -453,17 +505,23 @@ __device__ __forceinline__ void down_fused_kernel_impl(int bid_, int nb_, const 
         }
     }
     T av[W];
-    T bv = T(0);
+    T bv = T(0), dv = T(0);
     if (row) {
 #pragma unroll
         for (int g = 0; g < WQ; ++g) load4(A + size_t(v) * W + 4 * g, av + 4 * g);
+        dv = dinv[v];
+    }
+    // everything above is static (patch maps, operator rows): the vectors of
+    // the previous kernel only from here on
+    pdl_wait();
+    if (row) {
         bv = b[v];
         T ax = T(0);
 #pragma unroll
         for (int g = 0; g < WQ; ++g)
 #pragma unroll
             for (int u = 0; u < 4; ++u) ax = fma(av[4 * g + u], x[cget(cols[g], u)], ax);
-        const T xn = fma(omega * dinv[v], bv - ax, x[v]);
+        const T xn = fma(omega * dv, bv - ax, x[v]);
         xs[s] = xn;
         if (row0) xout[v] = xn;
     }
@@ -507,7 +565,6 @@ __global__ void __launch_bounds__(kPatchThreads<T>, 1) down_fused_kernel(const i
                                                                          const T *__restrict__ dinv_c, T omega,
                                                                          T *__restrict__ bc, T *__restrict__ xc,
                                                                          int max_f1) {
-    pdl_wait();
     down_fused_kernel_impl<T, WQ>(blockIdx.x, gridDim.x, f_ptr, f_n0, f_ids, f0_base, lcol, fcol, c_ptr, c_ids,
         cc_ptr, cc_slot, cc_w, A, dinv, b, x, xout, dinv_c, omega, bc, xc, max_f1);
 }
@@ -538,7 +595,6 @@ struct down_fused_kernel_args {
 };
 template <typename T, int WQ>
 __global__ void __launch_bounds__(kPatchThreads<T>, 1) down_fused_kernel_multi(const __grid_constant__ MultiP<down_fused_kernel_args<T, WQ>> M) {
-    pdl_wait();
     int b_;
     const down_fused_kernel_args<T, WQ> &q_ = M.a[merge_find(M.start, M.n, b_)];
     down_fused_kernel_impl<T, WQ>(b_, q_.nb_, q_.f_ptr, q_.f_n0, q_.f_ids, q_.f0_base, q_.lcol, q_.fcol, q_.c_ptr,
@@ -634,8 +690,13 @@ __device__ __forceinline__ void up_fused_kernel_impl(int bid_, int nb_, const in
     if (row) {
 #pragma unroll
         for (int g = 0; g < WQ; ++g) load4(A + size_t(v) * W + 4 * g, av + 4 * g);
-        bv = b[v];
         wv = omega * dinv[v];
+    }
+    // everything above is static (patch maps, operator rows): the vectors of
+    // the previous kernels only from here on
+    pdl_wait();
+    if (row) {
+        bv = b[v];
         T ax = T(0);
 #pragma unroll
         for (int g = 0; g < WQ; ++g)
@@ -674,7 +735,6 @@ __global__ void __launch_bounds__(kPatchThreads<T>, 1) up_fused_kernel(const int
                                                                        const T *__restrict__ x,
                                                                        const T *__restrict__ ec, T *__restrict__ xout,
                                                                        T omega) {
-    pdl_wait();
     up_fused_kernel_impl<T, WQ>(blockIdx.x, gridDim.x, g_ptr, g_nown, g_ids, g0_base, glcol, gcol, gpar, grow_par, A,
         dinv, b, x, ec, xout, omega);
 }
@@ -699,7 +759,6 @@ struct up_fused_kernel_args {
 };
 template <typename T, int WQ>
 __global__ void __launch_bounds__(kPatchThreads<T>, 1) up_fused_kernel_multi(const __grid_constant__ MultiP<up_fused_kernel_args<T, WQ>> M) {
-    pdl_wait();
     int b_;
     const up_fused_kernel_args<T, WQ> &q_ = M.a[merge_find(M.start, M.n, b_)];
     up_fused_kernel_impl<T, WQ>(b_, q_.nb_, q_.g_ptr, q_.g_nown, q_.g_ids, q_.g0_base, q_.glcol, q_.gcol, q_.gpar,
@@ -875,6 +934,10 @@ __device__ __forceinline__ void tail_kernel_impl(int bid_, int nb_, TailArgs a) 
         const uint32_t o = uint32_t(tid) * kChunk;
         if (o < a.img_bytes) bulk_g2s(tail_smem + o, a.img + o, min(kChunk, a.img_bytes - o), &bar);
     }
+    // the image is static: its copies are issued before the wait for the
+    // previous kernel, whose output (the first level's right-hand side) is read
+    // only after it
+    pdl_wait();
     const T om = T(a.omega);
     auto PT = [&](int32_t o) { return reinterpret_cast<T *>(tail_smem + o); };
     auto PI = [&](int32_t o) { return reinterpret_cast<int32_t *>(tail_smem + o); };
@@ -973,7 +1036,6 @@ __device__ __forceinline__ void tail_kernel_impl(int bid_, int nb_, TailArgs a) 
 }
 template <typename T>
 __global__ void __launch_bounds__(1024, 1) tail_kernel(TailArgs a) {
-    pdl_wait();
     tail_kernel_impl<T>(blockIdx.x, gridDim.x, a);
 }
 template <typename T>
@@ -983,7 +1045,6 @@ struct tail_kernel_args {
 };
 template <typename T>
 __global__ void __launch_bounds__(1024, 1) tail_kernel_multi(const __grid_constant__ MultiP<tail_kernel_args<T>> M) {
-    pdl_wait();
     int b_;
     const tail_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     tail_kernel_impl<T>(b_, q_.nb_, q_.a);
