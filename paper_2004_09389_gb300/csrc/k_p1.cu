@@ -200,9 +200,38 @@ __device__ __forceinline__ void down_kernel_impl(int bid_, int nb_, int nc, cons
                                                  T *__restrict__ xc) {
     const int gid = (bid_ * blockDim.x + threadIdx.x) >> 3, lane = threadIdx.x & 7;
     const bool valid = gid < nc;
+    // the lane's first child row (static: index, weight, columns, values)
+    // before the wait for the previous kernel, the vectors after it
+    int k0 = 0, k1 = 0, f0 = 0, cs[8];
+    T w0 = T(0), av[8];
+    bool pre = false;
+    if (valid) {
+        k0 = cp[gid] + lane;
+        k1 = cp[gid + 1];
+        if (k0 < k1 && W == 8) {
+            pre = true;
+            f0 = ci[k0];
+            w0 = cw[k0];
+            const int4 c0 = *reinterpret_cast<const int4 *>(col + size_t(f0) * 8);
+            const int4 c1 = *reinterpret_cast<const int4 *>(col + size_t(f0) * 8 + 4);
+            cs[0] = c0.x; cs[1] = c0.y; cs[2] = c0.z; cs[3] = c0.w;
+            cs[4] = c1.x; cs[5] = c1.y; cs[6] = c1.z; cs[7] = c1.w;
+            load4(A + size_t(f0) * 8, av);
+            load4(A + size_t(f0) * 8 + 4, av + 4);
+        }
+    }
+    pdl_wait();
     T acc = T(0);
     if (valid) {
-        for (int k = cp[gid] + lane; k < cp[gid + 1]; k += 8) {
+        int k = k0;
+        if (pre) {
+            T ax = T(0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) ax = fma(av[q], xf[cs[q]], ax);
+            acc = fma(w0, bf[f0] - ax, acc);
+            k += 8;
+        }
+        for (; k < k1; k += 8) {
             const int f = ci[k];
             acc = fma(cw[k], bf[f] - ell_row(f, W, col, A, xf), acc);
         }
@@ -222,7 +251,6 @@ __global__ void __launch_bounds__(256) down_kernel(int nc, const int32_t *__rest
                                                    const T *__restrict__ bf, const T *__restrict__ xf,
                                                    const T *__restrict__ dinv_c, T omega, T *__restrict__ bc,
                                                    T *__restrict__ xc) {
-    pdl_wait();
     down_kernel_impl<T>(blockIdx.x, gridDim.x, nc, cp, ci, cw, nf, W, col, A, bf, xf, dinv_c, omega, bc, xc);
 }
 template <typename T>
@@ -245,7 +273,6 @@ struct down_kernel_args {
 };
 template <typename T>
 __global__ void __launch_bounds__(256) down_kernel_multi(const __grid_constant__ MultiP<down_kernel_args<T>> M) {
-    pdl_wait();
     int b_;
     const down_kernel_args<T> &q_ = M.a[merge_find(M.start, M.n, b_)];
     down_kernel_impl<T>(b_, q_.nb_, q_.nc, q_.cp, q_.ci, q_.cw, q_.nf, q_.W, q_.col, q_.A, q_.bf, q_.xf, q_.dinv_c,
