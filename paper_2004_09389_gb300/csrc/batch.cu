@@ -78,7 +78,7 @@ void copy_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t 
         q_.dst = dst;
         q_.src = src;
         q_.n = n;
-        batch_record(r_, reinterpret_cast<const void *>(&copy_kernel_multi), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&copy_kernel_multi), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &copy_kernel, grid_, block_, smem_, s_, dst, src, n);
@@ -207,10 +207,24 @@ cudaError_t WaveRunner::build(Recorder *const *recs, int n, Entry &out) {
             kp.kernelParams = kargs;
             kp.extra = nullptr;
             cudaGraphNode_t node = nullptr;
-            if ((e = cudaGraphAddKernelNode(&node, g, deps.data(), deps.size(), &kp)) != cudaSuccess) {
+            if ((e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &kp)) != cudaSuccess) {
                 cudaGraphDestroy(g);
                 return e;
             }
+            // edges from the launches that hold the same problems' previous
+            // records: programmatic for the families launched that way in
+            // single solves (the merged kernels wait for their predecessors in
+            // griddepcontrol.wait), full dependencies otherwise
+            cudaGraphEdgeData ed{};
+            if (pdl_enabled(r0->family)) {
+                ed.from_port = cudaGraphKernelNodePortProgrammatic;
+                ed.type = cudaGraphDependencyTypeProgrammatic;
+            }
+            for (cudaGraphNode_t d : deps)
+                if ((e = cudaGraphAddDependencies(g, &d, &node, &ed, 1)) != cudaSuccess) {
+                    cudaGraphDestroy(g);
+                    return e;
+                }
             out.nodes += 1;
             out.records += m;
             for (int q = 0; q < m; ++q) {

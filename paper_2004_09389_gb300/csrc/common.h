@@ -439,6 +439,8 @@ struct MergeRec {
     unsigned grid, block;         // this problem's launch shape
     size_t smem;
     size_t off;                   // the arguments, in the recorder's arena
+    unsigned family;              // the kernel's launch family (pdl_launch): a merged launch of an
+                                  // enabled family depends on its predecessors by programmatic edges
 };
 struct Recorder {
     std::vector<MergeRec> recs;
@@ -464,9 +466,10 @@ void merge_pack(void *out, int n, const int *start, const unsigned char *const *
 // a (built in zeroed storage, so that its padding bytes are zero and two
 // records of the same launch compare equal byte for byte)
 template <class A>
-void batch_record(Recorder *r, const void *func, const A &a, unsigned grid, unsigned block, size_t smem) {
+void batch_record(Recorder *r, const void *func, const A &a, unsigned grid, unsigned block, size_t smem,
+                  unsigned family) {
     MergeRec m{func, &merge_pack<A>, uint32_t(sizeof(MultiP<A>)), uint32_t(sizeof(A)), grid, block, smem,
-               r->arena.size()};
+               r->arena.size(), family};
     const unsigned char *p = reinterpret_cast<const unsigned char *>(&a);
     r->arena.insert(r->arena.end(), p, p + sizeof(A));
     r->recs.push_back(m);

@@ -117,7 +117,7 @@ void axpby_split_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaSt
         q_.d = d;
         q_.scale = scale;
         q_.n = n;
-        batch_record(r_, reinterpret_cast<const void *>(&axpby_split_kernel_multi), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&axpby_split_kernel_multi), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &axpby_split_kernel, grid_, block_, smem_, s_, x, x2, d, scale, n);
@@ -197,7 +197,7 @@ void residual_ff_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaSt
         q_.b = b;
         q_.x2 = x2;
         q_.res = res;
-        batch_record(r_, reinterpret_cast<const void *>(&residual_ff_kernel_multi<P>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&residual_ff_kernel_multi<P>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &residual_ff_kernel<P>, grid_, block_, smem_, s_, NF, S2, nbr, b, x2, res);
@@ -286,7 +286,7 @@ void rhs_cell_ff_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaSt
         q_.ycell = ycell;
         q_.cu = cu;
         q_.ch = ch;
-        batch_record(r_, reinterpret_cast<const void *>(&rhs_cell_ff_kernel_multi<P>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&rhs_cell_ff_kernel_multi<P>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &rhs_cell_ff_kernel<P>, grid_, block_, smem_, s_, N, W2, r_u, r_h, ycell, cu, ch);

@@ -136,7 +136,7 @@ void dot1_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t 
         q_.seq = seq;
         q_.root_a = root_a;
         q_.root_b = root_b;
-        batch_record(r_, reinterpret_cast<const void *>(&dot1_kernel_multi<T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&dot1_kernel_multi<T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &dot1_kernel<T>, grid_, block_, smem_, s_, v, w, n, partial, nchunk, counter, out, pub, seq, root_a, root_b);
@@ -219,7 +219,7 @@ void multi_axpy_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         q_.coef = coef;
         q_.sign = sign;
         q_.n = n;
-        batch_record(r_, reinterpret_cast<const void *>(&multi_axpy_kernel_multi<T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&multi_axpy_kernel_multi<T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &multi_axpy_kernel<T>, grid_, block_, smem_, s_, w, V, ld, k, coef, sign, n);
@@ -302,7 +302,7 @@ void scale_copy_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         q_.v = v;
         q_.denom = denom;
         q_.n = n;
-        batch_record(r_, reinterpret_cast<const void *>(&scale_copy_kernel_multi<T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&scale_copy_kernel_multi<T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &scale_copy_kernel<T>, grid_, block_, smem_, s_, w, v, denom, n);
@@ -359,7 +359,7 @@ void hessenberg_solve_kernel_go(unsigned grid_, unsigned block_, size_t smem_, c
         q_.sv = sv;
         q_.k = k;
         q_.y = y;
-        batch_record(r_, reinterpret_cast<const void *>(&hessenberg_solve_kernel_multi), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&hessenberg_solve_kernel_multi), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &hessenberg_solve_kernel, grid_, block_, smem_, s_, Hm, ldh, sv, k, y);
@@ -399,7 +399,7 @@ void fill_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t 
         q_.x = x;
         q_.v = v;
         q_.n = n;
-        batch_record(r_, reinterpret_cast<const void *>(&fill_kernel_multi<T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&fill_kernel_multi<T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &fill_kernel<T>, grid_, block_, smem_, s_, x, v, n);
@@ -440,7 +440,7 @@ void d2f_scaled_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         q_.y = y;
         q_.scale = scale;
         q_.n = n;
-        batch_record(r_, reinterpret_cast<const void *>(&d2f_scaled_kernel_multi), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&d2f_scaled_kernel_multi), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &d2f_scaled_kernel, grid_, block_, smem_, s_, x, y, scale, n);
@@ -736,7 +736,7 @@ void gs_update_norm_givens_kernel_go(unsigned grid_, unsigned block_, size_t sme
         q_.bnorm = bnorm;
         q_.rb = rb;
         q_.host_rb = host_rb;
-        batch_record(r_, reinterpret_cast<const void *>(&gs_update_norm_givens_kernel_multi<T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&gs_update_norm_givens_kernel_multi<T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &gs_update_norm_givens_kernel<T>, grid_, block_, smem_, s_, V, ld, k, w, n, h1, h2, partial, counter, nrm2, Hm,
@@ -786,7 +786,7 @@ void gs_scale_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStrea
         q_.v = v;
         q_.n = n;
         q_.rb = rb;
-        batch_record(r_, reinterpret_cast<const void *>(&gs_scale_kernel_multi<T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&gs_scale_kernel_multi<T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &gs_scale_kernel<T>, grid_, block_, smem_, s_, w, v, n, rb);

@@ -130,7 +130,7 @@ void jacobi_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_
         q_.xout = xout;
         q_.omega = omega;
         q_.first = first;
-        batch_record(r_, reinterpret_cast<const void *>(&jacobi_kernel_multi<T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&jacobi_kernel_multi<T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &jacobi_kernel<T>, grid_, block_, smem_, s_, n, W, col, A, dinv, b, x, xout, omega, first);
@@ -177,7 +177,7 @@ void prolong_add_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaSt
         q_.parent = parent;
         q_.ec = ec;
         q_.xf = xf;
-        batch_record(r_, reinterpret_cast<const void *>(&prolong_add_kernel_multi<T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&prolong_add_kernel_multi<T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &prolong_add_kernel<T>, grid_, block_, smem_, s_, nf, parent, ec, xf);
@@ -300,7 +300,7 @@ void down_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t 
         q_.omega = omega;
         q_.bc = bc;
         q_.xc = xc;
-        batch_record(r_, reinterpret_cast<const void *>(&down_kernel_multi<T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&down_kernel_multi<T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &down_kernel<T>, grid_, block_, smem_, s_, nc, cp, ci, cw, nf, W, col, A, bf, xf, dinv_c, omega, bc, xc);
@@ -419,7 +419,7 @@ void up_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_
         q_.ec = ec;
         q_.xout = xout;
         q_.omega = omega;
-        batch_record(r_, reinterpret_cast<const void *>(&up_kernel_multi<T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&up_kernel_multi<T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &up_kernel<T>, grid_, block_, smem_, s_, nf, W, col, A, dinv, b, x, parent, ec, xout, omega);
@@ -659,7 +659,7 @@ void down_fused_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         q_.bc = bc;
         q_.xc = xc;
         q_.max_f1 = max_f1;
-        batch_record(r_, reinterpret_cast<const void *>(&down_fused_kernel_multi<T, WQ>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&down_fused_kernel_multi<T, WQ>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &down_fused_kernel<T, WQ>, grid_, block_, smem_, s_, f_ptr, f_n0, f_ids, f0_base, lcol, fcol, c_ptr, c_ids,
@@ -815,7 +815,7 @@ void up_fused_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStrea
         q_.ec = ec;
         q_.xout = xout;
         q_.omega = omega;
-        batch_record(r_, reinterpret_cast<const void *>(&up_fused_kernel_multi<T, WQ>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&up_fused_kernel_multi<T, WQ>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &up_fused_kernel<T, WQ>, grid_, block_, smem_, s_, g_ptr, g_nown, g_ids, g0_base, glcol, gcol, gpar, grow_par,
@@ -932,7 +932,7 @@ void coarse_dense_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaS
         q_.n = n;
         q_.b = b;
         q_.x = x;
-        batch_record(r_, reinterpret_cast<const void *>(&coarse_dense_kernel_multi<T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&coarse_dense_kernel_multi<T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &coarse_dense_kernel<T>, grid_, block_, smem_, s_, inv, n, b, x);
@@ -1083,7 +1083,7 @@ void tail_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t 
         std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
         q_.nb_ = int(grid_);
         q_.a = a;
-        batch_record(r_, reinterpret_cast<const void *>(&tail_kernel_multi<T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&tail_kernel_multi<T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &tail_kernel<T>, grid_, block_, smem_, s_, a);

@@ -250,7 +250,7 @@ void apply_dots_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         q_.partial = partial;
         q_.counter = counter;
         q_.h = h;
-        batch_record(r_, reinterpret_cast<const void *>(&apply_dots_kernel_multi<P, T, ST>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&apply_dots_kernel_multi<P, T, ST>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &apply_dots_kernel<P, T, ST>, grid_, block_, smem_, s_, NF, Sval, nbr, x, y, V, ld, k, partial, counter, h);
@@ -308,7 +308,7 @@ void residual_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStrea
         q_.b = b;
         q_.x = x;
         q_.res = res;
-        batch_record(r_, reinterpret_cast<const void *>(&residual_kernel_multi<P, T, ST>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&residual_kernel_multi<P, T, ST>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &residual_kernel<P, T, ST>, grid_, block_, smem_, s_, NF, Sval, nbr, b, x, res);
@@ -394,7 +394,7 @@ void smooth_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_
         q_.omega = omega;
         q_.beta = beta;
         q_.xprev = xprev;
-        batch_record(r_, reinterpret_cast<const void *>(&smooth_kernel_multi<P, T, ST, CHEB>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&smooth_kernel_multi<P, T, ST, CHEB>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &smooth_kernel<P, T, ST, CHEB>, grid_, block_, smem_, s_, NF, Sval, Dinv, nbr, b, x, xout, omega, beta, xprev);
@@ -498,7 +498,7 @@ void smooth_prolong_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cud
         q_.xout = xout;
         q_.omega = omega;
         q_.x0out = x0out;
-        batch_record(r_, reinterpret_cast<const void *>(&smooth_prolong_kernel_multi<P, T, ST, X0>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&smooth_prolong_kernel_multi<P, T, ST, X0>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &smooth_prolong_kernel<P, T, ST, X0>, grid_, block_, smem_, s_, NF, Sval, Dinv, nbr, fverts, ec, b, x, xout,
@@ -580,7 +580,7 @@ void smooth_first_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaS
         q_.w = w;
         q_.hnext = hnext;
         q_.bout = bout;
-        batch_record(r_, reinterpret_cast<const void *>(&smooth_first_kernel_multi<P, T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&smooth_first_kernel_multi<P, T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &smooth_first_kernel<P, T>, grid_, block_, smem_, s_, NF, Dinv, b, xout, omega, w, hnext, bout);
@@ -646,7 +646,7 @@ void to_external_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaSt
         q_.PP = PP;
         q_.in = in;
         q_.ext = ext;
-        batch_record(r_, reinterpret_cast<const void *>(&to_external_kernel_multi), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&to_external_kernel_multi), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &to_external_kernel, grid_, block_, smem_, s_, NF, PP, in, ext);
@@ -736,7 +736,7 @@ void rhs_gather_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         q_.fedge = fedge;
         q_.flip = flip;
         q_.g = g;
-        batch_record(r_, reinterpret_cast<const void *>(&rhs_gather_kernel_multi<P>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&rhs_gather_kernel_multi<P>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &rhs_gather_kernel<P>, grid_, block_, smem_, s_, N, NF, ycell, fcell, fedge, flip, g);
@@ -835,7 +835,7 @@ void restrict_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStrea
         q_.dinv0 = dinv0;
         q_.omega = omega;
         q_.x0 = x0;
-        batch_record(r_, reinterpret_cast<const void *>(&restrict_kernel_multi<P, T>), q_, grid_, block_, smem_);
+        batch_record(r_, reinterpret_cast<const void *>(&restrict_kernel_multi<P, T>), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &restrict_kernel<P, T>, grid_, block_, smem_, s_, nv, NF, v2f_ptr, v2f, r, rc, dinv0, omega, x0);
