@@ -148,3 +148,41 @@ def test_merged_batch_refuses_unsupported_handles():
     b.close()
     s.close()
     s64.close()
+
+
+def test_merged_batch_reports_failing_problems():
+    """A problem that stops on its iteration limit and one with a NaN in its
+    right-hand side report HDG_ENOCONV / HDG_ENAN through their info entries;
+    the batch returns the first failure in problem order, and the other
+    problems finish exactly as their own solves do."""
+    from paper_2004_09389_gb300 import HDGError, HDGSolver, MergedBatch
+    from paper_2004_09389_gb300 import _lib as L
+    probs = _problems()[:4]
+    solvers = [_solver(x) for x in probs]
+    probs[1] = dict(probs[1])
+    solvers[1].close()
+    x1 = probs[1]
+    solvers[1] = HDGSolver(x1["mesh"], x1["p"], x1["tau"], 1.0, 1.0, f_vertex=x1["f"], rtol=1e-10,
+                           precision=x1["precision"], smoother=x1["smoother"], max_iter=2)
+    ru = [torch.from_numpy(x["ru"]).cuda() for x in probs]
+    rh = [torch.from_numpy(x["rh"]).cuda() for x in probs]
+    rh[3] = rh[3].clone()
+    rh[3][0, 0] = float("nan")
+    single = []
+    for k in (0, 2):
+        lam = torch.zeros((solvers[k].n_facets, solvers[k].p + 1), dtype=torch.float64, device="cuda")
+        solvers[k].solve_dev(ru[k], rh[k], lam)
+        single.append(lam)
+    lam = [torch.zeros((s.n_facets, s.p + 1), dtype=torch.float64, device="cuda") for s in solvers]
+    b = MergedBatch(solvers)
+    with pytest.raises(HDGError) as ei:
+        b.solve_dev(ru, rh, lam)
+    assert ei.value.code == L.HDG_ENOCONV and "batch entry 1" in str(ei.value)
+    infos = b.solve_dev(ru, rh, lam, allow_fail=True)
+    assert infos[1]["status"] == L.HDG_ENOCONV
+    assert infos[3]["status"] == L.HDG_ENAN
+    assert infos[0]["status"] == 0 and infos[2]["status"] == 0
+    assert torch.equal(lam[0], single[0]) and torch.equal(lam[2], single[1])
+    b.close()
+    for s in solvers:
+        s.close()
