@@ -284,6 +284,13 @@ typedef struct hdg_batch hdg_batch;
 HDG_API int hdg_batch_create(hdg_handle *const *hs, int n, hdg_batch **out);
 HDG_API int hdg_batch_solve_dev(hdg_batch *b, const double *const *r_u, const double *const *r_h,
                                 double *const *lambda, hdg_solve_info *infos);
+/* The same with host buffers (r_u[i], r_h[i] in, lambda[i] out, layouts as for
+ * hdg_solve): the right-hand sides are copied to each handle's staging buffers
+ * on its stream, the merged solve runs on them, and lambda is copied back
+ * before the call returns; hdg_recover with NULL right-hand sides then uses
+ * this solve's.  Return values as hdg_batch_solve_dev. */
+HDG_API int hdg_batch_solve(hdg_batch *b, const double *const *r_u, const double *const *r_h, double *const *lambda,
+                            hdg_solve_info *infos);
 HDG_API int hdg_batch_stats(const hdg_batch *b, int64_t *stats);
 HDG_API int hdg_batch_destroy(hdg_batch *b);
 

@@ -70,7 +70,7 @@ EXPORTS = ["hdg_default_params", "hdg_setup", "hdg_condense", "hdg_set_tau", "hd
            "hdg_learned_collect_dev", "hdg_learned_train", "hdg_learned_params", "hdg_learned_enable",
            "hdg_learned_loss_grad_dev", "hdg_precond_apply32_dev", "hdg_fma_rate",
            "hdg_imex_init", "hdg_imex_rates_dev", "hdg_imex_step_dev", "hdg_get_chebyshev",
-           "hdg_get_rt0_chebyshev", "hdg_batch_create", "hdg_batch_solve_dev", "hdg_batch_stats",
+           "hdg_get_rt0_chebyshev", "hdg_batch_create", "hdg_batch_solve_dev", "hdg_batch_solve", "hdg_batch_stats",
            "hdg_batch_destroy"]
 
 HDG_PROF_N = 16
@@ -108,6 +108,7 @@ def load() -> C.CDLL:
     lib.hdg_solve_batch_dev.argtypes = [vp, C.c_int, vp, vp, vp, C.POINTER(hdg_solve_info), C.c_int]
     lib.hdg_batch_create.argtypes = [vp, C.c_int, C.POINTER(vp)]
     lib.hdg_batch_solve_dev.argtypes = [vp, vp, vp, vp, C.POINTER(hdg_solve_info)]
+    lib.hdg_batch_solve.argtypes = [vp, vp, vp, vp, C.POINTER(hdg_solve_info)]
     lib.hdg_batch_stats.argtypes = [vp, C.POINTER(C.c_int64)]
     lib.hdg_batch_destroy.argtypes = [vp]
     lib.hdg_autotune.argtypes = [vp, vp]

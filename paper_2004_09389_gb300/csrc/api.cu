@@ -2562,6 +2562,47 @@ int hdg_batch_solve_dev(hdg_batch *b, const double *const *r_u, const double *co
     return first_rc;
 }
 
+int hdg_batch_solve(hdg_batch *b, const double *const *r_u, const double *const *r_h, double *const *lambda,
+                    hdg_solve_info *infos) {
+    if (!b) return fail(nullptr, HDG_EINVAL, "batch is NULL");
+    if (!r_u || !r_h || !lambda) return fail(nullptr, HDG_EINVAL, "NULL pointer argument");
+    const int n = int(b->hs.size());
+    std::vector<const double *> du(static_cast<size_t>(n)), dh(static_cast<size_t>(n));
+    std::vector<double *> dl(static_cast<size_t>(n));
+    for (int i = 0; i < n; ++i) {
+        hdg_handle *h = b->hs[size_t(i)];
+        const std::string at = "batch entry " + std::to_string(i) + ": ";
+        if (!r_u[i] || !r_h[i] || !lambda[i]) return fail(nullptr, HDG_EINVAL, at + "NULL pointer argument");
+        if (!h->condensed) return fail(nullptr, HDG_ESTATE, at + "hdg_condense has not run on this handle");
+        if (ensure_staging(h)) return fail(nullptr, HDG_ECUDA, at + h->err);
+        Workspace &W = *h->ws;
+        cudaError_t e = cudaMemcpyAsync(W.ru, r_u[i], sizeof(double) * size_t(h->N) * 2 * h->np,
+                                        cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(W.rh, r_h[i], sizeof(double) * size_t(h->N) * h->np, cudaMemcpyHostToDevice,
+                                h->stream);
+        if (e != cudaSuccess) return fail(nullptr, HDG_ECUDA, at + "staging copy: " + cudaGetErrorString(e));
+        du[size_t(i)] = W.ru;
+        dh[size_t(i)] = W.rh;
+        dl[size_t(i)] = W.lam_ext;
+    }
+    const int rc = hdg_batch_solve_dev(b, du.data(), dh.data(), dl.data(), infos);
+    if (rc == HDG_ECUDA) return rc;
+    const std::string msg = rc ? g_setup_error : std::string();
+    for (int i = 0; i < n; ++i) {
+        hdg_handle *h = b->hs[size_t(i)];
+        Workspace &W = *h->ws;
+        cudaError_t e = cudaMemcpyAsync(lambda[i], W.lam_ext, sizeof(double) * W.NT, cudaMemcpyDeviceToHost,
+                                        h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess)
+            return fail(nullptr, HDG_ECUDA, "batch entry " + std::to_string(i) + ": " + cudaGetErrorString(e));
+        W.have_rhs = true;   // hdg_recover with NULL right-hand sides uses this solve's
+    }
+    if (rc) g_setup_error = msg;
+    return rc;
+}
+
 int hdg_batch_stats(const hdg_batch *b, int64_t *stats) {
     if (!b || !stats) return fail(nullptr, HDG_EINVAL, "NULL pointer argument");
     for (int k = 0; k < 8; ++k) stats[k] = 0;

@@ -307,6 +307,22 @@ class MergedBatch:
             raise L.HDGError(rc, (self.lib.hdg_last_error(None) or b"").decode())
         return [infos[i].as_dict() for i in range(n)]
 
+    def solve(self, r_u, r_h, allow_fail: bool = False):
+        """Host arrays: solver i solves ``r_u[i]`` ([n_cells][2][n_p]), ``r_h[i]``
+        ([n_cells][n_p]); returns (list of lambda arrays [n_facets][p+1], infos)."""
+        n = len(self.solvers)
+        ru = [np.ascontiguousarray(a, dtype=np.float64) for a in r_u]
+        rh = [np.ascontiguousarray(a, dtype=np.float64) for a in r_h]
+        lam = [np.empty((s.n_facets, s.p + 1)) for s in self.solvers]
+        pu = (C.c_void_p * n)(*[a.ctypes.data for a in ru])
+        ph = (C.c_void_p * n)(*[a.ctypes.data for a in rh])
+        pl = (C.c_void_p * n)(*[a.ctypes.data for a in lam])
+        infos = (L.hdg_solve_info * n)()
+        rc = self.lib.hdg_batch_solve(self.b, pu, ph, pl, infos)
+        if rc != 0 and not (allow_fail and rc in (L.HDG_ENOCONV, L.HDG_EBREAKDOWN)):
+            raise L.HDGError(rc, (self.lib.hdg_last_error(None) or b"").decode())
+        return lam, [infos[i].as_dict() for i in range(n)]
+
     def stats(self) -> dict:
         """Waves, merged launches, per-problem launches they carried, graphs
         replayed and graphs built since creation; host nanoseconds spent

@@ -74,6 +74,11 @@ def test_merged_batch_bit_identical_and_oracle():
     # the same output buffers both times: the waves (whose records carry
     # every argument, these pointers included) recur exactly
     lam = [torch.empty((s.n_facets, s.p + 1), dtype=torch.float64, device="cuda") for s in solvers]
+    # host buffers: the same bits through the staging copies
+    lam_h, infos_h = batch.solve([x["ru"] for x in probs], [x["rh"] for x in probs])
+    for i, (l, l0, info, info0) in enumerate(zip(lam_h, single, infos_h, single_info)):
+        assert np.array_equal(l, l0.cpu().numpy()), i
+        assert info["iters"] == info0["iters"], i
     st = []
     for rep in range(2):
         for l in lam:
@@ -85,8 +90,8 @@ def test_merged_batch_bit_identical_and_oracle():
             assert info["iters"] == info0["iters"], (rep, i)
             assert info["true_rel_res"] == info0["true_rel_res"], (rep, i)
             assert info["true_rel_res"] <= 1e-10
-    # the second call replays kept graphs only (a wave can also recur within
-    # one call, e.g. the first Arnoldi step of every refinement pass)
+    # the second device call replays kept graphs only (a wave can also recur
+    # within one call, e.g. the first Arnoldi step of every refinement pass)
     assert st[0]["builds"] > 0 and st[1]["builds"] == st[0]["builds"]
     assert st[1]["replays"] - st[0]["replays"] == st[1]["waves"] - st[0]["waves"] > 0
     assert st[1]["records"] > st[1]["launches"]       # launches of different problems were merged
