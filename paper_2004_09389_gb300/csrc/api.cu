@@ -702,14 +702,10 @@ int wait_host_value(hdg_handle *h, int32_t want) {
 
 // ||v||: the reduction kernel hands the squared norm to the host through
 // page-locked memory (no copy, no stream synchronisation)
-template <typename T>
-int norm_host(hdg_handle *h, const T *v, double &out) {
+// ||v|| from a squared norm that a kernel already launched hands over with
+// sequence number want
+int norm_wait(hdg_handle *h, int32_t want, double &out) {
     Workspace &W = *h->ws;
-    // the previous hand-over was seen, so no write to the word is in flight;
-    // one fixed number keeps the launch arguments the same from call to call
-    W.host_val->seq = 0;
-    const int32_t want = 1;
-    TRY(dots<T>(h, v, 1, v, W.nrm2, W.host_val_dev, want));
     if (h->prof.on) {
         TRY(cudaStreamSynchronize(h->stream));
         prof_flush(h);
@@ -718,6 +714,17 @@ int norm_host(hdg_handle *h, const T *v, double &out) {
     if (rc) return rc;
     out = std::sqrt(W.host_val->v);
     return HDG_OK;
+}
+
+template <typename T>
+int norm_host(hdg_handle *h, const T *v, double &out) {
+    Workspace &W = *h->ws;
+    // the previous hand-over was seen, so no write to the word is in flight;
+    // one fixed number keeps the launch arguments the same from call to call
+    W.host_val->seq = 0;
+    const int32_t want = 1;
+    TRY(dots<T>(h, v, 1, v, W.nrm2, W.host_val_dev, want));
+    return norm_wait(h, want, out);
 }
 
 // One Arnoldi step j of FGMRES: z_j = V(v_j), w = S z_j, classical
@@ -901,10 +908,11 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
 // exact norm goes from the reduction kernel straight into the device scalars
 // that use it (the estimate's denominator, the first basis vector's scale and
 // s_0), and the host keeps the nominal 1 for its bookkeeping, so the solve
-// starts without waiting for the GPU.
+// starts without waiting for the GPU.  norm_ready: the kernel that formed b
+// has already written that norm there.
 template <typename T>
 int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_residual, bool x_zero,
-           hdg_solve_info &info, bool unit_rhs = false) {
+           hdg_solve_info &info, bool unit_rhs = false, bool norm_ready = false) {
     Workspace &W = *h->ws;
     KSpace<T> &k = kspace<T>(h);
     cudaStream_t s = h->stream;
@@ -916,7 +924,8 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
     info.est_rel_res = 0;
     info.true_rel_res = 0;
     if (unit_rhs) {
-        TRY(dots<T>(h, b, 1, b, W.nrm2, nullptr, 0, W.bnorm, W.scal));
+        // (norm_ready: the kernel that formed b already left ||b|| in W.bnorm and W.scal)
+        if (!norm_ready) TRY(dots<T>(h, b, 1, b, W.nrm2, nullptr, 0, W.bnorm, W.scal));
     } else {
         rc = norm_host<T>(h, b, bnorm);
         if (rc) return rc;
@@ -1001,8 +1010,11 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info)
             r = g;
         } else {
             // in two-float arithmetic from the split copy of x kept by the update below
-            TRY(KL(HDG_PROF_RESIDUAL64, 1, launch_residual_ff(h, g, W.x2, W.r)));
-            rc = norm_host<double>(h, W.r, beta);
+            // with its norm in the same pass, handed to the host as norm_host does
+            W.host_val->seq = 0;
+            TRY(KL(HDG_PROF_RESIDUAL64, 1, launch_residual_ff(h, g, W.x2, W.r, W.partial, W.counter, W.nrm2,
+                                                              W.host_val_dev, 1)));
+            rc = norm_wait(h, 1, beta);
             if (rc) return rc;
         }
         info.true_rel_res = beta / bnorm;
@@ -1014,11 +1026,12 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info)
         // b32 = r / ||r||, solve S d = b32 in FP32, x += ||r|| d
         W.host_buf[2] = beta;
         TRY(dcopy(h, W.beta, W.host_buf + 2, sizeof(double), cudaMemcpyHostToDevice));
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_d2f_scaled(r, k.b, W.beta, W.NT, s)));
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<float>(k.x, 0.0f, W.NT, s)));
+        // b32 = r / ||r||, the zero initial guess and ||b32|| (into W.bnorm and W.scal) in one pass
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_d2f_norm(r, k.b, k.x, W.beta, W.NT, W.partial, W.nchunk, W.counter, W.nrm2,
+                                                   W.bnorm, W.scal, s)));
         hdg_solve_info inner{};
         const double inner_tol = std::max(h->prm.inner_rtol, 0.5 * h->prm.rtol * bnorm / beta);
-        rc = fgmres<float>(h, k.b, k.x, inner_tol, h->prm.max_iter - total, false, true, inner, true);
+        rc = fgmres<float>(h, k.b, k.x, inner_tol, h->prm.max_iter - total, false, true, inner, true, true);
         if (rc && rc != HDG_ENOCONV) return rc;
         total += inner.iters;
         info.iters = total;

@@ -709,7 +709,9 @@ cudaError_t launch_split(const double *a, float2 *out, size_t n, cudaStream_t s)
 // [ceil(N/32)][rows][(cols+1)/2][32] (float4)
 cudaError_t launch_split_pairs(const double *a, float2 *out, int rows, int cols, size_t N, cudaStream_t s);
 cudaError_t launch_axpby_split(double *x, float2 *x2, const float *d, const double *scale, size_t n, cudaStream_t s);
-cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2, double *res);
+cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2, double *res,
+                               double *partial = nullptr, unsigned int *counter = nullptr, double *out = nullptr,
+                               HostValue *pub = nullptr, int32_t seq = 0);
 // (r_u, r_h may be device aliases of page-locked host memory; copy_u / copy_h,
 // if non-null, receive a device copy of them)
 cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell,
@@ -792,5 +794,10 @@ cudaError_t launch_scale_round(const double *w, const double *hnext, double *v64
                                cudaStream_t s);
 cudaError_t launch_widen(const float *a, double *b, size_t n, cudaStream_t s);
 cudaError_t launch_d2f_scaled(const double *x, float *y, const double *scale, size_t n, cudaStream_t s);
+// y = float(x / scale[0]), z = 0 and ||y||^2 into out[0] (its root into root_a /
+// root_b), nchunk blocks, deterministic
+cudaError_t launch_d2f_norm(const double *x, float *y, float *z, const double *scale, size_t n, double *partial,
+                            int nchunk, unsigned int *counter, double *out, double *root_a, double *root_b,
+                            cudaStream_t s);
 
 }  // namespace hdg

@@ -126,46 +126,100 @@ void axpby_split_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaSt
 
 // r = b - S x with x given split; S split in the packed FP64 layout (element
 // j of facet e in 16-byte group (j / 2, e), lane j % 2, here two float pairs)
+// sum of a double over the block (fixed tree: warp shuffles, then warp 0 over
+// the warp sums); every thread gets the block's sum in warp 0, the others
+// their warp's
+__device__ __forceinline__ double ff_block_sum(double v) {
+    __shared__ double red[32];
+    __syncthreads();
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    const int nw = blockDim.x / 32;
+    v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    if (warp == 0)
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// res = b - S x in two-float arithmetic (x as split pairs); with partial
+// non-null also ||res||^2: per-thread double sums, block sums, the last block
+// adding the block sums in block order into out[0] and handing the value to
+// the host through pub (the value, a system fence, then seq)
 template <int P>
 __device__ __forceinline__ void residual_ff_kernel_impl(int bid_, int nb_, int NF, const float4 *__restrict__ S2,
                                                         const int32_t *__restrict__ nbr, const double *__restrict__ b,
-                                                        const float2 *__restrict__ x2, double *__restrict__ res) {
+                                                        const float2 *__restrict__ x2, double *__restrict__ res,
+                                                        double *partial, unsigned int *counter, double *out,
+                                                        HostValue *pub, int32_t seq) {
     constexpr int PP = P + 1, NS = 5 * PP * PP, NQ = (NS + 1) / 2;
     const int e = bid_ * blockDim.x + threadIdx.x;
-    if (e >= NF) return;
-    int src[5];
-    src[0] = e;
+    double sq = 0.0;
+    if (e < NF) {
+        int src[5];
+        src[0] = e;
 #pragma unroll
-    for (int q = 1; q < 5; ++q) src[q] = __ldg(nbr + size_t(q - 1) * NF + e);
-    float2 xs[5][PP];
+        for (int q = 1; q < 5; ++q) src[q] = __ldg(nbr + size_t(q - 1) * NF + e);
+        float2 xs[5][PP];
 #pragma unroll
-    for (int q = 0; q < 5; ++q)
+        for (int q = 0; q < 5; ++q)
 #pragma unroll
-        for (int c = 0; c < PP; ++c) xs[q][c] = x2[size_t(c) * NF + src[q]];
-    FFAcc acc[PP];
+            for (int c = 0; c < PP; ++c) xs[q][c] = x2[size_t(c) * NF + src[q]];
+        FFAcc acc[PP];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const float4 v = __ldg(S2 + size_t(q) * NF + e);
-        const float2 a[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+        for (int q = 0; q < NQ; ++q) {
+            const float4 v = __ldg(S2 + size_t(q) * NF + e);
+            const float2 a[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 #pragma unroll
-        for (int g = 0; g < 2; ++g) {
-            const int j = 2 * q + g;
-            if (j < NS) {
-                const int r = j / (5 * PP), rem = j % (5 * PP);
-                acc[r].add(a[g], xs[rem / PP][rem % PP]);
+            for (int g = 0; g < 2; ++g) {
+                const int j = 2 * q + g;
+                if (j < NS) {
+                    const int r = j / (5 * PP), rem = j % (5 * PP);
+                    acc[r].add(a[g], xs[rem / PP][rem % PP]);
+                }
             }
         }
-    }
 #pragma unroll
-    for (int r = 0; r < PP; ++r) res[size_t(r) * NF + e] = b[size_t(r) * NF + e] - acc[r].value();
+        for (int r = 0; r < PP; ++r) {
+            const double rv = b[size_t(r) * NF + e] - acc[r].value();
+            res[size_t(r) * NF + e] = rv;
+            sq = fma(rv, rv, sq);
+        }
+    }
+    if (!partial) return;
+    __shared__ bool last;
+    const double tot = ff_block_sum(sq);
+    if (threadIdx.x == 0) {
+        partial[bid_] = tot;
+        __threadfence();                       // the partial is visible before the count
+        last = atomicAdd(counter, 1u) == unsigned(nb_) - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nb_; i += blockDim.x) a += partial[i];
+    a = ff_block_sum(a);
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        out[0] = a;
+        if (pub) {
+            pub->v = a;
+            __threadfence_system();
+            *reinterpret_cast<volatile int32_t *>(&pub->seq) = seq;
+        }
+    }
 }
 template <int P>
 __global__ void __launch_bounds__(256) residual_ff_kernel(int NF, const float4 *__restrict__ S2,
                                                           const int32_t *__restrict__ nbr,
                                                           const double *__restrict__ b, const float2 *__restrict__ x2,
-                                                          double *__restrict__ res) {
+                                                          double *__restrict__ res, double *partial,
+                                                          unsigned int *counter, double *out, HostValue *pub,
+                                                          int32_t seq) {
     pdl_wait();
-    residual_ff_kernel_impl<P>(blockIdx.x, gridDim.x, NF, S2, nbr, b, x2, res);
+    residual_ff_kernel_impl<P>(blockIdx.x, gridDim.x, NF, S2, nbr, b, x2, res, partial, counter, out, pub, seq);
 }
 template <int P>
 struct residual_ff_kernel_args {
@@ -176,17 +230,24 @@ struct residual_ff_kernel_args {
     const double *b;
     const float2 *x2;
     double *res;
+    double *partial;
+    unsigned int *counter;
+    double *out;
+    HostValue *pub;
+    int32_t seq;
 };
 template <int P>
 __global__ void __launch_bounds__(256) residual_ff_kernel_multi(const __grid_constant__ MultiP<residual_ff_kernel_args<P>> M) {
     pdl_wait();
     int b_;
     const residual_ff_kernel_args<P> &q_ = M.a[merge_find(M.start, M.n, b_)];
-    residual_ff_kernel_impl<P>(b_, q_.nb_, q_.NF, q_.S2, q_.nbr, q_.b, q_.x2, q_.res);
+    residual_ff_kernel_impl<P>(b_, q_.nb_, q_.NF, q_.S2, q_.nbr, q_.b, q_.x2, q_.res, q_.partial, q_.counter, q_.out,
+                               q_.pub, q_.seq);
 }
 template <int P>
 void residual_ff_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int NF, const float4 *S2,
-                           const int32_t *nbr, const double *b, const float2 *x2, double *res) {
+                           const int32_t *nbr, const double *b, const float2 *x2, double *res, double *partial,
+                           unsigned int *counter, double *out, HostValue *pub, int32_t seq) {
     if (Recorder *r_ = batch_recorder()) {
         residual_ff_kernel_args<P> q_;
         std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
@@ -197,10 +258,17 @@ void residual_ff_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaSt
         q_.b = b;
         q_.x2 = x2;
         q_.res = res;
-        batch_record(r_, reinterpret_cast<const void *>(&residual_ff_kernel_multi<P>), q_, grid_, block_, smem_, kPdlFamily);
+        q_.partial = partial;
+        q_.counter = counter;
+        q_.out = out;
+        q_.pub = pub;
+        q_.seq = seq;
+        batch_record(r_, reinterpret_cast<const void *>(&residual_ff_kernel_multi<P>), q_, grid_, block_, smem_,
+                     kPdlFamily);
         return;
     }
-    pdl_launch(kPdlFamily, &residual_ff_kernel<P>, grid_, block_, smem_, s_, NF, S2, nbr, b, x2, res);
+    pdl_launch(kPdlFamily, &residual_ff_kernel<P>, grid_, block_, smem_, s_, NF, S2, nbr, b, x2, res, partial, counter,
+               out, pub, seq);
 }
 
 
@@ -350,9 +418,11 @@ cudaError_t launch_axpby_split(double *x, float2 *x2, const float *d, const doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2, double *res) {
-    HDG_DISPATCH_P(h->p, (residual_ff_kernel_go<P>(blocks(h->NF, 256), 256, 0, h->stream, 
-                             h->NF, reinterpret_cast<const float4 *>(h->d_Sval2), h->d_nbr, b, x2, res)));
+cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2, double *res, double *partial,
+                               unsigned int *counter, double *out, HostValue *pub, int32_t seq) {
+    HDG_DISPATCH_P(h->p, (residual_ff_kernel_go<P>(blocks(h->NF, 256), 256, 0, h->stream, h->NF,
+                                                   reinterpret_cast<const float4 *>(h->d_Sval2), h->d_nbr, b, x2, res,
+                                                   partial, counter, out, pub, seq)));
     return cudaGetLastError();
 }
 

@@ -407,6 +407,94 @@ void fill_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t 
 
 
 // y = float(x / scale[0])
+// b = float(x / scale[0]) and z = 0 on n entries, with ||b||^2 (float sums per
+// thread over a grid-stride range, block sums in double, the last block adding
+// the block sums in block order) into out[0] and its square root into root_a
+// and root_b: an inner solve's right-hand side, its zero initial guess and
+// the norm that starts it, in one pass
+__device__ __forceinline__ void d2f_norm_kernel_impl(int bid_, int nb_, const double *x, float *y, float *z,
+                                                     const double *scale, size_t n, double *partial,
+                                                     unsigned int *counter, double *out, double *root_a,
+                                                     double *root_b) {
+    __shared__ bool last;
+    const double inv = block_recip(scale);
+    float acc = 0.0f;
+    for (size_t i = size_t(bid_) * blockDim.x + threadIdx.x; i < n; i += size_t(nb_) * blockDim.x) {
+        const float v = float(x[i] * inv);
+        y[i] = v;
+        z[i] = 0.0f;
+        acc = fmaf(v, v, acc);
+    }
+    const double tot = block_sum(double(acc));
+    if (threadIdx.x == 0) {
+        partial[bid_] = tot;
+        __threadfence();                       // the partial is visible before the count
+        last = atomicAdd(counter, 1u) == unsigned(nb_) - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nb_; i += blockDim.x) a += partial[i];
+    a = block_sum(a);
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        out[0] = a;
+        const double r = sqrt(a);
+        if (root_a) *root_a = r;
+        if (root_b) *root_b = r;
+    }
+}
+__global__ void __launch_bounds__(256) d2f_norm_kernel(const double *x, float *y, float *z, const double *scale,
+                                                       size_t n, double *partial, unsigned int *counter, double *out,
+                                                       double *root_a, double *root_b) {
+    pdl_wait();
+    d2f_norm_kernel_impl(blockIdx.x, gridDim.x, x, y, z, scale, n, partial, counter, out, root_a, root_b);
+}
+struct d2f_norm_kernel_args {
+    int nb_;
+    const double *x;
+    float *y;
+    float *z;
+    const double *scale;
+    size_t n;
+    double *partial;
+    unsigned int *counter;
+    double *out;
+    double *root_a;
+    double *root_b;
+};
+__global__ void __launch_bounds__(256) d2f_norm_kernel_multi(const __grid_constant__ MultiP<d2f_norm_kernel_args> M) {
+    pdl_wait();
+    int b_;
+    const d2f_norm_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
+    d2f_norm_kernel_impl(b_, q_.nb_, q_.x, q_.y, q_.z, q_.scale, q_.n, q_.partial, q_.counter, q_.out, q_.root_a,
+                         q_.root_b);
+}
+void d2f_norm_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, const double *x, float *y,
+                        float *z, const double *scale, size_t n, double *partial, unsigned int *counter, double *out,
+                        double *root_a, double *root_b) {
+    if (Recorder *r_ = batch_recorder()) {
+        d2f_norm_kernel_args q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.x = x;
+        q_.y = y;
+        q_.z = z;
+        q_.scale = scale;
+        q_.n = n;
+        q_.partial = partial;
+        q_.counter = counter;
+        q_.out = out;
+        q_.root_a = root_a;
+        q_.root_b = root_b;
+        batch_record(r_, reinterpret_cast<const void *>(&d2f_norm_kernel_multi), q_, grid_, block_, smem_, kPdlFamily);
+        return;
+    }
+    pdl_launch(kPdlFamily, &d2f_norm_kernel, grid_, block_, smem_, s_, x, y, z, scale, n, partial, counter, out, root_a,
+               root_b);
+}
+
 __device__ __forceinline__ void d2f_scaled_kernel_impl(int bid_, int nb_, const double *x, float *y,
                                                        const double *scale, size_t n) {
     const double inv = block_recip(scale);
@@ -845,6 +933,12 @@ template <typename T>
 cudaError_t launch_fill(T *x, T v, size_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     fill_kernel_go<T>(blocks(n, 256), 256, 0, s, x, v, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_d2f_norm(const double *x, float *y, float *z, const double *scale, size_t n, double *partial,
+                            int nchunk, unsigned int *counter, double *out, double *root_a, double *root_b,
+                            cudaStream_t s) {
+    d2f_norm_kernel_go(unsigned(nchunk), 256, 0, s, x, y, z, scale, n, partial, counter, out, root_a, root_b);
     return cudaGetLastError();
 }
 cudaError_t launch_d2f_scaled(const double *x, float *y, const double *scale, size_t n, cudaStream_t s) {
