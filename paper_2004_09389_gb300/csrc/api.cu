@@ -912,7 +912,7 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
 // has already written that norm there.
 template <typename T>
 int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_residual, bool x_zero,
-           hdg_solve_info &info, bool unit_rhs = false, bool norm_ready = false) {
+           hdg_solve_info &info, bool unit_rhs = false, bool norm_ready = false, bool norm_pending = false) {
     Workspace &W = *h->ws;
     KSpace<T> &k = kspace<T>(h);
     cudaStream_t s = h->stream;
@@ -927,7 +927,8 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
         // (norm_ready: the kernel that formed b already left ||b|| in W.bnorm and W.scal)
         if (!norm_ready) TRY(dots<T>(h, b, 1, b, W.nrm2, nullptr, 0, W.bnorm, W.scal));
     } else {
-        rc = norm_host<T>(h, b, bnorm);
+        // (norm_pending: the kernel that formed b hands ||b||^2 over with sequence number 1)
+        rc = norm_pending ? norm_wait(h, 1, bnorm) : norm_host<T>(h, b, bnorm);
         if (rc) return rc;
         if (!std::isfinite(bnorm)) return fail(h, HDG_ENAN, "NaN or Inf in the right-hand side");
         if (bnorm == 0.0) {
@@ -990,12 +991,12 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
 }
 
 // FP64 iterative refinement with FP32 inner FGMRES solves
-int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info) {
+int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info, bool norm_pending = false) {
     Workspace &W = *h->ws;
     KSpace<float> &k = W.k32;
     cudaStream_t s = h->stream;
     double bnorm;
-    int rc = norm_host<double>(h, g, bnorm);
+    int rc = norm_pending ? norm_wait(h, 1, bnorm) : norm_host<double>(h, g, bnorm);
     if (rc) return rc;
     info = hdg_solve_info{};
     if (!std::isfinite(bnorm)) return fail(h, HDG_ENAN, "NaN or Inf in the right-hand side");
@@ -1612,14 +1613,22 @@ int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solv
     cudaStream_t s = h->stream;
     h->lc.suspended = false;
     h->lc.fallback = false;
-    if (!mode_ff(h->prm)) TRY(KL(HDG_PROF_RHS, 2, launch_rhs(h, r_u, r_h, W.g, W.ycell)));
-    else TRY(KL(HDG_PROF_RHS, 2, launch_rhs_ff(h, r_u, r_h, W.g, W.ycell, copy_u, copy_h)));
+    // the right-hand side g with ||g|| handed to the host by the same kernel
+    // (upwind flux; the Lax-Friedrichs right-hand side has no such kernel)
+    const bool norm_pending = h->prm.flux == 0;
+    NormOut nrm;
+    if (norm_pending) {
+        W.host_val->seq = 0;   // the previous hand-over was seen
+        nrm = NormOut{W.partial, W.counter, W.nrm2, W.host_val_dev, 1};
+    }
+    if (!mode_ff(h->prm)) TRY(KL(HDG_PROF_RHS, 2, launch_rhs(h, r_u, r_h, W.g, W.ycell, nrm)));
+    else TRY(KL(HDG_PROF_RHS, 2, launch_rhs_ff(h, r_u, r_h, W.g, W.ycell, copy_u, copy_h, nrm)));
     int rc;
     if (mode_krylov64(h->prm)) {
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<double>(W.x, 0.0, W.NT, s)));
-        rc = fgmres<double>(h, W.g, W.x, h->prm.rtol, h->prm.max_iter, true, true, info);
+        rc = fgmres<double>(h, W.g, W.x, h->prm.rtol, h->prm.max_iter, true, true, info, false, false, norm_pending);
     } else {
-        rc = solve_mixed(h, W.g, W.x, info);
+        rc = solve_mixed(h, W.g, W.x, info, norm_pending);
     }
     if (!batch_recorder()) {   // a batched solve checks the status words after its last wave
         int32_t st = 0;

@@ -701,8 +701,19 @@ inline __host__ __device__ size_t packed_index(size_t j, size_t e, size_t NF, si
     return ((j / G) * NF + e) * G + j % G;
 }
 cudaError_t launch_to_external(hdg_handle *h, const double *in, double *ext);
-cudaError_t launch_rhs(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell);
-cudaError_t launch_rhs_gather(hdg_handle *h, const double *ycell, double *g);
+// optional hand-over of ||v||^2 by the kernel that forms v: block partials,
+// the reduction counter, the device result and, with pub non-null, the
+// page-locked word the host polls (sequence number seq)
+struct NormOut {
+    double *partial = nullptr;
+    unsigned int *counter = nullptr;
+    double *out = nullptr;
+    HostValue *pub = nullptr;
+    int32_t seq = 0;
+};
+cudaError_t launch_rhs(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell,
+                       const NormOut &nrm = NormOut());
+cudaError_t launch_rhs_gather(hdg_handle *h, const double *ycell, double *g, const NormOut &nrm = NormOut());
 // two-float versions of the FP64 steps (mixed modes, k_ff.cu)
 cudaError_t launch_split(const double *a, float2 *out, size_t n, cudaStream_t s);
 // a per-cell matrix [rows][cols][N] split into pairs of row entries, tiled by 32 cells:
@@ -715,7 +726,7 @@ cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2,
 // (r_u, r_h may be device aliases of page-locked host memory; copy_u / copy_h,
 // if non-null, receive a device copy of them)
 cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell,
-                          double *copy_u = nullptr, double *copy_h = nullptr);
+                          double *copy_u, double *copy_h, const NormOut &nrm = NormOut());
 cudaError_t launch_recover_ff(hdg_handle *h, const double *r_u, const double *r_h, const double *lam, double *u,
                               double *hout);
 cudaError_t launch_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lam,

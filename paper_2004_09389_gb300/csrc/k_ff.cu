@@ -427,12 +427,12 @@ cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2,
 }
 
 cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell,
-                          double *copy_u, double *copy_h) {
+                          double *copy_u, double *copy_h, const NormOut &nrm) {
     HDG_DISPATCH_P(h->p, (rhs_cell_ff_kernel_go<P>(blocks(h->N, kCells), 128, 0, h->stream, h->N, reinterpret_cast<const float4 *>(h->d_W2), r_u, r_h,
                                                                                                ycell, copy_u, copy_h)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_rhs_gather(h, ycell, g);
+    return launch_rhs_gather(h, ycell, g, nrm);
 }
 
 cudaError_t launch_recover_ff(hdg_handle *h, const double *r_u, const double *r_h, const double *lam, double *u,

@@ -675,33 +675,84 @@ __global__ void rhs_cell_kernel(int N, const double *__restrict__ W, const doubl
 }
 
 // step 1, facet part: g_{e,r} = sum over the two cells of their row of edge i_s
+// sum of a double over the block (fixed tree: warp shuffles, then warp 0 over
+// the warp sums); thread 0 holds the block's sum
+__device__ __forceinline__ double gather_block_sum(double v) {
+    __shared__ double red[32];
+    __syncthreads();
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    const int nw = blockDim.x / 32;
+    v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    if (warp == 0)
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// g on facet e = the two cells' contributions (step 1 of Sec. 4.2); with
+// partial non-null also ||g||^2 (block sums, the last block adding them in
+// block order into out[0] and handing the value to the host through pub)
 template <int P>
 __device__ __forceinline__ void rhs_gather_kernel_impl(int bid_, int nb_, int N, int NF,
                                                        const double *__restrict__ ycell,
                                                        const int32_t *__restrict__ fcell,
                                                        const int32_t *__restrict__ fedge,
-                                                       const int32_t *__restrict__ flip, double *__restrict__ g) {
+                                                       const int32_t *__restrict__ flip, double *__restrict__ g,
+                                                       double *partial, unsigned int *counter, double *out,
+                                                       HostValue *pub, int32_t seq) {
     constexpr int PP = P + 1;
     const int e = bid_ * blockDim.x + threadIdx.x;
-    if (e >= NF) return;
-    double v[PP];
+    double sq = 0.0;
+    if (e < NF) {
+        double v[PP];
 #pragma unroll
-    for (int r = 0; r < PP; ++r) v[r] = 0.0;
+        for (int r = 0; r < PP; ++r) v[r] = 0.0;
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const int K = fcell[2 * e + s], i = fedge[2 * e + s], f = flip[3 * K + i];
+        for (int s = 0; s < 2; ++s) {
+            const int K = fcell[2 * e + s], i = fedge[2 * e + s], f = flip[3 * K + i];
 #pragma unroll
-        for (int r = 0; r < PP; ++r) v[r] += ycell[size_t(i * PP + (f ? P - r : r)) * N + K];
+            for (int r = 0; r < PP; ++r) v[r] += ycell[size_t(i * PP + (f ? P - r : r)) * N + K];
+        }
+#pragma unroll
+        for (int r = 0; r < PP; ++r) {
+            g[size_t(r) * NF + e] = v[r];
+            sq = fma(v[r], v[r], sq);
+        }
     }
-#pragma unroll
-    for (int r = 0; r < PP; ++r) g[size_t(r) * NF + e] = v[r];
+    if (!partial) return;
+    __shared__ bool last;
+    const double tot = gather_block_sum(sq);
+    if (threadIdx.x == 0) {
+        partial[bid_] = tot;
+        __threadfence();                       // the partial is visible before the count
+        last = atomicAdd(counter, 1u) == unsigned(nb_) - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nb_; i += blockDim.x) a += partial[i];
+    a = gather_block_sum(a);
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        out[0] = a;
+        if (pub) {
+            pub->v = a;
+            __threadfence_system();
+            *reinterpret_cast<volatile int32_t *>(&pub->seq) = seq;
+        }
+    }
 }
 template <int P>
 __global__ void rhs_gather_kernel(int N, int NF, const double *__restrict__ ycell, const int32_t *__restrict__ fcell,
                                   const int32_t *__restrict__ fedge, const int32_t *__restrict__ flip,
-                                  double *__restrict__ g) {
+                                  double *__restrict__ g, double *partial, unsigned int *counter, double *out,
+                                  HostValue *pub, int32_t seq) {
     pdl_wait();
-    rhs_gather_kernel_impl<P>(blockIdx.x, gridDim.x, N, NF, ycell, fcell, fedge, flip, g);
+    rhs_gather_kernel_impl<P>(blockIdx.x, gridDim.x, N, NF, ycell, fcell, fedge, flip, g, partial, counter, out, pub,
+                              seq);
 }
 template <int P>
 struct rhs_gather_kernel_args {
@@ -713,18 +764,25 @@ struct rhs_gather_kernel_args {
     const int32_t *fedge;
     const int32_t *flip;
     double *g;
+    double *partial;
+    unsigned int *counter;
+    double *out;
+    HostValue *pub;
+    int32_t seq;
 };
 template <int P>
 __global__ void rhs_gather_kernel_multi(const __grid_constant__ MultiP<rhs_gather_kernel_args<P>> M) {
     pdl_wait();
     int b_;
     const rhs_gather_kernel_args<P> &q_ = M.a[merge_find(M.start, M.n, b_)];
-    rhs_gather_kernel_impl<P>(b_, q_.nb_, q_.N, q_.NF, q_.ycell, q_.fcell, q_.fedge, q_.flip, q_.g);
+    rhs_gather_kernel_impl<P>(b_, q_.nb_, q_.N, q_.NF, q_.ycell, q_.fcell, q_.fedge, q_.flip, q_.g, q_.partial,
+                              q_.counter, q_.out, q_.pub, q_.seq);
 }
 template <int P>
 void rhs_gather_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int N, int NF,
                           const double *ycell, const int32_t *fcell, const int32_t *fedge, const int32_t *flip,
-                          double *g) {
+                          double *g, double *partial, unsigned int *counter, double *out, HostValue *pub,
+                          int32_t seq) {
     if (Recorder *r_ = batch_recorder()) {
         rhs_gather_kernel_args<P> q_;
         std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
@@ -736,10 +794,17 @@ void rhs_gather_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         q_.fedge = fedge;
         q_.flip = flip;
         q_.g = g;
-        batch_record(r_, reinterpret_cast<const void *>(&rhs_gather_kernel_multi<P>), q_, grid_, block_, smem_, kPdlFamily);
+        q_.partial = partial;
+        q_.counter = counter;
+        q_.out = out;
+        q_.pub = pub;
+        q_.seq = seq;
+        batch_record(r_, reinterpret_cast<const void *>(&rhs_gather_kernel_multi<P>), q_, grid_, block_, smem_,
+                     kPdlFamily);
         return;
     }
-    pdl_launch(kPdlFamily, &rhs_gather_kernel<P>, grid_, block_, smem_, s_, N, NF, ycell, fcell, fedge, flip, g);
+    pdl_launch(kPdlFamily, &rhs_gather_kernel<P>, grid_, block_, smem_, s_, N, NF, ycell, fcell, fedge, flip, g,
+               partial, counter, out, pub, seq);
 }
 
 
@@ -1013,18 +1078,21 @@ cudaError_t launch_to_external(hdg_handle *h, const double *in, double *ext) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_rhs_gather(hdg_handle *h, const double *ycell, double *g) {
-    HDG_DISPATCH_P(h->p, (rhs_gather_kernel_go<P>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->N, h->NF, ycell, h->d_facet_cell, h->d_facet_edge, h->d_flip, g)));
+cudaError_t launch_rhs_gather(hdg_handle *h, const double *ycell, double *g, const NormOut &nrm) {
+    HDG_DISPATCH_P(h->p, (rhs_gather_kernel_go<P>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->N, h->NF,
+                                                  ycell, h->d_facet_cell, h->d_facet_edge, h->d_flip, g, nrm.partial,
+                                                  nrm.counter, nrm.out, nrm.pub, nrm.seq)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_rhs(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell) {
-    if (h->prm.flux == 1) return launch_rhs_lf(h, r_u, r_h, g, ycell);
+cudaError_t launch_rhs(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell,
+                       const NormOut &nrm) {
+    if (h->prm.flux == 1) return nrm.partial ? cudaErrorInvalidValue : launch_rhs_lf(h, r_u, r_h, g, ycell);
     size_t n = size_t(h->N) * h->m;
     HDG_DISPATCH_P(h->p, (rhs_cell_kernel<P><<<blocks(n, 256), 256, 0, h->stream>>>(h->N, h->d_W, r_u, r_h, ycell)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_rhs_gather(h, ycell, g);
+    return launch_rhs_gather(h, ycell, g, nrm);
 }
 
 cudaError_t launch_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lam, double *u,
