@@ -197,6 +197,13 @@ HDG_API int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *st
  * C_K A_K^-1 M_K; then the facet-row trace operator (the S_K summed onto the
  * facets), the inverted facet diagonal blocks of the block-Jacobi smoother and
  * the P1 level operators (Eq. coarse_problem_upwind, divided by tau).
+ * FP64 handles eliminate in FP64.  Handles in HDG_MIXED_FP32 / HDG_MIXED_BF16,
+ * which use these matrices only as two-float pairs, invert A_K in FP32 and
+ * refine A_K^-1 [B_K | M_K] twice with two-float residuals (about 48-bit
+ * results, written directly as the pairs); the environment variable
+ * HDG_CONDENSE_FP64=1 (read once per process) gives them the FP64
+ * elimination too.  A coarsest P1 level of more than 256 vertices is inverted
+ * by one pivot and one update launch per column.
  * HDG_ESINGULAR if a cell or facet block has a zero pivot. */
 HDG_API int hdg_condense(hdg_handle *h);
 
