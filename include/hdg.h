@@ -180,8 +180,8 @@ HDG_API void hdg_default_params(hdg_params *prm);
  * error text is available from hdg_last_error(NULL).
  * Two environment variables, read here, select equivalent launch structures
  * (for timing comparisons; results agree up to summation order):
- * HDG_TAIL_MAX_VERTICES (16..4096, default 1024) bounds the P1 levels run by
- * the single-block coarse cycle; HDG_P1_FUSED=0 replaces the patch-fused P1
+ * HDG_TAIL_MAX_VERTICES (16..4096; default 1024 for the FP32 levels, 256 for
+ * the FP64 levels) bounds the P1 levels run by the single-block coarse cycle; HDG_P1_FUSED=0 replaces the patch-fused P1
  * kernels by one launch per smoothing / transfer step; HDG_FACET_BLOCK
  * (64, 128 or 256; default 128 for HDG_FP64 handles, 256 otherwise) sets the
  * threads per block of the facet-row kernels.  HDG_PDL (a bit mask, read once

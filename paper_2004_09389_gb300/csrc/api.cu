@@ -1182,10 +1182,11 @@ int build_tail_image(hdg_handle *h, int pi) {
 // First level of the single-CTA coarse cycle, per precision: the largest
 // suffix of P1 levels whose levels have at most tail_max vertices and whose
 // operators, transfers and vectors fit in one CTA's shared memory.
-int set_tail_start(hdg_handle *h, int tail_max) {
+int set_tail_start(hdg_handle *h, int tail_max64, int tail_max32) {
     const int nlev = int(h->lev.size());
     for (int pi = 0; pi < 2; ++pi) {
         const size_t tsz = pi == 0 ? sizeof(double) : sizeof(float);
+        const int tail_max = pi == 0 ? tail_max64 : tail_max32;
         int ts = nlev - 1;
         while (ts > 0 && h->lev[ts - 1].nv <= tail_max && nlev - (ts - 1) <= kTailMaxLevels &&
                tail_smem_bytes(h->lev, ts - 1, tsz) <= size_t(220) * 1024)
@@ -1331,8 +1332,11 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
         }
     }
     {
-        int tail_max = kTailMaxVertices;
-        if (const char *ev = std::getenv("HDG_TAIL_MAX_VERTICES")) tail_max = std::max(16, std::min(4096, std::atoi(ev)));
+        // largest level of the single-CTA coarse cycle per precision (FP64 levels:
+        // 256, FP32 levels: 1,024, as measured fastest); HDG_TAIL_MAX_VERTICES sets both
+        int tail_max64 = kTailMaxVertices64, tail_max32 = kTailMaxVertices;
+        if (const char *ev = std::getenv("HDG_TAIL_MAX_VERTICES"))
+            tail_max64 = tail_max32 = std::max(16, std::min(4096, std::atoi(ev)));
         // HDG_P1_FUSED=0 selects the unfused P1 kernels (same arithmetic; for timing comparisons)
         if (const char *ev = std::getenv("HDG_P1_FUSED")) h->p1_fused = std::atoi(ev) != 0;
         // HDG_FACET_BLOCK = 64 / 128 / 256: threads per block of the facet-row kernels
@@ -1341,7 +1345,7 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
             const int bs = std::atoi(ev);
             if (bs == 64 || bs == 128 || bs == 256) h->bs_facet = bs;
         }
-        int rc = set_tail_start(h, tail_max);
+        int rc = set_tail_start(h, tail_max64, tail_max32);
         if (rc) return rc;
     }
     if (prm->flux == 1) {
@@ -2240,18 +2244,18 @@ int hdg_autotune(hdg_handle *h, int32_t *choice) {
     }
     W.nblk_gs = best_nb;
     // first level of the single-CTA coarse cycle
-    int best_tm = kTailMaxVertices;
+    int best_tm = f32 ? kTailMaxVertices : kTailMaxVertices64;
     best_t = 1e30f;
     int last_ts = -1;
     for (int tm : {256, 1024, 4096}) {
-        if ((rc = set_tail_start(h, tm))) return rc;
+        if ((rc = set_tail_start(h, f32 ? kTailMaxVertices64 : tm, f32 ? tm : kTailMaxVertices))) return rc;
         const int ts = h->tail_start[f32 ? 1 : 0];
         if (ts == last_ts) continue;
         last_ts = ts;
         if ((rc = time_step(t))) return rc;
         if (t < best_t) { best_t = t; best_tm = tm; }
     }
-    if ((rc = set_tail_start(h, best_tm))) return rc;
+    if ((rc = set_tail_start(h, f32 ? kTailMaxVertices64 : best_tm, f32 ? best_tm : kTailMaxVertices))) return rc;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->prof.on = was_on;

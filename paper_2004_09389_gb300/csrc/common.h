@@ -255,6 +255,7 @@ __device__ __forceinline__ void finish_partials(const double *partial, int nb, i
 constexpr int kMaxGsBlocks = 1216;     // largest grid of the fused Gram-Schmidt kernels (8 x 152 SMs)
 constexpr int kTailMaxLevels = 8;
 constexpr int kTailMaxVertices = 1024;     // default largest level run inside the tail kernel
+constexpr int kTailMaxVertices64 = 256;    // the same for the FP64 levels (measured faster there)
 constexpr size_t kTailSmemMax = 226 * 1024; // dynamic shared memory limit of the tail kernel
 constexpr size_t kTailInvSmemMax = 64 * 1024; // largest coarsest-level inverse staged in shared memory
 constexpr int kPatchMaxVertices = 32768;      // largest P1 level smoothed by the fused patch kernels
