@@ -75,7 +75,9 @@ extern "C" {
 #define HDG_ESTATE     -9   /* call out of order (e.g. solve before condense)                 */
 
 #define HDG_FP64        0   /* every step in double precision                                 */
-#define HDG_MIXED_FP32  1   /* FP32 inner FGMRES + V-cycle, FP64 iterative refinement         */
+#define HDG_MIXED_FP32  1   /* FP32 inner FGMRES + V-cycle, iterative refinement with the
+                               residual, right-hand side, iterate and recovery in two-float
+                               arithmetic (about 48 bits); lambda returned in FP64         */
 #define HDG_MIXED_BF16  2   /* as HDG_MIXED_FP32, with a BF16 copy of the trace operator for the
                                smoother and V-cycle residual (FP32 accumulation)              */
 #define HDG_MIXED_FGMRES64 3 /* FP64 FGMRES (basis, orthogonalisation, residual, update, RHS and
@@ -188,7 +190,12 @@ HDG_API void hdg_default_params(hdg_params *prm);
  * per process; default 6) selects the kernel families launched with
  * programmatic dependent launch, so that a kernel's blocks are scheduled
  * while its predecessor drains: 1 the facet-row kernels, 2 the P1 kernels,
- * 4 the Krylov kernels; 0 none. */
+ * 4 the Krylov kernels; 0 none.  HDG_SPECULATE (read once per process) lets
+ * an FGMRES cycle queue Arnoldi step j + 1 behind step j before step j's
+ * residual estimate has reached the host, when the last two estimates,
+ * extrapolated geometrically, put step j's above the margin times the target:
+ * unset = margin 8, a number > 1 = that margin, 0 = off.  A step queued ahead
+ * whose predecessor meets the target runs for nothing and is not used. */
 HDG_API int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hdg_handle **out);
 
 /* (Re)build the cell operators for the handle's parameters: for every cell the

@@ -57,8 +57,13 @@ struct Workspace {
     int nchunk = 1;
     int nblk_gs = 1;      // blocks of the fused Gram-Schmidt kernels
     unsigned int *counter = nullptr;
-    ReadBack *rb = nullptr, *host_rb = nullptr;
-    ReadBack *host_rb_dev = nullptr;   // device address of host_rb (page-locked, written by the Gram-Schmidt kernel)
+    ReadBack *rb = nullptr;
+    // page-locked readbacks, one slot per Arnoldi step j (written by its
+    // Gram-Schmidt kernel), their device address, and per slot whether a
+    // launched step may still write it (set at launch, cleared once the host
+    // has seen the step's number)
+    ReadBack *host_rb = nullptr, *host_rb_dev = nullptr;
+    std::vector<char> rb_pending;
     HostValue *host_val = nullptr, *host_val_dev = nullptr;   // norms handed to the host
     int32_t val_seq = 0;
     double *g = nullptr, *x = nullptr, *r = nullptr, *ycell = nullptr;
@@ -767,7 +772,7 @@ cudaError_t arnoldi_step(hdg_handle *h, int j) {
     const bool reorth = h->prm.reorth != 0;
     if ((e = KL(HDG_PROF_KRYLOV, 1 + (reorth ? 1 : 0) + (fuse_scale ? 0 : 1),
                 launch_gs_step<T>(k.V, ld, j, k.w, W.partial, W.counter, W.nblk_gs, W.h1, W.h2, W.nrm2, W.Hm, ldh,
-                                  W.cs, W.sn, W.sv, W.bnorm, W.rb, W.host_rb_dev, k.V + size_t(j + 1) * ld, reorth,
+                                  W.cs, W.sn, W.sv, W.bnorm, W.rb, W.host_rb_dev + j, k.V + size_t(j + 1) * ld, reorth,
                                   !fuse_scale, s))) != cudaSuccess)
         return e;
     (void)NT;
@@ -775,17 +780,17 @@ cudaError_t arnoldi_step(hdg_handle *h, int j) {
 }
 
 // Wait for Arnoldi step j's readback: spin on the step number that the
-// Gram-Schmidt kernel writes last into the page-locked copy, checking the
-// stream every 256 polls (an error, or a finished stream without the number,
-// ends the wait with HDG_ECUDA).  Like wait_host_value, it relies on every
-// device-side wait of the library being bounded.
+// Gram-Schmidt kernel writes last into slot j of the page-locked copies,
+// checking the stream every 256 polls (an error, or a finished stream without
+// the number, ends the wait with HDG_ECUDA).  Like wait_host_value, it relies
+// on every device-side wait of the library being bounded.
 int wait_readback(hdg_handle *h, int j) {
     Workspace &W = *h->ws;
     if (batch_recorder()) {
-        const int rc = batch_yield(h, &W.host_rb->seq, j + 1);
+        const int rc = batch_yield(h, &W.host_rb[j].seq, j + 1);
         if (rc) return rc;
     }
-    const volatile int32_t *seq = &W.host_rb->seq;
+    const volatile int32_t *seq = &W.host_rb[j].seq;
     for (uint64_t it = 1;; ++it) {
         if (*seq == j + 1) break;
         if ((it & 255) == 0) {
@@ -797,6 +802,7 @@ int wait_readback(hdg_handle *h, int j) {
         }
     }
     std::atomic_thread_fence(std::memory_order_acquire);
+    W.rb_pending[j] = 0;
     return HDG_OK;
 }
 
@@ -840,6 +846,36 @@ int run_arnoldi_step(hdg_handle *h, int j) {
     return HDG_OK;
 }
 
+// Launch Arnoldi step j after clearing its readback slot.  A step launched
+// ahead whose number the host never waited for (its cycle ended first) may
+// still write the slot: that write comes first in the stream, so it is waited
+// for before the slot is cleared.
+template <typename T>
+int launch_arnoldi_step(hdg_handle *h, int j) {
+    Workspace &W = *h->ws;
+    if (W.rb_pending[j]) {
+        const int rc = wait_readback(h, j);
+        if (rc) return rc;
+    }
+    W.host_rb[j].seq = 0;
+    W.rb_pending[j] = 1;
+    return run_arnoldi_step<T>(h, j);
+}
+
+// Steps launched ahead: HDG_SPECULATE unset, a margin (> 1) or 0 (off), read
+// once.  fgmres_cycle launches step j + 1 before step j's readback arrives
+// when the last two estimates, extrapolated geometrically, put step j's
+// estimate above margin x the target (default margin 8).
+double speculation_margin() {
+    static const double v = [] {
+        const char *e = std::getenv("HDG_SPECULATE");
+        if (!e || !*e) return 8.0;
+        const double m = std::atof(e);
+        return m > 1.0 ? m : 0.0;
+    }();
+    return v;
+}
+
 // One FGMRES cycle (at most m iterations, possibly fewer) on S x = b starting
 // from x, with the current residual r0 = b - S x of norm beta already in
 // k.V[0] (scaled).  Stops when the estimate drops below tol_abs / bnorm.
@@ -867,18 +903,34 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
     }
     int j = 0;
     double hist[72];
+    // steps launched ahead (replayed step graphs only): step j + 1 is queued
+    // behind step j before j's estimate reaches the host, so that the GPU does
+    // not idle while the host reads it and launches the next step.  If step j
+    // then meets the target, step j + 1 has run for nothing; its results (the
+    // Hessenberg column j + 1, rotation j + 1, basis vectors past j) are not used.
+    const double margin = speculation_margin();
+    const bool ahead_ok = margin > 0.0 && !h->prof.on && W.use_graphs && !h->lc.on && !h->lc.collecting &&
+                          !batch_recorder();
+    bool launched[72] = {};
+    const double est0 = est_out;
     for (; j < m && j < max_it; ++j) {
-        W.host_rb->seq = 0;   // the previous step's number was seen, so no write to it is in flight
-        int rc = run_arnoldi_step<T>(h, j);
-        if (rc) return rc;
+        int rc;
+        if (!launched[j] && (rc = launch_arnoldi_step<T>(h, j))) return rc;
+        if (ahead_ok && j >= 1 && j + 1 < m && j + 1 < max_it) {
+            const double e1 = hist[j - 1], e2 = j >= 2 ? hist[j - 2] : est0;
+            if (e2 > 0.0 && e1 * (e1 / e2) > margin * rel_target) {
+                if ((rc = launch_arnoldi_step<T>(h, j + 1))) return rc;
+                launched[j + 1] = true;
+            }
+        }
         if (h->prof.on) {
             TRY(cudaStreamSynchronize(s));
             prof_flush(h);
         } else if ((rc = wait_readback(h, j))) {
             return rc;
         }
-        est_out = W.host_rb->est;
-        flag_out = W.host_rb->flags;
+        est_out = W.host_rb[j].est;
+        flag_out = W.host_rb[j].flags;
         hist[j] = est_out;
         // learned sweep as preconditioner: if the residual estimate stalls (less
         // than 10 % decrease over three iterations), fall back to the plain
@@ -990,8 +1042,17 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
     }
 }
 
-// FP64 iterative refinement with FP32 inner FGMRES solves
-int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info, bool norm_pending = false) {
+// FP64 iterative refinement with FP32 inner FGMRES solves.  The iterate is
+// kept as float pairs in W.x2 (the form the refinement residual reads), so the
+// correction x += d / sc runs in two-float arithmetic on the FP32 pipe;
+// `updated` tells whether a correction has been added yet.  Each inner solve
+// is S d = fp32(r sc) from a zero guess, sc a power of two, written with
+// ||r sc|| by the kernel that forms r: the right-hand-side gather for r = g
+// (norm_pending; sc = 1, g being in the FP32 range the two-float steps
+// require) and the two-float residual afterwards (sc = 2^-ilogb(||g||), so
+// that r sc stays near the relative residual).  Without norm_pending the
+// first right-hand side is rounded by a separate pass as fp32(r / ||r||).
+int solve_mixed_steps(hdg_handle *h, const double *g, hdg_solve_info &info, bool norm_pending, bool &updated) {
     Workspace &W = *h->ws;
     KSpace<float> &k = W.k32;
     cudaStream_t s = h->stream;
@@ -1000,21 +1061,27 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info,
     if (rc) return rc;
     info = hdg_solve_info{};
     if (!std::isfinite(bnorm)) return fail(h, HDG_ENAN, "NaN or Inf in the right-hand side");
-    TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<double>(x, 0.0, W.NT, s)));
     if (bnorm == 0.0) return HDG_OK;
+    const double sc_res = std::ldexp(1.0, -std::ilogb(bnorm));
     int total = 0;
     for (int outer = 0;; ++outer) {
-        // r = g - S x in FP64 (r = g while x is still zero)
-        const double *r = W.r;
-        double beta = bnorm;
-        if (outer == 0) {
-            r = g;
-        } else {
-            // in two-float arithmetic from the split copy of x kept by the update below
-            // with its norm in the same pass, handed to the host as norm_host does
+        double beta = bnorm, sc = 1.0;
+        bool rhs32 = norm_pending;   // the FP32 start of the inner solve is written
+        if (outer > 0) {
+            // r = g - S x in two-float arithmetic from the pairs kept by the update
+            // below, with the inner solve's start and ||r||^2 (handed to the host as
+            // norm_host does) in the same pass
+            sc = sc_res;
+            rhs32 = true;
+            F32Copy c32;
+            c32.b32 = k.b;
+            c32.z32 = k.x;
+            c32.scale = sc;
+            c32.root_a = W.bnorm;
+            c32.root_b = W.scal;
             W.host_val->seq = 0;
-            TRY(KL(HDG_PROF_RESIDUAL64, 1, launch_residual_ff(h, g, W.x2, W.r, W.partial, W.counter, W.nrm2,
-                                                              W.host_val_dev, 1)));
+            TRY(KL(HDG_PROF_RESIDUAL64, 1, launch_residual_ff(h, g, W.x2, nullptr, W.partial, W.counter, W.nrm2,
+                                                              W.host_val_dev, 1, c32)));
             rc = norm_wait(h, 1, beta);
             if (rc) return rc;
         }
@@ -1024,12 +1091,14 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info,
         if (beta / bnorm <= h->prm.rtol) return HDG_OK;
         if (total >= h->prm.max_iter || outer >= 100)
             return fail(h, HDG_ENOCONV, "maximum number of iterations reached");
-        // b32 = r / ||r||, solve S d = b32 in FP32, x += ||r|| d
-        W.host_buf[2] = beta;
+        // the correction's scale: x += d / sc, or x += ||r|| d for b32 = r / ||r||
+        W.host_buf[2] = rhs32 ? 1.0 / sc : beta;
         TRY(dcopy(h, W.beta, W.host_buf + 2, sizeof(double), cudaMemcpyHostToDevice));
-        // b32 = r / ||r||, the zero initial guess and ||b32|| (into W.bnorm and W.scal) in one pass
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_d2f_norm(r, k.b, k.x, W.beta, W.NT, W.partial, W.nchunk, W.counter, W.nrm2,
-                                                   W.bnorm, W.scal, s)));
+        if (!rhs32) {
+            // b32 = r / ||r||, the zero initial guess and ||b32|| (into W.bnorm and W.scal) in one pass
+            TRY(KL(HDG_PROF_KRYLOV, 1, launch_d2f_norm(g, k.b, k.x, W.beta, W.NT, W.partial, W.nchunk, W.counter,
+                                                       W.nrm2, W.bnorm, W.scal, s)));
+        }
         hdg_solve_info inner{};
         const double inner_tol = std::max(h->prm.inner_rtol, 0.5 * h->prm.rtol * bnorm / beta);
         rc = fgmres<float>(h, k.b, k.x, inner_tol, h->prm.max_iter - total, false, true, inner, true, true);
@@ -1037,9 +1106,26 @@ int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info,
         total += inner.iters;
         info.iters = total;
         info.est_rel_res = inner.est_rel_res;
-        // x += beta * d
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_axpby_split(x, W.x2, k.x, W.beta, W.NT, s)));
+        // x += scale * d (the first correction is x itself)
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_ff_axpy(W.x2, k.x, W.beta, W.NT, !updated, s)));
+        updated = true;
     }
+}
+
+// the refinement above; on return the iterate is joined into x and lam (FP64,
+// lam may be null), zero if no correction was added
+int solve_mixed(hdg_handle *h, const double *g, double *x, hdg_solve_info &info, bool norm_pending, double *lam) {
+    Workspace &W = *h->ws;
+    bool updated = false;
+    const int rc = solve_mixed_steps(h, g, info, norm_pending, updated);
+    if (rc == HDG_ECUDA) return rc;
+    if (updated) {
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_ff_join(W.x2, x, lam, W.NT, h->stream)));
+    } else {
+        TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<double>(x, 0.0, W.NT, h->stream)));
+        if (lam) TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<double>(lam, 0.0, W.NT, h->stream)));
+    }
+    return rc;
 }
 
 int ensure_staging(hdg_handle *h) {
@@ -1452,12 +1538,14 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(dalloc(&W.y, mm + 1));
     // partial sums: (m + 1) vectors x the largest grid of the multi-dot (nchunk) or
     // of the Gram-Schmidt kernels (nblk_gs, or up to 1216 blocks after autotuning)
-    TRY(dalloc(&W.partial, (mm + 1) * size_t(std::max({W.nchunk, W.nblk_gs, kMaxGsBlocks, int((h->NF + 255) / 256)}))));
+    TRY(dalloc(&W.partial, (mm + 1) * size_t(std::max({W.nchunk, W.nblk_gs, kMaxGsBlocks, int((h->NF + 255) / 256),
+                                                        int((h->NF + kResFFFacets - 1) / kResFFFacets)}))));
     TRY(dalloc(&W.counter, 1));
     TRY(cudaMemsetAsync(W.counter, 0, sizeof(unsigned int), s));
     TRY(dalloc(&W.rb, 1));
-    TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_rb), sizeof(ReadBack)));
-    std::memset(W.host_rb, 0, sizeof(ReadBack));
+    TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_rb), sizeof(ReadBack) * mm));
+    std::memset(W.host_rb, 0, sizeof(ReadBack) * mm);
+    W.rb_pending.assign(mm, 0);
     TRY(cudaHostGetDevicePointer(reinterpret_cast<void **>(&W.host_rb_dev), W.host_rb, 0));
     TRY(cudaMallocHost(reinterpret_cast<void **>(&W.host_val), sizeof(HostValue)));
     std::memset(W.host_val, 0, sizeof(HostValue));
@@ -1624,6 +1712,13 @@ int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solv
     if (norm_pending) {
         W.host_val->seq = 0;   // the previous hand-over was seen
         nrm = NormOut{W.partial, W.counter, W.nrm2, W.host_val_dev, 1};
+        if (mode_ff(h->prm)) {
+            // and the first inner solve's start: fp32(g), the zero guess, ||g||
+            nrm.f32.b32 = W.k32.b;
+            nrm.f32.z32 = W.k32.x;
+            nrm.f32.root_a = W.bnorm;
+            nrm.f32.root_b = W.scal;
+        }
     }
     if (!mode_ff(h->prm)) TRY(KL(HDG_PROF_RHS, 2, launch_rhs(h, r_u, r_h, W.g, W.ycell, nrm)));
     else TRY(KL(HDG_PROF_RHS, 2, launch_rhs_ff(h, r_u, r_h, W.g, W.ycell, copy_u, copy_h, nrm)));
@@ -1632,7 +1727,7 @@ int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solv
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<double>(W.x, 0.0, W.NT, s)));
         rc = fgmres<double>(h, W.g, W.x, h->prm.rtol, h->prm.max_iter, true, true, info, false, false, norm_pending);
     } else {
-        rc = solve_mixed(h, W.g, W.x, info, norm_pending);
+        rc = solve_mixed(h, W.g, W.x, info, norm_pending, W.lam_int);
     }
     if (!batch_recorder()) {   // a batched solve checks the status words after its last wave
         int32_t st = 0;
@@ -1647,7 +1742,8 @@ int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solv
     }
     info.status = rc;
     info.fallback_used = h->lc.fallback ? 1 : 0;
-    TRY(dcopy(h, W.lam_int, W.x, sizeof(double) * W.NT, cudaMemcpyDeviceToDevice));
+    // (the mixed refinement has written lam_int with x)
+    if (mode_krylov64(h->prm)) TRY(dcopy(h, W.lam_int, W.x, sizeof(double) * W.NT, cudaMemcpyDeviceToDevice));
     W.have_lambda = true;
     return rc;
 }

@@ -705,12 +705,24 @@ cudaError_t launch_to_external(hdg_handle *h, const double *in, double *ext);
 // optional hand-over of ||v||^2 by the kernel that forms v: block partials,
 // the reduction counter, the device result and, with pub non-null, the
 // page-locked word the host polls (sequence number seq)
+// The start of an FP32 inner solve, written by the kernel that forms its
+// right-hand side v in FP64 (b32 null: not wanted): b32 = fp32(v * scale),
+// z32 = 0 (the zero initial guess) and, by the block that completes the norm,
+// root_a = root_b = ||v|| * scale (scale a power of two, so exact).
+struct F32Copy {
+    float *b32 = nullptr;
+    float *z32 = nullptr;
+    double scale = 1.0;
+    double *root_a = nullptr;
+    double *root_b = nullptr;
+};
 struct NormOut {
     double *partial = nullptr;
     unsigned int *counter = nullptr;
     double *out = nullptr;
     HostValue *pub = nullptr;
     int32_t seq = 0;
+    F32Copy f32 = F32Copy();
 };
 cudaError_t launch_rhs(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell,
                        const NormOut &nrm = NormOut());
@@ -720,10 +732,16 @@ cudaError_t launch_split(const double *a, float2 *out, size_t n, cudaStream_t s)
 // a per-cell matrix [rows][cols][N] split into pairs of row entries, tiled by 32 cells:
 // [ceil(N/32)][rows][(cols+1)/2][32] (float4)
 cudaError_t launch_split_pairs(const double *a, float2 *out, int rows, int cols, size_t N, cudaStream_t s);
-cudaError_t launch_axpby_split(double *x, float2 *x2, const float *d, const double *scale, size_t n, cudaStream_t s);
+// facets per block of the two-float residual (its grid: ceil(NF / kResFFFacets)
+// blocks, each writing one partial sum)
+constexpr int kResFFFacets = 64;
+// x2 += scale[0] * d in two-float arithmetic (first: x2 = scale[0] * d)
+cudaError_t launch_ff_axpy(float2 *x2, const float *d, const double *scale, size_t n, bool first, cudaStream_t s);
+// a = b = hi + lo of each pair (b may be null)
+cudaError_t launch_ff_join(const float2 *x2, double *a, double *b, size_t n, cudaStream_t s);
 cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2, double *res,
                                double *partial = nullptr, unsigned int *counter = nullptr, double *out = nullptr,
-                               HostValue *pub = nullptr, int32_t seq = 0);
+                               HostValue *pub = nullptr, int32_t seq = 0, const F32Copy &c32 = F32Copy());
 // (r_u, r_h may be device aliases of page-locked host memory; copy_u / copy_h,
 // if non-null, receive a device copy of them)
 cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell,

@@ -77,50 +77,119 @@ __device__ __forceinline__ void row_pairs(FFAcc &acc, const float4 *__restrict__
     }
 }
 
-// x += scale * d (refinement correction, FP32 -> FP64) and its split copy
-__device__ __forceinline__ void axpby_split_kernel_impl(int bid_, int nb_, double *__restrict__ x,
-                                                        float2 *__restrict__ x2, const float *__restrict__ d,
-                                                        const double *__restrict__ scale, size_t n) {
+// The refinement iterate lambda is kept only as float pairs (hi, lo), the form
+// the residual kernel reads; the correction x += scale * d then runs on the
+// FP32 pipe, and the pairs are joined into FP64 once, when the solve ends.
+// (hi, lo) += (sh + sl) * d, (sh, sl) = split(scale) formed once per block:
+// the leading product by FMA with its exact error, the cross term sl * d, a
+// TwoSum of the leading parts, the trailing parts added to its error and a
+// renormalisation (about 2^-46 relative).  first: the iterate is zero and not
+// read.
+__device__ __forceinline__ void ff_axpy_kernel_impl(int bid_, int nb_, float2 *__restrict__ x2,
+                                                    const float *__restrict__ d, const double *__restrict__ scale,
+                                                    size_t n, int first) {
+    // the entry's loads are issued before the block waits for the split scale
     const size_t i = size_t(bid_) * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double v = fma(scale[0], double(d[i]), x[i]);
-    x[i] = v;
-    x2[i] = split(v);
+    const bool on = i < n;
+    const float di = on ? d[i] : 0.0f;
+    const float2 xv = on && !first ? x2[i] : make_float2(0.0f, 0.0f);
+    __shared__ float2 sc;
+    if (threadIdx.x == 0) sc = split(scale[0]);
+    __syncthreads();
+    if (!on) return;
+    const float ph = __fmul_rn(sc.x, di);
+    const float pl = __fmaf_rn(sc.y, di, __fmaf_rn(sc.x, di, -ph));
+    if (first) {
+        const float t = __fadd_rn(ph, pl);
+        x2[i] = make_float2(t, __fsub_rn(pl, __fsub_rn(t, ph)));
+        return;
+    }
+    const float t = __fadd_rn(xv.x, ph);
+    const float bp = __fsub_rn(t, xv.x);
+    float e = __fadd_rn(__fsub_rn(xv.x, __fsub_rn(t, bp)), __fsub_rn(ph, bp));
+    e = __fadd_rn(e, __fadd_rn(xv.y, pl));
+    const float hi = __fadd_rn(t, e);
+    x2[i] = make_float2(hi, __fsub_rn(e, __fsub_rn(hi, t)));
 }
-__global__ void axpby_split_kernel(double *__restrict__ x, float2 *__restrict__ x2, const float *__restrict__ d,
-                                   const double *__restrict__ scale, size_t n) {
+__global__ void ff_axpy_kernel(float2 *__restrict__ x2, const float *__restrict__ d, const double *__restrict__ scale,
+                               size_t n, int first) {
     pdl_wait();
-    axpby_split_kernel_impl(blockIdx.x, gridDim.x, x, x2, d, scale, n);
+    ff_axpy_kernel_impl(blockIdx.x, gridDim.x, x2, d, scale, n, first);
 }
-struct axpby_split_kernel_args {
+struct ff_axpy_kernel_args {
     int nb_;
-    double *x;
     float2 *x2;
     const float *d;
     const double *scale;
     size_t n;
+    int first;
 };
-__global__ void axpby_split_kernel_multi(const __grid_constant__ MultiP<axpby_split_kernel_args> M) {
+__global__ void ff_axpy_kernel_multi(const __grid_constant__ MultiP<ff_axpy_kernel_args> M) {
     pdl_wait();
     int b_;
-    const axpby_split_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
-    axpby_split_kernel_impl(b_, q_.nb_, q_.x, q_.x2, q_.d, q_.scale, q_.n);
+    const ff_axpy_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
+    ff_axpy_kernel_impl(b_, q_.nb_, q_.x2, q_.d, q_.scale, q_.n, q_.first);
 }
-void axpby_split_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, double *x, float2 *x2,
-                           const float *d, const double *scale, size_t n) {
+void ff_axpy_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, float2 *x2, const float *d,
+                       const double *scale, size_t n, int first) {
     if (Recorder *r_ = batch_recorder()) {
-        axpby_split_kernel_args q_;
+        ff_axpy_kernel_args q_;
         std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
         q_.nb_ = int(grid_);
-        q_.x = x;
         q_.x2 = x2;
         q_.d = d;
         q_.scale = scale;
         q_.n = n;
-        batch_record(r_, reinterpret_cast<const void *>(&axpby_split_kernel_multi), q_, grid_, block_, smem_, kPdlFamily);
+        q_.first = first;
+        batch_record(r_, reinterpret_cast<const void *>(&ff_axpy_kernel_multi), q_, grid_, block_, smem_, kPdlFamily);
         return;
     }
-    pdl_launch(kPdlFamily, &axpby_split_kernel, grid_, block_, smem_, s_, x, x2, d, scale, n);
+    pdl_launch(kPdlFamily, &ff_axpy_kernel, grid_, block_, smem_, s_, x2, d, scale, n, first);
+}
+
+// a = b = hi + lo of the pairs, rounded once to FP64 (within 2^-53 of the
+// pair's value); b may be null
+__device__ __forceinline__ void ff_join_kernel_impl(int bid_, int nb_, const float2 *__restrict__ x2,
+                                                    double *__restrict__ a, double *__restrict__ b, size_t n) {
+    const size_t i = size_t(bid_) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 v = x2[i];
+    const double r = double(v.x) + double(v.y);
+    a[i] = r;
+    if (b) b[i] = r;
+}
+__global__ void ff_join_kernel(const float2 *__restrict__ x2, double *__restrict__ a, double *__restrict__ b,
+                               size_t n) {
+    pdl_wait();
+    ff_join_kernel_impl(blockIdx.x, gridDim.x, x2, a, b, n);
+}
+struct ff_join_kernel_args {
+    int nb_;
+    const float2 *x2;
+    double *a;
+    double *b;
+    size_t n;
+};
+__global__ void ff_join_kernel_multi(const __grid_constant__ MultiP<ff_join_kernel_args> M) {
+    pdl_wait();
+    int b_;
+    const ff_join_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
+    ff_join_kernel_impl(b_, q_.nb_, q_.x2, q_.a, q_.b, q_.n);
+}
+void ff_join_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, const float2 *x2, double *a,
+                       double *b, size_t n) {
+    if (Recorder *r_ = batch_recorder()) {
+        ff_join_kernel_args q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.x2 = x2;
+        q_.a = a;
+        q_.b = b;
+        q_.n = n;
+        batch_record(r_, reinterpret_cast<const void *>(&ff_join_kernel_multi), q_, grid_, block_, smem_, kPdlFamily);
+        return;
+    }
+    pdl_launch(kPdlFamily, &ff_join_kernel, grid_, block_, smem_, s_, x2, a, b, n);
 }
 
 
@@ -143,49 +212,60 @@ __device__ __forceinline__ double ff_block_sum(double v) {
     return v;
 }
 
-// res = b - S x in two-float arithmetic (x as split pairs); with partial
-// non-null also ||res||^2: per-thread double sums, block sums, the last block
-// adding the block sums in block order into out[0] and handing the value to
-// the host through pub (the value, a system fence, then seq)
+// res = b - S x in two-float arithmetic (x as split pairs), one thread per
+// facet row: a block takes kResFacets facets, thread (r, f) of it row r of
+// facet f.  The threads first stage the pairs of their facets and of the four
+// neighbours in shared memory (thread (r, f) component r of the five), then
+// each adds the 5 (p+1) products of its row in the order of the packed layout.
+// res may be null, and c32 names the FP32 start of an inner solve on res
+// (F32Copy).  With partial non-null also ||res||^2: block sums of the rows'
+// squares, the last block adding the block sums in block order into out[0]
+// and handing the value to the host through pub (the value, a system fence,
+// then seq).
+constexpr int kResFacets = kResFFFacets;
+
 template <int P>
 __device__ __forceinline__ void residual_ff_kernel_impl(int bid_, int nb_, int NF, const float4 *__restrict__ S2,
                                                         const int32_t *__restrict__ nbr, const double *__restrict__ b,
                                                         const float2 *__restrict__ x2, double *__restrict__ res,
                                                         double *partial, unsigned int *counter, double *out,
-                                                        HostValue *pub, int32_t seq) {
-    constexpr int PP = P + 1, NS = 5 * PP * PP, NQ = (NS + 1) / 2;
-    const int e = bid_ * blockDim.x + threadIdx.x;
+                                                        HostValue *pub, int32_t seq, const F32Copy c32) {
+    constexpr int PP = P + 1, RS = 5 * PP, NQR = (RS + 1) / 2;   // entries of a row, 16-byte groups it touches
+    __shared__ float2 sx[5][PP][kResFacets];
+    const int r = threadIdx.x / kResFacets, f = threadIdx.x % kResFacets, e = bid_ * kResFacets + f;
+    const bool on = e < NF;
+    if (on) {
+        sx[0][r][f] = x2[size_t(r) * NF + e];
+#pragma unroll
+        for (int q = 1; q < 5; ++q) sx[q][r][f] = x2[size_t(r) * NF + __ldg(nbr + size_t(q - 1) * NF + e)];
+    }
+    __syncthreads();
     double sq = 0.0;
-    if (e < NF) {
-        int src[5];
-        src[0] = e;
+    if (on) {
+        // row r holds entries j0 .. j0 + RS - 1, in groups q0 .. q0 + NQR - 1
+        // (j0 is even whenever RS is, and the entry of lane g of group q0 + t
+        // is then 2t + g of the row)
+        const int j0 = r * RS, q0 = j0 / 2, odd = (RS % 2) ? (j0 & 1) : 0;
+        float4 v[NQR];
 #pragma unroll
-        for (int q = 1; q < 5; ++q) src[q] = __ldg(nbr + size_t(q - 1) * NF + e);
-        float2 xs[5][PP];
+        for (int t = 0; t < NQR; ++t) v[t] = __ldg(S2 + size_t(q0 + t) * NF + e);
+        FFAcc acc;
 #pragma unroll
-        for (int q = 0; q < 5; ++q)
-#pragma unroll
-            for (int c = 0; c < PP; ++c) xs[q][c] = x2[size_t(c) * NF + src[q]];
-        FFAcc acc[PP];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const float4 v = __ldg(S2 + size_t(q) * NF + e);
-            const float2 a[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+        for (int t = 0; t < NQR; ++t) {
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
-                const int j = 2 * q + g;
-                if (j < NS) {
-                    const int r = j / (5 * PP), rem = j % (5 * PP);
-                    acc[r].add(a[g], xs[rem / PP][rem % PP]);
-                }
+                const int k = 2 * t + g - odd;
+                if (k >= 0 && k < RS)
+                    acc.add(g ? make_float2(v[t].z, v[t].w) : make_float2(v[t].x, v[t].y), sx[k / PP][k % PP][f]);
             }
         }
-#pragma unroll
-        for (int r = 0; r < PP; ++r) {
-            const double rv = b[size_t(r) * NF + e] - acc[r].value();
-            res[size_t(r) * NF + e] = rv;
-            sq = fma(rv, rv, sq);
+        const double rv = b[size_t(r) * NF + e] - acc.value();
+        if (res) res[size_t(r) * NF + e] = rv;
+        if (c32.b32) {
+            c32.b32[size_t(r) * NF + e] = float(rv * c32.scale);
+            c32.z32[size_t(r) * NF + e] = 0.0f;
         }
+        sq = rv * rv;
     }
     if (!partial) return;
     __shared__ bool last;
@@ -204,6 +284,8 @@ __device__ __forceinline__ void residual_ff_kernel_impl(int bid_, int nb_, int N
     if (threadIdx.x == 0) {
         *counter = 0u;
         out[0] = a;
+        if (c32.root_a) *c32.root_a = sqrt(a) * c32.scale;
+        if (c32.root_b) *c32.root_b = sqrt(a) * c32.scale;
         if (pub) {
             pub->v = a;
             __threadfence_system();
@@ -212,14 +294,14 @@ __device__ __forceinline__ void residual_ff_kernel_impl(int bid_, int nb_, int N
     }
 }
 template <int P>
-__global__ void __launch_bounds__(256) residual_ff_kernel(int NF, const float4 *__restrict__ S2,
+__global__ void __launch_bounds__(kResFacets * (P + 1)) residual_ff_kernel(int NF, const float4 *__restrict__ S2,
                                                           const int32_t *__restrict__ nbr,
                                                           const double *__restrict__ b, const float2 *__restrict__ x2,
                                                           double *__restrict__ res, double *partial,
                                                           unsigned int *counter, double *out, HostValue *pub,
-                                                          int32_t seq) {
+                                                          int32_t seq, const F32Copy c32) {
     pdl_wait();
-    residual_ff_kernel_impl<P>(blockIdx.x, gridDim.x, NF, S2, nbr, b, x2, res, partial, counter, out, pub, seq);
+    residual_ff_kernel_impl<P>(blockIdx.x, gridDim.x, NF, S2, nbr, b, x2, res, partial, counter, out, pub, seq, c32);
 }
 template <int P>
 struct residual_ff_kernel_args {
@@ -235,19 +317,20 @@ struct residual_ff_kernel_args {
     double *out;
     HostValue *pub;
     int32_t seq;
+    F32Copy c32;
 };
 template <int P>
-__global__ void __launch_bounds__(256) residual_ff_kernel_multi(const __grid_constant__ MultiP<residual_ff_kernel_args<P>> M) {
+__global__ void __launch_bounds__(kResFacets * (P + 1)) residual_ff_kernel_multi(const __grid_constant__ MultiP<residual_ff_kernel_args<P>> M) {
     pdl_wait();
     int b_;
     const residual_ff_kernel_args<P> &q_ = M.a[merge_find(M.start, M.n, b_)];
     residual_ff_kernel_impl<P>(b_, q_.nb_, q_.NF, q_.S2, q_.nbr, q_.b, q_.x2, q_.res, q_.partial, q_.counter, q_.out,
-                               q_.pub, q_.seq);
+                               q_.pub, q_.seq, q_.c32);
 }
 template <int P>
 void residual_ff_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int NF, const float4 *S2,
                            const int32_t *nbr, const double *b, const float2 *x2, double *res, double *partial,
-                           unsigned int *counter, double *out, HostValue *pub, int32_t seq) {
+                           unsigned int *counter, double *out, HostValue *pub, int32_t seq, const F32Copy &c32) {
     if (Recorder *r_ = batch_recorder()) {
         residual_ff_kernel_args<P> q_;
         std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
@@ -263,12 +346,13 @@ void residual_ff_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaSt
         q_.out = out;
         q_.pub = pub;
         q_.seq = seq;
+        q_.c32 = c32;
         batch_record(r_, reinterpret_cast<const void *>(&residual_ff_kernel_multi<P>), q_, grid_, block_, smem_,
                      kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &residual_ff_kernel<P>, grid_, block_, smem_, s_, NF, S2, nbr, b, x2, res, partial, counter,
-               out, pub, seq);
+               out, pub, seq, c32);
 }
 
 
@@ -413,16 +497,23 @@ cudaError_t launch_split_pairs(const double *a, float2 *out, int rows, int cols,
     return cudaGetLastError();
 }
 
-cudaError_t launch_axpby_split(double *x, float2 *x2, const float *d, const double *scale, size_t n, cudaStream_t s) {
-    axpby_split_kernel_go(blocks(n, 256), 256, 0, s, x, x2, d, scale, n);
+cudaError_t launch_ff_axpy(float2 *x2, const float *d, const double *scale, size_t n, bool first, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    ff_axpy_kernel_go(blocks(n, 256), 256, 0, s, x2, d, scale, n, first ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ff_join(const float2 *x2, double *a, double *b, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    ff_join_kernel_go(blocks(n, 256), 256, 0, s, x2, a, b, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2, double *res, double *partial,
-                               unsigned int *counter, double *out, HostValue *pub, int32_t seq) {
-    HDG_DISPATCH_P(h->p, (residual_ff_kernel_go<P>(blocks(h->NF, 256), 256, 0, h->stream, h->NF,
+                               unsigned int *counter, double *out, HostValue *pub, int32_t seq, const F32Copy &c32) {
+    HDG_DISPATCH_P(h->p, (residual_ff_kernel_go<P>(blocks(h->NF, kResFacets), kResFacets * (P + 1), 0, h->stream, h->NF,
                                                    reinterpret_cast<const float4 *>(h->d_Sval2), h->d_nbr, b, x2, res,
-                                                   partial, counter, out, pub, seq)));
+                                                   partial, counter, out, pub, seq, c32)));
     return cudaGetLastError();
 }
 

@@ -412,18 +412,36 @@ void fill_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t 
 // the block sums in block order) into out[0] and its square root into root_a
 // and root_b: an inner solve's right-hand side, its zero initial guess and
 // the norm that starts it, in one pass
-__device__ __forceinline__ void d2f_norm_kernel_impl(int bid_, int nb_, const double *x, float *y, float *z,
+__device__ __forceinline__ void d2f_norm_kernel_impl(int bid_, int nb_, const double *__restrict__ x,
+                                                     float *__restrict__ y, float *__restrict__ z,
                                                      const double *scale, size_t n, double *partial,
                                                      unsigned int *counter, double *out, double *root_a,
                                                      double *root_b) {
     __shared__ bool last;
+    // kU loads in flight per thread before their results are used (the grid
+    // is a few blocks per SM), the first kU issued before the block waits for
+    // the reciprocal; each thread still adds its entries in index order
+    constexpr int kU = 8;
+    const size_t stride = size_t(nb_) * blockDim.x, i0 = size_t(bid_) * blockDim.x + threadIdx.x;
+    double a[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) a[u] = i0 + u * stride < n ? x[i0 + u * stride] : 0.0;
     const double inv = block_recip(scale);
     float acc = 0.0f;
-    for (size_t i = size_t(bid_) * blockDim.x + threadIdx.x; i < n; i += size_t(nb_) * blockDim.x) {
-        const float v = float(x[i] * inv);
-        y[i] = v;
-        z[i] = 0.0f;
-        acc = fmaf(v, v, acc);
+    for (size_t i = i0; i < n; i += kU * stride) {
+        if (i != i0) {
+#pragma unroll
+            for (int u = 0; u < kU; ++u) a[u] = i + u * stride < n ? x[i + u * stride] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (i + u * stride < n) {
+                const float v = float(a[u] * inv);
+                y[i + u * stride] = v;
+                z[i + u * stride] = 0.0f;
+                acc = fmaf(v, v, acc);
+            }
+        }
     }
     const double tot = block_sum(double(acc));
     if (threadIdx.x == 0) {
@@ -434,13 +452,13 @@ __device__ __forceinline__ void d2f_norm_kernel_impl(int bid_, int nb_, const do
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double a = 0.0;
-    for (int i = threadIdx.x; i < nb_; i += blockDim.x) a += partial[i];
-    a = block_sum(a);
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nb_; i += blockDim.x) t += partial[i];
+    t = block_sum(t);
     if (threadIdx.x == 0) {
         *counter = 0u;
-        out[0] = a;
-        const double r = sqrt(a);
+        out[0] = t;
+        const double r = sqrt(t);
         if (root_a) *root_a = r;
         if (root_b) *root_b = r;
     }

@@ -701,7 +701,7 @@ __device__ __forceinline__ void rhs_gather_kernel_impl(int bid_, int nb_, int N,
                                                        const int32_t *__restrict__ fedge,
                                                        const int32_t *__restrict__ flip, double *__restrict__ g,
                                                        double *partial, unsigned int *counter, double *out,
-                                                       HostValue *pub, int32_t seq) {
+                                                       HostValue *pub, int32_t seq, const F32Copy c32) {
     constexpr int PP = P + 1;
     const int e = bid_ * blockDim.x + threadIdx.x;
     double sq = 0.0;
@@ -719,6 +719,13 @@ __device__ __forceinline__ void rhs_gather_kernel_impl(int bid_, int nb_, int N,
         for (int r = 0; r < PP; ++r) {
             g[size_t(r) * NF + e] = v[r];
             sq = fma(v[r], v[r], sq);
+        }
+        if (c32.b32) {
+#pragma unroll
+            for (int r = 0; r < PP; ++r) {
+                c32.b32[size_t(r) * NF + e] = float(v[r] * c32.scale);
+                c32.z32[size_t(r) * NF + e] = 0.0f;
+            }
         }
     }
     if (!partial) return;
@@ -738,6 +745,8 @@ __device__ __forceinline__ void rhs_gather_kernel_impl(int bid_, int nb_, int N,
     if (threadIdx.x == 0) {
         *counter = 0u;
         out[0] = a;
+        if (c32.root_a) *c32.root_a = sqrt(a) * c32.scale;
+        if (c32.root_b) *c32.root_b = sqrt(a) * c32.scale;
         if (pub) {
             pub->v = a;
             __threadfence_system();
@@ -749,10 +758,10 @@ template <int P>
 __global__ void rhs_gather_kernel(int N, int NF, const double *__restrict__ ycell, const int32_t *__restrict__ fcell,
                                   const int32_t *__restrict__ fedge, const int32_t *__restrict__ flip,
                                   double *__restrict__ g, double *partial, unsigned int *counter, double *out,
-                                  HostValue *pub, int32_t seq) {
+                                  HostValue *pub, int32_t seq, const F32Copy c32) {
     pdl_wait();
     rhs_gather_kernel_impl<P>(blockIdx.x, gridDim.x, N, NF, ycell, fcell, fedge, flip, g, partial, counter, out, pub,
-                              seq);
+                              seq, c32);
 }
 template <int P>
 struct rhs_gather_kernel_args {
@@ -769,6 +778,7 @@ struct rhs_gather_kernel_args {
     double *out;
     HostValue *pub;
     int32_t seq;
+    F32Copy c32;
 };
 template <int P>
 __global__ void rhs_gather_kernel_multi(const __grid_constant__ MultiP<rhs_gather_kernel_args<P>> M) {
@@ -776,13 +786,13 @@ __global__ void rhs_gather_kernel_multi(const __grid_constant__ MultiP<rhs_gathe
     int b_;
     const rhs_gather_kernel_args<P> &q_ = M.a[merge_find(M.start, M.n, b_)];
     rhs_gather_kernel_impl<P>(b_, q_.nb_, q_.N, q_.NF, q_.ycell, q_.fcell, q_.fedge, q_.flip, q_.g, q_.partial,
-                              q_.counter, q_.out, q_.pub, q_.seq);
+                              q_.counter, q_.out, q_.pub, q_.seq, q_.c32);
 }
 template <int P>
 void rhs_gather_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int N, int NF,
                           const double *ycell, const int32_t *fcell, const int32_t *fedge, const int32_t *flip,
                           double *g, double *partial, unsigned int *counter, double *out, HostValue *pub,
-                          int32_t seq) {
+                          int32_t seq, const F32Copy &c32) {
     if (Recorder *r_ = batch_recorder()) {
         rhs_gather_kernel_args<P> q_;
         std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
@@ -799,12 +809,13 @@ void rhs_gather_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStr
         q_.out = out;
         q_.pub = pub;
         q_.seq = seq;
+        q_.c32 = c32;
         batch_record(r_, reinterpret_cast<const void *>(&rhs_gather_kernel_multi<P>), q_, grid_, block_, smem_,
                      kPdlFamily);
         return;
     }
     pdl_launch(kPdlFamily, &rhs_gather_kernel<P>, grid_, block_, smem_, s_, N, NF, ycell, fcell, fedge, flip, g,
-               partial, counter, out, pub, seq);
+               partial, counter, out, pub, seq, c32);
 }
 
 
@@ -1081,7 +1092,7 @@ cudaError_t launch_to_external(hdg_handle *h, const double *in, double *ext) {
 cudaError_t launch_rhs_gather(hdg_handle *h, const double *ycell, double *g, const NormOut &nrm) {
     HDG_DISPATCH_P(h->p, (rhs_gather_kernel_go<P>(blocks(h->NF, h->bs_facet), h->bs_facet, 0, h->stream, h->N, h->NF,
                                                   ycell, h->d_facet_cell, h->d_facet_edge, h->d_flip, g, nrm.partial,
-                                                  nrm.counter, nrm.out, nrm.pub, nrm.seq)));
+                                                  nrm.counter, nrm.out, nrm.pub, nrm.seq, nrm.f32)));
     return cudaGetLastError();
 }
 
