@@ -376,8 +376,9 @@ def gpu_arm(args, rank: int, world: int):
         infos = []
 
         def step():
+            # the recovery reads this solve's lambda from the handle (lambda = NULL)
             infos.append(s.solve_dev(ru_d, rh_d, lam_d))
-            s.recover_dev(ru_d, rh_d, lam_d, u_d, h_d)
+            s.recover_dev(ru_d, rh_d, None, u_d, h_d)
 
         clocks = ClockSampler(dev.index, args.clocks_csv) if arm == "mixed" else None
         for _ in range(args.warmup):
@@ -1004,11 +1005,11 @@ def profile_solve_main(args):
     h = torch.empty((s.n_cells, s.n_p), dtype=torch.float64, device="cuda")
     for _ in range(max(args.warmup, 1)):
         s.solve_dev(ru_d, rh_d, lam)
-        s.recover_dev(ru_d, rh_d, lam, u, h)
+        s.recover_dev(ru_d, rh_d, None, u, h)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
     info = s.solve_dev(ru_d, rh_d, lam)
-    s.recover_dev(ru_d, rh_d, lam, u, h)
+    s.recover_dev(ru_d, rh_d, None, u, h)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     print(json.dumps({"profile_solve": args.profile_solve, "workload": workload_label(args.workload, args.p,

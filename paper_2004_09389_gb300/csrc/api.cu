@@ -76,7 +76,8 @@ struct Workspace {
     double *scal = nullptr;   // restart normalisation of a Krylov cycle
     double *bnorm = nullptr;  // ||b|| of the current Krylov solve
     // CUDA graphs of one Arnoldi step per (precision, j); see arnoldi_step
-    struct StepGraph { cudaGraphExec_t exec = nullptr; int64_t counts[HDG_PROF_N] = {}; };
+    struct StepGraph { cudaGraphExec_t exec = nullptr; int64_t counts[HDG_PROF_N] = {}; const void *src = nullptr; };
+    // slots 0..m-1: step j; slot m: step 0 forming v_0 from the right-hand side (src)
     std::vector<StepGraph> graphs[3];   // FP64, FP32, FP32 with the learned sweep
     bool use_graphs = true;
     double *beta = nullptr;   // refinement scale ||g - S x|| (mixed mode)
@@ -519,9 +520,10 @@ cudaError_t precond_lf(hdg_handle *h, const double *v, double *z, const double *
 }
 
 // With w_src (Arnoldi steps j >= 1, n_pre >= 1), v is first formed as
-// w_src / h_{j+1,j} by the first smoothing sweep, which stores it to v.
+// w_src / h_{j+1,j} by the first smoothing sweep, which stores it to v (with
+// hsrc: w_src / hsrc[0] instead, the first step of a cycle).
 template <typename T>
-cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr) {
+cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr, const double *hsrc = nullptr) {
     if (h->prm.flux == 1) {
         if constexpr (std::is_same<T, double>::value) return precond_lf(h, v, z, w_src);
         return cudaErrorInvalidValue;
@@ -537,7 +539,7 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr) {
         // Chebyshev iteration from zero: x_1 = s_0 D^-1 v, then x_{k+1} = x_k +
         // 2 s_k D^-1 (v - S x_k) + delta^2 s_k s_{k-1} (x_k - x_{k-1})
         if ((e = KL(cat_first<T>(), 1,
-                    launch_smooth_first_t<T>(h, v, x, w_src, w_src ? &h->ws->rb->hnext : nullptr,
+                    launch_smooth_first_t<T>(h, v, x, w_src, w_src ? (hsrc ? hsrc : &h->ws->rb->hnext) : nullptr,
                                              const_cast<T *>(v), h->cheb_omega[0]))) != cudaSuccess)
             return e;
         T *prev = nullptr;
@@ -554,7 +556,7 @@ cudaError_t precond(hdg_handle *h, const T *v, T *z, const T *w_src = nullptr) {
         if ((e = KL(HDG_PROF_KRYLOV, 1, launch_fill<T>(x, T(0), NT, s))) != cudaSuccess) return e;
     } else {
         if ((e = KL(cat_first<T>(), 1,
-                    launch_smooth_first_t<T>(h, v, x, w_src, w_src ? &h->ws->rb->hnext : nullptr,
+                    launch_smooth_first_t<T>(h, v, x, w_src, w_src ? (hsrc ? hsrc : &h->ws->rb->hnext) : nullptr,
                                              const_cast<T *>(v)))) != cudaSuccess)
             return e;
         for (int i = 1; i < h->prm.n_pre; ++i) {
@@ -738,7 +740,7 @@ int norm_host(hdg_handle *h, const T *v, double &out) {
 // Every argument is a fixed device address, so the step can be captured once
 // in a CUDA graph and replayed.
 template <typename T>
-cudaError_t arnoldi_step(hdg_handle *h, int j) {
+cudaError_t arnoldi_step(hdg_handle *h, int j, const T *src0 = nullptr) {
     Workspace &W = *h->ws;
     KSpace<T> &k = kspace<T>(h);
     cudaStream_t s = h->stream;
@@ -762,8 +764,11 @@ cudaError_t arnoldi_step(hdg_handle *h, int j) {
             return e;
         fuse_scale = true;
     } else {
-        // v_j = w / h_{j,j-1} rides on the first smoothing sweep (w and h from step j-1)
-        if ((e = precond<T>(h, vj, zj, (fuse_scale && j > 0) ? k.w : nullptr)) != cudaSuccess) return e;
+        // v_j = w / h_{j,j-1} rides on the first smoothing sweep (w and h from step j-1);
+        // with src0, v_0 = src0 / ||src0|| (the scale the cycle left in W.scal)
+        if (j == 0 && src0) e = precond<T>(h, vj, zj, src0, W.scal);
+        else e = precond<T>(h, vj, zj, (fuse_scale && j > 0) ? k.w : nullptr);
+        if (e != cudaSuccess) return e;
     }
     // w = S z_j with the first Gram-Schmidt pass h1 = V^T w in the same kernel
     if ((e = KL(cat_apply<T>(), 1, launch_apply_dots_t<T>(h, zj, k.w, k.V, ld, j + 1, W.partial, W.counter, W.h1))) !=
@@ -809,20 +814,25 @@ int wait_readback(hdg_handle *h, int j) {
 // Run Arnoldi step j: directly while kernel timing is on, otherwise through
 // its CUDA graph (captured on first use).
 template <typename T>
-int run_arnoldi_step(hdg_handle *h, int j) {
+int run_arnoldi_step(hdg_handle *h, int j, const T *src0 = nullptr) {
     Workspace &W = *h->ws;
     cudaStream_t s = h->stream;
     if (h->prof.on || !W.use_graphs || h->lc.collecting || batch_recorder()) {
-        TRY(arnoldi_step<T>(h, j));
+        TRY(arnoldi_step<T>(h, j, src0));
         return HDG_OK;
     }
     const int gi = sizeof(T) == 8 ? 0 : ((h->lc.on && !h->lc.suspended) ? 2 : 1);
-    Workspace::StepGraph &G = W.graphs[gi][j];
+    Workspace::StepGraph &G = W.graphs[gi][(j == 0 && src0) ? W.m : j];
+    if (G.exec && G.src != static_cast<const void *>(src0)) {   // captured for another right-hand side
+        cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+    }
     if (!G.exec) {
         int64_t before[HDG_PROF_N];
         std::memcpy(before, h->prof.launches, sizeof(before));
+        G.src = src0;
         TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = arnoldi_step<T>(h, j);
+        cudaError_t e = arnoldi_step<T>(h, j, src0);
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(s, &graph);
         for (int c = 0; c < HDG_PROF_N; ++c) {
@@ -851,7 +861,7 @@ int run_arnoldi_step(hdg_handle *h, int j) {
 // still write the slot: that write comes first in the stream, so it is waited
 // for before the slot is cleared.
 template <typename T>
-int launch_arnoldi_step(hdg_handle *h, int j) {
+int launch_arnoldi_step(hdg_handle *h, int j, const T *src0 = nullptr) {
     Workspace &W = *h->ws;
     if (W.rb_pending[j]) {
         const int rc = wait_readback(h, j);
@@ -859,7 +869,7 @@ int launch_arnoldi_step(hdg_handle *h, int j) {
     }
     W.host_rb[j].seq = 0;
     W.rb_pending[j] = 1;
-    return run_arnoldi_step<T>(h, j);
+    return run_arnoldi_step<T>(h, j, src0);
 }
 
 // Steps launched ahead: HDG_SPECULATE unset, a margin (> 1) or 0 (off), read
@@ -876,13 +886,25 @@ double speculation_margin() {
     return v;
 }
 
+// The mixed refinement's iterate as seen by an inner solve: the last cycle of
+// the inner solve adds its correction scale * (x + Z y) straight into the
+// float pairs (ff_finish) instead of updating x; done says it has.
+struct PairsOut {
+    float2 *x2 = nullptr;
+    const double *scale = nullptr;
+    bool first = false;    // the refinement iterate is still zero
+    bool x_zero = false;   // (per cycle) the inner iterate x is still zero
+    bool done = false;
+};
+
 // One FGMRES cycle (at most m iterations, possibly fewer) on S x = b starting
 // from x, with the current residual r0 = b - S x of norm beta already in
 // k.V[0] (scaled).  Stops when the estimate drops below tol_abs / bnorm.
 // Returns the number of iterations; x is updated.
 template <typename T>
 int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_target, int max_it, int &its_done,
-                 double &est_out, int &flag_out, bool beta_on_device = false) {
+                 double &est_out, int &flag_out, bool beta_on_device = false, PairsOut *po = nullptr,
+                 const T *src0 = nullptr) {
     Workspace &W = *h->ws;
     KSpace<T> &k = kspace<T>(h);
     cudaStream_t s = h->stream;
@@ -915,7 +937,7 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
     const double est0 = est_out;
     for (; j < m && j < max_it; ++j) {
         int rc;
-        if (!launched[j] && (rc = launch_arnoldi_step<T>(h, j))) return rc;
+        if (!launched[j] && (rc = launch_arnoldi_step<T>(h, j, j == 0 ? src0 : nullptr))) return rc;
         if (ahead_ok && j >= 1 && j + 1 < m && j + 1 < max_it) {
             const double e1 = hist[j - 1], e2 = j >= 2 ? hist[j - 2] : est0;
             if (e2 > 0.0 && e1 * (e1 / e2) > margin * rel_target) {
@@ -946,6 +968,16 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
     }
     its_done = j;
     if (j > 0 && !(flag_out & 4)) {
+        // the inner solve ends with this cycle (the caller trusts the estimate)
+        const bool last = est_out <= rel_target || j >= max_it;
+        if constexpr (std::is_same<T, float>::value) {
+            if (po && po->x2 && last) {
+                TRY(KL(HDG_PROF_KRYLOV, 1, launch_ff_finish(W.Hm, ldh, W.sv, j, k.Z, W.ld, po->x_zero ? nullptr : x,
+                                                           po->x2, po->scale, NT, po->first, s)));
+                po->done = true;
+                return HDG_OK;
+            }
+        }
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_hessenberg_solve(W.Hm, ldh, W.sv, j, W.y, s)));
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_multi_axpy<T>(x, k.Z, W.ld, j, W.y, 1.0, NT, s)));
     }
@@ -964,7 +996,8 @@ int fgmres_cycle(hdg_handle *h, T *x, double beta, double bnorm, double rel_targ
 // has already written that norm there.
 template <typename T>
 int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_residual, bool x_zero,
-           hdg_solve_info &info, bool unit_rhs = false, bool norm_ready = false, bool norm_pending = false) {
+           hdg_solve_info &info, bool unit_rhs = false, bool norm_ready = false, bool norm_pending = false,
+           PairsOut *po = nullptr) {
     Workspace &W = *h->ws;
     KSpace<T> &k = kspace<T>(h);
     cudaStream_t s = h->stream;
@@ -1014,10 +1047,16 @@ int fgmres(hdg_handle *h, const T *b, T *x, double rtol, int max_it, bool true_r
             W.host_buf[1] = beta;
             TRY(dcopy(h, W.scal, W.host_buf + 1, sizeof(double), cudaMemcpyHostToDevice));
         }
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_scale_copy<T>(r0, k.V, W.scal, W.NT, s)));
+        // v_0 = r0 / beta: formed by the first step's first smoothing sweep when r0 is
+        // the right-hand side itself (a first cycle from a zero guess), else copied here
+        const bool v0_fused = first && x_zero && h->prm.n_pre >= 1 && h->prm.flux == 0 &&
+                              !(std::is_same<T, double>::value && mode_pre32(h->prm));
+        if (!v0_fused) TRY(KL(HDG_PROF_KRYLOV, 1, launch_scale_copy<T>(r0, k.V, W.scal, W.NT, s)));
         int done, flag;
         double est;
-        rc = fgmres_cycle<T>(h, x, beta, bnorm, rtol, max_it - total, done, est, flag, beta_dev);
+        if (po) po->x_zero = first && x_zero;
+        rc = fgmres_cycle<T>(h, x, beta, bnorm, rtol, max_it - total, done, est, flag, beta_dev,
+                             true_residual ? nullptr : po, v0_fused ? r0 : nullptr);
         if (rc) return rc;
         total += done;
         info.iters = total;
@@ -1101,13 +1140,19 @@ int solve_mixed_steps(hdg_handle *h, const double *g, hdg_solve_info &info, bool
         }
         hdg_solve_info inner{};
         const double inner_tol = std::max(h->prm.inner_rtol, 0.5 * h->prm.rtol * bnorm / beta);
-        rc = fgmres<float>(h, k.b, k.x, inner_tol, h->prm.max_iter - total, false, true, inner, true, true);
+        // (the inner solve's last cycle adds x += scale * d itself)
+        PairsOut po;
+        po.x2 = W.x2;
+        po.scale = W.beta;
+        po.first = !updated;
+        rc = fgmres<float>(h, k.b, k.x, inner_tol, h->prm.max_iter - total, false, true, inner, true, true, false,
+                           &po);
         if (rc && rc != HDG_ENOCONV) return rc;
         total += inner.iters;
         info.iters = total;
         info.est_rel_res = inner.est_rel_res;
         // x += scale * d (the first correction is x itself)
-        TRY(KL(HDG_PROF_KRYLOV, 1, launch_ff_axpy(W.x2, k.x, W.beta, W.NT, !updated, s)));
+        if (!po.done) TRY(KL(HDG_PROF_KRYLOV, 1, launch_ff_axpy(W.x2, k.x, W.beta, W.NT, !updated, s)));
         updated = true;
     }
 }
@@ -1529,7 +1574,7 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(dalloc(&W.est, 1));
     TRY(dalloc(&W.scal, 1));
     TRY(dalloc(&W.bnorm, 1));
-    for (auto &gv : W.graphs) gv.resize(W.m);
+    for (auto &gv : W.graphs) gv.resize(W.m + 1);
     {
         const char *ev = std::getenv("HDG_DISABLE_GRAPHS");
         W.use_graphs = !(ev && ev[0] == '1');

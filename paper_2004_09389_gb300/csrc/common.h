@@ -737,6 +737,11 @@ cudaError_t launch_split_pairs(const double *a, float2 *out, int rows, int cols,
 constexpr int kResFFFacets = 64;
 // x2 += scale[0] * d in two-float arithmetic (first: x2 = scale[0] * d)
 cudaError_t launch_ff_axpy(float2 *x2, const float *d, const double *scale, size_t n, bool first, cudaStream_t s);
+// the last cycle of a mixed inner solve: y = R^-1 s (k x k rotated Hessenberg
+// triangle), d = x + Z y (x null: zero), x2 += scale[0] * d in two-float
+// arithmetic (first: x2 = scale[0] * d); k <= 64
+cudaError_t launch_ff_finish(const double *Hm, int ldh, const double *sv, int k, const float *Z, size_t ld,
+                             const float *x, float2 *x2, const double *scale, size_t n, bool first, cudaStream_t s);
 // a = b = hi + lo of each pair (b may be null)
 cudaError_t launch_ff_join(const float2 *x2, double *a, double *b, size_t n, cudaStream_t s);
 cudaError_t launch_residual_ff(hdg_handle *h, const double *b, const float2 *x2, double *res,

@@ -19,8 +19,10 @@
 
 namespace hdg {
 
-// launch family of this file for pdl_launch (facet-row kernels)
+// launch family of this file for pdl_launch (facet-row kernels); the kernel
+// that ends an inner solve goes with the Krylov kernels
 constexpr unsigned kPdlFamily = 1;
+constexpr unsigned kPdlKrylov = 4;
 
 namespace {
 
@@ -85,6 +87,20 @@ __device__ __forceinline__ void row_pairs(FFAcc &acc, const float4 *__restrict__
 // TwoSum of the leading parts, the trailing parts added to its error and a
 // renormalisation (about 2^-46 relative).  first: the iterate is zero and not
 // read.
+__device__ __forceinline__ float2 ff_add_scaled(float2 xv, float2 sc, float di, bool first) {
+    const float ph = __fmul_rn(sc.x, di);
+    const float pl = __fmaf_rn(sc.y, di, __fmaf_rn(sc.x, di, -ph));
+    if (first) {
+        const float t = __fadd_rn(ph, pl);
+        return make_float2(t, __fsub_rn(pl, __fsub_rn(t, ph)));
+    }
+    const float t = __fadd_rn(xv.x, ph);
+    const float bp = __fsub_rn(t, xv.x);
+    float e = __fadd_rn(__fsub_rn(xv.x, __fsub_rn(t, bp)), __fsub_rn(ph, bp));
+    e = __fadd_rn(e, __fadd_rn(xv.y, pl));
+    const float hi = __fadd_rn(t, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, t)));
+}
 __device__ __forceinline__ void ff_axpy_kernel_impl(int bid_, int nb_, float2 *__restrict__ x2,
                                                     const float *__restrict__ d, const double *__restrict__ scale,
                                                     size_t n, int first) {
@@ -97,19 +113,7 @@ __device__ __forceinline__ void ff_axpy_kernel_impl(int bid_, int nb_, float2 *_
     if (threadIdx.x == 0) sc = split(scale[0]);
     __syncthreads();
     if (!on) return;
-    const float ph = __fmul_rn(sc.x, di);
-    const float pl = __fmaf_rn(sc.y, di, __fmaf_rn(sc.x, di, -ph));
-    if (first) {
-        const float t = __fadd_rn(ph, pl);
-        x2[i] = make_float2(t, __fsub_rn(pl, __fsub_rn(t, ph)));
-        return;
-    }
-    const float t = __fadd_rn(xv.x, ph);
-    const float bp = __fsub_rn(t, xv.x);
-    float e = __fadd_rn(__fsub_rn(xv.x, __fsub_rn(t, bp)), __fsub_rn(ph, bp));
-    e = __fadd_rn(e, __fadd_rn(xv.y, pl));
-    const float hi = __fadd_rn(t, e);
-    x2[i] = make_float2(hi, __fsub_rn(e, __fsub_rn(hi, t)));
+    x2[i] = ff_add_scaled(xv, sc, di, first != 0);
 }
 __global__ void ff_axpy_kernel(float2 *__restrict__ x2, const float *__restrict__ d, const double *__restrict__ scale,
                                size_t n, int first) {
@@ -145,6 +149,124 @@ void ff_axpy_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream
         return;
     }
     pdl_launch(kPdlFamily, &ff_axpy_kernel, grid_, block_, smem_, s_, x2, d, scale, n, first);
+}
+
+// The end of the last cycle of an inner solve of the mixed refinement, in one
+// pass: y = R^-1 s for the leading k x k triangle of the rotated Hessenberg
+// matrix (column-major, leading dimension ldh), solved by one thread of every
+// block with the substitution of the separate triangular-solve kernel; d = x +
+// sum_c y_c Z_c with the FP32 sums of the separate basis update (x null: the
+// inner iterate is still zero); then the refinement iterate's pairs +=
+// scale[0] * d as ff_axpy forms it (first: pairs = scale[0] * d).  The same
+// values as those three kernels, bit for bit.  Each thread takes kFinU entries
+// a block width apart.
+constexpr int kFinU = 8;
+__device__ __forceinline__ void ff_finish_kernel_impl(int bid_, int nb_, const double *__restrict__ Hm, int ldh,
+                                                      const double *__restrict__ sv, int k,
+                                                      const float *__restrict__ Z, size_t ld,
+                                                      const float *__restrict__ x, float2 *__restrict__ x2,
+                                                      const double *__restrict__ scale, size_t n, int first) {
+    extern __shared__ double R[];          // k x k, R[i * k + l] = row i, column l
+    __shared__ double sS[64], yS[64];
+    __shared__ float cf[64];
+    __shared__ float2 sc;
+    __shared__ double scl;
+    if (threadIdx.x == 0) scl = scale[0];
+    // the entries' x first (they do not wait for y)
+    const size_t base = size_t(bid_) * blockDim.x * kFinU + threadIdx.x;
+    float acc[kFinU];
+#pragma unroll
+    for (int u = 0; u < kFinU; ++u) {
+        const size_t i = base + size_t(u) * blockDim.x;
+        acc[u] = (x && i < n) ? x[i] : 0.0f;
+    }
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+        const int l = t / k, i = t % k;            // column l, row i
+        if (i <= l) R[i * k + l] = Hm[size_t(l) * ldh + i];
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) sS[i] = sv[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = k - 1; i >= 0; --i) {
+            double t = sS[i];
+            for (int l = i + 1; l < k; ++l) t -= R[i * k + l] * yS[l];
+            yS[i] = t / R[i * k + i];
+        }
+        sc = split(scl);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) cf[i] = float(1.0 * yS[i]);
+    __syncthreads();
+    // basis vector by basis vector, kFinU independent loads each and two
+    // vectors' loads in flight (each entry still adds its terms in the order
+    // c = 0, 1, ...)
+#pragma unroll 2
+    for (int c = 0; c < k; ++c) {
+        const float cc = cf[c];
+        const float *Zc = Z + size_t(c) * ld;
+#pragma unroll
+        for (int u = 0; u < kFinU; ++u) {
+            const size_t i = base + size_t(u) * blockDim.x;
+            if (i < n) acc[u] = fma(cc, Zc[i], acc[u]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kFinU; ++u) {
+        const size_t i = base + size_t(u) * blockDim.x;
+        if (i < n) x2[i] = ff_add_scaled(first ? make_float2(0.0f, 0.0f) : x2[i], sc, acc[u], first != 0);
+    }
+}
+__global__ void __launch_bounds__(256, 4) ff_finish_kernel(const double *__restrict__ Hm, int ldh,
+                                                        const double *__restrict__ sv, int k,
+                                                        const float *__restrict__ Z, size_t ld,
+                                                        const float *__restrict__ x, float2 *__restrict__ x2,
+                                                        const double *__restrict__ scale, size_t n, int first) {
+    pdl_wait();
+    ff_finish_kernel_impl(blockIdx.x, gridDim.x, Hm, ldh, sv, k, Z, ld, x, x2, scale, n, first);
+}
+struct ff_finish_kernel_args {
+    int nb_;
+    const double *Hm;
+    int ldh;
+    const double *sv;
+    int k;
+    const float *Z;
+    size_t ld;
+    const float *x;
+    float2 *x2;
+    const double *scale;
+    size_t n;
+    int first;
+};
+__global__ void __launch_bounds__(256, 4) ff_finish_kernel_multi(const __grid_constant__ MultiP<ff_finish_kernel_args> M) {
+    pdl_wait();
+    int b_;
+    const ff_finish_kernel_args &q_ = M.a[merge_find(M.start, M.n, b_)];
+    ff_finish_kernel_impl(b_, q_.nb_, q_.Hm, q_.ldh, q_.sv, q_.k, q_.Z, q_.ld, q_.x, q_.x2, q_.scale, q_.n, q_.first);
+}
+void ff_finish_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, const double *Hm, int ldh,
+                         const double *sv, int k, const float *Z, size_t ld, const float *x, float2 *x2,
+                         const double *scale, size_t n, int first) {
+    if (Recorder *r_ = batch_recorder()) {
+        ff_finish_kernel_args q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.Hm = Hm;
+        q_.ldh = ldh;
+        q_.sv = sv;
+        q_.k = k;
+        q_.Z = Z;
+        q_.ld = ld;
+        q_.x = x;
+        q_.x2 = x2;
+        q_.scale = scale;
+        q_.n = n;
+        q_.first = first;
+        batch_record(r_, reinterpret_cast<const void *>(&ff_finish_kernel_multi), q_, grid_, block_, smem_,
+                     kPdlKrylov);
+        return;
+    }
+    pdl_launch(kPdlKrylov, &ff_finish_kernel, grid_, block_, smem_, s_, Hm, ldh, sv, k, Z, ld, x, x2, scale, n, first);
 }
 
 // a = b = hi + lo of the pairs, rounded once to FP64 (within 2^-53 of the
@@ -500,6 +622,16 @@ cudaError_t launch_split_pairs(const double *a, float2 *out, int rows, int cols,
 cudaError_t launch_ff_axpy(float2 *x2, const float *d, const double *scale, size_t n, bool first, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     ff_axpy_kernel_go(blocks(n, 256), 256, 0, s, x2, d, scale, n, first ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ff_finish(const double *Hm, int ldh, const double *sv, int k, const float *Z, size_t ld,
+                             const float *x, float2 *x2, const double *scale, size_t n, bool first, cudaStream_t s) {
+    if (n == 0 || k <= 0) return cudaSuccess;
+    if (k > 64) return cudaErrorInvalidValue;
+    const size_t per = size_t(256) * kFinU;
+    ff_finish_kernel_go(unsigned((n + per - 1) / per), 256, sizeof(double) * size_t(k) * k, s, Hm, ldh, sv, k, Z, ld,
+                        x, x2, scale, n, first ? 1 : 0);
     return cudaGetLastError();
 }
 

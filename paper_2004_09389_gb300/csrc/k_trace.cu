@@ -123,6 +123,9 @@ __device__ __forceinline__ void block_solve_packed(const DT *__restrict__ Dinv, 
 // 256-thread blocks fit per SM (one wave over the facets of large meshes);
 // FP64 ones are bound by the FP64 pipe and keep their registers.
 template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 6 : 1; };
+// the operator kernel with the Gram-Schmidt dots: as above for FP32 (one wave),
+// four blocks per SM for FP64
+template <typename T> struct DotsMinBlocks { static constexpr int value = sizeof(T) == 4 ? 6 : 4; };
 
 template <int P, typename T, typename ST>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value) apply_kernel(int NF, const ST *__restrict__ Sval, const int32_t *__restrict__ nbr,
@@ -199,7 +202,7 @@ __device__ __forceinline__ void apply_dots_kernel_impl(int bid_, int nb_, int NF
     if (threadIdx.x == 0) *counter = 0u;
 }
 template <int P, typename T, typename ST>
-__global__ void __launch_bounds__(256, 4) apply_dots_kernel(int NF, const ST *__restrict__ Sval,
+__global__ void __launch_bounds__(256, DotsMinBlocks<T>::value) apply_dots_kernel(int NF, const ST *__restrict__ Sval,
                                                             const int32_t *__restrict__ nbr, const T *__restrict__ x,
                                                             T *__restrict__ y, const T *__restrict__ V, size_t ld,
                                                             int k, double *__restrict__ partial,
@@ -224,7 +227,7 @@ struct apply_dots_kernel_args {
     double *h;
 };
 template <int P, typename T, typename ST>
-__global__ void __launch_bounds__(256, 4) apply_dots_kernel_multi(const __grid_constant__ MultiP<apply_dots_kernel_args<P, T, ST>> M) {
+__global__ void __launch_bounds__(256, DotsMinBlocks<T>::value) apply_dots_kernel_multi(const __grid_constant__ MultiP<apply_dots_kernel_args<P, T, ST>> M) {
     pdl_wait();
     int b_;
     const apply_dots_kernel_args<P, T, ST> &q_ = M.a[merge_find(M.start, M.n, b_)];
