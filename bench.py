@@ -375,10 +375,13 @@ def gpu_arm(args, rank: int, world: int):
         h_d = torch.empty((s.n_cells, s.n_p), dtype=torch.float64, device=dev)
         infos = []
 
+        # the recovery of this solve: lambda from the handle (NULL); a two-float handle
+        # also takes what its step 1 kept of the right-hand side (NULL r_u, r_h)
+        rec_r = (None, None) if prec in (HDG_MIXED_FP32, HDG_MIXED_BF16) else (ru_d, rh_d)
+
         def step():
-            # the recovery reads this solve's lambda from the handle (lambda = NULL)
             infos.append(s.solve_dev(ru_d, rh_d, lam_d))
-            s.recover_dev(ru_d, rh_d, None, u_d, h_d)
+            s.recover_dev(rec_r[0], rec_r[1], None, u_d, h_d)
 
         clocks = ClockSampler(dev.index, args.clocks_csv) if arm == "mixed" else None
         for _ in range(args.warmup):
@@ -446,6 +449,7 @@ def gpu_arm(args, rank: int, world: int):
                         e2e_s=e2e_s, levels_nv=[lv.n_vertices for lv in levels],
                         condense_ms=condense_ms, n_p=s.n_p, prof_steps=nprof, tuned=tuned,
                         h2d=h2d, d2h=d2h, NF=NF, pp=pp, n_cells=s.n_cells,
+                        keep_z=prec in (HDG_MIXED_FP32, HDG_MIXED_BF16),
                         coarse=(f"P1 geometric V-cycle over {len(levels)} levels, {levels[0].n_vertices:,} -> "
                                 f"{levels[-1].n_vertices} vertices (dense coarsest solve)"),
                         data_gb=(8.0 * s.n_cells * (nK * nK + 2 * nK * m) + 8.0 * NF * 5 * pp * pp) / 1e9)
@@ -460,6 +464,19 @@ def gpu_arm(args, rank: int, world: int):
     return out, fma
 
 
+def step13_bytes(arm: dict):
+    """Algorithmic bytes of one condensed right-hand side (cell and gather
+    kernels together) and of one recovery.  Two-float handles keep z_K = R_M r_K
+    in step 1: its cell kernel reads R_M, r and the cell geometry (9 float pairs)
+    and writes z and the cell rows; the recovery reads X_B, z and lambda and
+    writes u, h.  FP64 handles read W_K, r in step 1 and R_M, X_B, r, lambda in
+    step 3."""
+    N, nK, m = arm["n_cells"], 3 * arm["n_p"], 3 * arm["pp"]
+    if arm.get("keep_z"):
+        return 8.0 * N * (nK * nK + 2 * nK + m) + 72.0 * N, 8.0 * N * (nK * m + 2 * nK + m)
+    return 8.0 * N * (m * nK + nK + m), 8.0 * N * (nK * nK + nK * m + 3 * nK + m)
+
+
 def whole_solve(arm: dict, peaks: dict, steps: int) -> dict:
     """Algorithmic bytes of one solve's facet-row kernels, condensed right-hand
     side and recovery (launch counts from the library's accounting) over the
@@ -472,10 +489,10 @@ def whole_solve(arm: dict, peaks: dict, steps: int) -> dict:
     for cat, (_, n) in prof.items():
         if n and cat.startswith(("apply", "residual", "smooth")):
             total += trace_bytes(cat, NF, pp) * n / ps
-    # rhs: W and r read, the cell rows written (two launches per call); recovery:
-    # A^-1 Mass and A^-1 B read, r and lambda read, u and h written
-    total += 8.0 * N * (m * nK + nK + m) * (prof["rhs"][1] / 2) / ps
-    total += 8.0 * N * (nK * nK + nK * m + 2 * nK + m) * prof["recover"][1] / ps
+    # step 1 (two launches per call) and step 3
+    rhs_b, rec_b = step13_bytes(arm)
+    total += rhs_b * (prof["rhs"][1] / 2) / ps
+    total += rec_b * prof["recover"][1] / ps
     ms = arm["ms"] / steps
     achieved = total / (ms * 1e-3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
@@ -562,9 +579,9 @@ def roofline(arm: dict, peaks: dict, fma: dict | None = None, bf16_pre: bool = F
         _kernel_entry("P1 V-cycle (all P1 kernels)", prof, cold, "p1",
                       p1_cycle_bytes(arm["levels_nv"], w32) * ncyc / max(prof["p1"][1], 1), peak, total,
                       "levels up to 32,768 vertices are L2-resident in the running solve: latency-bound"),
-        _kernel_entry("recover", prof, cold, "recover", 8.0 * N * (nK * nK + nK * m + 3 * nK + m), peak, total),
-        _kernel_entry("condensed RHS (cell + gather kernels)", prof, cold, "rhs",
-                      8.0 * N * (m * nK + nK + m) / 2, peak, total),
+        _kernel_entry("recover", prof, cold, "recover", step13_bytes(arm)[1], peak, total),
+        _kernel_entry("condensed RHS (cell + gather kernels)", prof, cold, "rhs", step13_bytes(arm)[0] / 2, peak,
+                      total),
         _kernel_entry("Krylov (Gram-Schmidt update with norm and Givens, dots, scalings)", prof, cold, "krylov",
                       None, peak, total, "reductions of (j+1) values per iteration: latency of the grid-wide sum"),
         _kernel_entry("restriction / prolongation", prof, cold, "transfer", None, peak, total),
@@ -1000,16 +1017,18 @@ def profile_solve_main(args):
     s = HDGSolver(wl["mesh"], args.p, wl["tau"], wl["g"], wl["H"], f_vertex=wl["f"], rtol=args.rtol, precision=prec,
                   inner_rtol=args.inner_rtol, restart=args.restart, reorth=args.reorth)
     ru_d, rh_d = torch.from_numpy(wl["ru"]).cuda(), torch.from_numpy(wl["rh"]).cuda()
+    # the recovery as the timed step runs it (two-float handles: NULL right-hand sides)
+    rec_r = (None, None) if prec in (HDG_MIXED_FP32, HDG_MIXED_BF16) else (ru_d, rh_d)
     lam = torch.empty((s.n_facets, args.p + 1), dtype=torch.float64, device="cuda")
     u = torch.empty((s.n_cells, 2, s.n_p), dtype=torch.float64, device="cuda")
     h = torch.empty((s.n_cells, s.n_p), dtype=torch.float64, device="cuda")
     for _ in range(max(args.warmup, 1)):
         s.solve_dev(ru_d, rh_d, lam)
-        s.recover_dev(ru_d, rh_d, None, u, h)
+        s.recover_dev(*rec_r, None, u, h)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
     info = s.solve_dev(ru_d, rh_d, lam)
-    s.recover_dev(ru_d, rh_d, None, u, h)
+    s.recover_dev(*rec_r, None, u, h)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     print(json.dumps({"profile_solve": args.profile_solve, "workload": workload_label(args.workload, args.p,

@@ -237,9 +237,17 @@ HDG_API int hdg_solve_dev(hdg_handle *h, const double *r_u, const double *r_h, d
  * call with NULLs still selects the last solve's data. */
 HDG_API int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lambda,
                 double *u, double *h_out);
-/* The same with device pointers on the handle's stream: r_u, r_h, u and h_out
- * are required (HDG_EINVAL if NULL); lambda may be NULL to use the handle's
- * last solution.  Results are complete once the stream has been synchronised. */
+/* The same with device pointers on the handle's stream: u and h_out are
+ * required (HDG_EINVAL if NULL); lambda may be NULL to use the handle's last
+ * solution; r_u and r_h may both be NULL to use the last solve's right-hand
+ * side (one NULL and one not: HDG_EINVAL).  With NULL right-hand sides a
+ * HDG_MIXED_FP32 / HDG_MIXED_BF16 handle reads what the last solve's step 1
+ * kept of it, z_K = A_K^-1 M_K r_K per cell (two-float pairs), and forms
+ * q_K = z_K - A_K^-1 B_K lambda_K: the recovery then reads no right-hand side
+ * and no A_K^-1 M_K (Eq. reconstruct_solution split at the solve's step 1).
+ * Other handles use the copies hdg_solve keeps; HDG_ESTATE if there is nothing
+ * kept (no solve yet, or the operator changed since, by hdg_condense or
+ * hdg_set_tau).  Results are complete once the stream has been synchronised. */
 HDG_API int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h, const double *lambda,
                     double *u, double *h_out);
 

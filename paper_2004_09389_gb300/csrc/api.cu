@@ -90,6 +90,10 @@ struct Workspace {
     double *ru = nullptr, *rh = nullptr, *lam_ext = nullptr, *u = nullptr, *hh = nullptr;
     double *ru_x = nullptr, *rh_x = nullptr;   // explicit hdg_recover inputs (ru/rh keep the last solve's)
     bool have_rhs = false, have_lambda = false;
+    // two-float handles: z_K = R_M r_K of the last solve's right-hand side ([nK][N]
+    // pairs, written by its step 1), valid until the operator changes
+    float2 *z2 = nullptr;
+    bool have_z = false;
     double *lam_int = nullptr;    // last solution, internal layout
 };
 
@@ -1205,6 +1209,7 @@ void free_handle(hdg_handle *h) {
     dfree(h->d_facet_cell); dfree(h->d_facet_edge); dfree(h->d_facet_verts); dfree(h->d_v2f_ptr); dfree(h->d_v2f);
     dfree(h->d_nbr); dfree(h->d_Xb); dfree(h->d_Rm); dfree(h->d_W); dfree(h->d_Scell); dfree(h->d_Sval);
     dfree(h->d_Xb2); dfree(h->d_Rm2); dfree(h->d_W2); dfree(h->d_Sval2);
+    dfree(h->d_cgeo); dfree(h->d_ctab_v); dfree(h->d_ctab_b);
     dfree(h->d_Dinv); dfree(h->d_Sval32); dfree(h->d_Dinv32); dfree(h->d_Sval16); dfree(h->d_status); dfree(h->d_coarse_inv);
     dfree(h->tail_img[0].d); dfree(h->tail_img[1].d);
     dfree(h->d_coarse_work);
@@ -1220,7 +1225,7 @@ void free_handle(hdg_handle *h) {
     }
     if (h->ws) {
         Workspace &W = *h->ws;
-        dfree(W.g); dfree(W.x); dfree(W.r); dfree(W.ycell); dfree(W.x2);
+        dfree(W.g); dfree(W.x); dfree(W.r); dfree(W.ycell); dfree(W.x2); dfree(W.z2);
         dfree(W.k64.V); dfree(W.k64.Z); dfree(W.k64.w); dfree(W.k64.t0); dfree(W.k64.t1); dfree(W.k64.res);
         dfree(W.k32.V); dfree(W.k32.Z); dfree(W.k32.w); dfree(W.k32.t0); dfree(W.k32.t1); dfree(W.k32.res);
         dfree(W.k32.b); dfree(W.k32.x);
@@ -1342,6 +1347,57 @@ void drop_graphs(hdg_handle *h) {
             }
 }
 
+// The tables of C_K formed from geometry in the solves' step 1 (two-float
+// handles): per cell and edge the pairs of H t_y, -H t_x and tau_s |e| (t the
+// edge vector, as the condensation's C_K uses them), and per row (edge i, trace
+// node j) the cell nodes b with a nonzero reference facet entry N_ibj and its
+// pair.  Those are the p + 1 nodes on the edge; another pattern leaves cz_ok
+// false and the solves read the stored W_K instead.
+float2 host_split(double v) {
+    const float hi = static_cast<float>(v);
+    return float2{hi, static_cast<float>(v - static_cast<double>(hi))};
+}
+int build_cz(hdg_handle *h, const RefElem &re) {
+    cudaStream_t s = h->stream;
+    const int np = h->np, pp = h->pp, N = h->N;
+    const HostMesh &hm = h->hm;
+    double nmax = 0.0;
+    for (double v : re.N) nmax = std::max(nmax, std::fabs(v));
+    std::vector<int32_t> tb(size_t(3) * pp * pp, 0);
+    std::vector<float2> tv(size_t(3) * pp * pp, float2{0.0f, 0.0f});
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < pp; ++j) {
+            int c = 0;
+            for (int b = 0; b < np; ++b) {
+                const double v = re.N[(size_t(i) * np + b) * pp + j];
+                if (!(std::fabs(v) > 1e-13 * nmax)) continue;
+                if (c == pp) return HDG_OK;
+                tb[(size_t(i) * pp + j) * pp + c] = b;
+                tv[(size_t(i) * pp + j) * pp + c] = host_split(v);
+                ++c;
+            }
+        }
+    const double H = h->prm.H, ts = h->tau_s;
+    std::vector<float2> cg(size_t(N) * 9);
+    for (int K = 0; K < N; ++K) {
+        const double *x = hm.X.data() + size_t(K) * 6;
+        for (int i = 0; i < 3; ++i) {
+            const int v1 = (i + 1) % 3, v2 = (i + 2) % 3;
+            const double tx = x[2 * v2] - x[2 * v1], ty = x[2 * v2 + 1] - x[2 * v1 + 1];
+            float2 *o = cg.data() + (size_t(K) * 3 + i) * 3;
+            o[0] = host_split(H * ty);
+            o[1] = host_split(-H * tx);
+            o[2] = host_split(ts * std::sqrt(tx * tx + ty * ty));
+        }
+    }
+    TRY(upload(&h->d_ctab_b, tb, s));
+    TRY(upload(&h->d_ctab_v, tv, s));
+    TRY(upload(&h->d_cgeo, cg, s));
+    TRY(cudaStreamSynchronize(s));      // the host vectors go out of scope
+    h->cz_ok = true;
+    return HDG_OK;
+}
+
 int setup_device(hdg_handle *h, const hdg_params *prm) {
     cudaStream_t s = h->stream;
     const HostMesh &hm = h->hm;
@@ -1384,6 +1440,10 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
             TRY(dalloc(&h->d_Rm2, nK * ((nK + 1) / 2 * 2) * Nt));
             TRY(dalloc(&h->d_W2, m * ((nK + 1) / 2 * 2) * Nt));
             TRY(dalloc(&h->d_Sval2, packed(5 * pp * pp, 2)));
+            if (prm->flux == 0) {
+                const int rc = build_cz(h, re);
+                if (rc) return rc;
+            }
         }
         if (prm->precision == HDG_MIXED_BF16) TRY(dalloc(&h->d_Sval16, packed(5 * pp * pp, 8)));
     }
@@ -1527,6 +1587,7 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(dalloc(&W.lam_int, W.NT));
     TRY(dalloc(&W.ycell, N * m));
     if (mode_ff(h->prm)) TRY(dalloc(&W.x2, W.NT));
+    if (h->cz_ok) TRY(dalloc(&W.z2, size_t(h->nK) * N));
     const size_t mm = W.m;
     W.ld = (W.NT + 3) / 4 * 4;
     // one 16-byte group of w per thread (enough loads in flight for the few-vector
@@ -1765,8 +1826,16 @@ int solve_internal(hdg_handle *h, const double *r_u, const double *r_h, hdg_solv
             nrm.f32.root_b = W.scal;
         }
     }
-    if (!mode_ff(h->prm)) TRY(KL(HDG_PROF_RHS, 2, launch_rhs(h, r_u, r_h, W.g, W.ycell, nrm)));
-    else TRY(KL(HDG_PROF_RHS, 2, launch_rhs_ff(h, r_u, r_h, W.g, W.ycell, copy_u, copy_h, nrm)));
+    W.have_z = false;
+    if (!mode_ff(h->prm)) {
+        TRY(KL(HDG_PROF_RHS, 2, launch_rhs(h, r_u, r_h, W.g, W.ycell, nrm)));
+    } else if (W.z2) {
+        // keeping z_K = R_M r_K for the recovery of this solve
+        TRY(KL(HDG_PROF_RHS, 2, launch_rhs_z(h, r_u, r_h, W.g, W.ycell, W.z2, copy_u, copy_h, nrm)));
+        W.have_z = true;
+    } else {
+        TRY(KL(HDG_PROF_RHS, 2, launch_rhs_ff(h, r_u, r_h, W.g, W.ycell, copy_u, copy_h, nrm)));
+    }
     int rc;
     if (mode_krylov64(h->prm)) {
         TRY(KL(HDG_PROF_KRYLOV, 1, launch_fill<double>(W.x, 0.0, W.NT, s)));
@@ -1996,6 +2065,7 @@ int hdg_condense(hdg_handle *h) {
     if (!h) return HDG_EINVAL;
     cudaStream_t s = h->stream;
     h->condensed = false;
+    if (h->ws) h->ws->have_z = false;      // z_K = R_M r_K belongs to the old operator
     TRY(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), s));
     if (h->prm.flux == 1) {
         // Lax-Friedrichs: cell operators and the facet-row operator on 2(p+1) blocks,
@@ -2149,8 +2219,13 @@ int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h, const d
                     double *h_out) {
     int rc = require_condensed(h);
     if (rc) return rc;
-    if (!u || !h_out || !r_u || !r_h) return fail(h, HDG_EINVAL, "NULL pointer argument");
+    if (!u || !h_out) return fail(h, HDG_EINVAL, "NULL output pointer");
+    if (!r_u != !r_h) return fail(h, HDG_EINVAL, "r_u and r_h must both be given or both be NULL");
     Workspace &W = *h->ws;
+    // r_u = r_h = NULL: the last solve's right-hand side, as z_K = R_M r_K kept by
+    // its step 1, else as the copies hdg_solve keeps
+    if (!r_u && !W.have_z && !W.have_rhs)
+        return fail(h, HDG_ESTATE, "no right-hand side given and none kept from the last solve");
     const double *lam = W.lam_int;
     if (lambda) {
         TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_internal(h, lambda, W.k64.res)));
@@ -2158,8 +2233,13 @@ int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h, const d
     } else if (!W.have_lambda) {
         return fail(h, HDG_ESTATE, "no lambda given and no previous solve");
     }
-    if (!mode_ff(h->prm)) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, r_u, r_h, lam, u, h_out)));
-    else TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, r_u, r_h, lam, u, h_out)));
+    if (!r_u && W.have_z) {
+        TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_z(h, W.z2, lam, u, h_out)));
+        return HDG_OK;
+    }
+    const double *ru = r_u ? r_u : W.ru, *rh = r_h ? r_h : W.rh;
+    if (!mode_ff(h->prm)) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, ru, rh, lam, u, h_out)));
+    else TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, ru, rh, lam, u, h_out)));
     return HDG_OK;
 }
 
@@ -2190,9 +2270,11 @@ int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, const doubl
             ru = W.ru_x;
             rh = W.rh_x;
         }
-    } else if (!W.have_rhs) {
-        return fail(h, HDG_ESTATE, "no right-hand side given and none kept from hdg_solve");
+    } else if (!W.have_z && !W.have_rhs) {
+        return fail(h, HDG_ESTATE, "no right-hand side given and none kept from the last solve");
     }
+    // the last solve's right-hand side as z_K = R_M r_K kept by its step 1
+    const bool from_z = !r_u && W.have_z;
     const double *lam = W.lam_int;
     if (lambda) {
         TRY(cudaMemcpyAsync(W.lam_ext, lambda, sizeof(double) * W.NT, cudaMemcpyHostToDevice, s));
@@ -2204,9 +2286,11 @@ int hdg_recover(hdg_handle *h, const double *r_u, const double *r_h, const doubl
     double *u_a = host_alias(u), *h_a = host_alias(h_out);
     if (mode_ff(h->prm) && u_a && h_a) {
         // page-locked outputs of a mixed handle: the recovery kernel writes them in place
-        TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, ru, rh, lam, u_a, h_a)));
+        if (from_z) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_z(h, W.z2, lam, u_a, h_a)));
+        else TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, ru, rh, lam, u_a, h_a)));
     } else {
-        if (!mode_ff(h->prm)) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, ru, rh, lam, W.u, W.hh)));
+        if (from_z) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_z(h, W.z2, lam, W.u, W.hh)));
+        else if (!mode_ff(h->prm)) TRY(KL(HDG_PROF_RECOVER, 1, launch_recover(h, ru, rh, lam, W.u, W.hh)));
         else TRY(KL(HDG_PROF_RECOVER, 1, launch_recover_ff(h, ru, rh, lam, W.u, W.hh)));
         TRY(cudaMemcpyAsync(u, W.u, sizeof(double) * size_t(h->N) * 2 * h->np, cudaMemcpyDeviceToHost, s));
         TRY(cudaMemcpyAsync(h_out, W.hh, sizeof(double) * size_t(h->N) * h->np, cudaMemcpyDeviceToHost, s));

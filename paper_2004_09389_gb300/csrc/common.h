@@ -558,6 +558,12 @@ struct hdg_handle {
     // mixed modes: the same three matrices and the FP64 trace operator as
     // (hi, lo) float pairs for the two-float FP64 steps (k_ff.cu)
     float2 *d_Xb2 = nullptr, *d_Rm2 = nullptr, *d_W2 = nullptr, *d_Sval2 = nullptr;
+    // C_K from geometry (two-float handles): pairs of H t_y, -H t_x, tau_s |e| per
+    // cell and edge [N][3][3]; per row of C_K the cell nodes and pairs of the
+    // nonzero reference facet entries [3(p+1)][p+1]; cz_ok once they are built
+    float2 *d_cgeo = nullptr, *d_ctab_v = nullptr;
+    int32_t *d_ctab_b = nullptr;
+    bool cz_ok = false;
     double *d_Scell = nullptr;      // S_K           [N][m][m]
     // facet-row trace operator
     double *d_Sval = nullptr;       // 5(p+1)^2 values per facet, packed in 16-byte groups
@@ -753,6 +759,11 @@ cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, d
                           double *copy_u, double *copy_h, const NormOut &nrm = NormOut());
 cudaError_t launch_recover_ff(hdg_handle *h, const double *r_u, const double *r_h, const double *lam, double *u,
                               double *hout);
+// step 1 of a solve keeping z_K = R_M r_K (pairs, [nK][N]) for step 3, C_K z_K
+// formed from the cell geometry (handles with cz_ok); step 3 from that z
+cudaError_t launch_rhs_z(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell, float2 *z2,
+                         double *copy_u, double *copy_h, const NormOut &nrm = NormOut());
+cudaError_t launch_recover_z(hdg_handle *h, const float2 *z2, const double *lam, double *u, double *hout);
 cudaError_t launch_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lam,
                            double *u, double *hout);
 

@@ -499,6 +499,151 @@ __device__ __forceinline__ void stage_cell_rhs(int N, int K0, const double *__re
     }
 }
 
+// the product of two pairs as a normalised pair (leading product by FMA with
+// its exact error, the cross terms added to it; about 2^-46 relative)
+__device__ __forceinline__ float2 ff_mul(const float2 a, const float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    const float hi = __fadd_rn(p, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, p)));
+}
+
+// Step 1 of a solve, keeping what step 3 needs: z_K = R_M r_K (= A_K^-1
+// Mass_K r_K, the cell solution for lambda = 0) in two-float arithmetic, stored
+// as normalised pairs (z2 [NK][N], when given), and the cell rows ycell =
+// C_K z_K (= W_K r_K) formed from the cell's geometry instead of a stored
+// W_K.  Row (i, j) of C_K (edge i, trace node j) is sum_b N_ibj (H t_y z_u[b]
+// - H t_x z_v[b] + tau_s |e_i| z_h[b]) with t the edge vector and N_ibj =
+// int_e phi_b mu_j, nonzero only for the cell nodes b on the edge: cgeo holds
+// the pairs of H t_y, -H t_x, tau_s |e_i| per cell and edge ([N][3][3]), ctab_b
+// / ctab_v the nodes and pairs of N per row ([3(p+1)][p+1]).  The block's 32
+// cells are the lanes; the eight warps take the rows of R_M in turn, then the
+// rows of C_K.
+template <int P>
+__device__ __forceinline__ void rhs_cell_z_kernel_impl(int bid_, int nb_, int N, const float4 *__restrict__ Rm2,
+                                                       const float2 *__restrict__ cgeo,
+                                                       const int32_t *__restrict__ ctab_b,
+                                                       const float2 *__restrict__ ctab_v,
+                                                       const double *__restrict__ r_u,
+                                                       const double *__restrict__ r_h, double *__restrict__ ycell,
+                                                       float2 *__restrict__ z2, double *__restrict__ cu,
+                                                       double *__restrict__ ch) {
+    constexpr int PP = P + 1, NP = (P + 1) * (P + 2) / 2, NK = 3 * NP, M = 3 * PP, NW = 8;
+    constexpr int KP = (NK + 1) / 2, RW = (NK + NW - 1) / NW;
+    __shared__ float2 sIn[NK][kCellsPad];      // r_K, then z_K
+    __shared__ int32_t tb[M][PP];
+    __shared__ float2 tv[M][PP];
+    for (int t = threadIdx.x; t < M * PP; t += blockDim.x) {
+        tb[t / PP][t % PP] = ctab_b[t];
+        tv[t / PP][t % PP] = ctab_v[t];
+    }
+    const int K0 = bid_ * kCells, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    stage_cell_rhs<NP>(N, K0, r_u, r_h, sIn, cu, ch);
+    __syncthreads();
+    const int K = K0 + lane;
+    const bool on = K < N;
+    float2 zr[RW];
+#pragma unroll
+    for (int u = 0; u < RW; ++u) {
+        const int rho = w + u * NW;
+        zr[u] = make_float2(0.0f, 0.0f);
+        if (on && rho < NK) {
+            FFAcc acc;
+            row_pairs<NK>(acc, Rm2 + (size_t(bid_) * NK * KP + size_t(rho) * KP) * kCells + lane, sIn, lane);
+            const float hi = __fadd_rn(acc.s, acc.c);
+            zr[u] = make_float2(hi, __fsub_rn(acc.c, __fsub_rn(hi, acc.s)));
+        }
+    }
+    __syncthreads();                            // every warp has read r_K
+#pragma unroll
+    for (int u = 0; u < RW; ++u) {
+        const int rho = w + u * NW;
+        if (rho < NK) {
+            sIn[rho][lane] = zr[u];
+            if (z2 && on) z2[size_t(rho) * N + K] = zr[u];
+        }
+    }
+    __syncthreads();
+    if (!on) return;
+    for (int t = w; t < M; t += NW) {
+        const float2 *gc = cgeo + (size_t(K) * 3 + t / PP) * 3;
+        const float2 g0 = gc[0], g1 = gc[1], g2 = gc[2];
+        FFAcc acc;
+#pragma unroll
+        for (int q = 0; q < PP; ++q) {
+            const int b = tb[t][q];
+            const float2 v = tv[t][q];
+            acc.add(ff_mul(v, g0), sIn[b][lane]);
+            acc.add(ff_mul(v, g1), sIn[NP + b][lane]);
+            acc.add(ff_mul(v, g2), sIn[2 * NP + b][lane]);
+        }
+        ycell[size_t(t) * N + K] = acc.value();
+    }
+}
+template <int P>
+__global__ void __launch_bounds__(256) rhs_cell_z_kernel(int N, const float4 *__restrict__ Rm2,
+                                                         const float2 *__restrict__ cgeo,
+                                                         const int32_t *__restrict__ ctab_b,
+                                                         const float2 *__restrict__ ctab_v,
+                                                         const double *__restrict__ r_u,
+                                                         const double *__restrict__ r_h, double *__restrict__ ycell,
+                                                         float2 *__restrict__ z2, double *__restrict__ cu,
+                                                         double *__restrict__ ch) {
+    pdl_wait();
+    rhs_cell_z_kernel_impl<P>(blockIdx.x, gridDim.x, N, Rm2, cgeo, ctab_b, ctab_v, r_u, r_h, ycell, z2, cu, ch);
+}
+template <int P>
+struct rhs_cell_z_kernel_args {
+    int nb_;
+    int N;
+    const float4 *Rm2;
+    const float2 *cgeo;
+    const int32_t *ctab_b;
+    const float2 *ctab_v;
+    const double *r_u;
+    const double *r_h;
+    double *ycell;
+    float2 *z2;
+    double *cu;
+    double *ch;
+};
+template <int P>
+__global__ void __launch_bounds__(256) rhs_cell_z_kernel_multi(const __grid_constant__ MultiP<rhs_cell_z_kernel_args<P>> M) {
+    pdl_wait();
+    int b_;
+    const rhs_cell_z_kernel_args<P> &q_ = M.a[merge_find(M.start, M.n, b_)];
+    rhs_cell_z_kernel_impl<P>(b_, q_.nb_, q_.N, q_.Rm2, q_.cgeo, q_.ctab_b, q_.ctab_v, q_.r_u, q_.r_h, q_.ycell, q_.z2,
+                              q_.cu, q_.ch);
+}
+template <int P>
+void rhs_cell_z_kernel_go(unsigned grid_, unsigned block_, size_t smem_, cudaStream_t s_, int N, const float4 *Rm2,
+                          const float2 *cgeo, const int32_t *ctab_b, const float2 *ctab_v, const double *r_u,
+                          const double *r_h, double *ycell, float2 *z2, double *cu, double *ch) {
+    if (Recorder *r_ = batch_recorder()) {
+        rhs_cell_z_kernel_args<P> q_;
+        std::memset(static_cast<void *>(&q_), 0, sizeof(q_));
+        q_.nb_ = int(grid_);
+        q_.N = N;
+        q_.Rm2 = Rm2;
+        q_.cgeo = cgeo;
+        q_.ctab_b = ctab_b;
+        q_.ctab_v = ctab_v;
+        q_.r_u = r_u;
+        q_.r_h = r_h;
+        q_.ycell = ycell;
+        q_.z2 = z2;
+        q_.cu = cu;
+        q_.ch = ch;
+        batch_record(r_, reinterpret_cast<const void *>(&rhs_cell_z_kernel_multi<P>), q_, grid_, block_, smem_,
+                     kPdlFamily);
+        return;
+    }
+    pdl_launch(kPdlFamily, &rhs_cell_z_kernel<P>, grid_, block_, smem_, s_, N, Rm2, cgeo, ctab_b, ctab_v, r_u, r_h,
+               ycell, z2, cu, ch);
+}
+
 // step 1, cell part: ycell[t][K] = sum_kappa W[t*NK + kappa][K] r_K[kappa]
 template <int P>
 __device__ __forceinline__ void rhs_cell_ff_kernel_impl(int bid_, int nb_, int N, const float4 *__restrict__ W2,
@@ -604,6 +749,45 @@ __global__ void __launch_bounds__(256) recover_ff_kernel(int N, int NF, const fl
     for (int j = threadIdx.x; j < nc * NP; j += blockDim.x) hout[size_t(K0) * NP + j] = sOut[2 * NP + j % NP][j / NP];
 }
 
+// step 3 from the kept z_K: q_K = z_K - X_B lambda_K (two-float, z as the
+// starting sum), written in the caller's u / h layout
+template <int P>
+__global__ void __launch_bounds__(256) recover_z_kernel(int N, int NF, const float2 *__restrict__ z2,
+                                                        const float4 *__restrict__ Xb2,
+                                                        const double *__restrict__ lam,
+                                                        const int32_t *__restrict__ facet_of,
+                                                        const int32_t *__restrict__ flip, double *__restrict__ u,
+                                                        double *__restrict__ hout) {
+    constexpr int PP = P + 1, NP = (P + 1) * (P + 2) / 2, NK = 3 * NP, M = 3 * PP, NW = 8;
+    constexpr int MP = (M + 1) / 2;
+    __shared__ float2 sIn[M][kCellsPad];        // lambda on the cell's three facets
+    __shared__ double sOut[NK][kCellsPad];
+    const int K0 = blockIdx.x * kCells, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nc = min(kCells, N - K0);
+    for (int j = threadIdx.x; j < nc * M; j += blockDim.x) {
+        const int cell = j / M, q = j % M, i = q / PP, jj = q % PP, K = K0 + cell;
+        const int f = facet_of[3 * K + i], fl = flip[3 * K + i];
+        sIn[q][cell] = split(lam[size_t(fl ? P - jj : jj) * NF + f]);
+    }
+    __syncthreads();
+    const int K = K0 + lane;
+    if (K < N) {
+        for (int rho = w; rho < NK; rho += NW) {
+            FFAcc acc;
+            const float2 z = z2[size_t(rho) * N + K];
+            acc.s = z.x;
+            acc.c = z.y;
+            row_pairs<M>(acc, Xb2 + (size_t(blockIdx.x) * NK * MP + size_t(rho) * MP) * kCells + lane, sIn, lane,
+                         true);
+            sOut[rho][lane] = acc.value();
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nc * 2 * NP; j += blockDim.x)
+        u[size_t(K0) * 2 * NP + j] = sOut[j % (2 * NP)][j / (2 * NP)];
+    for (int j = threadIdx.x; j < nc * NP; j += blockDim.x) hout[size_t(K0) * NP + j] = sOut[2 * NP + j % NP][j / NP];
+}
+
 }  // namespace
 
 cudaError_t launch_split(const double *a, float2 *out, size_t n, cudaStream_t s) {
@@ -656,6 +840,23 @@ cudaError_t launch_rhs_ff(hdg_handle *h, const double *r_u, const double *r_h, d
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_rhs_gather(h, ycell, g, nrm);
+}
+
+cudaError_t launch_rhs_z(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell, float2 *z2,
+                         double *copy_u, double *copy_h, const NormOut &nrm) {
+    HDG_DISPATCH_P(h->p, (rhs_cell_z_kernel_go<P>(blocks(h->N, kCells), 256, 0, h->stream, h->N,
+                                                  reinterpret_cast<const float4 *>(h->d_Rm2), h->d_cgeo, h->d_ctab_b,
+                                                  h->d_ctab_v, r_u, r_h, ycell, z2, copy_u, copy_h)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_rhs_gather(h, ycell, g, nrm);
+}
+
+cudaError_t launch_recover_z(hdg_handle *h, const float2 *z2, const double *lam, double *u, double *hout) {
+    HDG_DISPATCH_P(h->p, (recover_z_kernel<P><<<blocks(h->N, kCells), 256, 0, h->stream>>>(
+                             h->N, h->NF, z2, reinterpret_cast<const float4 *>(h->d_Xb2), lam, h->d_facet_of,
+                             h->d_flip, u, hout)));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_recover_ff(hdg_handle *h, const double *r_u, const double *r_h, const double *lam, double *u,
