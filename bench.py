@@ -901,8 +901,10 @@ def batch_main(args):
     from paper_2004_09389_gb300 import HDGSolver, HDG_MIXED_FP32, MergedBatch, build, solve_batch_dev
     build.build()
     probs = batch_workload(args.batch, args.seed)
+    # (solves only, no recovery: step 1 keeps nothing for one, keep_rhs = 0)
     solvers = [HDGSolver(x["mesh"], x["p"], x["tau"], x["g"], x["H"], f_vertex=x["f"], rtol=args.rtol,
-                         precision=HDG_MIXED_FP32, restart=args.restart, smoother=x["smoother"], max_iter=2000)
+                         precision=HDG_MIXED_FP32, restart=args.restart, smoother=x["smoother"], max_iter=2000,
+                         keep_rhs=0)
                for x in probs]
     tuned = [s.autotune() for s in solvers] if args.autotune else None
     ru = [torch.from_numpy(x["ru"]).cuda() for x in probs]
@@ -984,8 +986,10 @@ def profile_batch_main(args):
     from paper_2004_09389_gb300 import HDGSolver, HDG_MIXED_FP32, MergedBatch, build
     build.build()
     probs = batch_workload(args.batch or 64, args.seed)
+    # (solves only, no recovery: step 1 keeps nothing for one, keep_rhs = 0)
     solvers = [HDGSolver(x["mesh"], x["p"], x["tau"], x["g"], x["H"], f_vertex=x["f"], rtol=args.rtol,
-                         precision=HDG_MIXED_FP32, restart=args.restart, smoother=x["smoother"], max_iter=2000)
+                         precision=HDG_MIXED_FP32, restart=args.restart, smoother=x["smoother"], max_iter=2000,
+                         keep_rhs=0)
                for x in probs]
     ru = [torch.from_numpy(x["ru"]).cuda() for x in probs]
     rh = [torch.from_numpy(x["rh"]).cuda() for x in probs]

@@ -158,6 +158,13 @@ typedef struct {
                                        approximately by n_coarse Chebyshev steps).  Flat
                                        meshes, HDG_FP64, p = 1 or 2, coarse_mode 0 or 1.   */
     int32_t       n_coarse;     /* flux 1: Chebyshev steps of the RT0 coarse solve (1..200) */
+    int32_t       keep_rhs;     /* HDG_MIXED_FP32 / HDG_MIXED_BF16, upwind flux: 1 (default) =
+                                   each solve's step 1 keeps z_K = A_K^-1 M_K r_K for a
+                                   recovery with NULL right-hand sides and forms C_K z_K
+                                   from the cell geometry (step 1 reads A_K^-1 M_K instead
+                                   of C_K A_K^-1 M_K: more bytes there, far fewer in step 3);
+                                   0 = step 1 reads C_K A_K^-1 M_K and keeps nothing (for
+                                   solves that are not followed by a recovery)           */
 } hdg_params;
 
 typedef struct {

@@ -44,7 +44,7 @@ class hdg_params(C.Structure):
                 ("p1_omega", C.c_double), ("inner_rtol", C.c_double), ("coarse_mode", C.c_int32),
                 ("reorth", C.c_int32), ("smoother", C.c_int32), ("cheb_theta", C.c_double),
                 ("cheb_delta2", C.c_double), ("cheb_steps", C.c_int32), ("flux", C.c_int32),
-                ("n_coarse", C.c_int32)]
+                ("n_coarse", C.c_int32), ("keep_rhs", C.c_int32)]
 
 
 class hdg_solve_info(C.Structure):

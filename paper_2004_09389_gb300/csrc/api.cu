@@ -168,6 +168,7 @@ std::string check_params(const hdg_params *prm) {
     if (prm->reorth != 0 && prm->reorth != 1) return "reorth must be 0 or 1";
     if (prm->smoother != 0 && prm->smoother != 1) return "smoother must be 0 or 1";
     if (prm->flux != 0 && prm->flux != 1) return "flux must be 0 or 1";
+    if (prm->keep_rhs != 0 && prm->keep_rhs != 1) return "keep_rhs must be 0 or 1";
     if (prm->flux == 1) {
         if (prm->precision != HDG_FP64) return "the Lax-Friedrichs solver runs in HDG_FP64";
         if (prm->p < 1 || prm->p > 2) return "the Lax-Friedrichs solver supports p = 1 and 2";
@@ -233,6 +234,8 @@ cudaError_t klaunch(hdg_handle *h, int cat, int nk, F &&f) {
 #define KL(cat, nk, expr) klaunch(h, (cat), (nk), [&]() { return (expr); })
 
 }  // namespace
+
+bool hdg::solve_kept_z(const hdg_handle *h) { return h && h->ws && h->ws->have_z; }
 
 cudaError_t hdg::account_launch(hdg_handle *h, int cat, int nk, const std::function<cudaError_t()> &fn) {
     return klaunch(h, cat, nk, fn);
@@ -1587,7 +1590,7 @@ int setup_device(hdg_handle *h, const hdg_params *prm) {
     TRY(dalloc(&W.lam_int, W.NT));
     TRY(dalloc(&W.ycell, N * m));
     if (mode_ff(h->prm)) TRY(dalloc(&W.x2, W.NT));
-    if (h->cz_ok) TRY(dalloc(&W.z2, size_t(h->nK) * N));
+    if (h->cz_ok && h->prm.keep_rhs) TRY(dalloc(&W.z2, size_t(h->nK) * N));
     const size_t mm = W.m;
     W.ld = (W.NT + 3) / 4 * 4;
     // one 16-byte group of w per thread (enough loads in flight for the few-vector
@@ -2000,6 +2003,7 @@ void hdg_default_params(hdg_params *prm) {
     prm->cheb_steps = 20;
     prm->flux = 0;
     prm->n_coarse = 20;
+    prm->keep_rhs = 1;
 }
 
 int hdg_setup(const hdg_mesh_desc *mesh, const hdg_params *prm, void *stream, hdg_handle **out) {

@@ -764,6 +764,8 @@ cudaError_t launch_recover_ff(hdg_handle *h, const double *r_u, const double *r_
 cudaError_t launch_rhs_z(hdg_handle *h, const double *r_u, const double *r_h, double *g, double *ycell, float2 *z2,
                          double *copy_u, double *copy_h, const NormOut &nrm = NormOut());
 cudaError_t launch_recover_z(hdg_handle *h, const float2 *z2, const double *lam, double *u, double *hout);
+// whether the last solve's step 1 kept z_K (hdg_recover_dev may then take NULL right-hand sides)
+bool solve_kept_z(const hdg_handle *h);
 cudaError_t launch_recover(hdg_handle *h, const double *r_u, const double *r_h, const double *lam,
                            double *u, double *hout);
 

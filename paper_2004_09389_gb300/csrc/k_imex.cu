@@ -467,7 +467,9 @@ extern "C" int hdg_imex_step_dev(hdg_handle *h, int scheme, double theta, double
                 acc.est_rel_res = std::max(acc.est_rel_res, si.est_rel_res);
                 if (rc && !status) status = rc;
                 if (rc == HDG_ECUDA || rc == HDG_ENAN) break;
-                rc = hdg_recover_dev(h, R, R + nu_, nullptr, Q, Q + nu_);
+                // the stage's recovery from what its step 1 kept (two-float handles), else from R
+                const bool kz = solve_kept_z(h);
+                rc = hdg_recover_dev(h, kz ? nullptr : R, kz ? nullptr : R + nu_, nullptr, Q, Q + nu_);
                 if (rc) return rc;
                 Qi = Q;
             } else {

@@ -65,3 +65,10 @@ def test_setup_rejects_bad_arguments_without_gpu(lib_path):
     rc = lib.hdg_setup(None, ctypes.byref(prm), None, ctypes.byref(h))
     assert rc == _lib.HDG_EINVAL and not h.value
     assert b"reorth must be" in lib.hdg_last_error(None)
+    # keep_rhs, the struct's last field: 1 by default, 0 or 1 only
+    prm = _lib.default_params()
+    assert prm.keep_rhs == 1
+    prm.keep_rhs = 2
+    rc = lib.hdg_setup(None, ctypes.byref(prm), None, ctypes.byref(h))
+    assert rc == _lib.HDG_EINVAL and not h.value
+    assert b"keep_rhs must be" in lib.hdg_last_error(None)

@@ -13,7 +13,9 @@ lambda_K without reading r or A_K^-1 M_K again.
   1e-10, as in the mixed-precision parity test): a wrong C_K z_K in step 1
   would move lambda;
 * the state rules: one NULL right-hand side is HDG_EINVAL, and after the
-  operator changes (hdg_set_tau) nothing is kept until the next solve.
+  operator changes (hdg_set_tau) nothing is kept until the next solve;
+* keep_rhs = 0 (step 1 from the stored C_K A_K^-1 M_K, nothing kept) solves to
+  the same lambda and refuses a recovery with NULL right-hand sides.
 """
 import numpy as np
 import pytest
@@ -109,3 +111,31 @@ def test_null_right_hand_side_rules():
     assert _rel(u.cpu().numpy(), u0) <= 1e-8
     assert _rel(u_first, u0) > 1e-6                     # the first recovery belonged to the old tau
     s.close()
+
+
+def test_keep_rhs_off_keeps_nothing_and_solves_the_same():
+    """keep_rhs = 0: step 1 reads C_K A_K^-1 M_K and keeps nothing for the
+    recovery; the solve reaches the same lambda (both to rtol 1e-10)."""
+    from paper_2004_09389_gb300 import HDGSolver, HDGError, HDG_MIXED_FP32
+    mesh, prob, (tau, g, H, f), ru, rh = _case("sphere", 3)
+    ru_d, rh_d = _dev(ru), _dev(rh)
+    lams = []
+    for keep in (1, 0):
+        s = HDGSolver(mesh, 3, tau, g, H, f_vertex=f, rtol=1e-10, precision=HDG_MIXED_FP32, keep_rhs=keep)
+        lam = torch.zeros((s.n_facets, 4), dtype=torch.float64, device="cuda")
+        u = torch.empty((s.n_cells, 2, s.n_p), dtype=torch.float64, device="cuda")
+        h = torch.empty((s.n_cells, s.n_p), dtype=torch.float64, device="cuda")
+        info = s.solve_dev(ru_d, rh_d, lam)
+        assert info["true_rel_res"] <= 1e-10
+        if keep:
+            s.recover_dev(None, None, None, u, h)
+        else:
+            with pytest.raises(HDGError):
+                s.recover_dev(None, None, None, u, h)
+            s.recover_dev(ru_d, rh_d, None, u, h)
+        torch.cuda.synchronize()
+        (u0, _), _ = prob.solve_condensed(ru, rh)
+        assert _rel(u.cpu().numpy(), u0) <= 1e-8
+        lams.append(lam.cpu().numpy())
+        s.close()
+    assert _rel(lams[1], lams[0]) <= 1e-9
