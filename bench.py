@@ -429,8 +429,9 @@ def gpu_arm(args, rank: int, world: int):
         info = _lib.hdg_solve_info()
 
         def host_step():
-            _lib.check(s.h, s.lib.hdg_solve(s.h, ru_h.data_ptr(), rh_h.data_ptr(), lam_h.data_ptr(), C.byref(info)))
-            _lib.check(s.h, s.lib.hdg_recover(s.h, None, None, None, u_h.data_ptr(), hh_h.data_ptr()))
+            # steps 1-3 through the one-call host entry point (hdg_solve_recover)
+            _lib.check(s.h, s.lib.hdg_solve_recover(s.h, ru_h.data_ptr(), rh_h.data_ptr(), lam_h.data_ptr(),
+                                                    u_h.data_ptr(), hh_h.data_ptr(), C.byref(info)))
 
         for _ in range(args.warmup):
             host_step()

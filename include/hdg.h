@@ -237,6 +237,15 @@ HDG_API int hdg_solve(hdg_handle *h, const double *r_u, const double *r_h, doubl
 HDG_API int hdg_solve_dev(hdg_handle *h, const double *r_u, const double *r_h, double *lambda,
                   hdg_solve_info *info);
 
+/* Steps 1 to 3 with host buffers in one call (Sec. 4.2): hdg_solve, then the
+ * recovery of its solution (hdg_recover with NULL lambda and right-hand
+ * sides), with one stream synchronisation at the end instead of one per call.
+ * lambda ([n_facets][p+1]), u and h_out receive the results, info may be NULL.
+ * Returns the solve's status when it is not HDG_OK (HDG_ENOCONV / HDG_EBREAKDOWN
+ * / HDG_ENAN with the last iterate and its recovery), else the recovery's. */
+HDG_API int hdg_solve_recover(hdg_handle *h, const double *r_u, const double *r_h, double *lambda, double *u,
+                              double *h_out, hdg_solve_info *info);
+
 /* Step 3 with host buffers: (u, h) from lambda and the right-hand side.
  * lambda may be NULL to use the handle's last solution; r_u and r_h may both
  * be NULL to use the right-hand side of the handle's last hdg_solve (one NULL

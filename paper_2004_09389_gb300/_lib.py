@@ -63,6 +63,7 @@ class HDGError(RuntimeError):
 
 _LIB = None
 EXPORTS = ["hdg_default_params", "hdg_setup", "hdg_condense", "hdg_set_tau", "hdg_solve", "hdg_solve_dev",
+           "hdg_solve_recover",
            "hdg_recover", "hdg_recover_dev", "hdg_trace_apply_dev", "hdg_condensed_rhs_dev",
            "hdg_precond_apply_dev", "hdg_get_sizes", "hdg_get_facets", "hdg_get_cell_schur", "hdg_destroy",
            "hdg_last_error", "hdg_profile_enable", "hdg_profile_read", "hdg_condensed_rhs_noalloc_dev",
@@ -95,6 +96,7 @@ def load() -> C.CDLL:
     lib.hdg_set_tau.argtypes = [vp, C.c_double]
     for name in ("hdg_solve", "hdg_solve_dev"):
         getattr(lib, name).argtypes = [vp, vp, vp, vp, C.POINTER(hdg_solve_info)]
+    lib.hdg_solve_recover.argtypes = [vp, vp, vp, vp, vp, vp, C.POINTER(hdg_solve_info)]
     for name in ("hdg_recover", "hdg_recover_dev"):
         getattr(lib, name).argtypes = [vp, vp, vp, vp, vp, vp]
     lib.hdg_trace_apply_dev.argtypes = [vp, vp, vp]

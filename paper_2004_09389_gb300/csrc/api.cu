@@ -2184,7 +2184,10 @@ int hdg_solve_dev(hdg_handle *h, const double *r_u, const double *r_h, double *l
     return rc;
 }
 
-int hdg_solve(hdg_handle *h, const double *r_u, const double *r_h, double *lambda, hdg_solve_info *info) {
+namespace {
+// hdg_solve, ending with a stream synchronisation when sync is set
+int solve_host(hdg_handle *h, const double *r_u, const double *r_h, double *lambda, hdg_solve_info *info,
+               bool sync) {
     int rc = require_condensed(h);
     if (rc) return rc;
     if (!r_u || !r_h || !lambda) return fail(h, HDG_EINVAL, "NULL pointer argument");
@@ -2213,10 +2216,26 @@ int hdg_solve(hdg_handle *h, const double *r_u, const double *r_h, double *lambd
         TRY(KL(HDG_PROF_LAYOUT, 1, launch_to_external(h, W.x, W.lam_ext)));
         TRY(cudaMemcpyAsync(lambda, W.lam_ext, sizeof(double) * W.NT, cudaMemcpyDeviceToHost, s));
     }
-    TRY(cudaStreamSynchronize(s));
+    if (sync) TRY(cudaStreamSynchronize(s));
     W.have_rhs = true;
     if (info) *info = loc;
     return rc;
+}
+}  // namespace
+
+int hdg_solve(hdg_handle *h, const double *r_u, const double *r_h, double *lambda, hdg_solve_info *info) {
+    return solve_host(h, r_u, r_h, lambda, info, true);
+}
+
+int hdg_solve_recover(hdg_handle *h, const double *r_u, const double *r_h, double *lambda, double *u, double *h_out,
+                      hdg_solve_info *info) {
+    if (h && (!u || !h_out)) return fail(h, HDG_EINVAL, "NULL output pointer");
+    // steps 1 and 2 without the closing synchronisation, step 3 from what they left
+    // in the handle (this solve's lambda and right-hand side); one synchronisation
+    const int rc = solve_host(h, r_u, r_h, lambda, info, false);
+    if (rc == HDG_ECUDA || rc == HDG_EINVAL || rc == HDG_ESTATE) return rc;
+    const int rc2 = hdg_recover(h, nullptr, nullptr, nullptr, u, h_out);
+    return rc ? rc : rc2;
 }
 
 int hdg_recover_dev(hdg_handle *h, const double *r_u, const double *r_h, const double *lambda, double *u,

@@ -95,6 +95,21 @@ class HDGSolver:
         L.check(self.h, rc, allow=(L.HDG_ENOCONV, L.HDG_EBREAKDOWN) if allow_fail else ())
         return lam, info.as_dict()
 
+    def solve_recover(self, r_u: np.ndarray, r_h: np.ndarray, allow_fail: bool = False):
+        """Steps 1-3 from host arrays in one call (hdg_solve_recover); returns
+        (lambda, u, h, info dict)."""
+        ru = np.ascontiguousarray(r_u, dtype=np.float64)
+        rh = np.ascontiguousarray(r_h, dtype=np.float64)
+        assert ru.shape == (self.n_cells, 2, self.n_p) and rh.shape == (self.n_cells, self.n_p)
+        lam = np.empty((self.n_facets, self.n_trace // self.n_facets))
+        u = np.empty((self.n_cells, 2, self.n_p))
+        h = np.empty((self.n_cells, self.n_p))
+        info = L.hdg_solve_info()
+        rc = self.lib.hdg_solve_recover(self.h, ru.ctypes.data, rh.ctypes.data, lam.ctypes.data, u.ctypes.data,
+                                        h.ctypes.data, C.byref(info))
+        L.check(self.h, rc, allow=(L.HDG_ENOCONV, L.HDG_EBREAKDOWN) if allow_fail else ())
+        return lam, u, h, info.as_dict()
+
     def recover(self, r_u=None, r_h=None, lam=None):
         """Step 3 from host arrays; None selects the last solve's data."""
         u = np.empty((self.n_cells, 2, self.n_p))
