@@ -72,3 +72,17 @@ def test_setup_rejects_bad_arguments_without_gpu(lib_path):
     rc = lib.hdg_setup(None, ctypes.byref(prm), None, ctypes.byref(h))
     assert rc == _lib.HDG_EINVAL and not h.value
     assert b"keep_rhs must be" in lib.hdg_last_error(None)
+
+
+def test_step_entry_points_reject_a_null_handle_without_gpu(lib_path):
+    """Steps 1-3 (one call or separate) check the handle on the host before any
+    CUDA call: a NULL handle is HDG_EINVAL."""
+    from paper_2004_09389_gb300 import _lib
+    lib = _lib.load()
+    info = _lib.hdg_solve_info()
+    buf = (ctypes.c_double * 8)()
+    p = ctypes.addressof(buf)
+    assert lib.hdg_solve_recover(None, p, p, p, p, p, ctypes.byref(info)) == _lib.HDG_EINVAL
+    assert lib.hdg_solve(None, p, p, p, ctypes.byref(info)) == _lib.HDG_EINVAL
+    assert lib.hdg_recover(None, None, None, None, p, p) == _lib.HDG_EINVAL
+    assert lib.hdg_recover_dev(None, None, None, None, p, p) == _lib.HDG_EINVAL
